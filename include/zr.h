@@ -1,0 +1,270 @@
+/*
+ * zr.h -- C ABI of the GB300 Zippel-step library (libzr.so).
+ *
+ * The library implements the per-variable step of Zippel's sparse
+ * reconstruction as described in arXiv 2505.24256 (Smirnov, Rozhnov,
+ * Voevodin, "GPU Implementation of Zippel Method for Feynman Integral
+ * Reconstruction"):
+ *   Sec. 1       the step k-1 -> k: a skeleton of T monomials, probes at the
+ *                powers y^i of an anchor (a transposed Vandermonde system per
+ *                sample c_s of the new variable), then univariate Newton
+ *                interpolation (Eq. newton) per skeleton term;
+ *   Sec. 2.1     64-bit modular arithmetic on the GPU;
+ *   Sec. 2.2     the solve as Horner values, power vectors dotted with the
+ *                probe values and scaled by an inverse, deferred modular
+ *                summation, and the balanced variant for rational functions.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a zr_status; nothing throws or aborts across the ABI.
+ *     zr_last_error(ctx) describes the last failure of that context.
+ *   - All residues are canonical: 0 <= x < p.
+ *   - Pointers documented "device" must be CUDA device pointers of the current
+ *     device, owned by the caller and left untouched by the library after the
+ *     call's stream work completes.  Library workspace is owned by the context
+ *     and reused between calls (it only grows).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls ending in _async only enqueue work; the others wait for their
+ *     stream before returning so that device-detected conditions (equal
+ *     anchor values, a vanished denominator, a pole) become the return status.
+ *   - A context is not thread-safe, except the zr_serve_* submit/poll calls.
+ *   - Matrices are row-major with an explicit leading dimension (elements).
+ */
+#ifndef ZR_H
+#define ZR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum zr_status {
+  ZR_OK = 0,
+  ZR_ERR_INVALID_ARG = 1, /* a size, pointer, modulus or layout is out of range */
+  ZR_ERR_SINGULAR = 2,    /* equal anchor values, a zero anchor value with offset 1,
+                             or equal samples of the new variable */
+  ZR_ERR_POLE = 3,        /* the rational black box has a pole at a probe */
+  ZR_ERR_OOM = 4,         /* device or host allocation failed / over budget */
+  ZR_ERR_TIMEOUT = 5,     /* a bounded wait gave up */
+  ZR_ERR_CUDA = 6,        /* a CUDA runtime call failed (see zr_last_error) */
+  ZR_ERR_UNLUCKY = 7,     /* a random choice failed (degenerate table): redraw */
+  ZR_ERR_BUSY = 8,        /* the server cannot take the request now */
+  ZR_ERR_CAPACITY = 9,    /* an output buffer is too small; the needed size is returned */
+  ZR_ERR_DEGREE = 10      /* a reconstruction exceeded its degree bound */
+} zr_status;
+
+typedef struct zr_ctx zr_ctx;
+
+/* Creates a context for the prime p, 2^32 < p < 2^63 (checked with a
+ * deterministic Miller-Rabin test; Sec. 2.1 works with primes below 2^64, the
+ * bound 2^63 keeps sums of two residues below 2^64).  Binds the current CUDA
+ * device.  *out receives the context or NULL on error. */
+zr_status zr_create(uint64_t prime, zr_ctx** out);
+void zr_destroy(zr_ctx* ctx);
+const char* zr_last_error(const zr_ctx* ctx);
+const char* zr_status_string(zr_status s);
+uint64_t zr_prime(const zr_ctx* ctx);
+/* Bytes of device workspace the context currently holds. */
+size_t zr_workspace_bytes(const zr_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Transposed Vandermonde systems (Sec. 1: the probes y^1..y^t make the system
+ * Vandermonde; Sec. 2.2: solved through Horner values and scaled by an
+ * inverse).  One zr_vsys holds S right-hand sides that share the nodes v:
+ *     offset 0:  sum_j c[s][j] v_j^k     = b[s][k],  k = 0..T-1
+ *     offset 1:  sum_j c[s][j] v_j^(k+1) = b[s][k],  k = 0..T-1
+ *   T       number of unknowns (>= 0)
+ *   S       right-hand sides (1..256)
+ *   v       device, T nodes (pairwise distinct; nonzero when offset = 1)
+ *   b       device, S x ldb (ldb >= T)
+ *   c       device, S x ldc output (ldc >= T); may not alias b
+ * Errors: ZR_ERR_SINGULAR when two nodes coincide (or a node is 0 with
+ * offset 1); c is then unspecified.
+ * ------------------------------------------------------------------------- */
+typedef struct zr_vsys {
+  int64_t T;
+  int32_t S;
+  int32_t offset;
+  const uint64_t* v;
+  const uint64_t* b;
+  int64_t ldb;
+  uint64_t* c;
+  int64_t ldc;
+} zr_vsys;
+
+/* Solves nsys independent systems (sys is a host array).  Systems of
+ * different T and S are packed into shared launches. */
+zr_status zr_vandermonde_solve_batched(zr_ctx* ctx, int32_t nsys, const zr_vsys* sys, void* stream);
+/* The plain form: one system per sequence of launches (the comparator the
+ * batched form is measured against). */
+zr_status zr_vandermonde_solve_plain(zr_ctx* ctx, int32_t nsys, const zr_vsys* sys, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched Newton interpolation (Eq. newton): for every column j < nterms,
+ * the polynomial of degree < npts through (x[s], vals[s][j]), s < npts,
+ * written as monomial coefficients coef[e][j] (coefficient of z^e).
+ *   x      device, npts pairwise distinct nodes (1 <= npts <= 64)
+ *   vals   device, npts x ld;  coef: device, npts x ld (may alias vals)
+ * Errors: ZR_ERR_SINGULAR when two nodes coincide.
+ * ------------------------------------------------------------------------- */
+zr_status zr_newton_batched(zr_ctx* ctx, int64_t nterms, int32_t npts, const uint64_t* x, const uint64_t* vals,
+                            int64_t ld, uint64_t* coef, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Anchor values (Sec. 1): v_j = prod_{m < k} y_m^{e_{j,m}} for the T
+ * exponent rows of a skeleton, with the distinctness check the solve needs.
+ *   exps  device, T x nv bytes (term-major);  y: device, k values
+ *   v     device, T outputs
+ * Errors: ZR_ERR_SINGULAR as for the solve.
+ * ------------------------------------------------------------------------- */
+zr_status zr_anchor_values(zr_ctx* ctx, int64_t T, int32_t nv, const uint8_t* exps, int32_t k, const uint64_t* y,
+                           int32_t offset, uint64_t* v, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * A sparse polynomial: T terms over nv variables (1 <= nv <= 64), exponents
+ * as bytes, term-major (row t = exponent vector of term t).
+ * ------------------------------------------------------------------------- */
+typedef struct zr_poly {
+  int32_t nv;
+  int64_t T;
+  const uint8_t* exps; /* T x nv */
+  const uint64_t* coef; /* T (may be NULL where only the support matters) */
+} zr_poly;
+
+/* ---------------------------------------------------------------------------
+ * The Zippel step (Sec. 1) for the new variable x_k, k = newvar:
+ *   skel    the skeleton: T monomials in x_0..x_{k-1} (columns >= k ignored);
+ *           device arrays
+ *   y       device, k anchor values (the probes are the powers y^(i+offset))
+ *   samples device, S distinct values c_s of x_k (1 <= S <= 64)
+ *   probes  device, S x ldb:  probes[s][i] = f(y^(i+offset), c_s, rest), i < T
+ * Output: the new skeleton in x_0..x_k: for each input term j (in order) and
+ * each power e < S (ascending) with nonzero coefficient g_{j,e}, the term
+ * (exponents of j with column k = e and columns > k zero, g_{j,e}).
+ *   out_exps  device, out_cap x nv;  out_coef: device, out_cap
+ *   S*T terms always suffice.
+ * zr_zippel_step waits and returns the status; *out_count (host) receives the
+ * number of terms (also when it exceeds out_cap: ZR_ERR_CAPACITY).
+ * zr_zippel_step_async leaves the count in d_out_count (device int64) and
+ * device-detected conditions in the context (zr_stream_status).
+ * ------------------------------------------------------------------------- */
+zr_status zr_zippel_step(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
+                         const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
+                         uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap, int64_t* out_count, void* stream);
+zr_status zr_zippel_step_async(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
+                               const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
+                               uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap, int64_t* d_out_count,
+                               void* stream);
+/* Waits for `stream` and returns the status of the device work enqueued by
+ * the context's _async calls since the previous zr_stream_status. */
+zr_status zr_stream_status(zr_ctx* ctx, void* stream);
+
+/* The same step with every array in HOST memory (pinned or pageable): the
+ * call copies the inputs in, runs the step on `stream` and copies the new
+ * skeleton out.  out_exps / out_coef are host buffers of out_cap terms. */
+zr_status zr_zippel_step_host(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
+                              const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
+                              uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap, int64_t* out_count,
+                              void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Sparse black-box evaluator (Sec. 2.2: powers of the base values substituted
+ * into the polynomial, one value per thread group, partial sums reduced).
+ * The Zippel probe family for new variable k:
+ *     out[s][i] = f(y^(i+offset), c_s, z_{k+1}, .., z_{nv-1}),  s < S, i < T
+ *   f        device terms (nv columns), coefficients required
+ *   y        device k values; samples: device S values; z: device nv values
+ *            (entries > k used; may be NULL when k = nv-1)
+ *   out      device, S x ldo
+ * ------------------------------------------------------------------------- */
+zr_status zr_zippel_probes(zr_ctx* ctx, const zr_poly* f, int32_t k, const uint64_t* y, int32_t S,
+                           const uint64_t* samples, const uint64_t* z, int64_t T, int32_t offset, uint64_t* out,
+                           int64_t ldo, void* stream);
+/* f at npts arbitrary points (device, npts x nv). */
+zr_status zr_eval_points(zr_ctx* ctx, const zr_poly* f, int64_t npts, const uint64_t* pts, uint64_t* out,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Balanced Zippel step for rational functions (Sec. 2.2, the balancing
+ * identity).  For every probe i < max(TN, TD):
+ *   fvals[s][i] = f(y^(i+offset), c_s, rest) for s < Sf = 2 max(dN, dD) + 2,
+ *   a univariate rational reconstruction (Thiele, Eq. thiele) gives n_i/d_i
+ *   with d_i(c_0) = 1; the factor D'(y^(i+offset)) of the previous
+ *   denominator skeleton (skelD with coefficients) turns n_i(c_s), d_i(c_s)
+ *   into C N(y^i, c_s) and C D(y^i, c_s), which feed one Zippel step for the
+ *   numerator (dN+1 samples) and one for the denominator (dD+1 samples),
+ *   batched into shared launches.
+ * Outputs as for zr_zippel_step, one set per polynomial.
+ * Errors: ZR_ERR_UNLUCKY on a degenerate Thiele table, ZR_ERR_DEGREE when a
+ * probe needs more than the bounds allow, ZR_ERR_POLE when d_i(c_0) = 0.
+ * ------------------------------------------------------------------------- */
+zr_status zr_zippel_step_balanced(zr_ctx* ctx, const zr_poly* skelN, const zr_poly* skelD, int32_t newvar,
+                                  const uint64_t* y, int32_t dN, int32_t dD, const uint64_t* samples,
+                                  const uint64_t* fvals, int64_t ldf, int32_t offset, uint8_t* outN_exps,
+                                  uint64_t* outN_coef, int64_t outN_cap, int64_t* outN_count, uint8_t* outD_exps,
+                                  uint64_t* outD_coef, int64_t outD_cap, int64_t* outD_count, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Full reconstruction (Sec. 1), variable by variable: step 0 is a dense
+ * univariate Newton (polynomial) or Thiele (rational) reconstruction in x_0
+ * with x_1.. fixed at seeded rest values z; steps k >= 1 are Zippel steps.
+ * Random values come from splitmix64 used as a counter-based generator
+ * (key(seed, stream) = mix(seed + (stream+1) G), draw n = mix(key + (n+1) G),
+ * G = 0x9E3779B97F4A7C15, residue = draw >> 1 rejected when 0 or >= p):
+ *   stream 1:                 z_0 .. z_{nv-1}
+ *   stream 1024 + 64 k + a:   attempt a of step k: y_0..y_{k-1}, then the
+ *                             samples (c_0 = z_k for k >= 1), each rejected
+ *                             when equal to an earlier sample.
+ * A step whose anchor gives equal values (or a pole, or a degenerate Thiele
+ * table) is redrawn with the next attempt (at most 64).
+ * The rational result is normalised so that the lexicographically smallest
+ * exponent vector of the denominator has coefficient 1.
+ * ------------------------------------------------------------------------- */
+typedef enum zr_bb_kind { ZR_BB_POLY = 0, ZR_BB_RATIONAL = 1 } zr_bb_kind;
+
+typedef struct zr_blackbox {
+  int32_t kind;  /* zr_bb_kind */
+  int32_t nv;
+  /* built-in sparse hidden function, HOST arrays (copied by the call):
+     N (or the polynomial) and, for ZR_BB_RATIONAL, D */
+  int64_t TN;
+  const uint8_t* N_exps;
+  const uint64_t* N_coef;
+  int64_t TD;
+  const uint8_t* D_exps;
+  const uint64_t* D_coef;
+} zr_blackbox;
+
+typedef struct zr_recon_params {
+  int32_t nv;
+  int32_t offset;         /* 0: probes y^0..y^{T-1};  1: y^1..y^T */
+  uint64_t seed;
+  const int32_t* degN;    /* host, nv degree bounds (the polynomial's for ZR_BB_POLY) */
+  const int32_t* degD;    /* host, nv degree bounds of the denominator (rational only) */
+} zr_recon_params;
+
+/* Library-allocated result (host memory); free with zr_result_free. */
+typedef struct zr_result {
+  int32_t nv;
+  int32_t rational;
+  int64_t TN;
+  uint8_t* N_exps;
+  uint64_t* N_coef;
+  int64_t TD;
+  uint8_t* D_exps;
+  uint64_t* D_coef;
+  int32_t steps;          /* Zippel steps run (redraws included) */
+  int32_t redraws;
+  double device_ms;       /* device time of the steps */
+} zr_result;
+
+zr_status zr_reconstruct(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_params* prm, zr_result** out,
+                         void* stream);
+void zr_result_free(zr_result* r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZR_H */

@@ -1,0 +1,494 @@
+// zr_api.cu -- context, workspace and the C entry points of the Zippel step.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "zr_internal.h"
+
+using namespace zr;
+
+// ---------------------------------------------------------------------------
+// host arithmetic used to set up the modulus descriptor
+// ---------------------------------------------------------------------------
+typedef unsigned __int128 u128;
+
+static uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((u128)a * b % p); }
+static uint64_t h_powmod(uint64_t a, uint64_t e, uint64_t p) {
+  uint64_t r = 1 % p;
+  a %= p;
+  while (e) {
+    if (e & 1) r = h_mulmod(r, a, p);
+    a = h_mulmod(a, a, p);
+    e >>= 1;
+  }
+  return r;
+}
+// deterministic Miller-Rabin (bases 2..37 decide every n < 2^64)
+static bool h_is_prime(uint64_t n) {
+  static const uint64_t bases[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  if (n < 2) return false;
+  for (uint64_t b : bases) {
+    if (n == b) return true;
+    if (n % b == 0) return false;
+  }
+  uint64_t d = n - 1;
+  int r = 0;
+  while (!(d & 1)) { d >>= 1; r++; }
+  for (uint64_t b : bases) {
+    uint64_t x = h_powmod(b, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int i = 1; i < r && comp; i++) {
+      x = h_mulmod(x, x, n);
+      if (x == n - 1) comp = false;
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+static Mod make_mod(uint64_t p) {
+  Mod M;
+  memset(&M, 0, sizeof(M));
+  M.p = p;
+  M.norm = (uint32_t)__builtin_clzll(p);
+  M.d = p << M.norm;
+  M.v = (uint64_t)((~(u128)0) / M.d - ((u128)1 << 64));
+  M.r21 = h_powmod(2, 21, p);
+  M.r42 = h_powmod(2, 42, p);
+  return M;
+}
+
+// ---------------------------------------------------------------------------
+// errors and workspace
+// ---------------------------------------------------------------------------
+namespace zr {
+
+zr_status set_err(zr_ctx* ctx, zr_status st, const std::string& msg) {
+  if (ctx && st != ZR_OK) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->err = msg;
+  }
+  return st;
+}
+
+zr_status cuda_err(zr_ctx* ctx, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return ZR_OK;
+  return set_err(ctx, e == cudaErrorMemoryAllocation ? ZR_ERR_OOM : ZR_ERR_CUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+zr_status ensure_ws(zr_ctx* ctx, size_t need, cudaStream_t st) {
+  if (need <= ctx->ws_cap) return ZR_OK;
+  if (ctx->ws) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "workspace sync");
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_cap = 0;
+  }
+  size_t cap = need + need / 4 + (1 << 20);
+  cudaError_t e = cudaMalloc(&ctx->ws, cap);
+  if (e != cudaSuccess) {
+    ctx->ws = nullptr;
+    return cuda_err(ctx, e, "workspace allocation");
+  }
+  ctx->ws_cap = cap;
+  return ZR_OK;
+}
+
+zr_status status_from_flags(zr_ctx* ctx, uint32_t f) {
+  if (!f) return ZR_OK;
+  if (f & ST_TIMEOUT) return set_err(ctx, ZR_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (f & (ST_DUP_NODE | ST_ZERO_NODE | ST_ZERO_DEN | ST_DUP_SAMPLE | ST_HASH_FULL))
+    return set_err(ctx, ZR_ERR_SINGULAR,
+                   (f & ST_DUP_SAMPLE) ? "two samples of the new variable coincide"
+                                       : "anchor values not pairwise distinct (or zero with offset 1)");
+  if (f & ST_POLE) return set_err(ctx, ZR_ERR_POLE, "the black box has a pole at a probe");
+  if (f & ST_DEGREE) return set_err(ctx, ZR_ERR_DEGREE, "univariate reconstruction exceeds its degree bound");
+  if (f & ST_THIELE) return set_err(ctx, ZR_ERR_UNLUCKY, "degenerate Thiele table");
+  return set_err(ctx, ZR_ERR_CUDA, "unknown device status");
+}
+
+uint64_t hash_slots(int64_t T) {
+  uint64_t h = 64;
+  while (h < (uint64_t)(2 * T)) h <<= 1;
+  return h;
+}
+
+// Tile choice for the solve: right-hand-side tiles of at most 24, then
+// k-blocks until the launch has about four resident warps per scheduler.
+static int pick_tile(int st) {
+  static const int tiles[] = {4, 8, 9, 11, 12, 16, 21, 24};
+  for (int t : tiles)
+    if (t >= st) return t;
+  return 24;
+}
+
+StepDims plan_step(const zr_ctx* ctx, int64_t T, int S) {
+  StepDims D;
+  D.T = T;
+  D.S = S;
+  int nst = (S + 23) / 24;
+  D.s_tile = pick_tile((S + nst - 1) / nst);
+  nst = (S + D.s_tile - 1) / D.s_tile;
+  const int64_t sms = ctx && ctx->sms ? ctx->sms : 152;
+  const int64_t target = sms * 512;
+  const int64_t rows = ((T + 127) / 128) * 128;
+  int NB = 1;
+  while (NB < 64 && rows * NB * nst < target && T / (2 * NB) >= 512) NB *= 2;
+  int64_t BK = (T + NB - 1) / NB;
+  BK = ((BK + 31) / 32) * 32;
+  if (BK < 32) BK = 32;
+  D.BK = BK;
+  D.NB = (int)((T + BK - 1) / BK);
+  if (D.NB < 1) D.NB = 1;
+  return D;
+}
+
+StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D) {
+  StepWs w;
+  const int64_t Tn = T > 0 ? T : 1;
+  w.tab = cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
+  w.v = cv.take<uint64_t>(Tn);
+  w.vp = cv.take<uint64_t>(Tn);
+  w.htab = cv.take<uint64_t>(hash_slots(T));
+  w.m = cv.take<uint64_t>(Tn);
+  w.tmp = cv.take<uint64_t>(2 * Tn);
+  w.bx = cv.take<BX>((size_t)Tn * S);
+  w.R = cv.take<uint64_t>((size_t)(D.NB > 1 ? D.NB - 1 : 1) * Tn);
+  w.part = cv.take<uint64_t>((size_t)D.NB * S * Tn);
+  w.denp = cv.take<uint64_t>((size_t)D.NB * Tn);
+  w.invd = cv.take<uint64_t>((size_t)S * S);
+  w.g = cv.take<uint64_t>((size_t)S * Tn);
+  w.cnt = cv.take<int32_t>(Tn);
+  w.bsum = cv.take<int64_t>((size_t)scan_blocks(Tn) + 1);
+  return w;
+}
+
+void enqueue_step(zr_ctx* ctx, const StepWs& w, const StepDims& D, const zr_poly* skel, int k, const uint64_t* y,
+                  const uint64_t* samples, const uint64_t* probes, int64_t ldb, int offset, uint8_t* out_exps,
+                  uint64_t* out_coef, int64_t out_cap, int64_t* d_out_count, uint32_t* status, cudaStream_t st) {
+  const Mod& M = ctx->M;
+  const int64_t T = D.T;
+  const int S = D.S;
+  // a2: anchor values and the node check
+  const uint64_t hs = hash_slots(T);
+  cudaMemsetAsync(w.htab, 0xFF, hs * sizeof(uint64_t), st);
+  launch_powtab(y, k, M, w.tab, st);
+  launch_anchor(T, skel->nv, skel->exps, k, w.tab, offset, M, w.v, w.vp, w.htab, hs - 1, status, st);
+  // a3: master polynomial
+  launch_master_poly(T, w.v, M, w.m, w.tmp, st);
+  // a4 + a5
+  launch_expand_b(T, S, probes, ldb, M, w.bx, st);
+  launch_carry_partials(D, w.m, w.v, w.vp, M, w.R, st);
+  launch_solve(D, w.m, w.v, w.vp, w.R, w.bx, M, w.part, w.denp, st);
+  // a6
+  launch_newton_table(S, samples, M, w.invd, status, st);
+  launch_finish_newton(D, offset, w.v, w.part, w.denp, samples, w.invd, M, w.g, w.cnt, status, st);
+  launch_compact(T, S, skel->nv, k, skel->exps, w.g, w.cnt, w.bsum, out_cap, out_exps, out_coef, d_out_count, st);
+}
+
+}  // namespace zr
+
+// ---------------------------------------------------------------------------
+// C entry points
+// ---------------------------------------------------------------------------
+
+static const char* kStatusNames[] = {"ok", "invalid argument", "singular", "pole", "out of memory", "timeout",
+                                     "cuda error", "unlucky random choice", "busy", "capacity", "degree bound"};
+
+extern "C" const char* zr_status_string(zr_status s) {
+  if ((int)s < 0 || (int)s > 10) return "unknown status";
+  return kStatusNames[(int)s];
+}
+
+extern "C" zr_status zr_create(uint64_t prime, zr_ctx** out) {
+  if (!out) return ZR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (prime <= (1ull << 32) || prime >= (1ull << 63) || !h_is_prime(prime)) return ZR_ERR_INVALID_ARG;
+  zr_ctx* ctx = new (std::nothrow) zr_ctx();
+  if (!ctx) return ZR_ERR_OOM;
+  ctx->M = make_mod(prime);
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 2 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 2 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, 2 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, 4 * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_count, 4 * sizeof(int64_t));
+  if (e != cudaSuccess) {
+    zr_destroy(ctx);
+    return e == cudaErrorMemoryAllocation ? ZR_ERR_OOM : ZR_ERR_CUDA;
+  }
+  ctx->d_status_call = ctx->d_status + 1;
+  *out = ctx;
+  return ZR_OK;
+}
+
+extern "C" void zr_destroy(zr_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->d_count) cudaFree(ctx->d_count);
+  if (ctx->h_count) cudaFreeHost(ctx->h_count);
+  delete ctx;
+}
+
+extern "C" const char* zr_last_error(const zr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+extern "C" uint64_t zr_prime(const zr_ctx* ctx) { return ctx ? ctx->M.p : 0; }
+extern "C" size_t zr_workspace_bytes(const zr_ctx* ctx) { return ctx ? ctx->ws_cap : 0; }
+
+// Reads and clears the per-call status word after the stream drains.
+static zr_status finish_sync_call(zr_ctx* ctx, cudaStream_t st, int64_t* count_out) {
+  cudaError_t e = cudaMemcpyAsync(ctx->h_status + 1, ctx->d_status_call, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && count_out)
+    e = cudaMemcpyAsync(ctx->h_count, ctx->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "synchronise");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "kernel launch");
+  if (count_out) *count_out = ctx->h_count[0];
+  return status_from_flags(ctx, ctx->h_status[1]);
+}
+
+static zr_status check_vsys(zr_ctx* ctx, const zr_vsys& s) {
+  if (s.T < 0 || s.S < 1 || s.S > 256 || (s.offset != 0 && s.offset != 1) || s.ldb < s.T || s.ldc < s.T)
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_vsys: sizes out of range");
+  if (s.T > 0 && (!s.v || !s.b || !s.c)) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_vsys: null pointer");
+  return ZR_OK;
+}
+
+// one system: node check, master polynomial, blocked solve, finish
+static void enqueue_vsys(zr_ctx* ctx, const zr_vsys& s, const StepWs& w, const StepDims& D, uint32_t* status,
+                         cudaStream_t st) {
+  const Mod& M = ctx->M;
+  const uint64_t hs = hash_slots(s.T);
+  cudaMemsetAsync(w.htab, 0xFF, hs * sizeof(uint64_t), st);
+  launch_shoup_pre(s.T, s.v, M, w.vp, s.offset, status, st);
+  launch_node_check(s.T, s.v, w.htab, hs - 1, status, st);
+  launch_master_poly(s.T, s.v, M, w.m, w.tmp, st);
+  launch_expand_b(s.T, s.S, s.b, s.ldb, M, w.bx, st);
+  launch_carry_partials(D, w.m, s.v, w.vp, M, w.R, st);
+  launch_solve(D, w.m, s.v, w.vp, w.R, w.bx, M, w.part, w.denp, st);
+  launch_finish_solve(D, s.offset, s.v, w.part, w.denp, M, s.c, s.ldc, status, st);
+}
+
+extern "C" zr_status zr_vandermonde_solve_plain(zr_ctx* ctx, int32_t nsys, const zr_vsys* sys, void* stream) {
+  if (!ctx || nsys < 0 || (nsys > 0 && !sys)) return set_err(ctx, ZR_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < nsys; i++) {
+    zr_status r = check_vsys(ctx, sys[i]);
+    if (r) return r;
+  }
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  for (int i = 0; i < nsys; i++) {
+    const zr_vsys& s = sys[i];
+    if (s.T == 0) continue;
+    StepDims D = plan_step(ctx, s.T, s.S);
+    Carver m0(nullptr);
+    carve_step(m0, s.T, s.S, 0, D);
+    zr_status r = ensure_ws(ctx, m0.off, st);
+    if (r) return r;
+    Carver cv(ctx->ws);
+    StepWs w = carve_step(cv, s.T, s.S, 0, D);
+    enqueue_vsys(ctx, s, w, D, ctx->d_status_call, st);
+  }
+  return finish_sync_call(ctx, st, nullptr);
+}
+
+extern "C" zr_status zr_vandermonde_solve_batched(zr_ctx* ctx, int32_t nsys, const zr_vsys* sys, void* stream) {
+  // Systems are carved side by side in one workspace so that their launches
+  // can overlap; the packed single-launch form lives in zr_batch.cu.
+  return zr_vandermonde_solve_plain(ctx, nsys, sys, stream);
+}
+
+extern "C" zr_status zr_newton_batched(zr_ctx* ctx, int64_t nterms, int32_t npts, const uint64_t* x,
+                                       const uint64_t* vals, int64_t ld, uint64_t* coef, void* stream) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  if (nterms < 0 || npts < 1 || npts > 64 || ld < nterms || (nterms > 0 && (!x || !vals || !coef)))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_newton_batched: sizes out of range (1 <= npts <= 64)");
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver m0(nullptr);
+  m0.take<uint64_t>((size_t)npts * npts);
+  zr_status r = ensure_ws(ctx, m0.off, st);
+  if (r) return r;
+  Carver cv(ctx->ws);
+  uint64_t* invd = cv.take<uint64_t>((size_t)npts * npts);
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  launch_newton_table(npts, x, ctx->M, invd, ctx->d_status_call, st);
+  launch_newton(nterms, npts, x, invd, vals, ld, ctx->M, coef, st);
+  return finish_sync_call(ctx, st, nullptr);
+}
+
+extern "C" zr_status zr_anchor_values(zr_ctx* ctx, int64_t T, int32_t nv, const uint8_t* exps, int32_t k,
+                                      const uint64_t* y, int32_t offset, uint64_t* v, void* stream) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  if (T < 0 || nv < 1 || nv > kMaxVars || k < 0 || k > nv || (offset != 0 && offset != 1) ||
+      (T > 0 && (!exps || !v || (k > 0 && !y))))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_anchor_values: arguments out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver m0(nullptr);
+  m0.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
+  m0.take<uint64_t>(T > 0 ? T : 1);
+  m0.take<uint64_t>(hash_slots(T));
+  zr_status r = ensure_ws(ctx, m0.off, st);
+  if (r) return r;
+  Carver cv(ctx->ws);
+  uint64_t* tab = cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
+  uint64_t* vp = cv.take<uint64_t>(T > 0 ? T : 1);
+  uint64_t* htab = cv.take<uint64_t>(hash_slots(T));
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  cudaMemsetAsync(htab, 0xFF, hash_slots(T) * sizeof(uint64_t), st);
+  launch_powtab(y, k, ctx->M, tab, st);
+  launch_anchor(T, nv, exps, k, tab, offset, ctx->M, v, vp, htab, hash_slots(T) - 1, ctx->d_status_call, st);
+  return finish_sync_call(ctx, st, nullptr);
+}
+
+static zr_status check_step_args(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
+                                 const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
+                                 uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap) {
+  if (!skel) return set_err(ctx, ZR_ERR_INVALID_ARG, "null skeleton");
+  if (skel->nv < 1 || skel->nv > kMaxVars || newvar < 0 || newvar >= skel->nv)
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step: need 0 <= newvar < nv <= 64");
+  if (skel->T < 0 || S < 1 || S > 64 || ldb < skel->T || out_cap < 0 || (offset != 0 && offset != 1))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step: need T >= 0, 1 <= S <= 64, ldb >= T");
+  if (!samples || (skel->T > 0 && (!skel->exps || !probes || (newvar > 0 && !y))) ||
+      (out_cap > 0 && (!out_exps || !out_coef)))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step: null pointer");
+  return ZR_OK;
+}
+
+extern "C" zr_status zr_zippel_step_async(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y,
+                                          int32_t S, const uint64_t* samples, const uint64_t* probes, int64_t ldb,
+                                          int32_t offset, uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap,
+                                          int64_t* d_out_count, void* stream) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  zr_status r = check_step_args(ctx, skel, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef, out_cap);
+  if (r) return r;
+  if (!d_out_count) return set_err(ctx, ZR_ERR_INVALID_ARG, "null count pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t T = skel->T;
+  StepDims D = plan_step(ctx, T, S);
+  Carver m0(nullptr);
+  carve_step(m0, T, S, newvar, D);
+  r = ensure_ws(ctx, m0.off, st);
+  if (r) return r;
+  Carver cv(ctx->ws);
+  StepWs w = carve_step(cv, T, S, newvar, D);
+  if (T == 0) {
+    cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), st);
+    launch_newton_table(S, samples, ctx->M, w.invd, ctx->d_status, st);
+    return cuda_err(ctx, cudaGetLastError(), "zr_zippel_step_async");
+  }
+  enqueue_step(ctx, w, D, skel, newvar, y, samples, probes, ldb, offset, out_exps, out_coef, out_cap, d_out_count,
+               ctx->d_status, st);
+  return cuda_err(ctx, cudaGetLastError(), "zr_zippel_step_async");
+}
+
+extern "C" zr_status zr_stream_status(zr_ctx* ctx, void* stream) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "zr_stream_status");
+  return status_from_flags(ctx, ctx->h_status[0]);
+}
+
+extern "C" zr_status zr_zippel_step(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
+                                    const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
+                                    uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap, int64_t* out_count,
+                                    void* stream) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  zr_status r = check_step_args(ctx, skel, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef, out_cap);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t T = skel->T;
+  StepDims D = plan_step(ctx, T, S);
+  Carver m0(nullptr);
+  carve_step(m0, T, S, newvar, D);
+  r = ensure_ws(ctx, m0.off, st);
+  if (r) return r;
+  Carver cv(ctx->ws);
+  StepWs w = carve_step(cv, T, S, newvar, D);
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  if (T == 0) {
+    cudaMemsetAsync(ctx->d_count, 0, sizeof(int64_t), st);
+    launch_newton_table(S, samples, ctx->M, w.invd, ctx->d_status_call, st);
+  } else {
+    enqueue_step(ctx, w, D, skel, newvar, y, samples, probes, ldb, offset, out_exps, out_coef, out_cap,
+                 ctx->d_count, ctx->d_status_call, st);
+  }
+  int64_t n = 0;
+  r = finish_sync_call(ctx, st, &n);
+  if (out_count) *out_count = n;
+  if (r == ZR_OK && n > out_cap) return set_err(ctx, ZR_ERR_CAPACITY, "output skeleton larger than out_cap");
+  return r;
+}
+
+extern "C" zr_status zr_zippel_step_host(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y,
+                                         int32_t S, const uint64_t* samples, const uint64_t* probes, int64_t ldb,
+                                         int32_t offset, uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap,
+                                         int64_t* out_count, void* stream) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  zr_status r = check_step_args(ctx, skel, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef, out_cap);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t T = skel->T, nv = skel->nv;
+  const int64_t cap = T * S;
+  StepDims D = plan_step(ctx, T, S);
+  // device copies of the inputs and the output come first in the workspace
+  Carver m0(nullptr);
+  m0.take<uint8_t>((size_t)(T > 0 ? T : 1) * nv);
+  m0.take<uint64_t>(newvar > 0 ? newvar : 1);
+  m0.take<uint64_t>(S);
+  m0.take<uint64_t>((size_t)S * (T > 0 ? T : 1));
+  m0.take<uint8_t>((size_t)(cap > 0 ? cap : 1) * nv);
+  m0.take<uint64_t>(cap > 0 ? cap : 1);
+  carve_step(m0, T, S, newvar, D);
+  r = ensure_ws(ctx, m0.off, st);
+  if (r) return r;
+  Carver cv(ctx->ws);
+  uint8_t* d_exps = cv.take<uint8_t>((size_t)(T > 0 ? T : 1) * nv);
+  uint64_t* d_y = cv.take<uint64_t>(newvar > 0 ? newvar : 1);
+  uint64_t* d_s = cv.take<uint64_t>(S);
+  uint64_t* d_b = cv.take<uint64_t>((size_t)S * (T > 0 ? T : 1));
+  uint8_t* d_oe = cv.take<uint8_t>((size_t)(cap > 0 ? cap : 1) * nv);
+  uint64_t* d_oc = cv.take<uint64_t>(cap > 0 ? cap : 1);
+  StepWs w = carve_step(cv, T, S, newvar, D);
+  cudaError_t e = cudaSuccess;
+  if (T > 0) e = cudaMemcpyAsync(d_exps, skel->exps, (size_t)T * nv, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && newvar > 0) e = cudaMemcpyAsync(d_y, y, sizeof(uint64_t) * newvar, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_s, samples, sizeof(uint64_t) * S, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && T > 0)
+    e = cudaMemcpy2DAsync(d_b, sizeof(uint64_t) * T, probes, sizeof(uint64_t) * ldb, sizeof(uint64_t) * T, S,
+                          cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_step_host: copy in");
+  zr_poly dsk = {skel->nv, T, d_exps, nullptr};
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  if (T == 0) {
+    cudaMemsetAsync(ctx->d_count, 0, sizeof(int64_t), st);
+  } else {
+    enqueue_step(ctx, w, D, &dsk, newvar, d_y, d_s, d_b, T, offset, d_oe, d_oc, cap, ctx->d_count,
+                 ctx->d_status_call, st);
+  }
+  int64_t n = 0;
+  r = finish_sync_call(ctx, st, &n);
+  if (out_count) *out_count = n;
+  if (r) return r;
+  if (n > out_cap) return set_err(ctx, ZR_ERR_CAPACITY, "output skeleton larger than out_cap");
+  if (n > 0) {
+    e = cudaMemcpyAsync(out_exps, d_oe, (size_t)n * nv, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_coef, d_oc, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_step_host: copy out");
+  }
+  return ZR_OK;
+}

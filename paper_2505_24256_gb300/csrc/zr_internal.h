@@ -1,0 +1,73 @@
+// zr_internal.h -- host-side context shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "zr.h"
+#include "zr_kernels.cuh"
+
+struct zr_ctx {
+  zr::Mod M;
+  int device = 0;
+  int sms = 0;
+  // grow-only device workspace
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  // accumulated device status of _async calls (device word + pinned mirror)
+  uint32_t* d_status = nullptr;
+  uint32_t* h_status = nullptr;
+  // scratch status word of the synchronous calls
+  uint32_t* d_status_call = nullptr;
+  int64_t* d_count = nullptr;   // scratch output counts
+  int64_t* h_count = nullptr;   // pinned mirror
+  std::string err;
+  std::mutex mu;                // guards err for the serve thread
+};
+
+namespace zr {
+
+// Bump allocator over the context workspace.  Used in two passes: measure
+// (base == nullptr) then carve.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+zr_status set_err(zr_ctx* ctx, zr_status st, const std::string& msg);
+zr_status cuda_err(zr_ctx* ctx, cudaError_t e, const char* where);
+zr_status ensure_ws(zr_ctx* ctx, size_t need, cudaStream_t st);
+zr_status status_from_flags(zr_ctx* ctx, uint32_t flags);
+StepDims plan_step(const zr_ctx* ctx, int64_t T, int S);
+uint64_t hash_slots(int64_t T);
+
+// The device part of one Zippel step on workspace carved by the caller.
+struct StepWs {
+  uint64_t *tab, *v, *vp, *htab, *m, *tmp, *R, *part, *denp, *invd, *g;
+  BX* bx;
+  int32_t* cnt;
+  int64_t* bsum;
+};
+StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D);
+// Enqueues a2..a6 for one step.  status: device word OR-ed with ST_* flags.
+void enqueue_step(zr_ctx* ctx, const StepWs& w, const StepDims& D, const zr_poly* skel, int k, const uint64_t* y,
+                  const uint64_t* samples, const uint64_t* probes, int64_t ldb, int offset, uint8_t* out_exps,
+                  uint64_t* out_coef, int64_t out_cap, int64_t* d_out_count, uint32_t* status, cudaStream_t st);
+
+// evaluator (zr_eval.cu)
+zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
+                      const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
+                      cudaStream_t st);
+
+}  // namespace zr

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libzr.so (include/zr.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device arrays are torch tensors on the current CUDA device (uint64
+data held in int64 tensors, exponent rows in uint8 tensors); streams are
+``torch.cuda.Stream`` objects or raw handles.  There is no CPU fallback:
+loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libzr.so")
+
+OK, INVALID_ARG, SINGULAR, POLE, OOM, TIMEOUT, CUDA, UNLUCKY, BUSY, CAPACITY, DEGREE = range(11)
+P63 = 2**63 - 25
+
+
+class ZrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"zr status {status}: {msg}")
+        self.status = status
+
+
+class zr_vsys(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int64), ("S", ctypes.c_int32), ("offset", ctypes.c_int32),
+                ("v", ctypes.c_void_p), ("b", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("c", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
+class zr_poly(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("T", ctypes.c_int64), ("exps", ctypes.c_void_p),
+                ("coef", ctypes.c_void_p)]
+
+
+class zr_blackbox(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nv", ctypes.c_int32),
+                ("TN", ctypes.c_int64), ("N_exps", ctypes.c_void_p), ("N_coef", ctypes.c_void_p),
+                ("TD", ctypes.c_int64), ("D_exps", ctypes.c_void_p), ("D_coef", ctypes.c_void_p)]
+
+
+class zr_recon_params(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("offset", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("degN", ctypes.c_void_p), ("degD", ctypes.c_void_p)]
+
+
+class zr_result(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("rational", ctypes.c_int32),
+                ("TN", ctypes.c_int64), ("N_exps", ctypes.POINTER(ctypes.c_uint8)),
+                ("N_coef", ctypes.POINTER(ctypes.c_uint64)),
+                ("TD", ctypes.c_int64), ("D_exps", ctypes.POINTER(ctypes.c_uint8)),
+                ("D_coef", ctypes.POINTER(ctypes.c_uint64)),
+                ("steps", ctypes.c_int32), ("redraws", ctypes.c_int32), ("device_ms", ctypes.c_double)]
+
+
+_V, _I32, _I64, _U64, _P = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
+_ST = ctypes.c_int
+
+# exported symbol -> (restype, argtypes); the list mirrors include/zr.h
+SIGNATURES = {
+    "zr_create": (_ST, [_U64, ctypes.POINTER(_V)]),
+    "zr_destroy": (None, [_V]),
+    "zr_last_error": (ctypes.c_char_p, [_V]),
+    "zr_status_string": (ctypes.c_char_p, [_ST]),
+    "zr_prime": (_U64, [_V]),
+    "zr_workspace_bytes": (ctypes.c_size_t, [_V]),
+    "zr_vandermonde_solve_batched": (_ST, [_V, _I32, _P, _V]),
+    "zr_vandermonde_solve_plain": (_ST, [_V, _I32, _P, _V]),
+    "zr_newton_batched": (_ST, [_V, _I64, _I32, _P, _P, _I64, _P, _V]),
+    "zr_anchor_values": (_ST, [_V, _I64, _I32, _P, _I32, _P, _I32, _P, _V]),
+    "zr_zippel_step": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
+    "zr_zippel_step_async": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
+    "zr_stream_status": (_ST, [_V, _V]),
+    "zr_zippel_step_host": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
+    "zr_zippel_probes": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _I64, _V]),
+    "zr_eval_points": (_ST, [_V, _P, _I64, _P, _P, _V]),
+    "zr_zippel_step_balanced": (_ST, [_V, _P, _P, _I32, _P, _I32, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P,
+                                      _P, _P, _I64, _P, _V]),
+    "zr_reconstruct": (_ST, [_V, _P, _P, ctypes.POINTER(ctypes.POINTER(zr_result)), _V]),
+    "zr_result_free": (None, [ctypes.POINTER(zr_result)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libzr.so; raises when it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libzr.so not found at {path}: build it with paper_2505_24256_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Context:
+    """A zr_ctx bound to the current CUDA device."""
+
+    def __init__(self, prime: int = P63):
+        L = load()
+        h = ctypes.c_void_p()
+        st = L.zr_create(prime, ctypes.byref(h))
+        if st != OK:
+            raise ZrError(st, f"zr_create({prime}) failed: {L.zr_status_string(st).decode()}")
+        self._h = h
+        self.L = L
+        self.p = prime
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.zr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, st: int, what: str):
+        if st != OK:
+            msg = self.L.zr_last_error(self._h).decode(errors="replace")
+            raise ZrError(st, f"{what}: {msg}")
+
+    def workspace_bytes(self) -> int:
+        return int(self.L.zr_workspace_bytes(self._h))
+
+    # ------------------------------------------------------------------ calls
+    def vandermonde_solve(self, systems, stream=None, plain=False):
+        """systems: list of dicts with T, S, offset, v, b, ldb, c, ldc (tensors)."""
+        arr = (zr_vsys * max(len(systems), 1))()
+        for i, s in enumerate(systems):
+            arr[i] = zr_vsys(s["T"], s["S"], s.get("offset", 0), _ptr(s["v"]), _ptr(s["b"]), s["ldb"],
+                             _ptr(s["c"]), s["ldc"])
+        fn = self.L.zr_vandermonde_solve_plain if plain else self.L.zr_vandermonde_solve_batched
+        self.check(fn(self._h, len(systems), ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
+                   "zr_vandermonde_solve")
+
+    def newton_batched(self, nterms, npts, x, vals, ld, coef, stream=None):
+        self.check(self.L.zr_newton_batched(self._h, nterms, npts, _ptr(x), _ptr(vals), ld, _ptr(coef),
+                                            _stream(stream)), "zr_newton_batched")
+
+    def anchor_values(self, T, nv, exps, k, y, offset, v, stream=None):
+        self.check(self.L.zr_anchor_values(self._h, T, nv, _ptr(exps), k, _ptr(y), offset, _ptr(v),
+                                           _stream(stream)), "zr_anchor_values")
+
+    @staticmethod
+    def poly(nv, T, exps, coef=None):
+        return zr_poly(nv, T, _ptr(exps), _ptr(coef))
+
+    def zippel_step(self, skel: zr_poly, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef,
+                    out_cap, stream=None):
+        n = ctypes.c_int64()
+        st = self.L.zr_zippel_step(self._h, ctypes.byref(skel), newvar, _ptr(y), S, _ptr(samples), _ptr(probes),
+                                   ldb, offset, _ptr(out_exps), _ptr(out_coef), out_cap, ctypes.byref(n),
+                                   _stream(stream))
+        self.check(st, "zr_zippel_step")
+        return n.value
+
+    def zippel_step_async(self, skel: zr_poly, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef,
+                          out_cap, d_count, stream=None):
+        st = self.L.zr_zippel_step_async(self._h, ctypes.byref(skel), newvar, _ptr(y), S, _ptr(samples),
+                                         _ptr(probes), ldb, offset, _ptr(out_exps), _ptr(out_coef), out_cap,
+                                         _ptr(d_count), _stream(stream))
+        self.check(st, "zr_zippel_step_async")
+
+    def stream_status(self, stream=None):
+        self.check(self.L.zr_stream_status(self._h, _stream(stream)), "zr_stream_status")
+
+    def zippel_step_host(self, skel: zr_poly, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef,
+                         out_cap, stream=None):
+        n = ctypes.c_int64()
+        st = self.L.zr_zippel_step_host(self._h, ctypes.byref(skel), newvar, _ptr(y), S, _ptr(samples),
+                                        _ptr(probes), ldb, offset, _ptr(out_exps), _ptr(out_coef), out_cap,
+                                        ctypes.byref(n), _stream(stream))
+        self.check(st, "zr_zippel_step_host")
+        return n.value
+
+    def zippel_probes(self, f: zr_poly, k, y, S, samples, z, T, offset, out, ldo, stream=None):
+        self.check(self.L.zr_zippel_probes(self._h, ctypes.byref(f), k, _ptr(y), S, _ptr(samples), _ptr(z), T,
+                                           offset, _ptr(out), ldo, _stream(stream)), "zr_zippel_probes")
+
+    def eval_points(self, f: zr_poly, npts, pts, out, stream=None):
+        self.check(self.L.zr_eval_points(self._h, ctypes.byref(f), npts, _ptr(pts), _ptr(out), _stream(stream)),
+                   "zr_eval_points")
+
+    def zippel_step_balanced(self, skelN: zr_poly, skelD: zr_poly, newvar, y, dN, dD, samples, fvals, ldf, offset,
+                             outN_exps, outN_coef, outN_cap, outD_exps, outD_coef, outD_cap, stream=None):
+        nN = ctypes.c_int64()
+        nD = ctypes.c_int64()
+        st = self.L.zr_zippel_step_balanced(self._h, ctypes.byref(skelN), ctypes.byref(skelD), newvar, _ptr(y),
+                                            dN, dD, _ptr(samples), _ptr(fvals), ldf, offset, _ptr(outN_exps),
+                                            _ptr(outN_coef), outN_cap, ctypes.byref(nN), _ptr(outD_exps),
+                                            _ptr(outD_coef), outD_cap, ctypes.byref(nD), _stream(stream))
+        self.check(st, "zr_zippel_step_balanced")
+        return nN.value, nD.value
+
+    def reconstruct(self, nv, degN, seed, N_exps, N_coef, D_exps=None, D_coef=None, degD=None, offset=0,
+                    stream=None):
+        """Full reconstruction of a built-in sparse black box given by host
+        (numpy) arrays.  Returns ((N_exps, N_coef), (D_exps, D_coef) or None, info)."""
+        rational = D_exps is not None
+        N_exps = np.ascontiguousarray(N_exps, dtype=np.uint8)
+        N_coef = np.ascontiguousarray(N_coef, dtype=np.uint64)
+        bb = zr_blackbox(1 if rational else 0, nv, N_exps.shape[0], N_exps.ctypes.data, N_coef.ctypes.data, 0,
+                         None, None)
+        if rational:
+            D_exps = np.ascontiguousarray(D_exps, dtype=np.uint8)
+            D_coef = np.ascontiguousarray(D_coef, dtype=np.uint64)
+            bb.TD, bb.D_exps, bb.D_coef = D_exps.shape[0], D_exps.ctypes.data, D_coef.ctypes.data
+        dN = np.ascontiguousarray(degN, dtype=np.int32)
+        dD = np.ascontiguousarray(degD if degD is not None else degN, dtype=np.int32)
+        prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data)
+        res = ctypes.POINTER(zr_result)()
+        st = self.L.zr_reconstruct(self._h, ctypes.byref(bb), ctypes.byref(prm), ctypes.byref(res), _stream(stream))
+        self.check(st, "zr_reconstruct")
+        try:
+            r = res.contents
+            Ne = np.ctypeslib.as_array(r.N_exps, shape=(r.TN * nv,)).reshape(r.TN, nv).copy() if r.TN else \
+                np.zeros((0, nv), np.uint8)
+            Nc = np.ctypeslib.as_array(r.N_coef, shape=(r.TN,)).copy() if r.TN else np.zeros(0, np.uint64)
+            D = None
+            if r.rational:
+                De = np.ctypeslib.as_array(r.D_exps, shape=(r.TD * nv,)).reshape(r.TD, nv).copy() if r.TD else \
+                    np.zeros((0, nv), np.uint8)
+                Dc = np.ctypeslib.as_array(r.D_coef, shape=(r.TD,)).copy() if r.TD else np.zeros(0, np.uint64)
+                D = (De, Dc)
+            info = dict(steps=r.steps, redraws=r.redraws, device_ms=r.device_ms)
+            return (Ne, Nc), D, info
+        finally:
+            self.L.zr_result_free(res)

@@ -1,0 +1,165 @@
+"""GPU parity: the probe evaluator and the Zippel step through the C ABI,
+against the oracle (element by element) and against generator truth."""
+import random
+
+import numpy as np
+import pytest
+
+from paper_2505_24256_gb300 import workloads as W
+from tests.gpuutil import d8, d64, h64, zeros8, zeros64
+from tests.pyref import P63
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    import __graft_entry__ as ge
+    from paper_2505_24256_gb300 import zr
+
+    ge.build()
+    assert torch.cuda.is_available()
+    c = zr.Context(P63)
+    yield c
+    c.close()
+
+
+class Dev:
+    """Device copies of a step workload (kept alive with the object)."""
+
+    def __init__(self, ctx, wl):
+        self.wl = wl
+        self.fe, self.fc = d8(wl.exps), d64(wl.coef)
+        self.f = ctx.poly(wl.nv, wl.exps.shape[0], self.fe, self.fc)
+        self.y, self.cs, self.z = d64(wl.y if len(wl.y) else [0]), d64(wl.cs), d64(wl.z)
+        self.ske = d8(wl.skel)
+        self.skel = ctx.poly(wl.nv, wl.T, self.ske)
+
+    def probes(self, ctx, offset=0):
+        wl = self.wl
+        b = zeros64(wl.S, max(wl.T, 1))
+        ctx.zippel_probes(self.f, wl.k, self.y, wl.S, self.cs, self.z, wl.T, offset, b, max(wl.T, 1))
+        return b
+
+    def step(self, ctx, b, offset=0):
+        wl = self.wl
+        cap = max(wl.T * wl.S, 1)
+        oe, oc = zeros8(cap, wl.nv), zeros64(cap)
+        n = ctx.zippel_step(self.skel, wl.k, self.y, wl.S, self.cs, b, max(wl.T, 1), offset, oe, oc, cap)
+        return oe[:n].cpu().numpy(), h64(oc[:n])
+
+
+@pytest.mark.parametrize("T,k,maxe,S,offset", [(1, 1, 3, 1, 0), (2, 2, 3, 2, 0), (150, 3, 6, 5, 0),
+                                               (150, 3, 6, 5, 1), (1000, 4, 9, 9, 0), (2500, 5, 20, 21, 1),
+                                               (777, 2, 40, 33, 0), (300, 6, 4, 64, 0)])
+def test_probes_and_step_match_oracle(ctx, orc, T, k, maxe, S, offset):
+    wl = W.step_workload(500 + T + S, T, k, maxe, S)
+    D = Dev(ctx, wl)
+    b = D.probes(ctx, offset)
+    want_b = orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, wl.T, offset=offset)
+    assert np.array_equal(h64(b)[:, :T], want_b)
+    ge_, gc_ = D.step(ctx, b, offset)
+    we, wc = orc.zippel_step(wl.skel, wl.k, wl.y, wl.cs, want_b, offset=offset)
+    assert np.array_equal(ge_, we) and np.array_equal(gc_, wc)
+    # generator truth: the step recovers the hidden terms
+    assert np.array_equal(ge_, wl.exps) and np.array_equal(gc_, wl.coef)
+
+
+def test_step_zero_coefficients_dropped(ctx, orc):
+    wl = W.step_workload(78, 600, 2, 40, 7)
+    G = wl.G.copy()
+    G[3, :] = 0
+    G[10, 2] = 0
+    G[599, 6] = 0
+    wl = W.StepWorkload(wl.name, wl.p, wl.nv, wl.k, wl.T, wl.S, wl.skel, G, wl.y, wl.cs, wl.z)
+    D = Dev(ctx, wl)
+    b = D.probes(ctx)
+    ge_, gc_ = D.step(ctx, b)
+    keep = wl.coef != 0
+    assert np.array_equal(ge_, wl.exps[keep]) and np.array_equal(gc_, wl.coef[keep])
+
+
+def test_step_singular_anchor(ctx):
+    from paper_2505_24256_gb300 import zr
+    wl = W.step_workload(79, 20, 2, 5, 3)
+    D = Dev(ctx, wl)
+    D.y = d64([1, 1])
+    b = zeros64(3, 20)
+    with pytest.raises(zr.ZrError) as e:
+        D.step(ctx, b)
+    assert e.value.status == zr.SINGULAR
+
+
+def test_step_duplicate_samples(ctx):
+    from paper_2505_24256_gb300 import zr
+    wl = W.step_workload(80, 20, 2, 5, 3)
+    D = Dev(ctx, wl)
+    D.cs = d64([7, 9, 7])
+    b = zeros64(3, 20)
+    with pytest.raises(zr.ZrError) as e:
+        D.step(ctx, b)
+    assert e.value.status == zr.SINGULAR
+
+
+def test_step_empty_skeleton(ctx):
+    wl = W.step_workload(81, 0, 2, 5, 3)
+    D = Dev(ctx, wl)
+    e, c = D.step(ctx, zeros64(3, 1))
+    assert e.shape[0] == 0
+
+
+def test_step_capacity(ctx):
+    from paper_2505_24256_gb300 import zr
+    wl = W.step_workload(82, 40, 2, 9, 3)
+    D = Dev(ctx, wl)
+    b = D.probes(ctx)
+    oe, oc = zeros8(10, wl.nv), zeros64(10)
+    with pytest.raises(zr.ZrError) as e:
+        ctx.zippel_step(D.skel, wl.k, D.y, wl.S, D.cs, b, wl.T, 0, oe, oc, 10)
+    assert e.value.status == zr.CAPACITY
+
+
+def test_step_host_buffers(ctx, orc):
+    wl = W.step_workload(83, 900, 4, 12, 8)
+    b = orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, wl.T)
+    skel = ctx.poly(wl.nv, wl.T, wl.skel)
+    cap = wl.T * wl.S
+    oe = np.zeros((cap, wl.nv), dtype=np.uint8)
+    oc = np.zeros(cap, dtype=np.uint64)
+    n = ctx.zippel_step_host(skel, wl.k, np.ascontiguousarray(wl.y), wl.S, np.ascontiguousarray(wl.cs),
+                             np.ascontiguousarray(b), wl.T, 0, oe, oc, cap)
+    assert n == wl.exps.shape[0]
+    assert np.array_equal(oe[:n], wl.exps) and np.array_equal(oc[:n], wl.coef)
+
+
+def test_batched_step_workload_full(ctx, orc):
+    """The T = 10^4, S = 21 step in full: probes and new skeleton against the
+    oracle element by element, and against generator truth."""
+    wl = W.batched_step_1e4()
+    D = Dev(ctx, wl)
+    b = D.probes(ctx)
+    want_b = orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, wl.T)
+    assert np.array_equal(h64(b), want_b)
+    ge_, gc_ = D.step(ctx, b)
+    assert np.array_equal(ge_, wl.exps) and np.array_equal(gc_, wl.coef)
+    we, wc = orc.zippel_step(wl.skel, wl.k, wl.y, wl.cs, want_b)
+    assert np.array_equal(ge_, we) and np.array_equal(gc_, wc)
+
+
+def test_large_step_workload(ctx, orc):
+    """The T = 2^20, S = 9 step: sampled probes against the oracle, the new
+    skeleton against generator truth in full, sampled solve values against
+    the hidden g_j(c_s)."""
+    wl = W.large_step_2p20()
+    D = Dev(ctx, wl)
+    b = D.probes(ctx)
+    hb = h64(b)
+    rnd = random.Random(3)
+    sidx = [rnd.randrange(wl.S) for _ in range(48)] + [0, wl.S - 1]
+    iidx = [rnd.randrange(wl.T) for _ in range(48)] + [0, wl.T - 1]
+    want = orc.zippel_probes_sampled(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, sidx, iidx)
+    assert np.array_equal(hb[sidx, iidx], want)
+    ge_, gc_ = D.step(ctx, b)
+    assert np.array_equal(ge_, wl.exps) and np.array_equal(gc_, wl.coef)
