@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark of the Zippel step (prints one JSON line on rank 0).
+
+A step is one pass of the step's device path over one batch of synthetic
+input: anchor values + node check, master polynomial, the k-blocked
+synthetic-division / multi-right-hand-side solve, denominators with batch
+inversion, Newton in the new variable and compaction of the new skeleton.
+The probes (the black-box values) are generated once by the GPU evaluator
+before the timed region and stay resident in HBM; their generation time is
+reported separately.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl zr|reference]
+                    [--workload batched|large]
+
+Under torchrun every rank runs an independent replica of the step on its own
+GPU (the step needs no exchange between GPUs); the time is the maximum over
+ranks and `value` counts the terms of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Zippel-step skeleton terms/s and mulmod/s vs roofline; serve p50/p99 latency"
+SM_COUNT = 152
+IMAD_PER_CLK_PER_SM = 64      # 32-bit integer multiply(-add) issue rate per SM per clock
+IMAD_PER_MODMUL = 4           # 32x32->64 partial products of one 64x64-bit product
+
+
+def workload(name):
+    from paper_2505_24256_gb300 import workloads as W
+    return {"batched": W.batched_step_1e4, "large": W.large_step_2p20}[name]()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_step(wl, nthreads=0):
+    """The oracle's step on the full workload (probes from the oracle, untimed)."""
+    import oracle
+    b = oracle.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, wl.T, nthreads=nthreads)
+    t0 = time.perf_counter()
+    e, c = oracle.zippel_step(wl.skel, wl.k, wl.y, wl.cs, b, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    ok = e.shape == wl.exps.shape and (e == wl.exps).all() and (c == wl.coef).all()
+    return dt, bool(ok), b
+
+
+def run_reference(args):
+    """The oracle timed on the host cores (the reference arm)."""
+    import oracle
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    if args.workload != "batched":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle step at T=2^20 takes hours; only the "
+                          "T=10^4 workload has a reference arm"}))
+        return 0
+    cores = oracle.default_threads()
+    b = oracle.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, wl.T)
+    for _ in range(args.warmup):
+        oracle.zippel_step(wl.skel, wl.k, wl.y, wl.cs, b)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        e, c = oracle.zippel_step(wl.skel, wl.k, wl.y, wl.cs, b)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * wl.T / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name, "T": wl.T, "S": wl.S, "nv": wl.nv, "prime": wl.p},
+        "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                         "sample": f"full step T={wl.T} S={wl.S} per timed step (probes from the oracle, untimed)"},
+        "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "mulmod_per_s": (wl.S + 2.5) * wl.T ** 2 * args.steps / total,
+        "check": "generator truth" if (e.shape == wl.exps.shape and (c == wl.coef).all()) else "MISMATCH",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_zr(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as ge
+    from paper_2505_24256_gb300 import zr
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    ge.build()
+    wl = workload(args.workload)
+    T, S, nv, k = wl.T, wl.S, wl.nv, wl.k
+
+    def d64(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(dev)
+
+    ctx = zr.Context(wl.p)
+    stream = torch.cuda.current_stream()
+    # resident inputs: hidden function (for the evaluator), skeleton, anchor, samples, rest values
+    fe, fc = torch.from_numpy(wl.exps).to(dev), d64(wl.coef)
+    f = ctx.poly(nv, wl.exps.shape[0], fe, fc)
+    y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
+    ske = torch.from_numpy(wl.skel).to(dev)
+    skel = ctx.poly(nv, T, ske)
+    b = torch.empty((S, T), dtype=torch.int64, device=dev)
+    # probes by the GPU evaluator (outside the timed step)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.zippel_probes(f, k, y, S, cs, z, T, 0, b, T)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    probe_ms = e0.elapsed_time(e1)
+    cap = T * S
+    oe = torch.zeros((cap, nv), dtype=torch.uint8, device=dev)
+    oc = torch.zeros(cap, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)   # 256 MB > L2 (129 MB)
+
+    def step():
+        return ctx.zippel_step(skel, k, y, S, cs, b, T, 0, oe, oc, cap)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ctx.profile(True)
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = zr.launch_count()
+    total_ms = 0.0
+    n = 0
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flushed between timed steps (outside the events)
+        evs[i][0].record(stream)
+        n = step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = zr.launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(bb) for a, bb in evs)
+    solve_ms, solve_n = ctx.profile_query("solve")
+    phases = {ph: ctx.profile_query(ph)[0] / max(args.steps, 1) for ph in zr.Context.PHASES[:7]}
+    ctx.profile(False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    total_ms = float(t.item())
+    # the output of the last timed step against generator truth
+    ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
+        np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    h_exps = torch.from_numpy(wl.skel).pin_memory()
+    h_y = torch.from_numpy(wl.y.view(np.int64)).pin_memory()
+    h_cs = torch.from_numpy(wl.cs.view(np.int64)).pin_memory()
+    h_b = b.cpu().pin_memory()
+    h_oe = torch.zeros((cap, nv), dtype=torch.uint8).pin_memory()
+    h_oc = torch.zeros(cap, dtype=torch.int64).pin_memory()
+    hskel = ctx.poly(nv, T, h_exps)
+    e2e_steps = max(1, min(args.steps, 10))
+    ctx.zippel_step_host(hskel, k, h_y, S, h_cs, h_b, T, 0, h_oe, h_oc, cap)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ne = ctx.zippel_step_host(hskel, k, h_y, S, h_cs, h_b, T, 0, h_oe, h_oc, cap)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_ok = ne == wl.exps.shape[0] and np.array_equal(h_oc[:ne].numpy().view(np.uint64), wl.coef)
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * sm_max * 1e6 * IMAD_PER_CLK_PER_SM / IMAD_PER_MODMUL     # modular multiplies / s
+    solve_avg_s = solve_ms / max(solve_n, 1) / 1e3
+    solve_ops = (S + 2) * T * T                                                   # a5 dots + a4 chain + a4 denominators
+    achieved = solve_ops / solve_avg_s
+    ms_per_step = total_ms / args.steps
+    W = (S + 2.5) * T * T
+    line = {
+        "metric": METRIC,
+        "value": world * T * args.steps / (total_ms / 1e3),
+        "unit": "terms/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name, "T": T, "S": S, "nv": nv, "prime": wl.p,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}"},
+        "mulmod_per_s": world * W * args.steps / (total_ms / 1e3),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gmulmod/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_solve",
+                     "peak_basis": f"{SM_COUNT} SMs x {sm_max:.0f} MHz x {IMAD_PER_CLK_PER_SM} IMAD/clk / "
+                                   f"{IMAD_PER_MODMUL} partial products per 64x64 product"},
+        "phase_ms": phases,
+        "probe_gen_ms": probe_ms,
+        "e2e": {"value": world * T / e2e_s, "unit": "terms/s",
+                "h2d_bytes_per_step": T * nv + 8 * k + 8 * S + 8 * S * T,
+                "d2h_bytes_per_step": ne * (nv + 8) + 12},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "check": "generator truth" if (ok and e2e_ok) else "MISMATCH",
+    }
+    if world == 1 and not args.no_cpu_baseline and args.workload == "batched":
+        import oracle
+        cores = oracle.default_threads()
+        dt, cok, _ = cpu_baseline_step(wl)
+        line["cpu_baseline"] = {"value": T / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one full step T={T} S={S} (probes from the oracle, untimed)",
+                                "check": "generator truth" if cok else "MISMATCH"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="zr", choices=["zr", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_zr(args)
+
+
+if __name__ == "__main__":
+    rc = main()
+    sys.stdout.flush()
+    sys.stderr.flush()
+    # Leave without interpreter teardown: the result line is out, the
+    # library context is closed, and process-exit destructors of the CUDA
+    # libraries have crashed under the profiler.
+    os._exit(rc or 0)

@@ -68,6 +68,18 @@ uint64_t zr_prime(const zr_ctx* ctx);
 /* Bytes of device workspace the context currently holds. */
 size_t zr_workspace_bytes(const zr_ctx* ctx);
 
+/* Diagnostics.  zr_launch_count: kernels launched by the library in this
+ * process so far.  The profiler records CUDA events around the phases of
+ * every step enqueued by the context (0 anchor values + node check, 1 master
+ * polynomial, 2 right-hand sides in MAC form, 3 k-block carries, 4 the
+ * synthetic-division/dot kernel, 5 denominators + inverses + Newton,
+ * 6 compaction, 7 probe evaluation); zr_profile_enable resets the totals,
+ * zr_profile_query waits for the recorded events and returns the summed
+ * milliseconds and the number of timed occurrences of a phase. */
+uint64_t zr_launch_count(void);
+zr_status zr_profile_enable(zr_ctx* ctx, int32_t on);
+zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count);
+
 /* ---------------------------------------------------------------------------
  * Transposed Vandermonde systems (Sec. 1: the probes y^1..y^t make the system
  * Vandermonde; Sec. 2.2: solved through Horner values and scaled by an

@@ -69,7 +69,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
+    # one CUDA runtime per process: link the shared runtime (the one torch
+    # also uses), found through the toolkit's library directory
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
+    subprocess.run([cc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", f"-rpath,{cudalib}", "-o", tmp, *objs],
+                   check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -75,6 +76,37 @@ zr_status set_err(zr_ctx* ctx, zr_status st, const std::string& msg) {
     ctx->err = msg;
   }
   return st;
+}
+
+cudaEvent_t prof_mark(zr_ctx* ctx, cudaStream_t st) {
+  if (!ctx->prof.on) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (!ctx->prof.pool.empty()) {
+    e = ctx->prof.pool.back();
+    ctx->prof.pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return nullptr;
+  }
+  cudaEventRecord(e, st);
+  return e;
+}
+
+void prof_add(zr_ctx* ctx, int phase, cudaEvent_t a, cudaEvent_t b) {
+  if (!a || !b) return;
+  ctx->prof.pending.push_back({phase, a, b});
+}
+
+void prof_collect(zr_ctx* ctx) {
+  for (auto& p : ctx->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ctx->prof.total_ms[p.phase] += ms;
+      ctx->prof.count[p.phase] += 1;
+    }
+    ctx->prof.pool.push_back(p.a);
+    ctx->prof.pool.push_back(p.b);
+  }
+  ctx->prof.pending.clear();
 }
 
 zr_status cuda_err(zr_ctx* ctx, cudaError_t e, const char* where) {
@@ -179,19 +211,34 @@ void enqueue_step(zr_ctx* ctx, const StepWs& w, const StepDims& D, const zr_poly
   const int S = D.S;
   // a2: anchor values and the node check
   const uint64_t hs = hash_slots(T);
+  cudaEvent_t e0 = prof_mark(ctx, st);
   cudaMemsetAsync(w.htab, 0xFF, hs * sizeof(uint64_t), st);
   launch_powtab(y, k, M, w.tab, st);
   launch_anchor(T, skel->nv, skel->exps, k, w.tab, offset, M, w.v, w.vp, w.htab, hs - 1, status, st);
+  cudaEvent_t e1 = prof_mark(ctx, st);
   // a3: master polynomial
   launch_master_poly(T, w.v, M, w.m, w.tmp, st);
+  cudaEvent_t e2 = prof_mark(ctx, st);
   // a4 + a5
   launch_expand_b(T, S, probes, ldb, M, w.bx, st);
+  cudaEvent_t e3 = prof_mark(ctx, st);
   launch_carry_partials(D, w.m, w.v, w.vp, M, w.R, st);
+  cudaEvent_t e4 = prof_mark(ctx, st);
   launch_solve(D, w.m, w.v, w.vp, w.R, w.bx, M, w.part, w.denp, st);
+  cudaEvent_t e5 = prof_mark(ctx, st);
   // a6
   launch_newton_table(S, samples, M, w.invd, status, st);
   launch_finish_newton(D, offset, w.v, w.part, w.denp, samples, w.invd, M, w.g, w.cnt, status, st);
+  cudaEvent_t e6 = prof_mark(ctx, st);
   launch_compact(T, S, skel->nv, k, skel->exps, w.g, w.cnt, w.bsum, out_cap, out_exps, out_coef, d_out_count, st);
+  cudaEvent_t e7 = prof_mark(ctx, st);
+  prof_add(ctx, PH_ANCHOR, e0, e1);
+  prof_add(ctx, PH_MASTER, e1, e2);
+  prof_add(ctx, PH_EXPAND, e2, e3);
+  prof_add(ctx, PH_CARRY, e3, e4);
+  prof_add(ctx, PH_SOLVE, e4, e5);
+  prof_add(ctx, PH_NEWTON, e5, e6);
+  prof_add(ctx, PH_COMPACT, e6, e7);
 }
 
 }  // namespace zr
@@ -199,6 +246,33 @@ void enqueue_step(zr_ctx* ctx, const StepWs& w, const StepDims& D, const zr_poly
 // ---------------------------------------------------------------------------
 // C entry points
 // ---------------------------------------------------------------------------
+
+static std::atomic<unsigned long long> g_launches{0};
+namespace zr {
+unsigned long long launch_count() { return g_launches.load(); }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace zr
+
+extern "C" uint64_t zr_launch_count(void) { return (uint64_t)zr::launch_count(); }
+
+extern "C" zr_status zr_profile_enable(zr_ctx* ctx, int32_t on) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  prof_collect(ctx);
+  ctx->prof.on = on != 0;
+  for (int i = 0; i < PH_N; i++) {
+    ctx->prof.total_ms[i] = 0;
+    ctx->prof.count[i] = 0;
+  }
+  return ZR_OK;
+}
+
+extern "C" zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count) {
+  if (!ctx || phase < 0 || phase >= PH_N) return ZR_ERR_INVALID_ARG;
+  prof_collect(ctx);
+  if (total_ms) *total_ms = ctx->prof.total_ms[phase];
+  if (count) *count = ctx->prof.count[phase];
+  return ZR_OK;
+}
 
 static const char* kStatusNames[] = {"ok", "invalid argument", "singular", "pole", "out of memory", "timeout",
                                      "cuda error", "unlucky random choice", "busy", "capacity", "degree bound"};
@@ -233,6 +307,8 @@ extern "C" zr_status zr_create(uint64_t prime, zr_ctx** out) {
 
 extern "C" void zr_destroy(zr_ctx* ctx) {
   if (!ctx) return;
+  prof_collect(ctx);
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);

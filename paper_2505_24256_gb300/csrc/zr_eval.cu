@@ -276,7 +276,7 @@ static void launch_matvec_t(int64_t T, int S, int offset, int64_t G, int gsplit,
     configured = true;
   }
   dim3 grid(cdiv(T, kNI), gsplit, cdiv(S, ST));
-  k_eval_matvec<ST><<<grid, kNI, smem, st>>>(T, S, offset, G, gsplit, UP, Wbx, M, out, ldo, partial);
+  { k_eval_matvec<ST><<<grid, kNI, smem, st>>>(T, S, offset, G, gsplit, UP, Wbx, M, out, ldo, partial); note_launch(); }
 }
 
 static int eval_tile(int S) {
@@ -341,22 +341,22 @@ zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, i
   }
   cudaMemsetAsync(htab, 0xFF, H * sizeof(uint64_t), st);
   cudaMemsetAsync(Wacc, 0, (size_t)Tf * S * 2 * sizeof(unsigned long long), st);
-  if (k > 0) k_powrows<<<k, kPowTab, 0, st>>>(y, k, M, tabY);
-  if (z && nv > k + 1) k_powrows<<<nv, kPowTab, 0, st>>>(z, nv, M, tabZ);
+  if (k > 0) { k_powrows<<<k, kPowTab, 0, st>>>(y, k, M, tabY); note_launch(); }
+  if (z && nv > k + 1) { k_powrows<<<nv, kPowTab, 0, st>>>(z, nv, M, tabZ); note_launch(); }
   else cudaMemsetAsync(tabZ, 0, (size_t)nv * kPowTab * sizeof(uint64_t), st);
-  k_powrows<<<S, kPowTab, 0, st>>>(samples, S, M, tabC);
-  k_eval_terms<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, nv, f->exps, f->coef, k, tabY, tabZ, tabC, S, M, u, w, htab, H - 1);
-  k_slot_sums<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, htab, bsum);
-  k_scan_small<<<1, kB, 0, st>>>(nbH, bsum, Gdev);
-  k_slot_ids<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, htab, bsum, gid);
-  k_eval_accum<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, S, u, w, htab, H - 1, gid, U, Wacc, status);
+  { k_powrows<<<S, kPowTab, 0, st>>>(samples, S, M, tabC); note_launch(); }
+  { k_eval_terms<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, nv, f->exps, f->coef, k, tabY, tabZ, tabC, S, M, u, w, htab, H - 1); note_launch(); }
+  { k_slot_sums<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, htab, bsum); note_launch(); }
+  { k_scan_small<<<1, kB, 0, st>>>(nbH, bsum, Gdev); note_launch(); }
+  { k_slot_ids<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, htab, bsum, gid); note_launch(); }
+  { k_eval_accum<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, S, u, w, htab, H - 1, gid, U, Wacc, status); note_launch(); }
   // the group count is needed on the host to size the launch
   int64_t G = 0;
   cudaError_t e = cudaMemcpyAsync(ctx->h_count + 1, Gdev, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_probes: group count");
   G = ctx->h_count[1];
-  k_eval_finalize<<<cdiv(G * S > G ? G * S : G, 256), 256, 0, st>>>(G, S, Wacc, U, M, Wbx, UP);
+  { k_eval_finalize<<<cdiv(G * S > G ? G * S : G, 256), 256, 0, st>>>(G, S, Wacc, U, M, Wbx, UP); note_launch(); }
   uint64_t* target = out;
   switch (stile) {
     case 4: launch_matvec_t<4>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
@@ -366,7 +366,7 @@ zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, i
     case 16: launch_matvec_t<16>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
     default: launch_matvec_t<21>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
   }
-  if (gsplit > 1) k_eval_combine<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, gsplit, partial, M, out, ldo);
+  if (gsplit > 1) { k_eval_combine<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, gsplit, partial, M, out, ldo); note_launch(); }
   return cuda_err(ctx, cudaGetLastError(), "zr_zippel_probes");
 }
 
@@ -433,7 +433,7 @@ extern "C" zr_status zr_eval_points(zr_ctx* ctx, const zr_poly* f, int64_t npts,
       (f->T > 0 && (!f->exps || !f->coef)))
     return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_eval_points: arguments out of range");
   cudaStream_t st = (cudaStream_t)stream;
-  if (npts > 0) k_eval_points<<<(unsigned)npts, 256, 0, st>>>(f->T, f->nv, f->exps, f->coef, pts, ctx->M, out);
+  if (npts > 0) { k_eval_points<<<(unsigned)npts, 256, 0, st>>>(f->T, f->nv, f->exps, f->coef, pts, ctx->M, out); note_launch(); }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_err(ctx, e, "zr_eval_points");

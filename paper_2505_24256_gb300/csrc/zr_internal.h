@@ -10,8 +10,22 @@
 #include "zr.h"
 #include "zr_kernels.cuh"
 
+// Phases of a step timed by the optional profiler (CUDA events recorded on
+// the call's stream around each phase).
+enum zr_phase { PH_ANCHOR = 0, PH_MASTER, PH_EXPAND, PH_CARRY, PH_SOLVE, PH_NEWTON, PH_COMPACT, PH_EVAL, PH_N };
+
+struct zr_prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Pending { int phase; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  double total_ms[PH_N] = {};
+  long long count[PH_N] = {};
+};
+
 struct zr_ctx {
   zr::Mod M;
+  zr_prof prof;
   int device = 0;
   int sms = 0;
   // grow-only device workspace
@@ -46,6 +60,10 @@ struct Carver {
 };
 
 zr_status set_err(zr_ctx* ctx, zr_status st, const std::string& msg);
+// profiler marks (no-ops when profiling is off)
+cudaEvent_t prof_mark(zr_ctx* ctx, cudaStream_t st);
+void prof_add(zr_ctx* ctx, int phase, cudaEvent_t a, cudaEvent_t b);
+void prof_collect(zr_ctx* ctx);
 zr_status cuda_err(zr_ctx* ctx, cudaError_t e, const char* where);
 zr_status ensure_ws(zr_ctx* ctx, size_t need, cudaStream_t st);
 zr_status status_from_flags(zr_ctx* ctx, uint32_t flags);

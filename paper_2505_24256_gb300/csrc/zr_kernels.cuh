@@ -7,6 +7,10 @@
 
 namespace zr {
 
+// Number of kernels the library has launched (a diagnostic counter).
+unsigned long long launch_count();
+void note_launch();
+
 // Device status flags (OR-ed into one 32-bit word per call).
 enum : uint32_t {
   ST_DUP_NODE = 1u,      // two skeleton monomials take the same anchor value

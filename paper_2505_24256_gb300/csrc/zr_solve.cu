@@ -32,7 +32,7 @@ void launch_carry_partials(const StepDims& D, const uint64_t* m, const uint64_t*
                            const Mod& M, uint64_t* R, cudaStream_t st) {
   if (D.NB <= 1) return;
   dim3 grid(cdiv(D.T, 256), D.NB - 1);
-  k_carry_partials<<<grid, 256, 0, st>>>(D.T, D.NB, D.BK, m, v, vp, M, R);
+  { k_carry_partials<<<grid, 256, 0, st>>>(D.T, D.NB, D.BK, m, v, vp, M, R); note_launch(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -173,7 +173,7 @@ static void launch_solve_t(const StepDims& D, const uint64_t* m, const uint64_t*
     configured = true;
   }
   dim3 grid(cdiv(D.T, NT), D.NB, cdiv(D.S, ST));
-  k_solve<ST, NT, KC><<<grid, NT, smem, st>>>(D.T, D.S, D.NB, D.BK, m, v, vp, R, bx, M, part, denp);
+  { k_solve<ST, NT, KC><<<grid, NT, smem, st>>>(D.T, D.S, D.NB, D.BK, m, v, vp, R, bx, M, part, denp); note_launch(); }
 }
 
 void launch_solve(const StepDims& D, const uint64_t* m, const uint64_t* v, const uint64_t* vp, const uint64_t* R,

@@ -76,19 +76,19 @@ __global__ void k_node_check(int64_t T, const uint64_t* __restrict__ v, uint64_t
 }
 
 void launch_powtab(const uint64_t* y, int k, const Mod& M, uint64_t* tab, cudaStream_t st) {
-  if (k > 0) k_powtab<<<k, kPowTab, 0, st>>>(y, k, M, tab);
+  if (k > 0) { k_powtab<<<k, kPowTab, 0, st>>>(y, k, M, tab); note_launch(); }
 }
 void launch_anchor(int64_t T, int nv, const uint8_t* exps, int k, const uint64_t* tab, int offset, const Mod& M,
                    uint64_t* v, uint64_t* vp, uint64_t* htab, uint64_t hmask, uint32_t* status, cudaStream_t st) {
-  if (T > 0) k_anchor<<<cdiv(T, 256), 256, 0, st>>>(T, nv, exps, k, tab, offset, M, v, vp, htab, hmask, status);
+  if (T > 0) { k_anchor<<<cdiv(T, 256), 256, 0, st>>>(T, nv, exps, k, tab, offset, M, v, vp, htab, hmask, status); note_launch(); }
 }
 void launch_shoup_pre(int64_t T, const uint64_t* v, const Mod& M, uint64_t* vp, int offset, uint32_t* status,
                       cudaStream_t st) {
-  if (T > 0) k_shoup_pre<<<cdiv(T, 256), 256, 0, st>>>(T, v, M, vp, offset, status);
+  if (T > 0) { k_shoup_pre<<<cdiv(T, 256), 256, 0, st>>>(T, v, M, vp, offset, status); note_launch(); }
 }
 void launch_node_check(int64_t T, const uint64_t* v, uint64_t* htab, uint64_t hmask, uint32_t* status,
                        cudaStream_t st) {
-  if (T > 0) k_node_check<<<cdiv(T, 256), 256, 0, st>>>(T, v, htab, hmask, status);
+  if (T > 0) { k_node_check<<<cdiv(T, 256), 256, 0, st>>>(T, v, htab, hmask, status); note_launch(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -211,11 +211,11 @@ void launch_master_poly(int64_t T, const uint64_t* v, const Mod& M, uint64_t* m,
   uint64_t* bufs[2] = {tmp, tmp + T};
   int cur = 0;
   uint64_t* dst = levels <= kTreeL1 ? m : bufs[cur];
-  k_tree_leaf<<<cdiv(T, 1 << kTreeL1), 512, 0, st>>>(T, v, M, dst);
+  { k_tree_leaf<<<cdiv(T, 1 << kTreeL1), 512, 0, st>>>(T, v, M, dst); note_launch(); }
   const uint64_t* src = dst;
   for (int l = kTreeL1; l < levels; l++) {
     uint64_t* o = (l == levels - 1) ? m : bufs[cur ^ 1];
-    k_tree_level<<<cdiv(T, kNO), kNO * kNS, 0, st>>>(T, l, src, M, o);
+    { k_tree_level<<<cdiv(T, kNO), kNO * kNS, 0, st>>>(T, l, src, M, o); note_launch(); }
     src = o;
     cur ^= 1;
   }
@@ -237,7 +237,7 @@ __global__ void k_expand_b(int64_t T, int S, const uint64_t* __restrict__ b, int
 }
 
 void launch_expand_b(int64_t T, int S, const uint64_t* b, int64_t ldb, const Mod& M, BX* bx, cudaStream_t st) {
-  if (T > 0 && S > 0) k_expand_b<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, b, ldb, M, bx);
+  if (T > 0 && S > 0) { k_expand_b<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, b, ldb, M, bx); note_launch(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_finish_solve(int64_t T, int S, int NB, 
 void launch_finish_solve(const StepDims& D, int offset, const uint64_t* v, const uint64_t* part,
                          const uint64_t* denp, const Mod& M, uint64_t* c, int64_t ldc, uint32_t* status,
                          cudaStream_t st) {
-  if (D.T > 0) k_finish_solve<<<cdiv(D.T, 256), 256, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, M, c, ldc, status);
+  if (D.T > 0) { k_finish_solve<<<cdiv(D.T, 256), 256, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, M, c, ldc, status); note_launch(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -329,7 +329,7 @@ __global__ void k_newton_table(int S, const uint64_t* __restrict__ xs, Mod M, ui
 }
 
 void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* invd, uint32_t* status, cudaStream_t st) {
-  k_newton_table<<<1, 256, 0, st>>>(S, xs, M, invd, status);
+  { k_newton_table<<<1, 256, 0, st>>>(S, xs, M, invd, status); note_launch(); }
 }
 
 template <int SMAX>
@@ -434,10 +434,10 @@ void launch_finish_newton(const StepDims& D, int offset, const uint64_t* v, cons
                           uint64_t* g, int32_t* cnt, uint32_t* status, cudaStream_t st) {
   if (D.T <= 0) return;
   const unsigned grid = cdiv(D.T, 128);
-  if (D.S <= 8) k_finish_newton<8><<<grid, 128, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, xs, invd, M, g, cnt, status);
-  else if (D.S <= 16) k_finish_newton<16><<<grid, 128, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, xs, invd, M, g, cnt, status);
-  else if (D.S <= 32) k_finish_newton<32><<<grid, 128, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, xs, invd, M, g, cnt, status);
-  else k_finish_newton<64><<<grid, 128, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, xs, invd, M, g, cnt, status);
+  if (D.S <= 8) { k_finish_newton<8><<<grid, 128, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, xs, invd, M, g, cnt, status); note_launch(); }
+  else if (D.S <= 16) { k_finish_newton<16><<<grid, 128, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, xs, invd, M, g, cnt, status); note_launch(); }
+  else if (D.S <= 32) { k_finish_newton<32><<<grid, 128, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, xs, invd, M, g, cnt, status); note_launch(); }
+  else { k_finish_newton<64><<<grid, 128, 0, st>>>(D.T, D.S, D.NB, D.BK, offset, v, part, denp, xs, invd, M, g, cnt, status); note_launch(); }
 }
 
 template <int SMAX>
@@ -466,10 +466,10 @@ void launch_newton(int64_t nterms, int npts, const uint64_t* xs, const uint64_t*
                    int64_t ld, const Mod& M, uint64_t* coef, cudaStream_t st) {
   if (nterms <= 0) return;
   const unsigned grid = cdiv(nterms, 128);
-  if (npts <= 8) k_newton<8><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef);
-  else if (npts <= 16) k_newton<16><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef);
-  else if (npts <= 32) k_newton<32><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef);
-  else k_newton<64><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef);
+  if (npts <= 8) { k_newton<8><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef); note_launch(); }
+  else if (npts <= 16) { k_newton<16><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef); note_launch(); }
+  else if (npts <= 32) { k_newton<32><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef); note_launch(); }
+  else { k_newton<64><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef); note_launch(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -564,9 +564,9 @@ void launch_compact(int64_t T, int S, int nv, int k, const uint8_t* exps, const 
     cudaMemsetAsync(out_count, 0, sizeof(int64_t), st);
     return;
   }
-  k_block_sums<<<(unsigned)nb, kScanB, 0, st>>>(T, cnt, bsum);
-  k_scan_bsum<<<1, kScanB, 0, st>>>(nb, bsum, out_count);
-  k_scatter<<<(unsigned)nb, kScanB, 0, st>>>(T, S, nv, k, exps, g, cnt, bsum, cap, out_exps, out_coef);
+  { k_block_sums<<<(unsigned)nb, kScanB, 0, st>>>(T, cnt, bsum); note_launch(); }
+  { k_scan_bsum<<<1, kScanB, 0, st>>>(nb, bsum, out_count); note_launch(); }
+  { k_scatter<<<(unsigned)nb, kScanB, 0, st>>>(T, S, nv, k, exps, g, cnt, bsum, cap, out_exps, out_coef); note_launch(); }
 }
 
 }  // namespace zr

@@ -68,6 +68,9 @@ SIGNATURES = {
     "zr_status_string": (ctypes.c_char_p, [_ST]),
     "zr_prime": (_U64, [_V]),
     "zr_workspace_bytes": (ctypes.c_size_t, [_V]),
+    "zr_launch_count": (_U64, []),
+    "zr_profile_enable": (_ST, [_V, _I32]),
+    "zr_profile_query": (_ST, [_V, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "zr_vandermonde_solve_batched": (_ST, [_V, _I32, _P, _V]),
     "zr_vandermonde_solve_plain": (_ST, [_V, _I32, _P, _V]),
     "zr_newton_batched": (_ST, [_V, _I64, _I32, _P, _P, _I64, _P, _V]),
@@ -158,6 +161,19 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(self.L.zr_workspace_bytes(self._h))
+
+    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval")
+
+    def profile(self, on: bool = True):
+        self.check(self.L.zr_profile_enable(self._h, 1 if on else 0), "zr_profile_enable")
+
+    def profile_query(self, phase):
+        idx = self.PHASES.index(phase) if isinstance(phase, str) else int(phase)
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self.check(self.L.zr_profile_query(self._h, idx, ctypes.byref(ms), ctypes.byref(n)), "zr_profile_query")
+        return ms.value, n.value
+
 
     # ------------------------------------------------------------------ calls
     def vandermonde_solve(self, systems, stream=None, plain=False):
@@ -263,3 +279,8 @@ class Context:
             return (Ne, Nc), D, info
         finally:
             self.L.zr_result_free(res)
+
+
+def launch_count() -> int:
+    """Kernels launched by libzr in this process so far."""
+    return int(load().zr_launch_count())
