@@ -123,6 +123,22 @@ zr_status zr_vandermonde_solve_plain(zr_ctx* ctx, int32_t nsys, const zr_vsys* s
 zr_status zr_newton_batched(zr_ctx* ctx, int64_t nterms, int32_t npts, const uint64_t* x, const uint64_t* vals,
                             int64_t ld, uint64_t* coef, void* stream);
 
+/* Allocation-free variant of zr_newton_batched, for callers that cannot
+ * allocate device memory (a host program whose own pool owns the GPU memory,
+ * or a latency-critical path that cannot take cudaMalloc's implicit
+ * synchronisation) and therefore cannot create a zr_ctx.  The paper has no
+ * counterpart; this is a library convenience.  Same arguments and results as
+ * zr_newton_batched, with the prime passed directly (2^32 < p < 2^63) and
+ * npts <= 64 (larger npts returns ZR_ERR_INVALID_ARG).  Its only scratch is a
+ * fixed device array of 64*64+32 words that every GPU loading the library
+ * holds until exit.  The first call on a device looks that array up with the
+ * device current; make it before any stream capture.  All calls share the
+ * array (the call clears what must start at zero), so calls that overlap on
+ * the GPU race: serialise them.  Waits for `stream`; ZR_ERR_SINGULAR when two
+ * nodes coincide. */
+zr_status zr_newton_batched_noalloc(uint64_t prime, int64_t nterms, int32_t npts, const uint64_t* x,
+                                    const uint64_t* vals, int64_t ld, uint64_t* coef, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Anchor values (Sec. 1): v_j = prod_{m < k} y_m^{e_{j,m}} for the T
  * exponent rows of a skeleton, with the distinctness check the solve needs.

@@ -70,6 +70,12 @@ static Mod make_mod(uint64_t p) {
 // ---------------------------------------------------------------------------
 namespace zr {
 
+bool mod_for_prime(uint64_t p, Mod* out) {
+  if (!out || p <= (1ull << 32) || p >= (1ull << 63) || !h_is_prime(p)) return false;
+  *out = make_mod(p);
+  return true;
+}
+
 zr_status set_err(zr_ctx* ctx, zr_status st, const std::string& msg) {
   if (ctx && st != ZR_OK) {
     std::lock_guard<std::mutex> g(ctx->mu);

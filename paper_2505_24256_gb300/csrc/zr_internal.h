@@ -60,6 +60,9 @@ struct Carver {
 };
 
 zr_status set_err(zr_ctx* ctx, zr_status st, const std::string& msg);
+// Modulus descriptor for a prime 2^32 < p < 2^63; false when p is out of
+// range or composite.  Host arithmetic only (allocates nothing).
+bool mod_for_prime(uint64_t p, Mod* out);
 // profiler marks (no-ops when profiling is off)
 cudaEvent_t prof_mark(zr_ctx* ctx, cudaStream_t st);
 void prof_add(zr_ctx* ctx, int phase, cudaEvent_t a, cudaEvent_t b);

@@ -75,6 +75,7 @@ SIGNATURES = {
     "zr_vandermonde_solve_plain": (_ST, [_V, _I32, _P, _V]),
     "zr_newton_batched": (_ST, [_V, _I64, _I32, _P, _P, _I64, _P, _V]),
     "zr_anchor_values": (_ST, [_V, _I64, _I32, _P, _I32, _P, _I32, _P, _V]),
+    "zr_newton_batched_noalloc": (_ST, [_U64, _I64, _I32, _P, _P, _I64, _P, _V]),
     "zr_zippel_step": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
     "zr_zippel_step_async": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
     "zr_stream_status": (_ST, [_V, _V]),
@@ -284,3 +285,11 @@ class Context:
 def launch_count() -> int:
     """Kernels launched by libzr in this process so far."""
     return int(load().zr_launch_count())
+
+
+def newton_batched_noalloc(prime, nterms, npts, x, vals, ld, coef, stream=None) -> int:
+    """zr_newton_batched_noalloc: the batched Newton interpolation without a
+    context and without any allocation, for callers that cannot allocate
+    device memory.  Returns the zr status code (0 on success)."""
+    return int(load().zr_newton_batched_noalloc(prime, nterms, npts, _ptr(x), _ptr(vals), ld, _ptr(coef),
+                                                 _stream(stream)))
