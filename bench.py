@@ -196,6 +196,11 @@ def run_zr(args):
     def step():
         return ctx.zippel_step(skel, k, y, S, cs, b, T, 0, oe, oc, cap)
 
+    # launch plan: autotuned for this shape when tuning is affordable, else the model
+    if S * T * T <= 10**11:
+        ctx.autotune_step(T, S, 24)
+    plan = ctx.step_plan(T, S)
+
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -279,6 +284,7 @@ def run_zr(args):
                      "peak_basis": f"{SM_COUNT} SMs x {sm_max:.0f} MHz x {IMAD_PER_CLK_PER_SM} IMAD/clk / "
                                    f"{IMAD_PER_MODMUL} partial products per 64x64 product"},
         "phase_ms": phases,
+        "plan": {"s_tile": plan[0], "k_blocks": plan[1]},
         "probe_gen_ms": probe_ms,
         "e2e": {"value": world * T / e2e_s, "unit": "terms/s",
                 "h2d_bytes_per_step": T * nv + 8 * k + 8 * S + 8 * S * T,

@@ -80,6 +80,14 @@ uint64_t zr_launch_count(void);
 zr_status zr_profile_enable(zr_ctx* ctx, int32_t on);
 zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count);
 
+/* Autotuner of the solve's launch plan (right-hand-side tile x k-block
+ * count): times the `budget` best-ranked candidate plans on synthetic data of
+ * shape (T, S) and records the fastest in the context; later calls with that
+ * shape use it.  Plans change the schedule only, never the values.
+ * zr_step_plan reports the plan a call of shape (T, S) would use. */
+zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t budget, void* stream);
+zr_status zr_step_plan(zr_ctx* ctx, int64_t T, int32_t S, int32_t* s_tile, int32_t* nblocks);
+
 /* ---------------------------------------------------------------------------
  * Transposed Vandermonde systems (Sec. 1: the probes y^1..y^t make the system
  * Vandermonde; Sec. 2.2: solved through Horner values and scaled by an

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,8 @@ static Mod make_mod(uint64_t p) {
   M.v = (uint64_t)((~(u128)0) / M.d - ((u128)1 << 64));
   M.r21 = h_powmod(2, 21, p);
   M.r42 = h_powmod(2, 42, p);
+  M.r32 = h_powmod(2, 32, p);
+  M.r32p = (uint64_t)(((u128)M.r32 << 64) / p);
   return M;
 }
 
@@ -103,15 +106,20 @@ void prof_add(zr_ctx* ctx, int phase, cudaEvent_t a, cudaEvent_t b) {
 }
 
 void prof_collect(zr_ctx* ctx) {
+  // adjacent phases share their boundary event: return every event once
+  std::vector<cudaEvent_t> used;
   for (auto& p : ctx->prof.pending) {
     float ms = 0.f;
     if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       ctx->prof.total_ms[p.phase] += ms;
       ctx->prof.count[p.phase] += 1;
     }
-    ctx->prof.pool.push_back(p.a);
-    ctx->prof.pool.push_back(p.b);
+    used.push_back(p.a);
+    used.push_back(p.b);
   }
+  std::sort(used.begin(), used.end());
+  used.erase(std::unique(used.begin(), used.end()), used.end());
+  for (cudaEvent_t e : used) ctx->prof.pool.push_back(e);
   ctx->prof.pending.clear();
 }
 
@@ -159,34 +167,108 @@ uint64_t hash_slots(int64_t T) {
   return h;
 }
 
-// Tile choice for the solve: right-hand-side tiles of at most 24, then
-// k-blocks until the launch has about four resident warps per scheduler.
-static int pick_tile(int st) {
-  static const int tiles[] = {4, 8, 9, 11, 12, 16, 21, 24};
-  for (int t : tiles)
-    if (t >= st) return t;
-  return 24;
+// Launch plan of the solve: for every compiled right-hand-side tile, the
+// resident CTAs per SM (occupancy query, cached) give the CTA slots of one
+// wave; the number of k-blocks NB trades parallelism against the carry pass.
+// Model, in 32-bit multiply-add issue slots per thread and k:
+//   cost_k = 12 tile + 45   (four lo + four hi per MAC, two Shoup products)
+// and a wave with n CTAs per SM takes BK cost_k max(n, 4): fewer than four
+// resident CTAs (16 warps) leave the multiplier partly idle.  The carry pass
+// adds a 24-slot Shoup Horner step per k.  The cheapest plan wins; measured
+// plans from zr_autotune_step take precedence.
+static int occupancy_cached(int tile) {
+  static int cache[64] = {0};
+  if (tile <= 0 || tile >= 64) return 1;
+  if (!cache[tile]) cache[tile] = solve_blocks_per_sm(tile);
+  return cache[tile];
+}
+
+// A forced plan: the context's tuned plan table, else ZR_SOLVE_PLAN="tile,NB"
+// in the environment (a tuning override), else the model below.
+static bool forced_plan(const zr_ctx* ctx, int64_t T, int S, StepDims& D) {
+  if (ctx) {
+    for (const auto& e : ctx->plans)
+      if (e.T == T && e.S == S) {
+        D = e.D;
+        return true;
+      }
+  }
+  const char* env = getenv("ZR_SOLVE_PLAN");
+  int tile = 0, nb = 0;
+  if (!env || sscanf(env, "%d,%d", &tile, &nb) != 2 || tile <= 0 || nb <= 0) return false;
+  int tiles[16];
+  const int nt = solve_tiles(tiles, 16);
+  bool ok = false;
+  for (int i = 0; i < nt; i++) ok |= tiles[i] == tile;
+  if (!ok) return false;
+  D.T = T;
+  D.S = S;
+  D.s_tile = tile;
+  int64_t BK = (T + nb - 1) / nb;
+  BK = ((BK + 31) / 32) * 32;
+  D.BK = BK < 32 ? 32 : BK;
+  D.NB = (int)((T + D.BK - 1) / D.BK);
+  if (D.NB < 1) D.NB = 1;
+  return true;
+}
+
+double plan_cost(const zr_ctx* ctx, const StepDims& D) {
+  const int64_t sms = ctx && ctx->sms ? ctx->sms : 152;
+  const int64_t rows = (D.T + 127) / 128;
+  const int nst = (D.S + D.s_tile - 1) / D.s_tile;
+  const int per_sm = occupancy_cached(D.s_tile);
+  const int64_t slots = sms * per_sm;
+  const double cost_k = 12.0 * D.s_tile + 45.0;
+  const int64_t ctas = rows * D.NB * nst;
+  double cost = 0;
+  for (int64_t left = ctas; left > 0; left -= slots) {
+    const int64_t in_wave = left < slots ? left : slots;
+    const int64_t n = (in_wave + sms - 1) / sms;
+    cost += (double)D.BK * cost_k * (double)(n > 4 ? n : 4);
+  }
+  if (D.NB > 1) {
+    const int64_t cslots = sms * 16;                     // 128-thread rows of the carry kernel
+    const int64_t cw = (rows * (D.NB - 1) + cslots - 1) / cslots;
+    cost += (double)cw * D.BK * 24.0 * 4;
+  }
+  return cost;
 }
 
 StepDims plan_step(const zr_ctx* ctx, int64_t T, int S) {
-  StepDims D;
-  D.T = T;
-  D.S = S;
-  int nst = (S + 23) / 24;
-  D.s_tile = pick_tile((S + nst - 1) / nst);
-  nst = (S + D.s_tile - 1) / D.s_tile;
-  const int64_t sms = ctx && ctx->sms ? ctx->sms : 152;
-  const int64_t target = sms * 512;
-  const int64_t rows = ((T + 127) / 128) * 128;
-  int NB = 1;
-  while (NB < 64 && rows * NB * nst < target && T / (2 * NB) >= 512) NB *= 2;
-  int64_t BK = (T + NB - 1) / NB;
-  BK = ((BK + 31) / 32) * 32;
-  if (BK < 32) BK = 32;
-  D.BK = BK;
-  D.NB = (int)((T + BK - 1) / BK);
-  if (D.NB < 1) D.NB = 1;
-  return D;
+  StepDims best;
+  if (forced_plan(ctx, T, S, best)) return best;
+  best.T = T;
+  best.S = S;
+  best.NB = 1;
+  best.BK = ((T + 31) / 32) * 32;
+  best.s_tile = 21;
+  double best_cost = -1;
+  int tiles[16];
+  const int nt = solve_tiles(tiles, 16);
+  for (int ti = 0; ti < nt; ti++) {
+    const int tile = tiles[ti];
+    const int nst = (S + tile - 1) / tile;
+    if (nst > 8) continue;
+    for (int NBw = 1; NBw <= 64; NBw++) {
+      int64_t BK = (T + NBw - 1) / NBw;
+      BK = ((BK + 31) / 32) * 32;
+      if (BK < 32) BK = 32;
+      const int NB = (int)((T + BK - 1) / BK);
+      if (NB != NBw) continue;
+      StepDims D;
+      D.T = T;
+      D.S = S;
+      D.NB = NB;
+      D.BK = BK;
+      D.s_tile = tile;
+      const double cost = plan_cost(ctx, D);
+      if (best_cost < 0 || cost < best_cost * 0.999) {
+        best_cost = cost;
+        best = D;
+      }
+    }
+  }
+  return best;
 }
 
 StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D) {
@@ -198,7 +280,6 @@ StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D) {
   w.htab = cv.take<uint64_t>(hash_slots(T));
   w.m = cv.take<uint64_t>(Tn);
   w.tmp = cv.take<uint64_t>(2 * Tn);
-  w.bx = cv.take<BX>((size_t)Tn * S);
   w.R = cv.take<uint64_t>((size_t)(D.NB > 1 ? D.NB - 1 : 1) * Tn);
   w.part = cv.take<uint64_t>((size_t)D.NB * S * Tn);
   w.denp = cv.take<uint64_t>((size_t)D.NB * Tn);
@@ -226,11 +307,10 @@ void enqueue_step(zr_ctx* ctx, const StepWs& w, const StepDims& D, const zr_poly
   launch_master_poly(T, w.v, M, w.m, w.tmp, st);
   cudaEvent_t e2 = prof_mark(ctx, st);
   // a4 + a5
-  launch_expand_b(T, S, probes, ldb, M, w.bx, st);
   cudaEvent_t e3 = prof_mark(ctx, st);
   launch_carry_partials(D, w.m, w.v, w.vp, M, w.R, st);
   cudaEvent_t e4 = prof_mark(ctx, st);
-  launch_solve(D, w.m, w.v, w.vp, w.R, w.bx, M, w.part, w.denp, st);
+  launch_solve(D, w.m, w.v, w.vp, w.R, probes, ldb, M, w.part, w.denp, st);
   cudaEvent_t e5 = prof_mark(ctx, st);
   // a6
   launch_newton_table(S, samples, M, w.invd, status, st);
@@ -356,9 +436,8 @@ static void enqueue_vsys(zr_ctx* ctx, const zr_vsys& s, const StepWs& w, const S
   launch_shoup_pre(s.T, s.v, M, w.vp, s.offset, status, st);
   launch_node_check(s.T, s.v, w.htab, hs - 1, status, st);
   launch_master_poly(s.T, s.v, M, w.m, w.tmp, st);
-  launch_expand_b(s.T, s.S, s.b, s.ldb, M, w.bx, st);
   launch_carry_partials(D, w.m, s.v, w.vp, M, w.R, st);
-  launch_solve(D, w.m, s.v, w.vp, w.R, w.bx, M, w.part, w.denp, st);
+  launch_solve(D, w.m, s.v, w.vp, w.R, s.b, s.ldb, M, w.part, w.denp, st);
   launch_finish_solve(D, s.offset, s.v, w.part, w.denp, M, s.c, s.ldc, status, st);
 }
 

@@ -15,14 +15,17 @@
 //    precomputed quotient w' = floor(w 2^64 / p) (as analysed in D. Harvey,
 //    "Faster arithmetic for number-theoretic transforms", JSC 2014), with
 //    results kept lazily in [0, 2p);
-//  * long dot products accumulate without any carry handling: the per-thread
-//    operand x < 2^64 is cut into 21-bit limbs x0 + x1 2^21 + x2 2^42 and
-//    the shared operand b is supplied as the three residues b, b 2^21, b 2^42
-//    mod p, each as two 32-bit halves.  Then x b == sum_t x_t (b 2^{21t} mod p)
-//    and every partial product is below 2^54, so two 64-bit accumulators
-//    absorb 128 multiply-adds before they are folded back into a residue.
-//    This is the deferred reduction of Sec. 2.2 (sum of products reduced once)
-//    with the limb split chosen so that no step needs a carry.
+//  * long dot products accumulate without any carry handling.  With
+//    b = b_lo + 2^32 b_hi (the two 32-bit halves of a residue),
+//        x b == x b_lo + (x 2^32 mod p) b_hi   (mod p),
+//    so a thread that owns x computes x~ = x 2^32 mod p once, cuts x and x~
+//    into 21-bit limbs, and multiplies them by the halves of the shared b:
+//        A_t += x_t b_lo + x~_t b_hi,   t = 0, 1, 2,   value = sum_t A_t 2^{21 t}.
+//    Every partial product is below 2^53, so three 64-bit accumulators absorb
+//    256 multiply-adds before they are folded back into a residue, and the
+//    shared operand is the plain 8-byte residue.  This is the deferred
+//    reduction of Sec. 2.2 (a sum of products reduced once) with the limb
+//    split chosen so that no step needs a carry.
 //
 // The modulus is an odd prime 2^32 < p < 2^63, so 2p < 2^64.
 #pragma once
@@ -39,6 +42,8 @@ struct Mod {
   uint32_t pad;
   uint64_t r21;     // 2^21 mod p
   uint64_t r42;     // 2^42 mod p
+  uint64_t r32;     // 2^32 mod p
+  uint64_t r32p;    // floor(r32 2^64 / p) (Shoup quotient of r32)
 };
 
 __device__ __forceinline__ uint64_t wide(uint32_t a, uint32_t b) { return (uint64_t)a * b; }
@@ -46,22 +51,59 @@ __device__ __forceinline__ uint64_t wide_add(uint32_t a, uint32_t b, uint64_t c)
 __device__ __forceinline__ uint32_t lo32(uint64_t x) { return (uint32_t)x; }
 __device__ __forceinline__ uint32_t hi32(uint64_t x) { return (uint32_t)(x >> 32); }
 
-// Full 64x64 -> 128 product from four 32x32+64 multiply-adds.
+// Products are built from 32-bit low/high multiply-adds with carry chains:
+// on this GPU mad.lo issues at twice the rate of mad.hi and four times the
+// rate of the 32x32->64 mad.wide, so a 32x32->64 product costs least as a
+// (lo, hi) pair.
+
+// Full 64x64 -> 128 product.
 __device__ __forceinline__ void mul128(uint64_t a, uint64_t b, uint64_t& hi, uint64_t& lo) {
-  uint32_t a0 = lo32(a), a1 = hi32(a), b0 = lo32(b), b1 = hi32(b);
-  uint64_t t = wide(a0, b0);
-  uint64_t u = wide_add(a0, b1, hi32(t));      // < 2^64
-  uint64_t w = wide_add(a1, b0, lo32(u));      // < 2^64
-  lo = ((uint64_t)lo32(w) << 32) | lo32(t);
-  hi = wide_add(a1, b1, (uint64_t)hi32(u) + hi32(w));
+  const uint32_t a0 = lo32(a), a1 = hi32(a), b0 = lo32(b), b1 = hi32(b);
+  uint32_t r0, r1, r2, r3;
+  asm("mul.lo.u32 %0, %4, %6;\n\t"
+      "mul.hi.u32 %1, %4, %6;\n\t"
+      "mul.lo.u32 %2, %5, %7;\n\t"
+      "mul.hi.u32 %3, %5, %7;\n\t"
+      "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+      "addc.u32 %3, %3, 0;\n\t"
+      "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+      "addc.u32 %3, %3, 0;"
+      : "=&r"(r0), "=&r"(r1), "=&r"(r2), "=&r"(r3)
+      : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+  lo = ((uint64_t)r1 << 32) | r0;
+  hi = ((uint64_t)r3 << 32) | r2;
 }
 
+// High 64 bits of a 64x64 product (the low word of a0 b0 cannot carry into them).
 __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
-  uint32_t a0 = lo32(a), a1 = hi32(a), b0 = lo32(b), b1 = hi32(b);
-  uint64_t t = wide(a0, b0);
-  uint64_t u = wide_add(a0, b1, hi32(t));
-  uint64_t w = wide_add(a1, b0, lo32(u));
-  return wide_add(a1, b1, (uint64_t)hi32(u) + hi32(w));
+  const uint32_t a0 = lo32(a), a1 = hi32(a), b0 = lo32(b), b1 = hi32(b);
+  uint32_t t0, t1, t2;
+  asm("mul.hi.u32 %0, %3, %5;\n\t"
+      "mad.lo.cc.u32 %0, %3, %6, %0;\n\t"
+      "madc.hi.u32 %1, %3, %6, 0;\n\t"
+      "mad.lo.cc.u32 %0, %4, %5, %0;\n\t"
+      "madc.hi.cc.u32 %1, %4, %5, %1;\n\t"
+      "addc.u32 %2, 0, 0;\n\t"
+      "mad.lo.cc.u32 %1, %4, %6, %1;\n\t"
+      "madc.hi.u32 %2, %4, %6, %2;"
+      : "=&r"(t0), "=&r"(t1), "=&r"(t2)
+      : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+  return ((uint64_t)t2 << 32) | t1;
+}
+
+// Low 64 bits of a 64x64 product.
+__device__ __forceinline__ uint64_t mullo64(uint64_t a, uint64_t b) {
+  const uint32_t a0 = lo32(a), a1 = hi32(a), b0 = lo32(b), b1 = hi32(b);
+  uint32_t r0, r1;
+  asm("mul.lo.u32 %0, %2, %4;\n\t"
+      "mul.hi.u32 %1, %2, %4;\n\t"
+      "mad.lo.u32 %1, %2, %5, %1;\n\t"
+      "mad.lo.u32 %1, %3, %4, %1;"
+      : "=&r"(r0), "=&r"(r1)
+      : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+  return ((uint64_t)r1 << 32) | r0;
 }
 
 // (u1 2^64 + u0) mod p for u1 < p (Moller-Granlund 2/1 division).
@@ -73,7 +115,7 @@ __device__ __forceinline__ uint64_t reduce128(uint64_t u1, uint64_t u0, const Mo
   q0 += n0;
   q1 += n1 + (q0 < n0);
   q1 += 1;
-  uint64_t r = n0 - q1 * M.d;
+  uint64_t r = n0 - mullo64(q1, M.d);
   if (r > q0) r += M.d;
   if (r >= M.d) r -= M.d;
   return r >> M.norm;
@@ -87,7 +129,7 @@ __device__ __forceinline__ uint64_t shoup_pre(uint64_t w, const Mod& M) {
   q0 += n0;
   q1 += n1 + (q0 < n0);
   q1 += 1;
-  uint64_t r = n0 - q1 * M.d;
+  uint64_t r = n0 - mullo64(q1, M.d);
   if (r > q0) { q1 -= 1; r += M.d; }
   if (r >= M.d) { q1 += 1; }
   return q1;
@@ -107,8 +149,8 @@ __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const Mod& M
 }
 // x w mod p, lazily in [0, 2p), for any x < 2^64; wp = shoup_pre(w).
 __device__ __forceinline__ uint64_t shoup_lazy(uint64_t x, uint64_t w, uint64_t wp, const Mod& M) {
-  uint64_t q = mulhi64(x, wp);
-  return x * w - q * M.p;
+  const uint64_t q = mulhi64(x, wp);
+  return mullo64(x, w) - mullo64(q, M.p);
 }
 __device__ __forceinline__ uint64_t canon(uint64_t x, const Mod& M) {  // [0, 2p) -> [0, p)
   return x >= M.p ? x - M.p : x;
@@ -179,5 +221,75 @@ __device__ __forceinline__ void acc_fold(Acc& a, const Mod& M) {
   a.H = 0;
 }
 constexpr int MAC_FOLD = 128;
+
+// The per-thread operand of the three-accumulator MAC: limbs of x and of
+// x 2^32 mod p (x canonical, so every limb is below 2^21).
+struct XL2 { uint32_t a0, a1, a2, c0, c1, c2; };
+__device__ __forceinline__ XL2 limbs_pair(uint64_t x, const Mod& M) {
+  const uint64_t xt = canon(shoup_lazy(x, M.r32, M.r32p, M), M);
+  XL2 r;
+  r.a0 = (uint32_t)x & 0x1FFFFFu;
+  r.a1 = (uint32_t)(x >> 21) & 0x1FFFFFu;
+  r.a2 = (uint32_t)(x >> 42);
+  r.c0 = (uint32_t)xt & 0x1FFFFFu;
+  r.c1 = (uint32_t)(xt >> 21) & 0x1FFFFFu;
+  r.c2 = (uint32_t)(xt >> 42);
+  return r;
+}
+struct Acc3L { uint64_t A0, A1, A2; };
+__device__ __forceinline__ void mac3(Acc3L& a, const XL2& x, uint64_t b) {
+  const uint32_t lo = lo32(b), hi = hi32(b);
+  a.A0 = wide_add(x.a0, lo, a.A0);
+  a.A1 = wide_add(x.a1, lo, a.A1);
+  a.A2 = wide_add(x.a2, lo, a.A2);
+  a.A0 = wide_add(x.c0, hi, a.A0);
+  a.A1 = wide_add(x.c1, hi, a.A1);
+  a.A2 = wide_add(x.c2, hi, a.A2);
+}
+// residue of A0 + A1 2^21 + A2 2^42
+__device__ __forceinline__ uint64_t acc3l_value(const Acc3L& a, const Mod& M) {
+  uint64_t lo = a.A0, hi = 0;
+  uint64_t t = a.A1 << 21;
+  lo += t;
+  hi += (a.A1 >> 43) + (lo < t);
+  t = a.A2 << 42;
+  lo += t;
+  hi += (a.A2 >> 22) + (lo < t);
+  return reduce128(hi, lo, M);            // hi < 2^43 < p
+}
+// After a fold the accumulator holds one residue (< 2^63) and takes another
+// MAC3_FOLD multiply-adds: each adds below 2^54 to every word.
+__device__ __forceinline__ void acc3l_fold(Acc3L& a, const Mod& M) {
+  a.A0 = acc3l_value(a, M);
+  a.A1 = a.A2 = 0;
+}
+constexpr int MAC3_FOLD = 256;
+
+// Five-word accumulator r (160 bits) += x b for 64-bit x and b: the four
+// 32x32 partial products as lo/hi multiply-adds with carry chains.  The top
+// word counts carries out of 128 bits, so fewer than 2^32 products never
+// overflow and the sum is reduced once at the end.
+struct Acc5 { uint32_t r0, r1, r2, r3, r4; };
+__device__ __forceinline__ void mac5(Acc5& a, uint32_t x0, uint32_t x1, uint32_t b0, uint32_t b1) {
+  asm("mad.lo.cc.u32 %0, %5, %7, %0;\n\t"
+      "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+      "madc.lo.cc.u32 %2, %6, %8, %2;\n\t"
+      "madc.hi.cc.u32 %3, %6, %8, %3;\n\t"
+      "addc.u32 %4, %4, 0;\n\t"
+      "mad.lo.cc.u32 %1, %6, %7, %1;\n\t"
+      "madc.hi.cc.u32 %2, %6, %7, %2;\n\t"
+      "addc.cc.u32 %3, %3, 0;\n\t"
+      "addc.u32 %4, %4, 0;\n\t"
+      "mad.lo.cc.u32 %1, %5, %8, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %8, %2;\n\t"
+      "addc.cc.u32 %3, %3, 0;\n\t"
+      "addc.u32 %4, %4, 0;"
+      : "+r"(a.r0), "+r"(a.r1), "+r"(a.r2), "+r"(a.r3), "+r"(a.r4)
+      : "r"(x0), "r"(x1), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint64_t acc5_value(const Acc5& a, const Mod& M) {
+  const uint64_t mid = ((uint64_t)a.r3 << 32) | a.r2, low = ((uint64_t)a.r1 << 32) | a.r0;
+  return reduce128(reduce128(a.r4, mid, M), low, M);    // r4 < 2^32 < p
+}
 
 }  // namespace zr

@@ -23,9 +23,16 @@ struct zr_prof {
   long long count[PH_N] = {};
 };
 
+struct zr_plan_entry {
+  int64_t T;
+  int S;
+  zr::StepDims D;
+};
+
 struct zr_ctx {
   zr::Mod M;
   zr_prof prof;
+  std::vector<zr_plan_entry> plans;   // tuned launch plans by (T, S)
   int device = 0;
   int sms = 0;
   // grow-only device workspace
@@ -71,12 +78,12 @@ zr_status cuda_err(zr_ctx* ctx, cudaError_t e, const char* where);
 zr_status ensure_ws(zr_ctx* ctx, size_t need, cudaStream_t st);
 zr_status status_from_flags(zr_ctx* ctx, uint32_t flags);
 StepDims plan_step(const zr_ctx* ctx, int64_t T, int S);
+double plan_cost(const zr_ctx* ctx, const StepDims& D);
 uint64_t hash_slots(int64_t T);
 
 // The device part of one Zippel step on workspace carved by the caller.
 struct StepWs {
   uint64_t *tab, *v, *vp, *htab, *m, *tmp, *R, *part, *denp, *invd, *g;
-  BX* bx;
   int32_t* cnt;
   int64_t* bsum;
 };

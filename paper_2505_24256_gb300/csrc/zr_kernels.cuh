@@ -48,7 +48,10 @@ void launch_expand_b(int64_t T, int S, const uint64_t* b, int64_t ldb, const Mod
 void launch_carry_partials(const StepDims& D, const uint64_t* m, const uint64_t* v, const uint64_t* vp,
                            const Mod& M, uint64_t* R, cudaStream_t st);
 void launch_solve(const StepDims& D, const uint64_t* m, const uint64_t* v, const uint64_t* vp, const uint64_t* R,
-                  const BX* bx, const Mod& M, uint64_t* part, uint64_t* denp, cudaStream_t st);
+                  const uint64_t* b, int64_t ldb, const Mod& M, uint64_t* part, uint64_t* denp, cudaStream_t st);
+// right-hand-side tiles the solve kernel is built for, and its resident CTAs per SM
+int solve_tiles(int* out, int cap);
+int solve_blocks_per_sm(int s_tile);
 // finish: combine partials, batch-invert the denominators, scale.  Writes
 // c (S x ldc) when c != nullptr.
 void launch_finish_solve(const StepDims& D, int offset, const uint64_t* v, const uint64_t* part,

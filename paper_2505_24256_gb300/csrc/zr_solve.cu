@@ -38,17 +38,14 @@ void launch_carry_partials(const StepDims& D, const uint64_t* m, const uint64_t*
 // ---------------------------------------------------------------------------
 // a4 + a5: the hot loop.  Thread = one root j, one k-block, one tile of ST
 // right-hand sides.  Per k (descending):
-//     acc_s += q_{j,k} b[s][k]           (deferred, carry-free MAC)
+//     acc_s += q_{j,k} b[s][k]           (160-bit accumulator, lo/hi carry chains)
 //     u      = u v_j + q_{j,k}             (Horner value q_j(v_j) of the block)
 //     q      = m_k + v_j q_{j,k}           (synthetic division, Shoup multiply)
-// Right-hand sides (MAC form) and m_k are staged in shared memory by cp.async,
-// double buffered; every load is a broadcast.
+// The right-hand sides (plain residues, 8 bytes each) and m_k are staged in
+// shared memory by cp.async, double buffered; every load is a broadcast and
+// two right-hand sides arrive per 16-byte load.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
@@ -57,23 +54,24 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-template <int ST, int NT, int KC>
+template <int ST, int KC>
 struct SolveSmem {
-  uint4 bx[2][KC][ST][2];
+  static constexpr int STP = (ST + 1) & ~1;   // padded to pairs
+  uint64_t b[2][KC][STP];
   uint64_t m[2][KC];
 };
 
 template <int ST, int NT, int KC>
-__device__ __forceinline__ void solve_stage(SolveSmem<ST, NT, KC>& sm, int buf, const BX* __restrict__ bx,
-                                            const uint64_t* __restrict__ m, int S, int s0, int sn, int64_t clo,
-                                            int len) {
-  // bx rows k in [clo, clo+len), columns s0..s0+sn-1; zero padding for s >= sn.
-  const int pieces = len * ST * 2;
+__device__ __forceinline__ void solve_stage(SolveSmem<ST, KC>& sm, int buf, const uint64_t* __restrict__ b,
+                                            int64_t ldb, const uint64_t* __restrict__ m, int s0, int sn,
+                                            int64_t clo, int len) {
+  constexpr int STP = SolveSmem<ST, KC>::STP;
+  const int pieces = STP * len;
   for (int t = threadIdx.x; t < pieces; t += NT) {
-    int kk = t / (ST * 2), rem = t - kk * ST * 2, s = rem >> 1, h = rem & 1;
-    uint4* dst = &sm.bx[buf][kk][s][h];
-    if (s < sn) cp_async16(dst, reinterpret_cast<const uint4*>(bx + (clo + kk) * S + s0 + s) + h);
-    else *dst = make_uint4(0, 0, 0, 0);
+    const int s = t / len, kk = t - s * len;        // consecutive threads walk k: coalesced reads
+    uint64_t* dst = &sm.b[buf][kk][s];
+    if (s < sn) cp_async8(dst, b + (int64_t)(s0 + s) * ldb + clo + kk);
+    else *dst = 0;
   }
   for (int t = threadIdx.x; t < len; t += NT) cp_async8(&sm.m[buf][t], m + clo + t);
 }
@@ -81,10 +79,12 @@ __device__ __forceinline__ void solve_stage(SolveSmem<ST, NT, KC>& sm, int buf, 
 template <int ST, int NT, int KC>
 __global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t BK, const uint64_t* __restrict__ m,
                                               const uint64_t* __restrict__ v, const uint64_t* __restrict__ vp,
-                                              const uint64_t* __restrict__ R, const BX* __restrict__ bx, Mod M,
-                                              uint64_t* __restrict__ part, uint64_t* __restrict__ denp) {
+                                              const uint64_t* __restrict__ R, const uint64_t* __restrict__ b,
+                                              int64_t ldb, Mod M, uint64_t* __restrict__ part,
+                                              uint64_t* __restrict__ denp) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  SolveSmem<ST, NT, KC>& sm = *reinterpret_cast<SolveSmem<ST, NT, KC>*>(smraw);
+  SolveSmem<ST, KC>& sm = *reinterpret_cast<SolveSmem<ST, KC>*>(smraw);
+  constexpr int STP = SolveSmem<ST, KC>::STP;
   const int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x;
   const int kb = blockIdx.y;
   const int s0 = blockIdx.z * ST;
@@ -104,13 +104,11 @@ __global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t 
     q = c;
   }
   uint64_t u = 0;
-  Acc acc[ST];
+  Acc5 acc[ST];
 #pragma unroll
-  for (int s = 0; s < ST; s++) acc[s].L = acc[s].H = 0;
-  int fold = 0;
+  for (int s = 0; s < ST; s++) acc[s].r0 = acc[s].r1 = acc[s].r2 = acc[s].r3 = acc[s].r4 = 0;
 
   const int nchunks = (int)((khi - klo + KC - 1) / KC);
-  // chunk c covers [chi - len, chi) with chi = khi - c KC (descending)
   auto chunk_lo = [&](int c, int& len) -> int64_t {
     int64_t chi = khi - (int64_t)c * KC;
     int64_t clo = chi - KC > klo ? chi - KC : klo;
@@ -120,7 +118,7 @@ __global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t 
   {
     int len;
     int64_t clo = chunk_lo(0, len);
-    solve_stage<ST, NT, KC>(sm, 0, bx, m, S, s0, sn, clo, len);
+    solve_stage<ST, NT, KC>(sm, 0, b, ldb, m, s0, sn, clo, len);
     cp_async_commit();
   }
   for (int c = 0; c < nchunks; c++) {
@@ -128,7 +126,7 @@ __global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t 
     if (c + 1 < nchunks) {
       int len;
       int64_t clo = chunk_lo(c + 1, len);
-      solve_stage<ST, NT, KC>(sm, buf ^ 1, bx, m, S, s0, sn, clo, len);
+      solve_stage<ST, NT, KC>(sm, buf ^ 1, b, ldb, m, s0, sn, clo, len);
     }
     cp_async_commit();
     cp_async_wait<1>();
@@ -137,57 +135,83 @@ __global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t 
     chunk_lo(c, len);
     for (int kk = len - 1; kk >= 0; kk--) {
       const uint64_t qc = canon(q, M);
-      const XL x = limbs21(qc);
+      const uint32_t x0 = lo32(qc), x1 = hi32(qc);
+      const uint4* row = reinterpret_cast<const uint4*>(&sm.b[buf][kk][0]);
 #pragma unroll
-      for (int s = 0; s < ST; s++) {
-        const uint4 b0 = sm.bx[buf][kk][s][0];
-        const uint4 b1 = sm.bx[buf][kk][s][1];
-        mac(acc[s], x, b0, make_uint2(b1.x, b1.y));
+      for (int s = 0; s + 1 < ST; s += 2) {
+        const uint4 w = row[s >> 1];
+        mac5(acc[s], x0, x1, w.x, w.y);
+        mac5(acc[s + 1], x0, x1, w.z, w.w);
+      }
+      if (ST & 1) {
+        const uint2 w = reinterpret_cast<const uint2*>(row)[ST - 1];
+        mac5(acc[ST - 1], x0, x1, w.x, w.y);
       }
       if (do_den) u = canon(shoup_lazy(u, vj, vpj, M), M) + qc;
       q = canon(shoup_lazy(qc, vj, vpj, M), M) + sm.m[buf][kk];
-      if (++fold == MAC_FOLD) {
-#pragma unroll
-        for (int s = 0; s < ST; s++) acc_fold(acc[s], M);
-        fold = 0;
-      }
     }
     __syncthreads();
   }
   if (active) {
 #pragma unroll
     for (int s = 0; s < ST; s++)
-      if (s < sn) part[((int64_t)kb * S + s0 + s) * T + j] = acc_value(acc[s], M);
+      if (s < sn) part[((int64_t)kb * S + s0 + s) * T + j] = acc5_value(acc[s], M);
     if (do_den) denp[(int64_t)kb * T + j] = canon(u, M);
   }
 }
 
 template <int ST, int NT, int KC>
 static void launch_solve_t(const StepDims& D, const uint64_t* m, const uint64_t* v, const uint64_t* vp,
-                           const uint64_t* R, const BX* bx, const Mod& M, uint64_t* part, uint64_t* denp,
-                           cudaStream_t st) {
-  const size_t smem = sizeof(SolveSmem<ST, NT, KC>);
+                           const uint64_t* R, const uint64_t* b, int64_t ldb, const Mod& M, uint64_t* part,
+                           uint64_t* denp, cudaStream_t st) {
+  const size_t smem = sizeof(SolveSmem<ST, KC>);
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_solve<ST, NT, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
   dim3 grid(cdiv(D.T, NT), D.NB, cdiv(D.S, ST));
-  { k_solve<ST, NT, KC><<<grid, NT, smem, st>>>(D.T, D.S, D.NB, D.BK, m, v, vp, R, bx, M, part, denp); note_launch(); }
+  { k_solve<ST, NT, KC><<<grid, NT, smem, st>>>(D.T, D.S, D.NB, D.BK, m, v, vp, R, b, ldb, M, part, denp); note_launch(); }
+}
+
+template <int ST, int NT, int KC>
+static int solve_occupancy_t() {
+  int n = 0;
+  const size_t smem = sizeof(SolveSmem<ST, KC>);
+  cudaFuncSetAttribute(k_solve<ST, NT, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve<ST, NT, KC>, NT, smem) != cudaSuccess) n = 1;
+  return n > 0 ? n : 1;
+}
+
+#define ZR_SOLVE_TILES(X) X(4) X(6) X(8) X(9) X(11) X(12) X(16) X(21)
+
+int solve_tiles(int* out, int cap) {
+  static const int t[] = {4, 6, 8, 9, 11, 12, 16, 21};
+  int n = 0;
+  for (int x : t)
+    if (n < cap) out[n++] = x;
+  return n;
+}
+
+int solve_blocks_per_sm(int s_tile) {
+  switch (s_tile) {
+#define ZR_CASE(ST) \
+  case ST: return solve_occupancy_t<ST, 128, 32>();
+    ZR_SOLVE_TILES(ZR_CASE)
+#undef ZR_CASE
+    default: return 1;
+  }
 }
 
 void launch_solve(const StepDims& D, const uint64_t* m, const uint64_t* v, const uint64_t* vp, const uint64_t* R,
-                  const BX* bx, const Mod& M, uint64_t* part, uint64_t* denp, cudaStream_t st) {
+                  const uint64_t* b, int64_t ldb, const Mod& M, uint64_t* part, uint64_t* denp, cudaStream_t st) {
   if (D.T <= 0 || D.S <= 0) return;
   switch (D.s_tile) {
-    case 4: launch_solve_t<4, 128, 32>(D, m, v, vp, R, bx, M, part, denp, st); break;
-    case 8: launch_solve_t<8, 128, 32>(D, m, v, vp, R, bx, M, part, denp, st); break;
-    case 9: launch_solve_t<9, 128, 32>(D, m, v, vp, R, bx, M, part, denp, st); break;
-    case 11: launch_solve_t<11, 128, 32>(D, m, v, vp, R, bx, M, part, denp, st); break;
-    case 12: launch_solve_t<12, 128, 32>(D, m, v, vp, R, bx, M, part, denp, st); break;
-    case 16: launch_solve_t<16, 128, 32>(D, m, v, vp, R, bx, M, part, denp, st); break;
-    case 21: launch_solve_t<21, 128, 32>(D, m, v, vp, R, bx, M, part, denp, st); break;
-    default: launch_solve_t<24, 128, 32>(D, m, v, vp, R, bx, M, part, denp, st); break;
+#define ZR_CASE(ST) \
+  case ST: launch_solve_t<ST, 128, 32>(D, m, v, vp, R, b, ldb, M, part, denp, st); break;
+    ZR_SOLVE_TILES(ZR_CASE)
+#undef ZR_CASE
+    default: launch_solve_t<21, 128, 32>(D, m, v, vp, R, b, ldb, M, part, denp, st); break;
   }
 }
 

@@ -71,6 +71,8 @@ SIGNATURES = {
     "zr_launch_count": (_U64, []),
     "zr_profile_enable": (_ST, [_V, _I32]),
     "zr_profile_query": (_ST, [_V, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+    "zr_autotune_step": (_ST, [_V, _I64, _I32, _I32, _V]),
+    "zr_step_plan": (_ST, [_V, _I64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "zr_vandermonde_solve_batched": (_ST, [_V, _I32, _P, _V]),
     "zr_vandermonde_solve_plain": (_ST, [_V, _I32, _P, _V]),
     "zr_newton_batched": (_ST, [_V, _I64, _I32, _P, _P, _I64, _P, _V]),
@@ -167,6 +169,14 @@ class Context:
 
     def profile(self, on: bool = True):
         self.check(self.L.zr_profile_enable(self._h, 1 if on else 0), "zr_profile_enable")
+
+    def autotune_step(self, T, S, budget=12, stream=None):
+        self.check(self.L.zr_autotune_step(self._h, T, S, budget, _stream(stream)), "zr_autotune_step")
+
+    def step_plan(self, T, S):
+        tile, nb = ctypes.c_int32(), ctypes.c_int32()
+        self.check(self.L.zr_step_plan(self._h, T, S, ctypes.byref(tile), ctypes.byref(nb)), "zr_step_plan")
+        return tile.value, nb.value
 
     def profile_query(self, phase):
         idx = self.PHASES.index(phase) if isinstance(phase, str) else int(phase)
