@@ -287,6 +287,42 @@ __device__ __forceinline__ void mac5(Acc5& a, uint32_t x0, uint32_t x1, uint32_t
       : "+r"(a.r0), "+r"(a.r1), "+r"(a.r2), "+r"(a.r3), "+r"(a.r4)
       : "r"(x0), "r"(x1), "r"(b0), "r"(b1));
 }
+// Even/odd split: x0 b0 and x1 b1 (bit offsets 0 and 64) go into r0..r4, the
+// two cross products (bit offset 32) into t0..t2.  Two short independent
+// carry chains per product instead of one long one: more instruction-level
+// parallelism for the same eight multiplies.  r4 and t2 count carries, so
+// fewer than 2^31 products never overflow.
+struct Acc8 { uint32_t r0, r1, r2, r3, r4, t0, t1, t2; };
+__device__ __forceinline__ void mac8(Acc8& a, uint32_t x0, uint32_t x1, uint32_t b0, uint32_t b1) {
+  asm("mad.lo.cc.u32 %0, %8, %10, %0;\n\t"
+      "madc.hi.cc.u32 %1, %8, %10, %1;\n\t"
+      "madc.lo.cc.u32 %2, %9, %11, %2;\n\t"
+      "madc.hi.cc.u32 %3, %9, %11, %3;\n\t"
+      "addc.u32 %4, %4, 0;\n\t"
+      "mad.lo.cc.u32 %5, %9, %10, %5;\n\t"
+      "madc.hi.cc.u32 %6, %9, %10, %6;\n\t"
+      "addc.u32 %7, %7, 0;\n\t"
+      "mad.lo.cc.u32 %5, %8, %11, %5;\n\t"
+      "madc.hi.cc.u32 %6, %8, %11, %6;\n\t"
+      "addc.u32 %7, %7, 0;"
+      : "+r"(a.r0), "+r"(a.r1), "+r"(a.r2), "+r"(a.r3), "+r"(a.r4), "+r"(a.t0), "+r"(a.t1), "+r"(a.t2)
+      : "r"(x0), "r"(x1), "r"(b0), "r"(b1));
+}
+// residue of r + t 2^32
+__device__ __forceinline__ uint64_t acc8_value(const Acc8& a, const Mod& M) {
+  const uint64_t L = ((uint64_t)a.r1 << 32) | a.r0;
+  const uint64_t Mi = ((uint64_t)a.r3 << 32) | a.r2;
+  const uint64_t Tt = ((uint64_t)a.t2 << 32) | a.t1;
+  const uint64_t L2 = L + ((uint64_t)a.t0 << 32);
+  const uint64_t c1 = L2 < L;
+  const uint64_t M1 = Mi + Tt;
+  const uint64_t c2 = M1 < Mi;
+  const uint64_t M2 = M1 + c1;
+  const uint64_t c3 = M2 < M1;
+  const uint64_t top = (uint64_t)a.r4 + c2 + c3;       // < 2^33 < p
+  return reduce128(reduce128(top, M2, M), L2, M);
+}
+
 __device__ __forceinline__ uint64_t acc5_value(const Acc5& a, const Mod& M) {
   const uint64_t mid = ((uint64_t)a.r3 << 32) | a.r2, low = ((uint64_t)a.r1 << 32) | a.r0;
   return reduce128(reduce128(a.r4, mid, M), low, M);    // r4 < 2^32 < p

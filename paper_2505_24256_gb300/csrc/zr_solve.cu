@@ -38,7 +38,7 @@ void launch_carry_partials(const StepDims& D, const uint64_t* m, const uint64_t*
 // ---------------------------------------------------------------------------
 // a4 + a5: the hot loop.  Thread = one root j, one k-block, one tile of ST
 // right-hand sides.  Per k (descending):
-//     acc_s += q_{j,k} b[s][k]           (160-bit accumulator, lo/hi carry chains)
+//     acc_s += q_{j,k} b[s][k]           (even/odd lo/hi carry chains, reduced once)
 //     u      = u v_j + q_{j,k}             (Horner value q_j(v_j) of the block)
 //     q      = m_k + v_j q_{j,k}           (synthetic division, Shoup multiply)
 // The right-hand sides (plain residues, 8 bytes each) and m_k are staged in
@@ -76,8 +76,12 @@ __device__ __forceinline__ void solve_stage(SolveSmem<ST, KC>& sm, int buf, cons
   for (int t = threadIdx.x; t < len; t += NT) cp_async8(&sm.m[buf][t], m + clo + t);
 }
 
+// resident CTAs per SM the compiler is asked to fit (register budget)
+template <int ST>
+struct SolveMinBlocks { static constexpr int value = ST <= 6 ? 4 : (ST <= 12 ? 3 : 2); };
+
 template <int ST, int NT, int KC>
-__global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t BK, const uint64_t* __restrict__ m,
+__global__ void __launch_bounds__(NT, SolveMinBlocks<ST>::value) k_solve(int64_t T, int S, int NB, int64_t BK, const uint64_t* __restrict__ m,
                                               const uint64_t* __restrict__ v, const uint64_t* __restrict__ vp,
                                               const uint64_t* __restrict__ R, const uint64_t* __restrict__ b,
                                               int64_t ldb, Mod M, uint64_t* __restrict__ part,
@@ -104,9 +108,9 @@ __global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t 
     q = c;
   }
   uint64_t u = 0;
-  Acc5 acc[ST];
+  Acc8 acc[ST];
 #pragma unroll
-  for (int s = 0; s < ST; s++) acc[s].r0 = acc[s].r1 = acc[s].r2 = acc[s].r3 = acc[s].r4 = 0;
+  for (int s = 0; s < ST; s++) acc[s] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
 
   const int nchunks = (int)((khi - klo + KC - 1) / KC);
   auto chunk_lo = [&](int c, int& len) -> int64_t {
@@ -140,12 +144,12 @@ __global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t 
 #pragma unroll
       for (int s = 0; s + 1 < ST; s += 2) {
         const uint4 w = row[s >> 1];
-        mac5(acc[s], x0, x1, w.x, w.y);
-        mac5(acc[s + 1], x0, x1, w.z, w.w);
+        mac8(acc[s], x0, x1, w.x, w.y);
+        mac8(acc[s + 1], x0, x1, w.z, w.w);
       }
       if (ST & 1) {
         const uint2 w = reinterpret_cast<const uint2*>(row)[ST - 1];
-        mac5(acc[ST - 1], x0, x1, w.x, w.y);
+        mac8(acc[ST - 1], x0, x1, w.x, w.y);
       }
       if (do_den) u = canon(shoup_lazy(u, vj, vpj, M), M) + qc;
       q = canon(shoup_lazy(qc, vj, vpj, M), M) + sm.m[buf][kk];
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(NT) k_solve(int64_t T, int S, int NB, int64_t 
   if (active) {
 #pragma unroll
     for (int s = 0; s < ST; s++)
-      if (s < sn) part[((int64_t)kb * S + s0 + s) * T + j] = acc5_value(acc[s], M);
+      if (s < sn) part[((int64_t)kb * S + s0 + s) * T + j] = acc8_value(acc[s], M);
     if (do_den) denp[(int64_t)kb * T + j] = canon(u, M);
   }
 }
