@@ -288,9 +288,21 @@ static int eval_tile(int S) {
   return 21;
 }
 
+// Workspace bytes the evaluator needs for (f, S, T).
+size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);
+
 zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
                       const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
                       cudaStream_t st) {
+  zr_status r = ensure_ws(ctx, probes_ws_need(ctx, f, k, S, T), st);
+  if (r) return r;
+  return probes_enqueue(ctx, f, k, y, S, samples, z, T, offset, out, ldo, status, ctx->ws, st);
+}
+
+// The evaluation itself, with its scratch at `base` (capacity checked by the caller).
+zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
+                         const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
+                         char* base, cudaStream_t st) {
   const Mod& M = ctx->M;
   const int64_t Tf = f->T;
   const int nv = f->nv;
@@ -327,11 +339,7 @@ zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, i
   int32_t* gid;
   unsigned long long* Wacc;
   BX* Wbx;
-  Carver m0(nullptr);
-  layout(m0, &tabY, &tabZ, &tabC, &u, &w, &htab, &bsum, &gid, &U, &Wacc, &Wbx, &UP, &partial, &Gdev);
-  zr_status r = ensure_ws(ctx, m0.off, st);
-  if (r) return r;
-  Carver cv(ctx->ws);
+  Carver cv(base);
   layout(cv, &tabY, &tabZ, &tabC, &u, &w, &htab, &bsum, &gid, &U, &Wacc, &Wbx, &UP, &partial, &Gdev);
 
   if (T <= 0) return ZR_OK;
@@ -370,6 +378,36 @@ zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, i
   return cuda_err(ctx, cudaGetLastError(), "zr_zippel_probes");
 }
 
+size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T) {
+  const int64_t Tf = f->T;
+  const int nv = f->nv;
+  const uint64_t H = hash_slots(Tf > 0 ? Tf : 1);
+  const int64_t nbH = (int64_t)((H + kB - 1) / kB);
+  const int stile = eval_tile(S);
+  const int nst = (S + stile - 1) / stile;
+  const int64_t ctas = (int64_t)cdiv(T, kNI) * nst;
+  int gsplit = 1;
+  const int64_t want = 2ll * (ctx && ctx->sms ? ctx->sms : 152);
+  while (ctas * gsplit < want && gsplit < 64 && Tf / (gsplit * 2) >= 2 * kGC) gsplit *= 2;
+  const int64_t Tn = Tf > 0 ? Tf : 1;
+  Carver cv(nullptr);
+  cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
+  cv.take<uint64_t>((size_t)nv * kPowTab);
+  cv.take<uint64_t>((size_t)S * kPowTab);
+  cv.take<uint64_t>(Tn);
+  cv.take<uint64_t>((size_t)Tn * S);
+  cv.take<uint64_t>(H);
+  cv.take<int64_t>(nbH + 1);
+  cv.take<int32_t>(H);
+  cv.take<uint64_t>(Tn);
+  cv.take<unsigned long long>((size_t)Tn * S * 2);
+  cv.take<BX>((size_t)Tn * S);
+  cv.take<uint64_t>((size_t)Tn * 32);
+  cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
+  cv.take<int64_t>(1);
+  return cv.off;
+}
+
 // ---------------------------------------------------------------------------
 // f at arbitrary points: one CTA per point, terms split over the threads,
 // partial sums reduced with shuffles (Sec. 2.2's warp sum, full-warp mask).
@@ -399,6 +437,11 @@ __global__ void __launch_bounds__(256) k_eval_points(int64_t Tf, int nv, const u
     for (int q = 0; q < 8; q++) s = add_mod(s, red[q], M);
     out[pt] = s;
   }
+}
+
+void launch_eval_points(const zr_poly* f, int64_t npts, const uint64_t* pts, const Mod& M, uint64_t* out,
+                        cudaStream_t st) {
+  if (npts > 0) { k_eval_points<<<(unsigned)npts, 256, 0, st>>>(f->T, f->nv, f->exps, f->coef, pts, M, out); note_launch(); }
 }
 
 }  // namespace zr

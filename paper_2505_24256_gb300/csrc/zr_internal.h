@@ -94,8 +94,26 @@ void enqueue_step(zr_ctx* ctx, const StepWs& w, const StepDims& D, const zr_poly
                   uint64_t* out_coef, int64_t out_cap, int64_t* d_out_count, uint32_t* status, cudaStream_t st);
 
 // evaluator (zr_eval.cu)
+size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);
+zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
+                         const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
+                         char* base, cudaStream_t st);
 zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
                       const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
                       cudaStream_t st);
+
+// balanced step pieces (zr_balance.cu)
+void launch_ratio(int64_t T, int S, const uint64_t* Nv, const uint64_t* Dv, int64_t ld, const Mod& M, uint64_t* pre,
+                  uint64_t* out, int64_t ldo, uint32_t* status, cudaStream_t st);
+size_t thiele_scratch_words(int64_t Tmax, int n);
+void launch_thiele_balance(int64_t Tmax, int n, const uint64_t* xs, const uint64_t* fvals, int64_t ldf,
+                           const uint64_t* dprev, int dN, int dD, int64_t TN, int64_t TD, uint64_t* scratch,
+                           const Mod& M, uint64_t* bN, int64_t ldN, uint64_t* bD, int64_t ldD, uint32_t* status,
+                           cudaStream_t st);
+void launch_normalise(int64_t n1, uint64_t* a1, int64_t n2, uint64_t* a2, const uint64_t* pivot, uint64_t* tmp,
+                      const Mod& M, uint32_t* status, cudaStream_t st);
+// kernels used by the reconstruction driver
+void launch_eval_points(const zr_poly* f, int64_t npts, const uint64_t* pts, const Mod& M, uint64_t* out,
+                        cudaStream_t st);
 
 }  // namespace zr
