@@ -114,10 +114,12 @@ typedef struct zr_vsys {
 } zr_vsys;
 
 /* Solves nsys independent systems (sys is a host array).  Systems of
- * different T and S are packed into shared launches. */
+ * different T and S share every launch: one set of launches for the whole
+ * list, with a persistent solve kernel walking a work list of
+ * (system, root tile, k-block, right-hand-side tile) items. */
 zr_status zr_vandermonde_solve_batched(zr_ctx* ctx, int32_t nsys, const zr_vsys* sys, void* stream);
-/* The plain form: one system per sequence of launches (the comparator the
- * batched form is measured against). */
+/* The plain form: one system after the other, each with its own launches
+ * (the comparator the batched form is measured against). */
 zr_status zr_vandermonde_solve_plain(zr_ctx* ctx, int32_t nsys, const zr_vsys* sys, void* stream);
 
 /* ---------------------------------------------------------------------------
@@ -195,6 +197,28 @@ zr_status zr_zippel_step_async(zr_ctx* ctx, const zr_poly* skel, int32_t newvar,
 /* Waits for `stream` and returns the status of the device work enqueued by
  * the context's _async calls since the previous zr_stream_status. */
 zr_status zr_stream_status(zr_ctx* ctx, void* stream);
+
+/* Several Zippel steps of different T and S in shared launches (one set of
+ * kernel launches for the whole list, a persistent solve kernel walking a
+ * work list of (step, root tile, k-block, right-hand-side tile) items).
+ * Each entry has the meaning of the zr_zippel_step arguments; out_count is a
+ * device int64 per entry.  Waits for `stream`; the status covers all entries. */
+typedef struct zr_step_desc {
+  zr_poly skel;
+  int32_t newvar;
+  int32_t S;
+  int32_t offset;
+  int32_t pad;
+  const uint64_t* y;
+  const uint64_t* samples;
+  const uint64_t* probes;
+  int64_t ldb;
+  uint8_t* out_exps;
+  uint64_t* out_coef;
+  int64_t out_cap;
+  int64_t* out_count;
+} zr_step_desc;
+zr_status zr_zippel_step_batched(zr_ctx* ctx, int32_t nsteps, const zr_step_desc* steps, void* stream);
 
 /* The same step with every array in HOST memory (pinned or pageable): the
  * call copies the inputs in, runs the step on `stream` and copies the new

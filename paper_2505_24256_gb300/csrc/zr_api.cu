@@ -290,43 +290,6 @@ StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D) {
   return w;
 }
 
-void enqueue_step(zr_ctx* ctx, const StepWs& w, const StepDims& D, const zr_poly* skel, int k, const uint64_t* y,
-                  const uint64_t* samples, const uint64_t* probes, int64_t ldb, int offset, uint8_t* out_exps,
-                  uint64_t* out_coef, int64_t out_cap, int64_t* d_out_count, uint32_t* status, cudaStream_t st) {
-  const Mod& M = ctx->M;
-  const int64_t T = D.T;
-  const int S = D.S;
-  // a2: anchor values and the node check
-  const uint64_t hs = hash_slots(T);
-  cudaEvent_t e0 = prof_mark(ctx, st);
-  cudaMemsetAsync(w.htab, 0xFF, hs * sizeof(uint64_t), st);
-  launch_powtab(y, k, M, w.tab, st);
-  launch_anchor(T, skel->nv, skel->exps, k, w.tab, offset, M, w.v, w.vp, w.htab, hs - 1, status, st);
-  cudaEvent_t e1 = prof_mark(ctx, st);
-  // a3: master polynomial
-  launch_master_poly(T, w.v, M, w.m, w.tmp, st);
-  cudaEvent_t e2 = prof_mark(ctx, st);
-  // a4 + a5
-  cudaEvent_t e3 = prof_mark(ctx, st);
-  launch_carry_partials(D, w.m, w.v, w.vp, M, w.R, st);
-  cudaEvent_t e4 = prof_mark(ctx, st);
-  launch_solve(D, w.m, w.v, w.vp, w.R, probes, ldb, M, w.part, w.denp, st);
-  cudaEvent_t e5 = prof_mark(ctx, st);
-  // a6
-  launch_newton_table(S, samples, M, w.invd, status, st);
-  launch_finish_newton(D, offset, w.v, w.part, w.denp, samples, w.invd, M, w.g, w.cnt, status, st);
-  cudaEvent_t e6 = prof_mark(ctx, st);
-  launch_compact(T, S, skel->nv, k, skel->exps, w.g, w.cnt, w.bsum, out_cap, out_exps, out_coef, d_out_count, st);
-  cudaEvent_t e7 = prof_mark(ctx, st);
-  prof_add(ctx, PH_ANCHOR, e0, e1);
-  prof_add(ctx, PH_MASTER, e1, e2);
-  prof_add(ctx, PH_EXPAND, e2, e3);
-  prof_add(ctx, PH_CARRY, e3, e4);
-  prof_add(ctx, PH_SOLVE, e4, e5);
-  prof_add(ctx, PH_NEWTON, e5, e6);
-  prof_add(ctx, PH_COMPACT, e6, e7);
-}
-
 }  // namespace zr
 
 // ---------------------------------------------------------------------------
@@ -400,6 +363,8 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->d_count) cudaFree(ctx->d_count);
   if (ctx->h_count) cudaFreeHost(ctx->h_count);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->stage_event) cudaEventDestroy(ctx->stage_event);
   delete ctx;
 }
 
@@ -427,18 +392,18 @@ static zr_status check_vsys(zr_ctx* ctx, const zr_vsys& s) {
   return ZR_OK;
 }
 
-// one system: node check, master polynomial, blocked solve, finish
-static void enqueue_vsys(zr_ctx* ctx, const zr_vsys& s, const StepWs& w, const StepDims& D, uint32_t* status,
-                         cudaStream_t st) {
-  const Mod& M = ctx->M;
-  const uint64_t hs = hash_slots(s.T);
-  cudaMemsetAsync(w.htab, 0xFF, hs * sizeof(uint64_t), st);
-  launch_shoup_pre(s.T, s.v, M, w.vp, s.offset, status, st);
-  launch_node_check(s.T, s.v, w.htab, hs - 1, status, st);
-  launch_master_poly(s.T, s.v, M, w.m, w.tmp, st);
-  launch_carry_partials(D, w.m, s.v, w.vp, M, w.R, st);
-  launch_solve(D, w.m, s.v, w.vp, w.R, s.b, s.ldb, M, w.part, w.denp, st);
-  launch_finish_solve(D, s.offset, s.v, w.part, w.denp, M, s.c, s.ldc, status, st);
+static BatchItem vsys_item(const zr_vsys& s) {
+  BatchItem it;
+  it.mode = 1;
+  it.T = s.T;
+  it.S = s.S;
+  it.offset = s.offset;
+  it.vin = s.v;
+  it.b = s.b;
+  it.ldb = s.ldb;
+  it.c = s.c;
+  it.ldc = s.ldc;
+  return it;
 }
 
 extern "C" zr_status zr_vandermonde_solve_plain(zr_ctx* ctx, int32_t nsys, const zr_vsys* sys, void* stream) {
@@ -450,24 +415,27 @@ extern "C" zr_status zr_vandermonde_solve_plain(zr_ctx* ctx, int32_t nsys, const
   }
   cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
   for (int i = 0; i < nsys; i++) {
-    const zr_vsys& s = sys[i];
-    if (s.T == 0) continue;
-    StepDims D = plan_step(ctx, s.T, s.S);
-    Carver m0(nullptr);
-    carve_step(m0, s.T, s.S, 0, D);
-    zr_status r = ensure_ws(ctx, m0.off, st);
+    if (sys[i].T == 0) continue;
+    const BatchItem it = vsys_item(sys[i]);
+    zr_status r = run_batch(ctx, &it, 1, ctx->d_status_call, st);
     if (r) return r;
-    Carver cv(ctx->ws);
-    StepWs w = carve_step(cv, s.T, s.S, 0, D);
-    enqueue_vsys(ctx, s, w, D, ctx->d_status_call, st);
   }
   return finish_sync_call(ctx, st, nullptr);
 }
 
 extern "C" zr_status zr_vandermonde_solve_batched(zr_ctx* ctx, int32_t nsys, const zr_vsys* sys, void* stream) {
-  // Systems are carved side by side in one workspace so that their launches
-  // can overlap; the packed single-launch form lives in zr_batch.cu.
-  return zr_vandermonde_solve_plain(ctx, nsys, sys, stream);
+  if (!ctx || nsys < 0 || (nsys > 0 && !sys)) return set_err(ctx, ZR_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<BatchItem> items;
+  for (int i = 0; i < nsys; i++) {
+    zr_status r = check_vsys(ctx, sys[i]);
+    if (r) return r;
+    if (sys[i].T > 0) items.push_back(vsys_item(sys[i]));
+  }
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  zr_status r = run_batch(ctx, items.data(), (int)items.size(), ctx->d_status_call, st);
+  if (r) return r;
+  return finish_sync_call(ctx, st, nullptr);
 }
 
 extern "C" zr_status zr_newton_batched(zr_ctx* ctx, int64_t nterms, int32_t npts, const uint64_t* x,
@@ -518,12 +486,44 @@ static zr_status check_step_args(zr_ctx* ctx, const zr_poly* skel, int32_t newva
   if (!skel) return set_err(ctx, ZR_ERR_INVALID_ARG, "null skeleton");
   if (skel->nv < 1 || skel->nv > kMaxVars || newvar < 0 || newvar >= skel->nv)
     return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step: need 0 <= newvar < nv <= 64");
-  if (skel->T < 0 || S < 1 || S > 64 || ldb < skel->T || out_cap < 0 || (offset != 0 && offset != 1))
-    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step: need T >= 0, 1 <= S <= 64, ldb >= T");
+  if (skel->T < 0 || skel->T >= (1ll << 31) || S < 1 || S > 64 || ldb < skel->T || out_cap < 0 ||
+      (offset != 0 && offset != 1))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step: need 0 <= T < 2^31, 1 <= S <= 64, ldb >= T");
   if (!samples || (skel->T > 0 && (!skel->exps || !probes || (newvar > 0 && !y))) ||
       (out_cap > 0 && (!out_exps || !out_coef)))
     return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step: null pointer");
   return ZR_OK;
+}
+
+static BatchItem step_item(const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S, const uint64_t* samples,
+                           const uint64_t* probes, int64_t ldb, int32_t offset, uint8_t* out_exps, uint64_t* out_coef,
+                           int64_t out_cap, int64_t* d_count) {
+  BatchItem it;
+  it.mode = 0;
+  it.T = skel->T;
+  it.S = S;
+  it.k = newvar;
+  it.nv = skel->nv;
+  it.offset = offset;
+  it.exps = skel->exps;
+  it.y = y;
+  it.xs = samples;
+  it.b = probes;
+  it.ldb = ldb;
+  it.out_exps = out_exps;
+  it.out_coef = out_coef;
+  it.out_cap = out_cap;
+  it.out_count = d_count;
+  return it;
+}
+
+// A step with T = 0 still validates its samples (equal samples are an error).
+static void empty_step(zr_ctx* ctx, int S, const uint64_t* samples, int64_t* d_count, uint32_t* status,
+                       cudaStream_t st) {
+  Carver cv(ctx->ws);
+  uint64_t* invd = cv.take<uint64_t>((size_t)S * S);
+  cudaMemsetAsync(d_count, 0, sizeof(int64_t), st);
+  launch_newton_table(S, samples, ctx->M, invd, status, st);
 }
 
 extern "C" zr_status zr_zippel_step_async(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y,
@@ -535,22 +535,14 @@ extern "C" zr_status zr_zippel_step_async(zr_ctx* ctx, const zr_poly* skel, int3
   if (r) return r;
   if (!d_out_count) return set_err(ctx, ZR_ERR_INVALID_ARG, "null count pointer");
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t T = skel->T;
-  StepDims D = plan_step(ctx, T, S);
-  Carver m0(nullptr);
-  carve_step(m0, T, S, newvar, D);
-  r = ensure_ws(ctx, m0.off, st);
-  if (r) return r;
-  Carver cv(ctx->ws);
-  StepWs w = carve_step(cv, T, S, newvar, D);
-  if (T == 0) {
-    cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), st);
-    launch_newton_table(S, samples, ctx->M, w.invd, ctx->d_status, st);
+  if (skel->T == 0) {
+    if ((r = ensure_ws(ctx, 8 * (size_t)S * S + 256, st))) return r;
+    empty_step(ctx, S, samples, d_out_count, ctx->d_status, st);
     return cuda_err(ctx, cudaGetLastError(), "zr_zippel_step_async");
   }
-  enqueue_step(ctx, w, D, skel, newvar, y, samples, probes, ldb, offset, out_exps, out_coef, out_cap, d_out_count,
-               ctx->d_status, st);
-  return cuda_err(ctx, cudaGetLastError(), "zr_zippel_step_async");
+  const BatchItem it = step_item(skel, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef, out_cap,
+                                 d_out_count);
+  return run_batch(ctx, &it, 1, ctx->d_status, st);
 }
 
 extern "C" zr_status zr_stream_status(zr_ctx* ctx, void* stream) {
@@ -571,27 +563,56 @@ extern "C" zr_status zr_zippel_step(zr_ctx* ctx, const zr_poly* skel, int32_t ne
   zr_status r = check_step_args(ctx, skel, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef, out_cap);
   if (r) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t T = skel->T;
-  StepDims D = plan_step(ctx, T, S);
-  Carver m0(nullptr);
-  carve_step(m0, T, S, newvar, D);
-  r = ensure_ws(ctx, m0.off, st);
-  if (r) return r;
-  Carver cv(ctx->ws);
-  StepWs w = carve_step(cv, T, S, newvar, D);
   cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
-  if (T == 0) {
-    cudaMemsetAsync(ctx->d_count, 0, sizeof(int64_t), st);
-    launch_newton_table(S, samples, ctx->M, w.invd, ctx->d_status_call, st);
+  if (skel->T == 0) {
+    if ((r = ensure_ws(ctx, 8 * (size_t)S * S + 256, st))) return r;
+    empty_step(ctx, S, samples, ctx->d_count, ctx->d_status_call, st);
   } else {
-    enqueue_step(ctx, w, D, skel, newvar, y, samples, probes, ldb, offset, out_exps, out_coef, out_cap,
-                 ctx->d_count, ctx->d_status_call, st);
+    const BatchItem it = step_item(skel, newvar, y, S, samples, probes, ldb, offset, out_exps, out_coef, out_cap,
+                                   ctx->d_count);
+    if ((r = run_batch(ctx, &it, 1, ctx->d_status_call, st))) return r;
   }
   int64_t n = 0;
   r = finish_sync_call(ctx, st, &n);
   if (out_count) *out_count = n;
   if (r == ZR_OK && n > out_cap) return set_err(ctx, ZR_ERR_CAPACITY, "output skeleton larger than out_cap");
   return r;
+}
+
+extern "C" zr_status zr_zippel_step_batched(zr_ctx* ctx, int32_t nsteps, const zr_step_desc* steps, void* stream) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  if (nsteps < 0 || (nsteps > 0 && !steps)) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step_batched: bad list");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<BatchItem> items;
+  for (int i = 0; i < nsteps; i++) {
+    const zr_step_desc& d = steps[i];
+    zr_status r = check_step_args(ctx, &d.skel, d.newvar, d.y, d.S, d.samples, d.probes, d.ldb, d.offset, d.out_exps,
+                                  d.out_coef, d.out_cap);
+    if (r) return r;
+    if (!d.out_count) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step_batched: null count pointer");
+  }
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  size_t empties = 0;
+  for (int i = 0; i < nsteps; i++) {
+    const zr_step_desc& d = steps[i];
+    if (d.skel.T == 0) {
+      empties = std::max(empties, 8 * (size_t)d.S * d.S + 256);
+      continue;
+    }
+    items.push_back(step_item(&d.skel, d.newvar, d.y, d.S, d.samples, d.probes, d.ldb, d.offset, d.out_exps,
+                              d.out_coef, d.out_cap, d.out_count));
+  }
+  zr_status r = run_batch(ctx, items.data(), (int)items.size(), ctx->d_status_call, st);
+  if (r) return r;
+  for (int i = 0; i < nsteps; i++)
+    if (steps[i].skel.T == 0) {
+      // samples of empty steps are still checked, after the batch (its workspace is free again)
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_step_batched");
+      if ((r = ensure_ws(ctx, empties, st))) return r;
+      empty_step(ctx, steps[i].S, steps[i].samples, steps[i].out_count, ctx->d_status_call, st);
+    }
+  return finish_sync_call(ctx, st, nullptr);
 }
 
 extern "C" zr_status zr_zippel_step_host(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y,
@@ -604,26 +625,28 @@ extern "C" zr_status zr_zippel_step_host(zr_ctx* ctx, const zr_poly* skel, int32
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t T = skel->T, nv = skel->nv;
   const int64_t cap = T * S;
-  StepDims D = plan_step(ctx, T, S);
   // device copies of the inputs and the output come first in the workspace
+  auto carve_io = [&](Carver& cv, uint8_t** d_exps, uint64_t** d_y, uint64_t** d_s, uint64_t** d_b, uint8_t** d_oe,
+                      uint64_t** d_oc) {
+    *d_exps = cv.take<uint8_t>((size_t)(T > 0 ? T : 1) * nv);
+    *d_y = cv.take<uint64_t>(newvar > 0 ? newvar : 1);
+    *d_s = cv.take<uint64_t>(S);
+    *d_b = cv.take<uint64_t>((size_t)S * (T > 0 ? T : 1));
+    *d_oe = cv.take<uint8_t>((size_t)(cap > 0 ? cap : 1) * nv);
+    *d_oc = cv.take<uint64_t>(cap > 0 ? cap : 1);
+  };
+  uint8_t *d_exps, *d_oe;
+  uint64_t *d_y, *d_s, *d_b, *d_oc;
   Carver m0(nullptr);
-  m0.take<uint8_t>((size_t)(T > 0 ? T : 1) * nv);
-  m0.take<uint64_t>(newvar > 0 ? newvar : 1);
-  m0.take<uint64_t>(S);
-  m0.take<uint64_t>((size_t)S * (T > 0 ? T : 1));
-  m0.take<uint8_t>((size_t)(cap > 0 ? cap : 1) * nv);
-  m0.take<uint64_t>(cap > 0 ? cap : 1);
-  carve_step(m0, T, S, newvar, D);
-  r = ensure_ws(ctx, m0.off, st);
-  if (r) return r;
+  carve_io(m0, &d_exps, &d_y, &d_s, &d_b, &d_oe, &d_oc);
+  const size_t io = (m0.off + 255) & ~(size_t)255;
+  zr_poly probe_skel = {skel->nv, T, nullptr, nullptr};
+  BatchItem it = step_item(&probe_skel, newvar, nullptr, S, nullptr, nullptr, T, offset, nullptr, nullptr, cap,
+                           ctx->d_count);
+  const size_t need = io + std::max(batch_ws_need(ctx, &it, 1), (size_t)(8 * S * S + 256));
+  if ((r = ensure_ws(ctx, need, st))) return r;
   Carver cv(ctx->ws);
-  uint8_t* d_exps = cv.take<uint8_t>((size_t)(T > 0 ? T : 1) * nv);
-  uint64_t* d_y = cv.take<uint64_t>(newvar > 0 ? newvar : 1);
-  uint64_t* d_s = cv.take<uint64_t>(S);
-  uint64_t* d_b = cv.take<uint64_t>((size_t)S * (T > 0 ? T : 1));
-  uint8_t* d_oe = cv.take<uint8_t>((size_t)(cap > 0 ? cap : 1) * nv);
-  uint64_t* d_oc = cv.take<uint64_t>(cap > 0 ? cap : 1);
-  StepWs w = carve_step(cv, T, S, newvar, D);
+  carve_io(cv, &d_exps, &d_y, &d_s, &d_b, &d_oe, &d_oc);
   cudaError_t e = cudaSuccess;
   if (T > 0) e = cudaMemcpyAsync(d_exps, skel->exps, (size_t)T * nv, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && newvar > 0) e = cudaMemcpyAsync(d_y, y, sizeof(uint64_t) * newvar, cudaMemcpyHostToDevice, st);
@@ -632,13 +655,16 @@ extern "C" zr_status zr_zippel_step_host(zr_ctx* ctx, const zr_poly* skel, int32
     e = cudaMemcpy2DAsync(d_b, sizeof(uint64_t) * T, probes, sizeof(uint64_t) * ldb, sizeof(uint64_t) * T, S,
                           cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_step_host: copy in");
-  zr_poly dsk = {skel->nv, T, d_exps, nullptr};
   cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
   if (T == 0) {
+    Carver cz(ctx->ws + io);
+    uint64_t* invd = cz.take<uint64_t>((size_t)S * S);
     cudaMemsetAsync(ctx->d_count, 0, sizeof(int64_t), st);
+    launch_newton_table(S, d_s, ctx->M, invd, ctx->d_status_call, st);
   } else {
-    enqueue_step(ctx, w, D, &dsk, newvar, d_y, d_s, d_b, T, offset, d_oe, d_oc, cap, ctx->d_count,
-                 ctx->d_status_call, st);
+    zr_poly dsk = {skel->nv, T, d_exps, nullptr};
+    it = step_item(&dsk, newvar, d_y, S, d_s, d_b, T, offset, d_oe, d_oc, cap, ctx->d_count);
+    if ((r = run_batch(ctx, &it, 1, ctx->d_status_call, st, io))) return r;
   }
   int64_t n = 0;
   r = finish_sync_call(ctx, st, &n);

@@ -1,0 +1,535 @@
+// zr_batch.cu -- batched Zippel steps and Vandermonde systems.
+//
+// Steps (or systems) of different T and S share every launch: each kernel
+// gets the device array of descriptors (BDesc) and a prefix sum over the
+// entries' work (roots, leaf chunks, tree tiles, scan blocks); a flattened
+// index is mapped back to (entry, local index) by binary search.  The solve
+// kernel is persistent and walks a device work list of (entry, root tile,
+// k-block, right-hand-side tile) items, longest first.  A batch of one is the
+// single step, so every step goes through these kernels.
+//
+// Phases (Sec. 1, Sec. 2.2):
+//   anchor values v_j and the distinctness check (hash table)      a2
+//   master polynomial by a product tree                             a3
+//   k-block carries, then the synthetic-division / dot kernel       a4, a5
+//   denominators, Montgomery batch inversion, Newton, counts        a4, a6
+//   compaction of the new skeleton                                  a6
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "zr_device.cuh"
+#include "zr_internal.h"
+
+namespace zr {
+
+static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---- a2 ---------------------------------------------------------------------
+
+__global__ void k_b_fill_hash(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre, int n) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pre[n]) return;
+  const int i = seg_of(pre, n, x);
+  Ds[i].htab[x - pre[i]] = kEmptySlot;
+}
+
+__global__ void k_b_powtab(const BDesc* __restrict__ Ds, Mod M) {
+  const BDesc& D = Ds[blockIdx.y];
+  const int m = blockIdx.x, e = threadIdx.x;
+  if (D.mode == 0 && m < D.k) D.tab[m * kPowTab + e] = pow_mod(D.y[m], (uint64_t)e, M);
+}
+
+__global__ void k_b_anchor(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre, int n, Mod M) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pre[n]) return;
+  const int i = seg_of(pre, n, x);
+  const BDesc& D = Ds[i];
+  const int64_t j = x - pre[i];
+  uint64_t acc;
+  if (D.mode == 0) {
+    const uint8_t* e = D.exps + j * D.nv;
+    acc = 1;
+    for (int m = 0; m < D.k; m++) acc = mul_mod(acc, D.tab[m * kPowTab + e[m]], M);
+    D.v[j] = acc;
+  } else {
+    acc = D.v[j];
+    if (acc >= M.p) {
+      atomicOr(D.status, ST_DUP_NODE);
+      acc = 0;
+    }
+  }
+  D.vp[j] = shoup_pre(acc, M);
+  if (D.offset == 1 && acc == 0) atomicOr(D.status, ST_ZERO_NODE);
+  node_insert(acc, D.htab, D.hmask, D.status);
+}
+
+// ---- a3: product tree ---------------------------------------------------------
+
+constexpr int kTreeL1 = 10;  // levels 0..9 inside one CTA (1024 leaves)
+
+__global__ void __launch_bounds__(512) k_b_tree_leaf(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
+                                                     int n, Mod M) {
+  __shared__ uint64_t buf[2][1 << kTreeL1];
+  const int i = seg_of(pre, n, blockIdx.x);
+  const BDesc& D = Ds[i];
+  const int64_t base = (blockIdx.x - pre[i]) << kTreeL1;
+  const int cnt = (int)((D.T - base) < (1 << kTreeL1) ? (D.T - base) : (1 << kTreeL1));
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const uint64_t x = D.v[base + t];
+    buf[0][t] = x ? M.p - x : 0;               // z - v_j
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int l = 0; l < kTreeL1; l++) {
+    const int size = 1 << l, pair = 2 << l;
+    for (int pos = threadIdx.x; pos < cnt; pos += blockDim.x) {
+      const int po = pos & ~(pair - 1);
+      uint64_t r;
+      if (cnt - po <= size) r = buf[cur][pos];
+      else r = conv_coef(buf[cur], po, size, min(size, cnt - po - size), pos - po, M);
+      buf[cur ^ 1][pos] = r;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  uint64_t* out = D.levels <= kTreeL1 ? D.m : D.tmp;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) out[base + t] = buf[cur][t];
+}
+
+constexpr int kNO = 64, kNS = 4, kIC = 256;
+__global__ void __launch_bounds__(kNO* kNS) k_b_tree_level(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
+                                                           int n, int l, Mod M) {
+  __shared__ uint64_t As[kIC];
+  __shared__ uint64_t Bw[kIC + kNO];
+  __shared__ uint64_t red[kNS][kNO];
+  const int i = seg_of(pre, n, blockIdx.x);
+  const BDesc& D = Ds[i];
+  const int64_t T = D.T;
+  const int64_t t0 = (int64_t)(blockIdx.x - pre[i]) * kNO;
+  const bool even = ((l - kTreeL1) & 1) == 0;
+  const uint64_t* in = even ? D.tmp : D.tmp + T;
+  uint64_t* out = (l == D.levels - 1) ? D.m : (even ? D.tmp + T : D.tmp);
+  const int64_t size = 1ll << l, pair = 2ll << l;
+  const int64_t po = t0 & ~(pair - 1);
+  const int tid = threadIdx.x, o = tid % kNO, sl = tid / kNO;
+  if (T - po <= size) {
+    if (sl == 0 && t0 + o < T) out[t0 + o] = in[t0 + o];
+    return;
+  }
+  const int64_t a = size, b = (T - po - size) < size ? (T - po - size) : size;
+  const int64_t n0 = t0 - po;
+  const int64_t ilo = n0 - b > 0 ? n0 - b : 0;
+  const int64_t ihi = (n0 + kNO - 1) < a ? (n0 + kNO - 1) : a;
+  Acc3 acc = {0, 0, 0};
+  for (int64_t i0 = ilo; i0 <= ihi; i0 += kIC) {
+    __syncthreads();
+    for (int t = tid; t < kIC; t += blockDim.x) {
+      const int64_t ii = i0 + t;
+      As[t] = (ii < a) ? in[po + ii] : (ii == a ? 1 : 0);
+    }
+    const int64_t jlo = n0 - i0 - kIC + 1;
+    for (int t = tid; t < kIC + kNO - 1; t += blockDim.x) {
+      const int64_t jj = jlo + t;
+      Bw[t] = (jj < 0 || jj > b) ? 0 : (jj == b ? 1 : in[po + a + jj]);
+    }
+    __syncthreads();
+    for (int t = sl; t < kIC; t += kNS) mac128(acc, As[t], Bw[o - t + kIC - 1]);
+  }
+  __syncthreads();
+  red[sl][o] = acc3_value(acc, M);
+  __syncthreads();
+  if (sl == 0 && t0 + o < T) {
+    uint64_t s = red[0][o];
+    for (int q = 1; q < kNS; q++) s = add_mod(s, red[q][o], M);
+    out[t0 + o] = s;
+  }
+}
+
+// ---- a4/a6: finish ---------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t combine_den_d(const BDesc& D, int64_t j, uint64_t vj, const Mod& M) {
+  uint64_t den = 0, pw = 1;
+  const uint64_t vBK = D.NB > 1 ? pow_mod(vj, (uint64_t)D.BK, M) : 1;
+  for (int kb = 0; kb < D.NB; kb++) {
+    den = add_mod(den, mul_mod(D.denp[(int64_t)kb * D.T + j], pw, M), M);
+    pw = mul_mod(pw, vBK, M);
+  }
+  if (D.offset == 1) den = mul_mod(den, vj, M);
+  return den;
+}
+
+__global__ void k_b_newton_table(const BDesc* __restrict__ Ds, Mod M) {
+  const BDesc& D = Ds[blockIdx.x];
+  if (D.mode != 0 || D.T == 0) return;
+  const int S = D.S;
+  for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+    const int l = idx / S, s = idx - l * S;
+    if (l >= 1 && s >= l) {
+      const uint64_t d = sub_mod(D.xs[s], D.xs[s - l], M);
+      if (d == 0) atomicOr(D.status, ST_DUP_SAMPLE);
+      D.invd[idx] = inv_mod(d, M);
+    }
+  }
+}
+
+template <int SMAX>
+__global__ void __launch_bounds__(128) k_b_finish_newton(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
+                                                         int n, Mod M) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = x < pre[n];
+  const int i = active ? seg_of(pre, n, x) : 0;
+  const BDesc& D = Ds[i];
+  const int64_t j = x - pre[i];
+  uint64_t den = 1;
+  if (active) {
+    den = combine_den_d(D, j, D.v[j], M);
+    if (den == 0) atomicOr(D.status, ST_ZERO_DEN);
+  }
+  const uint64_t inv = warp_batch_inverse(den, M);
+  if (!active) return;
+  const int S = D.S;
+  uint64_t a[SMAX];
+#pragma unroll
+  for (int s = 0; s < SMAX; s++) {
+    a[s] = 0;
+    if (s < S) {
+      uint64_t num = 0;
+      for (int kb = 0; kb < D.NB; kb++) num = add_mod(num, D.part[((int64_t)kb * S + s) * D.T + j], M);
+      a[s] = mul_mod(num, inv, M);
+    }
+  }
+  newton_any<SMAX>(a, S, D.xs, D.invd, M);
+  int cnt = 0;
+#pragma unroll
+  for (int e = 0; e < SMAX; e++)
+    if (e < S) {
+      D.g[(int64_t)e * D.T + j] = a[e];
+      cnt += a[e] != 0;
+    }
+  D.cnt[j] = cnt;
+}
+
+__global__ void __launch_bounds__(256) k_b_finish_solve(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
+                                                        int n, Mod M) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = x < pre[n];
+  const int i = active ? seg_of(pre, n, x) : 0;
+  const BDesc& D = Ds[i];
+  const int64_t j = x - pre[i];
+  uint64_t den = 1;
+  if (active) {
+    den = combine_den_d(D, j, D.v[j], M);
+    if (den == 0) atomicOr(D.status, ST_ZERO_DEN);
+  }
+  const uint64_t inv = warp_batch_inverse(den, M);
+  if (!active) return;
+  for (int s = 0; s < D.S; s++) {
+    uint64_t num = 0;
+    for (int kb = 0; kb < D.NB; kb++) num = add_mod(num, D.part[((int64_t)kb * D.S + s) * D.T + j], M);
+    D.c[(int64_t)s * D.ldc + j] = mul_mod(num, inv, M);
+  }
+}
+
+// ---- a6: compaction ---------------------------------------------------------------
+
+constexpr int kScanB = 1024;
+
+__global__ void __launch_bounds__(kScanB) k_b_block_sums(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
+                                                         int n) {
+  __shared__ int64_t sh[33];
+  const int i = seg_of(pre, n, blockIdx.x);
+  const BDesc& D = Ds[i];
+  const int64_t blk = blockIdx.x - pre[i];
+  const int64_t j = blk * kScanB + threadIdx.x;
+  int64_t total;
+  block_exclusive_scan(j < D.T ? D.cnt[j] : 0, sh, total);
+  if (threadIdx.x == 0) D.bsum[blk] = total;
+}
+
+__global__ void __launch_bounds__(kScanB) k_b_scan(const BDesc* __restrict__ Ds) {
+  __shared__ int64_t sh[33];
+  const BDesc& D = Ds[blockIdx.x];
+  if (D.mode != 0) return;
+  const int64_t nb = (D.T + kScanB - 1) / kScanB;
+  int64_t carry = 0;
+  for (int64_t base = 0; base < nb; base += kScanB) {
+    const int64_t t = base + threadIdx.x;
+    int64_t total;
+    const int64_t ex = block_exclusive_scan(t < nb ? D.bsum[t] : 0, sh, total);
+    __syncthreads();
+    if (t < nb) D.bsum[t] = ex + carry;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *D.out_count = carry;
+}
+
+__global__ void __launch_bounds__(kScanB) k_b_scatter(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
+                                                      int n) {
+  __shared__ int64_t sh[33];
+  const int i = seg_of(pre, n, blockIdx.x);
+  const BDesc& D = Ds[i];
+  const int64_t blk = blockIdx.x - pre[i];
+  const int64_t j = blk * kScanB + threadIdx.x;
+  const int64_t x = j < D.T ? D.cnt[j] : 0;
+  int64_t total;
+  int64_t o = block_exclusive_scan(x, sh, total) + D.bsum[blk];
+  if (j >= D.T || x == 0) return;
+  const int nv = D.nv, k = D.k;
+  const uint8_t* e = D.exps + j * nv;
+  for (int s = 0; s < D.S; s++) {
+    const uint64_t val = D.g[(int64_t)s * D.T + j];
+    if (val == 0) continue;
+    if (o < D.out_cap) {
+      uint8_t* oe = D.out_exps + o * nv;
+      for (int m = 0; m < nv; m++) oe[m] = m < k ? e[m] : 0;
+      oe[k] = (uint8_t)s;
+      D.out_coef[o] = val;
+    }
+    o++;
+  }
+}
+
+// ---- host side ---------------------------------------------------------------------
+
+static int tree_levels(int64_t T) {
+  int l = 0;
+  while ((1ll << l) < T) l++;
+  return l;
+}
+
+static void push_prefix(std::vector<int64_t>& all, const std::vector<int64_t>& counts, size_t& off) {
+  off = all.size();
+  int64_t s = 0;
+  for (int64_t c : counts) {
+    all.push_back(s);
+    s += c;
+  }
+  all.push_back(s);
+}
+
+// Plans, prefix tables and work lists of a batch (host side).
+struct Prepared {
+  std::vector<StepDims> plan;
+  std::vector<int64_t> pre;
+  size_t o_hash = 0, o_roots = 0, o_leaf = 0, o_carry = 0;
+  std::vector<size_t> o_lvl;
+  std::vector<int> tiles_used;
+  std::vector<std::vector<int4>> work;
+  int kmax = 0, smax = 0, lmax = 0, mode = 0;
+  size_t ws_bytes = 0, table_bytes = 0;
+};
+
+static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& P) {
+  P.mode = items[0].mode;
+  P.plan.resize(n);
+  for (int i = 0; i < n; i++) {
+    const BatchItem& it = items[i];
+    if (it.mode != P.mode) return false;
+    P.plan[i] = plan_step(ctx, it.T, it.S);
+    P.kmax = std::max(P.kmax, it.k);
+    P.smax = std::max(P.smax, it.S);
+    P.lmax = std::max(P.lmax, tree_levels(it.T));
+  }
+  Carver m0(nullptr);
+  for (int i = 0; i < n; i++) carve_step(m0, items[i].T, items[i].S, items[i].k, P.plan[i]);
+  P.ws_bytes = m0.off;
+  std::vector<int64_t> c_hash(n), c_roots(n), c_leaf(n), c_carry(n);
+  for (int i = 0; i < n; i++) {
+    const int64_t T = items[i].T;
+    c_hash[i] = T > 0 ? (int64_t)hash_slots(T) : 0;
+    c_roots[i] = T;
+    c_leaf[i] = (T + 1023) / 1024;
+    c_carry[i] = (T > 0 && P.plan[i].NB > 1) ? (int64_t)((T + 255) / 256) * (P.plan[i].NB - 1) : 0;
+  }
+  push_prefix(P.pre, c_hash, P.o_hash);
+  push_prefix(P.pre, c_roots, P.o_roots);
+  push_prefix(P.pre, c_leaf, P.o_leaf);
+  push_prefix(P.pre, c_carry, P.o_carry);
+  for (int l = kTreeL1; l < P.lmax; l++) {
+    std::vector<int64_t> c(n);
+    for (int i = 0; i < n; i++) c[i] = tree_levels(items[i].T) > l ? (items[i].T + kNO - 1) / kNO : 0;
+    size_t o;
+    push_prefix(P.pre, c, o);
+    P.o_lvl.push_back(o);
+  }
+  for (int i = 0; i < n; i++) {
+    if (items[i].T == 0) continue;
+    const int tile = P.plan[i].s_tile;
+    int w = (int)(std::find(P.tiles_used.begin(), P.tiles_used.end(), tile) - P.tiles_used.begin());
+    if (w == (int)P.tiles_used.size()) {
+      P.tiles_used.push_back(tile);
+      P.work.emplace_back();
+    }
+    const int rows = (int)((items[i].T + 127) / 128), nst = (items[i].S + tile - 1) / tile;
+    for (int kb = 0; kb < P.plan[i].NB; kb++)
+      for (int r = 0; r < rows; r++)
+        for (int s = 0; s < nst; s++) P.work[w].push_back(make_int4(i, r, kb, s));
+  }
+  const std::vector<StepDims>& plan = P.plan;
+  for (auto& wl : P.work)
+    std::stable_sort(wl.begin(), wl.end(), [&](const int4& a, const int4& b) {
+      return plan[a.x].BK * plan[a.x].s_tile > plan[b.x].BK * plan[b.x].s_tile;
+    });
+  P.table_bytes = sizeof(BDesc) * n + sizeof(int64_t) * P.pre.size();
+  for (auto& wl : P.work) P.table_bytes += sizeof(int4) * wl.size() + 16;
+  return true;
+}
+
+size_t batch_ws_need(const zr_ctx* ctx, const BatchItem* items, int n) {
+  if (n <= 0) return 0;
+  Prepared P;
+  if (!prepare(ctx, items, n, P)) return 0;
+  return P.ws_bytes + P.table_bytes + 512;
+}
+
+zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status, cudaStream_t st, size_t base) {
+  if (n <= 0) return ZR_OK;
+  const Mod& M = ctx->M;
+  Prepared P;
+  if (!prepare(ctx, items, n, P)) return set_err(ctx, ZR_ERR_INVALID_ARG, "batch mixes steps and systems");
+  const int mode = P.mode, kmax = P.kmax, smax = P.smax, lmax = P.lmax;
+  const std::vector<StepDims>& plan = P.plan;
+  const std::vector<int64_t>& pre = P.pre;
+  const size_t o_hash = P.o_hash, o_roots = P.o_roots, o_leaf = P.o_leaf, o_carry = P.o_carry;
+  const std::vector<size_t>& o_lvl = P.o_lvl;
+  const std::vector<int>& tiles_used = P.tiles_used;
+  const std::vector<std::vector<int4>>& work = P.work;
+  const size_t table_bytes = P.table_bytes;
+  std::vector<BDesc> D(n);
+  zr_status r = ensure_ws(ctx, base + P.ws_bytes + table_bytes + 512, st);
+  if (r) return r;
+  // carve for real
+  Carver cv(ctx->ws + base);
+  for (int i = 0; i < n; i++) {
+    const BatchItem& it = items[i];
+    StepWs w = carve_step(cv, it.T, it.S, it.k, plan[i]);
+    BDesc& d = D[i];
+    memset(&d, 0, sizeof(d));
+    d.T = it.T;
+    d.S = it.S;
+    d.k = it.k;
+    d.nv = it.nv;
+    d.offset = it.offset;
+    d.mode = it.mode;
+    d.NB = plan[i].NB;
+    d.BK = plan[i].BK;
+    d.s_tile = plan[i].s_tile;
+    d.nst = (it.S + plan[i].s_tile - 1) / plan[i].s_tile;
+    d.levels = tree_levels(it.T);
+    d.hmask = hash_slots(it.T) - 1;
+    d.exps = it.exps;
+    d.y = it.y;
+    d.xs = it.xs;
+    d.b = it.b;
+    d.ldb = it.ldb;
+    d.tab = w.tab;
+    d.v = it.mode == 1 ? const_cast<uint64_t*>(it.vin) : w.v;
+    d.vp = w.vp;
+    d.htab = w.htab;
+    d.m = w.m;
+    d.tmp = w.tmp;
+    d.R = w.R;
+    d.part = w.part;
+    d.denp = w.denp;
+    d.invd = w.invd;
+    d.g = w.g;
+    d.cnt = w.cnt;
+    d.bsum = w.bsum;
+    d.out_exps = it.out_exps;
+    d.out_coef = it.out_coef;
+    d.out_cap = it.out_cap;
+    d.out_count = it.out_count;
+    d.c = it.c;
+    d.ldc = it.ldc;
+    d.status = status;
+  }
+  // stage the tables in pinned memory, then one copy
+  char* dtab = cv.take<char>(table_bytes + 256);
+  if (ctx->stage_event) cudaEventSynchronize(ctx->stage_event);
+  if (ctx->h_stage_cap < table_bytes) {
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_cap = 0;
+    if (cudaMallocHost(&ctx->h_stage, table_bytes * 2) != cudaSuccess)
+      return set_err(ctx, ZR_ERR_OOM, "pinned staging buffer");
+    ctx->h_stage_cap = table_bytes * 2;
+  }
+  char* hs = static_cast<char*>(ctx->h_stage);
+  size_t pos = 0;
+  memcpy(hs + pos, D.data(), sizeof(BDesc) * n);
+  const BDesc* dD = reinterpret_cast<const BDesc*>(dtab + pos);
+  pos += sizeof(BDesc) * n;
+  memcpy(hs + pos, pre.data(), sizeof(int64_t) * pre.size());
+  const int64_t* dpre = reinterpret_cast<const int64_t*>(dtab + pos);
+  pos += sizeof(int64_t) * pre.size();
+  std::vector<const int4*> dwork(work.size());
+  for (size_t w = 0; w < work.size(); w++) {
+    pos = (pos + 15) & ~(size_t)15;
+    memcpy(hs + pos, work[w].data(), sizeof(int4) * work[w].size());
+    dwork[w] = reinterpret_cast<const int4*>(dtab + pos);
+    pos += sizeof(int4) * work[w].size();
+  }
+  cudaError_t e = cudaMemcpyAsync(dtab, hs, pos, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "batch tables");
+  if (!ctx->stage_event) cudaEventCreateWithFlags(&ctx->stage_event, cudaEventDisableTiming);
+  cudaEventRecord(ctx->stage_event, st);
+
+  const int64_t nroots = pre[o_roots + n], nhash = pre[o_hash + n], nleaf = pre[o_leaf + n];
+  const int64_t ncarry = pre[o_carry + n];
+  // entries with T = 0 report an empty skeleton
+  for (int i = 0; i < n; i++)
+    if (items[i].T == 0 && mode == 0 && items[i].out_count) cudaMemsetAsync(items[i].out_count, 0, 8, st);
+  cudaEvent_t e0 = prof_mark(ctx, st);
+  // a2
+  if (nhash) { k_b_fill_hash<<<cdiv(nhash, 256), 256, 0, st>>>(dD, dpre + o_hash, n); note_launch(); }
+  if (mode == 0 && kmax > 0) { k_b_powtab<<<dim3(kmax, n), kPowTab, 0, st>>>(dD, M); note_launch(); }
+  if (nroots) { k_b_anchor<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+  cudaEvent_t e1 = prof_mark(ctx, st);
+  // a3
+  if (nleaf) { k_b_tree_leaf<<<(unsigned)nleaf, 512, 0, st>>>(dD, dpre + o_leaf, n, M); note_launch(); }
+  for (int l = kTreeL1; l < lmax; l++) {
+    const size_t o = o_lvl[l - kTreeL1];
+    const int64_t nt = pre[o + n];
+    if (nt) { k_b_tree_level<<<(unsigned)nt, kNO * kNS, 0, st>>>(dD, dpre + o, n, l, M); note_launch(); }
+  }
+  cudaEvent_t e2 = prof_mark(ctx, st);
+  // a4 + a5
+  if (ncarry) launch_b_carry(dD, dpre + o_carry, n, ncarry, M, st);
+  cudaEvent_t e3 = prof_mark(ctx, st);
+  for (size_t w = 0; w < work.size(); w++)
+    launch_b_solve(tiles_used[w], dD, dwork[w], (int)work[w].size(), ctx->sms ? ctx->sms : 152, M, st);
+  cudaEvent_t e4 = prof_mark(ctx, st);
+  // a6 (or the plain finish of a system)
+  if (nroots) {
+    if (mode == 0) {
+      { k_b_newton_table<<<n, 256, 0, st>>>(dD, M); note_launch(); }
+      const unsigned grid = cdiv(nroots, 128);
+      if (smax <= 8) { k_b_finish_newton<8><<<grid, 128, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+      else if (smax <= 16) { k_b_finish_newton<16><<<grid, 128, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+      else if (smax <= 32) { k_b_finish_newton<32><<<grid, 128, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+      else { k_b_finish_newton<64><<<grid, 128, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+    } else {
+      { k_b_finish_solve<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+    }
+  }
+  cudaEvent_t e5 = prof_mark(ctx, st);
+  if (mode == 0 && nleaf) {
+    { k_b_block_sums<<<(unsigned)nleaf, kScanB, 0, st>>>(dD, dpre + o_leaf, n); note_launch(); }
+    { k_b_scan<<<n, kScanB, 0, st>>>(dD); note_launch(); }
+    { k_b_scatter<<<(unsigned)nleaf, kScanB, 0, st>>>(dD, dpre + o_leaf, n); note_launch(); }
+  }
+  cudaEvent_t e6 = prof_mark(ctx, st);
+  prof_add(ctx, PH_ANCHOR, e0, e1);
+  prof_add(ctx, PH_MASTER, e1, e2);
+  prof_add(ctx, PH_CARRY, e2, e3);
+  prof_add(ctx, PH_SOLVE, e3, e4);
+  prof_add(ctx, PH_NEWTON, e4, e5);
+  prof_add(ctx, PH_COMPACT, e5, e6);
+  return cuda_err(ctx, cudaGetLastError(), "batch launch");
+}
+
+}  // namespace zr

@@ -45,6 +45,9 @@ struct zr_ctx {
   uint32_t* d_status_call = nullptr;
   int64_t* d_count = nullptr;   // scratch output counts
   int64_t* h_count = nullptr;   // pinned mirror
+  void* h_stage = nullptr;      // pinned staging of batch tables
+  size_t h_stage_cap = 0;
+  cudaEvent_t stage_event = nullptr;   // last copy out of h_stage
   std::string err;
   std::mutex mu;                // guards err for the serve thread
 };
@@ -81,17 +84,36 @@ StepDims plan_step(const zr_ctx* ctx, int64_t T, int S);
 double plan_cost(const zr_ctx* ctx, const StepDims& D);
 uint64_t hash_slots(int64_t T);
 
-// The device part of one Zippel step on workspace carved by the caller.
+// Workspace of one step or system (carved in the context workspace).
 struct StepWs {
   uint64_t *tab, *v, *vp, *htab, *m, *tmp, *R, *part, *denp, *invd, *g;
   int32_t* cnt;
   int64_t* bsum;
 };
 StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D);
-// Enqueues a2..a6 for one step.  status: device word OR-ed with ST_* flags.
-void enqueue_step(zr_ctx* ctx, const StepWs& w, const StepDims& D, const zr_poly* skel, int k, const uint64_t* y,
-                  const uint64_t* samples, const uint64_t* probes, int64_t ldb, int offset, uint8_t* out_exps,
-                  uint64_t* out_coef, int64_t out_cap, int64_t* d_out_count, uint32_t* status, cudaStream_t st);
+
+// One entry of a batch: a Zippel step (mode 0) or a transposed Vandermonde
+// system with given nodes (mode 1).  All pointers are device pointers.
+struct BatchItem {
+  int mode = 0;
+  int64_t T = 0;
+  int S = 1, k = 0, nv = 1, offset = 0;
+  const uint8_t* exps = nullptr;
+  const uint64_t *y = nullptr, *xs = nullptr, *b = nullptr, *vin = nullptr;
+  int64_t ldb = 0;
+  uint8_t* out_exps = nullptr;
+  uint64_t* out_coef = nullptr;
+  int64_t out_cap = 0;
+  int64_t* out_count = nullptr;
+  uint64_t* c = nullptr;
+  int64_t ldc = 0;
+};
+// Workspace bytes a batch needs (its regions plus the device tables).
+size_t batch_ws_need(const zr_ctx* ctx, const BatchItem* items, int n);
+// Enqueues a batch; its workspace starts `base` bytes into the context
+// workspace (the caller ensured base + batch_ws_need, or the call grows it
+// when nothing before `base` is live).  status: device word of ST_* flags.
+zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status, cudaStream_t st, size_t base = 0);
 
 // evaluator (zr_eval.cu)
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);

@@ -125,36 +125,58 @@ zr_status upload(Call& c, DBuf& b, const void* host, size_t bytes) {
   return c.cuda(e, "upload");
 }
 
-// One Zippel step on the device: probes of `f` (or given probes), the step,
-// and the new skeleton in `out`.  Workspace layout: the probes first, then
-// the evaluator's or the step's scratch (used one after the other).
-zr_status zippel_step_dev(Call& c, const DPoly& skel, int k, const uint64_t* d_y, int S, const uint64_t* d_cs,
-                          const uint64_t* d_b, int64_t ldb, int offset, DPoly& out) {
-  const int64_t T = skel.T;
-  const int64_t cap = T * S;
-  cudaError_t e = out.exps.ensure((size_t)(cap > 0 ? cap : 1) * skel.nv);
-  if (e == cudaSuccess) e = out.coef.ensure(sizeof(uint64_t) * (cap > 0 ? cap : 1));
-  if (e != cudaSuccess) return c.cuda(e, "step output");
-  out.nv = skel.nv;
-  if (T == 0) {
-    out.T = 0;
-    return ZR_OK;
+// Zippel steps on device skeletons, in one batch: entry i turns skel[i] into
+// out[i] (capacity T S) with its own samples and probes.  Counts come back
+// through the context's count words.
+zr_status zippel_steps_dev(Call& c, int n, const DPoly* const* skel, const int* k, const uint64_t* const* d_y,
+                           const int* S, const uint64_t* const* d_cs, const uint64_t* const* d_b, const int64_t* ldb,
+                           int offset, DPoly* const* out) {
+  std::vector<BatchItem> items;
+  std::vector<int> which;
+  for (int i = 0; i < n; i++) {
+    const int64_t T = skel[i]->T;
+    const int64_t cap = T * S[i];
+    cudaError_t e = out[i]->exps.ensure((size_t)(cap > 0 ? cap : 1) * skel[i]->nv);
+    if (e == cudaSuccess) e = out[i]->coef.ensure(sizeof(uint64_t) * (cap > 0 ? cap : 1));
+    if (e != cudaSuccess) return c.cuda(e, "step output");
+    out[i]->nv = skel[i]->nv;
+    out[i]->T = 0;
+    if (T == 0) continue;
+    BatchItem it;
+    it.mode = 0;
+    it.T = T;
+    it.S = S[i];
+    it.k = k[i];
+    it.nv = skel[i]->nv;
+    it.offset = offset;
+    it.exps = skel[i]->exps.as<uint8_t>();
+    it.y = d_y[i];
+    it.xs = d_cs[i];
+    it.b = d_b[i];
+    it.ldb = ldb[i];
+    it.out_exps = out[i]->exps.as<uint8_t>();
+    it.out_coef = out[i]->coef.as<uint64_t>();
+    it.out_cap = cap;
+    it.out_count = c.ctx->d_count + items.size();
+    items.push_back(it);
+    which.push_back(i);
   }
-  StepDims D = plan_step(c.ctx, T, S);
-  Carver m0(nullptr);
-  carve_step(m0, T, S, k, D);
-  zr_status r = ensure_ws(c.ctx, m0.off, c.st);
+  if (items.empty()) return ZR_OK;
+  zr_status r = run_batch(c.ctx, items.data(), (int)items.size(), c.ctx->d_status_call, c.st);
   if (r) return r;
-  Carver cv(c.ctx->ws);
-  StepWs w = carve_step(cv, T, S, k, D);
-  zr_poly sv = skel.view();
-  enqueue_step(c.ctx, w, D, &sv, k, d_y, d_cs, d_b, ldb, offset, out.exps.as<uint8_t>(), out.coef.as<uint64_t>(),
-               cap, c.ctx->d_count, c.ctx->d_status_call, c.st);
-  e = cudaMemcpyAsync(c.ctx->h_count, c.ctx->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st);
+  cudaError_t e = cudaMemcpyAsync(c.ctx->h_count, c.ctx->d_count, sizeof(int64_t) * items.size(),
+                                  cudaMemcpyDeviceToHost, c.st);
   if (e != cudaSuccess) return c.cuda(e, "step count");
   r = c.sync_status();
-  out.T = c.ctx->h_count[0];
+  for (size_t t = 0; t < which.size(); t++) out[which[t]]->T = c.ctx->h_count[t];
   return r;
+}
+
+zr_status zippel_step_dev(Call& c, const DPoly& skel, int k, const uint64_t* d_y, int S, const uint64_t* d_cs,
+                          const uint64_t* d_b, int64_t ldb, int offset, DPoly& out) {
+  const DPoly* sk[1] = {&skel};
+  DPoly* o[1] = {&out};
+  return zippel_steps_dev(c, 1, sk, &k, &d_y, &S, &d_cs, &d_b, &ldb, offset, o);
 }
 
 // Univariate dense reconstruction helpers for step 0 --------------------------
@@ -347,9 +369,15 @@ zr_status balanced_step_dev(Call& c, const DPoly& skN, const DPoly& skD, int k, 
                         c.ctx->d_status_call, c.st);
   zr_status r = c.sync_status();
   if (r) return r;
-  r = zippel_step_dev(c, skN, k, d_y, SN, d_cs, bN, TN ? TN : 1, offset, outN);
-  if (r) return r;
-  return zippel_step_dev(c, skD, k, d_y, SD, d_cs, bD, TD ? TD : 1, offset, outD);
+  // the numerator and denominator steps share one batch of launches
+  const DPoly* sk[2] = {&skN, &skD};
+  DPoly* o[2] = {&outN, &outD};
+  const int ks[2] = {k, k}, Ss[2] = {SN, SD};
+  const uint64_t* ys[2] = {d_y, d_y};
+  const uint64_t* css[2] = {d_cs, d_cs};
+  const uint64_t* bs[2] = {bN, bD};
+  const int64_t lds[2] = {TN ? TN : 1, TD ? TD : 1};
+  return zippel_steps_dev(c, 2, sk, ks, ys, Ss, css, bs, lds, offset, o);
 }
 
 // f = N/D at the step's probe family (Sf samples, Tmax probes).

@@ -4,6 +4,7 @@
 // modular addition deferred to one reduction per dot product).
 #include <cuda_runtime.h>
 
+#include "zr_device.cuh"
 #include "zr_kernels.cuh"
 
 namespace zr {
@@ -13,26 +14,28 @@ static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1
 // ---------------------------------------------------------------------------
 // a4: block partials of the tail Horner value for the k-blocked chain:
 //   R_kb(v_j) = sum_{l in block kb} m_l v_j^{l - k_lo(kb)},  kb >= 1.
+// One CTA = 256 roots of one entry and one k-block (flattened over a batch).
 // ---------------------------------------------------------------------------
 
-__global__ void k_carry_partials(int64_t T, int NB, int64_t BK, const uint64_t* __restrict__ m,
-                                 const uint64_t* __restrict__ v, const uint64_t* __restrict__ vp, Mod M,
-                                 uint64_t* __restrict__ R) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int kb = blockIdx.y + 1;
-  if (j >= T || kb >= NB) return;
-  const int64_t klo = kb * BK, khi = (klo + BK) < T ? (klo + BK) : T;
-  const uint64_t vj = v[j], vpj = vp[j];
+__global__ void __launch_bounds__(256) k_b_carry(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre, int n,
+                                                 Mod M) {
+  const int i = seg_of(pre, n, blockIdx.x);
+  const BDesc& D = Ds[i];
+  const int64_t local = blockIdx.x - pre[i];
+  const int64_t rows = (D.T + 255) / 256;
+  const int kb = 1 + (int)(local / rows);
+  const int64_t j = (local % rows) * 256 + threadIdx.x;
+  if (j >= D.T) return;
+  const int64_t klo = kb * D.BK, khi = (klo + D.BK) < D.T ? (klo + D.BK) : D.T;
+  const uint64_t vj = D.v[j], vpj = D.vp[j];
+  const uint64_t* __restrict__ m = D.m;
   uint64_t r = 0;
   for (int64_t l = khi - 1; l >= klo; l--) r = canon(shoup_lazy(r, vj, vpj, M), M) + __ldg(m + l);
-  R[(int64_t)(kb - 1) * T + j] = canon(r, M);
+  D.R[(int64_t)(kb - 1) * D.T + j] = canon(r, M);
 }
 
-void launch_carry_partials(const StepDims& D, const uint64_t* m, const uint64_t* v, const uint64_t* vp,
-                           const Mod& M, uint64_t* R, cudaStream_t st) {
-  if (D.NB <= 1) return;
-  dim3 grid(cdiv(D.T, 256), D.NB - 1);
-  { k_carry_partials<<<grid, 256, 0, st>>>(D.T, D.NB, D.BK, m, v, vp, M, R); note_launch(); }
+void launch_b_carry(const BDesc* Ds, const int64_t* pre, int n, int64_t nctas, const Mod& M, cudaStream_t st) {
+  if (nctas > 0) { k_b_carry<<<(unsigned)nctas, 256, 0, st>>>(Ds, pre, n, M); note_launch(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -81,101 +84,113 @@ template <int ST>
 struct SolveMinBlocks { static constexpr int value = ST <= 6 ? 4 : (ST <= 12 ? 3 : 2); };
 
 template <int ST, int NT, int KC>
-__global__ void __launch_bounds__(NT, SolveMinBlocks<ST>::value) k_solve(int64_t T, int S, int NB, int64_t BK, const uint64_t* __restrict__ m,
-                                              const uint64_t* __restrict__ v, const uint64_t* __restrict__ vp,
-                                              const uint64_t* __restrict__ R, const uint64_t* __restrict__ b,
-                                              int64_t ldb, Mod M, uint64_t* __restrict__ part,
-                                              uint64_t* __restrict__ denp) {
+__global__ void __launch_bounds__(NT, SolveMinBlocks<ST>::value) k_solve(const BDesc* __restrict__ Ds,
+                                                                         const int4* __restrict__ items, int nitems,
+                                                                         Mod M) {
   extern __shared__ __align__(16) unsigned char smraw[];
   SolveSmem<ST, KC>& sm = *reinterpret_cast<SolveSmem<ST, KC>*>(smraw);
-  constexpr int STP = SolveSmem<ST, KC>::STP;
-  const int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x;
-  const int kb = blockIdx.y;
-  const int s0 = blockIdx.z * ST;
-  const int sn = (S - s0) < ST ? (S - s0) : ST;
-  const bool do_den = blockIdx.z == 0;
-  const int64_t klo = kb * BK, khi = (klo + BK) < T ? (klo + BK) : T;
-  const bool active = j < T;
-  const uint64_t vj = active ? v[j] : 0, vpj = active ? vp[j] : 0;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int4 wi = items[item];
+    const BDesc& D = Ds[wi.x];
+    const int64_t T = D.T, BK = D.BK, ldb = D.ldb;
+    const int S = D.S, NB = D.NB;
+    const uint64_t* __restrict__ m = D.m;
+    const uint64_t* __restrict__ b = D.b;
+    const int64_t j = (int64_t)wi.y * NT + threadIdx.x;
+    const int kb = wi.z;
+    const int s0 = wi.w * ST;
+    const int sn = (S - s0) < ST ? (S - s0) : ST;
+    const bool do_den = wi.w == 0;
+    const int64_t klo = kb * BK, khi = (klo + BK) < T ? (klo + BK) : T;
+    const bool active = j < T;
+    const uint64_t vj = active ? D.v[j] : 0, vpj = active ? D.vp[j] : 0;
 
-  // carry-in q_{j, khi-1} = tail Horner value from khi (m_T = 1 at the top)
-  uint64_t q = 1;
-  if (active && kb < NB - 1) {
-    const uint64_t vBK = pow_mod(vj, (uint64_t)BK, M);
-    const uint64_t vtop = pow_mod(vj, (uint64_t)(T - (int64_t)(NB - 1) * BK), M);
-    uint64_t c = 1;
-    for (int kk = NB - 1; kk > kb; kk--) c = add_mod(R[(int64_t)(kk - 1) * T + j], mul_mod(kk == NB - 1 ? vtop : vBK, c, M), M);
-    q = c;
-  }
-  uint64_t u = 0;
-  Acc8 acc[ST];
+    // carry-in q_{j, khi-1} = tail Horner value from khi (m_T = 1 at the top)
+    uint64_t q = 1;
+    if (active && kb < NB - 1) {
+      const uint64_t vBK = pow_mod(vj, (uint64_t)BK, M);
+      const uint64_t vtop = pow_mod(vj, (uint64_t)(T - (int64_t)(NB - 1) * BK), M);
+      uint64_t c = 1;
+      for (int kk = NB - 1; kk > kb; kk--)
+        c = add_mod(D.R[(int64_t)(kk - 1) * T + j], mul_mod(kk == NB - 1 ? vtop : vBK, c, M), M);
+      q = c;
+    }
+    uint64_t u = 0;
+    Acc8 acc[ST];
 #pragma unroll
-  for (int s = 0; s < ST; s++) acc[s] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < ST; s++) acc[s] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
 
-  const int nchunks = (int)((khi - klo + KC - 1) / KC);
-  auto chunk_lo = [&](int c, int& len) -> int64_t {
-    int64_t chi = khi - (int64_t)c * KC;
-    int64_t clo = chi - KC > klo ? chi - KC : klo;
-    len = (int)(chi - clo);
-    return clo;
-  };
-  {
-    int len;
-    int64_t clo = chunk_lo(0, len);
-    solve_stage<ST, NT, KC>(sm, 0, b, ldb, m, s0, sn, clo, len);
-    cp_async_commit();
-  }
-  for (int c = 0; c < nchunks; c++) {
-    const int buf = c & 1;
-    if (c + 1 < nchunks) {
+    const int nchunks = (int)((khi - klo + KC - 1) / KC);
+    auto chunk_lo = [&](int c, int& len) -> int64_t {
+      int64_t chi = khi - (int64_t)c * KC;
+      int64_t clo = chi - KC > klo ? chi - KC : klo;
+      len = (int)(chi - clo);
+      return clo;
+    };
+    {
       int len;
-      int64_t clo = chunk_lo(c + 1, len);
-      solve_stage<ST, NT, KC>(sm, buf ^ 1, b, ldb, m, s0, sn, clo, len);
+      int64_t clo = chunk_lo(0, len);
+      solve_stage<ST, NT, KC>(sm, 0, b, ldb, m, s0, sn, clo, len);
+      cp_async_commit();
     }
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    int len;
-    chunk_lo(c, len);
-    for (int kk = len - 1; kk >= 0; kk--) {
-      const uint64_t qc = canon(q, M);
-      const uint32_t x0 = lo32(qc), x1 = hi32(qc);
-      const uint4* row = reinterpret_cast<const uint4*>(&sm.b[buf][kk][0]);
+    for (int c = 0; c < nchunks; c++) {
+      const int buf = c & 1;
+      if (c + 1 < nchunks) {
+        int len;
+        int64_t clo = chunk_lo(c + 1, len);
+        solve_stage<ST, NT, KC>(sm, buf ^ 1, b, ldb, m, s0, sn, clo, len);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      int len;
+      chunk_lo(c, len);
+      for (int kk = len - 1; kk >= 0; kk--) {
+        const uint64_t qc = canon(q, M);
+        const uint32_t x0 = lo32(qc), x1 = hi32(qc);
+        const uint4* row = reinterpret_cast<const uint4*>(&sm.b[buf][kk][0]);
 #pragma unroll
-      for (int s = 0; s + 1 < ST; s += 2) {
-        const uint4 w = row[s >> 1];
-        mac8(acc[s], x0, x1, w.x, w.y);
-        mac8(acc[s + 1], x0, x1, w.z, w.w);
+        for (int s = 0; s + 1 < ST; s += 2) {
+          const uint4 w = row[s >> 1];
+          mac8(acc[s], x0, x1, w.x, w.y);
+          mac8(acc[s + 1], x0, x1, w.z, w.w);
+        }
+        if (ST & 1) {
+          const uint2 w = reinterpret_cast<const uint2*>(row)[ST - 1];
+          mac8(acc[ST - 1], x0, x1, w.x, w.y);
+        }
+        if (do_den) u = canon(shoup_lazy(u, vj, vpj, M), M) + qc;
+        q = canon(shoup_lazy(qc, vj, vpj, M), M) + sm.m[buf][kk];
       }
-      if (ST & 1) {
-        const uint2 w = reinterpret_cast<const uint2*>(row)[ST - 1];
-        mac8(acc[ST - 1], x0, x1, w.x, w.y);
-      }
-      if (do_den) u = canon(shoup_lazy(u, vj, vpj, M), M) + qc;
-      q = canon(shoup_lazy(qc, vj, vpj, M), M) + sm.m[buf][kk];
+      __syncthreads();
+    }
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < ST; s++)
+        if (s < sn) D.part[((int64_t)kb * S + s0 + s) * T + j] = acc8_value(acc[s], M);
+      if (do_den) D.denp[(int64_t)kb * T + j] = canon(u, M);
     }
     __syncthreads();
-  }
-  if (active) {
-#pragma unroll
-    for (int s = 0; s < ST; s++)
-      if (s < sn) part[((int64_t)kb * S + s0 + s) * T + j] = acc8_value(acc[s], M);
-    if (do_den) denp[(int64_t)kb * T + j] = canon(u, M);
   }
 }
 
 template <int ST, int NT, int KC>
-static void launch_solve_t(const StepDims& D, const uint64_t* m, const uint64_t* v, const uint64_t* vp,
-                           const uint64_t* R, const uint64_t* b, int64_t ldb, const Mod& M, uint64_t* part,
-                           uint64_t* denp, cudaStream_t st) {
+static void launch_solve_t(const BDesc* Ds, const int4* items, int nitems, int sms, const Mod& M, cudaStream_t st);
+
+template <int ST, int NT, int KC>
+static int solve_occupancy_t();
+
+template <int ST, int NT, int KC>
+static void launch_solve_t(const BDesc* Ds, const int4* items, int nitems, int sms, const Mod& M, cudaStream_t st) {
   const size_t smem = sizeof(SolveSmem<ST, KC>);
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_solve<ST, NT, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  dim3 grid(cdiv(D.T, NT), D.NB, cdiv(D.S, ST));
-  { k_solve<ST, NT, KC><<<grid, NT, smem, st>>>(D.T, D.S, D.NB, D.BK, m, v, vp, R, b, ldb, M, part, denp); note_launch(); }
+  const int per_sm = solve_occupancy_t<ST, NT, KC>();
+  const int grid = nitems < sms * per_sm ? nitems : sms * per_sm;   // persistent: one wave walks the work list
+  if (grid > 0) { k_solve<ST, NT, KC><<<grid, NT, smem, st>>>(Ds, items, nitems, M); note_launch(); }
 }
 
 template <int ST, int NT, int KC>
@@ -207,15 +222,15 @@ int solve_blocks_per_sm(int s_tile) {
   }
 }
 
-void launch_solve(const StepDims& D, const uint64_t* m, const uint64_t* v, const uint64_t* vp, const uint64_t* R,
-                  const uint64_t* b, int64_t ldb, const Mod& M, uint64_t* part, uint64_t* denp, cudaStream_t st) {
-  if (D.T <= 0 || D.S <= 0) return;
-  switch (D.s_tile) {
+void launch_b_solve(int s_tile, const BDesc* Ds, const int4* items, int nitems, int sms, const Mod& M,
+                    cudaStream_t st) {
+  if (nitems <= 0) return;
+  switch (s_tile) {
 #define ZR_CASE(ST) \
-  case ST: launch_solve_t<ST, 128, 32>(D, m, v, vp, R, b, ldb, M, part, denp, st); break;
+  case ST: launch_solve_t<ST, 128, 32>(Ds, items, nitems, sms, M, st); break;
     ZR_SOLVE_TILES(ZR_CASE)
 #undef ZR_CASE
-    default: launch_solve_t<21, 128, 32>(D, m, v, vp, R, b, ldb, M, part, denp, st); break;
+    default: break;
   }
 }
 

@@ -59,49 +59,70 @@ extern "C" zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t
   }
   std::sort(cand.begin(), cand.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
   if ((int)cand.size() > budget) cand.resize(budget);
-  // workspace: the largest candidate's step layout plus synthetic inputs
-  size_t need = 0;
-  for (auto& c : cand) {
-    Carver m0(nullptr);
-    carve_step(m0, T, S, 0, c.second);
-    m0.take<uint64_t>((size_t)S * T);
-    need = std::max(need, m0.off);
+  // synthetic system of this shape in its own buffers (nodes, right-hand sides, output)
+  uint64_t *v = nullptr, *b = nullptr, *cc = nullptr;
+  cudaError_t e = cudaMalloc(&v, 8 * (size_t)T);
+  if (e == cudaSuccess) e = cudaMalloc(&b, 8 * (size_t)S * T);
+  if (e == cudaSuccess) e = cudaMalloc(&cc, 8 * (size_t)S * T);
+  if (e != cudaSuccess) {
+    cudaFree(v);
+    cudaFree(b);
+    cudaFree(cc);
+    return cuda_err(ctx, e, "zr_autotune_step: buffers");
   }
-  zr_status r = ensure_ws(ctx, need, st);
-  if (r) return r;
+  const unsigned g1 = (unsigned)((T + 255) / 256), g2 = (unsigned)((S * T + 255) / 256);
+  { k_synth<<<g1, 256, 0, st>>>(T, 11, ctx->M, v); note_launch(); }
+  { k_synth<<<g2, 256, 0, st>>>((int64_t)S * T, 14, ctx->M, b); note_launch(); }
+  BatchItem it;
+  it.mode = 1;
+  it.T = T;
+  it.S = S;
+  it.vin = v;
+  it.b = b;
+  it.ldb = T;
+  it.c = cc;
+  it.ldc = T;
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return set_err(ctx, ZR_ERR_CUDA, "zr_autotune_step: events");
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // time each candidate through the batch runner with that plan forced
+  std::vector<zr_plan_entry> saved;
+  for (const auto& pe : ctx->plans)
+    if (!(pe.T == T && pe.S == S)) saved.push_back(pe);
   double best_ms = -1;
   StepDims best = cand.empty() ? plan_step(ctx, T, S) : cand[0].second;
+  zr_status r = ZR_OK;
   for (auto& c : cand) {
-    const StepDims& D = c.second;
-    Carver cv(ctx->ws);
-    StepWs w = carve_step(cv, T, S, 0, D);
-    uint64_t* b = cv.take<uint64_t>((size_t)S * T);
-    const unsigned g1 = (unsigned)((T + 255) / 256), g2 = (unsigned)((S * T + 255) / 256);
-    { k_synth<<<g1, 256, 0, st>>>(T, 11, ctx->M, w.v); note_launch(); }
-    { k_synth<<<g1, 256, 0, st>>>(T, 12, ctx->M, w.m); note_launch(); }
-    { k_synth<<<g1, 256, 0, st>>>(T, 13, ctx->M, w.vp); note_launch(); }
-    { k_synth<<<g2, 256, 0, st>>>((int64_t)S * T, 14, ctx->M, b); note_launch(); }
+    ctx->plans = saved;
+    ctx->plans.push_back({T, S, c.second});
     float ms = 0;
-    for (int rep = 0; rep < 2; rep++) {
+    for (int rep = 0; rep < 2 && r == ZR_OK; rep++) {
       cudaEventRecord(e0, st);
-      launch_carry_partials(D, w.m, w.v, w.vp, ctx->M, w.R, st);
-      launch_solve(D, w.m, w.v, w.vp, w.R, b, T, ctx->M, w.part, w.denp, st);
+      r = run_batch(ctx, &it, 1, ctx->d_status_call, st);
       cudaEventRecord(e1, st);
     }
-    cudaError_t e = cudaEventSynchronize(e1);
+    if (r) break;
+    e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return cuda_err(ctx, e, "zr_autotune_step");
+      r = cuda_err(ctx, e, "zr_autotune_step");
+      break;
     }
     if (best_ms < 0 || ms < best_ms) {
       best_ms = ms;
-      best = D;
+      best = c.second;
     }
+  }
+  ctx->plans = saved;
+  cudaStreamSynchronize(st);
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);   // synthetic nodes may collide: not an error here
+  cudaFree(v);
+  cudaFree(b);
+  cudaFree(cc);
+  if (r) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return r;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

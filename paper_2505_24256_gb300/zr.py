@@ -37,6 +37,13 @@ class zr_poly(ctypes.Structure):
                 ("coef", ctypes.c_void_p)]
 
 
+class zr_step_desc(ctypes.Structure):
+    _fields_ = [("skel", zr_poly), ("newvar", ctypes.c_int32), ("S", ctypes.c_int32), ("offset", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("y", ctypes.c_void_p), ("samples", ctypes.c_void_p),
+                ("probes", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("out_exps", ctypes.c_void_p),
+                ("out_coef", ctypes.c_void_p), ("out_cap", ctypes.c_int64), ("out_count", ctypes.c_void_p)]
+
+
 class zr_blackbox(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nv", ctypes.c_int32),
                 ("TN", ctypes.c_int64), ("N_exps", ctypes.c_void_p), ("N_coef", ctypes.c_void_p),
@@ -81,6 +88,7 @@ SIGNATURES = {
     "zr_zippel_step": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
     "zr_zippel_step_async": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
     "zr_stream_status": (_ST, [_V, _V]),
+    "zr_zippel_step_batched": (_ST, [_V, _I32, _P, _V]),
     "zr_zippel_step_host": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
     "zr_zippel_probes": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _I64, _V]),
     "zr_eval_points": (_ST, [_V, _P, _I64, _P, _P, _V]),
@@ -224,6 +232,17 @@ class Context:
                                          _ptr(probes), ldb, offset, _ptr(out_exps), _ptr(out_coef), out_cap,
                                          _ptr(d_count), _stream(stream))
         self.check(st, "zr_zippel_step_async")
+
+    def zippel_step_batched(self, steps, stream=None):
+        """steps: list of dicts with skel (zr_poly), newvar, S, offset, y, samples, probes, ldb, out_exps,
+        out_coef, out_cap, out_count (device int64 tensor of one element)."""
+        arr = (zr_step_desc * max(len(steps), 1))()
+        for i, d in enumerate(steps):
+            arr[i] = zr_step_desc(d["skel"], d["newvar"], d["S"], d.get("offset", 0), 0, _ptr(d["y"]),
+                                  _ptr(d["samples"]), _ptr(d["probes"]), d["ldb"], _ptr(d["out_exps"]),
+                                  _ptr(d["out_coef"]), d["out_cap"], _ptr(d["out_count"]))
+        self.check(self.L.zr_zippel_step_batched(self._h, len(steps), ctypes.cast(arr, ctypes.c_void_p),
+                                                 _stream(stream)), "zr_zippel_step_batched")
 
     def stream_status(self, stream=None):
         self.check(self.L.zr_stream_status(self._h, _stream(stream)), "zr_stream_status")

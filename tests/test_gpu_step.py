@@ -163,3 +163,56 @@ def test_large_step_workload(ctx, orc):
     assert np.array_equal(hb[sidx, iidx], want)
     ge_, gc_ = D.step(ctx, b)
     assert np.array_equal(ge_, wl.exps) and np.array_equal(gc_, wl.coef)
+
+
+def test_batched_steps_match_single_steps(ctx, orc):
+    """Uneven steps (different T, S, k, nv, offset) in one batched call give
+    exactly the results of the single-step calls and of the oracle."""
+    import torch
+    shapes = [(700, 3, 9, 5, 0), (1, 2, 4, 3, 0), (2500, 5, 20, 21, 1), (64, 2, 9, 9, 0), (0, 2, 5, 4, 0),
+              (4100, 4, 12, 9, 0)]
+    devs, wls, steps, outs = [], [], [], []
+    for n, (T, k, maxe, S, off) in enumerate(shapes):
+        wl = W.step_workload(3000 + n, T, k, maxe, S)
+        D = Dev(ctx, wl)
+        b = D.probes(ctx, off) if T else zeros64(S, 1)
+        cap = max(T * S, 1)
+        oe, oc, cnt = zeros8(cap, wl.nv), zeros64(cap), zeros64(1)
+        steps.append(dict(skel=D.skel, newvar=wl.k, S=S, offset=off, y=D.y, samples=D.cs, probes=b,
+                          ldb=max(T, 1), out_exps=oe, out_coef=oc, out_cap=cap, out_count=cnt))
+        devs.append((D, b))
+        wls.append((wl, off))
+        outs.append((oe, oc, cnt))
+    ctx.zippel_step_batched(steps)
+    torch.cuda.synchronize()
+    for (wl, off), (D, b), (oe, oc, cnt) in zip(wls, devs, outs):
+        n = int(cnt.cpu().item())
+        ge_, gc_ = oe[:n].cpu().numpy(), h64(oc[:n])
+        assert np.array_equal(ge_, wl.exps) and np.array_equal(gc_, wl.coef)
+        if wl.T:
+            se, sc = D.step(ctx, b, off)
+            assert np.array_equal(ge_, se) and np.array_equal(gc_, sc)
+            if wl.T <= 2500:
+                we, wc = orc.zippel_step(wl.skel, wl.k, wl.y, wl.cs, h64(b)[:, :wl.T], offset=off)
+                assert np.array_equal(ge_, we) and np.array_equal(gc_, wc)
+
+
+def test_batched_solve_equals_plain(ctx, orc):
+    """zr_vandermonde_solve_batched (shared launches) against the plain form."""
+    rnd = random.Random(12)
+    systems, plain_out, batch_out, keep = [], [], [], []
+    from tests.gpuutil import rand_nodes, rand_res
+    for T, S, off in [(10, 3, 0), (3000, 21, 0), (1, 1, 1), (257, 9, 1), (5000, 4, 0)]:
+        v = rand_nodes(rnd, T, P63)
+        bb = rand_res(rnd, (S, T), P63)
+        dv, db = d64(v), d64(bb)
+        c1, c2 = zeros64(S, T), zeros64(S, T)
+        keep.append((dv, db))
+        systems.append((dict(T=T, S=S, offset=off, v=dv, b=db, ldb=T, c=c1, ldc=T),
+                        dict(T=T, S=S, offset=off, v=dv, b=db, ldb=T, c=c2, ldc=T)))
+        plain_out.append(c1)
+        batch_out.append(c2)
+    ctx.vandermonde_solve([s[0] for s in systems], plain=True)
+    ctx.vandermonde_solve([s[1] for s in systems], plain=False)
+    for c1, c2 in zip(plain_out, batch_out):
+        assert np.array_equal(h64(c1), h64(c2))
