@@ -10,7 +10,13 @@ before the timed region and stay resident in HBM; their generation time is
 reported separately.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl zr|reference]
-                    [--workload batched|large]
+                    [--workload batched|large|serve] [--requests R]
+
+--workload serve runs the serving mix instead (R requests of hidden sparse
+polynomials and rational functions, 2-8 variables, T log-uniform in
+[16, 2^17]): the plain per-request form (zr_reconstruct, one request after
+another) against the continuous-batching server, saturated and under Poisson
+arrivals at 0.7 of the server's saturated rate.
 
 Under torchrun every rank runs an independent replica of the step on its own
 GPU (the step needs no exchange between GPUs); the time is the maximum over
@@ -307,19 +313,159 @@ def run_zr(args):
     return 0
 
 
+def serve_stats(lat_ms):
+    import numpy as np
+    a = np.sort(np.asarray(lat_ms, dtype=np.float64))
+    q = lambda f: float(a[min(len(a) - 1, int(f * (len(a) - 1) + 0.5))])
+    return {"p50_ms": q(0.5), "p99_ms": q(0.99), "mean_ms": float(a.mean())}
+
+
+def run_serve(args):
+    """The serving mix: plain per-request form vs the continuous-batching server."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    from paper_2505_24256_gb300 import workloads as W
+    from paper_2505_24256_gb300 import zr
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ge.build()
+    reqs = W.serve_requests(args.requests, seed=1005 + 1000 * rank, tmax=args.tmax)
+    wls = [W.serve_blackbox(r) for r in reqs]
+    reqobjs = []
+    for wl in wls:
+        if isinstance(wl, W.RationalWorkload):
+            reqobjs.append(zr.make_request(wl.nv, wl.degN, wl.seed, wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef,
+                                           degD=wl.degD))
+        else:
+            reqobjs.append(zr.make_request(wl.nv, wl.deg, wl.seed, wl.exps, wl.coef))
+    terms = sum(int(wl.Ncoef.shape[0] + wl.Dcoef.shape[0]) if isinstance(wl, W.RationalWorkload)
+                else int(wl.coef.shape[0]) for wl in wls)
+
+    def truth(wl, res):
+        (e, c), D, _ = res
+        if isinstance(wl, W.RationalWorkload):
+            return np.array_equal(e, wl.Nexps) and np.array_equal(c, wl.Ncoef) and D is not None and \
+                np.array_equal(D[0], wl.Dexps) and np.array_equal(D[1], wl.Dcoef)
+        return np.array_equal(e, wl.exps) and np.array_equal(c, wl.coef)
+
+    ctx = zr.Context(W.P63)
+    # warm-up: the first few requests through both forms
+    for wl in wls[:min(args.warmup, len(wls))]:
+        if isinstance(wl, W.RationalWorkload):
+            ctx.reconstruct(wl.nv, wl.degN, wl.seed, wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef, degD=wl.degD)
+        else:
+            ctx.reconstruct(wl.nv, wl.deg, wl.seed, wl.exps, wl.coef)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = zr.launch_count()
+    # (1) plain per-request form: one zr_reconstruct after another
+    svc = []
+    ok_plain = True
+    t_plain0 = time.perf_counter()
+    for wl in wls:
+        t0 = time.perf_counter()
+        if isinstance(wl, W.RationalWorkload):
+            res = ctx.reconstruct(wl.nv, wl.degN, wl.seed, wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef, degD=wl.degD)
+        else:
+            res = ctx.reconstruct(wl.nv, wl.deg, wl.seed, wl.exps, wl.coef)
+        svc.append(time.perf_counter() - t0)
+        ok_plain &= truth(wl, res)
+    plain_s = time.perf_counter() - t_plain0
+    ctx.close()
+
+    def serve(gaps):
+        c = zr.Context(W.P63)
+        srv = zr.Server(c, args.serve_budget_gb << 30, args.slots)
+        arrivals = []
+        tickets = []
+        t0 = time.perf_counter()
+        for (req, _keep), g in zip(reqobjs, gaps):
+            if g > 0:
+                target = (arrivals[-1] if arrivals else 0.0) + g
+                while time.perf_counter() - t0 < target:
+                    time.sleep(min(0.0005, max(0.0, target - (time.perf_counter() - t0))))
+            arrivals.append(time.perf_counter() - t0)
+            tickets.append(srv.submit(req))
+        outs = [srv.wait(t, timeout_s=900) for t in tickets]
+        st = srv.stats()
+        srv.close()
+        c.close()
+        ok = all(truth(wl, r) for wl, r in zip(wls, outs))
+        return st, ok, outs
+
+    # (2) saturated: everything submitted at once -> server capacity
+    sat, ok_sat, _ = serve([0.0] * len(wls))
+    cap_rps = sat["completed"] / sat["wall_s"]
+    # (3) Poisson arrivals at 0.7 x the saturated rate
+    lam = 0.7 * cap_rps
+    rng = np.random.default_rng(1005)
+    gaps = list(rng.exponential(1.0 / lam, size=len(wls)))
+    poi, ok_poi, outs = serve(gaps)
+    launches = zr.launch_count() - launches0
+    clk = clocks.stop()
+    # the plain form under the same arrivals: one request at a time in arrival
+    # order (single-server FIFO queue on the measured service times)
+    arr = np.cumsum(gaps)
+    fin, lat = 0.0, []
+    for a, s_ in zip(arr, svc):
+        start = max(a, fin)
+        fin = start + s_
+        lat.append(1e3 * (fin - a))
+    plain_lat = serve_stats(lat)
+    line = {
+        "metric": METRIC,
+        "value": sat["terms_per_s"], "unit": "terms/s",
+        "n_gpus": world, "steps": len(wls), "warmup": args.warmup,
+        "ms_per_step": 1e3 * sat["wall_s"] / max(1, len(wls)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"serve_{len(wls)}_requests", "requests": len(wls), "seed": 1005, "tmax": args.tmax,
+                   "terms": terms, "slots": args.slots, "mem_budget_gb": args.serve_budget_gb,
+                   "l2": "inputs of the larger requests exceed L2", "parallelism": f"replicas{world}"},
+        "serve_saturated": {"terms_per_s": sat["terms_per_s"], "requests_per_s": cap_rps, "p50_ms": sat["p50_ms"],
+                            "p99_ms": sat["p99_ms"], "ticks": sat["ticks"], "batch_entries": sat["batch_entries"],
+                            "max_active": sat["max_active"]},
+        "serve_poisson": {"lambda_per_s": lam, "terms_per_s": poi["terms_per_s"], "p50_ms": poi["p50_ms"],
+                          "p99_ms": poi["p99_ms"], "mean_ms": poi["mean_ms"], "max_active": poi["max_active"]},
+        "plain_per_request": {"terms_per_s": terms / plain_s, "requests_per_s": len(wls) / plain_s,
+                              "poisson_same_arrivals": plain_lat,
+                              "service_ms": serve_stats([1e3 * x for x in svc])},
+        "e2e": {"value": sat["terms_per_s"], "unit": "terms/s",
+                "h2d_bytes_per_step": int(sum(o[0].bb.TN * (o[0].bb.nv + 8) + o[0].bb.TD * (o[0].bb.nv + 8)
+                                              for o in reqobjs) / max(1, len(wls))),
+                "d2h_bytes_per_step": int(sum((r[0][1].shape[0] + (0 if r[1] is None else r[1][1].shape[0]))
+                                              * (r[0][0].shape[1] + 8) for r in outs) / max(1, len(wls)))},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "check": "generator truth" if (ok_plain and ok_sat and ok_poi) else "MISMATCH",
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="zr", choices=["zr", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "large"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=512, help="serving mix size (--workload serve)")
+    ap.add_argument("--tmax", type=int, default=1 << 17, help="largest request T (--workload serve)")
+    ap.add_argument("--slots", type=int, default=64, help="server slots (--workload serve)")
+    ap.add_argument("--serve-budget-gb", type=int, default=64, help="server memory budget (--workload serve)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_zr(args)
 
 

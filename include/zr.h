@@ -323,6 +323,47 @@ zr_status zr_reconstruct(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_para
                          void* stream);
 void zr_result_free(zr_result* r);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of reconstructions.
+ *
+ * A server owns its context (do not use the context for anything else while
+ * the server exists) and runs a scheduler thread.  Requests are admitted
+ * while slots (max_slots) are free and the device memory held by the active
+ * requests plus the new request's estimate stays within mem_budget bytes (a
+ * request too large for the budget runs when nothing else is active).  Each
+ * scheduler tick generates the probes of every active request's next step and
+ * runs all those steps in one batch of launches; a finished request frees its
+ * slot at once and waiting requests join at the next tick.  Skeletons and
+ * probes stay on the device.  A request's result depends only on its own
+ * black box and seed, never on the other requests in its batches.
+ *
+ * zr_serve_submit copies the request (thread-safe) and returns a ticket.
+ * zr_serve_poll returns ZR_ERR_BUSY until the request is done, then its status
+ * and (on success) its result, once; a ticket never issued or already handed
+ * out gives ZR_ERR_INVALID_ARG.  zr_serve_wait waits at most timeout_us
+ * (ZR_ERR_TIMEOUT).  zr_serve_stats_get reports latencies (completion minus
+ * submission, milliseconds) over completed requests and the term throughput
+ * between the first submission and the last completion.  zr_serve_destroy
+ * completes every submitted request, frees uncollected results and the server.
+ * ------------------------------------------------------------------------- */
+typedef struct zr_server zr_server;
+typedef struct zr_request {
+  zr_blackbox bb;        /* host arrays, copied by zr_serve_submit */
+  zr_recon_params prm;
+} zr_request;
+typedef struct zr_serve_stats {
+  int64_t submitted, completed, failed, terms, ticks, batch_entries;
+  int32_t max_active, pad;
+  double p50_ms, p99_ms, mean_ms, wall_s, terms_per_s;
+} zr_serve_stats;
+
+zr_status zr_serve_create(zr_ctx* ctx, size_t mem_budget, int32_t max_slots, zr_server** out);
+zr_status zr_serve_submit(zr_server* server, const zr_request* req, uint64_t* ticket);
+zr_status zr_serve_poll(zr_server* server, uint64_t ticket, zr_result** out);
+zr_status zr_serve_wait(zr_server* server, uint64_t ticket, int64_t timeout_us, zr_result** out);
+zr_status zr_serve_stats_get(zr_server* server, zr_serve_stats* out);
+void zr_serve_destroy(zr_server* server);
+
 #ifdef __cplusplus
 }
 #endif

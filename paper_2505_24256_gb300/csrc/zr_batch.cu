@@ -445,7 +445,7 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
     d.out_count = it.out_count;
     d.c = it.c;
     d.ldc = it.ldc;
-    d.status = status;
+    d.status = it.status ? it.status : status;
   }
   // stage the tables in pinned memory, then one copy
   char* dtab = cv.take<char>(table_bytes + 256);

@@ -107,6 +107,7 @@ struct BatchItem {
   int64_t* out_count = nullptr;
   uint64_t* c = nullptr;
   int64_t ldc = 0;
+  uint32_t* status = nullptr;   // the entry's own status word (else the batch's)
 };
 // Workspace bytes a batch needs (its regions plus the device tables).
 size_t batch_ws_need(const zr_ctx* ctx, const BatchItem* items, int n);
@@ -123,6 +124,9 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
 zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
                       const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
                       cudaStream_t st);
+
+// argument check of a reconstruction request (zr_recon.cu)
+zr_status check_recon_args(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_params* prm);
 
 // balanced step pieces (zr_balance.cu)
 void launch_ratio(int64_t T, int S, const uint64_t* Nv, const uint64_t* Dv, int64_t ld, const Mod& M, uint64_t* pre,

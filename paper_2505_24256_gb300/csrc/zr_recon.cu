@@ -1,11 +1,11 @@
 // zr_recon.cu -- full reconstructions (Sec. 1) and the balanced step entry.
 //
-// zr_reconstruct runs the variable-by-variable loop on the device: step 0 is a
-// dense univariate reconstruction in x_0 (Newton for polynomials, Thiele for
-// rational functions) with x_1.. fixed at rest values z; every later step k is
-// a Zippel step in x_k whose probes come from the sparse evaluator.  The
+// A reconstruction runs variable by variable on the device: step 0 is a dense
+// univariate reconstruction in x_0 (Newton for polynomials, Thiele for
+// rational functions) with x_1.. fixed at rest values z; every later step k
+// is a Zippel step in x_k whose probes come from the sparse evaluator.  The
 // skeleton stays on the device between steps; the host reads back only the
-// term count of each step (it sizes the next launch) and the final result.
+// term counts (they size the next step) and the final result.
 //
 // Random values follow the documented splitmix64 schedule (include/zr.h), the
 // same one the CPU oracle implements independently, so both pick the same
@@ -17,15 +17,13 @@
 #include <algorithm>
 #include <vector>
 
-#include "zr_internal.h"
+#include "zr_recon.h"
 
-using namespace zr;
+namespace zr {
 
 namespace {
 
-typedef unsigned __int128 u128;
-
-// ---- splitmix64 as a counter-based generator ------------------------------
+// ---- splitmix64 as a counter-based generator --------------------------------
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 uint64_t sm_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -72,147 +70,8 @@ void draw_step(uint64_t seed, int k, int attempt, bool have_c0, uint64_t c0, int
     }
 }
 
-// ---- owned device memory -----------------------------------------------------
-struct DBuf {
-  void* p = nullptr;
-  size_t n = 0;
-  DBuf() = default;
-  DBuf(const DBuf&) = delete;
-  DBuf& operator=(const DBuf&) = delete;
-  ~DBuf() { if (p) cudaFree(p); }
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= n) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
-    cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 8);
-    if (e == cudaSuccess) n = bytes;
-    return e;
-  }
-  template <class T>
-  T* as() const { return static_cast<T*>(p); }
-};
+bool retryable(zr_status s) { return s == ZR_ERR_SINGULAR || s == ZR_ERR_POLE || s == ZR_ERR_UNLUCKY; }
 
-// A device-resident sparse polynomial.
-struct DPoly {
-  int nv = 0;
-  int64_t T = 0;
-  DBuf exps, coef;
-  zr_poly view() const { return zr_poly{nv, T, exps.as<uint8_t>(), coef.as<uint64_t>()}; }
-};
-
-struct Call {
-  zr_ctx* ctx;
-  cudaStream_t st;
-  const Mod& M;
-  zr_status fail(zr_status s, const char* what) { return set_err(ctx, s, what); }
-  zr_status cuda(cudaError_t e, const char* what) { return cuda_err(ctx, e, what); }
-  // waits for the stream and turns the call status word into a zr_status
-  zr_status sync_status() {
-    cudaError_t e = cudaMemcpyAsync(ctx->h_status + 1, ctx->d_status_call, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda(e, "reconstruct");
-    const uint32_t f = ctx->h_status[1];
-    cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
-    return status_from_flags(ctx, f);
-  }
-};
-
-zr_status upload(Call& c, DBuf& b, const void* host, size_t bytes) {
-  cudaError_t e = b.ensure(bytes);
-  if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b.p, host, bytes, cudaMemcpyHostToDevice, c.st);
-  return c.cuda(e, "upload");
-}
-
-// Zippel steps on device skeletons, in one batch: entry i turns skel[i] into
-// out[i] (capacity T S) with its own samples and probes.  Counts come back
-// through the context's count words.
-zr_status zippel_steps_dev(Call& c, int n, const DPoly* const* skel, const int* k, const uint64_t* const* d_y,
-                           const int* S, const uint64_t* const* d_cs, const uint64_t* const* d_b, const int64_t* ldb,
-                           int offset, DPoly* const* out) {
-  std::vector<BatchItem> items;
-  std::vector<int> which;
-  for (int i = 0; i < n; i++) {
-    const int64_t T = skel[i]->T;
-    const int64_t cap = T * S[i];
-    cudaError_t e = out[i]->exps.ensure((size_t)(cap > 0 ? cap : 1) * skel[i]->nv);
-    if (e == cudaSuccess) e = out[i]->coef.ensure(sizeof(uint64_t) * (cap > 0 ? cap : 1));
-    if (e != cudaSuccess) return c.cuda(e, "step output");
-    out[i]->nv = skel[i]->nv;
-    out[i]->T = 0;
-    if (T == 0) continue;
-    BatchItem it;
-    it.mode = 0;
-    it.T = T;
-    it.S = S[i];
-    it.k = k[i];
-    it.nv = skel[i]->nv;
-    it.offset = offset;
-    it.exps = skel[i]->exps.as<uint8_t>();
-    it.y = d_y[i];
-    it.xs = d_cs[i];
-    it.b = d_b[i];
-    it.ldb = ldb[i];
-    it.out_exps = out[i]->exps.as<uint8_t>();
-    it.out_coef = out[i]->coef.as<uint64_t>();
-    it.out_cap = cap;
-    it.out_count = c.ctx->d_count + items.size();
-    items.push_back(it);
-    which.push_back(i);
-  }
-  if (items.empty()) return ZR_OK;
-  zr_status r = run_batch(c.ctx, items.data(), (int)items.size(), c.ctx->d_status_call, c.st);
-  if (r) return r;
-  cudaError_t e = cudaMemcpyAsync(c.ctx->h_count, c.ctx->d_count, sizeof(int64_t) * items.size(),
-                                  cudaMemcpyDeviceToHost, c.st);
-  if (e != cudaSuccess) return c.cuda(e, "step count");
-  r = c.sync_status();
-  for (size_t t = 0; t < which.size(); t++) out[which[t]]->T = c.ctx->h_count[t];
-  return r;
-}
-
-zr_status zippel_step_dev(Call& c, const DPoly& skel, int k, const uint64_t* d_y, int S, const uint64_t* d_cs,
-                          const uint64_t* d_b, int64_t ldb, int offset, DPoly& out) {
-  const DPoly* sk[1] = {&skel};
-  DPoly* o[1] = {&out};
-  return zippel_steps_dev(c, 1, sk, &k, &d_y, &S, &d_cs, &d_b, &ldb, offset, o);
-}
-
-// Univariate dense reconstruction helpers for step 0 --------------------------
-
-// Newton through (cs[s], vals[s]), s < S, on the device; coefficients to host.
-zr_status newton_coeffs(Call& c, int S, const uint64_t* d_cs, const uint64_t* d_vals, std::vector<uint64_t>& coef,
-                        DBuf& scratch) {
-  cudaError_t e = scratch.ensure(sizeof(uint64_t) * ((size_t)S * S + S));
-  if (e != cudaSuccess) return c.cuda(e, "newton scratch");
-  uint64_t* invd = scratch.as<uint64_t>();
-  uint64_t* out = invd + (size_t)S * S;
-  launch_newton_table(S, d_cs, c.M, invd, c.ctx->d_status_call, c.st);
-  launch_newton(1, S, d_cs, invd, d_vals, 1, c.M, out, c.st);
-  coef.assign(S, 0);
-  e = cudaMemcpyAsync(coef.data(), out, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, c.st);
-  if (e != cudaSuccess) return c.cuda(e, "newton copy");
-  return c.sync_status();
-}
-
-// Skeleton in x_0 from coefficients (nonzero powers), uploaded to the device.
-zr_status skeleton_from_coeffs(Call& c, int nv, const std::vector<uint64_t>& coef, int deg, DPoly& out) {
-  std::vector<uint8_t> ex;
-  std::vector<uint64_t> cf;
-  for (int e = 0; e <= deg && e < (int)coef.size(); e++)
-    if (coef[e]) {
-      for (int m = 0; m < nv; m++) ex.push_back(m == 0 ? (uint8_t)e : 0);
-      cf.push_back(coef[e]);
-    }
-  out.nv = nv;
-  out.T = (int64_t)cf.size();
-  zr_status r = upload(c, out.exps, ex.data(), ex.size());
-  if (!r) r = upload(c, out.coef, cf.data(), cf.size() * sizeof(uint64_t));
-  return r;
-}
-
-// The probe points of step 0: (c_s, z_1, .., z_{nv-1}).
 std::vector<uint64_t> step0_points(int nv, int S, const uint64_t* cs, const uint64_t* z) {
   std::vector<uint64_t> pts((size_t)S * nv);
   for (int s = 0; s < S; s++)
@@ -220,317 +79,411 @@ std::vector<uint64_t> step0_points(int nv, int S, const uint64_t* cs, const uint
   return pts;
 }
 
-zr_result* make_result(int nv, bool rational) {
-  zr_result* r = (zr_result*)calloc(1, sizeof(zr_result));
-  if (r) {
-    r->nv = nv;
-    r->rational = rational ? 1 : 0;
+}  // namespace
+
+Recon::Recon(zr_ctx* ctx, cudaStream_t st, const zr_blackbox& bb, const zr_recon_params& prm)
+    : ctx_(ctx), st_(st), M_(ctx->M), nv_(prm.nv), rational_(bb.kind == ZR_BB_RATIONAL), seed_(prm.seed),
+      offset_(prm.offset) {
+  Ne_.assign(bb.N_exps, bb.N_exps + (size_t)bb.TN * nv_);
+  Nc_.assign(bb.N_coef, bb.N_coef + bb.TN);
+  degN_.assign(prm.degN, prm.degN + nv_);
+  if (rational_) {
+    De_.assign(bb.D_exps, bb.D_exps + (size_t)bb.TD * nv_);
+    Dc_.assign(bb.D_coef, bb.D_coef + bb.TD);
+    degD_.assign(prm.degD, prm.degD + nv_);
   }
+}
+
+zr_status Recon::fail(zr_status s) {
+  phase_ = FAILED;
+  err_ = s;
+  return s;
+}
+
+zr_status Recon::sync_status() {
+  cudaError_t e = cudaMemcpyAsync(ctx_->h_status + 1, ctx_->d_status_call, sizeof(uint32_t), cudaMemcpyDeviceToHost, st_);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx_, e, "reconstruct");
+  const uint32_t f = ctx_->h_status[1];
+  cudaMemsetAsync(ctx_->d_status_call, 0, sizeof(uint32_t), st_);
+  return status_from_flags(ctx_, f);
+}
+
+zr_status Recon::upload(DBuf& b, const void* host, size_t bytes) {
+  cudaError_t e = b.ensure(bytes);
+  if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b.p, host, bytes, cudaMemcpyHostToDevice, st_);
+  return cuda_err(ctx_, e, "upload");
+}
+
+size_t Recon::device_bytes() const {
+  const DBuf* bufs[] = {&d_y_, &d_cs_, &d_z_, &d_b_, &d_pts_, &d_vals_, &scratch_, &persist_, &fv_, &one_, &ones_};
+  size_t s = fN_.bytes() + fD_.bytes() + curN_.bytes() + curD_.bytes() + nextN_.bytes() + nextD_.bytes();
+  for (const DBuf* b : bufs) s += b->n;
+  return s;
+}
+
+size_t Recon::estimate_bytes(const zr_blackbox& bb, const zr_recon_params& prm) {
+  // hidden function(s), the largest step (skeleton <= hidden terms, S <= 64
+  // samples or 2 max(deg)+2 Thiele points) with its probes and outputs
+  const int64_t Tf = bb.TN + (bb.kind == ZR_BB_RATIONAL ? bb.TD : 0);
+  int smax = 1;
+  for (int m = 0; m < prm.nv; m++) {
+    int s = prm.degN[m] + 1;
+    if (bb.kind == ZR_BB_RATIONAL) s = 2 * std::max(prm.degN[m], prm.degD[m]) + 2;
+    smax = std::max(smax, s);
+  }
+  const size_t row = (size_t)prm.nv + 8;
+  return (size_t)Tf * row + 2 * (size_t)Tf * smax * row + (size_t)Tf * smax * 8 * (bb.kind == ZR_BB_RATIONAL ? 6 : 1) +
+         (1 << 16);
+}
+
+zr_status Recon::newton_coeffs(int S, const uint64_t* d_cs, const uint64_t* d_vals, std::vector<uint64_t>& coef) {
+  cudaError_t e = scratch_.ensure(sizeof(uint64_t) * ((size_t)S * S + S));
+  if (e != cudaSuccess) return cuda_err(ctx_, e, "newton scratch");
+  uint64_t* invd = scratch_.as<uint64_t>();
+  uint64_t* out = invd + (size_t)S * S;
+  launch_newton_table(S, d_cs, M_, invd, ctx_->d_status_call, st_);
+  launch_newton(1, S, d_cs, invd, d_vals, 1, M_, out, st_);
+  coef.assign(S, 0);
+  e = cudaMemcpyAsync(coef.data(), out, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st_);
+  if (e != cudaSuccess) return cuda_err(ctx_, e, "newton copy");
+  return sync_status();
+}
+
+zr_status Recon::skeleton_from_coeffs(const std::vector<uint64_t>& coef, int deg, DPoly& out) {
+  std::vector<uint8_t> ex;
+  std::vector<uint64_t> cf;
+  for (int e = 0; e <= deg && e < (int)coef.size(); e++)
+    if (coef[e]) {
+      for (int m = 0; m < nv_; m++) ex.push_back(m == 0 ? (uint8_t)e : 0);
+      cf.push_back(coef[e]);
+    }
+  out.nv = nv_;
+  out.T = (int64_t)cf.size();
+  zr_status r = upload(out.exps, ex.data(), ex.size());
+  if (!r) r = upload(out.coef, cf.data(), cf.size() * sizeof(uint64_t));
   return r;
 }
 
-zr_status download_poly(Call& c, const DPoly& p, int64_t* T, uint8_t** exps, uint64_t** coef) {
+zr_status Recon::download(const DPoly& p, int64_t* T, uint8_t** exps, uint64_t** coef) {
   *T = p.T;
-  *exps = (uint8_t*)malloc((size_t)(p.T > 0 ? p.T : 1) * p.nv);
+  *exps = (uint8_t*)malloc((size_t)(p.T > 0 ? p.T : 1) * nv_);
   *coef = (uint64_t*)malloc(sizeof(uint64_t) * (p.T > 0 ? p.T : 1));
-  if (!*exps || !*coef) return c.fail(ZR_ERR_OOM, "result allocation");
+  if (!*exps || !*coef) return set_err(ctx_, ZR_ERR_OOM, "result allocation");
   cudaError_t e = cudaSuccess;
   if (p.T > 0) {
-    e = cudaMemcpyAsync(*exps, p.exps.p, (size_t)p.T * p.nv, cudaMemcpyDeviceToHost, c.st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(*coef, p.coef.p, sizeof(uint64_t) * p.T, cudaMemcpyDeviceToHost, c.st);
+    e = cudaMemcpyAsync(*exps, p.exps.p, (size_t)p.T * nv_, cudaMemcpyDeviceToHost, st_);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*coef, p.coef.p, sizeof(uint64_t) * p.T, cudaMemcpyDeviceToHost, st_);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
-  return c.cuda(e, "result copy");
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
+  return cuda_err(ctx_, e, "result copy");
 }
 
-bool retryable(zr_status s) { return s == ZR_ERR_SINGULAR || s == ZR_ERR_POLE || s == ZR_ERR_UNLUCKY; }
-
-// ---- polynomial ---------------------------------------------------------------
-zr_status reconstruct_poly(Call& c, const zr_blackbox* bb, const zr_recon_params* prm, zr_result* res) {
-  const int nv = prm->nv;
-  const uint64_t p = c.M.p;
-  std::vector<uint64_t> z(nv), y(nv + 1), cs;
-  draw_rest(prm->seed, nv, p, z.data());
-  DPoly f;
-  f.nv = nv;
-  f.T = bb->TN;
-  zr_status r = upload(c, f.exps, bb->N_exps, (size_t)bb->TN * nv);
-  if (!r) r = upload(c, f.coef, bb->N_coef, sizeof(uint64_t) * bb->TN);
-  if (r) return r;
-  DBuf d_pts, d_vals, d_y, d_cs, d_z, d_b, scratch;
-  if ((r = upload(c, d_z, z.data(), sizeof(uint64_t) * nv))) return r;
-  DPoly cur, next;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, c.st);
-  // step 0: dense Newton in x_0
-  {
-    const int S = prm->degN[0] + 1;
-    cs.assign(S, 0);
-    draw_step(prm->seed, 0, 0, false, 0, S, p, y.data(), cs.data());
-    std::vector<uint64_t> pts = step0_points(nv, S, cs.data(), z.data());
-    if ((r = upload(c, d_pts, pts.data(), pts.size() * 8))) return r;
-    if ((r = upload(c, d_cs, cs.data(), cs.size() * 8))) return r;
-    cudaError_t e = d_vals.ensure(8 * (size_t)S);
-    if (e != cudaSuccess) return c.cuda(e, "values");
-    zr_poly fv = f.view();
-    launch_eval_points(&fv, S, d_pts.as<uint64_t>(), c.M, d_vals.as<uint64_t>(), c.st);
-    std::vector<uint64_t> coef;
-    if ((r = newton_coeffs(c, S, d_cs.as<uint64_t>(), d_vals.as<uint64_t>(), coef, scratch))) return r;
-    if ((r = skeleton_from_coeffs(c, nv, coef, S - 1, cur))) return r;
+zr_status Recon::start() {
+  const uint64_t p = M_.p;
+  z_.assign(nv_, 0);
+  y_.assign(nv_ + 1, 0);
+  draw_rest(seed_, nv_, p, z_.data());
+  cudaMemsetAsync(ctx_->d_status_call, 0, sizeof(uint32_t), st_);
+  fN_.nv = fD_.nv = nv_;
+  fN_.T = (int64_t)Nc_.size();
+  zr_status r = upload(fN_.exps, Ne_.data(), Ne_.size());
+  if (!r) r = upload(fN_.coef, Nc_.data(), 8 * Nc_.size());
+  if (!r && rational_) {
+    fD_.T = (int64_t)Dc_.size();
+    r = upload(fD_.exps, De_.data(), De_.size());
+    if (!r) r = upload(fD_.coef, Dc_.data(), 8 * Dc_.size());
   }
-  int steps = 0, redraws = 0;
-  for (int k = 1; k < nv; k++) {
-    const int S = prm->degN[k] + 1;
-    cs.assign(S, 0);
-    for (int attempt = 0;; attempt++) {
-      draw_step(prm->seed, k, attempt, true, z[k], S, p, y.data(), cs.data());
-      if ((r = upload(c, d_y, y.data(), 8 * (size_t)k))) return r;
-      if ((r = upload(c, d_cs, cs.data(), 8 * (size_t)S))) return r;
-      const int64_t T = cur.T;
-      cudaError_t e = d_b.ensure(8 * (size_t)S * (T > 0 ? T : 1));
-      if (e != cudaSuccess) return c.cuda(e, "probes");
-      zr_poly fv = f.view();
-      if (T > 0) {
-        r = probes_impl(c.ctx, &fv, k, d_y.as<uint64_t>(), S, d_cs.as<uint64_t>(), d_z.as<uint64_t>(), T,
-                        prm->offset, d_b.as<uint64_t>(), T, c.ctx->d_status_call, c.st);
-        if (r) return r;
-      }
-      r = zippel_step_dev(c, cur, k, d_y.as<uint64_t>(), S, d_cs.as<uint64_t>(), d_b.as<uint64_t>(), T > 0 ? T : 1,
-                          prm->offset, next);
-      steps++;
-      if (r == ZR_ERR_SINGULAR && attempt + 1 < kMaxAttempts) {
-        redraws++;
-        continue;
-      }
-      break;
+  if (!r) r = upload(d_z_, z_.data(), 8 * (size_t)nv_);
+  if (!r) r = rational_ ? step0_rational() : step0_poly();
+  if (r) return fail(r);
+  phase_ = RUN;
+  k_ = 1;
+  attempt_ = 0;
+  if (k_ >= nv_) return finalize();
+  return ZR_OK;
+}
+
+zr_status Recon::step0_poly() {
+  const int S = degN_[0] + 1;
+  cs_.assign(S, 0);
+  draw_step(seed_, 0, 0, false, 0, S, M_.p, y_.data(), cs_.data());
+  std::vector<uint64_t> pts = step0_points(nv_, S, cs_.data(), z_.data());
+  zr_status r = upload(d_pts_, pts.data(), pts.size() * 8);
+  if (!r) r = upload(d_cs_, cs_.data(), cs_.size() * 8);
+  if (r) return r;
+  cudaError_t e = d_vals_.ensure(8 * (size_t)S);
+  if (e != cudaSuccess) return cuda_err(ctx_, e, "values");
+  zr_poly fv = fN_.view();
+  launch_eval_points(&fv, S, d_pts_.as<uint64_t>(), M_, d_vals_.as<uint64_t>(), st_);
+  std::vector<uint64_t> coef;
+  if ((r = newton_coeffs(S, d_cs_.as<uint64_t>(), d_vals_.as<uint64_t>(), coef))) return r;
+  return skeleton_from_coeffs(coef, S - 1, curN_);
+}
+
+zr_status Recon::step0_rational() {
+  const int dN = degN_[0], dD = degD_[0];
+  const int Sf = 2 * std::max(dN, dD) + 2;
+  cs_.assign(Sf, 0);
+  const uint64_t unit = 1;
+  zr_status r = upload(one_, &unit, 8);
+  if (r) return r;
+  for (int attempt = 0;; attempt++) {
+    draw_step(seed_, 0, attempt, false, 0, Sf, M_.p, y_.data(), cs_.data());
+    std::vector<uint64_t> pts = step0_points(nv_, Sf, cs_.data(), z_.data());
+    if ((r = upload(d_pts_, pts.data(), pts.size() * 8))) return r;
+    if ((r = upload(d_cs_, cs_.data(), cs_.size() * 8))) return r;
+    cudaError_t e = d_vals_.ensure(8 * (size_t)Sf * 4 + 8 * (size_t)(dN + dD + 2));
+    if (e != cudaSuccess) return cuda_err(ctx_, e, "values");
+    uint64_t* nvls = d_vals_.as<uint64_t>();
+    uint64_t* dvls = nvls + Sf;
+    uint64_t* pre = dvls + Sf;
+    uint64_t* f = pre + Sf;
+    uint64_t* nval = f + Sf;
+    uint64_t* dval = nval + (dN + 1);
+    zr_poly nv_p = fN_.view(), dv_p = fD_.view();
+    launch_eval_points(&nv_p, Sf, d_pts_.as<uint64_t>(), M_, nvls, st_);
+    launch_eval_points(&dv_p, Sf, d_pts_.as<uint64_t>(), M_, dvls, st_);
+    launch_ratio(1, Sf, nvls, dvls, 1, M_, pre, f, 1, ctx_->d_status_call, st_);
+    r = sync_status();
+    if (!r) {
+      e = persist_.ensure(8 * thiele_scratch_words(1, Sf) + 256);
+      if (e != cudaSuccess) return cuda_err(ctx_, e, "thiele scratch");
+      launch_thiele_balance(1, Sf, d_cs_.as<uint64_t>(), f, 1, one_.as<uint64_t>(), dN, dD, 1, 1,
+                            persist_.as<uint64_t>(), M_, nval, 1, dval, 1, ctx_->d_status_call, st_);
+      r = sync_status();
+    }
+    if ((r == ZR_ERR_POLE || r == ZR_ERR_UNLUCKY) && attempt + 1 < kMaxAttempts) {
+      redraws_++;
+      continue;
     }
     if (r) return r;
-    std::swap(cur.exps.p, next.exps.p);
-    std::swap(cur.exps.n, next.exps.n);
-    std::swap(cur.coef.p, next.coef.p);
-    std::swap(cur.coef.n, next.coef.n);
-    cur.T = next.T;
+    std::vector<uint64_t> cn, cd;
+    if ((r = newton_coeffs(dN + 1, d_cs_.as<uint64_t>(), nval, cn))) return r;
+    if ((r = newton_coeffs(dD + 1, d_cs_.as<uint64_t>(), dval, cd))) return r;
+    if ((r = skeleton_from_coeffs(cn, dN, curN_))) return r;
+    return skeleton_from_coeffs(cd, dD, curD_);
   }
-  cudaEventRecord(e1, c.st);
-  cudaEventSynchronize(e1);
-  float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  res->steps = steps;
-  res->redraws = redraws;
-  res->device_ms = ms;
-  return download_poly(c, cur, &res->TN, &res->N_exps, &res->N_coef);
 }
 
-// ---- rational (balanced) ---------------------------------------------------------
-
-// The balanced step on device skeletons (N without, D with coefficients).
-zr_status balanced_step_dev(Call& c, const DPoly& skN, const DPoly& skD, int k, const uint64_t* d_y, int dN, int dD,
-                            const uint64_t* d_cs, const uint64_t* d_f, int64_t ldf, int offset, DPoly& outN,
-                            DPoly& outD, DBuf& persist) {
-  const int64_t TN = skN.T, TD = skD.T, Tmax = std::max(TN, TD);
-  const int Sf = 2 * std::max(dN, dD) + 2, SN = dN + 1, SD = dD + 1;
-  if (Tmax == 0) {
-    outN.T = outD.T = 0;
-    outN.nv = skN.nv;
-    outD.nv = skD.nv;
+zr_status Recon::step_entry(const DPoly& skel, int S, const uint64_t* b, int64_t ldb, DPoly& out, uint32_t* d_status,
+                            int64_t* d_count, std::vector<BatchItem>& items) {
+  const int64_t T = skel.T, cap = T * S;
+  cudaError_t e = out.exps.ensure((size_t)(cap > 0 ? cap : 1) * nv_);
+  if (e == cudaSuccess) e = out.coef.ensure(sizeof(uint64_t) * (cap > 0 ? cap : 1));
+  if (e != cudaSuccess) return cuda_err(ctx_, e, "step output");
+  out.nv = nv_;
+  out.T = 0;
+  if (T == 0) {
+    cudaMemsetAsync(d_count, 0, 8, st_);
     return ZR_OK;
   }
-  // persistent per-step buffers: dprev, bN, bD, Thiele scratch
-  const size_t w_dprev = (size_t)Tmax, w_bN = (size_t)SN * (TN ? TN : 1), w_bD = (size_t)SD * (TD ? TD : 1);
-  const size_t w_th = thiele_scratch_words(Tmax, Sf);
-  const size_t w_ones = (size_t)skD.nv;
-  cudaError_t e = persist.ensure(8 * (w_dprev + w_bN + w_bD + w_th + w_ones) + 4 * 256);
-  if (e != cudaSuccess) return c.cuda(e, "balanced buffers");
-  uint64_t* dprev = persist.as<uint64_t>();
-  uint64_t* bN = dprev + w_dprev;
-  uint64_t* bD = bN + w_bN;
-  uint64_t* th = bD + w_bD;
-  uint64_t* ones = th + w_th;
-  {
-    const std::vector<uint64_t> h(w_ones, 1);
-    e = cudaMemcpyAsync(ones, h.data(), 8 * w_ones, cudaMemcpyHostToDevice, c.st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
-    if (e != cudaSuccess) return c.cuda(e, "balanced buffers");
-  }
-  // D' at the probes: the evaluator on the denominator skeleton, whose
-  // exponents of x_k and later variables are zero (their values do not matter)
-  zr_poly dv = skD.view();
-  if (TD > 0) {
-    zr_status r = probes_impl(c.ctx, &dv, k, d_y, 1, ones, ones, Tmax, offset, dprev, Tmax, c.ctx->d_status_call, c.st);
-    if (r) return r;
-  } else {
-    cudaMemsetAsync(dprev, 0, 8 * Tmax, c.st);
-  }
-  launch_thiele_balance(Tmax, Sf, d_cs, d_f, ldf, dprev, dN, dD, TN, TD, th, c.M, bN, TN ? TN : 1, bD, TD ? TD : 1,
-                        c.ctx->d_status_call, c.st);
-  zr_status r = c.sync_status();
-  if (r) return r;
-  // the numerator and denominator steps share one batch of launches
-  const DPoly* sk[2] = {&skN, &skD};
-  DPoly* o[2] = {&outN, &outD};
-  const int ks[2] = {k, k}, Ss[2] = {SN, SD};
-  const uint64_t* ys[2] = {d_y, d_y};
-  const uint64_t* css[2] = {d_cs, d_cs};
-  const uint64_t* bs[2] = {bN, bD};
-  const int64_t lds[2] = {TN ? TN : 1, TD ? TD : 1};
-  return zippel_steps_dev(c, 2, sk, ks, ys, Ss, css, bs, lds, offset, o);
+  BatchItem it;
+  it.mode = 0;
+  it.T = T;
+  it.S = S;
+  it.k = k_;
+  it.nv = nv_;
+  it.offset = offset_;
+  it.exps = skel.exps.as<uint8_t>();
+  it.y = d_y_.as<uint64_t>();
+  it.xs = d_cs_.as<uint64_t>();
+  it.b = b;
+  it.ldb = ldb;
+  it.out_exps = out.exps.as<uint8_t>();
+  it.out_coef = out.coef.as<uint64_t>();
+  it.out_cap = cap;
+  it.out_count = d_count;
+  it.status = d_status;
+  items.push_back(it);
+  return ZR_OK;
 }
 
-// f = N/D at the step's probe family (Sf samples, Tmax probes).
-zr_status rational_probes(Call& c, const DPoly& N, const DPoly& D, int k, const uint64_t* d_y, int Sf,
-                          const uint64_t* d_cs, const uint64_t* d_z, int64_t Tmax, int offset, DBuf& vals,
-                          uint64_t** fout) {
-  cudaError_t e = vals.ensure(8 * (size_t)Sf * Tmax * 4);
-  if (e != cudaSuccess) return c.cuda(e, "rational probes");
-  uint64_t* nvls = vals.as<uint64_t>();
-  uint64_t* dvls = nvls + (size_t)Sf * Tmax;
-  uint64_t* pre = dvls + (size_t)Sf * Tmax;
-  uint64_t* f = pre + (size_t)Sf * Tmax;
-  zr_poly nv_ = N.view(), dv_ = D.view();
-  zr_status r = probes_impl(c.ctx, &nv_, k, d_y, Sf, d_cs, d_z, Tmax, offset, nvls, Tmax, c.ctx->d_status_call, c.st);
-  if (!r) r = probes_impl(c.ctx, &dv_, k, d_y, Sf, d_cs, d_z, Tmax, offset, dvls, Tmax, c.ctx->d_status_call, c.st);
-  if (r) return r;
-  launch_ratio(Tmax, Sf, nvls, dvls, Tmax, c.M, pre, f, Tmax, c.ctx->d_status_call, c.st);
-  *fout = f;
-  return c.sync_status();
-}
-
-zr_status reconstruct_rational(Call& c, const zr_blackbox* bb, const zr_recon_params* prm, zr_result* res) {
-  const int nv = prm->nv;
-  const uint64_t p = c.M.p;
-  std::vector<uint64_t> z(nv), y(nv + 1), cs;
-  draw_rest(prm->seed, nv, p, z.data());
-  DPoly N, D;
-  N.nv = D.nv = nv;
-  N.T = bb->TN;
-  D.T = bb->TD;
-  zr_status r = upload(c, N.exps, bb->N_exps, (size_t)bb->TN * nv);
-  if (!r) r = upload(c, N.coef, bb->N_coef, 8 * (size_t)bb->TN);
-  if (!r) r = upload(c, D.exps, bb->D_exps, (size_t)bb->TD * nv);
-  if (!r) r = upload(c, D.coef, bb->D_coef, 8 * (size_t)bb->TD);
-  if (r) return r;
-  DBuf d_pts, d_vals, d_y, d_cs, d_z, scratch, persist, fv, one;
-  if ((r = upload(c, d_z, z.data(), 8 * (size_t)nv))) return r;
-  DPoly curN, curD, nextN, nextD;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, c.st);
-  int steps = 0, redraws = 0;
-  // step 0: Thiele in x_0, then Newton through the dN+1 / dD+1 first samples
-  {
-    const int dN = prm->degN[0], dD = prm->degD[0];
-    const int Sf = 2 * std::max(dN, dD) + 2;
-    cs.assign(Sf, 0);
-    const uint64_t unit = 1;
-    if ((r = upload(c, one, &unit, 8))) return r;
-    for (int attempt = 0;; attempt++) {
-      draw_step(prm->seed, 0, attempt, false, 0, Sf, p, y.data(), cs.data());
-      std::vector<uint64_t> pts = step0_points(nv, Sf, cs.data(), z.data());
-      if ((r = upload(c, d_pts, pts.data(), pts.size() * 8))) return r;
-      if ((r = upload(c, d_cs, cs.data(), cs.size() * 8))) return r;
-      cudaError_t e = d_vals.ensure(8 * (size_t)Sf * 4 + 8 * (size_t)(dN + dD + 2));
-      if (e != cudaSuccess) return c.cuda(e, "values");
-      uint64_t* nvls = d_vals.as<uint64_t>();
-      uint64_t* dvls = nvls + Sf;
-      uint64_t* pre = dvls + Sf;
-      uint64_t* f = pre + Sf;
-      uint64_t* nval = f + Sf;
-      uint64_t* dval = nval + (dN + 1);
-      zr_poly nv_ = N.view(), dv_ = D.view();
-      launch_eval_points(&nv_, Sf, d_pts.as<uint64_t>(), c.M, nvls, c.st);
-      launch_eval_points(&dv_, Sf, d_pts.as<uint64_t>(), c.M, dvls, c.st);
-      launch_ratio(1, Sf, nvls, dvls, 1, c.M, pre, f, 1, c.ctx->d_status_call, c.st);
-      r = c.sync_status();
+zr_status Recon::prepare(std::vector<BatchItem>& items, uint32_t* d_status, int64_t* d_counts) {
+  if (phase_ != RUN) return err_;
+  const uint64_t p = M_.p;
+  const int k = k_;
+  if (!rational_) {
+    const int S = degN_[k] + 1;
+    cs_.assign(S, 0);
+    draw_step(seed_, k, attempt_, true, z_[k], S, p, y_.data(), cs_.data());
+    zr_status r = upload(d_y_, y_.data(), 8 * (size_t)k);
+    if (!r) r = upload(d_cs_, cs_.data(), 8 * (size_t)S);
+    if (r) return fail(r);
+    const int64_t T = curN_.T;
+    cudaError_t e = d_b_.ensure(8 * (size_t)S * (T > 0 ? T : 1));
+    if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "probes"));
+    if (T > 0) {
+      zr_poly fv = fN_.view();
+      r = probes_impl(ctx_, &fv, k, d_y_.as<uint64_t>(), S, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), T, offset_,
+                      d_b_.as<uint64_t>(), T, d_status, st_);
+      if (r) return fail(r);
+    }
+    r = step_entry(curN_, S, d_b_.as<uint64_t>(), T > 0 ? T : 1, nextN_, d_status, d_counts, items);
+    return r ? fail(r) : ZR_OK;
+  }
+  // rational: probes of N and D, their ratio, the per-probe Thiele and the
+  // balancing, checked before the two steps join the batch
+  const int dN = degN_[k], dD = degD_[k];
+  const int Sf = 2 * std::max(dN, dD) + 2, SN = dN + 1, SD = dD + 1;
+  for (;; attempt_++) {
+    cs_.assign(Sf, 0);
+    draw_step(seed_, k, attempt_, true, z_[k], Sf, p, y_.data(), cs_.data());
+    zr_status r = upload(d_y_, y_.data(), 8 * (size_t)k);
+    if (!r) r = upload(d_cs_, cs_.data(), 8 * (size_t)Sf);
+    if (r) return fail(r);
+    const int64_t TN = curN_.T, TD = curD_.T, Tmax = std::max(TN, TD);
+    if (Tmax == 0) break;
+    // f = N/D at (y^(i+off), c_s, z)
+    cudaError_t e = fv_.ensure(8 * (size_t)Sf * Tmax * 4);
+    if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "rational probes"));
+    uint64_t* nvls = fv_.as<uint64_t>();
+    uint64_t* dvls = nvls + (size_t)Sf * Tmax;
+    uint64_t* pre = dvls + (size_t)Sf * Tmax;
+    uint64_t* f = pre + (size_t)Sf * Tmax;
+    zr_poly nv_p = fN_.view(), dv_p = fD_.view();
+    r = probes_impl(ctx_, &nv_p, k, d_y_.as<uint64_t>(), Sf, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), Tmax, offset_,
+                    nvls, Tmax, ctx_->d_status_call, st_);
+    if (!r)
+      r = probes_impl(ctx_, &dv_p, k, d_y_.as<uint64_t>(), Sf, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), Tmax,
+                      offset_, dvls, Tmax, ctx_->d_status_call, st_);
+    if (r) return fail(r);
+    launch_ratio(Tmax, Sf, nvls, dvls, Tmax, M_, pre, f, Tmax, ctx_->d_status_call, st_);
+    r = sync_status();
+    if (!r) {
+      // D' at the probes, Thiele per probe, balancing
+      const size_t w_dprev = (size_t)Tmax, w_bN = (size_t)SN * (TN ? TN : 1), w_bD = (size_t)SD * (TD ? TD : 1);
+      const size_t w_th = thiele_scratch_words(Tmax, Sf);
+      e = persist_.ensure(8 * (w_dprev + w_bN + w_bD + w_th) + 256);
+      if (e == cudaSuccess) e = ones_.ensure(8 * (size_t)nv_);
+      if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "balanced buffers"));
+      {
+        const std::vector<uint64_t> h(nv_, 1);
+        e = cudaMemcpyAsync(ones_.p, h.data(), 8 * (size_t)nv_, cudaMemcpyHostToDevice, st_);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
+        if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "balanced buffers"));
+      }
+      uint64_t* dprev = persist_.as<uint64_t>();
+      uint64_t* bN = dprev + w_dprev;
+      uint64_t* bD = bN + w_bN;
+      uint64_t* th = bD + w_bD;
+      zr_poly dsk = curD_.view();
+      if (TD > 0)
+        r = probes_impl(ctx_, &dsk, k, d_y_.as<uint64_t>(), 1, ones_.as<uint64_t>(), ones_.as<uint64_t>(), Tmax,
+                        offset_, dprev, Tmax, ctx_->d_status_call, st_);
+      else
+        cudaMemsetAsync(dprev, 0, 8 * Tmax, st_);
+      if (r) return fail(r);
+      launch_thiele_balance(Tmax, Sf, d_cs_.as<uint64_t>(), f, Tmax, dprev, dN, dD, TN, TD, th, M_, bN, TN ? TN : 1, bD,
+                            TD ? TD : 1, ctx_->d_status_call, st_);
+      r = sync_status();
       if (!r) {
-        e = persist.ensure(8 * thiele_scratch_words(1, Sf) + 256);
-        if (e != cudaSuccess) return c.cuda(e, "thiele scratch");
-        launch_thiele_balance(1, Sf, d_cs.as<uint64_t>(), f, 1, one.as<uint64_t>(), dN, dD, 1, 1,
-                              persist.as<uint64_t>(), c.M, nval, 1, dval, 1, c.ctx->d_status_call, c.st);
-        r = c.sync_status();
+        r = step_entry(curN_, SN, bN, TN ? TN : 1, nextN_, d_status, d_counts, items);
+        if (!r) r = step_entry(curD_, SD, bD, TD ? TD : 1, nextD_, d_status, d_counts + 1, items);
+        return r ? fail(r) : ZR_OK;
       }
-      if (retryable(r) && r != ZR_ERR_SINGULAR && attempt + 1 < kMaxAttempts) {
-        redraws++;
-        continue;
-      }
-      if (r) return r;
-      std::vector<uint64_t> cn, cd;
-      if ((r = newton_coeffs(c, dN + 1, d_cs.as<uint64_t>(), nval, cn, scratch))) return r;
-      if ((r = newton_coeffs(c, dD + 1, d_cs.as<uint64_t>(), dval, cd, scratch))) return r;
-      if ((r = skeleton_from_coeffs(c, nv, cn, dN, curN))) return r;
-      if ((r = skeleton_from_coeffs(c, nv, cd, dD, curD))) return r;
-      break;
     }
-  }
-  for (int k = 1; k < nv; k++) {
-    const int dN = prm->degN[k], dD = prm->degD[k];
-    const int Sf = 2 * std::max(dN, dD) + 2;
-    cs.assign(Sf, 0);
-    for (int attempt = 0;; attempt++) {
-      draw_step(prm->seed, k, attempt, true, z[k], Sf, p, y.data(), cs.data());
-      if ((r = upload(c, d_y, y.data(), 8 * (size_t)k))) return r;
-      if ((r = upload(c, d_cs, cs.data(), 8 * (size_t)Sf))) return r;
-      const int64_t Tmax = std::max(curN.T, curD.T);
-      uint64_t* f = nullptr;
-      r = Tmax > 0 ? rational_probes(c, N, D, k, d_y.as<uint64_t>(), Sf, d_cs.as<uint64_t>(), d_z.as<uint64_t>(), Tmax,
-                                     prm->offset, fv, &f)
-                   : ZR_OK;
-      if (!r)
-        r = balanced_step_dev(c, curN, curD, k, d_y.as<uint64_t>(), dN, dD, d_cs.as<uint64_t>(), f, Tmax, prm->offset,
-                              nextN, nextD, persist);
-      steps++;
-      if (retryable(r) && attempt + 1 < kMaxAttempts) {
-        redraws++;
-        continue;
-      }
-      break;
+    steps_++;
+    if (retryable(r) && attempt_ + 1 < kMaxAttempts) {
+      redraws_++;
+      continue;
     }
-    if (r) return r;
-    std::swap(curN.exps.p, nextN.exps.p);
-    std::swap(curN.exps.n, nextN.exps.n);
-    std::swap(curN.coef.p, nextN.coef.p);
-    std::swap(curN.coef.n, nextN.coef.n);
-    curN.T = nextN.T;
-    std::swap(curD.exps.p, nextD.exps.p);
-    std::swap(curD.exps.n, nextD.exps.n);
-    std::swap(curD.coef.p, nextD.coef.p);
-    std::swap(curD.coef.n, nextD.coef.n);
-    curD.T = nextD.T;
+    return fail(r);
   }
-  // normalise on the lexicographically smallest denominator term
-  if (curD.T == 0) return c.fail(ZR_ERR_SINGULAR, "empty denominator");
-  std::vector<uint8_t> dex((size_t)curD.T * nv);
-  cudaError_t e = cudaMemcpyAsync(dex.data(), curD.exps.p, dex.size(), cudaMemcpyDeviceToHost, c.st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
-  if (e != cudaSuccess) return c.cuda(e, "denominator exponents");
-  int64_t best = 0;
-  for (int64_t j = 1; j < curD.T; j++)
-    if (memcmp(&dex[(size_t)j * nv], &dex[(size_t)best * nv], nv) < 0) best = j;
-  if ((e = scratch.ensure(64)) != cudaSuccess) return c.cuda(e, "normalise");
-  launch_normalise(curN.T, curN.coef.as<uint64_t>(), curD.T, curD.coef.as<uint64_t>(), curD.coef.as<uint64_t>() + best,
-                   scratch.as<uint64_t>(), c.M, c.ctx->d_status_call, c.st);
-  // the pivot itself is scaled last by the second launch only after the
-  // inverse was taken, so it becomes 1
-  if ((r = c.sync_status())) return r;
-  cudaEventRecord(e1, c.st);
-  cudaEventSynchronize(e1);
-  float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  res->steps = steps;
-  res->redraws = redraws;
-  res->device_ms = ms;
-  r = download_poly(c, curN, &res->TN, &res->N_exps, &res->N_coef);
-  if (!r) r = download_poly(c, curD, &res->TD, &res->D_exps, &res->D_coef);
+  // empty skeletons: nothing to run
+  cudaMemsetAsync(d_counts, 0, 16, st_);
+  return ZR_OK;
+}
+
+zr_status Recon::finish(uint32_t flags, const int64_t* counts) {
+  if (phase_ != RUN) return err_;
+  steps_++;
+  const zr_status st = status_from_flags(ctx_, flags);
+  if (st) {
+    if (retryable(st) && attempt_ + 1 < kMaxAttempts) {
+      attempt_++;
+      redraws_++;
+      return ZR_OK;
+    }
+    return fail(st);
+  }
+  nextN_.T = counts[0];
+  curN_.swap(nextN_);
+  if (rational_) {
+    nextD_.T = counts[1];
+    curD_.swap(nextD_);
+  }
+  k_++;
+  attempt_ = 0;
+  if (k_ >= nv_) return finalize();
+  return ZR_OK;
+}
+
+zr_status Recon::finalize() {
+  zr_result* res = (zr_result*)calloc(1, sizeof(zr_result));
+  if (!res) return fail(set_err(ctx_, ZR_ERR_OOM, "result allocation"));
+  res->nv = nv_;
+  res->rational = rational_ ? 1 : 0;
+  res->steps = steps_;
+  res->redraws = redraws_;
+  zr_status r = ZR_OK;
+  if (rational_) {
+    // normalise on the lexicographically smallest denominator term
+    if (curD_.T == 0) r = set_err(ctx_, ZR_ERR_SINGULAR, "empty denominator");
+    std::vector<uint8_t> dex;
+    if (!r) {
+      dex.resize((size_t)curD_.T * nv_);
+      cudaError_t e = cudaMemcpyAsync(dex.data(), curD_.exps.p, dex.size(), cudaMemcpyDeviceToHost, st_);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
+      if (e == cudaSuccess) e = scratch_.ensure(64);
+      if (e != cudaSuccess) r = cuda_err(ctx_, e, "normalise");
+    }
+    if (!r) {
+      int64_t best = 0;
+      for (int64_t j = 1; j < curD_.T; j++)
+        if (memcmp(&dex[(size_t)j * nv_], &dex[(size_t)best * nv_], nv_) < 0) best = j;
+      launch_normalise(curN_.T, curN_.coef.as<uint64_t>(), curD_.T, curD_.coef.as<uint64_t>(),
+                       curD_.coef.as<uint64_t>() + best, scratch_.as<uint64_t>(), M_, ctx_->d_status_call, st_);
+      r = sync_status();
+    }
+    if (!r) r = download(curD_, &res->TD, &res->D_exps, &res->D_coef);
+  }
+  if (!r) r = download(curN_, &res->TN, &res->N_exps, &res->N_coef);
+  if (r) {
+    zr_result_free(res);
+    return fail(r);
+  }
+  result_ = res;
+  phase_ = DONE;
+  return ZR_OK;
+}
+
+zr_result* Recon::take_result() {
+  zr_result* r = result_;
+  result_ = nullptr;
   return r;
 }
 
-}  // namespace
+zr_status check_recon_args(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_params* prm) {
+  if (!bb || !prm || prm->nv < 1 || prm->nv > kMaxVars || bb->nv != prm->nv || (prm->offset != 0 && prm->offset != 1) ||
+      !prm->degN || bb->TN < 0 || (bb->TN > 0 && (!bb->N_exps || !bb->N_coef)))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: bad black box or parameters");
+  const bool rational = bb->kind == ZR_BB_RATIONAL;
+  if (bb->kind != ZR_BB_POLY && !rational) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: unknown kind");
+  if (rational && (!prm->degD || bb->TD <= 0 || !bb->D_exps || !bb->D_coef))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: rational black box needs a denominator");
+  for (int m = 0; m < prm->nv; m++) {
+    const int dn = prm->degN[m], dd = rational ? prm->degD[m] : 0;
+    if (dn < 0 || dd < 0 || dn + 1 > 64 || (rational && 2 * std::max(dn, dd) + 2 > 64))
+      return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: degree bounds out of range");
+  }
+  return ZR_OK;
+}
+
+}  // namespace zr
+
+using namespace zr;
 
 extern "C" void zr_result_free(zr_result* r) {
   if (!r) return;
@@ -546,27 +499,43 @@ extern "C" zr_status zr_reconstruct(zr_ctx* ctx, const zr_blackbox* bb, const zr
   if (!ctx) return ZR_ERR_INVALID_ARG;
   if (!out) return set_err(ctx, ZR_ERR_INVALID_ARG, "null result pointer");
   *out = nullptr;
-  if (!bb || !prm || prm->nv < 1 || prm->nv > kMaxVars || bb->nv != prm->nv || (prm->offset != 0 && prm->offset != 1) ||
-      !prm->degN || bb->TN < 0 || (bb->TN > 0 && (!bb->N_exps || !bb->N_coef)))
-    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: bad black box or parameters");
-  const bool rational = bb->kind == ZR_BB_RATIONAL;
-  if (bb->kind != ZR_BB_POLY && !rational) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: unknown kind");
-  if (rational && (!prm->degD || bb->TD <= 0 || !bb->D_exps || !bb->D_coef))
-    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: rational black box needs a denominator");
-  for (int m = 0; m < prm->nv; m++) {
-    const int dn = prm->degN[m], dd = rational ? prm->degD[m] : 0;
-    if (dn < 0 || dd < 0 || dn + 1 > 64 || (rational && 2 * std::max(dn, dd) + 2 > 64))
-      return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: degree bounds out of range");
+  zr_status r = check_recon_args(ctx, bb, prm);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  Recon R(ctx, st, *bb, *prm);
+  r = R.start();
+  std::vector<BatchItem> items;
+  while (!r && !R.done()) {
+    items.clear();
+    cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+    r = R.prepare(items, ctx->d_status_call, ctx->d_count);
+    if (r) break;
+    r = run_batch(ctx, items.data(), (int)items.size(), ctx->d_status_call, st);
+    if (r) break;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_status + 1, ctx->d_status_call, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_count, ctx->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      r = cuda_err(ctx, e, "zr_reconstruct");
+      break;
+    }
+    r = R.finish(ctx->h_status[1], ctx->h_count);
   }
-  Call c{ctx, (cudaStream_t)stream, ctx->M};
-  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), c.st);
-  zr_result* res = make_result(prm->nv, rational);
-  if (!res) return set_err(ctx, ZR_ERR_OOM, "result allocation");
-  zr_status r = rational ? reconstruct_rational(c, bb, prm, res) : reconstruct_poly(c, bb, prm, res);
-  if (r) {
-    zr_result_free(res);
-    return r;
-  }
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  if (r) return r;
+  zr_result* res = R.take_result();
+  if (!res) return set_err(ctx, ZR_ERR_CUDA, "reconstruction ended without a result");
+  res->device_ms = ms;
   *out = res;
   return ZR_OK;
 }
@@ -583,32 +552,80 @@ extern "C" zr_status zr_zippel_step_balanced(zr_ctx* ctx, const zr_poly* skelN, 
       skelN->T < 0 || skelD->T < 0 || ldf < std::max(skelN->T, skelD->T) || !samples || !y ||
       (skelD->T > 0 && !skelD->coef))
     return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step_balanced: arguments out of range");
-  Call c{ctx, (cudaStream_t)stream, ctx->M};
-  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), c.st);
-  // wrap the caller's device arrays (no ownership)
-  DPoly sN, sD, oN, oD;
-  sN.nv = sD.nv = skelN->nv;
-  sN.T = skelN->T;
-  sD.T = skelD->T;
-  sN.exps.p = (void*)skelN->exps;
-  sD.exps.p = (void*)skelD->exps;
-  sD.coef.p = (void*)skelD->coef;
-  DBuf persist;
-  zr_status r = balanced_step_dev(c, sN, sD, newvar, y, dN, dD, samples, fvals, ldf, offset, oN, oD, persist);
-  sN.exps.p = sD.exps.p = sD.coef.p = nullptr;   // not owned
-  if (outN_count) *outN_count = oN.T;
-  if (outD_count) *outD_count = oD.T;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nv = skelN->nv;
+  const int64_t TN = skelN->T, TD = skelD->T, Tmax = std::max(TN, TD);
+  const int Sf = 2 * std::max(dN, dD) + 2, SN = dN + 1, SD = dD + 1;
+  if (outN_count) *outN_count = 0;
+  if (outD_count) *outD_count = 0;
+  if (Tmax == 0) return ZR_OK;
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  DBuf persist, ones;
+  const size_t w_dprev = (size_t)Tmax, w_bN = (size_t)SN * (TN ? TN : 1), w_bD = (size_t)SD * (TD ? TD : 1);
+  const size_t w_th = thiele_scratch_words(Tmax, Sf);
+  cudaError_t e = persist.ensure(8 * (w_dprev + w_bN + w_bD + w_th) + 256);
+  if (e == cudaSuccess) e = ones.ensure(8 * (size_t)nv);
+  if (e == cudaSuccess) {
+    const std::vector<uint64_t> h(nv, 1);
+    e = cudaMemcpyAsync(ones.p, h.data(), 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_step_balanced: buffers");
+  uint64_t* dprev = persist.as<uint64_t>();
+  uint64_t* bN = dprev + w_dprev;
+  uint64_t* bD = bN + w_bN;
+  uint64_t* th = bD + w_bD;
+  zr_status r = ZR_OK;
+  if (TD > 0) {
+    zr_poly dsk = *skelD;
+    r = probes_impl(ctx, &dsk, newvar, y, 1, ones.as<uint64_t>(), ones.as<uint64_t>(), Tmax, offset, dprev, Tmax,
+                    ctx->d_status_call, st);
+  } else {
+    cudaMemsetAsync(dprev, 0, 8 * Tmax, st);
+  }
   if (r) return r;
-  if (oN.T > outN_cap || oD.T > outD_cap) return set_err(ctx, ZR_ERR_CAPACITY, "output skeleton larger than capacity");
-  cudaError_t e = cudaSuccess;
-  if (oN.T > 0) {
-    e = cudaMemcpyAsync(outN_exps, oN.exps.p, (size_t)oN.T * skelN->nv, cudaMemcpyDeviceToDevice, c.st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(outN_coef, oN.coef.p, 8 * (size_t)oN.T, cudaMemcpyDeviceToDevice, c.st);
+  launch_thiele_balance(Tmax, Sf, samples, fvals, ldf, dprev, dN, dD, TN, TD, th, ctx->M, bN, TN ? TN : 1, bD,
+                        TD ? TD : 1, ctx->d_status_call, st);
+  // the numerator and denominator steps share one batch of launches
+  BatchItem items[2];
+  int n = 0;
+  const zr_poly* sk[2] = {skelN, skelD};
+  const int Ss[2] = {SN, SD};
+  uint64_t* bs[2] = {bN, bD};
+  uint8_t* oe[2] = {outN_exps, outD_exps};
+  uint64_t* oc[2] = {outN_coef, outD_coef};
+  const int64_t caps[2] = {outN_cap, outD_cap};
+  cudaMemsetAsync(ctx->d_count, 0, 2 * sizeof(int64_t), st);
+  for (int t = 0; t < 2; t++) {
+    if (sk[t]->T == 0) continue;
+    BatchItem& it = items[n++];
+    it.mode = 0;
+    it.T = sk[t]->T;
+    it.S = Ss[t];
+    it.k = newvar;
+    it.nv = nv;
+    it.offset = offset;
+    it.exps = sk[t]->exps;
+    it.y = y;
+    it.xs = samples;
+    it.b = bs[t];
+    it.ldb = sk[t]->T;
+    it.out_exps = oe[t];
+    it.out_coef = oc[t];
+    it.out_cap = caps[t];
+    it.out_count = ctx->d_count + t;
   }
-  if (e == cudaSuccess && oD.T > 0) {
-    e = cudaMemcpyAsync(outD_exps, oD.exps.p, (size_t)oD.T * skelD->nv, cudaMemcpyDeviceToDevice, c.st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(outD_coef, oD.coef.p, 8 * (size_t)oD.T, cudaMemcpyDeviceToDevice, c.st);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
-  return cuda_err(ctx, e, "zr_zippel_step_balanced");
+  if ((r = run_batch(ctx, items, n, ctx->d_status_call, st))) return r;
+  e = cudaMemcpyAsync(ctx->h_status + 1, ctx->d_status_call, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_count, ctx->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_step_balanced");
+  if (outN_count) *outN_count = ctx->h_count[0];
+  if (outD_count) *outD_count = ctx->h_count[1];
+  r = status_from_flags(ctx, ctx->h_status[1]);
+  if (r) return r;
+  if (ctx->h_count[0] > outN_cap || ctx->h_count[1] > outD_cap)
+    return set_err(ctx, ZR_ERR_CAPACITY, "output skeleton larger than capacity");
+  return ZR_OK;
 }

@@ -1,0 +1,113 @@
+// zr_recon.h -- one reconstruction as a state machine over its steps, so
+// that a single request (zr_reconstruct) and many requests at once (the
+// serving loop) run the same code: start() does the dense step in x_0,
+// prepare() enqueues the probe work of the next Zippel step and contributes
+// that step's entries to a shared batch, finish() consumes the batch's
+// status and counts for those entries and advances (or redraws).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "zr_internal.h"
+
+namespace zr {
+
+// Device memory owned by one request.
+struct DBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n && p) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 8);
+    if (e == cudaSuccess) n = bytes > 0 ? bytes : 8;
+    return e;
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+struct DPoly {
+  int nv = 0;
+  int64_t T = 0;
+  DBuf exps, coef;
+  zr_poly view() const { return zr_poly{nv, T, exps.as<uint8_t>(), coef.as<uint64_t>()}; }
+  void swap(DPoly& o) {
+    std::swap(T, o.T);
+    std::swap(nv, o.nv);
+    std::swap(exps.p, o.exps.p);
+    std::swap(exps.n, o.exps.n);
+    std::swap(coef.p, o.coef.p);
+    std::swap(coef.n, o.coef.n);
+  }
+  size_t bytes() const { return exps.n + coef.n; }
+};
+
+class Recon {
+ public:
+  // The black box arrays are copied.
+  Recon(zr_ctx* ctx, cudaStream_t st, const zr_blackbox& bb, const zr_recon_params& prm);
+  zr_status start();                  // uploads, dense step in x_0
+  bool done() const { return phase_ == DONE; }
+  bool failed() const { return phase_ == FAILED; }
+  zr_status error() const { return err_; }
+  // Enqueues the probes of the next step and appends its batch entries (one
+  // for a polynomial, two for N and D) with the given status word and count
+  // slots (two int64).  Synchronises when the rational path must check the
+  // univariate reconstruction before the step.
+  zr_status prepare(std::vector<BatchItem>& items, uint32_t* d_status, int64_t* d_counts);
+  // After the batch: this request's status flags and its count slots.
+  zr_status finish(uint32_t flags, const int64_t* counts);
+  zr_result* take_result();           // ownership passes to the caller
+  size_t device_bytes() const;
+  static size_t estimate_bytes(const zr_blackbox& bb, const zr_recon_params& prm);
+  int steps() const { return steps_; }
+  int redraws() const { return redraws_; }
+
+ private:
+  enum Phase { NEW, RUN, DONE, FAILED };
+  zr_status fail(zr_status s);
+  zr_status sync_status();
+  zr_status upload(DBuf& b, const void* host, size_t bytes);
+  zr_status step0_poly();
+  zr_status step0_rational();
+  zr_status finalize();
+  zr_status newton_coeffs(int S, const uint64_t* d_cs, const uint64_t* d_vals, std::vector<uint64_t>& coef);
+  zr_status skeleton_from_coeffs(const std::vector<uint64_t>& coef, int deg, DPoly& out);
+  zr_status download(const DPoly& p, int64_t* T, uint8_t** exps, uint64_t** coef);
+  zr_status step_entry(const DPoly& skel, int S, const uint64_t* b, int64_t ldb, DPoly& out, uint32_t* d_status,
+                       int64_t* d_count, std::vector<BatchItem>& items);
+
+  zr_ctx* ctx_;
+  cudaStream_t st_;
+  Mod M_;
+  // request
+  int nv_;
+  bool rational_;
+  std::vector<uint8_t> Ne_, De_;
+  std::vector<uint64_t> Nc_, Dc_;
+  std::vector<int32_t> degN_, degD_;
+  uint64_t seed_;
+  int offset_;
+  // state
+  Phase phase_ = NEW;
+  zr_status err_ = ZR_OK;
+  std::vector<uint64_t> z_, y_, cs_;
+  int k_ = 1, attempt_ = 0, steps_ = 0, redraws_ = 0;
+  DPoly fN_, fD_, curN_, curD_, nextN_, nextD_;
+  DBuf d_y_, d_cs_, d_z_, d_b_, d_pts_, d_vals_, scratch_, persist_, fv_, one_, ones_;
+  zr_result* result_ = nullptr;
+};
+
+}  // namespace zr

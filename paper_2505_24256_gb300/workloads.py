@@ -228,10 +228,10 @@ def rational_simplex_workload(seed: int, nv: int, total_deg: int, TN: int, TD: i
     iD = np.sort(choose_distinct(Stream(seed, 2), mons.shape[0], TD))
     Ncoef = Stream(seed, 3).residues(TN, p)
     Dcoef = Stream(seed, 4).residues(TD, p)
-    Dexps = mons[iD]
+    Nexps, Dexps = _cancel_monomial_content(mons[iN], mons[iD])
     Dcoef[0] = 1          # rows are in lexicographic order: row 0 is the smallest
     deg = np.full(nv, total_deg, dtype=np.int32)
-    return RationalWorkload(name or f"rat_n{nv}_d{total_deg}_N{TN}_D{TD}", p, nv, mons[iN], Ncoef, Dexps, Dcoef,
+    return RationalWorkload(name or f"rat_n{nv}_d{total_deg}_N{TN}_D{TD}", p, nv, Nexps, Ncoef, Dexps, Dcoef,
                             deg, deg.copy(), seed + 7)
 
 
@@ -271,3 +271,41 @@ def serve_requests(n: int = 4096, seed: int = 1005, p: int = P63, tmax: int = 1 
         T = max(1, min(T, (21 ** nv) // 2))
         out.append(dict(id=r, rational=rational, nv=nv, T=T, seed=seed * 100000 + r))
     return out
+
+
+def _lex_sorted(e: np.ndarray) -> np.ndarray:
+    if e.shape[0] == 0:
+        return e
+    order = np.lexsort(tuple(e[:, c] for c in range(e.shape[1] - 1, -1, -1)))
+    return e[order]
+
+
+def _cancel_monomial_content(Ne: np.ndarray, De: np.ndarray):
+    """Divides N and D by their common monomial factor, so that the hidden N/D
+    is in lowest terms (a random sparse pair shares no other factor with
+    overwhelming probability); row order is unchanged."""
+    m = np.minimum(Ne.min(axis=0), De.min(axis=0)).astype(np.uint8)
+    return Ne - m, De - m
+
+
+def serve_blackbox(req: dict, p: int = P63, maxexp: int = 20):
+    """The hidden function of one serving request: exponents uniform in
+    [0, maxexp] per variable (distinct, lexicographic rows), coefficients
+    uniform mod p, degree bound maxexp in every variable.  A rational request
+    splits T 60/40 between N and D, and D's lexicographically smallest term
+    has coefficient 1."""
+    nv, T, seed = req["nv"], req["T"], req["seed"]
+    deg = np.full(nv, maxexp, dtype=np.int32)
+    if not req["rational"]:
+        exps = _lex_sorted(distinct_monomials_box(Stream(seed, 1), T, nv, maxexp))
+        return PolyWorkload(f"serve{req['id']}_poly_n{nv}_T{T}", p, nv, exps, Stream(seed, 2).residues(T, p), deg,
+                            seed + 7)
+    TN = max(1, (T * 3 + 4) // 5)
+    TD = max(1, T - TN)
+    Ne = _lex_sorted(distinct_monomials_box(Stream(seed, 1), TN, nv, maxexp))
+    De = _lex_sorted(distinct_monomials_box(Stream(seed, 2), TD, nv, maxexp))
+    Ne, De = _cancel_monomial_content(Ne, De)
+    Nc = Stream(seed, 3).residues(TN, p)
+    Dc = Stream(seed, 4).residues(TD, p)
+    Dc[0] = 1
+    return RationalWorkload(f"serve{req['id']}_rat_n{nv}_N{TN}_D{TD}", p, nv, Ne, Nc, De, Dc, deg, deg.copy(), seed + 7)

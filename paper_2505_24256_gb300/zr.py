@@ -64,6 +64,18 @@ class zr_result(ctypes.Structure):
                 ("steps", ctypes.c_int32), ("redraws", ctypes.c_int32), ("device_ms", ctypes.c_double)]
 
 
+class zr_request(ctypes.Structure):
+    _fields_ = [("bb", zr_blackbox), ("prm", zr_recon_params)]
+
+
+class zr_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("terms", ctypes.c_int64), ("ticks", ctypes.c_int64), ("batch_entries", ctypes.c_int64),
+                ("max_active", ctypes.c_int32), ("pad", ctypes.c_int32), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("terms_per_s", ctypes.c_double)]
+
+
 _V, _I32, _I64, _U64, _P = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
 _ST = ctypes.c_int
 
@@ -96,6 +108,12 @@ SIGNATURES = {
                                       _P, _P, _I64, _P, _V]),
     "zr_reconstruct": (_ST, [_V, _P, _P, ctypes.POINTER(ctypes.POINTER(zr_result)), _V]),
     "zr_result_free": (None, [ctypes.POINTER(zr_result)]),
+    "zr_serve_create": (_ST, [_V, ctypes.c_size_t, _I32, ctypes.POINTER(_V)]),
+    "zr_serve_submit": (_ST, [_V, _P, ctypes.POINTER(_U64)]),
+    "zr_serve_poll": (_ST, [_V, _U64, ctypes.POINTER(ctypes.POINTER(zr_result))]),
+    "zr_serve_wait": (_ST, [_V, _U64, _I64, ctypes.POINTER(ctypes.POINTER(zr_result))]),
+    "zr_serve_stats_get": (_ST, [_V, ctypes.POINTER(zr_serve_stats)]),
+    "zr_serve_destroy": (None, [_V]),
 }
 
 _lib = None
@@ -294,21 +312,7 @@ class Context:
         res = ctypes.POINTER(zr_result)()
         st = self.L.zr_reconstruct(self._h, ctypes.byref(bb), ctypes.byref(prm), ctypes.byref(res), _stream(stream))
         self.check(st, "zr_reconstruct")
-        try:
-            r = res.contents
-            Ne = np.ctypeslib.as_array(r.N_exps, shape=(r.TN * nv,)).reshape(r.TN, nv).copy() if r.TN else \
-                np.zeros((0, nv), np.uint8)
-            Nc = np.ctypeslib.as_array(r.N_coef, shape=(r.TN,)).copy() if r.TN else np.zeros(0, np.uint64)
-            D = None
-            if r.rational:
-                De = np.ctypeslib.as_array(r.D_exps, shape=(r.TD * nv,)).reshape(r.TD, nv).copy() if r.TD else \
-                    np.zeros((0, nv), np.uint8)
-                Dc = np.ctypeslib.as_array(r.D_coef, shape=(r.TD,)).copy() if r.TD else np.zeros(0, np.uint64)
-                D = (De, Dc)
-            info = dict(steps=r.steps, redraws=r.redraws, device_ms=r.device_ms)
-            return (Ne, Nc), D, info
-        finally:
-            self.L.zr_result_free(res)
+        return _take_result(self.L, res)
 
 
 def launch_count() -> int:
@@ -322,3 +326,95 @@ def newton_batched_noalloc(prime, nterms, npts, x, vals, ld, coef, stream=None) 
     device memory.  Returns the zr status code (0 on success)."""
     return int(load().zr_newton_batched_noalloc(prime, nterms, npts, _ptr(x), _ptr(vals), ld, _ptr(coef),
                                                  _stream(stream)))
+
+
+def _take_result(L, res):
+    """Copies a zr_result into numpy arrays and frees it."""
+    try:
+        r = res.contents
+        nv = r.nv
+        Ne = np.ctypeslib.as_array(r.N_exps, shape=(r.TN * nv,)).reshape(r.TN, nv).copy() if r.TN else \
+            np.zeros((0, nv), np.uint8)
+        Nc = np.ctypeslib.as_array(r.N_coef, shape=(r.TN,)).copy() if r.TN else np.zeros(0, np.uint64)
+        D = None
+        if r.rational:
+            De = np.ctypeslib.as_array(r.D_exps, shape=(r.TD * nv,)).reshape(r.TD, nv).copy() if r.TD else \
+                np.zeros((0, nv), np.uint8)
+            Dc = np.ctypeslib.as_array(r.D_coef, shape=(r.TD,)).copy() if r.TD else np.zeros(0, np.uint64)
+            D = (De, Dc)
+        info = dict(steps=r.steps, redraws=r.redraws, device_ms=r.device_ms)
+        return (Ne, Nc), D, info
+    finally:
+        L.zr_result_free(res)
+
+
+def make_request(nv, degN, seed, N_exps, N_coef, D_exps=None, D_coef=None, degD=None, offset=0):
+    """A zr_request plus the numpy arrays it points to (keep both alive until submitted)."""
+    rational = D_exps is not None
+    keep = [np.ascontiguousarray(N_exps, dtype=np.uint8), np.ascontiguousarray(N_coef, dtype=np.uint64),
+            np.ascontiguousarray(degN, dtype=np.int32)]
+    bb = zr_blackbox(1 if rational else 0, nv, keep[0].shape[0], keep[0].ctypes.data, keep[1].ctypes.data, 0, None,
+                     None)
+    if rational:
+        keep += [np.ascontiguousarray(D_exps, dtype=np.uint8), np.ascontiguousarray(D_coef, dtype=np.uint64),
+                 np.ascontiguousarray(degD if degD is not None else degN, dtype=np.int32)]
+        bb.TD, bb.D_exps, bb.D_coef = keep[3].shape[0], keep[3].ctypes.data, keep[4].ctypes.data
+        degd_ptr = keep[5].ctypes.data
+    else:
+        degd_ptr = keep[2].ctypes.data
+    prm = zr_recon_params(nv, offset, seed, keep[2].ctypes.data, degd_ptr)
+    return zr_request(bb, prm), keep
+
+
+class Server:
+    """zr_serve_*: continuous batching of reconstructions on one context."""
+
+    def __init__(self, ctx: Context, mem_budget: int, max_slots: int):
+        self.ctx = ctx
+        self.L = ctx.L
+        h = ctypes.c_void_p()
+        st = self.L.zr_serve_create(ctx.handle, mem_budget, max_slots, ctypes.byref(h))
+        if st != OK:
+            raise ZrError(st, "zr_serve_create")
+        self._h = h
+
+    def submit(self, req) -> int:
+        t = ctypes.c_uint64()
+        st = self.L.zr_serve_submit(self._h, ctypes.byref(req), ctypes.byref(t))
+        if st != OK:
+            raise ZrError(st, "zr_serve_submit")
+        return t.value
+
+    def poll(self, ticket):
+        res = ctypes.POINTER(zr_result)()
+        st = self.L.zr_serve_poll(self._h, ticket, ctypes.byref(res))
+        if st == BUSY:
+            return None
+        if st != OK:
+            raise ZrError(st, f"request {ticket}")
+        return _take_result(self.L, res)
+
+    def wait(self, ticket, timeout_s=600.0):
+        res = ctypes.POINTER(zr_result)()
+        st = self.L.zr_serve_wait(self._h, ticket, int(timeout_s * 1e6), ctypes.byref(res))
+        if st != OK:
+            raise ZrError(st, f"request {ticket}")
+        return _take_result(self.L, res)
+
+    def stats(self) -> dict:
+        s = zr_serve_stats()
+        st = self.L.zr_serve_stats_get(self._h, ctypes.byref(s))
+        if st != OK:
+            raise ZrError(st, "zr_serve_stats_get")
+        return {f: getattr(s, f) for f, _ in zr_serve_stats._fields_ if f != "pad"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.zr_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

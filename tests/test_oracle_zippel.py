@@ -148,3 +148,22 @@ def test_reconstruct_rational_exact(orc, nv, deg, TN, TD, seed):
             continue
         f = pyref.eval_sparse(wl.Nexps, wl.Ncoef, pt) * pyref.inv(dv) % P63
         assert (pyref.eval_sparse(Ne, Nc, pt) - f * pyref.eval_sparse(De, Dc, pt)) % P63 == 0
+
+
+def test_oracle_recovers_serving_requests(orc):
+    """The serving mix's hidden functions (box exponents <= 20, rational ones
+    in lowest terms) are recovered exactly by the oracle."""
+    from paper_2505_24256_gb300 import workloads as W
+
+    reqs = W.serve_requests(12, seed=33, tmax=300)
+    reqs.append(dict(id=99, rational=True, nv=3, T=2, seed=5))    # D a single monomial
+    for r in reqs:
+        wl = W.serve_blackbox(r)
+        if isinstance(wl, W.RationalWorkload):
+            (Ne, Nc), (De, Dc) = orc.reconstruct_rational(wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef, wl.degN, wl.degD,
+                                                          seed=wl.seed)
+            assert np.array_equal(Ne, wl.Nexps) and np.array_equal(Nc, wl.Ncoef), wl.name
+            assert np.array_equal(De, wl.Dexps) and np.array_equal(Dc, wl.Dcoef), wl.name
+        else:
+            e, c = orc.reconstruct_poly(wl.exps, wl.coef, wl.deg, seed=wl.seed)
+            assert np.array_equal(e, wl.exps) and np.array_equal(c, wl.coef), wl.name
