@@ -38,22 +38,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Zippel-step skeleton terms/s and mulmod/s vs roofline; serve p50/p99 latency"
-SM_COUNT = 152
-IMAD_PER_CLK_PER_SM = 64      # 32-bit integer multiply(-add) issue rate per SM per clock
-IMAD_PER_MODMUL = 4           # 32x32->64 partial products of one 64x64-bit product
 
 
 def workload(name):
     from paper_2505_24256_gb300 import workloads as W
     return {"batched": W.batched_step_1e4, "large": W.large_step_2p20}[name]()
-
-
-def measured_peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except Exception:
-        return {}
 
 
 class Clocks:
@@ -206,6 +195,8 @@ def run_zr(args):
     if S * T * T <= 10**11:
         ctx.autotune_step(T, S, 24)
     plan = ctx.step_plan(T, S)
+    # measured ceilings of the solve's two instruction sequences (MAC, chain step)
+    peaks = ctx.measure_peaks()
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -262,18 +253,46 @@ def run_zr(args):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_s = float(te.item())
 
+    # the plain form on the same GPU: one single-right-hand-side system per
+    # launch sequence (S of them), then Newton; probes and nodes as above
+    v = torch.empty(T, dtype=torch.int64, device=dev)
+    cpl = torch.empty((S, T), dtype=torch.int64, device=dev)
+    gpl = torch.empty((S, T), dtype=torch.int64, device=dev)
+    systems = [dict(T=T, S=1, v=v, b=b[s], ldb=T, c=cpl[s], ldc=T) for s in range(S)]
+
+    def plain_step():
+        ctx.anchor_values(T, nv, ske, k, y, 0, v)
+        ctx.vandermonde_solve(systems, plain=True)
+        ctx.newton_batched(T, S, cs, cpl, T, gpl)
+
+    plain_reps = max(1, min(args.steps, 5))
+    plain_step()
+    torch.cuda.synchronize()
+    pevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(plain_reps)]
+    for i in range(plain_reps):
+        flush.zero_()
+        pevs[i][0].record(stream)
+        plain_step()
+        pevs[i][1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = sum(a.elapsed_time(bb) for a, bb in pevs) / plain_reps
+    plain_ok = np.array_equal(gpl.cpu().numpy().view(np.uint64).T.reshape(-1), wl.coef)
+
     if rank != 0:
         ctx.close()
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT * sm_max * 1e6 * IMAD_PER_CLK_PER_SM / IMAD_PER_MODMUL     # modular multiplies / s
     solve_avg_s = solve_ms / max(solve_n, 1) / 1e3
-    solve_ops = (S + 2) * T * T                                                   # a5 dots + a4 chain + a4 denominators
+    # the solve's algorithmic work per (root j, k): S multiply-accumulates of
+    # the dot products, one chain step of the synthetic division, one chain
+    # step of the denominator q_j(v_j)
+    macs, chain_steps = S * T * T, 2 * T * T
+    solve_ops = macs + chain_steps
+    t_star = macs / peaks["mac_per_s"] + chain_steps / peaks["chain_per_s"]      # measured ceiling
     achieved = solve_ops / solve_avg_s
+    peak = solve_ops / t_star
     ms_per_step = total_ms / args.steps
     W = (S + 2.5) * T * T
     line = {
@@ -285,10 +304,18 @@ def run_zr(args):
         "config": {"workload": wl.name, "T": T, "S": S, "nv": nv, "prime": wl.p,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}"},
         "mulmod_per_s": world * W * args.steps / (total_ms / 1e3),
-        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gmulmod/s",
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_solve",
-                     "peak_basis": f"{SM_COUNT} SMs x {sm_max:.0f} MHz x {IMAD_PER_CLK_PER_SM} IMAD/clk / "
-                                   f"{IMAD_PER_MODMUL} partial products per 64x64 product"},
+                     "ops": f"S*T^2 multiply-accumulates + 2*T^2 chain steps = {solve_ops:.4g} per launch",
+                     "peak_basis": "measured (zr_measure_peaks on this GPU, this run): "
+                                   f"{peaks['mac_per_s'] / 1e9:.0f} GMAC/s, {peaks['chain_per_s'] / 1e9:.0f} G chain "
+                                   "steps/s, weighted by the solve's mix"},
+        "peaks_measured": {"mac_per_s": peaks["mac_per_s"], "chain_per_s": peaks["chain_per_s"],
+                           "imad_lo_per_s": peaks["imad_lo_per_s"], "imad_hi_per_s": peaks["imad_hi_per_s"]},
+        "plain_form": {"ms_per_step": plain_ms, "terms_per_s": world * T / (plain_ms / 1e3),
+                       "batched_speedup": plain_ms / ms_per_step,
+                       "what": f"{S} single-RHS systems, one launch sequence each, + Newton",
+                       "check": "generator truth" if plain_ok else "MISMATCH"},
         "phase_ms": phases,
         "plan": {"s_tile": plan[0], "k_blocks": plan[1]},
         "probe_gen_ms": probe_ms,

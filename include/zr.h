@@ -80,6 +80,23 @@ uint64_t zr_launch_count(void);
 zr_status zr_profile_enable(zr_ctx* ctx, int32_t on);
 zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count);
 
+/* Measured ceilings (the paper has no counterpart: these are the rates the
+ * solve's throughput is reported against).  Each probe runs one instruction
+ * sequence of the solve with all operands in registers, independent
+ * accumulators per thread and every SM filled, times one launch of about
+ * 30 ms with CUDA events on `stream`, and returns operations per second:
+ *   mac_per_s      64x64-bit products added into a 160-bit accumulator
+ *                  (the dot product's multiply-accumulate, Sec. 2.2)
+ *   chain_per_s    synthetic-division steps q <- q v + m with Shoup's
+ *                  precomputed quotient (Sec. 2.1)
+ *   imad_lo_per_s, imad_hi_per_s   32-bit mad.lo / mad.hi
+ * Synchronous; uses the context workspace. */
+typedef struct zr_peaks {
+  double mac_per_s, chain_per_s, imad_lo_per_s, imad_hi_per_s;
+  int32_t sms, pad;
+} zr_peaks;
+zr_status zr_measure_peaks(zr_ctx* ctx, zr_peaks* out, void* stream);
+
 /* Autotuner of the solve's launch plan (right-hand-side tile x k-block
  * count): times the `budget` best-ranked candidate plans on synthetic data of
  * shape (T, S) and records the fastest in the context; later calls with that

@@ -452,7 +452,7 @@ extern "C" zr_status zr_newton_batched(zr_ctx* ctx, int64_t nterms, int32_t npts
   uint64_t* invd = cv.take<uint64_t>((size_t)npts * npts);
   cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
   launch_newton_table(npts, x, ctx->M, invd, ctx->d_status_call, st);
-  launch_newton(nterms, npts, x, invd, vals, ld, ctx->M, coef, st);
+  launch_newton(nterms, npts, invd, vals, ld, ctx->M, coef, st);
   return finish_sync_call(ctx, st, nullptr);
 }
 

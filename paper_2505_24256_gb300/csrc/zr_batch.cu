@@ -2,7 +2,7 @@
 //
 // Steps (or systems) of different T and S share every launch: each kernel
 // gets the device array of descriptors (BDesc) and a prefix sum over the
-// entries' work (roots, leaf chunks, tree tiles, scan blocks); a flattened
+// entries' work (roots, leaf chunks, tree tiles, 128-term blocks); a flattened
 // index is mapped back to (entry, local index) by binary search.  The solve
 // kernel is persistent and walks a device work list of (entry, root tile,
 // k-block, right-hand-side tile) items, longest first.  A batch of one is the
@@ -68,9 +68,9 @@ __global__ void k_b_anchor(const BDesc* __restrict__ Ds, const int64_t* __restri
 
 // ---- a3: product tree ---------------------------------------------------------
 
-constexpr int kTreeL1 = 10;  // levels 0..9 inside one CTA (1024 leaves)
+constexpr int kTreeL1 = 7;   // levels 0..6 inside one CTA (128 leaves, one per thread)
 
-__global__ void __launch_bounds__(512) k_b_tree_leaf(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
+__global__ void __launch_bounds__(1 << kTreeL1) k_b_tree_leaf(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
                                                      int n, Mod M) {
   __shared__ uint64_t buf[2][1 << kTreeL1];
   const int i = seg_of(pre, n, blockIdx.x);
@@ -150,66 +150,80 @@ __global__ void __launch_bounds__(kNO* kNS) k_b_tree_level(const BDesc* __restri
 
 // ---- a4/a6: finish ---------------------------------------------------------------
 
+// q_j(v_j) (times v_j for offset 1) from its k-block partials: Horner in
+// v_j^BK from the top block down, the partials loaded eight at a time.
 __device__ __forceinline__ uint64_t combine_den_d(const BDesc& D, int64_t j, uint64_t vj, const Mod& M) {
-  uint64_t den = 0, pw = 1;
   const uint64_t vBK = D.NB > 1 ? pow_mod(vj, (uint64_t)D.BK, M) : 1;
-  for (int kb = 0; kb < D.NB; kb++) {
-    den = add_mod(den, mul_mod(D.denp[(int64_t)kb * D.T + j], pw, M), M);
-    pw = mul_mod(pw, vBK, M);
+  uint64_t den = 0;
+  for (int kt = D.NB; kt > 0; kt -= 8) {
+    uint64_t x[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) x[q] = kt - 1 - q >= 0 ? D.denp[(int64_t)(kt - 1 - q) * D.T + j] : 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+      if (kt - 1 - q >= 0) den = add_mod(mul_mod(den, vBK, M), x[q], M);
   }
   if (D.offset == 1) den = mul_mod(den, vj, M);
   return den;
 }
 
-__global__ void k_b_newton_table(const BDesc* __restrict__ Ds, Mod M) {
+// W of every step entry (one block each): the values -> monomial map of Newton
+// interpolation on the entry's S samples.
+__global__ void __launch_bounds__(kNewtonThreads) k_b_newton_table(const BDesc* __restrict__ Ds, Mod M) {
+  extern __shared__ uint64_t tsm[];
   const BDesc& D = Ds[blockIdx.x];
   if (D.mode != 0 || D.T == 0) return;
-  const int S = D.S;
-  for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
-    const int l = idx / S, s = idx - l * S;
-    if (l >= 1 && s >= l) {
-      const uint64_t d = sub_mod(D.xs[s], D.xs[s - l], M);
-      if (d == 0) atomicOr(D.status, ST_DUP_SAMPLE);
-      D.invd[idx] = inv_mod(d, M);
-    }
-  }
+  newton_table_block(D.S, D.xs, D.invd, D.status, tsm, M);
 }
 
-template <int SMAX>
-__global__ void __launch_bounds__(128) k_b_finish_newton(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
-                                                         int n, Mod M) {
-  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = x < pre[n];
-  const int i = active ? seg_of(pre, n, x) : 0;
+// a4 + a6 per term: the denominator q_j(v_j) from its k-block partials, its
+// inverse (one inversion per warp), the S dot products from their k-block
+// partials, then the monomial coefficients through W.  Blocks of 128 terms
+// never straddle entries (pre counts blocks), so W sits in shared memory.
+__global__ void __launch_bounds__(128) k_b_finish_newton(const BDesc* __restrict__ Ds,
+                                                         const int64_t* __restrict__ pre_blk, int n, Mod M) {
+  extern __shared__ uint64_t fsm[];
+  const int i = seg_of(pre_blk, n, blockIdx.x);
   const BDesc& D = Ds[i];
-  const int64_t j = x - pre[i];
+  const int S = D.S;
+  uint64_t* W = fsm;
+  uint64_t* num = fsm + S * S;
+  for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) W[idx] = D.invd[idx];
+  const int64_t j = (blockIdx.x - pre_blk[i]) * 128 + threadIdx.x;
+  const bool active = j < D.T;
   uint64_t den = 1;
   if (active) {
     den = combine_den_d(D, j, D.v[j], M);
     if (den == 0) atomicOr(D.status, ST_ZERO_DEN);
   }
   const uint64_t inv = warp_batch_inverse(den, M);
-  if (!active) return;
-  const int S = D.S;
-  uint64_t a[SMAX];
+  if (active) {
+    // sum of the k-block partials; the S loads of one k-block are independent
+    uint64_t* nm = num + threadIdx.x;
+    for (int s = 0; s < S; s++) nm[s * 128] = D.part[(int64_t)s * D.T + j];
+    for (int kb = 1; kb < D.NB; kb++) {
+      const uint64_t* pp = D.part + (int64_t)kb * S * D.T + j;
+      for (int s0 = 0; s0 < S; s0 += 8) {
+        uint64_t x[8];
 #pragma unroll
-  for (int s = 0; s < SMAX; s++) {
-    a[s] = 0;
-    if (s < S) {
-      uint64_t num = 0;
-      for (int kb = 0; kb < D.NB; kb++) num = add_mod(num, D.part[((int64_t)kb * S + s) * D.T + j], M);
-      a[s] = mul_mod(num, inv, M);
+        for (int q = 0; q < 8; q++) x[q] = s0 + q < S ? pp[(int64_t)(s0 + q) * D.T] : 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+          if (s0 + q < S) nm[(s0 + q) * 128] = add_mod(nm[(s0 + q) * 128], x[q], M);
+      }
     }
   }
-  newton_any<SMAX>(a, S, D.xs, D.invd, M);
+  __syncthreads();
   int cnt = 0;
-#pragma unroll
-  for (int e = 0; e < SMAX; e++)
-    if (e < S) {
-      D.g[(int64_t)e * D.T + j] = a[e];
-      cnt += a[e] != 0;
-    }
-  D.cnt[j] = cnt;
+  if (active) {
+    cnt = newton_apply(S, W, num + threadIdx.x, 128, inv, D.g + j, D.T, M);
+    D.cnt[j] = cnt;
+  }
+  // nonzero coefficients of this block of terms, for the compaction
+  __shared__ int64_t sh[33];
+  int64_t total;
+  block_exclusive_scan(cnt, sh, total);
+  if (threadIdx.x == 0) D.bsum[blockIdx.x - pre_blk[i]] = total;
 }
 
 __global__ void __launch_bounds__(256) k_b_finish_solve(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
@@ -235,61 +249,68 @@ __global__ void __launch_bounds__(256) k_b_finish_solve(const BDesc* __restrict_
 
 // ---- a6: compaction ---------------------------------------------------------------
 
-constexpr int kScanB = 1024;
+constexpr int kScanB = 1024;   // width of the block-offset scan
+constexpr int kCompB = 128;    // terms per compaction block (the finish kernel's blocks)
 
-__global__ void __launch_bounds__(kScanB) k_b_block_sums(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
-                                                         int n) {
-  __shared__ int64_t sh[33];
-  const int i = seg_of(pre, n, blockIdx.x);
-  const BDesc& D = Ds[i];
-  const int64_t blk = blockIdx.x - pre[i];
-  const int64_t j = blk * kScanB + threadIdx.x;
-  int64_t total;
-  block_exclusive_scan(j < D.T ? D.cnt[j] : 0, sh, total);
-  if (threadIdx.x == 0) D.bsum[blk] = total;
-}
-
+// Exclusive offsets of the blocks' nonzero counts, one CTA per entry.
 __global__ void __launch_bounds__(kScanB) k_b_scan(const BDesc* __restrict__ Ds) {
   __shared__ int64_t sh[33];
   const BDesc& D = Ds[blockIdx.x];
   if (D.mode != 0) return;
-  const int64_t nb = (D.T + kScanB - 1) / kScanB;
+  const int64_t nb = (D.T + kCompB - 1) / kCompB;
   int64_t carry = 0;
   for (int64_t base = 0; base < nb; base += kScanB) {
     const int64_t t = base + threadIdx.x;
     int64_t total;
     const int64_t ex = block_exclusive_scan(t < nb ? D.bsum[t] : 0, sh, total);
-    __syncthreads();
     if (t < nb) D.bsum[t] = ex + carry;
     carry += total;
-    __syncthreads();
   }
   if (threadIdx.x == 0) *D.out_count = carry;
 }
 
-__global__ void __launch_bounds__(kScanB) k_b_scatter(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
-                                                      int n) {
+// The new skeleton: the nonzero coefficients of every term j in order of j,
+// then of the power s of x_k.  One block per 128 terms; its threads walk the
+// block's output slots, so consecutive threads write consecutive outputs.
+__global__ void __launch_bounds__(kCompB) k_b_scatter(const BDesc* __restrict__ Ds,
+                                                      const int64_t* __restrict__ pre_blk, int n) {
   __shared__ int64_t sh[33];
-  const int i = seg_of(pre, n, blockIdx.x);
+  __shared__ int32_t offs[kCompB];
+  __shared__ uint64_t masks[kCompB];
+  const int i = seg_of(pre_blk, n, blockIdx.x);
   const BDesc& D = Ds[i];
-  const int64_t blk = blockIdx.x - pre[i];
-  const int64_t j = blk * kScanB + threadIdx.x;
-  const int64_t x = j < D.T ? D.cnt[j] : 0;
+  const int64_t blk = blockIdx.x - pre_blk[i];
+  const int64_t j0 = blk * kCompB, j = j0 + threadIdx.x;
+  const int S = D.S;
+  uint64_t mask = 0;
+  if (j < D.T)
+    for (int s = 0; s < S; s++)
+      if (D.g[(int64_t)s * D.T + j] != 0) mask |= 1ull << s;
   int64_t total;
-  int64_t o = block_exclusive_scan(x, sh, total) + D.bsum[blk];
-  if (j >= D.T || x == 0) return;
+  const int64_t ex = block_exclusive_scan(__popcll(mask), sh, total);
+  offs[threadIdx.x] = (int32_t)ex;
+  masks[threadIdx.x] = mask;
+  __syncthreads();
+  const int64_t base = D.bsum[blk];
   const int nv = D.nv, k = D.k;
-  const uint8_t* e = D.exps + j * nv;
-  for (int s = 0; s < D.S; s++) {
-    const uint64_t val = D.g[(int64_t)s * D.T + j];
-    if (val == 0) continue;
-    if (o < D.out_cap) {
-      uint8_t* oe = D.out_exps + o * nv;
-      for (int m = 0; m < nv; m++) oe[m] = m < k ? e[m] : 0;
-      oe[k] = (uint8_t)s;
-      D.out_coef[o] = val;
+  for (int slot = threadIdx.x; slot < total; slot += kCompB) {
+    int lo = 0, hi = kCompB - 1;   // the term owning this slot: largest t with offs[t] <= slot
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (offs[mid] <= slot) lo = mid;
+      else hi = mid - 1;
     }
-    o++;
+    uint64_t m = masks[lo];
+    for (int r = slot - offs[lo]; r > 0; r--) m &= m - 1;
+    const int s = __ffsll((long long)m) - 1;
+    const int64_t jj = j0 + lo, o = base + slot;
+    if (o < D.out_cap) {
+      const uint8_t* e = D.exps + jj * nv;
+      uint8_t* oe = D.out_exps + o * nv;
+      for (int q = 0; q < nv; q++) oe[q] = q < k ? e[q] : 0;
+      oe[k] = (uint8_t)s;
+      D.out_coef[o] = D.g[(int64_t)s * D.T + jj];
+    }
   }
 }
 
@@ -315,7 +336,7 @@ static void push_prefix(std::vector<int64_t>& all, const std::vector<int64_t>& c
 struct Prepared {
   std::vector<StepDims> plan;
   std::vector<int64_t> pre;
-  size_t o_hash = 0, o_roots = 0, o_leaf = 0, o_carry = 0;
+  size_t o_hash = 0, o_roots = 0, o_leaf = 0, o_carry = 0, o_nblk = 0;
   std::vector<size_t> o_lvl;
   std::vector<int> tiles_used;
   std::vector<std::vector<int4>> work;
@@ -337,18 +358,20 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
   Carver m0(nullptr);
   for (int i = 0; i < n; i++) carve_step(m0, items[i].T, items[i].S, items[i].k, P.plan[i]);
   P.ws_bytes = m0.off;
-  std::vector<int64_t> c_hash(n), c_roots(n), c_leaf(n), c_carry(n);
+  std::vector<int64_t> c_hash(n), c_roots(n), c_leaf(n), c_carry(n), c_nblk(n);
   for (int i = 0; i < n; i++) {
     const int64_t T = items[i].T;
     c_hash[i] = T > 0 ? (int64_t)hash_slots(T) : 0;
     c_roots[i] = T;
-    c_leaf[i] = (T + 1023) / 1024;
+    c_leaf[i] = (T + (1 << kTreeL1) - 1) >> kTreeL1;
+    c_nblk[i] = (T + 127) / 128;
     c_carry[i] = (T > 0 && P.plan[i].NB > 1) ? (int64_t)((T + 255) / 256) * (P.plan[i].NB - 1) : 0;
   }
   push_prefix(P.pre, c_hash, P.o_hash);
   push_prefix(P.pre, c_roots, P.o_roots);
   push_prefix(P.pre, c_leaf, P.o_leaf);
   push_prefix(P.pre, c_carry, P.o_carry);
+  push_prefix(P.pre, c_nblk, P.o_nblk);
   for (int l = kTreeL1; l < P.lmax; l++) {
     std::vector<int64_t> c(n);
     for (int i = 0; i < n; i++) c[i] = tree_levels(items[i].T) > l ? (items[i].T + kNO - 1) / kNO : 0;
@@ -394,7 +417,7 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
   const int mode = P.mode, kmax = P.kmax, smax = P.smax, lmax = P.lmax;
   const std::vector<StepDims>& plan = P.plan;
   const std::vector<int64_t>& pre = P.pre;
-  const size_t o_hash = P.o_hash, o_roots = P.o_roots, o_leaf = P.o_leaf, o_carry = P.o_carry;
+  const size_t o_hash = P.o_hash, o_roots = P.o_roots, o_leaf = P.o_leaf, o_carry = P.o_carry, o_nblk = P.o_nblk;
   const std::vector<size_t>& o_lvl = P.o_lvl;
   const std::vector<int>& tiles_used = P.tiles_used;
   const std::vector<std::vector<int4>>& work = P.work;
@@ -490,7 +513,7 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
   if (nroots) { k_b_anchor<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
   cudaEvent_t e1 = prof_mark(ctx, st);
   // a3
-  if (nleaf) { k_b_tree_leaf<<<(unsigned)nleaf, 512, 0, st>>>(dD, dpre + o_leaf, n, M); note_launch(); }
+  if (nleaf) { k_b_tree_leaf<<<(unsigned)nleaf, 1 << kTreeL1, 0, st>>>(dD, dpre + o_leaf, n, M); note_launch(); }
   for (int l = kTreeL1; l < lmax; l++) {
     const size_t o = o_lvl[l - kTreeL1];
     const int64_t nt = pre[o + n];
@@ -506,21 +529,34 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
   // a6 (or the plain finish of a system)
   if (nroots) {
     if (mode == 0) {
-      { k_b_newton_table<<<n, 256, 0, st>>>(dD, M); note_launch(); }
-      const unsigned grid = cdiv(nroots, 128);
-      if (smax <= 8) { k_b_finish_newton<8><<<grid, 128, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
-      else if (smax <= 16) { k_b_finish_newton<16><<<grid, 128, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
-      else if (smax <= 32) { k_b_finish_newton<32><<<grid, 128, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
-      else { k_b_finish_newton<64><<<grid, 128, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+      static bool configured = false;
+      if (!configured) {
+        cudaFuncSetAttribute(k_b_newton_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(8 * newton_table_words(kNewtonMax)));
+        cudaFuncSetAttribute(k_b_finish_newton, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)newton_smem(kNewtonMax));
+        configured = true;
+      }
+      {
+        k_b_newton_table<<<n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), st>>>(dD, M);
+        note_launch();
+      }
+      const int64_t nblk = pre[o_nblk + n];
+      {
+        k_b_finish_newton<<<(unsigned)nblk, 128, newton_smem(smax), st>>>(dD, dpre + o_nblk, n, M);
+        note_launch();
+      }
     } else {
       { k_b_finish_solve<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
     }
   }
   cudaEvent_t e5 = prof_mark(ctx, st);
   if (mode == 0 && nleaf) {
-    { k_b_block_sums<<<(unsigned)nleaf, kScanB, 0, st>>>(dD, dpre + o_leaf, n); note_launch(); }
     { k_b_scan<<<n, kScanB, 0, st>>>(dD); note_launch(); }
-    { k_b_scatter<<<(unsigned)nleaf, kScanB, 0, st>>>(dD, dpre + o_leaf, n); note_launch(); }
+    {
+      k_b_scatter<<<(unsigned)pre[o_nblk + n], kCompB, 0, st>>>(dD, dpre + o_nblk, n);
+      note_launch();
+    }
   }
   cudaEvent_t e6 = prof_mark(ctx, st);
   prof_add(ctx, PH_ANCHOR, e0, e1);

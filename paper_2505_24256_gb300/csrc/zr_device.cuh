@@ -81,68 +81,131 @@ __device__ __forceinline__ uint64_t warp_batch_inverse(uint64_t d, const Mod& M)
   return d ? r : 0;
 }
 
-template <int SMAX>
-__device__ __forceinline__ void newton_to_monomial(uint64_t (&a)[SMAX], int S, const uint64_t* __restrict__ xs,
-                                                   const uint64_t* __restrict__ invd, const Mod& M) {
-  // divided differences
-#pragma unroll
-  for (int l = 1; l < SMAX; l++) {
-#pragma unroll
-    for (int s = SMAX - 1; s >= l; s--) {
-      if (l < S && s < S) a[s] = mul_mod(sub_mod(a[s], a[s - 1], M), __ldg(invd + l * S + s), M);
-    }
-  }
-  // nested expansion, innermost bracket first: coef <- coef (z - x_l) + a_l
-  uint64_t cf[SMAX];
-#pragma unroll
-  for (int e = 0; e < SMAX; e++) cf[e] = 0;
-#pragma unroll
-  for (int e = 0; e < SMAX; e++)
-    if (e == S - 1) cf[0] = a[e];
-#pragma unroll
-  for (int l = SMAX - 2; l >= 0; l--) {
-    if (l <= S - 2) {
-      const uint64_t xl = __ldg(xs + l);
-      // degree before this step: S - 2 - l
-#pragma unroll
-      for (int e = SMAX - 1; e >= 1; e--)
-        if (e <= S - 1 - l) cf[e] = sub_mod(cf[e - 1], mul_mod(xl, cf[e], M), M);
-      cf[0] = sub_mod(a[l], mul_mod(xl, cf[0], M), M);
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < SMAX; e++) a[e] = cf[e];
-}
+// ---- Newton interpolation on shared nodes (Introduction, the Newton formula) -----
+//
+// Every term of a step is interpolated on the same S nodes x_0..x_{S-1}, so
+// the map from the S values to the S monomial coefficients is one S x S
+// matrix W shared by all terms.  Column s of W is what Newton's method gives
+// for the unit vector e_s: the divided-difference table, then the nested
+// expansion of the Newton form into powers of z.  Applying W to a term's
+// values is S^2 independent multiply-accumulates with one reduction per
+// coefficient, instead of a chain of S^2 dependent modular products.
 
-// The same expansion with rolled loops (arrays in local memory) for the
-// largest point count, to keep compile time bounded.
-template <int SMAX>
-__device__ __noinline__ void newton_to_monomial_rolled(uint64_t* a, int S, const uint64_t* __restrict__ xs,
-                                                       const uint64_t* __restrict__ invd, const Mod& M) {
-  for (int l = 1; l < S; l++)
-    for (int s = S - 1; s >= l; s--) a[s] = mul_mod(sub_mod(a[s], a[s - 1], M), __ldg(invd + l * S + s), M);
-  uint64_t cf[SMAX];
-  for (int e = 0; e < S; e++) cf[e] = 0;
-  cf[0] = a[S - 1];
+constexpr int kNewtonMax = 64;   // largest point count
+
+// W for the nodes xs_g (device, S <= kNewtonMax) by one block of
+// kNewtonThreads threads, all S columns at once: level by level, every
+// (column, entry) pair of the divided-difference table and then of the nested
+// expansion is updated by its own thread.  smem: newton_table_words(S) words.
+// Equal nodes set ST_DUP_SAMPLE in *status (W is then meaningless).
+constexpr int kNewtonThreads = 1024;
+constexpr int kNewtonPairs = kNewtonMax * kNewtonMax / kNewtonThreads;   // pairs per thread
+__host__ __device__ constexpr int newton_table_words(int S) { return 2 * S * S + S; }
+
+__device__ inline void newton_table_block(int S, const uint64_t* __restrict__ xs_g, uint64_t* __restrict__ W,
+                                          uint32_t* status, uint64_t* smem, const Mod& M) {
+  uint64_t* xs = smem;
+  uint64_t* A = smem + S;        // A[s * S + t]: column s's divided differences
+  uint64_t* B = A + S * S;       // B[l * S + t] = 1 / (x_t - x_{t-l}), then the expansion cf[s * S + e]
+  const int n2 = S * S, tid = threadIdx.x;
+  for (int i = tid; i < S; i += kNewtonThreads) xs[i] = xs_g[i];
+  __syncthreads();
+  for (int idx = tid; idx < n2; idx += kNewtonThreads) {
+    const int l = idx / S, t = idx - l * S;
+    uint64_t r = 0;
+    if (l >= 1 && t >= l) {
+      const uint64_t d = sub_mod(xs[t], xs[t - l], M);
+      if (d == 0) atomicOr(status, ST_DUP_SAMPLE);
+      r = inv_mod(d, M);
+    }
+    B[idx] = r;
+    A[idx] = l == t ? 1 : 0;     // column l is the unit vector e_l
+  }
+  __syncthreads();
+  uint64_t nw[kNewtonPairs];
+  // divided differences: level l replaces a_t by (a_t - a_{t-1}) / (x_t - x_{t-l}), t >= l
+  for (int l = 1; l < S; l++) {
+#pragma unroll
+    for (int q = 0; q < kNewtonPairs; q++) {
+      const int idx = tid + q * kNewtonThreads, t = idx % S;
+      if (idx < n2 && t >= l) nw[q] = mul_mod(sub_mod(A[idx], A[idx - 1], M), B[l * S + t], M);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kNewtonPairs; q++) {
+      const int idx = tid + q * kNewtonThreads, t = idx % S;
+      if (idx < n2 && t >= l) A[idx] = nw[q];
+    }
+    __syncthreads();
+  }
+  // nested expansion, innermost bracket first: cf <- cf (z - x_l) + a_l
+  for (int idx = tid; idx < n2; idx += kNewtonThreads) {
+    const int s = idx / S, e = idx - s * S;
+    B[idx] = e == 0 ? A[s * S + S - 1] : 0;
+  }
+  __syncthreads();
   for (int l = S - 2; l >= 0; l--) {
-    const uint64_t xl = __ldg(xs + l);
-    for (int e = S - 1 - l; e >= 1; e--) cf[e] = sub_mod(cf[e - 1], mul_mod(xl, cf[e], M), M);
-    cf[0] = sub_mod(a[l], mul_mod(xl, cf[0], M), M);
+    const uint64_t xl = xs[l];
+#pragma unroll
+    for (int q = 0; q < kNewtonPairs; q++) {
+      const int idx = tid + q * kNewtonThreads, s = idx / S, e = idx - s * S;
+      if (idx < n2 && e <= S - 1 - l)
+        nw[q] = sub_mod(e == 0 ? A[s * S + l] : B[idx - 1], mul_mod(xl, B[idx], M), M);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kNewtonPairs; q++) {
+      const int idx = tid + q * kNewtonThreads, e = idx % S;
+      if (idx < n2 && e <= S - 1 - l) B[idx] = nw[q];
+    }
+    __syncthreads();
   }
-  for (int e = 0; e < S; e++) a[e] = cf[e];
+  for (int idx = tid; idx < n2; idx += kNewtonThreads) {
+    const int s = idx / S, e = idx - s * S;
+    W[e * S + s] = B[idx];
+  }
 }
 
-template <int SMAX>
-__device__ __forceinline__ void newton_any(uint64_t (&a)[SMAX], int S, const uint64_t* __restrict__ xs,
-                                           const uint64_t* __restrict__ invd, const Mod& M) {
-  if constexpr (SMAX > 32) newton_to_monomial_rolled<SMAX>(a, S, xs, invd, M);
-  else newton_to_monomial<SMAX>(a, S, xs, invd, M);
+// out[e * ld] = scale * sum_s W[e][s] val[s * stride] for e < S (W and val in
+// shared memory, val canonical); returns how many of them are nonzero.
+__device__ inline int newton_apply(int S, const uint64_t* W, const uint64_t* val, int stride, uint64_t scale,
+                                   uint64_t* out, int64_t ld, const Mod& M) {
+  int cnt = 0;
+  for (int e0 = 0; e0 < S; e0 += 4) {
+    Acc8 acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) acc[q] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
+    const uint64_t* w0 = W + (e0 + 0 < S ? e0 + 0 : S - 1) * S;
+    const uint64_t* w1 = W + (e0 + 1 < S ? e0 + 1 : S - 1) * S;
+    const uint64_t* w2 = W + (e0 + 2 < S ? e0 + 2 : S - 1) * S;
+    const uint64_t* w3 = W + (e0 + 3 < S ? e0 + 3 : S - 1) * S;
+    for (int s = 0; s < S; s++) {
+      const uint64_t x = val[s * stride];
+      const uint32_t x0 = lo32(x), x1 = hi32(x);
+      uint64_t w = w0[s];
+      mac8(acc[0], x0, x1, lo32(w), hi32(w));
+      w = w1[s];
+      mac8(acc[1], x0, x1, lo32(w), hi32(w));
+      w = w2[s];
+      mac8(acc[2], x0, x1, lo32(w), hi32(w));
+      w = w3[s];
+      mac8(acc[3], x0, x1, lo32(w), hi32(w));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if (e0 + q < S) {
+        const uint64_t g = mul_mod(acc8_value(acc[q], M), scale, M);
+        out[(int64_t)(e0 + q) * ld] = g;
+        cnt += g != 0;
+      }
+  }
+  return cnt;
 }
 
-// Exclusive scan over a CTA of 1024 threads; sh holds 33 words.
+// Exclusive scan over a CTA (blockDim.x a multiple of 32, at most 1024);
+// sh holds 33 words; every thread of the CTA must call it.
 __device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t* sh, int64_t& total) {
-  // blockDim.x == kScanB; sh holds 32 words
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int64_t incl = x;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -152,7 +215,7 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t* sh, 
   if (lane == 31) sh[w] = incl;
   __syncthreads();
   if (w == 0) {
-    int64_t s = sh[lane];
+    const int64_t s = lane < nw ? sh[lane] : 0;
     int64_t si = s;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -164,7 +227,9 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t* sh, 
   }
   __syncthreads();
   total = sh[32];
-  return incl - x + sh[w];
+  const int64_t r = incl - x + sh[w];
+  __syncthreads();              // sh may be reused right after
+  return r;
 }
 
 // Segment of a flattened index: the largest i < n with pre[i] <= x.

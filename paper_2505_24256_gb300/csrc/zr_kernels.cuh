@@ -67,10 +67,12 @@ void launch_b_solve(int s_tile, const BDesc* Ds, const int4* items, int nitems, 
 // right-hand-side tiles the solve kernel is built for, and its resident CTAs per SM
 int solve_tiles(int* out, int cap);
 int solve_blocks_per_sm(int s_tile);
-void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* invd, uint32_t* status, cudaStream_t st);
-// plain batched Newton: vals (npts x ld) -> coef (npts x ld)
-void launch_newton(int64_t nterms, int npts, const uint64_t* xs, const uint64_t* invd, const uint64_t* vals,
-                   int64_t ld, const Mod& M, uint64_t* coef, cudaStream_t st);
-int64_t scan_blocks(int64_t n);  // number of scan blocks
+// Newton on shared nodes: W (S x S) from the nodes, then vals (npts x ld) ->
+// monomial coefficients coef (npts x ld) through W
+void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* W, uint32_t* status, cudaStream_t st);
+void launch_newton(int64_t nterms, int npts, const uint64_t* W, const uint64_t* vals, int64_t ld, const Mod& M,
+                   uint64_t* coef, cudaStream_t st);
+size_t newton_smem(int S);   // dynamic shared memory of one 128-term block
+int64_t scan_blocks(int64_t n);  // number of 128-term compaction blocks
 
 }  // namespace zr

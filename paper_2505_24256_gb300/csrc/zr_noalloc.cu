@@ -76,7 +76,7 @@ extern "C" zr_status zr_newton_batched_noalloc(uint64_t prime, int64_t nterms, i
   uint32_t* status = reinterpret_cast<uint32_t*>(scratch + kStatusWord);
   if (cudaMemsetAsync(status, 0, sizeof(uint32_t), st) != cudaSuccess) return ZR_ERR_CUDA;
   zr::launch_newton_table(npts, x, M, invd, status, st);
-  zr::launch_newton(nterms, npts, x, invd, vals, ld, M, coef, st);
+  zr::launch_newton(nterms, npts, invd, vals, ld, M, coef, st);
   uint32_t flags = 0;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);

@@ -144,7 +144,7 @@ zr_status Recon::newton_coeffs(int S, const uint64_t* d_cs, const uint64_t* d_va
   uint64_t* invd = scratch_.as<uint64_t>();
   uint64_t* out = invd + (size_t)S * S;
   launch_newton_table(S, d_cs, M_, invd, ctx_->d_status_call, st_);
-  launch_newton(1, S, d_cs, invd, d_vals, 1, M_, out, st_);
+  launch_newton(1, S, invd, d_vals, 1, M_, out, st_);
   coef.assign(S, 0);
   e = cudaMemcpyAsync(coef.data(), out, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st_);
   if (e != cudaSuccess) return cuda_err(ctx_, e, "newton copy");

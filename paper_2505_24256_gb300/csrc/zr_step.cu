@@ -78,54 +78,55 @@ void launch_node_check(int64_t T, const uint64_t* v, uint64_t* htab, uint64_t hm
 //   invd[l S + s] = 1 / (x_s - x_{s-l}),  1 <= l <= s < S   (shared by all terms)
 // ---------------------------------------------------------------------------
 
-__global__ void k_newton_table(int S, const uint64_t* __restrict__ xs, Mod M, uint64_t* __restrict__ invd,
-                               uint32_t* status) {
-  for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
-    int l = idx / S, s = idx - l * S;
-    if (l >= 1 && s >= l) {
-      uint64_t d = sub_mod(xs[s], xs[s - l], M);
-      if (d == 0) atomicOr(status, ST_DUP_SAMPLE);
-      invd[idx] = inv_mod(d, M);
-    }
+__global__ void __launch_bounds__(kNewtonThreads) k_newton_table(int S, const uint64_t* __restrict__ xs, Mod M,
+                                                                  uint64_t* __restrict__ W, uint32_t* status) {
+  extern __shared__ uint64_t tsm[];
+  newton_table_block(S, xs, W, status, tsm, M);
+}
+
+void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* W, uint32_t* status, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_newton_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(8 * newton_table_words(kNewtonMax)));
+    configured = true;
   }
+  const size_t smem = 8 * (size_t)newton_table_words(S);
+  { k_newton_table<<<1, kNewtonThreads, smem, st>>>(S, xs, M, W, status); note_launch(); }
 }
 
-void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* invd, uint32_t* status, cudaStream_t st) {
-  { k_newton_table<<<1, 256, 0, st>>>(S, xs, M, invd, status); note_launch(); }
-}
-
-template <int SMAX>
-__global__ void __launch_bounds__(128) k_newton(int64_t nterms, int S, const uint64_t* __restrict__ xs,
-                                                const uint64_t* __restrict__ invd,
-                                                const uint64_t* __restrict__ vals, int64_t ld, Mod M,
-                                                uint64_t* __restrict__ coef) {
+// One block of 128 terms: the block's values and W in shared memory, then
+// S^2 multiply-accumulates per term.  coef may alias vals: a thread reads its
+// whole column before it writes it.
+__global__ void __launch_bounds__(128) k_newton(int64_t nterms, int S, const uint64_t* __restrict__ Wg,
+                                                const uint64_t* vals, int64_t ld, Mod M, uint64_t* coef) {
+  extern __shared__ uint64_t nsm[];
+  uint64_t* W = nsm;
+  uint64_t* val = nsm + S * S;
+  for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) W[idx] = Wg[idx];
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nterms) return;
-  uint64_t a[SMAX];
-#pragma unroll
-  for (int s = 0; s < SMAX; s++) {
-    a[s] = 0;
-    if (s < S) {
-      uint64_t x = vals[(int64_t)s * ld + j];
-      a[s] = x >= M.p ? x - M.p : x;
-    }
-  }
-  newton_any<SMAX>(a, S, xs, invd, M);
-#pragma unroll
-  for (int e = 0; e < SMAX; e++)
-    if (e < S) coef[(int64_t)e * ld + j] = a[e];
+  const bool active = j < nterms;
+  if (active)
+    for (int s = 0; s < S; s++) val[s * 128 + threadIdx.x] = canon(vals[(int64_t)s * ld + j], M);
+  __syncthreads();
+  if (!active) return;
+  newton_apply(S, W, val + threadIdx.x, 128, 1, coef + j, ld, M);
 }
 
-void launch_newton(int64_t nterms, int npts, const uint64_t* xs, const uint64_t* invd, const uint64_t* vals,
-                   int64_t ld, const Mod& M, uint64_t* coef, cudaStream_t st) {
+size_t newton_smem(int S) { return sizeof(uint64_t) * ((size_t)S * S + (size_t)S * 128); }
+
+void launch_newton(int64_t nterms, int npts, const uint64_t* W, const uint64_t* vals, int64_t ld, const Mod& M,
+                   uint64_t* coef, cudaStream_t st) {
   if (nterms <= 0) return;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)newton_smem(kNewtonMax));
+    configured = true;
+  }
   const unsigned grid = cdiv(nterms, 128);
-  if (npts <= 8) { k_newton<8><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef); note_launch(); }
-  else if (npts <= 16) { k_newton<16><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef); note_launch(); }
-  else if (npts <= 32) { k_newton<32><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef); note_launch(); }
-  else { k_newton<64><<<grid, 128, 0, st>>>(nterms, npts, xs, invd, vals, ld, M, coef); note_launch(); }
+  { k_newton<<<grid, 128, newton_smem(npts), st>>>(nterms, npts, W, vals, ld, M, coef); note_launch(); }
 }
 
-int64_t scan_blocks(int64_t n) { return (n + 1023) / 1024; }
+int64_t scan_blocks(int64_t n) { return (n + 127) / 128; }
 
 }  // namespace zr

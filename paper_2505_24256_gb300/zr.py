@@ -64,6 +64,12 @@ class zr_result(ctypes.Structure):
                 ("steps", ctypes.c_int32), ("redraws", ctypes.c_int32), ("device_ms", ctypes.c_double)]
 
 
+class zr_peaks(ctypes.Structure):
+    _fields_ = [("mac_per_s", ctypes.c_double), ("chain_per_s", ctypes.c_double),
+                ("imad_lo_per_s", ctypes.c_double), ("imad_hi_per_s", ctypes.c_double),
+                ("sms", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class zr_request(ctypes.Structure):
     _fields_ = [("bb", zr_blackbox), ("prm", zr_recon_params)]
 
@@ -108,6 +114,7 @@ SIGNATURES = {
                                       _P, _P, _I64, _P, _V]),
     "zr_reconstruct": (_ST, [_V, _P, _P, ctypes.POINTER(ctypes.POINTER(zr_result)), _V]),
     "zr_result_free": (None, [ctypes.POINTER(zr_result)]),
+    "zr_measure_peaks": (_ST, [_V, _P, _V]),
     "zr_serve_create": (_ST, [_V, ctypes.c_size_t, _I32, ctypes.POINTER(_V)]),
     "zr_serve_submit": (_ST, [_V, _P, ctypes.POINTER(_U64)]),
     "zr_serve_poll": (_ST, [_V, _U64, ctypes.POINTER(ctypes.POINTER(zr_result))]),
@@ -187,6 +194,12 @@ class Context:
         if st != OK:
             msg = self.L.zr_last_error(self._h).decode(errors="replace")
             raise ZrError(st, f"{what}: {msg}")
+
+    def measure_peaks(self, stream=None) -> dict:
+        """Measured MAC / chain-step / IMAD rates (operations per second)."""
+        p = zr_peaks()
+        self.check(self.L.zr_measure_peaks(self._h, ctypes.byref(p), _stream(stream)), "zr_measure_peaks")
+        return {f: getattr(p, f) for f, _ in zr_peaks._fields_ if f != "pad"}
 
     def workspace_bytes(self) -> int:
         return int(self.L.zr_workspace_bytes(self._h))
