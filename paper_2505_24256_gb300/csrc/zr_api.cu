@@ -167,20 +167,22 @@ uint64_t hash_slots(int64_t T) {
   return h;
 }
 
-// Launch plan of the solve: for every compiled right-hand-side tile, the
-// resident CTAs per SM (occupancy query, cached) give the CTA slots of one
-// wave; the number of k-blocks NB trades parallelism against the carry pass.
-// Model, in 32-bit multiply-add issue slots per thread and k:
-//   cost_k = 12 tile + 45   (four lo + four hi per MAC, two Shoup products)
-// and a wave with n CTAs per SM takes BK cost_k max(n, 4): fewer than four
-// resident CTAs (16 warps) leave the multiplier partly idle.  The carry pass
-// adds a 24-slot Shoup Horner step per k.  The cheapest plan wins; measured
-// plans from zr_autotune_step take precedence.
-static int occupancy_cached(int tile) {
-  static int cache[64] = {0};
-  if (tile <= 0 || tile >= 64) return 1;
-  if (!cache[tile]) cache[tile] = solve_blocks_per_sm(tile);
-  return cache[tile];
+// Launch plan of the solve: the right-hand sides per consumer thread (CG,
+// "tile"; G = ceil(S / CG) consumer groups of 64 threads plus one producer
+// warp per CTA) and the number of k-blocks NB.  For every compiled tile the
+// resident CTAs per SM (occupancy query, cached) give the slots of one wave.
+// Model, in 32-bit multiply issue slots per root and k:
+//   cost_k = 8 G CG + 32   (four lo + four hi per MAC over the padded
+//                           columns; two Shoup chain steps)
+// and a wave with n CTAs on an SM takes BK cost_k n / min(1, w / 16), w the
+// resident warps: fewer than 16 warps leave the multiplier partly idle.  The
+// carry pass adds a 24-slot Shoup Horner step per k.  The cheapest plan wins;
+// measured plans from zr_autotune_step take precedence.
+static int occupancy_cached(int tile, int groups) {
+  static int cache[64][8] = {{0}};
+  if (tile <= 0 || tile >= 64 || groups < 1 || groups > 7) return 1;
+  if (!cache[tile][groups]) cache[tile][groups] = solve_blocks_per_sm(tile, groups);
+  return cache[tile][groups];
 }
 
 // A forced plan: the context's tuned plan table, else ZR_SOLVE_PLAN="tile,NB"
@@ -214,22 +216,26 @@ static bool forced_plan(const zr_ctx* ctx, int64_t T, int S, StepDims& D) {
 
 double plan_cost(const zr_ctx* ctx, const StepDims& D) {
   const int64_t sms = ctx && ctx->sms ? ctx->sms : 152;
-  const int64_t rows = (D.T + 127) / 128;
-  const int nst = (D.S + D.s_tile - 1) / D.s_tile;
-  const int per_sm = occupancy_cached(D.s_tile);
+  const int rt = solve_roots_per_item();
+  const int64_t rows = (D.T + rt - 1) / rt;
+  const int G = (D.S + D.s_tile - 1) / D.s_tile;
+  if (G > solve_max_groups() || !solve_instance_exists(D.s_tile, G)) return 1e300;
+  const int per_sm = occupancy_cached(D.s_tile, G);
   const int64_t slots = sms * per_sm;
-  const double cost_k = 12.0 * D.s_tile + 45.0;
-  const int64_t ctas = rows * D.NB * nst;
+  const double cost_k = 8.0 * G * D.s_tile + 32.0;
+  const int64_t items = rows * D.NB;
   double cost = 0;
-  for (int64_t left = ctas; left > 0; left -= slots) {
+  for (int64_t left = items; left > 0; left -= slots) {
     const int64_t in_wave = left < slots ? left : slots;
     const int64_t n = (in_wave + sms - 1) / sms;
-    cost += (double)D.BK * cost_k * (double)(n > 4 ? n : 4);
+    const double warps = (double)n * (1 + 2 * G);
+    const double eff = warps >= 16 ? 1.0 : warps / 16.0;
+    cost += (double)D.BK * rt * cost_k * (double)n / eff;
   }
   if (D.NB > 1) {
-    const int64_t cslots = sms * 16;                     // 128-thread rows of the carry kernel
-    const int64_t cw = (rows * (D.NB - 1) + cslots - 1) / cslots;
-    cost += (double)cw * D.BK * 24.0 * 4;
+    const int64_t cslots = sms * 8;                      // 256-thread CTAs of the carry kernel
+    const int64_t cw = ((D.T + 255) / 256 * (D.NB - 1) + cslots - 1) / cslots;
+    cost += (double)cw * D.BK * 256 * 24.0;
   }
   return cost;
 }
@@ -241,14 +247,14 @@ StepDims plan_step(const zr_ctx* ctx, int64_t T, int S) {
   best.S = S;
   best.NB = 1;
   best.BK = ((T + 31) / 32) * 32;
-  best.s_tile = 21;
+  best.s_tile = 16;
   double best_cost = -1;
   int tiles[16];
   const int nt = solve_tiles(tiles, 16);
   for (int ti = 0; ti < nt; ti++) {
     const int tile = tiles[ti];
-    const int nst = (S + tile - 1) / tile;
-    if (nst > 8) continue;
+    const int groups = (S + tile - 1) / tile;
+    if (groups > solve_max_groups() || !solve_instance_exists(tile, groups)) continue;
     for (int NBw = 1; NBw <= 64; NBw++) {
       int64_t BK = (T + NBw - 1) / NBw;
       BK = ((BK + 31) / 32) * 32;

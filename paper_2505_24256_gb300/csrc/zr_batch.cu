@@ -338,7 +338,7 @@ struct Prepared {
   std::vector<int64_t> pre;
   size_t o_hash = 0, o_roots = 0, o_leaf = 0, o_carry = 0, o_nblk = 0;
   std::vector<size_t> o_lvl;
-  std::vector<int> tiles_used;
+  std::vector<int> tiles_used;        // solve instances: tile * 16 + consumer groups
   std::vector<std::vector<int4>> work;
   int kmax = 0, smax = 0, lmax = 0, mode = 0;
   size_t ws_bytes = 0, table_bytes = 0;
@@ -381,21 +381,23 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
   }
   for (int i = 0; i < n; i++) {
     if (items[i].T == 0) continue;
-    const int tile = P.plan[i].s_tile;
-    int w = (int)(std::find(P.tiles_used.begin(), P.tiles_used.end(), tile) - P.tiles_used.begin());
+    // one work list per (tile, consumer groups): the solve kernel instance
+    const int tile = P.plan[i].s_tile, groups = (items[i].S + tile - 1) / tile;
+    const int key = tile * 16 + groups;
+    int w = (int)(std::find(P.tiles_used.begin(), P.tiles_used.end(), key) - P.tiles_used.begin());
     if (w == (int)P.tiles_used.size()) {
-      P.tiles_used.push_back(tile);
+      P.tiles_used.push_back(key);
       P.work.emplace_back();
     }
-    const int rows = (int)((items[i].T + 127) / 128), nst = (items[i].S + tile - 1) / tile;
+    const int rt = solve_roots_per_item();
+    const int rows = (int)((items[i].T + rt - 1) / rt);
     for (int kb = 0; kb < P.plan[i].NB; kb++)
-      for (int r = 0; r < rows; r++)
-        for (int s = 0; s < nst; s++) P.work[w].push_back(make_int4(i, r, kb, s));
+      for (int r = 0; r < rows; r++) P.work[w].push_back(make_int4(i, r, kb, 0));
   }
   const std::vector<StepDims>& plan = P.plan;
   for (auto& wl : P.work)
     std::stable_sort(wl.begin(), wl.end(), [&](const int4& a, const int4& b) {
-      return plan[a.x].BK * plan[a.x].s_tile > plan[b.x].BK * plan[b.x].s_tile;
+      return plan[a.x].BK * plan[a.x].S > plan[b.x].BK * plan[b.x].S;
     });
   P.table_bytes = sizeof(BDesc) * n + sizeof(int64_t) * P.pre.size();
   for (auto& wl : P.work) P.table_bytes += sizeof(int4) * wl.size() + 16;
@@ -441,7 +443,7 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
     d.NB = plan[i].NB;
     d.BK = plan[i].BK;
     d.s_tile = plan[i].s_tile;
-    d.nst = (it.S + plan[i].s_tile - 1) / plan[i].s_tile;
+    d.nst = (it.S + plan[i].s_tile - 1) / plan[i].s_tile;   // consumer groups of the solve
     d.levels = tree_levels(it.T);
     d.hmask = hash_slots(it.T) - 1;
     d.exps = it.exps;
@@ -524,7 +526,9 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
   if (ncarry) launch_b_carry(dD, dpre + o_carry, n, ncarry, M, st);
   cudaEvent_t e3 = prof_mark(ctx, st);
   for (size_t w = 0; w < work.size(); w++)
-    launch_b_solve(tiles_used[w], dD, dwork[w], (int)work[w].size(), ctx->sms ? ctx->sms : 152, M, st);
+    if (!launch_b_solve(tiles_used[w] / 16, tiles_used[w] % 16, dD, dwork[w], (int)work[w].size(),
+                        ctx->sms ? ctx->sms : 152, M, st))
+      return set_err(ctx, ZR_ERR_INVALID_ARG, "no solve kernel for this launch plan");
   cudaEvent_t e4 = prof_mark(ctx, st);
   // a6 (or the plain finish of a system)
   if (nroots) {

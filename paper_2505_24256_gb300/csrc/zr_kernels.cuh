@@ -33,7 +33,7 @@ struct StepDims {
   int32_t S;
   int32_t NB;      // k-blocks
   int64_t BK;      // k-block length (the top block may be shorter)
-  int32_t s_tile;  // right-hand sides per thread
+  int32_t s_tile;  // right-hand sides per consumer thread of the solve
 };
 
 // One step (mode 0: a Zippel step whose nodes are the anchor values of a
@@ -62,11 +62,15 @@ void launch_shoup_pre(int64_t T, const uint64_t* v, const Mod& M, uint64_t* vp, 
 void launch_node_check(int64_t T, const uint64_t* v, uint64_t* htab, uint64_t hmask, uint32_t* status, cudaStream_t st);
 // batched carry and solve (zr_solve.cu)
 void launch_b_carry(const BDesc* Ds, const int64_t* pre, int n, int64_t nctas, const Mod& M, cudaStream_t st);
-void launch_b_solve(int s_tile, const BDesc* Ds, const int4* items, int nitems, int sms, const Mod& M,
+// false when no solve kernel is built for (s_tile, groups): nothing launched
+bool launch_b_solve(int s_tile, int groups, const BDesc* Ds, const int4* items, int nitems, int sms, const Mod& M,
                     cudaStream_t st);
 // right-hand-side tiles the solve kernel is built for, and its resident CTAs per SM
 int solve_tiles(int* out, int cap);
-int solve_blocks_per_sm(int s_tile);
+int solve_blocks_per_sm(int s_tile, int groups);
+bool solve_instance_exists(int s_tile, int groups);
+int solve_roots_per_item();   // roots of one work item
+int solve_max_groups();       // consumer groups per CTA: S <= groups * s_tile
 // Newton on shared nodes: W (S x S) from the nodes, then vals (npts x ld) ->
 // monomial coefficients coef (npts x ld) through W
 void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* W, uint32_t* status, cudaStream_t st);

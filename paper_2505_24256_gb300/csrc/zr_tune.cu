@@ -42,8 +42,8 @@ extern "C" zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t
   const int nt = solve_tiles(tiles, 16);
   const int nbs[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32};
   for (int ti = 0; ti < nt; ti++) {
-    const int nst = (S + tiles[ti] - 1) / tiles[ti];
-    if (nst > 8) continue;
+    const int groups = (S + tiles[ti] - 1) / tiles[ti];
+    if (groups > solve_max_groups() || !solve_instance_exists(tiles[ti], groups)) continue;
     for (int nb : nbs) {
       if (nb > 1 && T / nb < 64) continue;
       StepDims D;

@@ -1,0 +1,70 @@
+"""Runs Zippel steps of a named workload on cuda:0 for profiling.
+
+    python -m paper_2505_24256_gb300.profile_step [--workload batched|large]
+        [--steps N] [--plan TILE,NB]
+
+The probes are generated once by the GPU evaluator; then N steps run back to
+back (the first is a warm-up when N > 1) with the given solve plan (else the
+planner's model), and the per-phase device times of the context profiler
+are printed.  Under ncu, select the solve kernel with -k regex:k_solve and
+skip the warm-up launch with -s 1.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="batched", choices=["batched", "large"])
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--plan", default=None, help="solve plan TILE,NB (default: the planner's model)")
+    args = ap.parse_args()
+    if args.plan:
+        os.environ["ZR_SOLVE_PLAN"] = args.plan
+    import numpy as np
+    import torch
+
+    from paper_2505_24256_gb300 import build, workloads as W, zr
+
+    build.build()
+    wl = W.batched_step_1e4() if args.workload == "batched" else W.large_step_2p20()
+    dev = torch.device("cuda:0")
+
+    def d64(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(dev)
+
+    ctx = zr.Context(wl.p)
+    f = ctx.poly(wl.nv, wl.exps.shape[0], torch.from_numpy(wl.exps).to(dev), d64(wl.coef))
+    y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
+    ske = torch.from_numpy(wl.skel).to(dev)
+    skel = ctx.poly(wl.nv, wl.T, ske)
+    b = torch.empty((wl.S, wl.T), dtype=torch.int64, device=dev)
+    ctx.zippel_probes(f, wl.k, y, wl.S, cs, z, wl.T, 0, b, wl.T)
+    cap = wl.T * wl.S
+    oe = torch.zeros((cap, wl.nv), dtype=torch.uint8, device=dev)
+    oc = torch.zeros(cap, dtype=torch.int64, device=dev)
+    ctx.profile(True)
+    n = 0
+    for _ in range(args.steps):
+        n = ctx.zippel_step(skel, wl.k, y, wl.S, cs, b, wl.T, 0, oe, oc, cap)
+    torch.cuda.synchronize()
+    ok = n == wl.exps.shape[0] and np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
+    phases = {ph: ctx.profile_query(ph)[0] / args.steps for ph in zr.Context.PHASES[:7]}
+    print(json.dumps({"workload": wl.name, "steps": args.steps, "plan": ctx.step_plan(wl.T, wl.S),
+                      "phase_ms": phases, "check": "generator truth" if ok else "MISMATCH"}), flush=True)
+    ctx.close()
+    return 0 if ok else 1
+
+
+if __name__ == "__main__":
+    rc = main()
+    sys.stdout.flush()
+    os._exit(rc)
