@@ -286,8 +286,8 @@ def run_zr(args):
 
     solve_avg_s = solve_ms / max(solve_n, 1) / 1e3
     # the solve's algorithmic work per (root j, k): S multiply-accumulates of
-    # the dot products, one chain step of the synthetic division, one chain
-    # step of the denominator q_j(v_j)
+    # the dot products, one chain step of the synthetic division and one of
+    # the denominator q_j(v_j)
     macs, chain_steps = S * T * T, 2 * T * T
     solve_ops = macs + chain_steps
     t_star = macs / peaks["mac_per_s"] + chain_steps / peaks["chain_per_s"]      # measured ceiling

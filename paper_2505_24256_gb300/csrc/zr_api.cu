@@ -176,7 +176,7 @@ uint64_t hash_slots(int64_t T) {
 //                           columns; two Shoup chain steps)
 // and a wave with n CTAs on an SM takes BK cost_k n / min(1, w / 16), w the
 // resident warps: fewer than 16 warps leave the multiplier partly idle.  The
-// carry pass adds a 24-slot Shoup Horner step per k.  The cheapest plan wins;
+// carry pass adds a Shoup Horner step per k.  The cheapest plan wins;
 // measured plans from zr_autotune_step take precedence.
 static int occupancy_cached(int tile, int groups) {
   static int cache[64][8] = {{0}};
@@ -235,7 +235,7 @@ double plan_cost(const zr_ctx* ctx, const StepDims& D) {
   if (D.NB > 1) {
     const int64_t cslots = sms * 8;                      // 256-thread CTAs of the carry kernel
     const int64_t cw = ((D.T + 255) / 256 * (D.NB - 1) + cslots - 1) / cslots;
-    cost += (double)cw * D.BK * 256 * 24.0;
+    cost += (double)cw * D.BK * 256 * 24.0;              // one Shoup step per k
   }
   return cost;
 }

@@ -150,9 +150,12 @@ __global__ void __launch_bounds__(kNO* kNS) k_b_tree_level(const BDesc* __restri
 
 // ---- a4/a6: finish ---------------------------------------------------------------
 
-// q_j(v_j) (times v_j for offset 1) from its k-block partials: Horner in
-// v_j^BK from the top block down, the partials loaded eight at a time.
-__device__ __forceinline__ uint64_t combine_den_d(const BDesc& D, int64_t j, uint64_t vj, const Mod& M) {
+// The value to invert for root j and the factor its inverse is scaled by:
+// q_j(v_j) (times v_j for offset 1) from the solve's k-block partials u_kb,
+// q_j(v_j) = sum_kb u_kb v_j^{kb BK} (Horner in v_j^BK from the top block
+// down, the partials loaded eight at a time).
+__device__ __forceinline__ uint64_t root_den(const BDesc& D, int64_t j, uint64_t vj, const Mod& M, uint64_t& mult) {
+  mult = 1;
   const uint64_t vBK = D.NB > 1 ? pow_mod(vj, (uint64_t)D.BK, M) : 1;
   uint64_t den = 0;
   for (int kt = D.NB; kt > 0; kt -= 8) {
@@ -191,12 +194,12 @@ __global__ void __launch_bounds__(128) k_b_finish_newton(const BDesc* __restrict
   for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) W[idx] = D.invd[idx];
   const int64_t j = (blockIdx.x - pre_blk[i]) * 128 + threadIdx.x;
   const bool active = j < D.T;
-  uint64_t den = 1;
+  uint64_t den = 1, mult = 1;
   if (active) {
-    den = combine_den_d(D, j, D.v[j], M);
+    den = root_den(D, j, D.v[j], M, mult);
     if (den == 0) atomicOr(D.status, ST_ZERO_DEN);
   }
-  const uint64_t inv = warp_batch_inverse(den, M);
+  const uint64_t inv = mul_mod(warp_batch_inverse(den, M), mult, M);
   if (active) {
     // sum of the k-block partials; the S loads of one k-block are independent
     uint64_t* nm = num + threadIdx.x;
@@ -233,16 +236,23 @@ __global__ void __launch_bounds__(256) k_b_finish_solve(const BDesc* __restrict_
   const int i = active ? seg_of(pre, n, x) : 0;
   const BDesc& D = Ds[i];
   const int64_t j = x - pre[i];
-  uint64_t den = 1;
+  uint64_t den = 1, mult = 1;
   if (active) {
-    den = combine_den_d(D, j, D.v[j], M);
+    den = root_den(D, j, D.v[j], M, mult);
     if (den == 0) atomicOr(D.status, ST_ZERO_DEN);
   }
-  const uint64_t inv = warp_batch_inverse(den, M);
+  const uint64_t inv = mul_mod(warp_batch_inverse(den, M), mult, M);
   if (!active) return;
   for (int s = 0; s < D.S; s++) {
+    // the NB partials of one right-hand side, loaded eight at a time
     uint64_t num = 0;
-    for (int kb = 0; kb < D.NB; kb++) num = add_mod(num, D.part[((int64_t)kb * D.S + s) * D.T + j], M);
+    for (int k0 = 0; k0 < D.NB; k0 += 8) {
+      uint64_t x[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) x[q] = k0 + q < D.NB ? D.part[((int64_t)(k0 + q) * D.S + s) * D.T + j] : 0;
+#pragma unroll
+      for (int q = 0; q < 8; q++) num = add_mod(num, x[q], M);
+    }
     D.c[(int64_t)s * D.ldc + j] = mul_mod(num, inv, M);
   }
 }

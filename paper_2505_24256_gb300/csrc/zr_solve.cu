@@ -9,8 +9,10 @@
 namespace zr {
 
 // ---------------------------------------------------------------------------
-// a4: block partials of the tail Horner value for the k-blocked chain:
-//   R_kb(v_j) = sum_{l in block kb} m_l v_j^{l - k_lo(kb)},  kb >= 1.
+// a4: block partials of the tail Horner value for the k-blocked chain,
+//   R_kb(v_j) = sum_{l in block kb} m_l v_j^{l - k_lo(kb)},  kb >= 1,
+// with m_T = 1 included in the top block, so that the chain's carry-in at the
+// top of block kb is sum_{kk > kb} R_kk v_j^{(kk - kb - 1) BK}.
 // One CTA = 256 roots of one entry and one k-block (flattened over a batch).
 // ---------------------------------------------------------------------------
 
@@ -26,7 +28,7 @@ __global__ void __launch_bounds__(256) k_b_carry(const BDesc* __restrict__ Ds, c
   const int64_t klo = kb * D.BK, khi = (klo + D.BK) < D.T ? (klo + D.BK) : D.T;
   const uint64_t vj = D.v[j], vpj = D.vp[j];
   const uint64_t* __restrict__ m = D.m;
-  uint64_t r = 0;
+  uint64_t r = kb == D.NB - 1 ? 1 : 0;
   for (int64_t l = khi - 1; l >= klo; l--) r = canon(shoup_lazy(r, vj, vpj, M), M) + __ldg(m + l);
   D.R[(int64_t)(kb - 1) * D.T + j] = canon(r, M);
 }

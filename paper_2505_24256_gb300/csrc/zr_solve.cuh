@@ -52,20 +52,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // ---------------------------------------------------------------------------
 // a4 + a5: the hot loop, warp-specialised.  A work item is one entry, one
 // tile of 32 roots j and one k-block; k runs downwards in chunks of KC.
-//   warp 0 (producer)    lane = root: stages the right-hand sides of a chunk
-//                        with cp.async, runs the synthetic-division chain
-//                        q_{j,k-1} = m_k + v_j q_{j,k} and the Horner value
-//                        u = u v_j + q_{j,k} of the block (Shoup multiplies),
-//                        writes q to shared memory;
+//   warp 0 (producer)     lane = root: stages the right-hand sides of a chunk
+//                         with cp.async, runs the synthetic-division chain
+//                         q_{j,k-1} = m_k + v_j q_{j,k} and the Horner value
+//                         u = u v_j + q_{j,k} of the block (Shoup multiplies),
+//                         writes q to shared memory;
 //   warps 1.. (consumers) G of them, lane = root: CG right-hand sides each,
-//                        acc_s += q_{j,k} b[s][k] in 160-bit accumulators,
-//                        reduced once per item.
+//                         acc_s += q_{j,k} b[s][k] in 160-bit accumulators,
+//                         reduced once per item.
 // Chunks flow through a ring of NST shared-memory stages guarded by
-// mbarriers ("full": the producer's 32 lanes arrive; "empty": one arrival per
-// consumer warp), across item boundaries, so no warp waits for any other
-// warp except the producer for a filled stage and the producer for the
-// slowest consumer NST chunks back.  Every q_{j,k} is computed once and read
-// by all G consumer warps, whatever S is.
+// mbarriers ("full": the producer's 32 lanes arrive; "empty": one arrival
+// per consumer warp), across item boundaries, so no warp waits for another
+// except the consumers for a filled stage and the producer for the slowest
+// consumer NST chunks back.  Every q_{j,k} is computed once and read by all
+// G consumer warps, whatever S is.  (A second producer warp for u measured
+// slower: the extra warp costs more occupancy than it frees issue slots.)
 // ---------------------------------------------------------------------------
 
 template <int CG, int G>
@@ -75,7 +76,7 @@ struct SolveCfg {
   static constexpr int NST = 4;               // ring stages
   static constexpr int CGP = (CG + 1) & ~1;   // a consumer's columns, padded to pairs
   static constexpr int BW = G * CGP;          // staged right-hand-side row width
-  static constexpr int NT = 32 * (1 + G);     // threads per CTA: producer warp + G consumer warps
+  static constexpr int NT = 32 * (1 + G);     // threads per CTA: producer warp + G consumer warps     // threads per CTA: chain, denominator, G consumer warps
   // resident CTAs the register budget is sized for (measured register needs
   // of the consumer loop: about 8 CG accumulator words plus temporaries)
   static constexpr int REG = CG <= 2 ? 72 : (CG <= 3 ? 80 : (CG <= 4 ? 104 : (CG <= 6 ? 136 : 168)));
@@ -115,19 +116,18 @@ __global__ void __launch_bounds__(SolveCfg<CG, G>::NT, SolveCfg<CG, G>::MINB)
     const int nch = (int)((khi - klo + C::KC - 1) / C::KC);
 
     if (warp == 0) {
-      // ---- producer
+      // ---- producer warp
       const int NB = D.NB;
       uint64_t q = 1, u = 0, v = 0, vp = 0;
       if (live) {
         v = D.v[j];
         vp = D.vp[j];
-        // carry-in q_{j, khi-1}: the tail Horner value from the blocks above
+        // carry-in q_{j, khi-1}: the tail Horner value of the blocks above
+        // (the top block's partial includes m_T = 1)
         if (kb < NB - 1) {
           const uint64_t vBK = pow_mod(v, (uint64_t)BK, M);
-          const uint64_t vtop = pow_mod(v, (uint64_t)(T - (int64_t)(NB - 1) * BK), M);
-          uint64_t cin = 1;
-          for (int kk = NB - 1; kk > kb; kk--)
-            cin = add_mod(D.R[(int64_t)(kk - 1) * T + j], mul_mod(kk == NB - 1 ? vtop : vBK, cin, M), M);
+          uint64_t cin = 0;
+          for (int kk = NB - 1; kk > kb; kk--) cin = add_mod(D.R[(int64_t)(kk - 1) * T + j], mul_mod(vBK, cin, M), M);
           q = cin;
         }
       }
@@ -200,21 +200,22 @@ __global__ void __launch_bounds__(SolveCfg<CG, G>::NT, SolveCfg<CG, G>::MINB)
               mac8(acc[CG - 1], x0, x1, w.x, w.y);
             }
           }
-        } else
+        } else {
 #pragma unroll 1
-        for (int kk = 0; kk < len; kk++) {
-          const uint64_t x = qb[st][kk][lane];
-          const uint32_t x0 = lo32(x), x1 = hi32(x);
-          const uint64_t* row = &bb[st][kk][g * C::CGP];
+          for (int kk = 0; kk < len; kk++) {
+            const uint64_t x = qb[st][kk][lane];
+            const uint32_t x0 = lo32(x), x1 = hi32(x);
+            const uint64_t* row = &bb[st][kk][g * C::CGP];
 #pragma unroll
-          for (int q = 0; q + 1 < CG; q += 2) {
-            const uint4 w = *reinterpret_cast<const uint4*>(row + q);
-            mac8(acc[q], x0, x1, w.x, w.y);
-            mac8(acc[q + 1], x0, x1, w.z, w.w);
-          }
-          if (CG & 1) {
-            const uint2 w = *reinterpret_cast<const uint2*>(row + CG - 1);
-            mac8(acc[CG - 1], x0, x1, w.x, w.y);
+            for (int q = 0; q + 1 < CG; q += 2) {
+              const uint4 w = *reinterpret_cast<const uint4*>(row + q);
+              mac8(acc[q], x0, x1, w.x, w.y);
+              mac8(acc[q + 1], x0, x1, w.z, w.w);
+            }
+            if (CG & 1) {
+              const uint2 w = *reinterpret_cast<const uint2*>(row + CG - 1);
+              mac8(acc[CG - 1], x0, x1, w.x, w.y);
+            }
           }
         }
         __syncwarp();

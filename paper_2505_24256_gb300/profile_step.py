@@ -42,7 +42,8 @@ def main():
         return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(dev)
 
     ctx = zr.Context(wl.p)
-    f = ctx.poly(wl.nv, wl.exps.shape[0], torch.from_numpy(wl.exps).to(dev), d64(wl.coef))
+    fe, fc = torch.from_numpy(wl.exps).to(dev), d64(wl.coef)     # kept alive: zr_poly holds raw pointers
+    f = ctx.poly(wl.nv, wl.exps.shape[0], fe, fc)
     y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
     ske = torch.from_numpy(wl.skel).to(dev)
     skel = ctx.poly(wl.nv, wl.T, ske)
@@ -56,10 +57,19 @@ def main():
     for _ in range(args.steps):
         n = ctx.zippel_step(skel, wl.k, y, wl.S, cs, b, wl.T, 0, oe, oc, cap)
     torch.cuda.synchronize()
-    ok = n == wl.exps.shape[0] and np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
+    got = oc[:n].cpu().numpy().view(np.uint64)
+    ok = n == wl.exps.shape[0] and np.array_equal(got, wl.coef)
     phases = {ph: ctx.profile_query(ph)[0] / args.steps for ph in zr.Context.PHASES[:7]}
-    print(json.dumps({"workload": wl.name, "steps": args.steps, "plan": ctx.step_plan(wl.T, wl.S),
-                      "phase_ms": phases, "check": "generator truth" if ok else "MISMATCH"}), flush=True)
+    line = {"workload": wl.name, "steps": args.steps, "plan": ctx.step_plan(wl.T, wl.S), "phase_ms": phases,
+            "check": "generator truth" if ok else "MISMATCH"}
+    if not ok:
+        line["terms"] = [int(n), int(wl.exps.shape[0])]
+        if n == wl.exps.shape[0]:
+            bad = np.nonzero(got != wl.coef)[0]
+            line["bad_terms"] = int(bad.size)
+            line["bad_roots"] = int(np.unique(bad // wl.S).size)
+            line["first_bad"] = [[int(i // wl.S), int(i % wl.S)] for i in bad[:6]]
+    print(json.dumps(line), flush=True)
     ctx.close()
     return 0 if ok else 1
 
