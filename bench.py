@@ -40,6 +40,23 @@ if ROOT not in sys.path:
 METRIC = "Zippel-step skeleton terms/s and mulmod/s vs roofline; serve p50/p99 latency"
 
 
+def solve_traffic(workload_name):
+    """DRAM bytes per solve launch from the committed ncu summary of this
+    workload, or None when there is none or the solve source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"k_solve_{workload_name}.md")
+    src = os.path.join(ROOT, "paper_2505_24256_gb300", "csrc", "zr_solve.cuh")
+    try:
+        fields = dict(line.split(": ", 1) for line in open(path).read().splitlines()
+                      if line.startswith(("traffic_bytes_per_launch: ", "source_sha256_prefix: ")))
+        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if fields.get("source_sha256_prefix", "").strip() != cur:
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def workload(name):
     from paper_2505_24256_gb300 import workloads as W
     return {"batched": W.batched_step_1e4, "large": W.large_step_2p20}[name]()
@@ -305,7 +322,8 @@ def run_zr(args):
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}"},
         "mulmod_per_s": world * W * args.steps / (total_ms / 1e3),
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_solve",
+                     "frac": achieved / peak, "traffic": solve_traffic(wl.name), "traffic_unit": "bytes/launch",
+                     "kernel": "k_solve",
                      "ops": f"S*T^2 multiply-accumulates + 2*T^2 chain steps = {solve_ops:.4g} per launch",
                      "peak_basis": "measured (zr_measure_peaks on this GPU, this run): "
                                    f"{peaks['mac_per_s'] / 1e9:.0f} GMAC/s, {peaks['chain_per_s'] / 1e9:.0f} G chain "
