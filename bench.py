@@ -163,6 +163,70 @@ def run_reference(args):
     return 0
 
 
+def small_steps_modes(ctx, dev, n=64, reps=20):
+    """64 small uneven Zippel steps (T = 20..66, S = 11, like the plain
+    3-variable reconstruction's steps) three ways, wall clock per round of
+    all 64: one asynchronous call per step, one batched call, one launch of
+    a captured graph."""
+    import numpy as np
+    import torch
+
+    from paper_2505_24256_gb300 import workloads as W
+
+    def d64(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(dev)
+
+    keep, descs, wls = [], [], []
+    for i in range(n):
+        wl = W.step_workload(2000 + i, 20 + (i * 7) % 47, 2, 10, 11)
+        fe, fc = torch.from_numpy(wl.exps).to(dev), d64(wl.coef)
+        f = ctx.poly(wl.nv, wl.exps.shape[0], fe, fc)
+        y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
+        ske = torch.from_numpy(wl.skel).to(dev)
+        b = torch.empty((wl.S, wl.T), dtype=torch.int64, device=dev)
+        ctx.zippel_probes(f, wl.k, y, wl.S, cs, z, wl.T, 0, b, wl.T)
+        cap = wl.T * wl.S
+        oe = torch.zeros((cap, wl.nv), dtype=torch.uint8, device=dev)
+        oc = torch.zeros(cap, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        keep += [fe, fc, y, cs, z, ske, b, oe, oc, cnt]
+        descs.append(dict(skel=ctx.poly(wl.nv, wl.T, ske), newvar=wl.k, S=wl.S, offset=0, y=y, samples=cs, probes=b,
+                          ldb=wl.T, out_exps=oe, out_coef=oc, out_cap=cap, out_count=cnt))
+        wls.append(wl)
+
+    def per_call():
+        for d in descs:
+            ctx.zippel_step_async(d["skel"], d["newvar"], d["y"], d["S"], d["samples"], d["probes"], d["ldb"], 0,
+                                  d["out_exps"], d["out_coef"], d["out_cap"], d["out_count"])
+        ctx.stream_status()
+
+    def batched():
+        ctx.zippel_step_batched(descs)
+
+    g = ctx.step_graph(descs)
+
+    def graph():
+        g.launch()
+        g.status()
+
+    out = {"steps": n, "T": "20..66", "S": 11, "unit": "ms per round of all steps (wall clock, host + device)"}
+    for name, fn in (("one_call_per_step", per_call), ("batched_call", batched), ("graph_launch", graph)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        out[name] = 1e3 * (time.perf_counter() - t0) / reps
+    ok = all(int(d["out_count"].item()) == wl.exps.shape[0] and
+             np.array_equal(d["out_coef"][:wl.exps.shape[0]].cpu().numpy().view(np.uint64), wl.coef)
+             for d, wl in zip(descs, wls))
+    out["check"] = "generator truth" if ok else "MISMATCH"
+    g.close()
+    return out
+
+
 def run_zr(args):
     import numpy as np
     import torch
@@ -295,6 +359,21 @@ def run_zr(args):
     plain_ms = sum(a.elapsed_time(bb) for a, bb in pevs) / plain_reps
     plain_ok = np.array_equal(gpl.cpu().numpy().view(np.uint64).T.reshape(-1), wl.coef)
 
+    # the same step as a captured graph (one launch per step)
+    graph = ctx.step_graph([dict(skel=skel, newvar=k, S=S, offset=0, y=y, samples=cs, probes=b, ldb=T, out_exps=oe,
+                                 out_coef=oc, out_cap=cap, out_count=torch.zeros(1, dtype=torch.int64, device=dev))])
+    gevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(plain_reps)]
+    for i in range(plain_reps):
+        flush.zero_()
+        gevs[i][0].record(stream)
+        graph.launch()
+        gevs[i][1].record(stream)
+    graph.status()
+    graph_ms = sum(a.elapsed_time(bb) for a, bb in gevs) / plain_reps
+    graph_kernels = graph.kernels
+    graph.close()
+    small = small_steps_modes(ctx, dev)
+
     if rank != 0:
         ctx.close()
         if world > 1:
@@ -334,6 +413,8 @@ def run_zr(args):
                        "batched_speedup": plain_ms / ms_per_step,
                        "what": f"{S} single-RHS systems, one launch sequence each, + Newton",
                        "check": "generator truth" if plain_ok else "MISMATCH"},
+        "graph": {"ms_per_step": graph_ms, "kernels_per_launch": graph_kernels},
+        "small_steps": small,
         "phase_ms": phases,
         "plan": {"s_tile": plan[0], "k_blocks": plan[1]},
         "probe_gen_ms": probe_ms,

@@ -237,6 +237,27 @@ typedef struct zr_step_desc {
 } zr_step_desc;
 zr_status zr_zippel_step_batched(zr_ctx* ctx, int32_t nsteps, const zr_step_desc* steps, void* stream);
 
+/* Steps captured into a CUDA graph (one graph per batch shape).  Create
+ * checks the entries like zr_zippel_step_batched (every entry needs T >= 1),
+ * stages their tables into workspace the graph owns, runs the steps once on
+ * `stream` (waits; returns that run's status) and captures the kernel
+ * sequence.  Every pointer of `steps` is baked into the graph: a launch
+ * re-runs the same shapes on whatever those buffers hold at that time and
+ * overwrites the same outputs, with one graph launch (asynchronous on
+ * `stream`).  zr_step_graph_status waits for `stream` and returns the status
+ * of the last run (ZR_ERR_SINGULAR etc.); zr_step_graph_kernels is the number
+ * of kernels one launch runs.  *out is set whenever the graph was built, also
+ * when the first run's status is an error (destroy it either way).  The
+ * context must outlive the graph; the graph does not use the context's
+ * workspace. */
+typedef struct zr_step_graph zr_step_graph;
+zr_status zr_step_graph_create(zr_ctx* ctx, int32_t nsteps, const zr_step_desc* steps, void* stream,
+                               zr_step_graph** out);
+zr_status zr_step_graph_launch(zr_step_graph* graph, void* stream);
+zr_status zr_step_graph_status(zr_step_graph* graph, void* stream);
+uint64_t zr_step_graph_kernels(const zr_step_graph* graph);
+void zr_step_graph_destroy(zr_step_graph* graph);
+
 /* The same step with every array in HOST memory (pinned or pageable): the
  * call copies the inputs in, runs the step on `stream` and copies the new
  * skeleton out.  out_exps / out_coef are host buffers of out_cap terms. */

@@ -306,6 +306,7 @@ static std::atomic<unsigned long long> g_launches{0};
 namespace zr {
 unsigned long long launch_count() { return g_launches.load(); }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace zr
 
 extern "C" uint64_t zr_launch_count(void) { return (uint64_t)zr::launch_count(); }
@@ -486,9 +487,10 @@ extern "C" zr_status zr_anchor_values(zr_ctx* ctx, int64_t T, int32_t nv, const 
   return finish_sync_call(ctx, st, nullptr);
 }
 
-static zr_status check_step_args(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
-                                 const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
-                                 uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap) {
+namespace zr {
+zr_status check_step_args(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
+                          const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
+                          uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap) {
   if (!skel) return set_err(ctx, ZR_ERR_INVALID_ARG, "null skeleton");
   if (skel->nv < 1 || skel->nv > kMaxVars || newvar < 0 || newvar >= skel->nv)
     return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_zippel_step: need 0 <= newvar < nv <= 64");
@@ -501,9 +503,9 @@ static zr_status check_step_args(zr_ctx* ctx, const zr_poly* skel, int32_t newva
   return ZR_OK;
 }
 
-static BatchItem step_item(const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S, const uint64_t* samples,
-                           const uint64_t* probes, int64_t ldb, int32_t offset, uint8_t* out_exps, uint64_t* out_coef,
-                           int64_t out_cap, int64_t* d_count) {
+BatchItem step_item(const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S, const uint64_t* samples,
+                    const uint64_t* probes, int64_t ldb, int32_t offset, uint8_t* out_exps, uint64_t* out_coef,
+                    int64_t out_cap, int64_t* d_count) {
   BatchItem it;
   it.mode = 0;
   it.T = skel->T;
@@ -522,6 +524,7 @@ static BatchItem step_item(const zr_poly* skel, int32_t newvar, const uint64_t* 
   it.out_count = d_count;
   return it;
 }
+}  // namespace zr
 
 // A step with T = 0 still validates its samples (equal samples are an error).
 static void empty_step(zr_ctx* ctx, int S, const uint64_t* samples, int64_t* d_count, uint32_t* status,

@@ -421,24 +421,32 @@ size_t batch_ws_need(const zr_ctx* ctx, const BatchItem* items, int n) {
   return P.ws_bytes + P.table_bytes + 512;
 }
 
-zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status, cudaStream_t st, size_t base) {
-  if (n <= 0) return ZR_OK;
-  const Mod& M = ctx->M;
+// A batch whose descriptor tables are on the device: everything launch_batch
+// needs to enqueue (or to have captured) the kernels.
+struct StagedBatch {
   Prepared P;
+  int n = 0;
+  const BDesc* dD = nullptr;
+  const int64_t* dpre = nullptr;
+  std::vector<const int4*> dwork;
+  std::vector<int64_t*> zero_counts;   // out_count of entries with T = 0
+};
+
+// Plans the batch, carves its workspace at `ws` (batch_ws_need bytes) and
+// copies the descriptor tables to the device on `st` (through the context's
+// pinned staging buffer).
+static zr_status stage_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status, cudaStream_t st, char* ws,
+                             StagedBatch& SB) {
+  Prepared& P = SB.P;
+  SB.n = n;
   if (!prepare(ctx, items, n, P)) return set_err(ctx, ZR_ERR_INVALID_ARG, "batch mixes steps and systems");
-  const int mode = P.mode, kmax = P.kmax, smax = P.smax, lmax = P.lmax;
   const std::vector<StepDims>& plan = P.plan;
   const std::vector<int64_t>& pre = P.pre;
-  const size_t o_hash = P.o_hash, o_roots = P.o_roots, o_leaf = P.o_leaf, o_carry = P.o_carry, o_nblk = P.o_nblk;
-  const std::vector<size_t>& o_lvl = P.o_lvl;
-  const std::vector<int>& tiles_used = P.tiles_used;
   const std::vector<std::vector<int4>>& work = P.work;
   const size_t table_bytes = P.table_bytes;
   std::vector<BDesc> D(n);
-  zr_status r = ensure_ws(ctx, base + P.ws_bytes + table_bytes + 512, st);
-  if (r) return r;
   // carve for real
-  Carver cv(ctx->ws + base);
+  Carver cv(ws);
   for (int i = 0; i < n; i++) {
     const BatchItem& it = items[i];
     StepWs w = carve_step(cv, it.T, it.S, it.k, plan[i]);
@@ -512,18 +520,42 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
   if (e != cudaSuccess) return cuda_err(ctx, e, "batch tables");
   if (!ctx->stage_event) cudaEventCreateWithFlags(&ctx->stage_event, cudaEventDisableTiming);
   cudaEventRecord(ctx->stage_event, st);
+  SB.dD = dD;
+  SB.dpre = dpre;
+  SB.dwork = dwork;
+  SB.zero_counts.clear();
+  for (int i = 0; i < n; i++)
+    if (items[i].T == 0 && P.mode == 0 && items[i].out_count) SB.zero_counts.push_back(items[i].out_count);
+  return ZR_OK;
+}
+
+// Enqueues the batch's kernels on `st` (capturable: no host synchronisation,
+// no allocation).  `prof` records the profiler's phase events.
+static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t st, bool prof) {
+  const Prepared& P = SB.P;
+  const int n = SB.n;
+  const Mod& M = ctx->M;
+  const int mode = P.mode, kmax = P.kmax, smax = P.smax, lmax = P.lmax;
+  const std::vector<int64_t>& pre = P.pre;
+  const size_t o_hash = P.o_hash, o_roots = P.o_roots, o_leaf = P.o_leaf, o_carry = P.o_carry, o_nblk = P.o_nblk;
+  const std::vector<size_t>& o_lvl = P.o_lvl;
+  const std::vector<int>& tiles_used = P.tiles_used;
+  const std::vector<std::vector<int4>>& work = P.work;
+  const BDesc* dD = SB.dD;
+  const int64_t* dpre = SB.dpre;
+  const std::vector<const int4*>& dwork = SB.dwork;
+  auto mark = [&]() -> cudaEvent_t { return prof ? prof_mark(ctx, st) : nullptr; };
 
   const int64_t nroots = pre[o_roots + n], nhash = pre[o_hash + n], nleaf = pre[o_leaf + n];
   const int64_t ncarry = pre[o_carry + n];
   // entries with T = 0 report an empty skeleton
-  for (int i = 0; i < n; i++)
-    if (items[i].T == 0 && mode == 0 && items[i].out_count) cudaMemsetAsync(items[i].out_count, 0, 8, st);
-  cudaEvent_t e0 = prof_mark(ctx, st);
+  for (int64_t* c : SB.zero_counts) cudaMemsetAsync(c, 0, 8, st);
+  cudaEvent_t e0 = mark();
   // a2
   if (nhash) { k_b_fill_hash<<<cdiv(nhash, 256), 256, 0, st>>>(dD, dpre + o_hash, n); note_launch(); }
   if (mode == 0 && kmax > 0) { k_b_powtab<<<dim3(kmax, n), kPowTab, 0, st>>>(dD, M); note_launch(); }
   if (nroots) { k_b_anchor<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
-  cudaEvent_t e1 = prof_mark(ctx, st);
+  cudaEvent_t e1 = mark();
   // a3
   if (nleaf) { k_b_tree_leaf<<<(unsigned)nleaf, 1 << kTreeL1, 0, st>>>(dD, dpre + o_leaf, n, M); note_launch(); }
   for (int l = kTreeL1; l < lmax; l++) {
@@ -531,15 +563,15 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
     const int64_t nt = pre[o + n];
     if (nt) { k_b_tree_level<<<(unsigned)nt, kNO * kNS, 0, st>>>(dD, dpre + o, n, l, M); note_launch(); }
   }
-  cudaEvent_t e2 = prof_mark(ctx, st);
+  cudaEvent_t e2 = mark();
   // a4 + a5
   if (ncarry) launch_b_carry(dD, dpre + o_carry, n, ncarry, M, st);
-  cudaEvent_t e3 = prof_mark(ctx, st);
+  cudaEvent_t e3 = mark();
   for (size_t w = 0; w < work.size(); w++)
     if (!launch_b_solve(tiles_used[w] / 16, tiles_used[w] % 16, dD, dwork[w], (int)work[w].size(),
                         ctx->sms ? ctx->sms : 152, M, st))
       return set_err(ctx, ZR_ERR_INVALID_ARG, "no solve kernel for this launch plan");
-  cudaEvent_t e4 = prof_mark(ctx, st);
+  cudaEvent_t e4 = mark();
   // a6 (or the plain finish of a system)
   if (nroots) {
     if (mode == 0) {
@@ -564,7 +596,7 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
       { k_b_finish_solve<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
     }
   }
-  cudaEvent_t e5 = prof_mark(ctx, st);
+  cudaEvent_t e5 = mark();
   if (mode == 0 && nleaf) {
     { k_b_scan<<<n, kScanB, 0, st>>>(dD); note_launch(); }
     {
@@ -572,7 +604,7 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
       note_launch();
     }
   }
-  cudaEvent_t e6 = prof_mark(ctx, st);
+  cudaEvent_t e6 = mark();
   prof_add(ctx, PH_ANCHOR, e0, e1);
   prof_add(ctx, PH_MASTER, e1, e2);
   prof_add(ctx, PH_CARRY, e2, e3);
@@ -580,6 +612,48 @@ zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status
   prof_add(ctx, PH_NEWTON, e4, e5);
   prof_add(ctx, PH_COMPACT, e5, e6);
   return cuda_err(ctx, cudaGetLastError(), "batch launch");
+}
+
+zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status, cudaStream_t st, size_t base) {
+  if (n <= 0) return ZR_OK;
+  const size_t need = batch_ws_need(ctx, items, n);
+  zr_status r = ensure_ws(ctx, base + need, st);
+  if (r) return r;
+  StagedBatch SB;
+  r = stage_batch(ctx, items, n, status, st, ctx->ws + base, SB);
+  if (r) return r;
+  return launch_batch(ctx, SB, st, true);
+}
+
+// ---- captured batches (CUDA graphs) ----------------------------------------------
+
+zr_status batch_graph_capture(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status, char* ws,
+                              cudaStream_t st, cudaGraph_t* graph, uint64_t* launches) {
+  StagedBatch SB;
+  zr_status r = stage_batch(ctx, items, n, status, st, ws, SB);
+  if (r) return r;
+  // one uncaptured run first: the tables land, and every kernel's one-time
+  // attribute setup happens outside the capture
+  cudaMemsetAsync(status, 0, sizeof(uint32_t), st);
+  if ((r = launch_batch(ctx, SB, st, false))) return r;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "graph warm-up");
+  cudaStream_t cs;
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_err(ctx, e, "graph");
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const uint64_t c0 = launch_count();
+    cudaMemsetAsync(status, 0, sizeof(uint32_t), cs);
+    r = launch_batch(ctx, SB, cs, false);
+    *launches = launch_count() - c0;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess && !r) *graph = g;
+    else if (g) cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cs);
+  if (r) return r;
+  return cuda_err(ctx, e, "graph capture");
 }
 
 }  // namespace zr

@@ -115,6 +115,18 @@ size_t batch_ws_need(const zr_ctx* ctx, const BatchItem* items, int n);
 // workspace (the caller ensured base + batch_ws_need, or the call grows it
 // when nothing before `base` is live).  status: device word of ST_* flags.
 zr_status run_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status, cudaStream_t st, size_t base = 0);
+// The same batch with its workspace at `ws` (batch_ws_need bytes, owned by
+// the caller): the tables are staged and the batch run once on `st`, then its
+// kernels are captured into *graph; *launches counts the captured kernels.
+zr_status batch_graph_capture(zr_ctx* ctx, const BatchItem* items, int n, uint32_t* status, char* ws,
+                              cudaStream_t st, cudaGraph_t* graph, uint64_t* launches);
+// argument checks and batch entry of one Zippel step (zr_zippel_step's arguments)
+zr_status check_step_args(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
+                          const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
+                          uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap);
+BatchItem step_item(const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S, const uint64_t* samples,
+                    const uint64_t* probes, int64_t ldb, int32_t offset, uint8_t* out_exps, uint64_t* out_coef,
+                    int64_t out_cap, int64_t* d_count);
 
 // evaluator (zr_eval.cu)
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);

@@ -10,6 +10,7 @@ namespace zr {
 // Number of kernels the library has launched (a diagnostic counter).
 unsigned long long launch_count();
 void note_launch();
+void note_launches(uint64_t n);   // kernels of a replayed graph
 
 // Device status flags (OR-ed into one 32-bit word per call).
 enum : uint32_t {

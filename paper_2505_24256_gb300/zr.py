@@ -115,6 +115,11 @@ SIGNATURES = {
     "zr_reconstruct": (_ST, [_V, _P, _P, ctypes.POINTER(ctypes.POINTER(zr_result)), _V]),
     "zr_result_free": (None, [ctypes.POINTER(zr_result)]),
     "zr_measure_peaks": (_ST, [_V, _P, _V]),
+    "zr_step_graph_create": (_ST, [_V, _I32, _P, _V, ctypes.POINTER(_V)]),
+    "zr_step_graph_launch": (_ST, [_V, _V]),
+    "zr_step_graph_status": (_ST, [_V, _V]),
+    "zr_step_graph_kernels": (_U64, [_V]),
+    "zr_step_graph_destroy": (None, [_V]),
     "zr_serve_create": (_ST, [_V, ctypes.c_size_t, _I32, ctypes.POINTER(_V)]),
     "zr_serve_submit": (_ST, [_V, _P, ctypes.POINTER(_U64)]),
     "zr_serve_poll": (_ST, [_V, _U64, ctypes.POINTER(ctypes.POINTER(zr_result))]),
@@ -275,6 +280,21 @@ class Context:
         self.check(self.L.zr_zippel_step_batched(self._h, len(steps), ctypes.cast(arr, ctypes.c_void_p),
                                                  _stream(stream)), "zr_zippel_step_batched")
 
+    def step_graph(self, steps, stream=None):
+        """A StepGraph for the given step descriptors (same dicts as zippel_step_batched)."""
+        arr = (zr_step_desc * len(steps))()
+        for i, d in enumerate(steps):
+            arr[i] = zr_step_desc(d["skel"], d["newvar"], d["S"], d.get("offset", 0), 0, _ptr(d["y"]),
+                                  _ptr(d["samples"]), _ptr(d["probes"]), d["ldb"], _ptr(d["out_exps"]),
+                                  _ptr(d["out_coef"]), d["out_cap"], _ptr(d["out_count"]))
+        h = ctypes.c_void_p()
+        st = self.L.zr_step_graph_create(self._h, len(steps), ctypes.cast(arr, ctypes.c_void_p), _stream(stream),
+                                         ctypes.byref(h))
+        if st != OK and h.value:
+            self.L.zr_step_graph_destroy(h)
+        self.check(st, "zr_step_graph_create")
+        return StepGraph(self, h)
+
     def stream_status(self, stream=None):
         self.check(self.L.zr_stream_status(self._h, _stream(stream)), "zr_stream_status")
 
@@ -339,6 +359,34 @@ def newton_batched_noalloc(prime, nterms, npts, x, vals, ld, coef, stream=None) 
     device memory.  Returns the zr status code (0 on success)."""
     return int(load().zr_newton_batched_noalloc(prime, nterms, npts, _ptr(x), _ptr(vals), ld, _ptr(coef),
                                                  _stream(stream)))
+
+
+class StepGraph:
+    """zr_step_graph_*: captured steps re-run by one graph launch."""
+
+    def __init__(self, ctx, h):
+        self.ctx, self.L, self._h = ctx, ctx.L, h
+
+    def launch(self, stream=None):
+        self.ctx.check(self.L.zr_step_graph_launch(self._h, _stream(stream)), "zr_step_graph_launch")
+
+    def status(self, stream=None):
+        self.ctx.check(self.L.zr_step_graph_status(self._h, _stream(stream)), "zr_step_graph_status")
+
+    @property
+    def kernels(self) -> int:
+        return int(self.L.zr_step_graph_kernels(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.zr_step_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _take_result(L, res):
