@@ -569,7 +569,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   cudaEvent_t e3 = mark();
   for (size_t w = 0; w < work.size(); w++)
     if (!launch_b_solve(tiles_used[w] / 16, tiles_used[w] % 16, dD, dwork[w], (int)work[w].size(),
-                        ctx->sms ? ctx->sms : 152, M, st))
+                        ctx->solve_persistent ? (ctx->sms ? ctx->sms : 152) : 0, M, st))
       return set_err(ctx, ZR_ERR_INVALID_ARG, "no solve kernel for this launch plan");
   cudaEvent_t e4 = mark();
   // a6 (or the plain finish of a system)

@@ -48,6 +48,10 @@ struct zr_ctx {
   void* h_stage = nullptr;      // pinned staging of batch tables
   size_t h_stage_cap = 0;
   cudaEvent_t stage_event = nullptr;   // last copy out of h_stage
+  // the solve runs one wave of CTAs walking its work list (persistent), or
+  // one CTA per work item, which lets higher-priority streams take SMs
+  // between items (the serving loop's lane of large requests)
+  bool solve_persistent = true;
   std::string err;
   std::mutex mu;                // guards err for the serve thread
 };

@@ -123,6 +123,19 @@ size_t Recon::device_bytes() const {
   return s;
 }
 
+double Recon::next_cost() const {
+  if (phase_ != RUN || k_ >= nv_) return 0;
+  const double TN = (double)curN_.T, TfN = (double)fN_.T;
+  if (!rational_) {
+    const double S = degN_[k_] + 1;
+    return S * TN * TN + S * TN * TfN;
+  }
+  const double TD = (double)curD_.T, TfD = (double)fD_.T;
+  const double SN = degN_[k_] + 1, SD = degD_[k_] + 1;
+  const double Sf = 2.0 * std::max(degN_[k_], degD_[k_]) + 2, Tm = std::max(TN, TD);
+  return SN * TN * TN + SD * TD * TD + Sf * Tm * (TfN + TfD);
+}
+
 size_t Recon::estimate_bytes(const zr_blackbox& bb, const zr_recon_params& prm) {
   // hidden function(s), the largest step (skeleton <= hidden terms, S <= 64
   // samples or 2 max(deg)+2 Thiele points) with its probes and outputs

@@ -71,6 +71,9 @@ class Recon {
   zr_status finish(uint32_t flags, const int64_t* counts);
   zr_result* take_result();           // ownership passes to the caller
   size_t device_bytes() const;
+  // multiply-accumulates of the next step (solves and probe evaluation),
+  // for scheduling; 0 when the reconstruction is not running
+  double next_cost() const;
   static size_t estimate_bytes(const zr_blackbox& bb, const zr_recon_params& prm);
   int steps() const { return steps_; }
   int redraws() const { return redraws_; }

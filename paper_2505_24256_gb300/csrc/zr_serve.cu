@@ -1,19 +1,27 @@
 // zr_serve.cu -- the serving loop: continuous batching of reconstructions.
 //
 // Requests (sparse polynomial or rational black boxes with their parameters)
-// are submitted from any thread.  A scheduler thread owns the context:
+// are submitted from any thread and routed by size to one of two lanes: small
+// requests (at most kSmallTerms hidden terms) to the fast lane, the rest to
+// the slow lane.  Each lane has its own context, stream and scheduler thread;
+// the fast lane's stream has the highest priority and the slow lane's solve
+// runs one CTA per work item, so the small requests' kernels get SMs between
+// the items of a large step instead of waiting for the whole step.  Per lane:
 //   * admission: a pending request starts when a slot is free and the device
-//     memory held by the active requests plus its estimate fits the budget
-//     (a request that cannot fit even alone runs when nothing else does);
-//     starting runs its dense step in x_0;
-//   * every tick gathers the next Zippel step of every active request -- their
-//     probes are generated on the device, then all steps run in one batch of
-//     launches (run_batch) -- reads back each request's own status word and
-//     term counts, and advances each request (or redraws its anchor);
+//     memory held by the active requests of both lanes plus its estimate fits
+//     the budget (a request that cannot fit even alone runs when nothing else
+//     does); starting runs its dense step in x_0;
+//   * every tick gathers the next Zippel step of the lane's active requests,
+//     oldest first, until the steps add up to kTickWork multiply-accumulates
+//     -- their probes are generated on the device, then all those steps run
+//     in one batch of launches (run_batch) -- reads back each request's own
+//     status word and term counts, and advances each request (or redraws its
+//     anchor);
 //   * finished requests leave their slot at once, so requests that arrive
 //     while others are on the GPU join at the next tick.
 // A request's result depends only on its own black box and seed, never on
-// the batch it ran in.  Skeletons and probe buffers stay on the device.
+// the lane or the batch it ran in.  Skeletons and probe buffers stay on the
+// device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,15 +79,35 @@ struct Done {
 
 }  // namespace
 
-struct zr_server {
+constexpr int64_t kSmallTerms = 2048;   // fast-lane requests: at most this many hidden terms
+// A tick takes active requests oldest first until their next steps add up to
+// this many multiply-accumulates (about 50 ms of the GPU), at least one: a
+// single large step already fills the GPU, so batching more large steps only
+// stretches every one of them, while small steps still share a tick.
+constexpr double kTickWork = 1e11;
+
+struct Lane {
   zr_ctx* ctx = nullptr;
+  bool own_ctx = false;
+  cudaStream_t stream = nullptr;
+  std::deque<Request> pending;
+  std::condition_variable cv_work;
+  std::thread th;
+  int active = 0;          // under the server mutex
+  size_t held = 0;         // device bytes of the lane's active requests (under the mutex)
+  uint32_t* d_status = nullptr;
+  uint32_t* h_status = nullptr;
+  int64_t* d_counts = nullptr;
+  int64_t* h_counts = nullptr;
+};
+
+struct zr_server {
   size_t budget = 0;
   int max_slots = 0;
-  std::thread th;
+  Lane lanes[2];
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_done;
   bool stop = false;
-  std::deque<Request> pending;
   std::unordered_map<uint64_t, Done> done;
   std::unordered_set<uint64_t> live;     // submitted, result not yet handed out
   uint64_t next_ticket = 1;
@@ -88,20 +116,15 @@ struct zr_server {
   int64_t submitted = 0, completed = 0, failed = 0, terms = 0, ticks = 0, batch_entries = 0;
   int max_active = 0;
   double t_first = -1, t_last = 0;
-  // device per-slot words
-  cudaStream_t stream = nullptr;
-  uint32_t* d_status = nullptr;
-  uint32_t* h_status = nullptr;
-  int64_t* d_counts = nullptr;
-  int64_t* h_counts = nullptr;
 };
 
-static void finish_request(zr_server* s, Active& a, zr_status st) {
+static void finish_request(zr_server* s, int li, Active& a, zr_status st) {
   zr_result* res = st == ZR_OK ? a.recon->take_result() : nullptr;
   const double t = now_ms();
   delete a.recon;
   a.recon = nullptr;
   std::lock_guard<std::mutex> g(s->mu);
+  s->lanes[li].active--;
   s->done[a.ticket] = Done{st, res, a.t_submit, t};
   if (st == ZR_OK) {
     s->completed++;
@@ -112,10 +135,12 @@ static void finish_request(zr_server* s, Active& a, zr_status st) {
   }
   s->t_last = t;
   s->cv_done.notify_all();
+  s->lanes[1 - li].cv_work.notify_one();   // memory and a slot came free
 }
 
-static void server_loop(zr_server* s) {
-  cudaSetDevice(s->ctx->device);
+static void server_loop(zr_server* s, int li) {
+  Lane& L = s->lanes[li];
+  cudaSetDevice(L.ctx->device);
   std::vector<Active> active;
   std::vector<int> free_slots;
   for (int i = s->max_slots - 1; i >= 0; i--) free_slots.push_back(i);
@@ -126,56 +151,74 @@ static void server_loop(zr_server* s) {
     std::vector<Request> admit;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty() || !active.empty(); });
-      if (s->stop && s->pending.empty() && active.empty()) break;
-      size_t held = 0;
-      for (auto& a : active) held += a.recon->device_bytes();
+      L.cv_work.wait(lk, [&] { return s->stop || !L.pending.empty() || !active.empty(); });
+      if (s->stop && L.pending.empty() && active.empty()) break;
+      size_t held = s->lanes[0].held + s->lanes[1].held;
+      const int busy = s->lanes[0].active + s->lanes[1].active;
       size_t planned = 0;
-      while (!s->pending.empty() && (int)(active.size() + admit.size()) < s->max_slots) {
-        Request& r = s->pending.front();
+      while (!L.pending.empty() && busy + (int)admit.size() < s->max_slots) {
+        Request& r = L.pending.front();
         r.bind();
         const size_t need = Recon::estimate_bytes(r.bb, r.prm);
-        const bool alone = active.empty() && admit.empty();
+        const bool alone = busy == 0 && admit.empty();
         if (!alone && held + planned + need > s->budget) break;
         planned += need;
         admit.push_back(std::move(r));
-        s->pending.pop_front();
+        L.pending.pop_front();
+      }
+      L.active += (int)admit.size();
+      L.held += planned;
+      s->max_active = std::max(s->max_active, s->lanes[0].active + s->lanes[1].active);
+      if (admit.empty() && active.empty()) {
+        // waiting for memory or slots the other lane holds: it notifies this
+        // lane when a request finishes; the timeout bounds a missed wake-up
+        L.cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        continue;
       }
     }
     for (auto& r : admit) {
       r.bind();
-      Active a{r.ticket, r.t_submit, free_slots.back(), new Recon(s->ctx, s->stream, r.bb, r.prm)};
+      Active a{r.ticket, r.t_submit, free_slots.back(), new Recon(L.ctx, L.stream, r.bb, r.prm)};
       free_slots.pop_back();
       const zr_status st = a.recon->start();
       if (st || a.recon->done()) {
         free_slots.push_back(a.slot);
-        finish_request(s, a, st);
+        finish_request(s, li, a, st);
       } else {
         active.push_back(a);
       }
     }
-    if (active.empty()) continue;
-    {
+    if (active.empty()) {
       std::lock_guard<std::mutex> g(s->mu);
-      s->max_active = std::max(s->max_active, (int)active.size());
+      L.held = 0;
+      continue;
     }
-    // one tick: the next step of every active request in one batch
+    // one tick: the next steps of the oldest active requests, up to kTickWork
+    // multiply-accumulates, in one batch
+    std::stable_sort(active.begin(), active.end(),
+                     [](const Active& x, const Active& y) { return x.t_submit < y.t_submit; });
     items.clear();
     in_batch.assign(active.size(), 0);
-    cudaMemsetAsync(s->d_status, 0, sizeof(uint32_t) * s->max_slots, s->stream);
+    std::vector<char> stepped(active.size(), 0);
+    cudaMemsetAsync(L.d_status, 0, sizeof(uint32_t) * s->max_slots, L.stream);
+    double work = 0;
     for (size_t i = 0; i < active.size(); i++) {
       Active& a = active[i];
-      const zr_status st = a.recon->prepare(items, s->d_status + a.slot, s->d_counts + 2 * a.slot);
+      const double c = a.recon->next_cost();
+      if (i > 0 && work + c > kTickWork) continue;
+      work += c;
+      stepped[i] = 1;
+      const zr_status st = a.recon->prepare(items, L.d_status + a.slot, L.d_counts + 2 * a.slot);
       in_batch[i] = st == ZR_OK;
     }
-    zr_status bst = run_batch(s->ctx, items.data(), (int)items.size(), s->ctx->d_status_call, s->stream);
-    cudaError_t e = cudaMemcpyAsync(s->h_status, s->d_status, sizeof(uint32_t) * s->max_slots, cudaMemcpyDeviceToHost,
-                                    s->stream);
+    zr_status bst = run_batch(L.ctx, items.data(), (int)items.size(), L.ctx->d_status_call, L.stream);
+    cudaError_t e = cudaMemcpyAsync(L.h_status, L.d_status, sizeof(uint32_t) * s->max_slots, cudaMemcpyDeviceToHost,
+                                    L.stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s->h_counts, s->d_counts, sizeof(int64_t) * 2 * s->max_slots, cudaMemcpyDeviceToHost,
-                          s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess && bst == ZR_OK) bst = cuda_err(s->ctx, e, "serve tick");
+      e = cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(int64_t) * 2 * s->max_slots, cudaMemcpyDeviceToHost,
+                          L.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+    if (e != cudaSuccess && bst == ZR_OK) bst = cuda_err(L.ctx, e, "serve tick");
     {
       std::lock_guard<std::mutex> g(s->mu);
       s->ticks++;
@@ -184,17 +227,39 @@ static void server_loop(zr_server* s) {
     std::vector<Active> still;
     for (size_t i = 0; i < active.size(); i++) {
       Active& a = active[i];
-      zr_status st = in_batch[i] ? (bst ? bst : a.recon->finish(s->h_status[a.slot], s->h_counts + 2 * a.slot))
+      if (!stepped[i]) {
+        still.push_back(a);
+        continue;
+      }
+      zr_status st = in_batch[i] ? (bst ? bst : a.recon->finish(L.h_status[a.slot], L.h_counts + 2 * a.slot))
                                  : a.recon->error();
       if (st || a.recon->done()) {
         free_slots.push_back(a.slot);
-        finish_request(s, a, st);
+        finish_request(s, li, a, st);
       } else {
         still.push_back(a);
       }
     }
     active.swap(still);
+    size_t held = 0;
+    for (auto& a : active) held += a.recon->device_bytes();
+    std::lock_guard<std::mutex> g(s->mu);
+    L.held = held;
   }
+}
+
+static void lane_free(Lane& L) {
+  if (L.d_status) cudaFree(L.d_status);
+  if (L.h_status) cudaFreeHost(L.h_status);
+  if (L.d_counts) cudaFree(L.d_counts);
+  if (L.h_counts) cudaFreeHost(L.h_counts);
+  if (L.stream) cudaStreamDestroy(L.stream);
+  if (L.own_ctx && L.ctx) zr_destroy(L.ctx);
+  L.d_status = L.h_status = nullptr;
+  L.d_counts = L.h_counts = nullptr;
+  L.stream = nullptr;
+  L.ctx = nullptr;
+  L.own_ctx = false;
 }
 
 extern "C" zr_status zr_serve_create(zr_ctx* ctx, size_t mem_budget, int32_t max_slots, zr_server** out) {
@@ -202,24 +267,34 @@ extern "C" zr_status zr_serve_create(zr_ctx* ctx, size_t mem_budget, int32_t max
   *out = nullptr;
   zr_server* s = new (std::nothrow) zr_server();
   if (!s) return ZR_ERR_OOM;
-  s->ctx = ctx;
   s->budget = mem_budget;
   s->max_slots = max_slots;
-  cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_status, sizeof(uint32_t) * max_slots);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_status, sizeof(uint32_t) * max_slots);
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_counts, sizeof(int64_t) * 2 * max_slots);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_counts, sizeof(int64_t) * 2 * max_slots);
-  if (e != cudaSuccess) {
-    if (s->d_status) cudaFree(s->d_status);
-    if (s->h_status) cudaFreeHost(s->h_status);
-    if (s->d_counts) cudaFree(s->d_counts);
-    if (s->h_counts) cudaFreeHost(s->h_counts);
-    if (s->stream) cudaStreamDestroy(s->stream);
-    delete s;
-    return cuda_err(ctx, e, "zr_serve_create");
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);   // lo: least, hi: greatest priority
+  zr_status r = ZR_OK;
+  for (int li = 0; li < 2 && e == cudaSuccess && !r; li++) {
+    Lane& L = s->lanes[li];
+    if (li == 0) {
+      L.ctx = ctx;
+    } else {
+      r = zr_create(ctx->M.p, &L.ctx);
+      if (r) break;
+      L.own_ctx = true;
+      L.ctx->solve_persistent = false;   // let the fast lane's kernels in between work items
+    }
+    e = cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, li == 0 ? hi : lo);
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_status, sizeof(uint32_t) * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&L.h_status, sizeof(uint32_t) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_counts, sizeof(int64_t) * 2 * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&L.h_counts, sizeof(int64_t) * 2 * max_slots);
   }
-  s->th = std::thread(server_loop, s);
+  if (e != cudaSuccess || r) {
+    for (auto& L : s->lanes) lane_free(L);
+    delete s;
+    return r ? r : cuda_err(ctx, e, "zr_serve_create");
+  }
+  for (int li = 0; li < 2; li++) s->lanes[li].th = std::thread(server_loop, s, li);
   *out = s;
   return ZR_OK;
 }
@@ -241,6 +316,7 @@ extern "C" zr_status zr_serve_submit(zr_server* s, const zr_request* req, uint64
     q.degD.assign(req->prm.degD, req->prm.degD + nv);
   }
   q.t_submit = now_ms();
+  const int li = (int64_t)req->bb.TN + (req->bb.kind == ZR_BB_RATIONAL ? req->bb.TD : 0) <= kSmallTerms ? 0 : 1;
   {
     std::lock_guard<std::mutex> g(s->mu);
     if (s->stop) return ZR_ERR_BUSY;
@@ -249,9 +325,11 @@ extern "C" zr_status zr_serve_submit(zr_server* s, const zr_request* req, uint64
     s->live.insert(q.ticket);
     if (s->t_first < 0) s->t_first = q.t_submit;
     s->submitted++;
-    s->pending.push_back(std::move(q));
+    s->lanes[li].pending.push_back(std::move(q));
   }
-  s->cv_work.notify_one();
+  s->lanes[li].cv_work.notify_one();
+  // the other lane may be waiting for memory this request no longer needs
+  s->lanes[1 - li].cv_work.notify_one();
   return ZR_OK;
 }
 
@@ -321,13 +399,10 @@ extern "C" void zr_serve_destroy(zr_server* s) {
     std::lock_guard<std::mutex> g(s->mu);
     s->stop = true;
   }
-  s->cv_work.notify_all();
-  if (s->th.joinable()) s->th.join();
+  for (auto& L : s->lanes) L.cv_work.notify_all();
+  for (auto& L : s->lanes)
+    if (L.th.joinable()) L.th.join();
   for (auto& kv : s->done) zr_result_free(kv.second.res);
-  cudaFree(s->d_status);
-  cudaFreeHost(s->h_status);
-  cudaFree(s->d_counts);
-  cudaFreeHost(s->h_counts);
-  cudaStreamDestroy(s->stream);
+  for (auto& L : s->lanes) lane_free(L);
   delete s;
 }

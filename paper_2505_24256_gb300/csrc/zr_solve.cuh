@@ -246,7 +246,8 @@ static void launch_solve_t(const BDesc* Ds, const int4* items, int nitems, int s
   using C = SolveCfg<CG, G>;
   static int per_sm = 0;
   if (!per_sm) per_sm = solve_occupancy_t<CG, G>();   // also sets the shared-memory attribute
-  const int grid = nitems < sms * per_sm ? nitems : sms * per_sm;   // persistent: one wave walks the work list
+  // persistent: one wave walks the work list; sms <= 0: one CTA per item
+  const int grid = (sms <= 0 || nitems < sms * per_sm) ? nitems : sms * per_sm;
   if (grid > 0) { k_solve<CG, G><<<grid, C::NT, C::SMEM, st>>>(Ds, items, nitems, M); note_launch(); }
 }
 
