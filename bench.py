@@ -115,6 +115,25 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The maximum of x over all ranks (the slowest rank's time); x itself
+    on one rank.  Every rank must call it."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas: every rank processes the same units)."""
+    return world * units_per_rank / seconds_max
+
+
 def cpu_baseline_step(wl, nthreads=0):
     """The oracle's step on the full workload (probes from the oracle, untimed)."""
     import oracle
@@ -304,11 +323,7 @@ def run_zr(args):
     solve_ms, solve_n = ctx.profile_query("solve")
     phases = {ph: ctx.profile_query(ph)[0] / max(args.steps, 1) for ph in zr.Context.PHASES[:7]}
     ctx.profile(False)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     # the output of the last timed step against generator truth
     ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
         np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
@@ -329,10 +344,7 @@ def run_zr(args):
         ne = ctx.zippel_step_host(hskel, k, h_y, S, h_cs, h_b, T, 0, h_oe, h_oc, cap)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_ok = ne == wl.exps.shape[0] and np.array_equal(h_oc[:ne].numpy().view(np.uint64), wl.coef)
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
 
     # the plain form on the same GPU: one single-right-hand-side system per
     # launch sequence (S of them), then Newton; probes and nodes as above
@@ -393,7 +405,7 @@ def run_zr(args):
     W = (S + 2.5) * T * T
     line = {
         "metric": METRIC,
-        "value": world * T * args.steps / (total_ms / 1e3),
+        "value": job_rate(T * args.steps, world, total_ms / 1e3),
         "unit": "terms/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -418,7 +430,7 @@ def run_zr(args):
         "phase_ms": phases,
         "plan": {"s_tile": plan[0], "k_blocks": plan[1]},
         "probe_gen_ms": probe_ms,
-        "e2e": {"value": world * T / e2e_s, "unit": "terms/s",
+        "e2e": {"value": job_rate(T, world, e2e_s), "unit": "terms/s",
                 "h2d_bytes_per_step": T * nv + 8 * k + 8 * S + 8 * S * T,
                 "d2h_bytes_per_step": ne * (nv + 8) + 12},
         "gpu_launches": int(launches),

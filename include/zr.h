@@ -91,6 +91,13 @@ zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t
  *                  precomputed quotient (Sec. 2.1)
  *   imad_lo_per_s, imad_hi_per_s   32-bit mad.lo / mad.hi
  * Synchronous; uses the context workspace. */
+/* Self-check of the bounded device waits (the paper has no counterpart):
+ * one warp waits on a shared-memory barrier that nothing arrives on, gives
+ * up after `tries` tries and reports it, exactly as the solve's pipeline
+ * does after its own limit.  Returns ZR_ERR_TIMEOUT when the mechanism works
+ * (the context stays usable); synchronous. */
+zr_status zr_check_bounded_wait(zr_ctx* ctx, uint32_t tries, void* stream);
+
 typedef struct zr_peaks {
   double mac_per_s, chain_per_s, imad_lo_per_s, imad_hi_per_s;
   int32_t sms, pad;

@@ -688,3 +688,11 @@ extern "C" zr_status zr_zippel_step_host(zr_ctx* ctx, const zr_poly* skel, int32
   }
   return ZR_OK;
 }
+
+extern "C" zr_status zr_check_bounded_wait(zr_ctx* ctx, uint32_t tries, void* stream) {
+  if (!ctx || tries < 1) return ZR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
+  launch_wait_check(tries, ctx->d_status_call, st);
+  return finish_sync_call(ctx, st, nullptr);
+}

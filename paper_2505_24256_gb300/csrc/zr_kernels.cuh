@@ -62,6 +62,7 @@ void launch_shoup_pre(int64_t T, const uint64_t* v, const Mod& M, uint64_t* vp, 
                       cudaStream_t st);
 void launch_node_check(int64_t T, const uint64_t* v, uint64_t* htab, uint64_t hmask, uint32_t* status, cudaStream_t st);
 // batched carry and solve (zr_solve.cu)
+void launch_wait_check(uint32_t limit, uint32_t* status, cudaStream_t st);
 void launch_b_carry(const BDesc* Ds, const int64_t* pre, int n, int64_t nctas, const Mod& M, cudaStream_t st);
 // false when no solve kernel is built for (s_tile, groups): nothing launched
 bool launch_b_solve(int s_tile, int groups, const BDesc* Ds, const int4* items, int nitems, int sms, const Mod& M,

@@ -33,6 +33,24 @@ __global__ void __launch_bounds__(256) k_b_carry(const BDesc* __restrict__ Ds, c
   D.R[(int64_t)(kb - 1) * D.T + j] = canon(r, M);
 }
 
+// ---------------------------------------------------------------------------
+// Self-check of the bounded waits: one warp waits on an mbarrier that nothing
+// arrives on; the wait must give up after `limit` tries and report
+// ST_TIMEOUT, and the kernel must return.
+// ---------------------------------------------------------------------------
+
+__global__ void k_wait_check(uint32_t limit, uint32_t* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x < 32 && !mbar_wait(&bar, 0, limit) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+void launch_wait_check(uint32_t limit, uint32_t* status, cudaStream_t st) {
+  k_wait_check<<<1, 64, 0, st>>>(limit, status);
+  note_launch();
+}
+
 void launch_b_carry(const BDesc* Ds, const int64_t* pre, int n, int64_t nctas, const Mod& M, cudaStream_t st) {
   if (nctas > 0) { k_b_carry<<<(unsigned)nctas, 256, 0, st>>>(Ds, pre, n, M); note_launch(); }
 }

@@ -115,6 +115,7 @@ SIGNATURES = {
     "zr_reconstruct": (_ST, [_V, _P, _P, ctypes.POINTER(ctypes.POINTER(zr_result)), _V]),
     "zr_result_free": (None, [ctypes.POINTER(zr_result)]),
     "zr_measure_peaks": (_ST, [_V, _P, _V]),
+    "zr_check_bounded_wait": (_ST, [_V, ctypes.c_uint32, _V]),
     "zr_step_graph_create": (_ST, [_V, _I32, _P, _V, ctypes.POINTER(_V)]),
     "zr_step_graph_launch": (_ST, [_V, _V]),
     "zr_step_graph_status": (_ST, [_V, _V]),
@@ -199,6 +200,10 @@ class Context:
         if st != OK:
             msg = self.L.zr_last_error(self._h).decode(errors="replace")
             raise ZrError(st, f"{what}: {msg}")
+
+    def check_bounded_wait(self, tries=4096, stream=None) -> int:
+        """Status of a device wait that nothing completes (TIMEOUT when it gives up as designed)."""
+        return int(self.L.zr_check_bounded_wait(self._h, tries, _stream(stream)))
 
     def measure_peaks(self, stream=None) -> dict:
         """Measured MAC / chain-step / IMAD rates (operations per second)."""
