@@ -286,6 +286,7 @@ StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D) {
   w.htab = cv.take<uint64_t>(hash_slots(T));
   w.m = cv.take<uint64_t>(Tn);
   w.tmp = cv.take<uint64_t>(2 * Tn);
+  w.tpart = cv.take<uint64_t>((size_t)tree_split_max(Tn) * Tn);
   w.R = cv.take<uint64_t>((size_t)(D.NB > 1 ? D.NB - 1 : 1) * Tn);
   w.part = cv.take<uint64_t>((size_t)D.NB * S * Tn);
   w.denp = cv.take<uint64_t>((size_t)D.NB * Tn);

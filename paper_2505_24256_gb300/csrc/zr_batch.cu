@@ -99,53 +99,111 @@ __global__ void __launch_bounds__(1 << kTreeL1) k_b_tree_leaf(const BDesc* __res
   for (int t = threadIdx.x; t < cnt; t += blockDim.x) out[base + t] = buf[cur][t];
 }
 
-constexpr int kNO = 64, kNS = 4, kIC = 256;
-__global__ void __launch_bounds__(kNO* kNS) k_b_tree_level(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
-                                                           int n, int l, Mod M) {
-  __shared__ uint64_t As[kIC];
-  __shared__ uint64_t Bw[kIC + kNO];
-  __shared__ uint64_t red[kNS][kNO];
+// Levels >= kTreeL1: each pair (A, B) of sibling polynomials (monic, leading
+// 1 implicit) is multiplied by a schoolbook convolution.  A CTA owns up to
+// kTNO consecutive output coefficients of one pair; thread t keeps kTR of them
+// (t, t + NT, .. : conflict-free shared-memory reads) in 160-bit accumulators,
+// so every staged A coefficient feeds kTR multiply-accumulates.  When a level
+// has too few output tiles to fill the GPU, the inner (A) range is split over
+// gridDim.y CTAs whose partial sums a second kernel adds.
+constexpr int kTR = 4;
+constexpr int kTNO = 512;
+constexpr int kTIC = 256;
+
+__host__ __device__ inline int tree_tile(int l) {
+  const int pair = 2 << l;
+  return pair < kTNO ? pair : kTNO;
+}
+
+__device__ __forceinline__ void tree_bufs(const BDesc& D, int l, const uint64_t*& in, uint64_t*& out) {
+  const bool even = ((l - kTreeL1) & 1) == 0;
+  in = even ? D.tmp : D.tmp + D.T;
+  out = (l == D.levels - 1) ? D.m : (even ? D.tmp + D.T : D.tmp);
+}
+
+__global__ void __launch_bounds__(kTNO / kTR) k_b_tree_conv(const BDesc* __restrict__ Ds,
+                                                            const int64_t* __restrict__ pre, int n, int l, int split,
+                                                            Mod M) {
+  __shared__ uint64_t As[kTIC];
+  __shared__ uint64_t Bs[kTIC + kTNO];
   const int i = seg_of(pre, n, blockIdx.x);
   const BDesc& D = Ds[i];
   const int64_t T = D.T;
-  const int64_t t0 = (int64_t)(blockIdx.x - pre[i]) * kNO;
-  const bool even = ((l - kTreeL1) & 1) == 0;
-  const uint64_t* in = even ? D.tmp : D.tmp + T;
-  uint64_t* out = (l == D.levels - 1) ? D.m : (even ? D.tmp + T : D.tmp);
+  const int NO = tree_tile(l), NT = NO / kTR;
+  const int64_t t0 = (int64_t)(blockIdx.x - pre[i]) * NO;
+  const uint64_t* in;
+  uint64_t* out;
+  tree_bufs(D, l, in, out);
+  uint64_t* dst = split > 1 ? D.tpart + (int64_t)blockIdx.y * T : out;
   const int64_t size = 1ll << l, pair = 2ll << l;
   const int64_t po = t0 & ~(pair - 1);
-  const int tid = threadIdx.x, o = tid % kNO, sl = tid / kNO;
-  if (T - po <= size) {
-    if (sl == 0 && t0 + o < T) out[t0 + o] = in[t0 + o];
+  const int tid = threadIdx.x;
+  if (T - po <= size) {   // no sibling: the coefficients pass through
+#pragma unroll
+    for (int r = 0; r < kTR; r++) {
+      const int64_t x = t0 + tid + NT * r;
+      if (x < T) dst[x] = blockIdx.y == 0 ? in[x] : 0;
+    }
     return;
   }
   const int64_t a = size, b = (T - po - size) < size ? (T - po - size) : size;
-  const int64_t n0 = t0 - po;
+  const int64_t n0 = t0 - po;                                           // first output of the tile
   const int64_t ilo = n0 - b > 0 ? n0 - b : 0;
-  const int64_t ihi = (n0 + kNO - 1) < a ? (n0 + kNO - 1) : a;
-  Acc3 acc = {0, 0, 0};
-  for (int64_t i0 = ilo; i0 <= ihi; i0 += kIC) {
+  const int64_t ihi = (n0 + NO - 1) < a ? (n0 + NO - 1) : a;            // inclusive; A_a = 1
+  const int64_t per = (ihi - ilo + split) / split;
+  const int64_t slo = ilo + per * blockIdx.y;
+  const int64_t shi = (slo + per - 1) < ihi ? (slo + per - 1) : ihi;
+  Acc8 acc[kTR];
+#pragma unroll
+  for (int r = 0; r < kTR; r++) acc[r] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i0 = slo; i0 <= shi; i0 += kTIC) {
+    const int64_t i1 = (i0 + kTIC - 1) < shi ? (i0 + kTIC - 1) : shi;  // inclusive
+    const int ic = (int)(i1 - i0 + 1);
+    const int64_t jlo = n0 - i1;                                        // smallest B index of the chunk
     __syncthreads();
-    for (int t = tid; t < kIC; t += blockDim.x) {
+    for (int t = tid; t < ic; t += NT) {
       const int64_t ii = i0 + t;
-      As[t] = (ii < a) ? in[po + ii] : (ii == a ? 1 : 0);
+      As[t] = ii < a ? in[po + ii] : 1;
     }
-    const int64_t jlo = n0 - i0 - kIC + 1;
-    for (int t = tid; t < kIC + kNO - 1; t += blockDim.x) {
+    for (int t = tid; t < NO + ic - 1; t += NT) {
       const int64_t jj = jlo + t;
-      Bw[t] = (jj < 0 || jj > b) ? 0 : (jj == b ? 1 : in[po + a + jj]);
+      Bs[t] = (jj < 0 || jj > b) ? 0 : (jj == b ? 1 : in[po + a + jj]);
     }
     __syncthreads();
-    for (int t = sl; t < kIC; t += kNS) mac128(acc, As[t], Bw[o - t + kIC - 1]);
+    // output n = n0 + tid + NT r takes A_{i0+t} B_{n-i0-t} = As[t] Bs[tid + NT r + ic - 1 - t]
+    const uint64_t* bw = Bs + tid + ic - 1;
+    for (int t = 0; t < ic; t++) {
+      const uint64_t x = As[t];
+      const uint32_t x0 = lo32(x), x1 = hi32(x);
+#pragma unroll
+      for (int r = 0; r < kTR; r++) {
+        const uint64_t w = bw[NT * r - t];
+        mac8(acc[r], lo32(w), hi32(w), x0, x1);
+      }
+    }
   }
-  __syncthreads();
-  red[sl][o] = acc3_value(acc, M);
-  __syncthreads();
-  if (sl == 0 && t0 + o < T) {
-    uint64_t s = red[0][o];
-    for (int q = 1; q < kNS; q++) s = add_mod(s, red[q][o], M);
-    out[t0 + o] = s;
+#pragma unroll
+  for (int r = 0; r < kTR; r++) {
+    const int64_t nn = n0 + tid + NT * r;
+    if (nn < a + b) dst[po + nn] = acc8_value(acc[r], M);
   }
+}
+
+// out = sum of the split partials, for the entries that have level l
+__global__ void k_b_tree_combine(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre, int n, int l,
+                                 int split, Mod M) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pre[n]) return;
+  const int i = seg_of(pre, n, x);
+  const BDesc& D = Ds[i];
+  if (D.levels <= l) return;
+  const int64_t j = x - pre[i];
+  const uint64_t* in;
+  uint64_t* out;
+  tree_bufs(D, l, in, out);
+  uint64_t s = 0;
+  for (int y = 0; y < split; y++) s = add_mod(s, D.tpart[(int64_t)y * D.T + j], M);
+  out[j] = s;
 }
 
 // ---- a4/a6: finish ---------------------------------------------------------------
@@ -384,7 +442,7 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
   push_prefix(P.pre, c_nblk, P.o_nblk);
   for (int l = kTreeL1; l < P.lmax; l++) {
     std::vector<int64_t> c(n);
-    for (int i = 0; i < n; i++) c[i] = tree_levels(items[i].T) > l ? (items[i].T + kNO - 1) / kNO : 0;
+    for (int i = 0; i < n; i++) c[i] = tree_levels(items[i].T) > l ? (items[i].T + tree_tile(l) - 1) / tree_tile(l) : 0;
     size_t o;
     push_prefix(P.pre, c, o);
     P.o_lvl.push_back(o);
@@ -476,6 +534,7 @@ static zr_status stage_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_
     d.m = w.m;
     d.tmp = w.tmp;
     d.R = w.R;
+    d.tpart = w.tpart;
     d.part = w.part;
     d.denp = w.denp;
     d.invd = w.invd;
@@ -561,7 +620,22 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   for (int l = kTreeL1; l < lmax; l++) {
     const size_t o = o_lvl[l - kTreeL1];
     const int64_t nt = pre[o + n];
-    if (nt) { k_b_tree_level<<<(unsigned)nt, kNO * kNS, 0, st>>>(dD, dpre + o, n, l, M); note_launch(); }
+    if (!nt) continue;
+    // split the inner range when the level has fewer than ~4 tiles per SM,
+    // within every participating entry's partial-sum capacity
+    const int64_t want = 4ll * (ctx->sms ? ctx->sms : 152);
+    int split = (int)((want + nt - 1) / nt);
+    for (int i = 0; i < n; i++)
+      if (tree_levels(P.plan[i].T) > l) split = std::min(split, (int)tree_split_max(P.plan[i].T));
+    split = std::max(1, std::min(split, 16));
+    {
+      k_b_tree_conv<<<dim3((unsigned)nt, (unsigned)split), tree_tile(l) / kTR, 0, st>>>(dD, dpre + o, n, l, split, M);
+      note_launch();
+    }
+    if (split > 1) {
+      k_b_tree_combine<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, l, split, M);
+      note_launch();
+    }
   }
   cudaEvent_t e2 = mark();
   // a4 + a5

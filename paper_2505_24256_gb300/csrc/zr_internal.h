@@ -90,7 +90,7 @@ uint64_t hash_slots(int64_t T);
 
 // Workspace of one step or system (carved in the context workspace).
 struct StepWs {
-  uint64_t *tab, *v, *vp, *htab, *m, *tmp, *R, *part, *denp, *invd, *g;
+  uint64_t *tab, *v, *vp, *htab, *m, *tmp, *tpart, *R, *part, *denp, *invd, *g;
   int32_t* cnt;
   int64_t* bsum;
 };

@@ -47,7 +47,7 @@ struct BDesc {
   int32_t S, k, nv, offset, mode, NB, s_tile, nst, levels, pad;
   const uint8_t* exps;
   const uint64_t *y, *xs, *b;
-  uint64_t *tab, *v, *vp, *htab, *m, *tmp, *R, *part, *denp, *invd, *g, *c;
+  uint64_t *tab, *v, *vp, *htab, *m, *tmp, *tpart, *R, *part, *denp, *invd, *g, *c;
   int32_t* cnt;
   int64_t *bsum, *out_count;
   uint8_t* out_exps;
@@ -80,5 +80,10 @@ void launch_newton(int64_t nterms, int npts, const uint64_t* W, const uint64_t* 
                    uint64_t* coef, cudaStream_t st);
 size_t newton_smem(int S);   // dynamic shared memory of one 128-term block
 int64_t scan_blocks(int64_t n);  // number of 128-term compaction blocks
+// split partials the product tree may use for T leaves (words = that x T)
+inline int64_t tree_split_max(int64_t T) {
+  const int64_t s = T > 0 ? (4 * 152 * 512 + T - 1) / T : 1;
+  return s < 1 ? 1 : (s > 16 ? 16 : s);
+}
 
 }  // namespace zr
