@@ -373,6 +373,9 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
   if (ctx->h_count) cudaFreeHost(ctx->h_count);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->stage_event) cudaEventDestroy(ctx->stage_event);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   delete ctx;
 }
 

@@ -609,6 +609,28 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   const int64_t ncarry = pre[o_carry + n];
   // entries with T = 0 report an empty skeleton
   for (int64_t* c : SB.zero_counts) cudaMemsetAsync(c, 0, 8, st);
+  // Newton's matrix W depends only on the samples: build it on the side
+  // stream while the tree, carries and solve run (joined before the finish)
+  bool side = false;
+  if (mode == 0 && nroots) {
+    if (!ctx->side) cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (!ctx->ev_fork) cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (!ctx->ev_join) cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (ctx->side && ctx->ev_fork && ctx->ev_join) {
+      static bool configured = false;
+      if (!configured) {
+        cudaFuncSetAttribute(k_b_newton_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(8 * newton_table_words(kNewtonMax)));
+        configured = true;
+      }
+      cudaEventRecord(ctx->ev_fork, st);
+      cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+      k_b_newton_table<<<n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), ctx->side>>>(dD, M);
+      note_launch();
+      cudaEventRecord(ctx->ev_join, ctx->side);
+      side = true;
+    }
+  }
   cudaEvent_t e0 = mark();
   // a2
   if (nhash) { k_b_fill_hash<<<cdiv(nhash, 256), 256, 0, st>>>(dD, dpre + o_hash, n); note_launch(); }
@@ -657,7 +679,8 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
                              (int)newton_smem(kNewtonMax));
         configured = true;
       }
-      {
+      if (side) cudaStreamWaitEvent(st, ctx->ev_join, 0);   // W of every entry (forked above)
+      else {
         k_b_newton_table<<<n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), st>>>(dD, M);
         note_launch();
       }

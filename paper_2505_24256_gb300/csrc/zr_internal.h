@@ -52,6 +52,10 @@ struct zr_ctx {
   // one CTA per work item, which lets higher-priority streams take SMs
   // between items (the serving loop's lane of large requests)
   bool solve_persistent = true;
+  // side stream of a step batch (work that depends only on the samples runs
+  // there, overlapping the tree and the solve), with its fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
   std::mutex mu;                // guards err for the serve thread
 };
