@@ -9,10 +9,11 @@
 //     u_t = prod_{m<k} y_m^{e_{t,m}},  w_{t,s} = coef_t c_s^{e_{t,k}} prod_{m>k} z_m^{e_{t,m}}.
 // Terms with equal u are merged first (their w are added), which turns the
 // evaluation into a transposed Vandermonde product over the G distinct u.
-// The kernel tiles it: a CTA owns 256 consecutive i and walks the groups in
-// chunks; for each chunk it builds the table X[g][t] = u_g^(I0+off+t) in
-// shared memory by doubling (the paper's stride-k power table, Sec. 2.2) and
-// every thread accumulates sum_g w_{g,s} X[g][t] with the deferred MAC.
+// The kernel tiles it: a CTA owns a range of consecutive i and walks the
+// groups in chunks; for each chunk it builds the table X[g][t] = u_g^(I0+off+t)
+// in shared memory by doubling (the paper's stride-k power table, Sec. 2.2)
+// and its thread groups accumulate sum_g w_{g,s} X[g][t] for their columns
+// with the deferred multiply-accumulate.
 #include <cuda_runtime.h>
 
 #include "zr_internal.h"
@@ -143,9 +144,10 @@ __global__ void k_eval_accum(int64_t Tf, int S, const uint64_t* __restrict__ u, 
   }
 }
 
-// finalize: W in MAC form and the squares table UP[g][a] = u_g^(2^a), a < 32
+// finalize: the merged weights as residues and the squares table
+// UP[g][a] = u_g^(2^a), a < 32
 __global__ void k_eval_finalize(int64_t G, int S, const unsigned long long* __restrict__ Wacc,
-                                const uint64_t* __restrict__ U, Mod M, BX* __restrict__ Wbx,
+                                const uint64_t* __restrict__ U, Mod M, uint64_t* __restrict__ Wp,
                                 uint64_t* __restrict__ UP) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < G * S) {
@@ -153,7 +155,7 @@ __global__ void k_eval_finalize(int64_t G, int S, const unsigned long long* __re
     // value = hi 2^32 + lo, as a 128-bit number
     uint64_t vlo = lo + (hi << 32);
     uint64_t vhi = (hi >> 32) + (vlo < lo);
-    Wbx[idx] = make_bx(reduce128(vhi, vlo, M), M);
+    Wp[idx] = reduce128(vhi, vlo, M);
   }
   if (idx < G) {
     uint64_t x = U[idx];
@@ -164,94 +166,105 @@ __global__ void k_eval_finalize(int64_t G, int S, const unsigned long long* __re
   }
 }
 
-constexpr int kNI = 256, kGC = 32;
+constexpr int kGC = 32;   // groups per staged chunk
 
-template <int ST>
+// The matrix-vector product out[s][i] = sum_g W[g][s] u_g^(i+off): a CTA owns
+// NI consecutive i and NG thread groups of NI threads; group q accumulates
+// the ST columns q ST .. q ST + ST - 1 for its thread's i.  Per chunk of kGC
+// groups the CTA stages the weights and builds X[g][t] = u_g^(I0+off+t) by
+// doubling (the paper's power table), shared by all NG groups; every thread
+// then runs ST deferred multiply-accumulates per group, X[g][t] times a
+// broadcast pair of weights.
+template <int ST, int NG, int NI>
+struct EvalCfg {
+  static constexpr int STP = (ST + 1) & ~1;
+  static constexpr int NT = NI * NG;
+  static constexpr int WW = NG * STP;
+  static constexpr int MINB = NT <= 448 ? 2 : 1;   // two CTAs per SM where the registers allow
+};
+
+template <int ST, int NG, int NI>
 struct EvalSmem {
-  uint64_t X[kGC][kNI];
-  uint4 W[kGC][ST][2];
-  uint64_t base[kGC];
+  uint64_t X[kGC][NI];
+  uint64_t W[kGC][EvalCfg<ST, NG, NI>::WW];
   uint64_t part[kGC][8];
 };
 
-template <int ST>
-__global__ void __launch_bounds__(kNI) k_eval_matvec(int64_t T, int S, int offset, int64_t G, int gsplit,
-                                                     const uint64_t* __restrict__ UP, const BX* __restrict__ Wbx,
-                                                     Mod M, uint64_t* __restrict__ out, int64_t ldo,
-                                                     uint64_t* __restrict__ partial) {
+template <int ST, int NG, int NI>
+__global__ void __launch_bounds__(NI* NG, EvalCfg<ST, NG, NI>::MINB) k_eval_matvec(int64_t T, int S, int offset, int64_t G, int gsplit,
+                                                           const uint64_t* __restrict__ UP,
+                                                           const uint64_t* __restrict__ Wp, Mod M,
+                                                           uint64_t* __restrict__ out, int64_t ldo,
+                                                           uint64_t* __restrict__ partial) {
+  using C = EvalCfg<ST, NG, NI>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  EvalSmem<ST>& sm = *reinterpret_cast<EvalSmem<ST>*>(smraw);
-  const int tid = threadIdx.x;
-  const int64_t I0 = (int64_t)blockIdx.x * kNI;
+  EvalSmem<ST, NG, NI>& sm = *reinterpret_cast<EvalSmem<ST, NG, NI>*>(smraw);
+  const int tid = threadIdx.x, li = tid % NI, grp = tid / NI;
+  const int64_t I0 = (int64_t)blockIdx.x * NI;
   const int split = blockIdx.y;
-  const int s0 = blockIdx.z * ST;
-  const int sn = (S - s0) < ST ? (S - s0) : ST;
   const int64_t glo = G * split / gsplit, ghi = G * (split + 1) / gsplit;
   const uint64_t E = (uint64_t)(I0 + offset);
-  Acc acc[ST];
+  Acc8 acc[ST];
 #pragma unroll
-  for (int s = 0; s < ST; s++) acc[s].L = acc[s].H = 0;
-  int fold = 0;
+  for (int c = 0; c < ST; c++) acc[c] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t gc = glo; gc < ghi; gc += kGC) {
     const int gn = (ghi - gc) < kGC ? (int)(ghi - gc) : kGC;
     __syncthreads();
-    // base_g = u_g^E = prod over the set bits of E of UP[g][a]; 8 threads per group
-    {
-      const int g = tid >> 3, part = tid & 7;
+    // base_g = u_g^E = prod over the set bits of E of UP[g][a]; 8 parts per group
+    for (int t = tid; t < kGC * 8; t += C::NT) {
+      const int g = t >> 3, pt = t & 7;
       uint64_t prod = 1;
       if (g < gn)
-        for (int a = part; a < 32; a += 8)
+        for (int a = pt; a < 32; a += 8)
           if ((E >> a) & 1) prod = mul_mod(prod, UP[(gc + g) * 32 + a], M);
-      sm.part[g][part] = prod;
+      sm.part[g][pt] = prod;
     }
-    // weights of the chunk (MAC form), zero padded
-    for (int t = tid; t < kGC * ST * 2; t += kNI) {
-      int g = t / (ST * 2), r = t - g * ST * 2, s = r >> 1, h = r & 1;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (g < gn && s < sn) val = reinterpret_cast<const uint4*>(Wbx + (gc + g) * S + s0 + s)[h];
-      sm.W[g][s][h] = val;
+    // weights of the chunk, [g][group][column], zero padded
+    for (int t = tid; t < kGC * C::WW; t += C::NT) {
+      const int g = t / C::WW, r = t - g * C::WW, q = r / C::STP, c = r - q * C::STP, sidx = q * ST + c;
+      sm.W[g][r] = (g < gn && c < ST && sidx < S) ? Wp[(gc + g) * S + sidx] : 0;
     }
     __syncthreads();
-    if (tid < kGC) {
+    for (int g = tid; g < kGC; g += C::NT) {
       uint64_t b = 1;
-      if (tid < gn)
-        for (int q = 0; q < 8; q++) b = mul_mod(b, sm.part[tid][q], M);
-      sm.base[tid] = b;
-      sm.X[tid][0] = b;
+      for (int q = 0; q < 8; q++) b = mul_mod(b, sm.part[g][q], M);
+      sm.X[g][0] = b;
     }
     __syncthreads();
     // doubling: X[g][t + 2^a] = X[g][t] u_g^(2^a)
-    for (int a = 0; (1 << a) < kNI; a++) {
+    for (int a = 0; (1 << a) < NI; a++) {
       const int half = 1 << a;
-      for (int idx = tid; idx < kGC * half; idx += kNI) {
+      for (int idx = tid; idx < kGC * half; idx += C::NT) {
         const int g = idx / half, t = idx - g * half;
         if (g < gn) sm.X[g][t + half] = mul_mod(sm.X[g][t], UP[(gc + g) * 32 + a], M);
       }
       __syncthreads();
     }
     for (int g = 0; g < gn; g++) {
-      const XL x = limbs21(sm.X[g][tid]);
+      const uint64_t x = sm.X[g][li];
+      const uint32_t x0 = lo32(x), x1 = hi32(x);
+      const uint64_t* row = &sm.W[g][grp * C::STP];
 #pragma unroll
-      for (int s = 0; s < ST; s++) {
-        const uint4 b0 = sm.W[g][s][0];
-        const uint4 b1 = sm.W[g][s][1];
-        mac(acc[s], x, b0, make_uint2(b1.x, b1.y));
+      for (int c = 0; c + 1 < ST; c += 2) {
+        const uint4 w = *reinterpret_cast<const uint4*>(row + c);
+        mac8(acc[c], x0, x1, w.x, w.y);
+        mac8(acc[c + 1], x0, x1, w.z, w.w);
       }
-      if (++fold == MAC_FOLD) {
-#pragma unroll
-        for (int s = 0; s < ST; s++) acc_fold(acc[s], M);
-        fold = 0;
+      if (ST & 1) {
+        const uint2 w = *reinterpret_cast<const uint2*>(row + ST - 1);
+        mac8(acc[ST - 1], x0, x1, w.x, w.y);
       }
     }
   }
-  const int64_t i = I0 + tid;
+  const int64_t i = I0 + li;
   if (i >= T) return;
 #pragma unroll
-  for (int s = 0; s < ST; s++) {
-    if (s >= sn) continue;
-    uint64_t r = acc_value(acc[s], M);
-    if (gsplit == 1) out[(int64_t)(s0 + s) * ldo + i] = r;
-    else partial[((int64_t)split * S + s0 + s) * T + i] = r;
+  for (int c = 0; c < ST; c++) {
+    const int sidx = grp * ST + c;
+    if (sidx >= S) continue;
+    const uint64_t r = acc8_value(acc[c], M);
+    if (gsplit == 1) out[(int64_t)sidx * ldo + i] = r;
+    else partial[((int64_t)split * S + sidx) * T + i] = r;
   }
 }
 
@@ -266,26 +279,63 @@ __global__ void k_eval_combine(int64_t T, int S, int gsplit, const uint64_t* __r
   out[(int64_t)s * ldo + i] = r;
 }
 
-template <int ST>
-static void launch_matvec_t(int64_t T, int S, int offset, int64_t G, int gsplit, const uint64_t* UP, const BX* Wbx,
-                            const Mod& M, uint64_t* out, int64_t ldo, uint64_t* partial, cudaStream_t st) {
-  const size_t smem = sizeof(EvalSmem<ST>);
+template <int ST, int NG, int NI>
+static void launch_matvec_t(int64_t T, int S, int offset, int64_t G, int gsplit, const uint64_t* UP,
+                            const uint64_t* Wp, const Mod& M, uint64_t* out, int64_t ldo, uint64_t* partial,
+                            cudaStream_t st) {
+  const size_t smem = sizeof(EvalSmem<ST, NG, NI>);
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_eval_matvec<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_eval_matvec<ST, NG, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  dim3 grid(cdiv(T, kNI), gsplit, cdiv(S, ST));
-  { k_eval_matvec<ST><<<grid, kNI, smem, st>>>(T, S, offset, G, gsplit, UP, Wbx, M, out, ldo, partial); note_launch(); }
+  dim3 grid(cdiv(T, NI), gsplit);
+  {
+    k_eval_matvec<ST, NG, NI><<<grid, NI * NG, smem, st>>>(T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial);
+    note_launch();
+  }
 }
 
-static int eval_tile(int S) {
-  static const int tiles[] = {4, 8, 9, 12, 16, 21};
-  int nst = (S + 20) / 21;
-  int want = (S + nst - 1) / nst;
-  for (int t : tiles)
-    if (t >= want) return t;
-  return 21;
+// Launch shape by S: (columns per thread, thread groups, i per CTA).
+struct EvalShape {
+  int st, ng, ni;
+};
+static EvalShape eval_shape(int S) {
+  // four (or three) columns per thread keep a thread within ~90 registers
+  if (S <= 4) return {4, 1, 128};
+  if (S <= 8) return {4, 2, 128};
+  if (S <= 16) return {4, 4, 64};
+  if (S <= 21) return {3, 7, 64};
+  if (S <= 24) return {4, 6, 64};
+  if (S <= 44) return {4, 11, 32};
+  return {4, 16, 32};
+}
+
+static void launch_matvec(const EvalShape& sh, int64_t T, int S, int offset, int64_t G, int gsplit,
+                          const uint64_t* UP, const uint64_t* Wp, const Mod& M, uint64_t* out, int64_t ldo,
+                          uint64_t* partial, cudaStream_t st) {
+#define ZR_MV(A, B, C) launch_matvec_t<A, B, C>(T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, st)
+  switch (sh.ng) {
+    case 1: ZR_MV(4, 1, 128); break;
+    case 2: ZR_MV(4, 2, 128); break;
+    case 4: ZR_MV(4, 4, 64); break;
+    case 7: ZR_MV(3, 7, 64); break;
+    case 6: ZR_MV(4, 6, 64); break;
+    case 11: ZR_MV(4, 11, 32); break;
+    default: ZR_MV(4, 16, 32); break;
+  }
+#undef ZR_MV
+}
+
+// Group splits so that the launch has at least eight CTAs per SM (about four
+// waves of two: the last wave's imbalance stays small).
+static int eval_gsplit(const zr_ctx* ctx, int64_t T, int S, int64_t Tf) {
+  const EvalShape sh = eval_shape(S);
+  const int64_t ctas = (int64_t)cdiv(T, sh.ni);
+  int gsplit = 1;
+  const int64_t want = 8ll * (ctx && ctx->sms ? ctx->sms : 152);
+  while (ctas * gsplit < want && gsplit < 64 && Tf / (gsplit * 2) >= 2 * kGC) gsplit *= 2;
+  return gsplit;
 }
 
 // Workspace bytes the evaluator needs for (f, S, T).
@@ -308,16 +358,10 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   const int nv = f->nv;
   const uint64_t H = hash_slots(Tf > 0 ? Tf : 1);
   const int64_t nbH = (int64_t)((H + kB - 1) / kB);
-  const int stile = eval_tile(S);
-  const int nst = (S + stile - 1) / stile;
-  // split the groups so that the launch has at least ~2 CTAs per SM
-  const int64_t ctas = (int64_t)cdiv(T, kNI) * nst;
-  int gsplit = 1;
-  const int64_t want = 2ll * (ctx->sms ? ctx->sms : 152);
-  while (ctas * gsplit < want && gsplit < 64 && Tf / (gsplit * 2) >= 2 * kGC) gsplit *= 2;
+  const int gsplit = eval_gsplit(ctx, T, S, Tf);
   auto layout = [&](Carver& cv, uint64_t** tabY, uint64_t** tabZ, uint64_t** tabC, uint64_t** u, uint64_t** w,
                     uint64_t** htab, int64_t** bsum, int32_t** gid, uint64_t** U, unsigned long long** Wacc,
-                    BX** Wbx, uint64_t** UP, uint64_t** partial, int64_t** Gdev) {
+                    uint64_t** Wp, uint64_t** UP, uint64_t** partial, int64_t** Gdev) {
     const int64_t Tn = Tf > 0 ? Tf : 1;
     *tabY = cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
     *tabZ = cv.take<uint64_t>((size_t)nv * kPowTab);
@@ -329,7 +373,7 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
     *gid = cv.take<int32_t>(H);
     *U = cv.take<uint64_t>(Tn);
     *Wacc = cv.take<unsigned long long>((size_t)Tn * S * 2);
-    *Wbx = cv.take<BX>((size_t)Tn * S);
+    *Wp = cv.take<uint64_t>((size_t)Tn * S);
     *UP = cv.take<uint64_t>((size_t)Tn * 32);
     *partial = cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
     *Gdev = cv.take<int64_t>(1);
@@ -338,9 +382,9 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   int64_t *bsum, *Gdev;
   int32_t* gid;
   unsigned long long* Wacc;
-  BX* Wbx;
+  uint64_t* Wp;
   Carver cv(base);
-  layout(cv, &tabY, &tabZ, &tabC, &u, &w, &htab, &bsum, &gid, &U, &Wacc, &Wbx, &UP, &partial, &Gdev);
+  layout(cv, &tabY, &tabZ, &tabC, &u, &w, &htab, &bsum, &gid, &U, &Wacc, &Wp, &UP, &partial, &Gdev);
 
   if (T <= 0) return ZR_OK;
   if (Tf == 0) {
@@ -364,16 +408,8 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_probes: group count");
   G = ctx->h_count[1];
-  { k_eval_finalize<<<cdiv(G * S > G ? G * S : G, 256), 256, 0, st>>>(G, S, Wacc, U, M, Wbx, UP); note_launch(); }
-  uint64_t* target = out;
-  switch (stile) {
-    case 4: launch_matvec_t<4>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
-    case 8: launch_matvec_t<8>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
-    case 9: launch_matvec_t<9>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
-    case 12: launch_matvec_t<12>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
-    case 16: launch_matvec_t<16>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
-    default: launch_matvec_t<21>(T, S, offset, G, gsplit, UP, Wbx, M, target, ldo, partial, st); break;
-  }
+  { k_eval_finalize<<<cdiv(G * S > G ? G * S : G, 256), 256, 0, st>>>(G, S, Wacc, U, M, Wp, UP); note_launch(); }
+  launch_matvec(eval_shape(S), T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, st);
   if (gsplit > 1) { k_eval_combine<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, gsplit, partial, M, out, ldo); note_launch(); }
   return cuda_err(ctx, cudaGetLastError(), "zr_zippel_probes");
 }
@@ -383,12 +419,7 @@ size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t
   const int nv = f->nv;
   const uint64_t H = hash_slots(Tf > 0 ? Tf : 1);
   const int64_t nbH = (int64_t)((H + kB - 1) / kB);
-  const int stile = eval_tile(S);
-  const int nst = (S + stile - 1) / stile;
-  const int64_t ctas = (int64_t)cdiv(T, kNI) * nst;
-  int gsplit = 1;
-  const int64_t want = 2ll * (ctx && ctx->sms ? ctx->sms : 152);
-  while (ctas * gsplit < want && gsplit < 64 && Tf / (gsplit * 2) >= 2 * kGC) gsplit *= 2;
+  const int gsplit = eval_gsplit(ctx, T, S, Tf);
   const int64_t Tn = Tf > 0 ? Tf : 1;
   Carver cv(nullptr);
   cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
@@ -401,7 +432,7 @@ size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t
   cv.take<int32_t>(H);
   cv.take<uint64_t>(Tn);
   cv.take<unsigned long long>((size_t)Tn * S * 2);
-  cv.take<BX>((size_t)Tn * S);
+  cv.take<uint64_t>((size_t)Tn * S);
   cv.take<uint64_t>((size_t)Tn * 32);
   cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
   cv.take<int64_t>(1);
