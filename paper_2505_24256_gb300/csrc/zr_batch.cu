@@ -2,7 +2,7 @@
 //
 // Steps (or systems) of different T and S share every launch: each kernel
 // gets the device array of descriptors (BDesc) and a prefix sum over the
-// entries' work (roots, leaf chunks, tree tiles, 128-term blocks); a flattened
+// entries' work (roots, leaf chunks, tree tiles, kFinB-term blocks); a flattened
 // index is mapped back to (entry, local index) by binary search.  The solve
 // kernel is persistent and walks a device work list of (entry, root tile,
 // k-block, right-hand-side tile) items, longest first.  A batch of one is the
@@ -239,9 +239,9 @@ __global__ void __launch_bounds__(kNewtonThreads) k_b_newton_table(const BDesc* 
 
 // a4 + a6 per term: the denominator q_j(v_j) from its k-block partials, its
 // inverse (one inversion per warp), the S dot products from their k-block
-// partials, then the monomial coefficients through W.  Blocks of 128 terms
+// partials, then the monomial coefficients through W.  Blocks of kFinB terms
 // never straddle entries (pre counts blocks), so W sits in shared memory.
-__global__ void __launch_bounds__(128) k_b_finish_newton(const BDesc* __restrict__ Ds,
+__global__ void __launch_bounds__(kFinB) k_b_finish_newton(const BDesc* __restrict__ Ds,
                                                          const int64_t* __restrict__ pre_blk, int n, Mod M) {
   extern __shared__ uint64_t fsm[];
   const int i = seg_of(pre_blk, n, blockIdx.x);
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(128) k_b_finish_newton(const BDesc* __restrict
   uint64_t* W = fsm;
   uint64_t* num = fsm + S * S;
   for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) W[idx] = D.invd[idx];
-  const int64_t j = (blockIdx.x - pre_blk[i]) * 128 + threadIdx.x;
+  const int64_t j = (blockIdx.x - pre_blk[i]) * kFinB + threadIdx.x;
   const bool active = j < D.T;
   uint64_t den = 1, mult = 1;
   if (active) {
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(128) k_b_finish_newton(const BDesc* __restrict
   if (active) {
     // sum of the k-block partials; the S loads of one k-block are independent
     uint64_t* nm = num + threadIdx.x;
-    for (int s = 0; s < S; s++) nm[s * 128] = D.part[(int64_t)s * D.T + j];
+    for (int s = 0; s < S; s++) nm[s * kFinB] = D.part[(int64_t)s * D.T + j];
     for (int kb = 1; kb < D.NB; kb++) {
       const uint64_t* pp = D.part + (int64_t)kb * S * D.T + j;
       for (int s0 = 0; s0 < S; s0 += 8) {
@@ -270,14 +270,14 @@ __global__ void __launch_bounds__(128) k_b_finish_newton(const BDesc* __restrict
         for (int q = 0; q < 8; q++) x[q] = s0 + q < S ? pp[(int64_t)(s0 + q) * D.T] : 0;
 #pragma unroll
         for (int q = 0; q < 8; q++)
-          if (s0 + q < S) nm[(s0 + q) * 128] = add_mod(nm[(s0 + q) * 128], x[q], M);
+          if (s0 + q < S) nm[(s0 + q) * kFinB] = add_mod(nm[(s0 + q) * kFinB], x[q], M);
       }
     }
   }
   __syncthreads();
   int cnt = 0;
   if (active) {
-    cnt = newton_apply(S, W, num + threadIdx.x, 128, inv, D.g + j, D.T, M);
+    cnt = newton_apply(S, W, num + threadIdx.x, kFinB, inv, D.g + j, D.T, M);
     D.cnt[j] = cnt;
   }
   // nonzero coefficients of this block of terms, for the compaction
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(256) k_b_finish_solve(const BDesc* __restrict_
 // ---- a6: compaction ---------------------------------------------------------------
 
 constexpr int kScanB = 1024;   // width of the block-offset scan
-constexpr int kCompB = 128;    // terms per compaction block (the finish kernel's blocks)
+constexpr int kCompB = kFinB;  // terms per compaction block (the finish kernel's blocks)
 
 // Exclusive offsets of the blocks' nonzero counts, one CTA per entry.
 __global__ void __launch_bounds__(kScanB) k_b_scan(const BDesc* __restrict__ Ds) {
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kScanB) k_b_scan(const BDesc* __restrict__ Ds)
 }
 
 // The new skeleton: the nonzero coefficients of every term j in order of j,
-// then of the power s of x_k.  One block per 128 terms; its threads walk the
+// then of the power s of x_k.  One block per kFinB terms; its threads walk the
 // block's output slots, so consecutive threads write consecutive outputs.
 __global__ void __launch_bounds__(kCompB) k_b_scatter(const BDesc* __restrict__ Ds,
                                                       const int64_t* __restrict__ pre_blk, int n) {
@@ -432,7 +432,7 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
     c_hash[i] = T > 0 ? (int64_t)hash_slots(T) : 0;
     c_roots[i] = T;
     c_leaf[i] = (T + (1 << kTreeL1) - 1) >> kTreeL1;
-    c_nblk[i] = (T + 127) / 128;
+    c_nblk[i] = (T + kFinB - 1) / kFinB;
     c_carry[i] = (T > 0 && P.plan[i].NB > 1) ? (int64_t)((T + 255) / 256) * (P.plan[i].NB - 1) : 0;
   }
   push_prefix(P.pre, c_hash, P.o_hash);
@@ -676,7 +676,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
         cudaFuncSetAttribute(k_b_newton_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(8 * newton_table_words(kNewtonMax)));
         cudaFuncSetAttribute(k_b_finish_newton, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)newton_smem(kNewtonMax));
+                             (int)newton_smem(kNewtonMax, kFinB));
         configured = true;
       }
       if (side) cudaStreamWaitEvent(st, ctx->ev_join, 0);   // W of every entry (forked above)
@@ -686,7 +686,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
       }
       const int64_t nblk = pre[o_nblk + n];
       {
-        k_b_finish_newton<<<(unsigned)nblk, 128, newton_smem(smax), st>>>(dD, dpre + o_nblk, n, M);
+        k_b_finish_newton<<<(unsigned)nblk, kFinB, newton_smem(smax, kFinB), st>>>(dD, dpre + o_nblk, n, M);
         note_launch();
       }
     } else {

@@ -78,8 +78,9 @@ int solve_max_groups();       // consumer groups per CTA: S <= groups * s_tile
 void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* W, uint32_t* status, cudaStream_t st);
 void launch_newton(int64_t nterms, int npts, const uint64_t* W, const uint64_t* vals, int64_t ld, const Mod& M,
                    uint64_t* coef, cudaStream_t st);
-size_t newton_smem(int S);   // dynamic shared memory of one 128-term block
-int64_t scan_blocks(int64_t n);  // number of 128-term compaction blocks
+constexpr int kFinB = 32;                 // terms per block of a step's finish and compaction
+size_t newton_smem(int S, int terms);     // dynamic shared memory of one block of `terms` terms
+int64_t scan_blocks(int64_t n);           // number of kFinB-term compaction blocks
 // split partials the product tree may use for T leaves (words = that x T)
 inline int64_t tree_split_max(int64_t T) {
   const int64_t s = T > 0 ? (4 * 152 * 512 + T - 1) / T : 1;

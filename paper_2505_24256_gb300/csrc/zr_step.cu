@@ -113,20 +113,20 @@ __global__ void __launch_bounds__(128) k_newton(int64_t nterms, int S, const uin
   newton_apply(S, W, val + threadIdx.x, 128, 1, coef + j, ld, M);
 }
 
-size_t newton_smem(int S) { return sizeof(uint64_t) * ((size_t)S * S + (size_t)S * 128); }
+size_t newton_smem(int S, int terms) { return sizeof(uint64_t) * ((size_t)S * S + (size_t)S * terms); }
 
 void launch_newton(int64_t nterms, int npts, const uint64_t* W, const uint64_t* vals, int64_t ld, const Mod& M,
                    uint64_t* coef, cudaStream_t st) {
   if (nterms <= 0) return;
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)newton_smem(kNewtonMax));
+    cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)newton_smem(kNewtonMax, 128));
     configured = true;
   }
   const unsigned grid = cdiv(nterms, 128);
-  { k_newton<<<grid, 128, newton_smem(npts), st>>>(nterms, npts, W, vals, ld, M, coef); note_launch(); }
+  { k_newton<<<grid, 128, newton_smem(npts, 128), st>>>(nterms, npts, W, vals, ld, M, coef); note_launch(); }
 }
 
-int64_t scan_blocks(int64_t n) { return (n + 127) / 128; }
+int64_t scan_blocks(int64_t n) { return (n + kFinB - 1) / kFinB; }
 
 }  // namespace zr
