@@ -188,6 +188,7 @@ struct EvalSmem {
   uint64_t X[kGC][NI];
   uint64_t W[kGC][EvalCfg<ST, NG, NI>::WW];
   uint64_t part[kGC][8];
+  uint64_t sq[kGC][8], sqp[kGC][8];   // u_g^(2^a) and its Shoup quotient, a < log2(NI)
 };
 
 template <int ST, int NG, int NI>
@@ -230,13 +231,20 @@ __global__ void __launch_bounds__(NI* NG, EvalCfg<ST, NG, NI>::MINB) k_eval_matv
       for (int q = 0; q < 8; q++) b = mul_mod(b, sm.part[g][q], M);
       sm.X[g][0] = b;
     }
+    constexpr int LA = NI >= 256 ? 8 : (NI >= 128 ? 7 : (NI >= 64 ? 6 : 5));   // doubling levels
+    for (int t = tid; t < kGC * LA; t += C::NT) {
+      const int g = t / LA, a = t - g * LA;
+      const uint64_t q = g < gn ? UP[(gc + g) * 32 + a] : 0;
+      sm.sq[g][a] = q;
+      sm.sqp[g][a] = shoup_pre(q, M);
+    }
     __syncthreads();
-    // doubling: X[g][t + 2^a] = X[g][t] u_g^(2^a)
-    for (int a = 0; (1 << a) < NI; a++) {
+    // doubling: X[g][t + 2^a] = X[g][t] u_g^(2^a), a Shoup multiply by a constant of the level
+    for (int a = 0; a < LA; a++) {
       const int half = 1 << a;
       for (int idx = tid; idx < kGC * half; idx += C::NT) {
         const int g = idx / half, t = idx - g * half;
-        if (g < gn) sm.X[g][t + half] = mul_mod(sm.X[g][t], UP[(gc + g) * 32 + a], M);
+        if (g < gn) sm.X[g][t + half] = canon(shoup_lazy(sm.X[g][t], sm.sq[g][a], sm.sqp[g][a], M), M);
       }
       __syncthreads();
     }
@@ -301,28 +309,39 @@ struct EvalShape {
   int st, ng, ni;
 };
 static EvalShape eval_shape(int S) {
-  // four (or three) columns per thread keep a thread within ~90 registers
-  if (S <= 4) return {4, 1, 128};
-  if (S <= 8) return {4, 2, 128};
-  if (S <= 16) return {4, 4, 64};
-  if (S <= 21) return {3, 7, 64};
-  if (S <= 24) return {4, 6, 64};
-  if (S <= 44) return {4, 11, 32};
-  return {4, 16, 32};
+  // three columns per thread (four beyond 48 columns) keep a thread within
+  // ~80 registers; as many i per CTA as keep two CTAs (<= 448 threads) per SM
+  const int st = S <= 48 ? 3 : 4;
+  const int ng = (S + st - 1) / st;
+  int ni = 256;
+  while (ni > 32 && ni * ng > 448) ni >>= 1;
+  return {st, ng, ni};
+}
+
+template <int NG>
+static void launch_matvec_g(int st, int ni, int64_t T, int S, int offset, int64_t G, int gsplit, const uint64_t* UP,
+                            const uint64_t* Wp, const Mod& M, uint64_t* out, int64_t ldo, uint64_t* partial,
+                            cudaStream_t s) {
+  if (st == 4) {
+    if constexpr (NG >= 13) launch_matvec_t<4, NG, 32>(T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, s);
+    return;
+  }
+  if constexpr (NG <= 16) {
+    constexpr int NI1 = NG == 1 ? 256 : (NG <= 3 ? 128 : (NG <= 7 ? 64 : 32));
+    (void)ni;
+    launch_matvec_t<3, NG, NI1>(T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, s);
+  }
 }
 
 static void launch_matvec(const EvalShape& sh, int64_t T, int S, int offset, int64_t G, int gsplit,
                           const uint64_t* UP, const uint64_t* Wp, const Mod& M, uint64_t* out, int64_t ldo,
                           uint64_t* partial, cudaStream_t st) {
-#define ZR_MV(A, B, C) launch_matvec_t<A, B, C>(T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, st)
+#define ZR_MV(NGV) \
+  case NGV: launch_matvec_g<NGV>(sh.st, sh.ni, T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, st); break;
   switch (sh.ng) {
-    case 1: ZR_MV(4, 1, 128); break;
-    case 2: ZR_MV(4, 2, 128); break;
-    case 4: ZR_MV(4, 4, 64); break;
-    case 7: ZR_MV(3, 7, 64); break;
-    case 6: ZR_MV(4, 6, 64); break;
-    case 11: ZR_MV(4, 11, 32); break;
-    default: ZR_MV(4, 16, 32); break;
+    ZR_MV(1) ZR_MV(2) ZR_MV(3) ZR_MV(4) ZR_MV(5) ZR_MV(6) ZR_MV(7) ZR_MV(8)
+    ZR_MV(9) ZR_MV(10) ZR_MV(11) ZR_MV(12) ZR_MV(13) ZR_MV(14) ZR_MV(15) ZR_MV(16)
+    default: break;
   }
 #undef ZR_MV
 }
