@@ -61,10 +61,6 @@ static Mod make_mod(uint64_t p) {
   M.norm = (uint32_t)__builtin_clzll(p);
   M.d = p << M.norm;
   M.v = (uint64_t)((~(u128)0) / M.d - ((u128)1 << 64));
-  M.r21 = h_powmod(2, 21, p);
-  M.r42 = h_powmod(2, 42, p);
-  M.r32 = h_powmod(2, 32, p);
-  M.r32p = (uint64_t)(((u128)M.r32 << 64) / p);
   return M;
 }
 

@@ -2,12 +2,12 @@
 //
 // The paper ports FLINT's precomputed-inverse reduction to CUDA (Sec. 2.1,
 // Table 1: ~17x faster than the next variant) and defers the reduction of long
-// dot products with a 3-limb accumulator (Sec. 2.2).  This header is written
-// from the published methods, for a GPU whose 32x32->64 multiply-add
-// (IMAD.WIDE) issues at the full integer-multiply rate while the 32-bit
-// high-half multiply issues at half rate:
+// dot products with a multi-word accumulator (Sec. 2.2).  This header is
+// written from the published methods, for a GPU on which the 32-bit mad.lo
+// issues at 64 lanes per SM per clock and mad.hi at 32 (measured), and the
+// 32x32->64 mad.wide slower still:
 //
-//  * products are built from 32x32+64->64 multiply-adds only;
+//  * products are built from 32-bit mad.lo / mad.hi with carry chains;
 //  * reduction of a 128-bit value uses the 2/1 division with a precomputed
 //    reciprocal of Moller and Granlund ("Improved division by invariant
 //    integers", IEEE TC 60(2), 2011, Algorithm 4) on the normalised modulus;
@@ -15,17 +15,8 @@
 //    precomputed quotient w' = floor(w 2^64 / p) (as analysed in D. Harvey,
 //    "Faster arithmetic for number-theoretic transforms", JSC 2014), with
 //    results kept lazily in [0, 2p);
-//  * long dot products accumulate without any carry handling.  With
-//    b = b_lo + 2^32 b_hi (the two 32-bit halves of a residue),
-//        x b == x b_lo + (x 2^32 mod p) b_hi   (mod p),
-//    so a thread that owns x computes x~ = x 2^32 mod p once, cuts x and x~
-//    into 21-bit limbs, and multiplies them by the halves of the shared b:
-//        A_t += x_t b_lo + x~_t b_hi,   t = 0, 1, 2,   value = sum_t A_t 2^{21 t}.
-//    Every partial product is below 2^53, so three 64-bit accumulators absorb
-//    256 multiply-adds before they are folded back into a residue, and the
-//    shared operand is the plain 8-byte residue.  This is the deferred
-//    reduction of Sec. 2.2 (a sum of products reduced once) with the limb
-//    split chosen so that no step needs a carry.
+//  * long dot products add full 128-bit products into a 160-bit accumulator
+//    (mac8) and reduce once: the deferred reduction of Sec. 2.2.
 //
 // The modulus is an odd prime 2^32 < p < 2^63, so 2p < 2^64.
 #pragma once
@@ -40,14 +31,8 @@ struct Mod {
   uint64_t v;       // floor((2^128 - 1) / d) - 2^64
   uint32_t norm;    // leading zero count of p, in [1, 31]
   uint32_t pad;
-  uint64_t r21;     // 2^21 mod p
-  uint64_t r42;     // 2^42 mod p
-  uint64_t r32;     // 2^32 mod p
-  uint64_t r32p;    // floor(r32 2^64 / p) (Shoup quotient of r32)
 };
 
-__device__ __forceinline__ uint64_t wide(uint32_t a, uint32_t b) { return (uint64_t)a * b; }
-__device__ __forceinline__ uint64_t wide_add(uint32_t a, uint32_t b, uint64_t c) { return (uint64_t)a * b + c; }
 __device__ __forceinline__ uint32_t lo32(uint64_t x) { return (uint32_t)x; }
 __device__ __forceinline__ uint32_t hi32(uint64_t x) { return (uint32_t)(x >> 32); }
 
@@ -168,125 +153,9 @@ __device__ __forceinline__ uint64_t pow_mod(uint64_t a, uint64_t e, const Mod& M
 __device__ __forceinline__ uint64_t inv_mod(uint64_t a, const Mod& M) { return pow_mod(a, M.p - 2, M); }
 
 // ---------------------------------------------------------------------------
-// Deferred multiply-accumulate (see the header comment).
+// Deferred multiply-accumulate: acc += x b for 64-bit x, b, reduced once.
 // ---------------------------------------------------------------------------
 
-// A shared operand b in MAC form: halves of b, b 2^21, b 2^42 (mod p).
-struct BX {
-  uint32_t l0, l1, l2, h0;  // first 16 bytes
-  uint32_t h1, h2, z0, z1;  // second 16 bytes (z*: padding)
-};
-
-__device__ __forceinline__ BX make_bx(uint64_t b, const Mod& M) {
-  uint64_t b1 = mul_mod(b, M.r21, M), b2 = mul_mod(b, M.r42, M);
-  BX r;
-  r.l0 = lo32(b); r.h0 = hi32(b);
-  r.l1 = lo32(b1); r.h1 = hi32(b1);
-  r.l2 = lo32(b2); r.h2 = hi32(b2);
-  r.z0 = r.z1 = 0;
-  return r;
-}
-
-// The 21-bit limbs of a per-thread operand x < 2^64.
-struct XL { uint32_t x0, x1, x2; };
-__device__ __forceinline__ XL limbs21(uint64_t x) {
-  XL r;
-  r.x0 = (uint32_t)x & 0x1FFFFFu;
-  r.x1 = (uint32_t)(x >> 21) & 0x1FFFFFu;
-  r.x2 = (uint32_t)(x >> 42);
-  return r;
-}
-
-// acc (two u64) += x * b, value = accL + accH 2^32 (congruent mod p).
-struct Acc { uint64_t L, H; };
-__device__ __forceinline__ void mac(Acc& a, const XL& x, const uint4& b0, const uint2& b1) {
-  // b0 = (l0, l1, l2, h0), b1 = (h1, h2)
-  a.L = wide_add(x.x0, b0.x, a.L);
-  a.L = wide_add(x.x1, b0.y, a.L);
-  a.L = wide_add(x.x2, b0.z, a.L);
-  a.H = wide_add(x.x0, b0.w, a.H);
-  a.H = wide_add(x.x1, b1.x, a.H);
-  a.H = wide_add(x.x2, b1.y, a.H);
-}
-// The residue of an accumulator.
-__device__ __forceinline__ uint64_t acc_value(const Acc& a, const Mod& M) {
-  uint64_t lo = a.L + (a.H << 32);
-  uint64_t hi = (a.H >> 32) + (lo < a.L);
-  return reduce128(hi, lo, M);             // hi < 2^32 + 1 < p
-}
-// Fold: acc <- (residue, 0).  After a fold the accumulator holds < p < 2^63
-// and takes another MAC_FOLD multiply-adds: each adds < 2^55 - 2^33 to L.
-__device__ __forceinline__ void acc_fold(Acc& a, const Mod& M) {
-  a.L = acc_value(a, M);
-  a.H = 0;
-}
-constexpr int MAC_FOLD = 128;
-
-// The per-thread operand of the three-accumulator MAC: limbs of x and of
-// x 2^32 mod p (x canonical, so every limb is below 2^21).
-struct XL2 { uint32_t a0, a1, a2, c0, c1, c2; };
-__device__ __forceinline__ XL2 limbs_pair(uint64_t x, const Mod& M) {
-  const uint64_t xt = canon(shoup_lazy(x, M.r32, M.r32p, M), M);
-  XL2 r;
-  r.a0 = (uint32_t)x & 0x1FFFFFu;
-  r.a1 = (uint32_t)(x >> 21) & 0x1FFFFFu;
-  r.a2 = (uint32_t)(x >> 42);
-  r.c0 = (uint32_t)xt & 0x1FFFFFu;
-  r.c1 = (uint32_t)(xt >> 21) & 0x1FFFFFu;
-  r.c2 = (uint32_t)(xt >> 42);
-  return r;
-}
-struct Acc3L { uint64_t A0, A1, A2; };
-__device__ __forceinline__ void mac3(Acc3L& a, const XL2& x, uint64_t b) {
-  const uint32_t lo = lo32(b), hi = hi32(b);
-  a.A0 = wide_add(x.a0, lo, a.A0);
-  a.A1 = wide_add(x.a1, lo, a.A1);
-  a.A2 = wide_add(x.a2, lo, a.A2);
-  a.A0 = wide_add(x.c0, hi, a.A0);
-  a.A1 = wide_add(x.c1, hi, a.A1);
-  a.A2 = wide_add(x.c2, hi, a.A2);
-}
-// residue of A0 + A1 2^21 + A2 2^42
-__device__ __forceinline__ uint64_t acc3l_value(const Acc3L& a, const Mod& M) {
-  uint64_t lo = a.A0, hi = 0;
-  uint64_t t = a.A1 << 21;
-  lo += t;
-  hi += (a.A1 >> 43) + (lo < t);
-  t = a.A2 << 42;
-  lo += t;
-  hi += (a.A2 >> 22) + (lo < t);
-  return reduce128(hi, lo, M);            // hi < 2^43 < p
-}
-// After a fold the accumulator holds one residue (< 2^63) and takes another
-// MAC3_FOLD multiply-adds: each adds below 2^54 to every word.
-__device__ __forceinline__ void acc3l_fold(Acc3L& a, const Mod& M) {
-  a.A0 = acc3l_value(a, M);
-  a.A1 = a.A2 = 0;
-}
-constexpr int MAC3_FOLD = 256;
-
-// Five-word accumulator r (160 bits) += x b for 64-bit x and b: the four
-// 32x32 partial products as lo/hi multiply-adds with carry chains.  The top
-// word counts carries out of 128 bits, so fewer than 2^32 products never
-// overflow and the sum is reduced once at the end.
-struct Acc5 { uint32_t r0, r1, r2, r3, r4; };
-__device__ __forceinline__ void mac5(Acc5& a, uint32_t x0, uint32_t x1, uint32_t b0, uint32_t b1) {
-  asm("mad.lo.cc.u32 %0, %5, %7, %0;\n\t"
-      "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
-      "madc.lo.cc.u32 %2, %6, %8, %2;\n\t"
-      "madc.hi.cc.u32 %3, %6, %8, %3;\n\t"
-      "addc.u32 %4, %4, 0;\n\t"
-      "mad.lo.cc.u32 %1, %6, %7, %1;\n\t"
-      "madc.hi.cc.u32 %2, %6, %7, %2;\n\t"
-      "addc.cc.u32 %3, %3, 0;\n\t"
-      "addc.u32 %4, %4, 0;\n\t"
-      "mad.lo.cc.u32 %1, %5, %8, %1;\n\t"
-      "madc.hi.cc.u32 %2, %5, %8, %2;\n\t"
-      "addc.cc.u32 %3, %3, 0;\n\t"
-      "addc.u32 %4, %4, 0;"
-      : "+r"(a.r0), "+r"(a.r1), "+r"(a.r2), "+r"(a.r3), "+r"(a.r4)
-      : "r"(x0), "r"(x1), "r"(b0), "r"(b1));
-}
 // Even/odd split: x0 b0 and x1 b1 (bit offsets 0 and 64) go into r0..r4, the
 // two cross products (bit offset 32) into t0..t2.  Two short independent
 // carry chains per product instead of one long one: more instruction-level
@@ -323,9 +192,5 @@ __device__ __forceinline__ uint64_t acc8_value(const Acc8& a, const Mod& M) {
   return reduce128(reduce128(top, M2, M), L2, M);
 }
 
-__device__ __forceinline__ uint64_t acc5_value(const Acc5& a, const Mod& M) {
-  const uint64_t mid = ((uint64_t)a.r3 << 32) | a.r2, low = ((uint64_t)a.r1 << 32) | a.r0;
-  return reduce128(reduce128(a.r4, mid, M), low, M);    // r4 < 2^32 < p
-}
 
 }  // namespace zr

@@ -32,30 +32,16 @@ __device__ __forceinline__ void node_insert(uint64_t x, uint64_t* htab, uint64_t
 }
 
 // Dot products of the product tree: a full 128-bit product per term.
-struct Acc3 { uint64_t lo, hi, top; };
-__device__ __forceinline__ void mac128(Acc3& a, uint64_t x, uint64_t y) {
-  uint64_t h, l;
-  mul128(x, y, h, l);
-  a.lo += l;
-  uint64_t hh = h + (a.lo < l);           // h <= 2^64 - 2: no overflow
-  a.hi += hh;
-  a.top += (a.hi < hh);
-}
-__device__ __forceinline__ uint64_t acc3_value(const Acc3& a, const Mod& M) {
-  return reduce128(reduce128(a.top, a.hi, M), a.lo, M);   // top < p
-}
-
-// coefficient n of (A + z^a)(B + z^b), A at in[po..po+a), B at in[po+a..po+a+b)
 __device__ __forceinline__ uint64_t conv_coef(const uint64_t* in, int po, int a, int b, int n, const Mod& M) {
-  Acc3 acc = {0, 0, 0};
+  Acc8 acc = {0, 0, 0, 0, 0, 0, 0, 0};
   int ilo = n - b > 0 ? n - b : 0, ihi = n < a ? n : a;
   for (int i = ilo; i <= ihi; i++) {
     uint64_t Ai = (i < a) ? in[po + i] : 1;
     int jj = n - i;
     uint64_t Bj = (jj < b) ? in[po + a + jj] : 1;
-    mac128(acc, Ai, Bj);
+    mac8(acc, lo32(Ai), hi32(Ai), lo32(Bj), hi32(Bj));
   }
-  return acc3_value(acc, M);
+  return acc8_value(acc, M);
 }
 
 // Inverse of d for every lane of a full warp; lanes with d = 0 get 0.

@@ -216,3 +216,19 @@ def test_batched_solve_equals_plain(ctx, orc):
     ctx.vandermonde_solve([s[1] for s in systems], plain=False)
     for c1, c2 in zip(plain_out, batch_out):
         assert np.array_equal(h64(c1), h64(c2))
+
+
+def test_autotuned_plan_gives_the_same_skeleton(ctx):
+    """The autotuner only changes the schedule: after tuning a shape the
+    step's output is unchanged, and the stored plan is one the solve is
+    built for."""
+    wl = W.step_workload(701, 3000, 4, 12, 9)
+    D = Dev(ctx, wl)
+    b = D.probes(ctx)
+    before = D.step(ctx, b)
+    ctx.autotune_step(wl.T, wl.S, 8)
+    tile, nb = ctx.step_plan(wl.T, wl.S)
+    assert tile in (2, 3, 4, 6, 8) and 1 <= nb <= wl.T // 32 + 1
+    after = D.step(ctx, b)
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    assert np.array_equal(after[0], wl.exps) and np.array_equal(after[1], wl.coef)
