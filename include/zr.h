@@ -290,6 +290,13 @@ zr_status zr_zippel_probes(zr_ctx* ctx, const zr_poly* f, int32_t k, const uint6
 zr_status zr_eval_points(zr_ctx* ctx, const zr_poly* f, int64_t npts, const uint64_t* pts, uint64_t* out,
                          void* stream);
 
+/* The Zippel probe points themselves, for a caller that evaluates its own
+ * black box: pts[(s T + i) nv + m] = y_m^(i+offset) (m < k), c_s (m = k),
+ * z_m (m > k), for s < S, i < T; device arrays as for zr_zippel_probes, pts
+ * a device buffer of S T nv residues.  Asynchronous on `stream`. */
+zr_status zr_probe_points(zr_ctx* ctx, int32_t nv, int32_t k, const uint64_t* y, int32_t S, const uint64_t* samples,
+                          const uint64_t* z, int64_t T, int32_t offset, uint64_t* pts, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Balanced Zippel step for rational functions (Sec. 2.2, the balancing
  * identity).  For every probe i < max(TN, TD):
@@ -326,19 +333,40 @@ zr_status zr_zippel_step_balanced(zr_ctx* ctx, const zr_poly* skelN, const zr_po
  * The rational result is normalised so that the lexicographically smallest
  * exponent vector of the denominator has coefficient 1.
  * ------------------------------------------------------------------------- */
-typedef enum zr_bb_kind { ZR_BB_POLY = 0, ZR_BB_RATIONAL = 1 } zr_bb_kind;
+typedef enum zr_bb_kind {
+  ZR_BB_POLY = 0,          /* built-in sparse polynomial (term arrays) */
+  ZR_BB_RATIONAL = 1,      /* built-in sparse N / D */
+  ZR_BB_CALL_POLY = 2,     /* a polynomial evaluated by the caller's function */
+  ZR_BB_CALL_RATIONAL = 3  /* a rational function evaluated by the caller's function */
+} zr_bb_kind;
+
+/* A black box given as a function.  It evaluates the hidden function at npts
+ * points: pts is device memory, npts x nv residues row-major; out is device
+ * memory, npts residues (for a rational function the value N/D).  It runs on
+ * `stream` (enqueuing work there, or working synchronously) and returns 0, or
+ * nonzero when some point cannot be evaluated (for a rational function, a
+ * pole): the library then draws new points where the method allows (the
+ * rational steps), else the reconstruction fails with ZR_ERR_POLE.  It is
+ * called from the thread that runs the reconstruction (the server's lane
+ * thread for zr_serve) and must not use the calling context. */
+typedef int32_t (*zr_eval_fn)(void* user, int64_t npts, int32_t nv, const uint64_t* pts, uint64_t* out,
+                              void* stream);
 
 typedef struct zr_blackbox {
   int32_t kind;  /* zr_bb_kind */
   int32_t nv;
   /* built-in sparse hidden function, HOST arrays (copied by the call):
-     N (or the polynomial) and, for ZR_BB_RATIONAL, D */
+     N (or the polynomial) and, for ZR_BB_RATIONAL, D.  For the callback
+     kinds the arrays are unused and TN + TD is only a size hint (the
+     server's lanes and memory estimate). */
   int64_t TN;
   const uint8_t* N_exps;
   const uint64_t* N_coef;
   int64_t TD;
   const uint8_t* D_exps;
   const uint64_t* D_coef;
+  zr_eval_fn eval;       /* callback kinds */
+  void* user;            /* passed to eval */
 } zr_blackbox;
 
 typedef struct zr_recon_params {

@@ -489,6 +489,28 @@ __global__ void __launch_bounds__(256) k_eval_points(int64_t Tf, int nv, const u
   }
 }
 
+// The probe points of a Zippel step: thread i computes y_m^(i+off) once per
+// variable and writes it into the S points of probe i.
+__global__ void k_probe_points(int64_t T, int S, int nv, int k, int offset, const uint64_t* __restrict__ y,
+                               const uint64_t* __restrict__ cs, const uint64_t* __restrict__ z, Mod M,
+                               uint64_t* __restrict__ pts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T) return;
+  for (int m = 0; m < nv; m++) {
+    if (m == k) {
+      for (int s = 0; s < S; s++) pts[((int64_t)s * T + i) * nv + m] = canon(cs[s], M);
+    } else {
+      const uint64_t val = m < k ? pow_mod(canon(y[m], M), (uint64_t)(i + offset), M) : canon(z[m], M);
+      for (int s = 0; s < S; s++) pts[((int64_t)s * T + i) * nv + m] = val;
+    }
+  }
+}
+
+void launch_probe_points(int64_t T, int S, int nv, int k, int offset, const uint64_t* y, const uint64_t* cs,
+                         const uint64_t* z, const Mod& M, uint64_t* pts, cudaStream_t st) {
+  if (T > 0 && S > 0) { k_probe_points<<<cdiv(T, 128), 128, 0, st>>>(T, S, nv, k, offset, y, cs, z, M, pts); note_launch(); }
+}
+
 void launch_eval_points(const zr_poly* f, int64_t npts, const uint64_t* pts, const Mod& M, uint64_t* out,
                         cudaStream_t st) {
   if (npts > 0) { k_eval_points<<<(unsigned)npts, 256, 0, st>>>(f->T, f->nv, f->exps, f->coef, pts, M, out); note_launch(); }
@@ -530,4 +552,15 @@ extern "C" zr_status zr_eval_points(zr_ctx* ctx, const zr_poly* f, int64_t npts,
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_err(ctx, e, "zr_eval_points");
+}
+
+extern "C" zr_status zr_probe_points(zr_ctx* ctx, int32_t nv, int32_t k, const uint64_t* y, int32_t S,
+                                     const uint64_t* samples, const uint64_t* z, int64_t T, int32_t offset,
+                                     uint64_t* pts, void* stream) {
+  if (!ctx) return ZR_ERR_INVALID_ARG;
+  if (nv < 1 || nv > kMaxVars || k < 0 || k >= nv || S < 1 || T < 0 || (offset != 0 && offset != 1) ||
+      (T > 0 && (!pts || !samples || (k > 0 && !y) || (k + 1 < nv && !z))))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_probe_points: arguments out of range");
+  launch_probe_points(T, S, nv, k, offset, y, samples, z, ctx->M, pts, (cudaStream_t)stream);
+  return cuda_err(ctx, cudaGetLastError(), "zr_probe_points");
 }

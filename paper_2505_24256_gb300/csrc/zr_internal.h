@@ -149,6 +149,8 @@ zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, i
 zr_status check_recon_args(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_params* prm);
 
 // balanced step pieces (zr_balance.cu)
+void launch_probe_points(int64_t T, int S, int nv, int k, int offset, const uint64_t* y, const uint64_t* cs,
+                         const uint64_t* z, const Mod& M, uint64_t* pts, cudaStream_t st);
 void launch_ratio(int64_t T, int S, const uint64_t* Nv, const uint64_t* Dv, int64_t ld, const Mod& M, uint64_t* pre,
                   uint64_t* out, int64_t ldo, uint32_t* status, cudaStream_t st);
 size_t thiele_scratch_words(int64_t Tmax, int n);

@@ -82,16 +82,37 @@ std::vector<uint64_t> step0_points(int nv, int S, const uint64_t* cs, const uint
 }  // namespace
 
 Recon::Recon(zr_ctx* ctx, cudaStream_t st, const zr_blackbox& bb, const zr_recon_params& prm)
-    : ctx_(ctx), st_(st), M_(ctx->M), nv_(prm.nv), rational_(bb.kind == ZR_BB_RATIONAL), seed_(prm.seed),
+    : ctx_(ctx),
+      st_(st),
+      M_(ctx->M),
+      nv_(prm.nv),
+      rational_(bb.kind == ZR_BB_RATIONAL || bb.kind == ZR_BB_CALL_RATIONAL),
+      callback_(bb.kind == ZR_BB_CALL_POLY || bb.kind == ZR_BB_CALL_RATIONAL),
+      eval_(bb.eval),
+      user_(bb.user),
+      seed_(prm.seed),
       offset_(prm.offset) {
-  Ne_.assign(bb.N_exps, bb.N_exps + (size_t)bb.TN * nv_);
-  Nc_.assign(bb.N_coef, bb.N_coef + bb.TN);
-  degN_.assign(prm.degN, prm.degN + nv_);
-  if (rational_) {
-    De_.assign(bb.D_exps, bb.D_exps + (size_t)bb.TD * nv_);
-    Dc_.assign(bb.D_coef, bb.D_coef + bb.TD);
-    degD_.assign(prm.degD, prm.degD + nv_);
+  if (!callback_) {
+    Ne_.assign(bb.N_exps, bb.N_exps + (size_t)bb.TN * nv_);
+    Nc_.assign(bb.N_coef, bb.N_coef + bb.TN);
+    if (rational_) {
+      De_.assign(bb.D_exps, bb.D_exps + (size_t)bb.TD * nv_);
+      Dc_.assign(bb.D_coef, bb.D_coef + bb.TD);
+    }
   }
+  degN_.assign(prm.degN, prm.degN + nv_);
+  if (rational_) degD_.assign(prm.degD, prm.degD + nv_);
+}
+
+zr_status Recon::eval_at(const DPoly& f, int64_t npts, const uint64_t* pts, uint64_t* out) {
+  if (!callback_) {
+    zr_poly fv = f.view();
+    launch_eval_points(&fv, npts, pts, M_, out, st_);
+    return cuda_err(ctx_, cudaGetLastError(), "black box");
+  }
+  const int32_t rc = eval_(user_, npts, nv_, pts, out, (void*)st_);
+  if (rc) return set_err(ctx_, ZR_ERR_POLE, "the black box could not be evaluated at a probe");
+  return cuda_err(ctx_, cudaGetLastError(), "black box");
 }
 
 zr_status Recon::fail(zr_status s) {
@@ -118,7 +139,7 @@ zr_status Recon::upload(DBuf& b, const void* host, size_t bytes) {
 
 size_t Recon::device_bytes() const {
   const DBuf* bufs[] = {&d_y_, &d_cs_, &d_z_, &d_b_, &d_pts_, &d_vals_, &scratch_, &persist_, &fv_, &one_, &ones_};
-  size_t s = fN_.bytes() + fD_.bytes() + curN_.bytes() + curD_.bytes() + nextN_.bytes() + nextD_.bytes();
+  size_t s = fN_.bytes() + fD_.bytes() + curN_.bytes() + curD_.bytes() + nextN_.bytes() + nextD_.bytes() + d_ppts_.n;
   for (const DBuf* b : bufs) s += b->n;
   return s;
 }
@@ -139,16 +160,18 @@ double Recon::next_cost() const {
 size_t Recon::estimate_bytes(const zr_blackbox& bb, const zr_recon_params& prm) {
   // hidden function(s), the largest step (skeleton <= hidden terms, S <= 64
   // samples or 2 max(deg)+2 Thiele points) with its probes and outputs
-  const int64_t Tf = bb.TN + (bb.kind == ZR_BB_RATIONAL ? bb.TD : 0);
+  const bool rational = bb.kind == ZR_BB_RATIONAL || bb.kind == ZR_BB_CALL_RATIONAL;
+  const bool callback = bb.kind == ZR_BB_CALL_POLY || bb.kind == ZR_BB_CALL_RATIONAL;
+  const int64_t Tf = bb.TN + (rational ? bb.TD : 0);
   int smax = 1;
   for (int m = 0; m < prm.nv; m++) {
     int s = prm.degN[m] + 1;
-    if (bb.kind == ZR_BB_RATIONAL) s = 2 * std::max(prm.degN[m], prm.degD[m]) + 2;
+    if (rational) s = 2 * std::max(prm.degN[m], prm.degD[m]) + 2;
     smax = std::max(smax, s);
   }
   const size_t row = (size_t)prm.nv + 8;
-  return (size_t)Tf * row + 2 * (size_t)Tf * smax * row + (size_t)Tf * smax * 8 * (bb.kind == ZR_BB_RATIONAL ? 6 : 1) +
-         (1 << 16);
+  return (size_t)Tf * row + 2 * (size_t)Tf * smax * row + (size_t)Tf * smax * 8 * (rational ? 6 : 1) +
+         (callback ? (size_t)Tf * smax * 8 * prm.nv : 0) + (1 << 16);
 }
 
 zr_status Recon::newton_coeffs(int S, const uint64_t* d_cs, const uint64_t* d_vals, std::vector<uint64_t>& coef) {
@@ -201,9 +224,9 @@ zr_status Recon::start() {
   cudaMemsetAsync(ctx_->d_status_call, 0, sizeof(uint32_t), st_);
   fN_.nv = fD_.nv = nv_;
   fN_.T = (int64_t)Nc_.size();
-  zr_status r = upload(fN_.exps, Ne_.data(), Ne_.size());
-  if (!r) r = upload(fN_.coef, Nc_.data(), 8 * Nc_.size());
-  if (!r && rational_) {
+  zr_status r = callback_ ? ZR_OK : upload(fN_.exps, Ne_.data(), Ne_.size());
+  if (!r && !callback_) r = upload(fN_.coef, Nc_.data(), 8 * Nc_.size());
+  if (!r && rational_ && !callback_) {
     fD_.T = (int64_t)Dc_.size();
     r = upload(fD_.exps, De_.data(), De_.size());
     if (!r) r = upload(fD_.coef, Dc_.data(), 8 * Dc_.size());
@@ -228,8 +251,7 @@ zr_status Recon::step0_poly() {
   if (r) return r;
   cudaError_t e = d_vals_.ensure(8 * (size_t)S);
   if (e != cudaSuccess) return cuda_err(ctx_, e, "values");
-  zr_poly fv = fN_.view();
-  launch_eval_points(&fv, S, d_pts_.as<uint64_t>(), M_, d_vals_.as<uint64_t>(), st_);
+  if ((r = eval_at(fN_, S, d_pts_.as<uint64_t>(), d_vals_.as<uint64_t>()))) return r;
   std::vector<uint64_t> coef;
   if ((r = newton_coeffs(S, d_cs_.as<uint64_t>(), d_vals_.as<uint64_t>(), coef))) return r;
   return skeleton_from_coeffs(coef, S - 1, curN_);
@@ -255,11 +277,14 @@ zr_status Recon::step0_rational() {
     uint64_t* f = pre + Sf;
     uint64_t* nval = f + Sf;
     uint64_t* dval = nval + (dN + 1);
-    zr_poly nv_p = fN_.view(), dv_p = fD_.view();
-    launch_eval_points(&nv_p, Sf, d_pts_.as<uint64_t>(), M_, nvls, st_);
-    launch_eval_points(&dv_p, Sf, d_pts_.as<uint64_t>(), M_, dvls, st_);
-    launch_ratio(1, Sf, nvls, dvls, 1, M_, pre, f, 1, ctx_->d_status_call, st_);
-    r = sync_status();
+    if (callback_) {
+      r = eval_at(fN_, Sf, d_pts_.as<uint64_t>(), f);     // the caller's N / D
+    } else {
+      if (!(r = eval_at(fN_, Sf, d_pts_.as<uint64_t>(), nvls)) && !(r = eval_at(fD_, Sf, d_pts_.as<uint64_t>(), dvls))) {
+        launch_ratio(1, Sf, nvls, dvls, 1, M_, pre, f, 1, ctx_->d_status_call, st_);
+        r = sync_status();
+      }
+    }
     if (!r) {
       e = persist_.ensure(8 * thiele_scratch_words(1, Sf) + 256);
       if (e != cudaSuccess) return cuda_err(ctx_, e, "thiele scratch");
@@ -327,7 +352,13 @@ zr_status Recon::prepare(std::vector<BatchItem>& items, uint32_t* d_status, int6
     const int64_t T = curN_.T;
     cudaError_t e = d_b_.ensure(8 * (size_t)S * (T > 0 ? T : 1));
     if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "probes"));
-    if (T > 0) {
+    if (T > 0 && callback_) {
+      e = d_ppts_.ensure(8 * (size_t)S * T * nv_);
+      if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "probe points"));
+      launch_probe_points(T, S, nv_, k, offset_, d_y_.as<uint64_t>(), d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), M_,
+                          d_ppts_.as<uint64_t>(), st_);
+      if ((r = eval_at(fN_, (int64_t)S * T, d_ppts_.as<uint64_t>(), d_b_.as<uint64_t>()))) return fail(r);
+    } else if (T > 0) {
       zr_poly fv = fN_.view();
       r = probes_impl(ctx_, &fv, k, d_y_.as<uint64_t>(), S, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), T, offset_,
                       d_b_.as<uint64_t>(), T, d_status, st_);
@@ -355,15 +386,25 @@ zr_status Recon::prepare(std::vector<BatchItem>& items, uint32_t* d_status, int6
     uint64_t* dvls = nvls + (size_t)Sf * Tmax;
     uint64_t* pre = dvls + (size_t)Sf * Tmax;
     uint64_t* f = pre + (size_t)Sf * Tmax;
-    zr_poly nv_p = fN_.view(), dv_p = fD_.view();
-    r = probes_impl(ctx_, &nv_p, k, d_y_.as<uint64_t>(), Sf, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), Tmax, offset_,
-                    nvls, Tmax, ctx_->d_status_call, st_);
-    if (!r)
-      r = probes_impl(ctx_, &dv_p, k, d_y_.as<uint64_t>(), Sf, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), Tmax,
-                      offset_, dvls, Tmax, ctx_->d_status_call, st_);
-    if (r) return fail(r);
-    launch_ratio(Tmax, Sf, nvls, dvls, Tmax, M_, pre, f, Tmax, ctx_->d_status_call, st_);
-    r = sync_status();
+    if (callback_) {
+      // f = N/D from the caller at the probe points
+      e = d_ppts_.ensure(8 * (size_t)Sf * Tmax * nv_);
+      if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "probe points"));
+      launch_probe_points(Tmax, Sf, nv_, k, offset_, d_y_.as<uint64_t>(), d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(),
+                          M_, d_ppts_.as<uint64_t>(), st_);
+      r = eval_at(fN_, (int64_t)Sf * Tmax, d_ppts_.as<uint64_t>(), f);
+      if (r && r != ZR_ERR_POLE) return fail(r);
+    } else {
+      zr_poly nv_p = fN_.view(), dv_p = fD_.view();
+      r = probes_impl(ctx_, &nv_p, k, d_y_.as<uint64_t>(), Sf, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), Tmax,
+                      offset_, nvls, Tmax, ctx_->d_status_call, st_);
+      if (!r)
+        r = probes_impl(ctx_, &dv_p, k, d_y_.as<uint64_t>(), Sf, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), Tmax,
+                        offset_, dvls, Tmax, ctx_->d_status_call, st_);
+      if (r) return fail(r);
+      launch_ratio(Tmax, Sf, nvls, dvls, Tmax, M_, pre, f, Tmax, ctx_->d_status_call, st_);
+      r = sync_status();
+    }
     if (!r) {
       // D' at the probes, Thiele per probe, balancing
       const size_t w_dprev = (size_t)Tmax, w_bN = (size_t)SN * (TN ? TN : 1), w_bD = (size_t)SD * (TD ? TD : 1);
@@ -480,11 +521,17 @@ zr_result* Recon::take_result() {
 
 zr_status check_recon_args(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_params* prm) {
   if (!bb || !prm || prm->nv < 1 || prm->nv > kMaxVars || bb->nv != prm->nv || (prm->offset != 0 && prm->offset != 1) ||
-      !prm->degN || bb->TN < 0 || (bb->TN > 0 && (!bb->N_exps || !bb->N_coef)))
+      !prm->degN || bb->TN < 0 || bb->TD < 0)
     return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: bad black box or parameters");
-  const bool rational = bb->kind == ZR_BB_RATIONAL;
-  if (bb->kind != ZR_BB_POLY && !rational) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: unknown kind");
-  if (rational && (!prm->degD || bb->TD <= 0 || !bb->D_exps || !bb->D_coef))
+  const bool callback = bb->kind == ZR_BB_CALL_POLY || bb->kind == ZR_BB_CALL_RATIONAL;
+  const bool rational = bb->kind == ZR_BB_RATIONAL || bb->kind == ZR_BB_CALL_RATIONAL;
+  if (bb->kind < ZR_BB_POLY || bb->kind > ZR_BB_CALL_RATIONAL)
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: unknown kind");
+  if (callback && !bb->eval) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: callback black box without eval");
+  if (!callback && bb->TN > 0 && (!bb->N_exps || !bb->N_coef))
+    return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: bad black box or parameters");
+  if (rational && !prm->degD) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: rational needs degD");
+  if (rational && !callback && (bb->TD <= 0 || !bb->D_exps || !bb->D_coef))
     return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: rational black box needs a denominator");
   for (int m = 0; m < prm->nv; m++) {
     const int dn = prm->degN[m], dd = rational ? prm->degD[m] : 0;

@@ -92,12 +92,19 @@ class Recon {
   zr_status step_entry(const DPoly& skel, int S, const uint64_t* b, int64_t ldb, DPoly& out, uint32_t* d_status,
                        int64_t* d_count, std::vector<BatchItem>& items);
 
+  // values of the black box at npts device points (npts x nv_) into out:
+  // the built-in evaluator or the caller's function (nonzero: a pole)
+  zr_status eval_at(const DPoly& f, int64_t npts, const uint64_t* pts, uint64_t* out);
+
   zr_ctx* ctx_;
   cudaStream_t st_;
   Mod M_;
   // request
   int nv_;
   bool rational_;
+  bool callback_ = false;       // the black box is the caller's function
+  zr_eval_fn eval_ = nullptr;
+  void* user_ = nullptr;
   std::vector<uint8_t> Ne_, De_;
   std::vector<uint64_t> Nc_, Dc_;
   std::vector<int32_t> degN_, degD_;
@@ -109,7 +116,7 @@ class Recon {
   std::vector<uint64_t> z_, y_, cs_;
   int k_ = 1, attempt_ = 0, steps_ = 0, redraws_ = 0;
   DPoly fN_, fD_, curN_, curD_, nextN_, nextD_;
-  DBuf d_y_, d_cs_, d_z_, d_b_, d_pts_, d_vals_, scratch_, persist_, fv_, one_, ones_;
+  DBuf d_y_, d_cs_, d_z_, d_b_, d_pts_, d_vals_, scratch_, persist_, fv_, one_, ones_, d_ppts_;
   zr_result* result_ = nullptr;
 };
 

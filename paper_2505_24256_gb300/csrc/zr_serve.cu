@@ -307,16 +307,23 @@ extern "C" zr_status zr_serve_submit(zr_server* s, const zr_request* req, uint64
   const int nv = req->prm.nv;
   q.bb = req->bb;
   q.prm = req->prm;
-  q.Ne.assign(req->bb.N_exps, req->bb.N_exps + (size_t)req->bb.TN * nv);
-  q.Nc.assign(req->bb.N_coef, req->bb.N_coef + req->bb.TN);
+  const bool callback = req->bb.kind == ZR_BB_CALL_POLY || req->bb.kind == ZR_BB_CALL_RATIONAL;
+  const bool rational = req->bb.kind == ZR_BB_RATIONAL || req->bb.kind == ZR_BB_CALL_RATIONAL;
+  if (!callback) {
+    q.Ne.assign(req->bb.N_exps, req->bb.N_exps + (size_t)req->bb.TN * nv);
+    q.Nc.assign(req->bb.N_coef, req->bb.N_coef + req->bb.TN);
+  }
   q.degN.assign(req->prm.degN, req->prm.degN + nv);
-  if (req->bb.kind == ZR_BB_RATIONAL) {
-    q.De.assign(req->bb.D_exps, req->bb.D_exps + (size_t)req->bb.TD * nv);
-    q.Dc.assign(req->bb.D_coef, req->bb.D_coef + req->bb.TD);
+  if (rational) {
+    if (!callback) {
+      q.De.assign(req->bb.D_exps, req->bb.D_exps + (size_t)req->bb.TD * nv);
+      q.Dc.assign(req->bb.D_coef, req->bb.D_coef + req->bb.TD);
+    }
     q.degD.assign(req->prm.degD, req->prm.degD + nv);
   }
   q.t_submit = now_ms();
-  const int li = (int64_t)req->bb.TN + (req->bb.kind == ZR_BB_RATIONAL ? req->bb.TD : 0) <= kSmallTerms ? 0 : 1;
+  // a callback's TN + TD is the caller's size hint
+  const int li = (int64_t)req->bb.TN + (rational ? req->bb.TD : 0) <= kSmallTerms ? 0 : 1;
   {
     std::lock_guard<std::mutex> g(s->mu);
     if (s->stop) return ZR_ERR_BUSY;

@@ -44,10 +44,18 @@ class zr_step_desc(ctypes.Structure):
                 ("out_coef", ctypes.c_void_p), ("out_cap", ctypes.c_int64), ("out_count", ctypes.c_void_p)]
 
 
+BB_POLY, BB_RATIONAL, BB_CALL_POLY, BB_CALL_RATIONAL = range(4)
+
+# zr_eval_fn(user, npts, nv, pts, out, stream) -> 0, or nonzero at a pole
+zr_eval_fn = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_void_p)
+
+
 class zr_blackbox(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nv", ctypes.c_int32),
                 ("TN", ctypes.c_int64), ("N_exps", ctypes.c_void_p), ("N_coef", ctypes.c_void_p),
-                ("TD", ctypes.c_int64), ("D_exps", ctypes.c_void_p), ("D_coef", ctypes.c_void_p)]
+                ("TD", ctypes.c_int64), ("D_exps", ctypes.c_void_p), ("D_coef", ctypes.c_void_p),
+                ("eval", zr_eval_fn), ("user", ctypes.c_void_p)]
 
 
 class zr_recon_params(ctypes.Structure):
@@ -110,6 +118,7 @@ SIGNATURES = {
     "zr_zippel_step_host": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P, _V]),
     "zr_zippel_probes": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _I64, _V]),
     "zr_eval_points": (_ST, [_V, _P, _I64, _P, _P, _V]),
+    "zr_probe_points": (_ST, [_V, _I32, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _V]),
     "zr_zippel_step_balanced": (_ST, [_V, _P, _P, _I32, _P, _I32, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P,
                                       _P, _P, _I64, _P, _V]),
     "zr_reconstruct": (_ST, [_V, _P, _P, ctypes.POINTER(ctypes.POINTER(zr_result)), _V]),
@@ -154,6 +163,8 @@ def load(path: str = LIB_PATH):
 def _ptr(t):
     if t is None:
         return None
+    if isinstance(t, int):
+        return t
     if isinstance(t, np.ndarray):
         return t.ctypes.data
     return t.data_ptr()
@@ -320,6 +331,10 @@ class Context:
         self.check(self.L.zr_eval_points(self._h, ctypes.byref(f), npts, _ptr(pts), _ptr(out), _stream(stream)),
                    "zr_eval_points")
 
+    def probe_points(self, nv, k, y, S, samples, z, T, offset, pts, stream=None):
+        self.check(self.L.zr_probe_points(self._h, nv, k, _ptr(y), S, _ptr(samples), _ptr(z), T, offset, _ptr(pts),
+                                          _stream(stream)), "zr_probe_points")
+
     def zippel_step_balanced(self, skelN: zr_poly, skelD: zr_poly, newvar, y, dN, dD, samples, fvals, ldf, offset,
                              outN_exps, outN_coef, outN_cap, outD_exps, outD_coef, outD_cap, stream=None):
         nN = ctypes.c_int64()
@@ -349,6 +364,29 @@ class Context:
         prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data)
         res = ctypes.POINTER(zr_result)()
         st = self.L.zr_reconstruct(self._h, ctypes.byref(bb), ctypes.byref(prm), ctypes.byref(res), _stream(stream))
+        self.check(st, "zr_reconstruct")
+        return _take_result(self.L, res)
+
+
+    def reconstruct_callback(self, nv, degN, seed, fn, rational=False, degD=None, TN_hint=0, TD_hint=0, offset=0,
+                             stream=None):
+        """Full reconstruction of a black box given as a function
+        fn(npts, nv, pts, out, stream) -> int over raw device pointers (pts:
+        npts x nv residues, out: npts residues; nonzero return: a pole).
+        Returns ((N_exps, N_coef), (D_exps, D_coef) or None, info)."""
+        raised = []
+        cb = _callback(fn, raised)
+        bb = zr_blackbox(BB_CALL_RATIONAL if rational else BB_CALL_POLY, nv, TN_hint, None, None, TD_hint, None,
+                         None, cb, None)
+        dN = np.ascontiguousarray(degN, dtype=np.int32)
+        dD = np.ascontiguousarray(degD if degD is not None else degN, dtype=np.int32)
+        prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data)
+        res = ctypes.POINTER(zr_result)()
+        st = self.L.zr_reconstruct(self._h, ctypes.byref(bb), ctypes.byref(prm), ctypes.byref(res), _stream(stream))
+        if raised:
+            if st == OK:
+                self.L.zr_result_free(res)
+            raise raised[0]
         self.check(st, "zr_reconstruct")
         return _take_result(self.L, res)
 
@@ -430,6 +468,41 @@ def make_request(nv, degN, seed, N_exps, N_coef, D_exps=None, D_coef=None, degD=
         degd_ptr = keep[2].ctypes.data
     prm = zr_recon_params(nv, offset, seed, keep[2].ctypes.data, degd_ptr)
     return zr_request(bb, prm), keep
+
+
+def _callback(fn, raised):
+    def call(user, npts, nv, pts, out, st):
+        try:
+            return int(fn(npts, nv, pts, out, st))
+        except BaseException as e:  # the library sees a failed evaluation; the caller re-raises
+            raised.append(e)
+            return 1
+    return zr_eval_fn(call)
+
+
+def make_callback_request(nv, degN, seed, fn, rational=False, degD=None, TN_hint=0, TD_hint=0, offset=0):
+    """A zr_request whose black box is fn(npts, nv, pts, out, stream) -> int
+    over raw device pointers (see Context.reconstruct_callback), plus what it
+    points to.  keep[-1] collects exceptions raised inside fn."""
+    raised = []
+    cb = _callback(fn, raised)
+    dN = np.ascontiguousarray(degN, dtype=np.int32)
+    dD = np.ascontiguousarray(degD if degD is not None else degN, dtype=np.int32)
+    bb = zr_blackbox(BB_CALL_RATIONAL if rational else BB_CALL_POLY, nv, TN_hint, None, None, TD_hint, None, None,
+                     cb, None)
+    prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data)
+    return zr_request(bb, prm), [cb, dN, dD, raised]
+
+
+def device_array(ptr: int, n: int):
+    """A torch int64 view of n residues at a raw device address (no copy),
+    for black-box functions that receive device pointers."""
+    import torch
+
+    class _Dev:
+        __cuda_array_interface__ = dict(shape=(n,), typestr="<i8", data=(ptr, False), version=3)
+
+    return torch.as_tensor(_Dev(), device="cuda")
 
 
 class Server:
