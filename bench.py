@@ -40,16 +40,23 @@ if ROOT not in sys.path:
 METRIC = "Zippel-step skeleton terms/s and mulmod/s vs roofline; serve p50/p99 latency"
 
 
+# the sources of the solve kernel, hashed in this order to key its ncu summary
+SOLVE_SOURCES = ("zr_solve.cuh", "zr_ring.cuh")
+
+
 def solve_traffic(workload_name):
     """DRAM bytes per solve launch from the committed ncu summary of this
     workload, or None when there is none or the solve source changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"k_solve_{workload_name}.md")
-    src = os.path.join(ROOT, "paper_2505_24256_gb300", "csrc", "zr_solve.cuh")
+    csrc = os.path.join(ROOT, "paper_2505_24256_gb300", "csrc")
     try:
         fields = dict(line.split(": ", 1) for line in open(path).read().splitlines()
                       if line.startswith(("traffic_bytes_per_launch: ", "source_sha256_prefix: ")))
-        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for name in SOLVE_SOURCES:
+            h.update(open(os.path.join(csrc, name), "rb").read())
+        cur = h.hexdigest()[:16]
         if fields.get("source_sha256_prefix", "").strip() != cur:
             return None
         return int(fields["traffic_bytes_per_launch"])
@@ -275,14 +282,20 @@ def run_zr(args):
     ske = torch.from_numpy(wl.skel).to(dev)
     skel = ctx.poly(nv, T, ske)
     b = torch.empty((S, T), dtype=torch.int64, device=dev)
-    # probes by the GPU evaluator (outside the timed step)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ctx.zippel_probes(f, k, y, S, cs, z, T, 0, b, T)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    probe_ms = e0.elapsed_time(e1)
+    # probes by the GPU evaluator (outside the timed step): the first call,
+    # then, when that is short, the median of three more
+    probe_times = []
+    for _ in range(4):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.zippel_probes(f, k, y, S, cs, z, T, 0, b, T)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        probe_times.append(e0.elapsed_time(e1))
+        if probe_times[0] > 100.0:
+            break
+    probe_ms = probe_times[0] if len(probe_times) == 1 else sorted(probe_times[1:])[1]
     cap = T * S
     oe = torch.zeros((cap, nv), dtype=torch.uint8, device=dev)
     oc = torch.zeros(cap, dtype=torch.int64, device=dev)
@@ -430,6 +443,10 @@ def run_zr(args):
         "phase_ms": phases,
         "plan": {"s_tile": plan[0], "k_blocks": plan[1]},
         "probe_gen_ms": probe_ms,
+        # the evaluator's product: S x T probes over the G = T distinct anchor
+        # monomials of the hidden function (its terms share x' with the skeleton)
+        "probe_gen": {"ms": probe_ms, "macs": S * T * T, "mac_per_s": S * T * T / (probe_ms * 1e-3),
+                      "frac_of_measured_mac_peak": S * T * T / (probe_ms * 1e-3) / peaks["mac_per_s"]},
         "e2e": {"value": job_rate(T, world, e2e_s), "unit": "terms/s",
                 "h2d_bytes_per_step": T * nv + 8 * k + 8 * S + 8 * S * T,
                 "d2h_bytes_per_step": ne * (nv + 8) + 12},

@@ -16,7 +16,10 @@
 // with the deferred multiply-accumulate.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "zr_internal.h"
+#include "zr_ring.cuh"
 
 namespace zr {
 
@@ -144,133 +147,230 @@ __global__ void k_eval_accum(int64_t Tf, int S, const uint64_t* __restrict__ u, 
   }
 }
 
-// finalize: the merged weights as residues and the squares table
-// UP[g][a] = u_g^(2^a), a < 32
-__global__ void k_eval_finalize(int64_t G, int S, const unsigned long long* __restrict__ Wacc,
-                                const uint64_t* __restrict__ U, Mod M, uint64_t* __restrict__ Wp,
-                                uint64_t* __restrict__ UP) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < G * S) {
-    uint64_t lo = Wacc[idx * 2], hi = Wacc[idx * 2 + 1];
-    // value = hi 2^32 + lo, as a 128-bit number
-    uint64_t vlo = lo + (hi << 32);
-    uint64_t vhi = (hi >> 32) + (vlo < lo);
-    Wp[idx] = reduce128(vhi, vlo, M);
+// Where the weights of the matrix-vector kernel live: column block b
+// (columns s0[b] .. s0[b] + 63) holds, per group, its row of bw[b] words laid
+// out as the kernel stages it ([consumer][column], pairs padded with zero).
+struct RingLayout {
+  int nb;
+  int cg[4], cgp[4], bw[4];
+  int64_t off[4];   // word offset of block b (G bw[b'] words per block before it)
+};
+
+// finalize, for the G groups counted on the device (G <= Tn, the stride of
+// the tables): the merged weights as residues in the ring layout, zero in
+// the padding; the squares table UP[a][g] = u_g^(2^a), a < 32, with its
+// Shoup quotients UPq; the quotients Uq[g] of u_g.
+__global__ void k_eval_finalize(const int64_t* __restrict__ Gdev, int64_t Tn, int S,
+                                const unsigned long long* __restrict__ Wacc, const uint64_t* __restrict__ U, Mod M,
+                                RingLayout L, int rw, uint64_t* __restrict__ Wr, uint64_t* __restrict__ UP,
+                                uint64_t* __restrict__ UPq, uint64_t* __restrict__ Uq) {
+  const int64_t G = *Gdev;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < G * rw) {
+    // entry j of group g's rows: block b, consumer q, column c
+    const int64_t g = idx / rw;
+    int j = (int)(idx - g * rw), b = 0;
+    while (j >= L.bw[b]) j -= L.bw[b++];
+    const int q = j / L.cgp[b], c = j - q * L.cgp[b], sc = q * L.cg[b] + c, s = 64 * b + sc;
+    uint64_t r = 0;
+    if (c < L.cg[b] && s < S) {
+      const uint64_t lo = Wacc[(g * S + s) * 2], hi = Wacc[(g * S + s) * 2 + 1];
+      // value = hi 2^32 + lo, as a 128-bit number
+      const uint64_t vlo = lo + (hi << 32);
+      const uint64_t vhi = (hi >> 32) + (vlo < lo);
+      r = reduce128(vhi, vlo, M);
+    }
+    Wr[L.off[b] + g * L.bw[b] + j] = r;
   }
   if (idx < G) {
     uint64_t x = U[idx];
+    Uq[idx] = shoup_pre(x, M);
     for (int a = 0; a < 32; a++) {
-      UP[idx * 32 + a] = x;
+      UP[a * Tn + idx] = x;
+      UPq[a * Tn + idx] = shoup_pre(x, M);
       x = mul_mod(x, x, M);
     }
   }
 }
 
-constexpr int kGC = 32;   // groups per staged chunk
-
-// The matrix-vector product out[s][i] = sum_g W[g][s] u_g^(i+off): a CTA owns
-// NI consecutive i and NG thread groups of NI threads; group q accumulates
-// the ST columns q ST .. q ST + ST - 1 for its thread's i.  Per chunk of kGC
-// groups the CTA stages the weights and builds X[g][t] = u_g^(I0+off+t) by
-// doubling (the paper's power table), shared by all NG groups; every thread
-// then runs ST deferred multiply-accumulates per group, X[g][t] times a
-// broadcast pair of weights.
-template <int ST, int NG, int NI>
-struct EvalCfg {
-  static constexpr int STP = (ST + 1) & ~1;
-  static constexpr int NT = NI * NG;
-  static constexpr int WW = NG * STP;
-  static constexpr int MINB = NT <= 448 ? 2 : 1;   // two CTAs per SM where the registers allow
+// The matrix-vector product out[s][i] = sum_g W[g][s] u_g^(i+off),
+// warp-specialised like the solve.  A CTA owns a tile of 32 consecutive i and
+// a range of groups, walked in chunks of 32 through a ring of shared-memory
+// stages:
+//   warp 0 (producer)     lane = group: stages the chunk's weights with
+//                         cp.async and fills the power table
+//                         X[t][g] = u_g^(I0+off+t), t < 32, starting from
+//                         u_g^(I0+off) (a product of squares u_g^(2^a) over
+//                         the set bits of the exponent) and running a Shoup
+//                         multiply by u_g along t (the paper's power table,
+//                         Sec. 2.2, one row per group);
+//   warps 1.. (consumers) lane = i: CG columns each, acc_s += X[i][g] W[g][s]
+//                         in 160-bit accumulators, reduced once.
+// Every power is computed once and read by all consumer warps.  Columns
+// beyond 64 run as further launches over the next column block.
+template <int CG, int G>
+struct EvalRingCfg {
+  static constexpr int TI = 32;               // i per CTA: one per consumer lane
+  static constexpr int GC = 32;               // groups per chunk: one per producer lane
+  static constexpr int NST = 4;               // ring stages
+  static constexpr int XP = GC + 1;           // padded row of X: the consumers read it across rows
+  static constexpr int CGP = (CG + 1) & ~1;   // a consumer's columns, padded to pairs
+  static constexpr int BW = G * CGP;          // staged weight row width
+  static constexpr int NT = 32 * (1 + G);
+  static constexpr int REG = CG <= 2 ? 72 : (CG <= 3 ? 80 : (CG <= 4 ? 104 : (CG <= 6 ? 136 : 168)));
+  static constexpr int FIT = 65536 / (NT * REG);
+  static constexpr int MINB = FIT < 1 ? 1 : (FIT > 6 ? 6 : FIT);
+  static constexpr size_t XB = sizeof(uint64_t) * NST * TI * XP;
+  static constexpr size_t WB = sizeof(uint64_t) * NST * GC * BW;
+  static constexpr size_t SMEM = XB + WB + sizeof(uint64_t) * 2 * NST;
 };
 
-template <int ST, int NG, int NI>
-struct EvalSmem {
-  uint64_t X[kGC][NI];
-  uint64_t W[kGC][EvalCfg<ST, NG, NI>::WW];
-  uint64_t part[kGC][8];
-  uint64_t sq[kGC][8], sqp[kGC][8];   // u_g^(2^a) and its Shoup quotient, a < log2(NI)
-};
-
-template <int ST, int NG, int NI>
-__global__ void __launch_bounds__(NI* NG, EvalCfg<ST, NG, NI>::MINB) k_eval_matvec(int64_t T, int S, int offset, int64_t G, int gsplit,
-                                                           const uint64_t* __restrict__ UP,
-                                                           const uint64_t* __restrict__ Wp, Mod M,
-                                                           uint64_t* __restrict__ out, int64_t ldo,
-                                                           uint64_t* __restrict__ partial) {
-  using C = EvalCfg<ST, NG, NI>;
+template <int CG, int G>
+__global__ void __launch_bounds__(EvalRingCfg<CG, G>::NT, EvalRingCfg<CG, G>::MINB)
+    k_eval_ring(int64_t T, int S, int s0, int offset, const int64_t* __restrict__ Gdev, int64_t NG, int gsplit,
+                const uint64_t* __restrict__ UP,
+                const uint64_t* __restrict__ UPq, const uint64_t* __restrict__ U, const uint64_t* __restrict__ Uq,
+                const uint64_t* __restrict__ Wb, Mod M, uint64_t* __restrict__ out, int64_t ldo,
+                uint64_t* __restrict__ partial, uint32_t* __restrict__ status) {
+  using C = EvalRingCfg<CG, G>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  EvalSmem<ST, NG, NI>& sm = *reinterpret_cast<EvalSmem<ST, NG, NI>*>(smraw);
-  const int tid = threadIdx.x, li = tid % NI, grp = tid / NI;
-  const int64_t I0 = (int64_t)blockIdx.x * NI;
+  uint64_t(*xs)[C::TI][C::XP] = reinterpret_cast<uint64_t(*)[C::TI][C::XP]>(smraw);
+  uint64_t(*ws)[C::GC][C::BW] = reinterpret_cast<uint64_t(*)[C::GC][C::BW]>(smraw + C::XB);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw + C::XB + C::WB);
+  uint64_t* empty = full + C::NST;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int SC = (S - s0) < G * CG ? S - s0 : G * CG;   // columns of this launch
+  if (tid == 0)
+    for (int st = 0; st < C::NST; st++) {
+      mbar_init(&full[st], 32);
+      mbar_init(&empty[st], G);
+    }
+  __syncthreads();
+  const int64_t I0 = (int64_t)blockIdx.x * C::TI;
   const int split = blockIdx.y;
-  const int64_t glo = G * split / gsplit, ghi = G * (split + 1) / gsplit;
-  const uint64_t E = (uint64_t)(I0 + offset);
-  Acc8 acc[ST];
+  const int64_t G_ = *Gdev;   // groups; NG (>= G_) is the stride of the squares table
+  const int64_t glo = G_ * split / gsplit, ghi = G_ * (split + 1) / gsplit;
+  const int nch = (int)((ghi - glo + C::GC - 1) / C::GC);
+
+  if (warp == 0) {
+    // ---- producer warp
+    const uint32_t emask = (uint32_t)(I0 + offset);   // the exponent E < 2^32 of t = 0
+    for (int c = 0; c < nch; c++) {
+      const int st = c % C::NST;
+      const uint32_t ph = (c / C::NST) & 1;
+      if (c >= C::NST && !mbar_wait(&empty[st], ph ^ 1)) {
+        atomicOr(status, ST_TIMEOUT);
+        cp_async_wait<0>();
+        return;
+      }
+      const int64_t gc = glo + (int64_t)c * C::GC;
+      const int gn = (ghi - gc) < C::GC ? (int)(ghi - gc) : C::GC;
+      // weights of the chunk: gn consecutive rows, already in the staged layout
+      {
+        const uint64_t* src = Wb + gc * C::BW;
+        uint64_t* dst = &ws[st][0][0];
+        const int n16 = gn * C::BW / 2;
+        for (int q = lane; q < n16; q += 32) cp_async16(dst + 2 * q, src + 2 * q);
+      }
+      cp_async_commit();
+      if (lane < gn) {
+        const int64_t gg = gc + lane;
+        const uint64_t u = __ldg(U + gg), uq = __ldg(Uq + gg);
+        const uint64_t u16 = __ldg(UP + 4 * NG + gg), u16q = __ldg(UPq + 4 * NG + gg);
+        // u_g^E: a Shoup product of the squares of E's set bits, their loads
+        // issued eight at a time
+        uint64_t x = 1;
+        for (uint32_t m = emask; m;) {
+          uint64_t f[8], fq[8];
+          bool have[8];
 #pragma unroll
-  for (int c = 0; c < ST; c++) acc[c] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
-  for (int64_t gc = glo; gc < ghi; gc += kGC) {
-    const int gn = (ghi - gc) < kGC ? (int)(ghi - gc) : kGC;
-    __syncthreads();
-    // base_g = u_g^E = prod over the set bits of E of UP[g][a]; 8 parts per group
-    for (int t = tid; t < kGC * 8; t += C::NT) {
-      const int g = t >> 3, pt = t & 7;
-      uint64_t prod = 1;
-      if (g < gn)
-        for (int a = pt; a < 32; a += 8)
-          if ((E >> a) & 1) prod = mul_mod(prod, UP[(gc + g) * 32 + a], M);
-      sm.part[g][pt] = prod;
-    }
-    // weights of the chunk, [g][group][column], zero padded
-    for (int t = tid; t < kGC * C::WW; t += C::NT) {
-      const int g = t / C::WW, r = t - g * C::WW, q = r / C::STP, c = r - q * C::STP, sidx = q * ST + c;
-      sm.W[g][r] = (g < gn && c < ST && sidx < S) ? Wp[(gc + g) * S + sidx] : 0;
-    }
-    __syncthreads();
-    for (int g = tid; g < kGC; g += C::NT) {
-      uint64_t b = 1;
-      for (int q = 0; q < 8; q++) b = mul_mod(b, sm.part[g][q], M);
-      sm.X[g][0] = b;
-    }
-    constexpr int LA = NI >= 256 ? 8 : (NI >= 128 ? 7 : (NI >= 64 ? 6 : 5));   // doubling levels
-    for (int t = tid; t < kGC * LA; t += C::NT) {
-      const int g = t / LA, a = t - g * LA;
-      const uint64_t q = g < gn ? UP[(gc + g) * 32 + a] : 0;
-      sm.sq[g][a] = q;
-      sm.sqp[g][a] = shoup_pre(q, M);
-    }
-    __syncthreads();
-    // doubling: X[g][t + 2^a] = X[g][t] u_g^(2^a), a Shoup multiply by a constant of the level
-    for (int a = 0; a < LA; a++) {
-      const int half = 1 << a;
-      for (int idx = tid; idx < kGC * half; idx += C::NT) {
-        const int g = idx / half, t = idx - g * half;
-        if (g < gn) sm.X[g][t + half] = canon(shoup_lazy(sm.X[g][t], sm.sq[g][a], sm.sqp[g][a], M), M);
-      }
-      __syncthreads();
-    }
-    for (int g = 0; g < gn; g++) {
-      const uint64_t x = sm.X[g][li];
-      const uint32_t x0 = lo32(x), x1 = hi32(x);
-      const uint64_t* row = &sm.W[g][grp * C::STP];
+          for (int q = 0; q < 8; q++) {
+            have[q] = m != 0;
+            const int a = have[q] ? __ffs(m) - 1 : 0;
+            m &= m - 1;
+            f[q] = have[q] ? __ldg(UP + (int64_t)a * NG + gg) : 0;
+            fq[q] = have[q] ? __ldg(UPq + (int64_t)a * NG + gg) : 0;
+          }
 #pragma unroll
-      for (int c = 0; c + 1 < ST; c += 2) {
-        const uint4 w = *reinterpret_cast<const uint4*>(row + c);
-        mac8(acc[c], x0, x1, w.x, w.y);
-        mac8(acc[c + 1], x0, x1, w.z, w.w);
+          for (int q = 0; q < 8; q++)
+            if (have[q]) x = shoup_lazy(x, f[q], fq[q], M);
+        }
+        x = canon(x, M);
+        // two interleaved chains, t < 16 and t >= 16, one Shoup multiply by u per step
+        uint64_t xb = canon(shoup_lazy(x, u16, u16q, M), M);
+#pragma unroll 4
+        for (int t = 0; t < C::TI / 2; t++) {
+          xs[st][t][lane] = x;
+          xs[st][t + C::TI / 2][lane] = xb;
+          x = canon(shoup_lazy(x, u, uq, M), M);
+          xb = canon(shoup_lazy(xb, u, uq, M), M);
+        }
       }
-      if (ST & 1) {
-        const uint2 w = *reinterpret_cast<const uint2*>(row + ST - 1);
-        mac8(acc[ST - 1], x0, x1, w.x, w.y);
-      }
+      cp_async_wait<0>();
+      mbar_arrive(&full[st]);
     }
+    return;
   }
-  const int64_t i = I0 + li;
+  // ---- consumer w: columns s0 + w CG .. s0 + w CG + CG - 1
+  const int w = warp - 1;
+  Acc8 acc[CG];
+#pragma unroll
+  for (int q = 0; q < CG; q++) acc[q] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
+  for (int c = 0; c < nch; c++) {
+    const int st = c % C::NST;
+    const uint32_t ph = (c / C::NST) & 1;
+    if (!mbar_wait(&full[st], ph)) {
+      atomicOr(status, ST_TIMEOUT);
+      return;
+    }
+    const int64_t gc = glo + (int64_t)c * C::GC;
+    const int gn = (ghi - gc) < C::GC ? (int)(ghi - gc) : C::GC;
+    const uint64_t* xrow = xs[st][lane];
+    if (gn == C::GC) {
+#pragma unroll
+      for (int g = 0; g < C::GC; g++) {
+        const uint64_t x = xrow[g];
+        const uint32_t x0 = lo32(x), x1 = hi32(x);
+        const uint64_t* row = &ws[st][g][w * C::CGP];
+#pragma unroll
+        for (int q = 0; q + 1 < CG; q += 2) {
+          const uint4 v = *reinterpret_cast<const uint4*>(row + q);
+          mac8(acc[q], x0, x1, v.x, v.y);
+          mac8(acc[q + 1], x0, x1, v.z, v.w);
+        }
+        if (CG & 1) {
+          const uint2 v = *reinterpret_cast<const uint2*>(row + CG - 1);
+          mac8(acc[CG - 1], x0, x1, v.x, v.y);
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int g = 0; g < gn; g++) {
+        const uint64_t x = xrow[g];
+        const uint32_t x0 = lo32(x), x1 = hi32(x);
+        const uint64_t* row = &ws[st][g][w * C::CGP];
+#pragma unroll
+        for (int q = 0; q + 1 < CG; q += 2) {
+          const uint4 v = *reinterpret_cast<const uint4*>(row + q);
+          mac8(acc[q], x0, x1, v.x, v.y);
+          mac8(acc[q + 1], x0, x1, v.z, v.w);
+        }
+        if (CG & 1) {
+          const uint2 v = *reinterpret_cast<const uint2*>(row + CG - 1);
+          mac8(acc[CG - 1], x0, x1, v.x, v.y);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+  const int64_t i = I0 + lane;
   if (i >= T) return;
 #pragma unroll
-  for (int c = 0; c < ST; c++) {
-    const int sidx = grp * ST + c;
-    if (sidx >= S) continue;
-    const uint64_t r = acc8_value(acc[c], M);
+  for (int q = 0; q < CG; q++) {
+    const int sidx = s0 + w * CG + q;
+    if (w * CG + q >= SC) continue;
+    const uint64_t r = acc8_value(acc[q], M);
     if (gsplit == 1) out[(int64_t)sidx * ldo + i] = r;
     else partial[((int64_t)split * S + sidx) * T + i] = r;
   }
@@ -287,74 +387,111 @@ __global__ void k_eval_combine(int64_t T, int S, int gsplit, const uint64_t* __r
   out[(int64_t)s * ldo + i] = r;
 }
 
-template <int ST, int NG, int NI>
-static void launch_matvec_t(int64_t T, int S, int offset, int64_t G, int gsplit, const uint64_t* UP,
-                            const uint64_t* Wp, const Mod& M, uint64_t* out, int64_t ldo, uint64_t* partial,
-                            cudaStream_t st) {
-  const size_t smem = sizeof(EvalSmem<ST, NG, NI>);
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_eval_matvec<ST, NG, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = true;
+template <int CG, int G>
+static int ring_occupancy_t() {
+  using C = EvalRingCfg<CG, G>;
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaFuncSetAttribute(k_eval_ring<CG, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval_ring<CG, G>, C::NT, C::SMEM) != cudaSuccess || n < 1)
+      n = 1;
+    per_sm = n;
   }
-  dim3 grid(cdiv(T, NI), gsplit);
-  {
-    k_eval_matvec<ST, NG, NI><<<grid, NI * NG, smem, st>>>(T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial);
-    note_launch();
-  }
+  return per_sm;
 }
 
-// Launch shape by S: (columns per thread, thread groups, i per CTA).
-struct EvalShape {
-  int st, ng, ni;
+template <int CG, int G>
+static void launch_ring_t(int64_t T, int S, int s0, int offset, const int64_t* Gdev, int64_t NG, int gsplit,
+                          const uint64_t* UP,
+                          const uint64_t* UPq, const uint64_t* U, const uint64_t* Uq, const uint64_t* Wb,
+                          const Mod& M, uint64_t* out, int64_t ldo, uint64_t* partial, uint32_t* status,
+                          cudaStream_t st) {
+  using C = EvalRingCfg<CG, G>;
+  ring_occupancy_t<CG, G>();   // also sets the shared-memory attribute
+  dim3 grid(cdiv(T, C::TI), gsplit);
+  k_eval_ring<CG, G><<<grid, C::NT, C::SMEM, st>>>(T, S, s0, offset, Gdev, NG, gsplit, UP, UPq, U, Uq, Wb, M, out,
+                                                   ldo, partial, status);
+  note_launch();
+}
+
+// The instances: columns per consumer and consumer warps for a block of
+// SC <= 64 columns (at most 8 consumers).
+using RingLaunch = void (*)(int64_t, int, int, int, const int64_t*, int64_t, int, const uint64_t*, const uint64_t*,
+                            const uint64_t*,
+                            const uint64_t*, const uint64_t*, const Mod&, uint64_t*, int64_t, uint64_t*, uint32_t*,
+                            cudaStream_t);
+struct RingInst {
+  int cg, g;
+  RingLaunch launch;
+  int (*occupancy)();
 };
-static EvalShape eval_shape(int S) {
-  // three columns per thread (four beyond 48 columns) keep a thread within
-  // ~80 registers; as many i per CTA as keep two CTAs (<= 448 threads) per SM
-  const int st = S <= 48 ? 3 : 4;
-  const int ng = (S + st - 1) / st;
-  int ni = 256;
-  while (ni > 32 && ni * ng > 448) ni >>= 1;
-  return {st, ng, ni};
+#define ZR_RING(CGV, GV) {CGV, GV, launch_ring_t<CGV, GV>, ring_occupancy_t<CGV, GV>}
+static const RingInst kRing[] = {ZR_RING(1, 1), ZR_RING(2, 1), ZR_RING(3, 1), ZR_RING(3, 2), ZR_RING(3, 3),
+                                 ZR_RING(3, 4), ZR_RING(3, 5), ZR_RING(3, 6), ZR_RING(3, 7), ZR_RING(3, 8),
+                                 ZR_RING(4, 7), ZR_RING(4, 8), ZR_RING(6, 6), ZR_RING(6, 7), ZR_RING(6, 8),
+                                 ZR_RING(8, 7), ZR_RING(8, 8)};
+#undef ZR_RING
+
+static const RingInst* ring_inst(int SC) {
+  const int cg = SC <= 2 ? SC : (SC <= 24 ? 3 : (SC <= 32 ? 4 : (SC <= 48 ? 6 : 8)));
+  const int g = (SC + cg - 1) / cg;
+  for (const RingInst& r : kRing)
+    if (r.cg == cg && r.g == g) return &r;
+  return nullptr;
 }
 
-template <int NG>
-static void launch_matvec_g(int st, int ni, int64_t T, int S, int offset, int64_t G, int gsplit, const uint64_t* UP,
-                            const uint64_t* Wp, const Mod& M, uint64_t* out, int64_t ldo, uint64_t* partial,
-                            cudaStream_t s) {
-  if (st == 4) {
-    if constexpr (NG >= 13) launch_matvec_t<4, NG, 32>(T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, s);
-    return;
+// The weight layout for S columns over G groups (blocks of 64 columns).
+static RingLayout ring_layout(int S, int64_t G) {
+  RingLayout L{};
+  int64_t off = 0;
+  for (int s0 = 0; s0 < S; s0 += 64) {
+    const RingInst* r = ring_inst(S - s0 < 64 ? S - s0 : 64);
+    const int b = L.nb++;
+    L.cg[b] = r->cg;
+    L.cgp[b] = (r->cg + 1) & ~1;
+    L.bw[b] = r->g * L.cgp[b];
+    L.off[b] = off;
+    off += G * L.bw[b];
   }
-  if constexpr (NG <= 16) {
-    constexpr int NI1 = NG == 1 ? 256 : (NG <= 3 ? 128 : (NG <= 7 ? 64 : 32));
-    (void)ni;
-    launch_matvec_t<3, NG, NI1>(T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, s);
+  return L;
+}
+static int64_t ring_words(int S, int64_t G) {
+  const RingLayout L = ring_layout(S, G);
+  return L.off[L.nb - 1] + G * L.bw[L.nb - 1];
+}
+
+static void launch_ring(int64_t T, int S, int offset, const int64_t* Gdev, int64_t NG, int gsplit, const uint64_t* UP,
+                        const uint64_t* UPq, const uint64_t* U, const uint64_t* Uq, const uint64_t* Wr,
+                        const RingLayout& L, const Mod& M, uint64_t* out, int64_t ldo, uint64_t* partial,
+                        uint32_t* status, cudaStream_t st) {
+  for (int b = 0; b < L.nb; b++) {
+    const int s0 = 64 * b;
+    const RingInst* r = ring_inst(S - s0 < 64 ? S - s0 : 64);
+    r->launch(T, S, s0, offset, Gdev, NG, gsplit, UP, UPq, U, Uq, Wr + L.off[b], M, out, ldo, partial, status, st);
   }
 }
 
-static void launch_matvec(const EvalShape& sh, int64_t T, int S, int offset, int64_t G, int gsplit,
-                          const uint64_t* UP, const uint64_t* Wp, const Mod& M, uint64_t* out, int64_t ldo,
-                          uint64_t* partial, cudaStream_t st) {
-#define ZR_MV(NGV) \
-  case NGV: launch_matvec_g<NGV>(sh.st, sh.ni, T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, st); break;
-  switch (sh.ng) {
-    ZR_MV(1) ZR_MV(2) ZR_MV(3) ZR_MV(4) ZR_MV(5) ZR_MV(6) ZR_MV(7) ZR_MV(8)
-    ZR_MV(9) ZR_MV(10) ZR_MV(11) ZR_MV(12) ZR_MV(13) ZR_MV(14) ZR_MV(15) ZR_MV(16)
-    default: break;
-  }
-#undef ZR_MV
-}
-
-// Group splits so that the launch has at least eight CTAs per SM (about four
-// waves of two: the last wave's imbalance stays small).
+// Group splits: the smallest count that gives at least two waves of CTAs
+// with the last one at least 97% full (else the best fill up to 32 splits),
+// keeping 64 or more groups per split.
 static int eval_gsplit(const zr_ctx* ctx, int64_t T, int S, int64_t Tf) {
-  const EvalShape sh = eval_shape(S);
-  const int64_t ctas = (int64_t)cdiv(T, sh.ni);
-  int gsplit = 1;
-  const int64_t want = 8ll * (ctx && ctx->sms ? ctx->sms : 152);
-  while (ctas * gsplit < want && gsplit < 64 && Tf / (gsplit * 2) >= 2 * kGC) gsplit *= 2;
-  return gsplit;
+  const int64_t ctas = (int64_t)cdiv(T, 32);
+  const int64_t slots = (int64_t)(ctx && ctx->sms ? ctx->sms : 152) * ring_inst(S < 64 ? S : 64)->occupancy();
+  if (ctas >= 8 * slots) return 1;
+  int best = 1;
+  double best_fill = 0;
+  for (int gs = 1; gs <= 32; gs++) {
+    if (gs > 1 && Tf / gs < 64) break;
+    const double waves = (double)(ctas * gs) / (double)slots;
+    const double fill = waves / std::ceil(waves);
+    if (waves >= 2 && fill >= 0.97) return gs;
+    if (fill > best_fill + 1e-9) {
+      best = gs;
+      best_fill = fill;
+    }
+  }
+  return best;
 }
 
 // Workspace bytes the evaluator needs for (f, S, T).
@@ -380,7 +517,8 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   const int gsplit = eval_gsplit(ctx, T, S, Tf);
   auto layout = [&](Carver& cv, uint64_t** tabY, uint64_t** tabZ, uint64_t** tabC, uint64_t** u, uint64_t** w,
                     uint64_t** htab, int64_t** bsum, int32_t** gid, uint64_t** U, unsigned long long** Wacc,
-                    uint64_t** Wp, uint64_t** UP, uint64_t** partial, int64_t** Gdev) {
+                    uint64_t** Wp, uint64_t** UP, uint64_t** UPq, uint64_t** Uq, uint64_t** partial,
+                    int64_t** Gdev) {
     const int64_t Tn = Tf > 0 ? Tf : 1;
     *tabY = cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
     *tabZ = cv.take<uint64_t>((size_t)nv * kPowTab);
@@ -392,18 +530,20 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
     *gid = cv.take<int32_t>(H);
     *U = cv.take<uint64_t>(Tn);
     *Wacc = cv.take<unsigned long long>((size_t)Tn * S * 2);
-    *Wp = cv.take<uint64_t>((size_t)Tn * S);
+    *Wp = cv.take<uint64_t>((size_t)ring_words(S, Tn));
     *UP = cv.take<uint64_t>((size_t)Tn * 32);
+    *UPq = cv.take<uint64_t>((size_t)Tn * 32);
+    *Uq = cv.take<uint64_t>(Tn);
     *partial = cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
     *Gdev = cv.take<int64_t>(1);
   };
-  uint64_t *tabY, *tabZ, *tabC, *u, *w, *htab, *U, *UP, *partial;
+  uint64_t *tabY, *tabZ, *tabC, *u, *w, *htab, *U, *UP, *UPq, *Uq, *partial;
   int64_t *bsum, *Gdev;
   int32_t* gid;
   unsigned long long* Wacc;
   uint64_t* Wp;
   Carver cv(base);
-  layout(cv, &tabY, &tabZ, &tabC, &u, &w, &htab, &bsum, &gid, &U, &Wacc, &Wp, &UP, &partial, &Gdev);
+  layout(cv, &tabY, &tabZ, &tabC, &u, &w, &htab, &bsum, &gid, &U, &Wacc, &Wp, &UP, &UPq, &Uq, &partial, &Gdev);
 
   if (T <= 0) return ZR_OK;
   if (Tf == 0) {
@@ -421,14 +561,13 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   { k_scan_small<<<1, kB, 0, st>>>(nbH, bsum, Gdev); note_launch(); }
   { k_slot_ids<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, htab, bsum, gid); note_launch(); }
   { k_eval_accum<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, S, u, w, htab, H - 1, gid, U, Wacc, status); note_launch(); }
-  // the group count is needed on the host to size the launch
-  int64_t G = 0;
-  cudaError_t e = cudaMemcpyAsync(ctx->h_count + 1, Gdev, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_probes: group count");
-  G = ctx->h_count[1];
-  { k_eval_finalize<<<cdiv(G * S > G ? G * S : G, 256), 256, 0, st>>>(G, S, Wacc, U, M, Wp, UP); note_launch(); }
-  launch_matvec(eval_shape(S), T, S, offset, G, gsplit, UP, Wp, M, out, ldo, partial, st);
+  // the group count stays on the device: the kernels read it, sized for Tf groups
+  const int64_t Tn = Tf;
+  const RingLayout L = ring_layout(S, Tn);
+  int rw = 0;
+  for (int b = 0; b < L.nb; b++) rw += L.bw[b];
+  { k_eval_finalize<<<cdiv(Tn * rw, 256), 256, 0, st>>>(Gdev, Tn, S, Wacc, U, M, L, rw, Wp, UP, UPq, Uq); note_launch(); }
+  launch_ring(T, S, offset, Gdev, Tn, gsplit, UP, UPq, U, Uq, Wp, L, M, out, ldo, partial, status, st);
   if (gsplit > 1) { k_eval_combine<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, gsplit, partial, M, out, ldo); note_launch(); }
   return cuda_err(ctx, cudaGetLastError(), "zr_zippel_probes");
 }
@@ -451,8 +590,10 @@ size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t
   cv.take<int32_t>(H);
   cv.take<uint64_t>(Tn);
   cv.take<unsigned long long>((size_t)Tn * S * 2);
-  cv.take<uint64_t>((size_t)Tn * S);
+  cv.take<uint64_t>((size_t)ring_words(S, Tn));
   cv.take<uint64_t>((size_t)Tn * 32);
+  cv.take<uint64_t>((size_t)Tn * 32);
+  cv.take<uint64_t>(Tn);
   cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
   cv.take<int64_t>(1);
   return cv.off;

@@ -5,50 +5,9 @@
 
 #include "zr_device.cuh"
 #include "zr_kernels.cuh"
+#include "zr_ring.cuh"
 
 namespace zr {
-
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-// ---------------------------------------------------------------------------
-// Shared-memory barriers (mbarrier) for the producer/consumer ring.  A wait
-// uses try_wait (the warp sleeps in hardware until the phase completes or a
-// short time limit passes) and is bounded: after kSpinLimit tries it gives
-// up and reports failure.
-// ---------------------------------------------------------------------------
-
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-// true once the phase of the given parity has completed; false after `limit`
-// tries (timeout)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit) {
-  const uint32_t a = smem_addr(bar);
-  for (uint32_t it = 0; it < limit; it++) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
 
 // ---------------------------------------------------------------------------
 // a4 + a5: the hot loop, warp-specialised.  A work item is one entry, one

@@ -232,3 +232,22 @@ def test_autotuned_plan_gives_the_same_skeleton(ctx):
     after = D.step(ctx, b)
     assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
     assert np.array_equal(after[0], wl.exps) and np.array_equal(after[1], wl.coef)
+
+
+@pytest.mark.parametrize("S,T,k,offset", [(80, 300, 2, 0), (130, 97, 3, 1), (7, 5000, 1, 0)])
+def test_probes_general_function(ctx, orc, S, T, k, offset):
+    """Probes of a hidden function without the step's structure (groups of
+    uneven size), with sample sets wider than one column block of the
+    evaluator, and split group ranges."""
+    rnd = random.Random(S * 1000 + T)
+    nv = 5
+    wl = W.poly_simplex_workload(600 + S, nv, 8, 400)
+    y = [rnd.randrange(1, P63) for _ in range(k)]
+    cs = [rnd.randrange(1, P63) for _ in range(S)]
+    z = [rnd.randrange(1, P63) for _ in range(nv)]
+    fe, fc = d8(wl.exps), d64(wl.coef)
+    f = ctx.poly(nv, wl.exps.shape[0], fe, fc)
+    b = zeros64(S, T)
+    ctx.zippel_probes(f, k, d64(y), S, d64(cs), d64(z), T, offset, b, T)
+    want = orc.zippel_probes(wl.exps, wl.coef, k, y, cs, z, T, offset=offset)
+    assert np.array_equal(h64(b), want)
