@@ -189,6 +189,46 @@ def run_reference(args):
     return 0
 
 
+def reconstruction_configs(ctx, with_oracle):
+    """Full reconstructions through zr_reconstruct (host arrays in, host
+    arrays out): the plain 3-variable polynomial (T = 200) and the balanced
+    rational function (N 5000 / D 3000 terms); wall time per call after one
+    warm-up, checked against the hidden function."""
+    import numpy as np
+    from paper_2505_24256_gb300 import workloads as W
+
+    out = {}
+    wl = W.plain_poly_3var()
+    ctx.reconstruct(wl.nv, wl.deg, wl.seed, wl.exps, wl.coef)
+    reps, t0 = 20, time.perf_counter()
+    for _ in range(reps):
+        (e, c), _, info = ctx.reconstruct(wl.nv, wl.deg, wl.seed, wl.exps, wl.coef)
+    dt = (time.perf_counter() - t0) / reps
+    ok = np.array_equal(e, wl.exps) and np.array_equal(c, wl.coef)
+    r = {"ms": 1e3 * dt, "reconstructions_per_s": 1.0 / dt, "terms_per_s": wl.exps.shape[0] / dt,
+         "device_ms": info["device_ms"], "steps": info["steps"], "check": "generator truth" if ok else "MISMATCH"}
+    if with_oracle:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.reconstruct_poly(wl.exps, wl.coef, wl.deg, seed=wl.seed)
+        r["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+    out[wl.name] = r
+    wl = W.balanced_5var()
+    args_ = (wl.nv, wl.degN, wl.seed, wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef)
+    ctx.reconstruct(*args_, degD=wl.degD)
+    reps, t0 = 3, time.perf_counter()
+    for _ in range(reps):
+        (Ne, Nc), (De, Dc), info = ctx.reconstruct(*args_, degD=wl.degD)
+    dt = (time.perf_counter() - t0) / reps
+    ok = np.array_equal(Ne, wl.Nexps) and np.array_equal(Nc, wl.Ncoef) and np.array_equal(De, wl.Dexps) and \
+        np.array_equal(Dc, wl.Dcoef)
+    terms = wl.Ncoef.shape[0] + wl.Dcoef.shape[0]
+    out[wl.name] = {"ms": 1e3 * dt, "terms_per_s": terms / dt, "device_ms": info["device_ms"],
+                    "steps": info["steps"], "redraws": info["redraws"],
+                    "check": "generator truth" if ok else "MISMATCH"}
+    return out
+
+
 def small_steps_modes(ctx, dev, n=64, reps=20):
     """64 small uneven Zippel steps (T = 20..66, S = 11, like the plain
     3-variable reconstruction's steps) three ways, wall clock per round of
@@ -398,6 +438,8 @@ def run_zr(args):
     graph_kernels = graph.kernels
     graph.close()
     small = small_steps_modes(ctx, dev)
+    recons = reconstruction_configs(ctx, with_oracle=world == 1 and not args.no_cpu_baseline) \
+        if args.workload == "batched" else None
 
     if rank != 0:
         ctx.close()
@@ -440,6 +482,7 @@ def run_zr(args):
                        "check": "generator truth" if plain_ok else "MISMATCH"},
         "graph": {"ms_per_step": graph_ms, "kernels_per_launch": graph_kernels},
         "small_steps": small,
+        "reconstructions": recons,
         "phase_ms": phases,
         "plan": {"s_tile": plan[0], "k_blocks": plan[1]},
         "probe_gen_ms": probe_ms,

@@ -330,6 +330,17 @@ zr_status zr_zippel_step_balanced(zr_ctx* ctx, const zr_poly* skelN, const zr_po
  *                             when equal to an earlier sample.
  * A step whose anchor gives equal values (or a pole, or a degenerate Thiele
  * table) is redrawn with the next attempt (at most 64).
+ * Verification (prm.verify, forced on by an unknown degree): after step k the
+ * new skeleton P (N, D for a rational function) is compared with the black
+ * box at one point (r_0..r_k, z_{k+1}..), r from stream 2^32 + 64 k + a:
+ * P(r) = f(r) (N(r) = f(r) D(r), or N(r) D_f(r) = D(r) N_f(r) for a built-in
+ * rational box).  A mismatch (an unlucky anchor, or a degree above the bound)
+ * discards the step and redraws it.  A negative degree bound means unknown:
+ * the step starts with bound 3 and, after each mismatch (or a Thiele table
+ * longer than the bounds allow), doubles it plus one (7, 15, 31, 63; 31 for
+ * a rational function), failing with ZR_ERR_DEGREE after three mismatches at
+ * the largest bound.  Verification draws no value of the other streams, so
+ * a verified run that never mismatches takes the same probes as one without.
  * The rational result is normalised so that the lexicographically smallest
  * exponent vector of the denominator has coefficient 1.
  * ------------------------------------------------------------------------- */
@@ -373,8 +384,10 @@ typedef struct zr_recon_params {
   int32_t nv;
   int32_t offset;         /* 0: probes y^0..y^{T-1};  1: y^1..y^T */
   uint64_t seed;
-  const int32_t* degN;    /* host, nv degree bounds (the polynomial's for ZR_BB_POLY) */
-  const int32_t* degD;    /* host, nv degree bounds of the denominator (rational only) */
+  const int32_t* degN;    /* host, nv degree bounds (the polynomial's for ZR_BB_POLY); < 0: unknown */
+  const int32_t* degD;    /* host, nv degree bounds of the denominator (rational only); < 0: unknown */
+  int32_t verify;         /* nonzero: check every step at a fresh point (see above) */
+  int32_t reserved;       /* 0 */
 } zr_recon_params;
 
 /* Library-allocated result (host memory); free with zr_result_free. */
@@ -395,6 +408,30 @@ typedef struct zr_result {
 zr_status zr_reconstruct(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_params* prm, zr_result** out,
                          void* stream);
 void zr_result_free(zr_result* r);
+
+/* ---------------------------------------------------------------------------
+ * Rational numbers from modular images (Sec. 1: the reconstruction runs
+ * modulo large primes; the rationals are recovered as a final step).
+ * For each of n values, res[i ld + j] is value j modulo primes[i] (device,
+ * i < nprimes, distinct primes in (2^32, 2^63), host array of nprimes <= 8).
+ * The images are combined by the Chinese remainder theorem into x modulo
+ * P = prod primes (Garner's mixed radix), then Wang's rational
+ * reconstruction finds n / d = x (mod P) with |n|, d <= N =
+ * floor(sqrt((P - 1) / 2)): the extended Euclidean algorithm on (P, x) is
+ * stopped at the first remainder r <= N; with the cofactor t of x the value
+ * is sign(t) r / |t|, accepted when 0 < |t| <= N and gcd(r, |t|) = 1 (the
+ * answer is then unique).
+ *   num, den  device, n x words uint64 each, little-endian; num in two's
+ *             complement, den > 0; words >= zr_lift_words(nprimes) (2, 4 or
+ *             8), the high words sign- or zero-extended
+ *   ok        device, n int32: 1 accepted, 0 not (num = den = 0): more
+ *             primes are needed, or the value is no such fraction
+ * Synchronous on `stream`.  Errors: ZR_ERR_INVALID_ARG (sizes, a modulus
+ * that is not a prime in range, repeated primes).
+ * ------------------------------------------------------------------------- */
+int32_t zr_lift_words(int32_t nprimes);   /* 0 when nprimes is not in 1..8 */
+zr_status zr_rational_lift(zr_ctx* ctx, int32_t nprimes, const uint64_t* primes, int64_t n, const uint64_t* res,
+                           int64_t ld, int32_t words, uint64_t* num, uint64_t* den, int32_t* ok, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of reconstructions.

@@ -43,7 +43,11 @@ struct Rng {
 };
 constexpr uint64_t kStreamRest = 1;
 uint64_t stream_step(int k, int attempt) { return 1024ull + 64ull * (uint64_t)k + (uint64_t)attempt; }
+uint64_t stream_verify(int k, int attempt) { return (1ull << 32) + 64ull * (uint64_t)k + (uint64_t)attempt; }
 constexpr int kMaxAttempts = 64;
+constexpr int kAutoDegree = 3;    // first bound of a variable whose degree is unknown
+
+uint64_t hmul(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((unsigned __int128)a * b % p); }
 
 void draw_rest(uint64_t seed, int nv, uint64_t p, uint64_t* z) {
   Rng r(seed, kStreamRest);
@@ -102,6 +106,73 @@ Recon::Recon(zr_ctx* ctx, cudaStream_t st, const zr_blackbox& bb, const zr_recon
   }
   degN_.assign(prm.degN, prm.degN + nv_);
   if (rational_) degD_.assign(prm.degD, prm.degD + nv_);
+  else degD_.assign(nv_, 0);
+  autoN_.assign(nv_, 0);
+  autoD_.assign(nv_, 0);
+  verify_ = prm.verify != 0;
+  for (int m = 0; m < nv_; m++) {
+    if (degN_[m] < 0) autoN_[m] = 1, degN_[m] = kAutoDegree, verify_ = true;
+    if (degD_[m] < 0) autoD_[m] = 1, degD_[m] = kAutoDegree, verify_ = true;
+  }
+}
+
+zr_status Recon::grow_degree(int k) {
+  const int maxd = rational_ ? 31 : 63;
+  bool any = false, grew = false;
+  auto grow = [&](std::vector<int32_t>& d, const std::vector<char>& a) {
+    if (!a[k]) return;
+    any = true;
+    if (d[k] < maxd) {
+      d[k] = std::min(2 * d[k] + 1, maxd);
+      grew = true;
+    }
+  };
+  grow(degN_, autoN_);
+  if (rational_) grow(degD_, autoD_);
+  if (any && !grew && ++maxed_fails_ >= 3)
+    return set_err(ctx_, ZR_ERR_DEGREE, "zr_reconstruct: degree above the largest detectable bound");
+  return ZR_OK;
+}
+
+zr_status Recon::verify_step(int k) {
+  const uint64_t p = M_.p;
+  Rng rng(seed_, stream_verify(k, attempt_));
+  std::vector<uint64_t> pt(nv_);
+  cudaError_t e = d_vpt_.ensure(8 * (size_t)nv_);
+  if (e == cudaSuccess) e = d_vval_.ensure(8 * 4);
+  if (e != cudaSuccess) return cuda_err(ctx_, e, "verification");
+  uint64_t* vv = d_vval_.as<uint64_t>();
+  const uint64_t* dpt = d_vpt_.as<uint64_t>();
+  for (int tries = 0; tries < 8; tries++) {
+    for (int m = 0; m < nv_; m++) pt[m] = m <= k ? rng.residue(p) : z_[m];
+    zr_status r = upload(d_vpt_, pt.data(), 8 * (size_t)nv_);
+    if (r) return r;
+    // the black box: f (or N_f, D_f for a built-in rational function)
+    r = eval_at(fN_, 1, dpt, vv);
+    if (!r && rational_ && !callback_) r = eval_at(fD_, 1, dpt, vv + 1);
+    if (r == ZR_ERR_POLE) continue;   // the function's pole: another point
+    if (r) return r;
+    // the skeleton
+    zr_poly sN = curN_.view();
+    launch_eval_points(&sN, 1, dpt, M_, vv + 2, st_);
+    if (rational_) {
+      zr_poly sD = curD_.view();
+      launch_eval_points(&sD, 1, dpt, M_, vv + 3, st_);
+    }
+    uint64_t h[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(h, vv, sizeof(h), cudaMemcpyDeviceToHost, st_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
+    if (e != cudaSuccess) return cuda_err(ctx_, e, "verification");
+    bool ok;
+    if (!rational_) ok = h[0] == h[2];
+    else if (callback_) ok = h[2] == hmul(h[0], h[3], p);
+    else {
+      if (h[1] == 0) continue;   // a pole of the built-in function
+      ok = hmul(h[2], h[1], p) == hmul(h[3], h[0], p);
+    }
+    return ok ? ZR_OK : set_err(ctx_, ZR_ERR_UNLUCKY, "verification point mismatch");
+  }
+  return set_err(ctx_, ZR_ERR_UNLUCKY, "verification: no point off the poles");
 }
 
 zr_status Recon::eval_at(const DPoly& f, int64_t npts, const uint64_t* pts, uint64_t* out) {
@@ -165,8 +236,11 @@ size_t Recon::estimate_bytes(const zr_blackbox& bb, const zr_recon_params& prm) 
   const int64_t Tf = bb.TN + (rational ? bb.TD : 0);
   int smax = 1;
   for (int m = 0; m < prm.nv; m++) {
-    int s = prm.degN[m] + 1;
-    if (rational) s = 2 * std::max(prm.degN[m], prm.degD[m]) + 2;
+    // an unknown degree may grow to the largest bound
+    const int dn = prm.degN[m] < 0 ? (rational ? 31 : 63) : prm.degN[m];
+    const int dd = rational ? (prm.degD[m] < 0 ? 31 : prm.degD[m]) : 0;
+    int s = dn + 1;
+    if (rational) s = 2 * std::max(dn, dd) + 2;
     smax = std::max(smax, s);
   }
   const size_t row = (size_t)prm.nv + 8;
@@ -232,11 +306,27 @@ zr_status Recon::start() {
     if (!r) r = upload(fD_.coef, Dc_.data(), 8 * Dc_.size());
   }
   if (!r) r = upload(d_z_, z_.data(), 8 * (size_t)nv_);
-  if (!r) r = rational_ ? step0_rational() : step0_poly();
   if (r) return fail(r);
+  attempt_ = 0;
+  for (;;) {
+    r = rational_ ? step0_rational() : step0_poly();
+    if (!r && verify_) r = verify_step(0);
+    if (!r) break;
+    if (r == ZR_ERR_UNLUCKY || (r == ZR_ERR_DEGREE && (autoN_[0] || autoD_[0]))) {
+      const zr_status g = grow_degree(0);
+      if (g) return fail(g);
+      if (attempt_ + 1 < kMaxAttempts) {
+        attempt_++;
+        redraws_++;
+        continue;
+      }
+    }
+    return fail(r);
+  }
   phase_ = RUN;
   k_ = 1;
   attempt_ = 0;
+  maxed_fails_ = 0;
   if (k_ >= nv_) return finalize();
   return ZR_OK;
 }
@@ -244,7 +334,7 @@ zr_status Recon::start() {
 zr_status Recon::step0_poly() {
   const int S = degN_[0] + 1;
   cs_.assign(S, 0);
-  draw_step(seed_, 0, 0, false, 0, S, M_.p, y_.data(), cs_.data());
+  draw_step(seed_, 0, attempt_, false, 0, S, M_.p, y_.data(), cs_.data());
   std::vector<uint64_t> pts = step0_points(nv_, S, cs_.data(), z_.data());
   zr_status r = upload(d_pts_, pts.data(), pts.size() * 8);
   if (!r) r = upload(d_cs_, cs_.data(), cs_.size() * 8);
@@ -264,8 +354,8 @@ zr_status Recon::step0_rational() {
   const uint64_t unit = 1;
   zr_status r = upload(one_, &unit, 8);
   if (r) return r;
-  for (int attempt = 0;; attempt++) {
-    draw_step(seed_, 0, attempt, false, 0, Sf, M_.p, y_.data(), cs_.data());
+  for (;; attempt_++) {
+    draw_step(seed_, 0, attempt_, false, 0, Sf, M_.p, y_.data(), cs_.data());
     std::vector<uint64_t> pts = step0_points(nv_, Sf, cs_.data(), z_.data());
     if ((r = upload(d_pts_, pts.data(), pts.size() * 8))) return r;
     if ((r = upload(d_cs_, cs_.data(), cs_.size() * 8))) return r;
@@ -292,7 +382,7 @@ zr_status Recon::step0_rational() {
                             persist_.as<uint64_t>(), M_, nval, 1, dval, 1, ctx_->d_status_call, st_);
       r = sync_status();
     }
-    if ((r == ZR_ERR_POLE || r == ZR_ERR_UNLUCKY) && attempt + 1 < kMaxAttempts) {
+    if ((r == ZR_ERR_POLE || r == ZR_ERR_UNLUCKY) && attempt_ + 1 < kMaxAttempts) {
       redraws_++;
       continue;
     }
@@ -369,9 +459,10 @@ zr_status Recon::prepare(std::vector<BatchItem>& items, uint32_t* d_status, int6
   }
   // rational: probes of N and D, their ratio, the per-probe Thiele and the
   // balancing, checked before the two steps join the batch
-  const int dN = degN_[k], dD = degD_[k];
-  const int Sf = 2 * std::max(dN, dD) + 2, SN = dN + 1, SD = dD + 1;
   for (;; attempt_++) {
+    // (unknown degrees grow between attempts)
+    const int dN = degN_[k], dD = degD_[k];
+    const int Sf = 2 * std::max(dN, dD) + 2, SN = dN + 1, SD = dD + 1;
     cs_.assign(Sf, 0);
     draw_step(seed_, k, attempt_, true, z_[k], Sf, p, y_.data(), cs_.data());
     zr_status r = upload(d_y_, y_.data(), 8 * (size_t)k);
@@ -439,6 +530,11 @@ zr_status Recon::prepare(std::vector<BatchItem>& items, uint32_t* d_status, int6
       }
     }
     steps_++;
+    if (r == ZR_ERR_DEGREE && (autoN_[k] || autoD_[k])) {
+      const zr_status g = grow_degree(k);
+      if (g) return fail(g);
+      r = ZR_ERR_UNLUCKY;
+    }
     if (retryable(r) && attempt_ + 1 < kMaxAttempts) {
       redraws_++;
       continue;
@@ -468,8 +564,25 @@ zr_status Recon::finish(uint32_t flags, const int64_t* counts) {
     nextD_.T = counts[1];
     curD_.swap(nextD_);
   }
+  if (verify_) {
+    zr_status v = verify_step(k_);
+    if (v == ZR_ERR_UNLUCKY) {
+      // back to the previous skeleton; the step runs again
+      curN_.swap(nextN_);
+      if (rational_) curD_.swap(nextD_);
+      v = grow_degree(k_);
+      if (!v && attempt_ + 1 < kMaxAttempts) {
+        attempt_++;
+        redraws_++;
+        return ZR_OK;
+      }
+      return fail(v ? v : ZR_ERR_UNLUCKY);
+    }
+    if (v) return fail(v);
+  }
   k_++;
   attempt_ = 0;
+  maxed_fails_ = 0;
   if (k_ >= nv_) return finalize();
   return ZR_OK;
 }
@@ -533,9 +646,11 @@ zr_status check_recon_args(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_pa
   if (rational && !prm->degD) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: rational needs degD");
   if (rational && !callback && (bb->TD <= 0 || !bb->D_exps || !bb->D_coef))
     return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: rational black box needs a denominator");
+  if (prm->reserved != 0) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: reserved must be 0");
   for (int m = 0; m < prm->nv; m++) {
-    const int dn = prm->degN[m], dd = rational ? prm->degD[m] : 0;
-    if (dn < 0 || dd < 0 || dn + 1 > 64 || (rational && 2 * std::max(dn, dd) + 2 > 64))
+    // negative: unknown (detected); the detection's first bound fits every range
+    const int dn = std::max(prm->degN[m], 0), dd = rational ? std::max(prm->degD[m], 0) : 0;
+    if (dn + 1 > 64 || (rational && 2 * std::max(dn, dd) + 2 > 64))
       return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_reconstruct: degree bounds out of range");
   }
   return ZR_OK;

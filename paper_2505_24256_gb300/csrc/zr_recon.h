@@ -92,6 +92,14 @@ class Recon {
   zr_status step_entry(const DPoly& skel, int S, const uint64_t* b, int64_t ldb, DPoly& out, uint32_t* d_status,
                        int64_t* d_count, std::vector<BatchItem>& items);
 
+  // the skeleton of step k against the black box at one fresh point:
+  // ZR_OK, ZR_ERR_UNLUCKY on a mismatch, or an error
+  zr_status verify_step(int k);
+  // after a mismatch or a Thiele table too long for the bounds of step k:
+  // grows the unknown bounds of variable k; ZR_OK to redraw, ZR_ERR_DEGREE
+  // after repeated mismatches at the largest bound
+  zr_status grow_degree(int k);
+
   // values of the black box at npts device points (npts x nv_) into out:
   // the built-in evaluator or the caller's function (nonzero: a pole)
   zr_status eval_at(const DPoly& f, int64_t npts, const uint64_t* pts, uint64_t* out);
@@ -108,6 +116,9 @@ class Recon {
   std::vector<uint8_t> Ne_, De_;
   std::vector<uint64_t> Nc_, Dc_;
   std::vector<int32_t> degN_, degD_;
+  std::vector<char> autoN_, autoD_;   // degree of the variable unknown: detected
+  bool verify_ = false;
+  int maxed_fails_ = 0;
   uint64_t seed_;
   int offset_;
   // state
@@ -116,7 +127,7 @@ class Recon {
   std::vector<uint64_t> z_, y_, cs_;
   int k_ = 1, attempt_ = 0, steps_ = 0, redraws_ = 0;
   DPoly fN_, fD_, curN_, curD_, nextN_, nextD_;
-  DBuf d_y_, d_cs_, d_z_, d_b_, d_pts_, d_vals_, scratch_, persist_, fv_, one_, ones_, d_ppts_;
+  DBuf d_y_, d_cs_, d_z_, d_b_, d_pts_, d_vals_, scratch_, persist_, fv_, one_, ones_, d_ppts_, d_vpt_, d_vval_;
   zr_result* result_ = nullptr;
 };
 

@@ -60,7 +60,8 @@ class zr_blackbox(ctypes.Structure):
 
 class zr_recon_params(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int32), ("offset", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("degN", ctypes.c_void_p), ("degD", ctypes.c_void_p)]
+                ("degN", ctypes.c_void_p), ("degD", ctypes.c_void_p), ("verify", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class zr_result(ctypes.Structure):
@@ -119,6 +120,8 @@ SIGNATURES = {
     "zr_zippel_probes": (_ST, [_V, _P, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _I64, _V]),
     "zr_eval_points": (_ST, [_V, _P, _I64, _P, _P, _V]),
     "zr_probe_points": (_ST, [_V, _I32, _I32, _P, _I32, _P, _P, _I64, _I32, _P, _V]),
+    "zr_lift_words": (_I32, [_I32]),
+    "zr_rational_lift": (_ST, [_V, _I32, _P, _I64, _P, _I64, _I32, _P, _P, _P, _V]),
     "zr_zippel_step_balanced": (_ST, [_V, _P, _P, _I32, _P, _I32, _I32, _P, _P, _I64, _I32, _P, _P, _I64, _P,
                                       _P, _P, _I64, _P, _V]),
     "zr_reconstruct": (_ST, [_V, _P, _P, ctypes.POINTER(ctypes.POINTER(zr_result)), _V]),
@@ -347,9 +350,11 @@ class Context:
         return nN.value, nD.value
 
     def reconstruct(self, nv, degN, seed, N_exps, N_coef, D_exps=None, D_coef=None, degD=None, offset=0,
-                    stream=None):
+                    stream=None, verify=False):
         """Full reconstruction of a built-in sparse black box given by host
-        (numpy) arrays.  Returns ((N_exps, N_coef), (D_exps, D_coef) or None, info)."""
+        (numpy) arrays (a negative degree bound: unknown, detected; verify:
+        check every step at a fresh point).
+        Returns ((N_exps, N_coef), (D_exps, D_coef) or None, info)."""
         rational = D_exps is not None
         N_exps = np.ascontiguousarray(N_exps, dtype=np.uint8)
         N_coef = np.ascontiguousarray(N_coef, dtype=np.uint64)
@@ -361,15 +366,22 @@ class Context:
             bb.TD, bb.D_exps, bb.D_coef = D_exps.shape[0], D_exps.ctypes.data, D_coef.ctypes.data
         dN = np.ascontiguousarray(degN, dtype=np.int32)
         dD = np.ascontiguousarray(degD if degD is not None else degN, dtype=np.int32)
-        prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data)
+        prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data, 1 if verify else 0, 0)
         res = ctypes.POINTER(zr_result)()
         st = self.L.zr_reconstruct(self._h, ctypes.byref(bb), ctypes.byref(prm), ctypes.byref(res), _stream(stream))
         self.check(st, "zr_reconstruct")
         return _take_result(self.L, res)
 
 
+    def rational_lift(self, primes, res, ld, words, num, den, ok, stream=None):
+        """zr_rational_lift over n = res's columns (device tensors; primes a host list)."""
+        pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint64))
+        n = int(ok.shape[0])
+        self.check(self.L.zr_rational_lift(self._h, len(pr), pr.ctypes.data, n, _ptr(res), ld, words, _ptr(num),
+                                           _ptr(den), _ptr(ok), _stream(stream)), "zr_rational_lift")
+
     def reconstruct_callback(self, nv, degN, seed, fn, rational=False, degD=None, TN_hint=0, TD_hint=0, offset=0,
-                             stream=None):
+                             stream=None, verify=False):
         """Full reconstruction of a black box given as a function
         fn(npts, nv, pts, out, stream) -> int over raw device pointers (pts:
         npts x nv residues, out: npts residues; nonzero return: a pole).
@@ -380,7 +392,7 @@ class Context:
                          None, cb, None)
         dN = np.ascontiguousarray(degN, dtype=np.int32)
         dD = np.ascontiguousarray(degD if degD is not None else degN, dtype=np.int32)
-        prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data)
+        prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data, 1 if verify else 0, 0)
         res = ctypes.POINTER(zr_result)()
         st = self.L.zr_reconstruct(self._h, ctypes.byref(bb), ctypes.byref(prm), ctypes.byref(res), _stream(stream))
         if raised:
@@ -389,6 +401,20 @@ class Context:
             raise raised[0]
         self.check(st, "zr_reconstruct")
         return _take_result(self.L, res)
+
+
+def lift_words(nprimes: int) -> int:
+    return int(load().zr_lift_words(nprimes))
+
+
+def words_to_int(words, signed: bool) -> int:
+    """A little-endian uint64 word row as a Python integer."""
+    v = 0
+    for i, w in enumerate(np.asarray(words, dtype=np.uint64).tolist()):
+        v |= int(w) << (64 * i)
+    if signed and words.size and (int(words[-1]) >> 63):
+        v -= 1 << (64 * words.size)
+    return v
 
 
 def launch_count() -> int:
@@ -452,7 +478,7 @@ def _take_result(L, res):
         L.zr_result_free(res)
 
 
-def make_request(nv, degN, seed, N_exps, N_coef, D_exps=None, D_coef=None, degD=None, offset=0):
+def make_request(nv, degN, seed, N_exps, N_coef, D_exps=None, D_coef=None, degD=None, offset=0, verify=False):
     """A zr_request plus the numpy arrays it points to (keep both alive until submitted)."""
     rational = D_exps is not None
     keep = [np.ascontiguousarray(N_exps, dtype=np.uint8), np.ascontiguousarray(N_coef, dtype=np.uint64),
@@ -466,7 +492,7 @@ def make_request(nv, degN, seed, N_exps, N_coef, D_exps=None, D_coef=None, degD=
         degd_ptr = keep[5].ctypes.data
     else:
         degd_ptr = keep[2].ctypes.data
-    prm = zr_recon_params(nv, offset, seed, keep[2].ctypes.data, degd_ptr)
+    prm = zr_recon_params(nv, offset, seed, keep[2].ctypes.data, degd_ptr, 1 if verify else 0, 0)
     return zr_request(bb, prm), keep
 
 
@@ -480,7 +506,8 @@ def _callback(fn, raised):
     return zr_eval_fn(call)
 
 
-def make_callback_request(nv, degN, seed, fn, rational=False, degD=None, TN_hint=0, TD_hint=0, offset=0):
+def make_callback_request(nv, degN, seed, fn, rational=False, degD=None, TN_hint=0, TD_hint=0, offset=0,
+                          verify=False):
     """A zr_request whose black box is fn(npts, nv, pts, out, stream) -> int
     over raw device pointers (see Context.reconstruct_callback), plus what it
     points to.  keep[-1] collects exceptions raised inside fn."""
@@ -490,7 +517,7 @@ def make_callback_request(nv, degN, seed, fn, rational=False, degD=None, TN_hint
     dD = np.ascontiguousarray(degD if degD is not None else degN, dtype=np.int32)
     bb = zr_blackbox(BB_CALL_RATIONAL if rational else BB_CALL_POLY, nv, TN_hint, None, None, TD_hint, None, None,
                      cb, None)
-    prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data)
+    prm = zr_recon_params(nv, offset, seed, dN.ctypes.data, dD.ctypes.data, 1 if verify else 0, 0)
     return zr_request(bb, prm), [cb, dN, dD, raised]
 
 

@@ -128,3 +128,95 @@ def test_reconstruct_balanced_workload(ctx, orc):
                                                       seed=wl.seed)
     assert np.array_equal(Ne, oNe) and np.array_equal(Nc, oNc)
     assert np.array_equal(De, oDe) and np.array_equal(Dc, oDc)
+
+
+# ---- verification at a fresh point and unknown degrees -----------------------
+
+@pytest.mark.parametrize("nv,deg,T,seed", [(3, 4, 20, 11), (5, 6, 150, 12)])
+def test_verify_changes_nothing_when_lucky(ctx, nv, deg, T, seed):
+    """A verified run takes the same probes as an unverified one (its points
+    come from streams of their own) and returns the same result."""
+    wl = W.poly_simplex_workload(700 + seed, nv, deg, T)
+    (e0, c0), _, i0 = ctx.reconstruct(nv, wl.deg, wl.seed, wl.exps, wl.coef)
+    (e1, c1), _, i1 = ctx.reconstruct(nv, wl.deg, wl.seed, wl.exps, wl.coef, verify=True)
+    assert np.array_equal(e0, e1) and np.array_equal(c0, c1)
+    assert np.array_equal(e1, wl.exps) and np.array_equal(c1, wl.coef)
+    assert i0["steps"] == i1["steps"] and i1["redraws"] == 0
+    rw = W.rational_simplex_workload(710 + seed, nv, deg, T, T // 2 + 1)
+    a = (nv, rw.degN, rw.seed, rw.Nexps, rw.Ncoef, rw.Dexps, rw.Dcoef)
+    (N0, D0, j0), (N1, D1, j1) = ctx.reconstruct(*a, degD=rw.degD), ctx.reconstruct(*a, degD=rw.degD, verify=True)
+    for x, y in zip(N0 + D0, N1 + D1):
+        assert np.array_equal(x, y)
+    assert np.array_equal(N1[0], rw.Nexps) and np.array_equal(N1[1], rw.Ncoef)
+    assert np.array_equal(D1[0], rw.Dexps) and np.array_equal(D1[1], rw.Dcoef)
+    assert j0["steps"] == j1["steps"]
+
+
+@pytest.mark.parametrize("nv,deg,T,seed,known", [(1, 9, 8, 1, []), (3, 5, 30, 2, [1]), (4, 12, 60, 3, []),
+                                                 (6, 5, 120, 4, [0, 5])])
+def test_unknown_degrees_poly(ctx, orc, nv, deg, T, seed, known):
+    """Negative bounds: detected by growing the bound after each mismatch;
+    the result is the hidden polynomial, the same as the oracle's with the
+    true bounds."""
+    wl = W.poly_simplex_workload(720 + seed, nv, deg, T)
+    true_deg = [int(wl.exps[:, m].max()) for m in range(nv)]
+    bounds = [true_deg[m] if m in known else -1 for m in range(nv)]
+    (e, c), _, info = ctx.reconstruct(nv, bounds, wl.seed, wl.exps, wl.coef)
+    assert np.array_equal(e, wl.exps) and np.array_equal(c, wl.coef)
+    oe, oc = orc.reconstruct_poly(wl.exps, wl.coef, true_deg, seed=wl.seed)
+    assert np.array_equal(e, oe) and np.array_equal(c, oc)
+    if max(true_deg[m] for m in range(nv) if m not in known) > 3:
+        assert info["redraws"] >= 1
+
+
+def test_unknown_degrees_rational(ctx):
+    wl = W.rational_simplex_workload(731, 3, 9, 30, 20)
+    (Ne, Nc), (De, Dc), info = ctx.reconstruct(3, [-1] * 3, wl.seed, wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef,
+                                               degD=[-1] * 3)
+    assert np.array_equal(Ne, wl.Nexps) and np.array_equal(Nc, wl.Ncoef)
+    assert np.array_equal(De, wl.Dexps) and np.array_equal(Dc, wl.Dcoef)
+    assert info["redraws"] >= 1
+
+
+def test_degree_beyond_detection(ctx):
+    """x_0^70 needs 71 samples; detection stops at 64 with ZR_ERR_DEGREE."""
+    from paper_2505_24256_gb300 import zr
+    exps = np.array([[0, 0], [0, 1], [70, 0]], dtype=np.uint8)
+    coef = np.array([5, 7, 11], dtype=np.uint64)
+    with pytest.raises(zr.ZrError) as ei:
+        ctx.reconstruct(2, [-1, 1], 3, exps, coef)
+    assert ei.value.status == zr.DEGREE
+
+
+def test_verify_catches_a_low_bound(ctx):
+    """A known bound below the true degree: unverified, the result is wrong;
+    verified, every attempt mismatches and the call fails with ZR_ERR_UNLUCKY."""
+    from paper_2505_24256_gb300 import zr
+    wl = W.poly_simplex_workload(741, 3, 6, 25)
+    low = [6, 6, 2]
+    assert int(wl.exps[:, 2].max()) > 2
+    (e, c), _, _ = ctx.reconstruct(3, low, wl.seed, wl.exps, wl.coef)
+    assert not (e.shape == wl.exps.shape and np.array_equal(e, wl.exps) and np.array_equal(c, wl.coef))
+    with pytest.raises(zr.ZrError) as ei:
+        ctx.reconstruct(3, low, wl.seed, wl.exps, wl.coef, verify=True)
+    assert ei.value.status == zr.UNLUCKY
+
+
+def test_unknown_degrees_served(ctx):
+    from paper_2505_24256_gb300 import zr
+    c2 = zr.Context(P63)
+    try:
+        srv = zr.Server(c2, 1 << 30, 4)
+        wl = W.poly_simplex_workload(751, 4, 8, 70)
+        rw = W.rational_simplex_workload(752, 3, 6, 20, 12)
+        r1, k1 = zr.make_request(4, [-1] * 4, wl.seed, wl.exps, wl.coef)
+        r2, k2 = zr.make_request(3, [-1] * 3, rw.seed, rw.Nexps, rw.Ncoef, rw.Dexps, rw.Dcoef, degD=[-1] * 3)
+        t1, t2 = srv.submit(r1), srv.submit(r2)
+        (e, c), _, _ = srv.wait(t1)
+        assert np.array_equal(e, wl.exps) and np.array_equal(c, wl.coef)
+        (Ne, Nc), (De, Dc), _ = srv.wait(t2)
+        assert np.array_equal(Ne, rw.Nexps) and np.array_equal(Nc, rw.Ncoef)
+        assert np.array_equal(De, rw.Dexps) and np.array_equal(Dc, rw.Dcoef)
+        srv.close()
+    finally:
+        c2.close()
