@@ -165,8 +165,9 @@ __global__ void k_eval_finalize(const int64_t* __restrict__ Gdev, int64_t Tn, in
                                 RingLayout L, int rw, uint64_t* __restrict__ Wr, uint64_t* __restrict__ UP,
                                 uint64_t* __restrict__ UPq, uint64_t* __restrict__ Uq) {
   const int64_t G = *Gdev;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < G * rw) {
+  // a grid-stride loop: the launch is sized for the SMs, the work for G
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < G * rw; idx += stride) {
     // entry j of group g's rows: block b, consumer q, column c
     const int64_t g = idx / rw;
     int j = (int)(idx - g * rw), b = 0;
@@ -182,7 +183,7 @@ __global__ void k_eval_finalize(const int64_t* __restrict__ Gdev, int64_t Tn, in
     }
     Wr[L.off[b] + g * L.bw[b] + j] = r;
   }
-  if (idx < G) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < G; idx += stride) {
     uint64_t x = U[idx];
     Uq[idx] = shoup_pre(x, M);
     for (int a = 0; a < 32; a++) {
@@ -566,7 +567,11 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   const RingLayout L = ring_layout(S, Tn);
   int rw = 0;
   for (int b = 0; b < L.nb; b++) rw += L.bw[b];
-  { k_eval_finalize<<<cdiv(Tn * rw, 256), 256, 0, st>>>(Gdev, Tn, S, Wacc, U, M, L, rw, Wp, UP, UPq, Uq); note_launch(); }
+  {
+    const int64_t want = cdiv(Tn * rw, 256), cap = 8ll * (ctx->sms ? ctx->sms : 152);
+    k_eval_finalize<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(Gdev, Tn, S, Wacc, U, M, L, rw, Wp, UP, UPq, Uq);
+    note_launch();
+  }
   launch_ring(T, S, offset, Gdev, Tn, gsplit, UP, UPq, U, Uq, Wp, L, M, out, ldo, partial, status, st);
   if (gsplit > 1) { k_eval_combine<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, gsplit, partial, M, out, ldo); note_launch(); }
   return cuda_err(ctx, cudaGetLastError(), "zr_zippel_probes");

@@ -1,13 +1,14 @@
 """Runs Zippel steps of a named workload on cuda:0 for profiling.
 
     python -m paper_2505_24256_gb300.profile_step [--workload batched|large]
-        [--steps N] [--plan TILE,NB]
+        [--steps N] [--plan TILE,NB] [--probe-sets M]
 
-The probes are generated once by the GPU evaluator; then N steps run back to
-back (the first is a warm-up when N > 1) with the given solve plan (else the
-planner's model), and the per-phase device times of the context profiler
-are printed.  Under ncu, select the solve kernel with -k regex:k_solve and
-skip the warm-up launch with -s 1.
+The probes are generated M times (default 1) by the GPU evaluator, each
+timed with CUDA events; then N steps run back to back (the first is a
+warm-up when N > 1) with the given solve plan (else the planner's model),
+and the per-phase device times of the context profiler are printed.  Under
+ncu, select the solve kernel with -k regex:k_solve (or the evaluator's
+product with -k regex:k_eval_ring) and skip the warm-up launch with -s 1.
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ def main():
     ap.add_argument("--workload", default="batched", choices=["batched", "large"])
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--plan", default=None, help="solve plan TILE,NB (default: the planner's model)")
+    ap.add_argument("--probe-sets", type=int, default=1, help="probe generations, each timed")
     args = ap.parse_args()
     if args.plan:
         os.environ["ZR_SOLVE_PLAN"] = args.plan
@@ -48,7 +50,14 @@ def main():
     ske = torch.from_numpy(wl.skel).to(dev)
     skel = ctx.poly(wl.nv, wl.T, ske)
     b = torch.empty((wl.S, wl.T), dtype=torch.int64, device=dev)
-    ctx.zippel_probes(f, wl.k, y, wl.S, cs, z, wl.T, 0, b, wl.T)
+    probe_ms = []
+    for _ in range(max(1, args.probe_sets)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.zippel_probes(f, wl.k, y, wl.S, cs, z, wl.T, 0, b, wl.T)
+        e1.record()
+        torch.cuda.synchronize()
+        probe_ms.append(e0.elapsed_time(e1))
     cap = wl.T * wl.S
     oe = torch.zeros((cap, wl.nv), dtype=torch.uint8, device=dev)
     oc = torch.zeros(cap, dtype=torch.int64, device=dev)
@@ -61,7 +70,7 @@ def main():
     ok = n == wl.exps.shape[0] and np.array_equal(got, wl.coef)
     phases = {ph: ctx.profile_query(ph)[0] / args.steps for ph in zr.Context.PHASES[:7]}
     line = {"workload": wl.name, "steps": args.steps, "plan": ctx.step_plan(wl.T, wl.S), "phase_ms": phases,
-            "check": "generator truth" if ok else "MISMATCH"}
+            "probe_ms": probe_ms, "check": "generator truth" if ok else "MISMATCH"}
     if not ok:
         line["terms"] = [int(n), int(wl.exps.shape[0])]
         if n == wl.exps.shape[0]:
