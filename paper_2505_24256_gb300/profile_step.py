@@ -1,7 +1,7 @@
 """Runs Zippel steps of a named workload on cuda:0 for profiling.
 
     python -m paper_2505_24256_gb300.profile_step [--workload batched|large]
-        [--steps N] [--plan TILE,NB] [--probe-sets M]
+        [--steps N] [--plan TILE,NB] [--probe-sets M] [--T N]
 
 The probes are generated M times (default 1) by the GPU evaluator, each
 timed with CUDA events; then N steps run back to back (the first is a
@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--plan", default=None, help="solve plan TILE,NB (default: the planner's model)")
     ap.add_argument("--probe-sets", type=int, default=1, help="probe generations, each timed")
+    ap.add_argument("--T", type=int, default=0,
+                    help="the large workload's recipe at this many terms (a smaller case for counters)")
     args = ap.parse_args()
     if args.plan:
         os.environ["ZR_SOLVE_PLAN"] = args.plan
@@ -37,7 +39,12 @@ def main():
     from paper_2505_24256_gb300 import build, workloads as W, zr
 
     build.build()
-    wl = W.batched_step_1e4() if args.workload == "batched" else W.large_step_2p20()
+    if args.workload == "batched":
+        wl = W.batched_step_1e4()
+    elif args.T:
+        wl = W.step_workload(1003, args.T, 7, 12, 9, name=f"step_T{args.T}_S9")
+    else:
+        wl = W.large_step_2p20()
     dev = torch.device("cuda:0")
 
     def d64(a):
