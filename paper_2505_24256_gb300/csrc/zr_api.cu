@@ -273,7 +273,8 @@ StepDims plan_step(const zr_ctx* ctx, int64_t T, int S) {
   return best;
 }
 
-StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D) {
+StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D, int Ssolve) {
+  if (Ssolve < 0) Ssolve = S;
   StepWs w;
   const int64_t Tn = T > 0 ? T : 1;
   w.tab = cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
@@ -284,7 +285,7 @@ StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D) {
   w.tmp = cv.take<uint64_t>(2 * Tn);
   w.tpart = cv.take<uint64_t>((size_t)tree_split_max(Tn) * Tn);
   w.R = cv.take<uint64_t>((size_t)(D.NB > 1 ? D.NB - 1 : 1) * Tn);
-  w.part = cv.take<uint64_t>((size_t)D.NB * S * Tn);
+  w.part = cv.take<uint64_t>((size_t)D.NB * Ssolve * Tn);
   w.denp = cv.take<uint64_t>((size_t)D.NB * Tn);
   w.invd = cv.take<uint64_t>((size_t)S * S);
   w.g = cv.take<uint64_t>((size_t)S * Tn);

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kNewtonThreads) k_b_newton_table(const BDesc* 
   extern __shared__ uint64_t tsm[];
   const BDesc& D = Ds[blockIdx.x];
   if (D.mode != 0 || D.T == 0) return;
-  newton_table_block(D.S, D.xs, D.invd, D.status, tsm, M);
+  newton_table_block(D.Sn, D.xs, D.invd, D.status, tsm, M);
 }
 
 // a4 + a6 per term: the denominator q_j(v_j) from its k-block partials, its
@@ -246,10 +246,10 @@ __global__ void __launch_bounds__(kFinB) k_b_finish_newton(const BDesc* __restri
   extern __shared__ uint64_t fsm[];
   const int i = seg_of(pre_blk, n, blockIdx.x);
   const BDesc& D = Ds[i];
-  const int S = D.S;
+  const int S = D.S, Sn = D.Sn, s1 = Sn - S;   // s1 = 1: sample 0 is given (c0)
   uint64_t* W = fsm;
-  uint64_t* num = fsm + S * S;
-  for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) W[idx] = D.invd[idx];
+  uint64_t* num = fsm + Sn * Sn;
+  for (int idx = threadIdx.x; idx < Sn * Sn; idx += blockDim.x) W[idx] = D.invd[idx];
   const int64_t j = (blockIdx.x - pre_blk[i]) * kFinB + threadIdx.x;
   const bool active = j < D.T;
   uint64_t den = 1, mult = 1;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kFinB) k_b_finish_newton(const BDesc* __restri
   const uint64_t inv = mul_mod(warp_batch_inverse(den, M), mult, M);
   if (active) {
     // sum of the k-block partials; the S loads of one k-block are independent
-    uint64_t* nm = num + threadIdx.x;
+    uint64_t* nm = num + threadIdx.x + s1 * kFinB;
     for (int s = 0; s < S; s++) nm[s * kFinB] = D.part[(int64_t)s * D.T + j];
     for (int kb = 1; kb < D.NB; kb++) {
       const uint64_t* pp = D.part + (int64_t)kb * S * D.T + j;
@@ -274,10 +274,16 @@ __global__ void __launch_bounds__(kFinB) k_b_finish_newton(const BDesc* __restri
       }
     }
   }
+  if (active && s1) {
+    // the given solution at sample 0, the solved ones scaled by the inverse
+    uint64_t* nm = num + threadIdx.x;
+    nm[0] = D.c0[j];
+    for (int s = 1; s < Sn; s++) nm[s * kFinB] = mul_mod(nm[s * kFinB], inv, M);
+  }
   __syncthreads();
   int cnt = 0;
   if (active) {
-    cnt = newton_apply(S, W, num + threadIdx.x, kFinB, inv, D.g + j, D.T, M);
+    cnt = newton_apply(Sn, W, num + threadIdx.x, kFinB, s1 ? 1 : inv, D.g + j, D.T, M);
     D.cnt[j] = cnt;
   }
   // nonzero coefficients of this block of terms, for the compaction
@@ -349,7 +355,7 @@ __global__ void __launch_bounds__(kCompB) k_b_scatter(const BDesc* __restrict__ 
   const BDesc& D = Ds[i];
   const int64_t blk = blockIdx.x - pre_blk[i];
   const int64_t j0 = blk * kCompB, j = j0 + threadIdx.x;
-  const int S = D.S;
+  const int S = D.Sn;
   uint64_t mask = 0;
   if (j < D.T)
     for (int s = 0; s < S; s++)
@@ -418,13 +424,13 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
   for (int i = 0; i < n; i++) {
     const BatchItem& it = items[i];
     if (it.mode != P.mode) return false;
-    P.plan[i] = plan_step(ctx, it.T, it.S);
+    P.plan[i] = plan_step(ctx, it.T, it.solve_S());
     P.kmax = std::max(P.kmax, it.k);
     P.smax = std::max(P.smax, it.S);
     P.lmax = std::max(P.lmax, tree_levels(it.T));
   }
   Carver m0(nullptr);
-  for (int i = 0; i < n; i++) carve_step(m0, items[i].T, items[i].S, items[i].k, P.plan[i]);
+  for (int i = 0; i < n; i++) carve_step(m0, items[i].T, items[i].S, items[i].k, P.plan[i], items[i].solve_S());
   P.ws_bytes = m0.off;
   std::vector<int64_t> c_hash(n), c_roots(n), c_leaf(n), c_carry(n), c_nblk(n);
   for (int i = 0; i < n; i++) {
@@ -450,7 +456,7 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
   for (int i = 0; i < n; i++) {
     if (items[i].T == 0) continue;
     // one work list per (tile, consumer groups): the solve kernel instance
-    const int tile = P.plan[i].s_tile, groups = (items[i].S + tile - 1) / tile;
+    const int tile = P.plan[i].s_tile, groups = (items[i].solve_S() + tile - 1) / tile;
     const int key = tile * 16 + groups;
     int w = (int)(std::find(P.tiles_used.begin(), P.tiles_used.end(), key) - P.tiles_used.begin());
     if (w == (int)P.tiles_used.size()) {
@@ -507,11 +513,14 @@ static zr_status stage_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_
   Carver cv(ws);
   for (int i = 0; i < n; i++) {
     const BatchItem& it = items[i];
-    StepWs w = carve_step(cv, it.T, it.S, it.k, plan[i]);
+    StepWs w = carve_step(cv, it.T, it.S, it.k, plan[i], it.solve_S());
+    const bool given0 = it.solve_S() != it.S;
     BDesc& d = D[i];
     memset(&d, 0, sizeof(d));
     d.T = it.T;
-    d.S = it.S;
+    d.S = it.solve_S();
+    d.Sn = it.S;
+    d.c0 = given0 ? it.c0 : nullptr;
     d.k = it.k;
     d.nv = it.nv;
     d.offset = it.offset;
@@ -519,13 +528,13 @@ static zr_status stage_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_
     d.NB = plan[i].NB;
     d.BK = plan[i].BK;
     d.s_tile = plan[i].s_tile;
-    d.nst = (it.S + plan[i].s_tile - 1) / plan[i].s_tile;   // consumer groups of the solve
+    d.nst = (d.S + plan[i].s_tile - 1) / plan[i].s_tile;   // consumer groups of the solve
     d.levels = tree_levels(it.T);
     d.hmask = hash_slots(it.T) - 1;
     d.exps = it.exps;
     d.y = it.y;
     d.xs = it.xs;
-    d.b = it.b;
+    d.b = given0 ? it.b + it.ldb : it.b;   // the solved samples' rows
     d.ldb = it.ldb;
     d.tab = w.tab;
     d.v = it.mode == 1 ? const_cast<uint64_t*>(it.vin) : w.v;

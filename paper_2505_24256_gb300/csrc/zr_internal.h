@@ -98,7 +98,9 @@ struct StepWs {
   int32_t* cnt;
   int64_t* bsum;
 };
-StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D);
+// S: samples of the step (Newton points); Ssolve: systems solved (S, or S - 1
+// when the first sample's solution is given)
+StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D, int Ssolve = -1);
 
 // One entry of a batch: a Zippel step (mode 0) or a transposed Vandermonde
 // system with given nodes (mode 1).  All pointers are device pointers.
@@ -116,6 +118,12 @@ struct BatchItem {
   uint64_t* c = nullptr;
   int64_t ldc = 0;
   uint32_t* status = nullptr;   // the entry's own status word (else the batch's)
+  // Zippel steps (mode 0) with S >= 2 only: the skeleton's coefficients (T,
+  // device), which are the solution at the first sample (the value of x_k
+  // they were taken at).  The step then solves only samples 1..S-1 (b's row
+  // 0 is not read) and interpolates through all S.
+  const uint64_t* c0 = nullptr;
+  int solve_S() const { return c0 && mode == 0 && S >= 2 ? S - 1 : S; }
 };
 // Workspace bytes a batch needs (its regions plus the device tables).
 size_t batch_ws_need(const zr_ctx* ctx, const BatchItem* items, int n);

@@ -44,7 +44,8 @@ struct StepDims {
 struct BDesc {
   int64_t T, BK, ldb, ldc, out_cap;
   uint64_t hmask;
-  int32_t S, k, nv, offset, mode, NB, s_tile, nst, levels, pad;
+  int32_t S, k, nv, offset, mode, NB, s_tile, nst, levels;
+  int32_t Sn;   // samples interpolated: S (systems solved), or S + 1 with c0
   const uint8_t* exps;
   const uint64_t *y, *xs, *b;
   uint64_t *tab, *v, *vp, *htab, *m, *tmp, *tpart, *R, *part, *denp, *invd, *g, *c;
@@ -53,6 +54,7 @@ struct BDesc {
   uint8_t* out_exps;
   uint64_t* out_coef;
   uint32_t* status;
+  const uint64_t* c0;   // the solution at samples[0] (then b starts at the second sample), or null
 };
 
 void launch_powtab(const uint64_t* y, int k, const Mod& M, uint64_t* tab, cudaStream_t st);

@@ -424,6 +424,7 @@ zr_status Recon::step_entry(const DPoly& skel, int S, const uint64_t* b, int64_t
   it.out_cap = cap;
   it.out_count = d_count;
   it.status = d_status;
+  it.c0 = skel.coef.as<uint64_t>();   // the samples start at c_0 = z_k, where skel was taken
   items.push_back(it);
   return ZR_OK;
 }
@@ -442,16 +443,21 @@ zr_status Recon::prepare(std::vector<BatchItem>& items, uint32_t* d_status, int6
     const int64_t T = curN_.T;
     cudaError_t e = d_b_.ensure(8 * (size_t)S * (T > 0 ? T : 1));
     if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "probes"));
+    // the probes of samples 1..S-1 (rows 1.. of b): the step takes the
+    // solution at c_0 = z_k from the skeleton's coefficients
+    const int S1 = S >= 2 ? 1 : 0;
+    uint64_t* b1 = d_b_.as<uint64_t>() + (size_t)S1 * (T > 0 ? T : 1);
+    const uint64_t* cs1 = d_cs_.as<uint64_t>() + S1;
     if (T > 0 && callback_) {
-      e = d_ppts_.ensure(8 * (size_t)S * T * nv_);
+      e = d_ppts_.ensure(8 * (size_t)(S - S1) * T * nv_);
       if (e != cudaSuccess) return fail(cuda_err(ctx_, e, "probe points"));
-      launch_probe_points(T, S, nv_, k, offset_, d_y_.as<uint64_t>(), d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), M_,
+      launch_probe_points(T, S - S1, nv_, k, offset_, d_y_.as<uint64_t>(), cs1, d_z_.as<uint64_t>(), M_,
                           d_ppts_.as<uint64_t>(), st_);
-      if ((r = eval_at(fN_, (int64_t)S * T, d_ppts_.as<uint64_t>(), d_b_.as<uint64_t>()))) return fail(r);
+      if ((r = eval_at(fN_, (int64_t)(S - S1) * T, d_ppts_.as<uint64_t>(), b1))) return fail(r);
     } else if (T > 0) {
       zr_poly fv = fN_.view();
-      r = probes_impl(ctx_, &fv, k, d_y_.as<uint64_t>(), S, d_cs_.as<uint64_t>(), d_z_.as<uint64_t>(), T, offset_,
-                      d_b_.as<uint64_t>(), T, d_status, st_);
+      r = probes_impl(ctx_, &fv, k, d_y_.as<uint64_t>(), S - S1, cs1, d_z_.as<uint64_t>(), T, offset_, b1, T,
+                      d_status, st_);
       if (r) return fail(r);
     }
     r = step_entry(curN_, S, d_b_.as<uint64_t>(), T > 0 ? T : 1, nextN_, d_status, d_counts, items);

@@ -89,6 +89,8 @@ class Recon {
   zr_status newton_coeffs(int S, const uint64_t* d_cs, const uint64_t* d_vals, std::vector<uint64_t>& coef);
   zr_status skeleton_from_coeffs(const std::vector<uint64_t>& coef, int deg, DPoly& out);
   zr_status download(const DPoly& p, int64_t* T, uint8_t** exps, uint64_t** coef);
+  // the step of skeleton skel (its coefficients are the solution at the first
+  // sample, so only samples 1..S-1 are solved; b's row 0 is not read)
   zr_status step_entry(const DPoly& skel, int S, const uint64_t* b, int64_t ldb, DPoly& out, uint32_t* d_status,
                        int64_t* d_count, std::vector<BatchItem>& items);
 
