@@ -75,6 +75,7 @@ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
       "madc.hi.u32 %2, %4, %6, %2;"
       : "=&r"(t0), "=&r"(t1), "=&r"(t2)
       : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+  (void)t0;   // only its carry reaches the high words
   return ((uint64_t)t2 << 32) | t1;
 }
 
