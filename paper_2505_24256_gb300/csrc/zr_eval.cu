@@ -9,11 +9,12 @@
 //     u_t = prod_{m<k} y_m^{e_{t,m}},  w_{t,s} = coef_t c_s^{e_{t,k}} prod_{m>k} z_m^{e_{t,m}}.
 // Terms with equal u are merged first (their w are added), which turns the
 // evaluation into a transposed Vandermonde product over the G distinct u.
-// The kernel tiles it: a CTA owns a range of consecutive i and walks the
-// groups in chunks; for each chunk it builds the table X[g][t] = u_g^(I0+off+t)
-// in shared memory by doubling (the paper's stride-k power table, Sec. 2.2)
-// and its thread groups accumulate sum_g w_{g,s} X[g][t] for their columns
-// with the deferred multiply-accumulate.
+// The kernel (k_eval_ring) tiles it: a CTA owns 32 consecutive i and walks a
+// range of groups in chunks of 32; for each chunk a producer warp fills the
+// power table X[t][g] = u_g^(I0+off+t) in shared memory (the paper's power
+// table, Sec. 2.2: a starting power, then one multiply by u_g per entry) and
+// consumer warps accumulate sum_g w_{g,s} X[t][g] for their columns with the
+// deferred multiply-accumulate.
 #include <cuda_runtime.h>
 
 #include <cmath>
