@@ -228,10 +228,19 @@ double plan_cost(const zr_ctx* ctx, const StepDims& D) {
     const double eff = warps >= 16 ? 1.0 : warps / 16.0;
     cost += (double)D.BK * rt * cost_k * (double)n / eff;
   }
+  // Terms calibrated on GB300 against a sweep of k-block counts (T = 10^4,
+  // S = 21; about 8.7e7 units per millisecond):
+  //  * each work item's prologue (the carry-in from the blocks above), ~15 ns;
+  cost += 1300.0 * (double)items;
+  //  * the finish reads NB partials per right-hand side and root;
+  cost += (double)D.NB * D.S * D.T;
+  //  * the carry kernel: (NB - 1) BK T chain steps at ~0.8 of the chain
+  //    rate, but never faster than one root's serial chain of BK steps
+  //    (~80 ns a step when few CTAs run).
   if (D.NB > 1) {
-    const int64_t cslots = sms * 8;                      // 256-thread CTAs of the carry kernel
-    const int64_t cw = ((D.T + 255) / 256 * (D.NB - 1) + cslots - 1) / cslots;
-    cost += (double)cw * D.BK * 256 * 24.0;              // one Shoup step per k
+    const double through = 20.5 * (double)(D.NB - 1) * D.BK * D.T / (double)sms;
+    const double serial = 6960.0 * (double)D.BK;
+    cost += through > serial ? through : serial;
   }
   return cost;
 }

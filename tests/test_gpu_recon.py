@@ -220,3 +220,26 @@ def test_unknown_degrees_served(ctx):
         srv.close()
     finally:
         c2.close()
+
+
+def test_reconstruct_most_variables(ctx, orc):
+    """64 variables (the limit): 63 Zippel steps over a sparse polynomial,
+    against the oracle and the hidden terms; 65 variables are rejected."""
+    from paper_2505_24256_gb300 import zr
+    nv = 64
+    rnd = random.Random(64)
+    rows = set()
+    while len(rows) < 24:
+        rows.add(tuple(rnd.randrange(3) if rnd.random() < 0.15 else 0 for _ in range(nv)))
+    exps = np.array(sorted(rows), dtype=np.uint8)
+    coef = np.array([rnd.randrange(1, P63) for _ in range(exps.shape[0])], dtype=np.uint64)
+    degs = [2] * nv
+    (e, c), _, info = ctx.reconstruct(nv, degs, 6400, exps, coef)
+    assert np.array_equal(e, exps) and np.array_equal(c, coef)
+    oe, oc = orc.reconstruct_poly(exps, coef, degs, seed=6400)
+    assert np.array_equal(e, oe) and np.array_equal(c, oc)
+    assert info["steps"] >= nv - 1
+    wide = np.zeros((1, 65), dtype=np.uint8)
+    with pytest.raises(zr.ZrError) as ei:
+        ctx.reconstruct(65, [1] * 65, 1, wide, np.array([1], dtype=np.uint64))
+    assert ei.value.status == zr.INVALID_ARG
