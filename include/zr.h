@@ -293,7 +293,9 @@ zr_status zr_eval_points(zr_ctx* ctx, const zr_poly* f, int64_t npts, const uint
 /* The Zippel probe points themselves, for a caller that evaluates its own
  * black box: pts[(s T + i) nv + m] = y_m^(i+offset) (m < k), c_s (m = k),
  * z_m (m > k), for s < S, i < T; device arrays as for zr_zippel_probes, pts
- * a device buffer of S T nv residues.  Asynchronous on `stream`. */
+ * a device buffer of S T nv residues.  Asynchronous on `stream`.
+ * Errors: ZR_ERR_INVALID_ARG (nv outside 1..64, k outside 0..nv-1, S < 1,
+ * T < 0, offset not 0/1, a needed pointer NULL). */
 zr_status zr_probe_points(zr_ctx* ctx, int32_t nv, int32_t k, const uint64_t* y, int32_t S, const uint64_t* samples,
                           const uint64_t* z, int64_t T, int32_t offset, uint64_t* pts, void* stream);
 
