@@ -658,6 +658,9 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
     int split = (int)((want + nt - 1) / nt);
     for (int i = 0; i < n; i++)
       if (tree_levels(P.plan[i].T) > l) split = std::min(split, (int)tree_split_max(P.plan[i].T));
+    // and keep at least 128 inner terms per split: below that the combine
+    // launch costs more than the shorter serial work saves
+    split = std::min(split, (int)std::max<int64_t>(1, (1ll << l) / 128));
     split = std::max(1, std::min(split, 16));
     {
       k_b_tree_conv<<<dim3((unsigned)nt, (unsigned)split), tree_tile(l) / kTR, 0, st>>>(dD, dpre + o, n, l, split, M);
