@@ -152,6 +152,25 @@ def cpu_baseline_step(wl, nthreads=0):
     return dt, bool(ok), b
 
 
+def cpu_single_thread_step(wl, b, nroots=256):
+    """The oracle's step on one host thread, from a sample: the master
+    polynomial in full, the solves of nroots evenly spaced roots, scaled to
+    all T roots (every root costs the same: one synthetic division and S dot
+    products of length T)."""
+    import numpy as np
+
+    import oracle
+    v = oracle.anchor_values(wl.skel, wl.k, wl.y)
+    t0 = time.perf_counter()
+    m = oracle.master_poly(v)
+    t_master = time.perf_counter() - t0
+    roots = np.linspace(0, wl.T - 1, min(nroots, wl.T)).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.tvandermonde_solve_roots(v, m, b, roots, nthreads=1)
+    t_roots = time.perf_counter() - t0
+    return t_master + t_roots * wl.T / roots.size, roots.size
+
+
 def run_reference(args):
     """The oracle timed on the host cores (the reference arm)."""
     import oracle
@@ -500,10 +519,14 @@ def run_zr(args):
     if world == 1 and not args.no_cpu_baseline and args.workload == "batched":
         import oracle
         cores = oracle.default_threads()
-        dt, cok, _ = cpu_baseline_step(wl)
+        dt, cok, ob = cpu_baseline_step(wl)
+        st, nr = cpu_single_thread_step(wl, ob)
         line["cpu_baseline"] = {"value": T / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one full step T={T} S={S} (probes from the oracle, untimed)",
-                                "check": "generator truth" if cok else "MISMATCH"}
+                                "check": "generator truth" if cok else "MISMATCH",
+                                "single_thread": {"value": T / st, "unit": "terms/s", "cores": 1,
+                                                  "sample": f"master polynomial in full + {nr} of the {T} roots' "
+                                                            "solves, scaled to all roots"}}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -39,3 +39,38 @@ def test_library_exports_every_declared_symbol():
     assert set(zr.SIGNATURES) == declared_functions()
     # host-only calls work without a device
     assert lib.zr_status_string(0)
+
+
+def test_struct_layouts_match_the_header():
+    """Every struct the binding mirrors has the header's size and field
+    offsets (a C program built from include/zr.h with gcc reports them)."""
+    import subprocess
+    import tempfile
+
+    from paper_2505_24256_gb300 import zr
+
+    structs = {name: getattr(zr, name) for name in dir(zr)
+               if name.startswith("zr_") and isinstance(getattr(zr, name), type)
+               and issubclass(getattr(zr, name), ctypes.Structure)}
+    assert {"zr_blackbox", "zr_recon_params", "zr_result", "zr_request", "zr_poly", "zr_vsys", "zr_step_desc",
+            "zr_serve_stats", "zr_peaks"} <= set(structs)
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "zr.h"', "int main(void) {"]
+    for name, cls in sorted(structs.items()):
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines) + "\n")
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", exe, src], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            parts = line.split()
+            got[tuple(parts[:2])] = int(parts[2])
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
