@@ -39,10 +39,11 @@ __global__ void k_powrows(const uint64_t* __restrict__ base, int nrows, Mod M, u
   if (r < nrows) tab[(int64_t)r * kPowTab + e] = pow_mod(base[r] >= M.p ? base[r] - M.p : base[r], (uint64_t)e, M);
 }
 
+// per term: its anchor value u_t and its weight without the new variable,
+// a_t = coef_t prod_{m>k} z_m^{e_{t,m}}; u_t goes into the hash table
 __global__ void k_eval_terms(int64_t Tf, int nv, const uint8_t* __restrict__ exps, const uint64_t* __restrict__ coef,
-                             int k, const uint64_t* __restrict__ tabY, const uint64_t* __restrict__ tabZ,
-                             const uint64_t* __restrict__ tabC, int S, Mod M, uint64_t* __restrict__ u,
-                             uint64_t* __restrict__ w, uint64_t* htab, uint64_t hmask) {
+                             int k, const uint64_t* __restrict__ tabY, const uint64_t* __restrict__ tabZ, Mod M,
+                             uint64_t* __restrict__ u, uint64_t* __restrict__ a, uint64_t* htab, uint64_t hmask) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Tf) return;
   const uint8_t* e = exps + t * nv;
@@ -52,7 +53,7 @@ __global__ void k_eval_terms(int64_t Tf, int nv, const uint8_t* __restrict__ exp
   if (c >= M.p) c -= M.p;
   for (int m = k + 1; m < nv; m++) c = mul_mod(c, tabZ[m * kPowTab + e[m]], M);
   u[t] = uu;
-  for (int s = 0; s < S; s++) w[t * S + s] = mul_mod(c, tabC[s * kPowTab + e[k]], M);
+  a[t] = c;
   // insert the key; equal keys share a slot
   uint64_t idx = ehash(uu) & hmask;
   for (uint64_t probe = 0; probe <= hmask; probe++) {
@@ -130,22 +131,45 @@ __global__ void __launch_bounds__(kB) k_slot_ids(int64_t H, const uint64_t* __re
   if (i < H) gid[i] = used ? (int32_t)o : -1;
 }
 
-// W[g][s] accumulated as sums of 32-bit halves (no overflow below 2^32 terms)
-__global__ void k_eval_accum(int64_t Tf, int S, const uint64_t* __restrict__ u, const uint64_t* __restrict__ w,
-                             const uint64_t* __restrict__ htab, uint64_t hmask, const int32_t* __restrict__ gid,
-                             uint64_t* __restrict__ U, unsigned long long* __restrict__ Wacc, uint32_t* status) {
+// The terms of every group, listed by a counting sort: tg[t] = the term's
+// group, tp[t] = its place in the group, cnt[g] = the group's size.
+__global__ void k_eval_count(int64_t Tf, const uint64_t* __restrict__ u, const uint64_t* __restrict__ htab,
+                             uint64_t hmask, const int32_t* __restrict__ gid, uint64_t* __restrict__ U,
+                             int32_t* __restrict__ cnt, int32_t* __restrict__ tg, int32_t* __restrict__ tp,
+                             uint32_t* status) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Tf) return;
   const uint64_t uu = u[t];
   int64_t slot = find_slot(uu, htab, hmask);
-  if (slot < 0) { atomicOr(status, ST_HASH_FULL); return; }
+  if (slot < 0) {
+    atomicOr(status, ST_HASH_FULL);
+    tg[t] = -1;
+    return;
+  }
   const int g = gid[slot];
   U[g] = uu;
-  for (int s = 0; s < S; s++) {
-    uint64_t x = w[t * S + s];
-    atomicAdd(&Wacc[((int64_t)g * S + s) * 2 + 0], (unsigned long long)lo32(x));
-    atomicAdd(&Wacc[((int64_t)g * S + s) * 2 + 1], (unsigned long long)hi32(x));
-  }
+  tg[t] = g;
+  tp[t] = atomicAdd(&cnt[g], 1);
+}
+// block sums of the group sizes, then each group's first place
+__global__ void __launch_bounds__(kB) k_cnt_sums(int64_t n, const int32_t* __restrict__ cnt, int64_t* __restrict__ bsum) {
+  __shared__ int64_t sh[33];
+  int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x, total;
+  blk_scan(i < n ? cnt[i] : 0, sh, total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+__global__ void __launch_bounds__(kB) k_cnt_start(int64_t n, const int32_t* __restrict__ cnt,
+                                                  const int64_t* __restrict__ bsum, int64_t* __restrict__ start) {
+  __shared__ int64_t sh[33];
+  int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x, total;
+  const int64_t o = blk_scan(i < n ? cnt[i] : 0, sh, total) + bsum[blockIdx.x];
+  if (i < n) start[i] = o;
+}
+__global__ void k_eval_scatter(int64_t Tf, const int32_t* __restrict__ tg, const int32_t* __restrict__ tp,
+                               const int64_t* __restrict__ start, int64_t* __restrict__ order) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Tf || tg[t] < 0) return;
+  order[start[tg[t]] + tp[t]] = t;
 }
 
 // Where the weights of the matrix-vector kernel live: column block b
@@ -161,9 +185,11 @@ struct RingLayout {
 // the tables): the merged weights as residues in the ring layout, zero in
 // the padding; the squares table UP[a][g] = u_g^(2^a), a < 32, with its
 // Shoup quotients UPq; the quotients Uq[g] of u_g.
-__global__ void k_eval_finalize(const int64_t* __restrict__ Gdev, int64_t Tn, int S,
-                                const unsigned long long* __restrict__ Wacc, const uint64_t* __restrict__ U, Mod M,
-                                RingLayout L, int rw, uint64_t* __restrict__ Wr, uint64_t* __restrict__ UP,
+__global__ void k_eval_finalize(const int64_t* __restrict__ Gdev, int64_t Tn, int S, const int64_t* __restrict__ start,
+                                const int32_t* __restrict__ cnt, const int64_t* __restrict__ order,
+                                const uint64_t* __restrict__ a, const uint8_t* __restrict__ exps, int nv, int k,
+                                const uint64_t* __restrict__ tabC, const uint64_t* __restrict__ U, Mod M, RingLayout L,
+                                int rw, uint64_t* __restrict__ Wr, uint64_t* __restrict__ UP,
                                 uint64_t* __restrict__ UPq, uint64_t* __restrict__ Uq) {
   const int64_t G = *Gdev;
   // a grid-stride loop: the launch is sized for the SMs, the work for G
@@ -176,20 +202,25 @@ __global__ void k_eval_finalize(const int64_t* __restrict__ Gdev, int64_t Tn, in
     const int q = j / L.cgp[b], c = j - q * L.cgp[b], sc = q * L.cg[b] + c, s = 64 * b + sc;
     uint64_t r = 0;
     if (c < L.cg[b] && s < S) {
-      const uint64_t lo = Wacc[(g * S + s) * 2], hi = Wacc[(g * S + s) * 2 + 1];
-      // value = hi 2^32 + lo, as a 128-bit number
-      const uint64_t vlo = lo + (hi << 32);
-      const uint64_t vhi = (hi >> 32) + (vlo < lo);
-      r = reduce128(vhi, vlo, M);
+      // W[g][s] = sum over the group's terms of a_t c_s^{e_{t,k}}
+      Acc8 acc{0, 0, 0, 0, 0, 0, 0, 0};
+      const uint64_t* cs = tabC + (int64_t)s * kPowTab;
+      const int64_t r0 = start[g], n = cnt[g];
+      for (int64_t x = 0; x < n; x++) {
+        const int64_t t = order[r0 + x];
+        const uint64_t at = a[t], w = cs[exps[t * nv + k]];
+        mac8(acc, lo32(at), hi32(at), lo32(w), hi32(w));
+      }
+      r = acc8_value(acc, M);
     }
     Wr[L.off[b] + g * L.bw[b] + j] = r;
   }
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < G; idx += stride) {
     uint64_t x = U[idx];
     Uq[idx] = shoup_pre(x, M);
-    for (int a = 0; a < 32; a++) {
-      UP[a * Tn + idx] = x;
-      UPq[a * Tn + idx] = shoup_pre(x, M);
+    for (int e = 0; e < 32; e++) {
+      UP[e * Tn + idx] = x;
+      UPq[e * Tn + idx] = shoup_pre(x, M);
       x = mul_mod(x, x, M);
     }
   }
@@ -507,6 +538,42 @@ zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, i
   return probes_enqueue(ctx, f, k, y, S, samples, z, T, offset, out, ldo, status, ctx->ws, st);
 }
 
+// The evaluator's scratch, carved the same way for sizing and for use.
+struct EvalWs {
+  uint64_t *tabY, *tabZ, *tabC, *u, *a, *htab, *U, *Wp, *UP, *UPq, *Uq, *partial;
+  int64_t *bsum, *cbsum, *start, *order, *Gdev, *total;
+  int32_t *gid, *cnt, *tg, *tp;
+};
+static EvalWs carve_eval(Carver& cv, int64_t Tf, int nv, int k, int S, int64_t T, int gsplit) {
+  EvalWs w;
+  const int64_t Tn = Tf > 0 ? Tf : 1;
+  const uint64_t H = hash_slots(Tn);
+  const int64_t nbH = (int64_t)((H + kB - 1) / kB), nbT = (Tn + kB - 1) / kB;
+  w.tabY = cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
+  w.tabZ = cv.take<uint64_t>((size_t)nv * kPowTab);
+  w.tabC = cv.take<uint64_t>((size_t)S * kPowTab);
+  w.u = cv.take<uint64_t>(Tn);
+  w.a = cv.take<uint64_t>(Tn);
+  w.htab = cv.take<uint64_t>(H);
+  w.bsum = cv.take<int64_t>(nbH + 1);
+  w.gid = cv.take<int32_t>(H);
+  w.U = cv.take<uint64_t>(Tn);
+  w.cnt = cv.take<int32_t>(Tn);
+  w.tg = cv.take<int32_t>(Tn);
+  w.tp = cv.take<int32_t>(Tn);
+  w.cbsum = cv.take<int64_t>(nbT + 1);
+  w.start = cv.take<int64_t>(Tn);
+  w.order = cv.take<int64_t>(Tn);
+  w.Wp = cv.take<uint64_t>((size_t)ring_words(S, Tn));
+  w.UP = cv.take<uint64_t>((size_t)Tn * 32);
+  w.UPq = cv.take<uint64_t>((size_t)Tn * 32);
+  w.Uq = cv.take<uint64_t>(Tn);
+  w.partial = cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
+  w.Gdev = cv.take<int64_t>(1);
+  w.total = cv.take<int64_t>(1);
+  return w;
+}
+
 // The evaluation itself, with its scratch at `base` (capacity checked by the caller).
 zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
                          const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
@@ -517,91 +584,51 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   const uint64_t H = hash_slots(Tf > 0 ? Tf : 1);
   const int64_t nbH = (int64_t)((H + kB - 1) / kB);
   const int gsplit = eval_gsplit(ctx, T, S, Tf);
-  auto layout = [&](Carver& cv, uint64_t** tabY, uint64_t** tabZ, uint64_t** tabC, uint64_t** u, uint64_t** w,
-                    uint64_t** htab, int64_t** bsum, int32_t** gid, uint64_t** U, unsigned long long** Wacc,
-                    uint64_t** Wp, uint64_t** UP, uint64_t** UPq, uint64_t** Uq, uint64_t** partial,
-                    int64_t** Gdev) {
-    const int64_t Tn = Tf > 0 ? Tf : 1;
-    *tabY = cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
-    *tabZ = cv.take<uint64_t>((size_t)nv * kPowTab);
-    *tabC = cv.take<uint64_t>((size_t)S * kPowTab);
-    *u = cv.take<uint64_t>(Tn);
-    *w = cv.take<uint64_t>((size_t)Tn * S);
-    *htab = cv.take<uint64_t>(H);
-    *bsum = cv.take<int64_t>(nbH + 1);
-    *gid = cv.take<int32_t>(H);
-    *U = cv.take<uint64_t>(Tn);
-    *Wacc = cv.take<unsigned long long>((size_t)Tn * S * 2);
-    *Wp = cv.take<uint64_t>((size_t)ring_words(S, Tn));
-    *UP = cv.take<uint64_t>((size_t)Tn * 32);
-    *UPq = cv.take<uint64_t>((size_t)Tn * 32);
-    *Uq = cv.take<uint64_t>(Tn);
-    *partial = cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
-    *Gdev = cv.take<int64_t>(1);
-  };
-  uint64_t *tabY, *tabZ, *tabC, *u, *w, *htab, *U, *UP, *UPq, *Uq, *partial;
-  int64_t *bsum, *Gdev;
-  int32_t* gid;
-  unsigned long long* Wacc;
-  uint64_t* Wp;
   Carver cv(base);
-  layout(cv, &tabY, &tabZ, &tabC, &u, &w, &htab, &bsum, &gid, &U, &Wacc, &Wp, &UP, &UPq, &Uq, &partial, &Gdev);
+  const EvalWs w = carve_eval(cv, Tf, nv, k, S, T, gsplit);
 
   if (T <= 0) return ZR_OK;
   if (Tf == 0) {
     for (int s = 0; s < S; s++) cudaMemsetAsync(out + (int64_t)s * ldo, 0, sizeof(uint64_t) * T, st);
     return cuda_err(ctx, cudaGetLastError(), "zr_zippel_probes");
   }
-  cudaMemsetAsync(htab, 0xFF, H * sizeof(uint64_t), st);
-  cudaMemsetAsync(Wacc, 0, (size_t)Tf * S * 2 * sizeof(unsigned long long), st);
-  if (k > 0) { k_powrows<<<k, kPowTab, 0, st>>>(y, k, M, tabY); note_launch(); }
-  if (z && nv > k + 1) { k_powrows<<<nv, kPowTab, 0, st>>>(z, nv, M, tabZ); note_launch(); }
-  else cudaMemsetAsync(tabZ, 0, (size_t)nv * kPowTab * sizeof(uint64_t), st);
-  { k_powrows<<<S, kPowTab, 0, st>>>(samples, S, M, tabC); note_launch(); }
-  { k_eval_terms<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, nv, f->exps, f->coef, k, tabY, tabZ, tabC, S, M, u, w, htab, H - 1); note_launch(); }
-  { k_slot_sums<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, htab, bsum); note_launch(); }
-  { k_scan_small<<<1, kB, 0, st>>>(nbH, bsum, Gdev); note_launch(); }
-  { k_slot_ids<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, htab, bsum, gid); note_launch(); }
-  { k_eval_accum<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, S, u, w, htab, H - 1, gid, U, Wacc, status); note_launch(); }
+  const int64_t Tn = Tf, nbT = (Tn + kB - 1) / kB;
+  cudaMemsetAsync(w.htab, 0xFF, H * sizeof(uint64_t), st);
+  cudaMemsetAsync(w.cnt, 0, (size_t)Tn * sizeof(int32_t), st);
+  if (k > 0) { k_powrows<<<k, kPowTab, 0, st>>>(y, k, M, w.tabY); note_launch(); }
+  if (z && nv > k + 1) { k_powrows<<<nv, kPowTab, 0, st>>>(z, nv, M, w.tabZ); note_launch(); }
+  else cudaMemsetAsync(w.tabZ, 0, (size_t)nv * kPowTab * sizeof(uint64_t), st);
+  { k_powrows<<<S, kPowTab, 0, st>>>(samples, S, M, w.tabC); note_launch(); }
+  { k_eval_terms<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, nv, f->exps, f->coef, k, w.tabY, w.tabZ, M, w.u, w.a, w.htab, H - 1); note_launch(); }
+  // groups: the distinct u, numbered by a scan over the hash slots
+  { k_slot_sums<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, w.htab, w.bsum); note_launch(); }
+  { k_scan_small<<<1, kB, 0, st>>>(nbH, w.bsum, w.Gdev); note_launch(); }
+  { k_slot_ids<<<(unsigned)nbH, kB, 0, st>>>((int64_t)H, w.htab, w.bsum, w.gid); note_launch(); }
+  // the terms of each group, by a counting sort
+  { k_eval_count<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, w.u, w.htab, H - 1, w.gid, w.U, w.cnt, w.tg, w.tp, status); note_launch(); }
+  { k_cnt_sums<<<(unsigned)nbT, kB, 0, st>>>(Tn, w.cnt, w.cbsum); note_launch(); }
+  { k_scan_small<<<1, kB, 0, st>>>(nbT, w.cbsum, w.total); note_launch(); }
+  { k_cnt_start<<<(unsigned)nbT, kB, 0, st>>>(Tn, w.cnt, w.cbsum, w.start); note_launch(); }
+  { k_eval_scatter<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, w.tg, w.tp, w.start, w.order); note_launch(); }
   // the group count stays on the device: the kernels read it, sized for Tf groups
-  const int64_t Tn = Tf;
   const RingLayout L = ring_layout(S, Tn);
   int rw = 0;
   for (int b = 0; b < L.nb; b++) rw += L.bw[b];
   {
     const int64_t want = cdiv(Tn * rw, 256), cap = 8ll * (ctx->sms ? ctx->sms : 152);
-    k_eval_finalize<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(Gdev, Tn, S, Wacc, U, M, L, rw, Wp, UP, UPq, Uq);
+    k_eval_finalize<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(w.Gdev, Tn, S, w.start, w.cnt, w.order, w.a,
+                                                                         f->exps, nv, k, w.tabC, w.U, M, L, rw, w.Wp,
+                                                                         w.UP, w.UPq, w.Uq);
     note_launch();
   }
-  launch_ring(T, S, offset, Gdev, Tn, gsplit, UP, UPq, U, Uq, Wp, L, M, out, ldo, partial, status, st);
-  if (gsplit > 1) { k_eval_combine<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, gsplit, partial, M, out, ldo); note_launch(); }
+  launch_ring(T, S, offset, w.Gdev, Tn, gsplit, w.UP, w.UPq, w.U, w.Uq, w.Wp, L, M, out, ldo, w.partial, status, st);
+  if (gsplit > 1) { k_eval_combine<<<cdiv(T * S, 256), 256, 0, st>>>(T, S, gsplit, w.partial, M, out, ldo); note_launch(); }
   return cuda_err(ctx, cudaGetLastError(), "zr_zippel_probes");
 }
 
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T) {
-  const int64_t Tf = f->T;
-  const int nv = f->nv;
-  const uint64_t H = hash_slots(Tf > 0 ? Tf : 1);
-  const int64_t nbH = (int64_t)((H + kB - 1) / kB);
-  const int gsplit = eval_gsplit(ctx, T, S, Tf);
-  const int64_t Tn = Tf > 0 ? Tf : 1;
   Carver cv(nullptr);
-  cv.take<uint64_t>((size_t)(k > 0 ? k : 1) * kPowTab);
-  cv.take<uint64_t>((size_t)nv * kPowTab);
-  cv.take<uint64_t>((size_t)S * kPowTab);
-  cv.take<uint64_t>(Tn);
-  cv.take<uint64_t>((size_t)Tn * S);
-  cv.take<uint64_t>(H);
-  cv.take<int64_t>(nbH + 1);
-  cv.take<int32_t>(H);
-  cv.take<uint64_t>(Tn);
-  cv.take<unsigned long long>((size_t)Tn * S * 2);
-  cv.take<uint64_t>((size_t)ring_words(S, Tn));
-  cv.take<uint64_t>((size_t)Tn * 32);
-  cv.take<uint64_t>((size_t)Tn * 32);
-  cv.take<uint64_t>(Tn);
-  cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
-  cv.take<int64_t>(1);
+  carve_eval(cv, f->T, f->nv, k, S, T, eval_gsplit(ctx, T, S, f->T));
   return cv.off;
 }
 
