@@ -359,6 +359,16 @@ extern "C" zr_status zr_create(uint64_t prime, zr_ctx** out) {
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, 2 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, 4 * sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_count, 4 * sizeof(int64_t));
+  if (e == cudaSuccess) {
+    // reconstructions allocate their per-request buffers from the device's
+    // pool in stream order; keep freed blocks in the pool for the next ones
+    // (a property of this process's pool, not a setting of the device)
+    cudaMemPool_t pool;
+    uint64_t keep = ~0ull;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess)
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     zr_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? ZR_ERR_OOM : ZR_ERR_CUDA;

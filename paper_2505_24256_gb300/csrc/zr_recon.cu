@@ -104,6 +104,10 @@ Recon::Recon(zr_ctx* ctx, cudaStream_t st, const zr_blackbox& bb, const zr_recon
       Dc_.assign(bb.D_coef, bb.D_coef + bb.TD);
     }
   }
+  for (DBuf* b : {&d_y_, &d_cs_, &d_z_, &d_b_, &d_pts_, &d_vals_, &scratch_, &persist_, &fv_, &one_, &ones_, &d_ppts_,
+                  &d_vpt_, &d_vval_, &fN_.exps, &fN_.coef, &fD_.exps, &fD_.coef, &curN_.exps, &curN_.coef,
+                  &curD_.exps, &curD_.coef, &nextN_.exps, &nextN_.coef, &nextD_.exps, &nextD_.coef})
+    b->s = st_;
   degN_.assign(prm.degN, prm.degN + nv_);
   if (rational_) degD_.assign(prm.degD, prm.degD + nv_);
   else degD_.assign(nv_, 0);

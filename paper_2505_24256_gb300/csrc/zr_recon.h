@@ -14,24 +14,29 @@
 
 namespace zr {
 
-// Device memory owned by one request.
+// Device memory owned by one request, allocated and freed in the order of
+// the request's stream (the device's memory pool): growing a buffer between
+// steps does not synchronise the device, so requests on other streams keep
+// running.
 struct DBuf {
   void* p = nullptr;
   size_t n = 0;
+  cudaStream_t s = nullptr;   // the owner's stream
   DBuf() = default;
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     n = 0;
   }
   cudaError_t ensure(size_t bytes) {
     if (bytes <= n && p) return cudaSuccess;
     release();
-    cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 8);
+    cudaError_t e = cudaMallocAsync(&p, bytes > 0 ? bytes : 8, s);
     if (e == cudaSuccess) n = bytes > 0 ? bytes : 8;
+    else p = nullptr;
     return e;
   }
   template <class T>
