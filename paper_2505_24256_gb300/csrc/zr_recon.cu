@@ -746,6 +746,7 @@ extern "C" zr_status zr_zippel_step_balanced(zr_ctx* ctx, const zr_poly* skelN, 
   if (Tmax == 0) return ZR_OK;
   cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);
   DBuf persist, ones;
+  persist.s = ones.s = st;   // allocated and freed in the order of the call's stream
   const size_t w_dprev = (size_t)Tmax, w_bN = (size_t)SN * (TN ? TN : 1), w_bD = (size_t)SD * (TD ? TD : 1);
   const size_t w_th = thiele_scratch_words(Tmax, Sf);
   cudaError_t e = persist.ensure(8 * (w_dprev + w_bN + w_bD + w_th) + 256);
