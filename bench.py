@@ -391,7 +391,10 @@ def run_zr(args):
     torch.cuda.synchronize()
     launches = zr.launch_count() - launches0
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(bb) for a, bb in evs)
+    step_times = sorted(a.elapsed_time(bb) for a, bb in evs)
+    total_ms = sum(step_times)
+    median_ms = step_times[len(step_times) // 2] if len(step_times) % 2 else \
+        0.5 * (step_times[len(step_times) // 2 - 1] + step_times[len(step_times) // 2])
     solve_ms, solve_n = ctx.profile_query("solve")
     phases = {ph: ctx.profile_query(ph)[0] / max(args.steps, 1) for ph in zr.Context.PHASES[:7]}
     ctx.profile(False)
@@ -486,6 +489,8 @@ def run_zr(args):
         "config": {"workload": wl.name, "T": T, "S": S, "nv": nv, "prime": wl.p,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}"},
         "mulmod_per_s": world * W * args.steps / (total_ms / 1e3),
+        # the median step of this rank (the per-step figure the paper reports)
+        "median": {"ms_per_step": median_ms, "terms_per_s": T / (median_ms / 1e3), "steps": len(step_times)},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
                      "frac": achieved / peak, "traffic": solve_traffic(wl.name), "traffic_unit": "bytes/launch",
                      "kernel": "k_solve",
