@@ -389,6 +389,8 @@ def run_zr(args):
         n = step()
         evs[i][1].record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     launches = zr.launch_count() - launches0
     clk = clocks.stop()
     step_times = sorted(a.elapsed_time(bb) for a, bb in evs)
