@@ -64,6 +64,7 @@ _SIGS = {
     "zro_submod": (_u64, [_u64, _u64, _u64]),
     "zro_powmod": (_u64, [_u64, _u64, _u64]),
     "zro_invmod": (_u64, [_u64, _u64]),
+    "zro_arith_batch": (ctypes.c_int, [_i32, _i64, _i64, _u64p, _u64p, _u64, _u64p]),
     "zro_is_prime": (ctypes.c_int, [_u64]),
     "zro_default_threads": (ctypes.c_int, []),
     "zro_splitmix_at": (_u64, [_u64, _u64]),
@@ -151,6 +152,23 @@ def invmod(a, p=P63):
 
 def is_prime(n):
     return bool(lib().zro_is_prime(n))
+
+
+ARITH_OPS = {"mulmod": 0, "reduce": 1, "shoup_pre": 2, "shoup_lazy": 3, "pow": 4, "inv": 5, "dot": 6, "add": 7,
+             "sub": 8, "batch_inv": 9}
+
+
+def arith_batch(op, a, b=None, p=P63, length=1):
+    """Elementwise modular primitive `op` (see zro_arith_batch) on uint64
+    arrays; for "dot" the operands hold len(out) groups of `length` terms."""
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    b = np.ascontiguousarray(np.zeros_like(a) if b is None else b, dtype=np.uint64)
+    n = a.size // length if op == "dot" else a.size
+    out = np.zeros(n, dtype=np.uint64)
+    r = lib().zro_arith_batch(ARITH_OPS[op], n, length, _p(a), _p(b), p, _p(out))
+    if r:
+        raise OracleError(r, f"arith_batch({op})")
+    return out
 
 
 def default_threads():

@@ -96,6 +96,51 @@ u64 zro_invmod(u64 a, u64 p) {
   return (u64)s0;
 }
 
+/* The modular primitives applied elementwise, for the device-arithmetic
+ * parity test (Sec. 2.1: modular products of residues below 2^64; Sec. 2.2:
+ * a long dot product reduced once).  Each case is the plain definition in
+ * 128-bit integers:
+ *   0 mulmod      out = a b mod p
+ *   1 reduce      out = (a 2^64 + b) mod p                     (a < p)
+ *   2 shoup_pre   out = floor(a 2^64 / p)                      (a < p)
+ *   3 shoup_lazy  out = a b - floor(a w' / 2^64) p mod 2^64,
+ *                 w' = floor(b 2^64 / p): Shoup's product, congruent to
+ *                 a b and below 2p                             (b < p)
+ *   4 pow         out = a^b mod p
+ *   5 inv         out = a^-1 mod p (extended Euclid), 0 for a = 0
+ *   6 dot         out[g] = sum_{t < len} a[g len + t] b[g len + t] mod p,
+ *                 reduced at every step
+ *   7 add, 8 sub  out = a + b, a - b mod p
+ *   9 batch inv   out = a^-1 mod p, 0 for a = 0 (as 5)
+ * n outputs; returns 1 for an unknown op. */
+int zro_arith_batch(int op, i64 n, i64 len, const u64* a, const u64* b, u64 p, u64* out) {
+  for (i64 i = 0; i < n; i++) {
+    switch (op) {
+      case 0: out[i] = mulm(a[i], b[i], p); break;
+      case 1: out[i] = (u64)((((u128)a[i]) << 64 | b[i]) % p); break;
+      case 2: out[i] = (u64)((((u128)a[i]) << 64) / p); break;
+      case 3: {
+        const u64 wq = (u64)((((u128)b[i]) << 64) / p);
+        const u64 q = (u64)(((u128)a[i] * wq) >> 64);
+        out[i] = a[i] * b[i] - q * p;   /* arithmetic mod 2^64 */
+        break;
+      }
+      case 4: out[i] = zro_powmod(a[i], b[i], p); break;
+      case 5: case 9: out[i] = a[i] % p ? zro_invmod(a[i], p) : 0; break;
+      case 6: {
+        u64 acc = 0;
+        for (i64 t = 0; t < len; t++) acc = addm(acc, mulm(a[i * len + t], b[i * len + t], p), p);
+        out[i] = acc;
+        break;
+      }
+      case 7: out[i] = addm(a[i], b[i], p); break;
+      case 8: out[i] = subm(a[i], b[i], p); break;
+      default: return 1;
+    }
+  }
+  return 0;
+}
+
 /* Deterministic Miller-Rabin for n < 2^64 (bases 2..37). */
 int zro_is_prime(u64 n) {
   static const u64 bases[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
