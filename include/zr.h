@@ -80,6 +80,13 @@ uint64_t zr_launch_count(void);
 zr_status zr_profile_enable(zr_ctx* ctx, int32_t on);
 zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count);
 
+/* Self-check of the bounded device waits (the paper has no counterpart):
+ * one warp waits on a shared-memory barrier that nothing arrives on, gives
+ * up after `tries` tries and reports it, exactly as the solve's pipeline
+ * does after its own limit.  Returns ZR_ERR_TIMEOUT when the mechanism works
+ * (the context stays usable); synchronous. */
+zr_status zr_check_bounded_wait(zr_ctx* ctx, uint32_t tries, void* stream);
+
 /* Measured ceilings (the paper has no counterpart: these are the rates the
  * solve's throughput is reported against).  Each probe runs one instruction
  * sequence of the solve with all operands in registers, independent
@@ -91,13 +98,6 @@ zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t
  *                  precomputed quotient (Sec. 2.1)
  *   imad_lo_per_s, imad_hi_per_s   32-bit mad.lo / mad.hi
  * Synchronous; uses the context workspace. */
-/* Self-check of the bounded device waits (the paper has no counterpart):
- * one warp waits on a shared-memory barrier that nothing arrives on, gives
- * up after `tries` tries and reports it, exactly as the solve's pipeline
- * does after its own limit.  Returns ZR_ERR_TIMEOUT when the mechanism works
- * (the context stays usable); synchronous. */
-zr_status zr_check_bounded_wait(zr_ctx* ctx, uint32_t tries, void* stream);
-
 typedef struct zr_peaks {
   double mac_per_s, chain_per_s, imad_lo_per_s, imad_hi_per_s;
   int32_t sms, pad;
@@ -169,7 +169,9 @@ zr_status zr_newton_batched(zr_ctx* ctx, int64_t nterms, int32_t npts, const uin
  * device current; make it before any stream capture.  All calls share the
  * array (the call clears what must start at zero), so calls that overlap on
  * the GPU race: serialise them.  Waits for `stream`; ZR_ERR_SINGULAR when two
- * nodes coincide. */
+ * nodes coincide.  A CUDA error already pending on the calling thread belongs
+ * to an earlier call: this call then returns ZR_ERR_CUDA without doing
+ * anything and leaves that error pending. */
 zr_status zr_newton_batched_noalloc(uint64_t prime, int64_t nterms, int32_t npts, const uint64_t* x,
                                     const uint64_t* vals, int64_t ld, uint64_t* coef, void* stream);
 

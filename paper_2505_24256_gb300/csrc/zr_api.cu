@@ -175,10 +175,9 @@ uint64_t hash_slots(int64_t T) {
 // carry pass adds a Shoup Horner step per k.  The cheapest plan wins;
 // measured plans from zr_autotune_step take precedence.
 static int occupancy_cached(int tile, int groups) {
-  static int cache[64][8] = {{0}};
-  if (tile <= 0 || tile >= 64 || groups < 1 || groups > 7) return 1;
-  if (!cache[tile][groups]) cache[tile][groups] = solve_blocks_per_sm(tile, groups);
-  return cache[tile][groups];
+  static DeviceValue cache[16][9];   // per device: the occupancy query sets per-device attributes
+  if (tile <= 0 || tile >= 16 || groups < 1 || groups > 8) return 1;
+  return cache[tile][groups].get([&] { return solve_blocks_per_sm(tile, groups); });
 }
 
 // A forced plan: the context's tuned plan table, else ZR_SOLVE_PLAN="tile,NB"
@@ -311,6 +310,10 @@ StepWs carve_step(Carver& cv, int64_t T, int S, int k, const StepDims& D, int Ss
 
 static std::atomic<unsigned long long> g_launches{0};
 namespace zr {
+int current_device() {
+  int d = 0;
+  return cudaGetDevice(&d) == cudaSuccess ? d : 0;
+}
 unsigned long long launch_count() { return g_launches.load(); }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -597,6 +597,17 @@ static zr_status stage_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_
   return ZR_OK;
 }
 
+// Shared-memory limits of the Newton kernels, set once per device.
+static void configure_newton_kernels() {
+  static DeviceOnce attr;
+  attr.run([] {
+    cudaFuncSetAttribute(k_b_newton_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(8 * newton_table_words(kNewtonMax)));
+    cudaFuncSetAttribute(k_b_finish_newton, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)newton_smem(kNewtonMax, kFinB));
+  });
+}
+
 // Enqueues the batch's kernels on `st` (capturable: no host synchronisation,
 // no allocation).  `prof` records the profiler's phase events.
 static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t st, bool prof) {
@@ -626,12 +637,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
     if (!ctx->ev_fork) cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (!ctx->ev_join) cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
     if (ctx->side && ctx->ev_fork && ctx->ev_join) {
-      static bool configured = false;
-      if (!configured) {
-        cudaFuncSetAttribute(k_b_newton_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(8 * newton_table_words(kNewtonMax)));
-        configured = true;
-      }
+      configure_newton_kernels();
       cudaEventRecord(ctx->ev_fork, st);
       cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
       k_b_newton_table<<<n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), ctx->side>>>(dD, M);
@@ -683,14 +689,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   // a6 (or the plain finish of a system)
   if (nroots) {
     if (mode == 0) {
-      static bool configured = false;
-      if (!configured) {
-        cudaFuncSetAttribute(k_b_newton_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(8 * newton_table_words(kNewtonMax)));
-        cudaFuncSetAttribute(k_b_finish_newton, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)newton_smem(kNewtonMax, kFinB));
-        configured = true;
-      }
+      configure_newton_kernels();
       if (side) cudaStreamWaitEvent(st, ctx->ev_join, 0);   // W of every entry (forked above)
       else {
         k_b_newton_table<<<n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), st>>>(dD, M);

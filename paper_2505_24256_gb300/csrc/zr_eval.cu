@@ -423,15 +423,14 @@ __global__ void k_eval_combine(int64_t T, int S, int gsplit, const uint64_t* __r
 template <int CG, int G>
 static int ring_occupancy_t() {
   using C = EvalRingCfg<CG, G>;
-  static int per_sm = 0;
-  if (!per_sm) {
+  static DeviceValue occ;
+  return occ.get([] {
     cudaFuncSetAttribute(k_eval_ring<CG, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval_ring<CG, G>, C::NT, C::SMEM) != cudaSuccess || n < 1)
       n = 1;
-    per_sm = n;
-  }
-  return per_sm;
+    return n;
+  });
 }
 
 template <int CG, int G>

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "zr_arith.cuh"
 
 namespace zr {
@@ -11,6 +13,41 @@ namespace zr {
 unsigned long long launch_count();
 void note_launch();
 void note_launches(uint64_t n);   // kernels of a replayed graph
+
+// Kernel attributes (the dynamic shared-memory limit) belong to a device, so
+// a once-per-process flag would configure only the first device a process
+// uses.  DeviceOnce runs its set-up once per device (the current one at the
+// call); DeviceValue caches a per-device integer such as an occupancy.
+// Devices beyond kAttrDevices simply redo the set-up on every call.  Two
+// threads may both run a set-up the first time: setting an attribute twice is
+// harmless.
+constexpr int kAttrDevices = 64;
+int current_device();
+struct DeviceOnce {
+  std::atomic<uint64_t> done{0};
+  template <class F>
+  void run(F&& fn) {
+    const int d = current_device();
+    const uint64_t bit = (d >= 0 && d < kAttrDevices) ? 1ull << d : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+    fn();
+    if (bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  }
+};
+struct DeviceValue {
+  std::atomic<int> v[kAttrDevices] = {};
+  template <class F>
+  int get(F&& compute) {
+    const int d = current_device();
+    if (d < 0 || d >= kAttrDevices) return compute();
+    int x = v[d].load(std::memory_order_acquire);
+    if (!x) {
+      x = compute();
+      v[d].store(x, std::memory_order_release);
+    }
+    return x;
+  }
+};
 
 // Device status flags (OR-ed into one 32-bit word per call).
 enum : uint32_t {

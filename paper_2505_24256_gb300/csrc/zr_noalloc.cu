@@ -22,7 +22,11 @@
 //   * every call shares the array and it keeps the previous call's contents:
 //     the status word is cleared at the start of each call and the table is
 //     rewritten for the entries the call reads.  Calls that overlap on the GPU
-//     (other streams, other host threads) race on it: serialise them.
+//     (other streams, other host threads) race on it: serialise them;
+//   * a CUDA error already pending on the calling thread (left by an earlier,
+//     unrelated runtime call) is not this call's: the call then returns
+//     ZR_ERR_CUDA at once and leaves that error pending for its owner, so that
+//     an error reported after the launches is always one of this call's.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -53,7 +57,10 @@ zr_status scratch_address(uint64_t** out) {
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_newton_scratch);
-    if (e != cudaSuccess || !p) return ZR_ERR_CUDA;
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();   // this call's own error: do not leave it pending
+      return ZR_ERR_CUDA;
+    }
     g_scratch_addr[dev] = static_cast<uint64_t*>(p);
   }
   *out = g_scratch_addr[dev];
@@ -68,20 +75,32 @@ extern "C" zr_status zr_newton_batched_noalloc(uint64_t prime, int64_t nterms, i
   if (!zr::mod_for_prime(prime, &M)) return ZR_ERR_INVALID_ARG;
   if (npts < 1 || npts > kNoAllocMaxPts || nterms < 0 || ld < nterms || !x || (nterms > 0 && (!vals || !coef)))
     return ZR_ERR_INVALID_ARG;
+  // someone else's pending error: report it without taking it
+  if (cudaPeekAtLastError() != cudaSuccess) return ZR_ERR_CUDA;
   uint64_t* scratch = nullptr;
   zr_status r = scratch_address(&scratch);
   if (r != ZR_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
   uint64_t* invd = scratch;
   uint32_t* status = reinterpret_cast<uint32_t*>(scratch + kStatusWord);
-  if (cudaMemsetAsync(status, 0, sizeof(uint32_t), st) != cudaSuccess) return ZR_ERR_CUDA;
-  zr::launch_newton_table(npts, x, M, invd, status, st);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) {
+    zr::launch_newton_table(npts, x, M, invd, status, st);
+    e = cudaGetLastError();   // nothing was pending at entry: an error here is this call's
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ZR_ERR_CUDA;
+  }
   zr::launch_newton(nterms, npts, invd, vals, ld, M, coef, st);
   uint32_t flags = 0;
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return ZR_ERR_CUDA;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ZR_ERR_CUDA;
+  }
   if (flags & zr::ST_DUP_SAMPLE) return ZR_ERR_SINGULAR;
   return flags ? ZR_ERR_CUDA : ZR_OK;
 }

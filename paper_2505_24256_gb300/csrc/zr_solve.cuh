@@ -36,7 +36,7 @@ struct SolveCfg {
   static constexpr int NST = 4;               // ring stages
   static constexpr int CGP = (CG + 1) & ~1;   // a consumer's columns, padded to pairs
   static constexpr int BW = G * CGP;          // staged right-hand-side row width
-  static constexpr int NT = 32 * (1 + G);     // threads per CTA: producer warp + G consumer warps     // threads per CTA: chain, denominator, G consumer warps
+  static constexpr int NT = 32 * (1 + G);     // threads per CTA: producer warp + G consumer warps
   // resident CTAs the register budget is sized for (measured register needs
   // of the consumer loop: about 8 CG accumulator words plus temporaries)
   static constexpr int REG = CG <= 2 ? 72 : (CG <= 3 ? 80 : (CG <= 4 ? 104 : (CG <= 6 ? 136 : 168)));
@@ -204,8 +204,8 @@ static int solve_occupancy_t() {
 template <int CG, int G>
 static void launch_solve_t(const BDesc* Ds, const int4* items, int nitems, int sms, const Mod& M, cudaStream_t st) {
   using C = SolveCfg<CG, G>;
-  static int per_sm = 0;
-  if (!per_sm) per_sm = solve_occupancy_t<CG, G>();   // also sets the shared-memory attribute
+  static DeviceValue occ;
+  const int per_sm = occ.get(solve_occupancy_t<CG, G>);   // also sets the shared-memory attribute
   // persistent: one wave walks the work list; sms <= 0: one CTA per item
   const int grid = (sms <= 0 || nitems < sms * per_sm) ? nitems : sms * per_sm;
   if (grid > 0) { k_solve<CG, G><<<grid, C::NT, C::SMEM, st>>>(Ds, items, nitems, M); note_launch(); }

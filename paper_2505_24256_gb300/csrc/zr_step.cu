@@ -85,12 +85,11 @@ __global__ void __launch_bounds__(kNewtonThreads) k_newton_table(int S, const ui
 }
 
 void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* W, uint32_t* status, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
+  static DeviceOnce attr;
+  attr.run([] {
     cudaFuncSetAttribute(k_newton_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(8 * newton_table_words(kNewtonMax)));
-    configured = true;
-  }
+  });
   const size_t smem = 8 * (size_t)newton_table_words(S);
   { k_newton_table<<<1, kNewtonThreads, smem, st>>>(S, xs, M, W, status); note_launch(); }
 }
@@ -118,11 +117,10 @@ size_t newton_smem(int S, int terms) { return sizeof(uint64_t) * ((size_t)S * S 
 void launch_newton(int64_t nterms, int npts, const uint64_t* W, const uint64_t* vals, int64_t ld, const Mod& M,
                    uint64_t* coef, cudaStream_t st) {
   if (nterms <= 0) return;
-  static bool configured = false;
-  if (!configured) {
+  static DeviceOnce attr;
+  attr.run([] {
     cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)newton_smem(kNewtonMax, 128));
-    configured = true;
-  }
+  });
   const unsigned grid = cdiv(nterms, 128);
   { k_newton<<<grid, 128, newton_smem(npts, 128), st>>>(nterms, npts, W, vals, ld, M, coef); note_launch(); }
 }

@@ -65,3 +65,54 @@ def test_noalloc_limits_and_status_reset(zrmod):
     assert zr.newton_batched_noalloc(P63, 10, 5, d64(xs), d64(v), 10, got) == zr.OK
     import oracle
     assert np.array_equal(h64(got), oracle.newton_batched(xs, v))
+
+
+def test_noalloc_allocates_no_device_memory(zrmod):
+    """The defining property: after a warm-up call (which looks the scratch
+    array up), calls of different sizes leave the device's free memory
+    unchanged.  Every input and output is allocated before the first reading."""
+    import torch
+
+    zr = zrmod
+    rnd = random.Random(11)
+    cases = []
+    for npts, nterms in [(3, 10), (21, 5000), (64, 2048), (40, 1)]:
+        x = d64(rand_nodes(rnd, npts, P63))
+        vals = d64(rand_res(rnd, (npts, nterms), P63))
+        cases.append((npts, nterms, x, vals, zeros64(npts, nterms)))
+    npts, nterms, x, vals, out = cases[0]
+    assert zr.newton_batched_noalloc(P63, nterms, npts, x, vals, nterms, out) == zr.OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        for npts, nterms, x, vals, out in cases:
+            assert zr.newton_batched_noalloc(P63, nterms, npts, x, vals, nterms, out) == zr.OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_on_a_second_device(zrmod):
+    """The scratch address and the kernels' shared-memory limits are set up per
+    device: npts = 64 (above the default shared-memory limit) on device 1 after
+    device 0 gives the context version's result."""
+    import torch
+
+    zr = zrmod
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    rnd = random.Random(12)
+    xs, v = rand_nodes(rnd, 64, P63), rand_res(rnd, (64, 300), P63)
+    for d in (0, 1):
+        with torch.cuda.device(d):
+            x = torch.from_numpy(xs.view(np.int64)).to(f"cuda:{d}")
+            vals = torch.from_numpy(v.view(np.int64)).to(f"cuda:{d}")
+            got = torch.zeros((64, 300), dtype=torch.int64, device=f"cuda:{d}")
+            assert zr.newton_batched_noalloc(P63, 300, 64, x, vals, 300, got) == zr.OK
+            ctx = zr.Context(P63)
+            try:
+                want = torch.zeros_like(got)
+                ctx.newton_batched(300, 64, x, vals, 300, want)
+            finally:
+                ctx.close()
+            assert np.array_equal(h64(got), h64(want))
