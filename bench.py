@@ -11,6 +11,11 @@ reported separately.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl zr|reference]
                     [--workload batched|large|serve] [--requests R]
+                    [--no-large] [--no-serve] [--serve-requests R]
+
+The default line times the step at T = 10^4, S = 21 (`value`), and adds the
+large single step at T = 2^20, S = 9 (`large_step`) and the serving mix of
+512 requests (`serve`), each checked against its hidden function.
 
 --workload serve runs the serving mix instead (R requests of hidden sparse
 polynomials and rational functions, 2-8 variables, T log-uniform in
@@ -67,6 +72,30 @@ def solve_traffic(workload_name):
 def workload(name):
     from paper_2505_24256_gb300 import workloads as W
     return {"batched": W.batched_step_1e4, "large": W.large_step_2p20}[name]()
+
+
+L2_NOTE = "flushed between timed steps (256 MB write)"
+
+
+def bench_config(wl, world):
+    """The `config` of the JSON line; both arms print the same dict."""
+    return {"workload": wl.name, "T": wl.T, "S": wl.S, "nv": wl.nv, "prime": wl.p, "l2": L2_NOTE,
+            "parallelism": f"replicas{world}"}
+
+
+# Instruction counts of the solve's two sequences (csrc/zr_arith.cuh), in the
+# 32-bit multiply forms of the PTX they are written in: a mac8 is 4 mad.lo +
+# 4 mad.hi (+ 3 addc); a Shoup chain step (mulhi64 + two mullo64) is 9 mad.lo
+# + 6 mad.hi.  mad.hi issues at 32 lanes per SM per clock on this GPU, mad.lo
+# at 64 on a separate pipe (zr_measure_peaks), so mad.hi bounds both.
+MAC_HI, CHAIN_HI = 4, 6
+HI_LANES_PER_SM_CLK = 32
+
+
+def theoretical_rates(sms, sm_mhz):
+    """mad.hi-issue ceilings (per second) of the MAC and of the chain step."""
+    hi = sms * HI_LANES_PER_SM_CLK * sm_mhz * 1e6
+    return hi / MAC_HI, hi / CHAIN_HI
 
 
 class Clocks:
@@ -197,7 +226,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": wl.name, "T": wl.T, "S": wl.S, "nv": wl.nv, "prime": wl.p},
+        "config": bench_config(wl, args.gpus),
         "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle",
                          "sample": f"full step T={wl.T} S={wl.S} per timed step (probes from the oracle, untimed)"},
         "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -310,6 +339,36 @@ def small_steps_modes(ctx, dev, n=64, reps=20):
     out["check"] = "generator truth" if ok else "MISMATCH"
     g.close()
     return out
+
+
+def solve_roofline(T, S, solve_avg_s, peaks, workload_name):
+    """Roofline entry of the O(T^2) solve kernel k_solve: its algorithmic work
+    per launch (S T^2 multiply-accumulates of the dot products, T^2 chain
+    steps of the synthetic division and T^2 of the denominator q_j(v_j))
+    over its average launch time, against two ceilings weighted by that mix:
+    the measured rates of the two instruction sequences (zr_measure_peaks,
+    this run) and their mad.hi-issue bound at the maximum SM clock."""
+    macs, chain_steps = S * T * T, 2 * T * T
+    ops = macs + chain_steps
+    achieved = ops / solve_avg_s
+    peak = ops / (macs / peaks["mac_per_s"] + chain_steps / peaks["chain_per_s"])
+    sms = peaks.get("sms") or 152
+    mac_th, chain_th = theoretical_rates(sms, SM_MAX_MHZ)
+    peak_th = ops / (macs / mac_th + chain_steps / chain_th)
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
+            "frac": achieved / peak, "traffic": solve_traffic(workload_name), "traffic_unit": "bytes/launch",
+            "kernel": "k_solve",
+            "ops": f"S*T^2 multiply-accumulates + 2*T^2 chain steps = {ops:.4g} per launch",
+            "peak_basis": "measured (zr_measure_peaks on this GPU, this run): "
+                          f"{peaks['mac_per_s'] / 1e9:.0f} GMAC/s, {peaks['chain_per_s'] / 1e9:.0f} G chain "
+                          "steps/s, weighted by the solve's mix",
+            "peak_theoretical": peak_th / 1e9, "frac_theoretical": achieved / peak_th,
+            "theoretical_basis": f"mad.hi issue: {sms} SMs x {HI_LANES_PER_SM_CLK} lanes/clk x {SM_MAX_MHZ:.0f} MHz; "
+                                 f"{MAC_HI} mad.hi per MAC ({mac_th / 1e9:.0f} G/s), {CHAIN_HI} per chain step "
+                                 f"({chain_th / 1e9:.0f} G/s), weighted by the solve's mix"}
+
+
+SM_MAX_MHZ = 2070.0   # GB300 maximum SM clock (the clocks record of each run gives the live value)
 
 
 def run_zr(args):
@@ -464,6 +523,14 @@ def run_zr(args):
     small = small_steps_modes(ctx, dev)
     recons = reconstruction_configs(ctx, with_oracle=world == 1 and not args.no_cpu_baseline) \
         if args.workload == "batched" else None
+    # the largest single-GPU configuration (T = 2^20) and the serving mix, on
+    # every rank (replicas), in the same line
+    large = None
+    if args.workload == "batched" and not args.no_large:
+        large = large_step_bench(ctx, dev, flush, peaks, steps=2, warmup=1)
+    serve = None
+    if args.workload == "batched" and not args.no_serve:
+        serve = serve_mix(args, args.serve_requests, 1005 + 1000 * rank)
 
     if rank != 0:
         ctx.close()
@@ -472,14 +539,6 @@ def run_zr(args):
         return 0
 
     solve_avg_s = solve_ms / max(solve_n, 1) / 1e3
-    # the solve's algorithmic work per (root j, k): S multiply-accumulates of
-    # the dot products, one chain step of the synthetic division and one of
-    # the denominator q_j(v_j)
-    macs, chain_steps = S * T * T, 2 * T * T
-    solve_ops = macs + chain_steps
-    t_star = macs / peaks["mac_per_s"] + chain_steps / peaks["chain_per_s"]      # measured ceiling
-    achieved = solve_ops / solve_avg_s
-    peak = solve_ops / t_star
     ms_per_step = total_ms / args.steps
     W = (S + 2.5) * T * T
     line = {
@@ -488,18 +547,11 @@ def run_zr(args):
         "unit": "terms/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": wl.name, "T": T, "S": S, "nv": nv, "prime": wl.p,
-                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}"},
+        "config": bench_config(wl, world),
         "mulmod_per_s": world * W * args.steps / (total_ms / 1e3),
         # the median step of this rank (the per-step figure the paper reports)
         "median": {"ms_per_step": median_ms, "terms_per_s": T / (median_ms / 1e3), "steps": len(step_times)},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
-                     "frac": achieved / peak, "traffic": solve_traffic(wl.name), "traffic_unit": "bytes/launch",
-                     "kernel": "k_solve",
-                     "ops": f"S*T^2 multiply-accumulates + 2*T^2 chain steps = {solve_ops:.4g} per launch",
-                     "peak_basis": "measured (zr_measure_peaks on this GPU, this run): "
-                                   f"{peaks['mac_per_s'] / 1e9:.0f} GMAC/s, {peaks['chain_per_s'] / 1e9:.0f} G chain "
-                                   "steps/s, weighted by the solve's mix"},
+        "roofline": solve_roofline(T, S, solve_avg_s, peaks, wl.name),
         "peaks_measured": {"mac_per_s": peaks["mac_per_s"], "chain_per_s": peaks["chain_per_s"],
                            "imad_lo_per_s": peaks["imad_lo_per_s"], "imad_hi_per_s": peaks["imad_hi_per_s"]},
         "plain_form": {"ms_per_step": plain_ms, "terms_per_s": world * T / (plain_ms / 1e3),
@@ -509,6 +561,8 @@ def run_zr(args):
         "graph": {"ms_per_step": graph_ms, "kernels_per_launch": graph_kernels},
         "small_steps": small,
         "reconstructions": recons,
+        "large_step": large,
+        "serve": serve,
         "phase_ms": phases,
         "plan": {"s_tile": plan[0], "k_blocks": plan[1]},
         "probe_gen_ms": probe_ms,
@@ -521,7 +575,8 @@ def run_zr(args):
                 "d2h_bytes_per_step": ne * (nv + 8) + 12},
         "gpu_launches": int(launches),
         "clocks": clk,
-        "check": "generator truth" if (ok and e2e_ok) else "MISMATCH",
+        "check": "generator truth" if (ok and e2e_ok and (large is None or large["check"] == "generator truth")
+                                       and (serve is None or serve["check"] == "generator truth")) else "MISMATCH",
     }
     if world == 1 and not args.no_cpu_baseline and args.workload == "batched":
         import oracle
@@ -541,6 +596,106 @@ def run_zr(args):
     return 0
 
 
+def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
+    """The large single step, T = 2^20 terms in 7 variables, S = 9: probes by
+    the GPU evaluator (timed apart), then `warmup` untimed and `steps` timed
+    steps with the L2 flushed before each, checked against the hidden function;
+    the plain one-system-per-launch form is timed on one of its S identical
+    single-right-hand-side systems and scaled by S."""
+    import numpy as np
+    import torch
+
+    from paper_2505_24256_gb300 import workloads as W
+
+    def d64(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(dev)
+
+    wl = W.large_step_2p20()
+    T, S, nv, k = wl.T, wl.S, wl.nv, wl.k
+    stream = torch.cuda.current_stream()
+    fe, fc = torch.from_numpy(wl.exps).to(dev), d64(wl.coef)
+    f = ctx.poly(nv, wl.exps.shape[0], fe, fc)
+    y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
+    ske = torch.from_numpy(wl.skel).to(dev)
+    skel = ctx.poly(nv, T, ske)
+    b = torch.empty((S, T), dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.zippel_probes(f, k, y, S, cs, z, T, 0, b, T)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    probe_ms = e0.elapsed_time(e1)
+    del fe, fc
+    cap = T * S
+    oe = torch.zeros((cap, nv), dtype=torch.uint8, device=dev)
+    oc = torch.zeros(cap, dtype=torch.int64, device=dev)
+    for _ in range(warmup):
+        flush.zero_()
+        ctx.zippel_step(skel, k, y, S, cs, b, T, 0, oe, oc, cap)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    n = 0
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        n = ctx.zippel_step(skel, k, y, S, cs, b, T, 0, oe, oc, cap)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    times = [a.elapsed_time(bb) for a, bb in evs]
+    solve_ms, solve_n = ctx.profile_query("solve")
+    phases = {ph: ctx.profile_query(ph)[0] / max(steps, 1) for ph in ctx.PHASES[:7]}
+    ctx.profile(False)
+    ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
+        np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
+    del oe, oc
+    ms = sum(times) / len(times)
+    # the plain form: one single-right-hand-side system per launch sequence;
+    # its S systems are identical in cost, so one is timed and scaled by S
+    v = torch.empty(T, dtype=torch.int64, device=dev)
+    c1 = torch.empty(T, dtype=torch.int64, device=dev)
+    ctx.anchor_values(T, nv, ske, k, y, 0, v)
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.vandermonde_solve([dict(T=T, S=1, v=v, b=b[0], ldb=T, c=c1, ldc=T)], plain=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_one_ms = e0.elapsed_time(e1)
+    # the first system's solution is c_j = g_j(c_0) = sum_e G[j, e] c_0^e:
+    # 64 sampled roots against the hidden coefficients (Python integers)
+    plain_ok = True
+    idx = np.linspace(0, T - 1, 64).astype(np.int64)
+    got = c1.cpu().numpy().view(np.uint64)[idx]
+    c0 = int(wl.cs[0])
+    for jj, gv in zip(idx, got):
+        want = 0
+        for e in range(S - 1, -1, -1):
+            want = (want * c0 + int(wl.G[jj, e])) % wl.p
+        plain_ok &= int(gv) == want
+    W_ = (S + 2.5) * T * T
+    return {
+        "workload": wl.name, "T": T, "S": S, "nv": nv, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms, "terms_per_s": T / (ms / 1e3), "mulmod_per_s": W_ / (ms / 1e3),
+        "roofline": solve_roofline(T, S, solve_ms / max(solve_n, 1) / 1e3, peaks, wl.name),
+        "phase_ms": phases,
+        "plain_form": {"ms_per_step": plain_one_ms * S, "terms_per_s": T / (plain_one_ms * S / 1e3),
+                       "batched_speedup": plain_one_ms * S / ms,
+                       "what": f"{S} single-RHS systems, one launch sequence each; one timed "
+                               f"({plain_one_ms:.0f} ms) and scaled by {S} (identical cost)",
+                       "check": "generator truth (64 sampled roots)" if plain_ok else "MISMATCH"},
+        "probe_gen": {"ms": probe_ms, "macs": S * T * T, "mac_per_s": S * T * T / (probe_ms * 1e-3),
+                      "frac_of_measured_mac_peak": S * T * T / (probe_ms * 1e-3) / peaks["mac_per_s"]},
+        "clocks": clk,
+        "l2": "flushed before each timed step (256 MB write); the step's inputs exceed L2",
+        "check": "generator truth" if ok else "MISMATCH",
+    }
+
+
 def serve_stats(lat_ms):
     import numpy as np
     a = np.sort(np.asarray(lat_ms, dtype=np.float64))
@@ -548,19 +703,24 @@ def serve_stats(lat_ms):
     return {"p50_ms": q(0.5), "p99_ms": q(0.99), "mean_ms": float(a.mean())}
 
 
-def run_serve(args):
-    """The serving mix: plain per-request form vs the continuous-batching server."""
+def serve_mix(args, nreq, seed):
+    """The serving mix of nreq requests (hidden sparse polynomials and rational
+    functions, 2-8 variables, T log-uniform in [16, tmax]):
+      * the plain per-request form, zr_reconstruct once per request, back to
+        back (throughput and service times);
+      * the continuous-batching server with every request submitted at once
+        (saturated throughput);
+      * the server under Poisson arrivals at 0.7 of its saturated rate;
+      * the plain form under the same arrivals, run in real time (a request
+        starts at its arrival or when the previous one ends).
+    Every result is checked against its hidden function."""
     import numpy as np
     import torch
 
-    import __graft_entry__ as ge
     from paper_2505_24256_gb300 import workloads as W
     from paper_2505_24256_gb300 import zr
 
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    ge.build()
-    reqs = W.serve_requests(args.requests, seed=1005 + 1000 * rank, tmax=args.tmax)
+    reqs = W.serve_requests(nreq, seed=seed, tmax=args.tmax)
     wls = [W.serve_blackbox(r) for r in reqs]
     reqobjs = []
     for wl in wls:
@@ -579,31 +739,28 @@ def run_serve(args):
                 np.array_equal(D[0], wl.Dexps) and np.array_equal(D[1], wl.Dcoef)
         return np.array_equal(e, wl.exps) and np.array_equal(c, wl.coef)
 
-    ctx = zr.Context(W.P63)
-    # warm-up: the first few requests through both forms
-    for wl in wls[:min(args.warmup, len(wls))]:
+    def plain_one(ctx, wl):
         if isinstance(wl, W.RationalWorkload):
-            ctx.reconstruct(wl.nv, wl.degN, wl.seed, wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef, degD=wl.degD)
-        else:
-            ctx.reconstruct(wl.nv, wl.deg, wl.seed, wl.exps, wl.coef)
+            return ctx.reconstruct(wl.nv, wl.degN, wl.seed, wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef, degD=wl.degD)
+        return ctx.reconstruct(wl.nv, wl.deg, wl.seed, wl.exps, wl.coef)
+
+    ctx = zr.Context(W.P63)
+    for wl in wls[:min(args.warmup, len(wls))]:
+        plain_one(ctx, wl)
     torch.cuda.synchronize()
-    clocks = Clocks(local)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     launches0 = zr.launch_count()
-    # (1) plain per-request form: one zr_reconstruct after another
+    # (1) plain per-request form, back to back
     svc = []
     ok_plain = True
     t_plain0 = time.perf_counter()
     for wl in wls:
         t0 = time.perf_counter()
-        if isinstance(wl, W.RationalWorkload):
-            res = ctx.reconstruct(wl.nv, wl.degN, wl.seed, wl.Nexps, wl.Ncoef, wl.Dexps, wl.Dcoef, degD=wl.degD)
-        else:
-            res = ctx.reconstruct(wl.nv, wl.deg, wl.seed, wl.exps, wl.coef)
+        res = plain_one(ctx, wl)
         svc.append(time.perf_counter() - t0)
         ok_plain &= truth(wl, res)
     plain_s = time.perf_counter() - t_plain0
-    ctx.close()
 
     def serve(gaps):
         c = zr.Context(W.P63)
@@ -630,45 +787,75 @@ def run_serve(args):
     cap_rps = sat["completed"] / sat["wall_s"]
     # (3) Poisson arrivals at 0.7 x the saturated rate
     lam = 0.7 * cap_rps
-    rng = np.random.default_rng(1005)
+    rng = np.random.default_rng(seed)
     gaps = list(rng.exponential(1.0 / lam, size=len(wls)))
     poi, ok_poi, outs = serve(gaps)
+    # (4) the plain form under the same arrivals, in real time
+    arr = np.cumsum(gaps)
+    lat = []
+    ok_plain_poi = True
+    t0 = time.perf_counter()
+    for a, wl in zip(arr, wls):
+        while time.perf_counter() - t0 < a:
+            time.sleep(min(0.0005, max(0.0, a - (time.perf_counter() - t0))))
+        res = plain_one(ctx, wl)
+        lat.append(1e3 * (time.perf_counter() - t0 - a))
+        ok_plain_poi &= truth(wl, res)
+    plain_poi_s = time.perf_counter() - t0
+    ctx.close()
     launches = zr.launch_count() - launches0
     clk = clocks.stop()
-    # the plain form under the same arrivals: one request at a time in arrival
-    # order (single-server FIFO queue on the measured service times)
-    arr = np.cumsum(gaps)
-    fin, lat = 0.0, []
-    for a, s_ in zip(arr, svc):
-        start = max(a, fin)
-        fin = start + s_
-        lat.append(1e3 * (fin - a))
-    plain_lat = serve_stats(lat)
-    line = {
-        "metric": METRIC,
-        "value": sat["terms_per_s"], "unit": "terms/s",
-        "n_gpus": world, "steps": len(wls), "warmup": args.warmup,
-        "ms_per_step": 1e3 * sat["wall_s"] / max(1, len(wls)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"serve_{len(wls)}_requests", "requests": len(wls), "seed": 1005, "tmax": args.tmax,
-                   "terms": terms, "slots": args.slots, "mem_budget_gb": args.serve_budget_gb,
-                   "l2": "inputs of the larger requests exceed L2", "parallelism": f"replicas{world}"},
+    return {
+        "requests": len(wls), "seed": seed, "tmax": args.tmax, "terms": terms, "slots": args.slots,
+        "mem_budget_gb": args.serve_budget_gb,
         "serve_saturated": {"terms_per_s": sat["terms_per_s"], "requests_per_s": cap_rps, "p50_ms": sat["p50_ms"],
-                            "p99_ms": sat["p99_ms"], "ticks": sat["ticks"], "batch_entries": sat["batch_entries"],
-                            "max_active": sat["max_active"]},
+                            "p99_ms": sat["p99_ms"], "wall_s": sat["wall_s"], "ticks": sat["ticks"],
+                            "batch_entries": sat["batch_entries"], "max_active": sat["max_active"]},
         "serve_poisson": {"lambda_per_s": lam, "terms_per_s": poi["terms_per_s"], "p50_ms": poi["p50_ms"],
                           "p99_ms": poi["p99_ms"], "mean_ms": poi["mean_ms"], "max_active": poi["max_active"]},
         "plain_per_request": {"terms_per_s": terms / plain_s, "requests_per_s": len(wls) / plain_s,
-                              "poisson_same_arrivals": plain_lat,
-                              "service_ms": serve_stats([1e3 * x for x in svc])},
-        "e2e": {"value": sat["terms_per_s"], "unit": "terms/s",
-                "h2d_bytes_per_step": int(sum(o[0].bb.TN * (o[0].bb.nv + 8) + o[0].bb.TD * (o[0].bb.nv + 8)
-                                              for o in reqobjs) / max(1, len(wls))),
-                "d2h_bytes_per_step": int(sum((r[0][1].shape[0] + (0 if r[1] is None else r[1][1].shape[0]))
-                                              * (r[0][0].shape[1] + 8) for r in outs) / max(1, len(wls)))},
+                              "service_ms": serve_stats([1e3 * x for x in svc]),
+                              "poisson_same_arrivals": dict(serve_stats(lat), wall_s=plain_poi_s,
+                                                            how="measured: run in real time under the same "
+                                                                "arrivals, one request at a time")},
+        "saturated_speedup": sat["terms_per_s"] / (terms / plain_s),
         "gpu_launches": int(launches),
         "clocks": clk,
-        "check": "generator truth" if (ok_plain and ok_sat and ok_poi) else "MISMATCH",
+        "h2d_bytes_per_request": int(sum(o[0].bb.TN * (o[0].bb.nv + 8) + o[0].bb.TD * (o[0].bb.nv + 8)
+                                         for o in reqobjs) / max(1, len(wls))),
+        "d2h_bytes_per_request": int(sum((r[0][1].shape[0] + (0 if r[1] is None else r[1][1].shape[0]))
+                                         * (r[0][0].shape[1] + 8) for r in outs) / max(1, len(wls))),
+        "check": "generator truth" if (ok_plain and ok_sat and ok_poi and ok_plain_poi) else "MISMATCH",
+    }
+
+
+def run_serve(args):
+    """The serving mix alone (--workload serve), its own JSON line."""
+    import torch
+
+    import __graft_entry__ as ge
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ge.build()
+    r = serve_mix(args, args.requests, 1005 + 1000 * rank)
+    sat = r["serve_saturated"]
+    line = {
+        "metric": METRIC,
+        "value": sat["terms_per_s"], "unit": "terms/s",
+        "n_gpus": world, "steps": r["requests"], "warmup": args.warmup,
+        "ms_per_step": 1e3 * sat["wall_s"] / max(1, r["requests"]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"serve_{r['requests']}_requests", "requests": r["requests"], "seed": 1005,
+                   "tmax": args.tmax, "terms": r["terms"], "slots": args.slots,
+                   "mem_budget_gb": args.serve_budget_gb,
+                   "l2": "inputs of the larger requests exceed L2", "parallelism": f"replicas{world}"},
+        "e2e": {"value": sat["terms_per_s"], "unit": "terms/s", "h2d_bytes_per_step": r["h2d_bytes_per_request"],
+                "d2h_bytes_per_step": r["d2h_bytes_per_request"]},
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
+        "serve": r,
+        "check": r["check"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -684,6 +871,9 @@ def main():
     ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=512, help="serving mix size (--workload serve)")
+    ap.add_argument("--serve-requests", type=int, default=512, help="serving mix size in the default line")
+    ap.add_argument("--no-large", action="store_true", help="leave the T = 2^20 step out of the default line")
+    ap.add_argument("--no-serve", action="store_true", help="leave the serving mix out of the default line")
     ap.add_argument("--tmax", type=int, default=1 << 17, help="largest request T (--workload serve)")
     ap.add_argument("--slots", type=int, default=64, help="server slots (--workload serve)")
     ap.add_argument("--serve-budget-gb", type=int, default=64, help="server memory budget (--workload serve)")
@@ -701,7 +891,9 @@ if __name__ == "__main__":
     rc = main()
     sys.stdout.flush()
     sys.stderr.flush()
-    # Leave without interpreter teardown: the result line is out, the
-    # library context is closed, and process-exit destructors of the CUDA
-    # libraries have crashed under the profiler.
-    os._exit(rc or 0)
+    # Under the profiler, process-exit destructors of the CUDA libraries have
+    # crashed after the result line was out: the profiling commands set
+    # ZR_BENCH_HARD_EXIT=1 to leave without interpreter teardown.
+    if os.environ.get("ZR_BENCH_HARD_EXIT") == "1":
+        os._exit(rc or 0)
+    sys.exit(rc or 0)

@@ -34,3 +34,30 @@ def test_reference_line_keys():
 def test_reference_large_is_unavailable():
     d = _run("--impl", "reference", "--workload", "large")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_both_arms_print_the_same_config():
+    """The driver compares the two arms' `config` dicts: both come from one
+    function, so they are equal for every workload and world size."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2505_24256_gb300 import workloads as W
+
+    wl = W.step_workload(1002, 50, 5, 20, 21, name="step_T10000_S21")
+    d = _run("--impl", "reference", "--steps", "1", "--warmup", "3")
+    full = W.batched_step_1e4()
+    assert d["config"] == bench.bench_config(full, 1)
+    assert bench.bench_config(wl, 2)["parallelism"] == "replicas2"
+
+
+def test_theoretical_ceiling_arithmetic():
+    """mad.hi-issue ceilings: 152 SMs x 32 lanes x 2070 MHz over 4 (MAC) and 6 (chain step)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    mac, chain = bench.theoretical_rates(152, 2070.0)
+    assert abs(mac - 152 * 32 * 2070e6 / 4) < 1 and abs(chain - 152 * 32 * 2070e6 / 6) < 1
+    r = bench.solve_roofline(10_000, 21, 1.5e-3, {"mac_per_s": 2.0e12, "chain_per_s": 0.8e12, "sms": 152},
+                             "no_such_workload")
+    ops = 23 * 10_000 ** 2
+    assert abs(r["achieved"] - ops / 1.5e-3 / 1e9) < 1e-6
+    assert r["frac_theoretical"] < r["frac"] and r["traffic"] is None
