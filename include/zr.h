@@ -87,6 +87,31 @@ zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t
  * (the context stays usable); synchronous. */
 zr_status zr_check_bounded_wait(zr_ctx* ctx, uint32_t tries, void* stream);
 
+/* Self-check of the device modular arithmetic (Sec. 2.1: the 64-bit modular
+ * product through a precomputed reciprocal; Sec. 2.2: a long dot product
+ * accumulated without reduction and reduced once).  Applies one primitive of
+ * the step kernels elementwise, i = 0..n-1, with the context's prime p:
+ *   0 mulmod      out = a b mod p                                (a, b < p)
+ *   1 reduce      out = (a 2^64 + b) mod p                       (a < p)
+ *   2 shoup_pre   out = floor(a 2^64 / p)                        (a < p)
+ *   3 shoup_lazy  out = Shoup's product of a (any 64-bit value) and b < p:
+ *                 a b - floor(a floor(b 2^64 / p) / 2^64) p mod 2^64, in [0, 2p)
+ *   4 pow         out = a^b mod p
+ *   5 inv         out = a^(p-2) mod p (0 for a = 0)
+ *   6 dot         out[i] = sum_{t < len} a[i len + t] b[i len + t] mod p
+ *                 (1 <= len < 2^31; one 160-bit accumulator per i)
+ *   7 add, 8 sub  out = a +- b mod p                             (a, b < p)
+ *   9 batch_inv   out = a^-1 mod p (0 for a = 0) by Montgomery's batch trick
+ *                 over consecutive groups of 32
+ * a, b, out: device arrays (b unused by 2, 5, 9); for dot, a and b hold
+ * n len values.  hits: NULL, or a device uint32[4] to which the call adds how
+ * often the two correction steps of the Moller-Granlund division ran
+ * (hits[0], hits[1]: in the reductions of ops 0, 1, 6; hits[2], hits[3]: in
+ * op 2).  Synchronous; ZR_ERR_INVALID_ARG for an unknown op or bad sizes.
+ * The paper has no counterpart: this is test instrumentation. */
+zr_status zr_check_arith(zr_ctx* ctx, int32_t op, int64_t n, int64_t len, const uint64_t* a, const uint64_t* b,
+                         uint64_t* out, uint32_t* hits, void* stream);
+
 /* Measured ceilings (the paper has no counterpart: these are the rates the
  * solve's throughput is reported against).  Each probe runs one instruction
  * sequence of the solve with all operands in registers, independent

@@ -92,8 +92,11 @@ __device__ __forceinline__ uint64_t mullo64(uint64_t a, uint64_t b) {
   return ((uint64_t)r1 << 32) | r0;
 }
 
-// (u1 2^64 + u0) mod p for u1 < p (Moller-Granlund 2/1 division).
-__device__ __forceinline__ uint64_t reduce128(uint64_t u1, uint64_t u0, const Mod& M) {
+// (u1 2^64 + u0) mod p for u1 < p (Moller-Granlund 2/1 division).  With
+// COUNT (the arithmetic self-test only) the two correction steps are counted
+// in hits[0] and hits[1]; the default form compiles without them.
+template <bool COUNT = false>
+__device__ __forceinline__ uint64_t reduce128(uint64_t u1, uint64_t u0, const Mod& M, uint32_t* hits = nullptr) {
   uint64_t n1 = (u1 << M.norm) | (u0 >> (64 - M.norm));
   uint64_t n0 = u0 << M.norm;
   uint64_t q1, q0;
@@ -102,13 +105,21 @@ __device__ __forceinline__ uint64_t reduce128(uint64_t u1, uint64_t u0, const Mo
   q1 += n1 + (q0 < n0);
   q1 += 1;
   uint64_t r = n0 - mullo64(q1, M.d);
-  if (r > q0) r += M.d;
-  if (r >= M.d) r -= M.d;
+  if (r > q0) {
+    r += M.d;
+    if (COUNT) atomicAdd(&hits[0], 1u);
+  }
+  if (r >= M.d) {
+    r -= M.d;
+    if (COUNT) atomicAdd(&hits[1], 1u);
+  }
   return r >> M.norm;
 }
 
-// floor(w 2^64 / p) for w < p: the quotient of the same division.
-__device__ __forceinline__ uint64_t shoup_pre(uint64_t w, const Mod& M) {
+// floor(w 2^64 / p) for w < p: the quotient of the same division (COUNT as
+// for reduce128).
+template <bool COUNT = false>
+__device__ __forceinline__ uint64_t shoup_pre(uint64_t w, const Mod& M, uint32_t* hits = nullptr) {
   uint64_t n1 = w << M.norm, n0 = 0;
   uint64_t q1, q0;
   mul128(M.v, n1, q1, q0);
@@ -116,8 +127,15 @@ __device__ __forceinline__ uint64_t shoup_pre(uint64_t w, const Mod& M) {
   q1 += n1 + (q0 < n0);
   q1 += 1;
   uint64_t r = n0 - mullo64(q1, M.d);
-  if (r > q0) { q1 -= 1; r += M.d; }
-  if (r >= M.d) { q1 += 1; }
+  if (r > q0) {
+    q1 -= 1;
+    r += M.d;
+    if (COUNT) atomicAdd(&hits[0], 1u);
+  }
+  if (r >= M.d) {
+    q1 += 1;
+    if (COUNT) atomicAdd(&hits[1], 1u);
+  }
   return q1;
 }
 
@@ -191,6 +209,20 @@ __device__ __forceinline__ uint64_t acc8_value(const Acc8& a, const Mod& M) {
   const uint64_t c3 = M2 < M1;
   const uint64_t top = (uint64_t)a.r4 + c2 + c3;       // < 2^33 < p
   return reduce128(reduce128(top, M2, M), L2, M);
+}
+// The same with the corrections of both reductions counted (self-test only).
+__device__ __forceinline__ uint64_t acc8_value_counted(const Acc8& a, const Mod& M, uint32_t* hits) {
+  const uint64_t L = ((uint64_t)a.r1 << 32) | a.r0;
+  const uint64_t Mi = ((uint64_t)a.r3 << 32) | a.r2;
+  const uint64_t Tt = ((uint64_t)a.t2 << 32) | a.t1;
+  const uint64_t L2 = L + ((uint64_t)a.t0 << 32);
+  const uint64_t c1 = L2 < L;
+  const uint64_t M1 = Mi + Tt;
+  const uint64_t c2 = M1 < Mi;
+  const uint64_t M2 = M1 + c1;
+  const uint64_t c3 = M2 < M1;
+  const uint64_t top = (uint64_t)a.r4 + c2 + c3;
+  return reduce128<true>(reduce128<true>(top, M2, M, hits), L2, M, hits);
 }
 
 

@@ -128,6 +128,7 @@ SIGNATURES = {
     "zr_result_free": (None, [ctypes.POINTER(zr_result)]),
     "zr_measure_peaks": (_ST, [_V, _P, _V]),
     "zr_check_bounded_wait": (_ST, [_V, ctypes.c_uint32, _V]),
+    "zr_check_arith": (_ST, [_V, _I32, _I64, _I64, _P, _P, _P, _P, _V]),
     "zr_step_graph_create": (_ST, [_V, _I32, _P, _V, ctypes.POINTER(_V)]),
     "zr_step_graph_launch": (_ST, [_V, _V]),
     "zr_step_graph_status": (_ST, [_V, _V]),
@@ -218,6 +219,14 @@ class Context:
     def check_bounded_wait(self, tries=4096, stream=None) -> int:
         """Status of a device wait that nothing completes (TIMEOUT when it gives up as designed)."""
         return int(self.L.zr_check_bounded_wait(self._h, tries, _stream(stream)))
+
+    ARITH_OPS = {"mulmod": 0, "reduce": 1, "shoup_pre": 2, "shoup_lazy": 3, "pow": 4, "inv": 5, "dot": 6, "add": 7,
+                 "sub": 8, "batch_inv": 9}
+
+    def check_arith(self, op, n, a, b, out, hits=None, length=1, stream=None):
+        """zr_check_arith: device primitive `op` on device arrays (see the header)."""
+        self.check(self.L.zr_check_arith(self._h, self.ARITH_OPS[op], n, length, _ptr(a), _ptr(b), _ptr(out),
+                                         _ptr(hits), _stream(stream)), "zr_check_arith")
 
     def measure_peaks(self, stream=None) -> dict:
         """Measured MAC / chain-step / IMAD rates (operations per second)."""

@@ -1,5 +1,6 @@
 """GPU parity: the probe evaluator and the Zippel step through the C ABI,
 against the oracle (element by element) and against generator truth."""
+import os
 import random
 
 import numpy as np
@@ -134,14 +135,31 @@ def test_step_host_buffers(ctx, orc):
     assert np.array_equal(oe[:n], wl.exps) and np.array_equal(oc[:n], wl.coef)
 
 
+def probes_at_points(orc, wl, sidx, iidx, offset=0):
+    """The probes (s, i) by the oracle's plain point-by-point evaluation at the
+    explicit points (y^(i+offset), c_s, z), one point per host thread."""
+    from concurrent.futures import ThreadPoolExecutor
+    k = wl.k
+    pts = [[pow(int(wl.y[m]), i + offset, wl.p) for m in range(k)] + [int(wl.cs[s])] +
+           [int(x) for x in wl.z[k + 1:]] for s, i in zip(sidx, iidx)]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        vals = list(ex.map(lambda pt: int(orc.eval_points(wl.exps, wl.coef, [pt])[0]), pts))
+    return np.array(vals, dtype=np.uint64)
+
+
 def test_batched_step_workload_full(ctx, orc):
     """The T = 10^4, S = 21 step in full: probes and new skeleton against the
-    oracle element by element, and against generator truth."""
+    oracle element by element, and against generator truth; 64 sampled probes
+    also against the plain evaluation at their explicit points."""
     wl = W.batched_step_1e4()
     D = Dev(ctx, wl)
     b = D.probes(ctx)
     want_b = orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, wl.T)
     assert np.array_equal(h64(b), want_b)
+    rnd = random.Random(4)
+    sidx = [rnd.randrange(wl.S) for _ in range(62)] + [0, wl.S - 1]
+    iidx = [rnd.randrange(wl.T) for _ in range(62)] + [wl.T - 1, 0]
+    assert np.array_equal(h64(b)[sidx, iidx], probes_at_points(orc, wl, sidx, iidx))
     ge_, gc_ = D.step(ctx, b)
     assert np.array_equal(ge_, wl.exps) and np.array_equal(gc_, wl.coef)
     we, wc = orc.zippel_step(wl.skel, wl.k, wl.y, wl.cs, want_b)
@@ -161,6 +179,9 @@ def test_large_step_workload(ctx, orc):
     iidx = [rnd.randrange(wl.T) for _ in range(48)] + [0, wl.T - 1]
     want = orc.zippel_probes_sampled(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, sidx, iidx)
     assert np.array_equal(hb[sidx, iidx], want)
+    # 16 of them also by the plain point-by-point evaluation (9.4 M terms each)
+    assert np.array_equal(hb[sidx[:14] + sidx[-2:], iidx[:14] + iidx[-2:]],
+                          probes_at_points(orc, wl, sidx[:14] + sidx[-2:], iidx[:14] + iidx[-2:]))
     ge_, gc_ = D.step(ctx, b)
     assert np.array_equal(ge_, wl.exps) and np.array_equal(gc_, wl.coef)
 

@@ -39,6 +39,30 @@ def test_probes_match_plain_definition(orc):
         assert [int(x) for x in samp] == [int(b[0, 8]), int(b[2, 0]), int(b[1, 4])]
 
 
+def test_probes_match_plain_definition_heavy_sharing(orc):
+    """2000 hidden terms whose x_0, x_1 exponents come from only 12 prefixes
+    (groups of ~170 terms merged by the regrouped sum), against the plain
+    point-by-point definition in Python integers."""
+    rnd = random.Random(52)
+    nv, k, Tf, T, S = 4, 2, 2000, 30, 3
+    prefixes = [(rnd.randrange(9), rnd.randrange(9)) for _ in range(12)]
+    rows = set()
+    while len(rows) < Tf:
+        a, b = prefixes[rnd.randrange(12)]
+        rows.add((a, b, rnd.randrange(15), rnd.randrange(15)))
+    exps = np.array(sorted(rows, key=lambda r: rnd.random()), dtype=np.uint8)
+    coef = np.array([rnd.randrange(P63) for _ in range(Tf)], dtype=np.uint64)
+    y = [rnd.randrange(1, P63) for _ in range(k)]
+    cs = [rnd.randrange(P63) for _ in range(S)]
+    z = [rnd.randrange(P63) for _ in range(nv)]
+    for offset in (0, 1):
+        b = orc.zippel_probes(exps, coef, k, y, cs, z, T, offset=offset)
+        for s in range(S):
+            for i in range(T):
+                pt = [pow(y[m], i + offset, P63) for m in range(k)] + [cs[s]] + z[k + 1:]
+                assert int(b[s, i]) == pyref.eval_sparse(exps, coef, pt)
+
+
 def test_eval_points_definition(orc):
     rnd = random.Random(51)
     exps = np.array([[rnd.randrange(7) for _ in range(3)] for _ in range(25)], dtype=np.uint8)
