@@ -457,7 +457,7 @@ def run_zr(args):
     median_ms = step_times[len(step_times) // 2] if len(step_times) % 2 else \
         0.5 * (step_times[len(step_times) // 2 - 1] + step_times[len(step_times) // 2])
     solve_ms, solve_n = ctx.profile_query("solve")
-    phases = {ph: ctx.profile_query(ph)[0] / max(args.steps, 1) for ph in zr.Context.PHASES[:7]}
+    phases = {ph: ctx.profile_query(ph)[0] / max(args.steps, 1) for ph in zr.Context.PHASES[:7] + ("fast",)}
     ctx.profile(False)
     total_ms = max_over_ranks(total_ms, world, dev)
     # the output of the last timed step against generator truth
@@ -648,7 +648,7 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
     clk = clocks.stop()
     times = [a.elapsed_time(bb) for a, bb in evs]
     solve_ms, solve_n = ctx.profile_query("solve")
-    phases = {ph: ctx.profile_query(ph)[0] / max(steps, 1) for ph in ctx.PHASES[:7]}
+    phases = {ph: ctx.profile_query(ph)[0] / max(steps, 1) for ph in ctx.PHASES[:7] + ("fast",)}
     ctx.profile(False)
     ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
         np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)

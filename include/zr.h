@@ -73,7 +73,9 @@ size_t zr_workspace_bytes(const zr_ctx* ctx);
  * every step enqueued by the context (0 anchor values + node check, 1 master
  * polynomial, 2 right-hand sides in MAC form, 3 k-block carries, 4 the
  * synthetic-division/dot kernel, 5 denominators + inverses + Newton,
- * 6 compaction, 7 probe evaluation); zr_profile_enable resets the totals,
+ * 6 compaction, 7 probe evaluation, 8 the O(T log^2 T) solve of the systems
+ * that take it: tree, power sums, descent and leaves); zr_profile_enable
+ * resets the totals,
  * zr_profile_query waits for the recorded events and returns the summed
  * milliseconds and the number of timed occurrences of a phase. */
 uint64_t zr_launch_count(void);
@@ -161,6 +163,25 @@ typedef struct zr_vsys {
   uint64_t* c;
   int64_t ldc;
 } zr_vsys;
+
+/* Choice of solve method for the systems of every later call on the context
+ * (steps, systems, reconstructions, the server):
+ *   0  by size: the O(T log^2 T) method for T >= crossover (crossover 0: the
+ *      library's measured default), the O(T^2) method below it;
+ *   1  always the O(T^2) method of Sec. 2.2 (Horner quotients, deferred dot
+ *      products, one inverse per root);
+ *   2  the O(T log^2 T) method for every T it supports.
+ * The O(T log^2 T) method evaluates the same solution c_j = N(v_j) / M'(v_j)
+ * through a subproduct tree: products of polynomials modulo p by
+ * number-theoretic transforms over five 30-bit primes and the Chinese
+ * remainder theorem, and a descent of the tree with middle products (a scaled
+ * remainder tree), with M'(v_j) from the power sums of the nodes (a
+ * power-series inverse by Newton's iteration).  It handles 1 <= T <= 2^21;
+ * larger systems always take the O(T^2) method.  Results are identical.
+ * The paper's method is the O(T^2) one; this is a faster route to the same
+ * values.  Errors: ZR_ERR_INVALID_ARG for a method outside 0..2 or a negative
+ * crossover. */
+zr_status zr_solve_method(zr_ctx* ctx, int32_t method, int64_t crossover);
 
 /* Solves nsys independent systems (sys is a host array).  Systems of
  * different T and S share every launch: one set of launches for the whole

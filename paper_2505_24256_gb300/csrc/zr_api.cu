@@ -355,6 +355,7 @@ extern "C" zr_status zr_create(uint64_t prime, zr_ctx** out) {
   zr_ctx* ctx = new (std::nothrow) zr_ctx();
   if (!ctx) return ZR_ERR_OOM;
   ctx->M = make_mod(prime);
+  ctx->ntt = make_ntt_consts(prime);
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 2 * sizeof(uint32_t));
@@ -395,10 +396,31 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ntt_tw) cudaFree(ctx->ntt_tw);
   delete ctx;
 }
 
 extern "C" const char* zr_last_error(const zr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+// Size from which the automatic choice takes the fast solve (measured on
+// GB300: below it the quadratic kernel's single pass beats the fast path's
+// chain of transform launches).
+static constexpr int64_t kFastDefaultMinT = 4096;
+
+namespace zr {
+bool use_fast_solve(const zr_ctx* ctx, int64_t T) {
+  if (T < 1 || T > kFastMaxT || ctx->solve_method == 1) return false;
+  if (ctx->solve_method == 2) return true;
+  return T >= (ctx->fast_min_T > 0 ? ctx->fast_min_T : kFastDefaultMinT);
+}
+}  // namespace zr
+
+extern "C" zr_status zr_solve_method(zr_ctx* ctx, int32_t method, int64_t crossover) {
+  if (!ctx || method < 0 || method > 2 || crossover < 0) return set_err(ctx, ZR_ERR_INVALID_ARG, "zr_solve_method");
+  ctx->solve_method = method;
+  ctx->fast_min_T = crossover;
+  return ZR_OK;
+}
 extern "C" uint64_t zr_prime(const zr_ctx* ctx) { return ctx ? ctx->M.p : 0; }
 extern "C" size_t zr_workspace_bytes(const zr_ctx* ctx) { return ctx ? ctx->ws_cap : 0; }
 

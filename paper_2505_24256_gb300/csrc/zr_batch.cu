@@ -414,20 +414,36 @@ struct Prepared {
   std::vector<size_t> o_lvl;
   std::vector<int> tiles_used;        // solve instances: tile * 16 + consumer groups
   std::vector<std::vector<int4>> work;
+  std::vector<char> fast;             // entries solved by the O(T log^2 T) path
   int kmax = 0, smax = 0, lmax = 0, mode = 0;
-  size_t ws_bytes = 0, table_bytes = 0;
+  size_t ws_bytes = 0, table_bytes = 0, fast_bytes = 0;
 };
 
 static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& P) {
   P.mode = items[0].mode;
   P.plan.resize(n);
+  P.fast.assign(n, 0);
   for (int i = 0; i < n; i++) {
     const BatchItem& it = items[i];
     if (it.mode != P.mode) return false;
-    P.plan[i] = plan_step(ctx, it.T, it.solve_S());
+    P.fast[i] = use_fast_solve(ctx, it.T) ? 1 : 0;
+    if (P.fast[i]) {
+      // one k-block: the finish kernels read the numerators and M'(v_j) as a
+      // single block's partials
+      StepDims D;
+      D.T = it.T;
+      D.S = it.solve_S();
+      D.NB = 1;
+      D.BK = it.T;
+      D.s_tile = 2;
+      P.plan[i] = D;
+      P.fast_bytes = std::max(P.fast_bytes, fast_ws_need(it.T, it.solve_S() + 1));
+    } else {
+      P.plan[i] = plan_step(ctx, it.T, it.solve_S());
+      P.lmax = std::max(P.lmax, tree_levels(it.T));
+    }
     P.kmax = std::max(P.kmax, it.k);
     P.smax = std::max(P.smax, it.S);
-    P.lmax = std::max(P.lmax, tree_levels(it.T));
   }
   Carver m0(nullptr);
   for (int i = 0; i < n; i++) carve_step(m0, items[i].T, items[i].S, items[i].k, P.plan[i], items[i].solve_S());
@@ -437,7 +453,7 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
     const int64_t T = items[i].T;
     c_hash[i] = T > 0 ? (int64_t)hash_slots(T) : 0;
     c_roots[i] = T;
-    c_leaf[i] = (T + (1 << kTreeL1) - 1) >> kTreeL1;
+    c_leaf[i] = P.fast[i] ? 0 : (T + (1 << kTreeL1) - 1) >> kTreeL1;
     c_nblk[i] = (T + kFinB - 1) / kFinB;
     c_carry[i] = (T > 0 && P.plan[i].NB > 1) ? (int64_t)((T + 255) / 256) * (P.plan[i].NB - 1) : 0;
   }
@@ -448,13 +464,14 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
   push_prefix(P.pre, c_nblk, P.o_nblk);
   for (int l = kTreeL1; l < P.lmax; l++) {
     std::vector<int64_t> c(n);
-    for (int i = 0; i < n; i++) c[i] = tree_levels(items[i].T) > l ? (items[i].T + tree_tile(l) - 1) / tree_tile(l) : 0;
+    for (int i = 0; i < n; i++)
+      c[i] = (!P.fast[i] && tree_levels(items[i].T) > l) ? (items[i].T + tree_tile(l) - 1) / tree_tile(l) : 0;
     size_t o;
     push_prefix(P.pre, c, o);
     P.o_lvl.push_back(o);
   }
   for (int i = 0; i < n; i++) {
-    if (items[i].T == 0) continue;
+    if (items[i].T == 0 || P.fast[i]) continue;
     // one work list per (tile, consumer groups): the solve kernel instance
     const int tile = P.plan[i].s_tile, groups = (items[i].solve_S() + tile - 1) / tile;
     const int key = tile * 16 + groups;
@@ -482,7 +499,7 @@ size_t batch_ws_need(const zr_ctx* ctx, const BatchItem* items, int n) {
   if (n <= 0) return 0;
   Prepared P;
   if (!prepare(ctx, items, n, P)) return 0;
-  return P.ws_bytes + P.table_bytes + 512;
+  return P.ws_bytes + P.table_bytes + 512 + (P.fast_bytes ? P.fast_bytes + 256 : 0);
 }
 
 // A batch whose descriptor tables are on the device: everything launch_batch
@@ -494,6 +511,8 @@ struct StagedBatch {
   const int64_t* dpre = nullptr;
   std::vector<const int4*> dwork;
   std::vector<int64_t*> zero_counts;   // out_count of entries with T = 0
+  std::vector<BDesc> hD;               // host copy of the descriptors (the fast entries' pointers)
+  char* fast_ws = nullptr;             // workspace of the fast entries (one at a time)
 };
 
 // Plans the batch, carves its workspace at `ws` (batch_ws_need bytes) and
@@ -529,7 +548,7 @@ static zr_status stage_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_
     d.BK = plan[i].BK;
     d.s_tile = plan[i].s_tile;
     d.nst = (d.S + plan[i].s_tile - 1) / plan[i].s_tile;   // consumer groups of the solve
-    d.levels = tree_levels(it.T);
+    d.levels = P.fast[i] ? 0 : tree_levels(it.T);
     d.hmask = hash_slots(it.T) - 1;
     d.exps = it.exps;
     d.y = it.y;
@@ -560,6 +579,7 @@ static zr_status stage_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_
   }
   // stage the tables in pinned memory, then one copy
   char* dtab = cv.take<char>(table_bytes + 256);
+  SB.fast_ws = P.fast_bytes ? cv.take<char>(P.fast_bytes) : nullptr;
   if (ctx->stage_event) cudaEventSynchronize(ctx->stage_event);
   if (ctx->h_stage_cap < table_bytes) {
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -591,6 +611,7 @@ static zr_status stage_batch(zr_ctx* ctx, const BatchItem* items, int n, uint32_
   SB.dD = dD;
   SB.dpre = dpre;
   SB.dwork = dwork;
+  SB.hD = D;
   SB.zero_counts.clear();
   for (int i = 0; i < n; i++)
     if (items[i].T == 0 && P.mode == 0 && items[i].out_count) SB.zero_counts.push_back(items[i].out_count);
@@ -663,7 +684,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
     const int64_t want = 4ll * (ctx->sms ? ctx->sms : 152);
     int split = (int)((want + nt - 1) / nt);
     for (int i = 0; i < n; i++)
-      if (tree_levels(P.plan[i].T) > l) split = std::min(split, (int)tree_split_max(P.plan[i].T));
+      if (!P.fast[i] && tree_levels(P.plan[i].T) > l) split = std::min(split, (int)tree_split_max(P.plan[i].T));
     // and keep at least 128 inner terms per split: below that the combine
     // launch costs more than the shorter serial work saves
     split = std::min(split, (int)std::max<int64_t>(1, (1ll << l) / 128));
@@ -686,6 +707,15 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
                         ctx->solve_persistent ? (ctx->sms ? ctx->sms : 152) : 0, M, st))
       return set_err(ctx, ZR_ERR_INVALID_ARG, "no solve kernel for this launch plan");
   cudaEvent_t e4 = mark();
+  // entries of the O(T log^2 T) solve: numerators and M'(v_j) into the
+  // single-block partials the finish reads
+  for (int i = 0; i < n; i++) {
+    if (!P.fast[i]) continue;
+    const BDesc& d = SB.hD[i];
+    zr_status r = fast_solve_enqueue(ctx, d.T, d.S, d.v, d.vp, d.b, d.ldb, d.part, d.denp, SB.fast_ws, st);
+    if (r) return r;
+  }
+  cudaEvent_t e4f = mark();
   // a6 (or the plain finish of a system)
   if (nroots) {
     if (mode == 0) {
@@ -717,7 +747,8 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   prof_add(ctx, PH_MASTER, e1, e2);
   prof_add(ctx, PH_CARRY, e2, e3);
   prof_add(ctx, PH_SOLVE, e3, e4);
-  prof_add(ctx, PH_NEWTON, e4, e5);
+  prof_add(ctx, PH_FAST, e4, e4f);
+  prof_add(ctx, PH_NEWTON, e4f, e5);
   prof_add(ctx, PH_COMPACT, e5, e6);
   return cuda_err(ctx, cudaGetLastError(), "batch launch");
 }

@@ -1,0 +1,669 @@
+// zr_fast.cu -- the transposed Vandermonde solve in O(T log^2 T).
+//
+// The step's systems sum_j c_j v_j^k = b_k (k < T) have the solution
+// c_j = N(v_j) / M'(v_j) (Sec. 1; Sec. 2.2 writes it with the quotients
+// q_j = M / (z - v_j): N(v_j) = <q_j, b>), where M = prod_j (z - v_j) and the
+// generating function sum_k b_k z^(-k-1) = sum_j c_j / (z - v_j) = N / M.  The
+// quadratic kernel forms every dot product <q_j, b>; this path evaluates N at
+// all nodes with a subproduct tree instead (Bernstein's scaled remainder
+// tree; the transposed multipoint evaluation of Bostan, Lecerf and Schost):
+//
+//   tree     M's factors are paired level by level: leaf blocks of 128 roots
+//            (products in one CTA), then products of sibling polynomials by
+//            transforms (zr_ntt.cuh).  The children's spectra are kept.
+//   descent  b itself is the expansion of N / M to precision T.  A node P
+//            with children L, R passes to L the expansion of (N mod P) R / P
+//            truncated to deg L terms: X_L[m] = sum_{i <= deg R} r_i X_P[m+i],
+//            a middle product computed as a cyclic convolution of size 2^l of
+//            the reversed X_P with R, read backwards; likewise for R.
+//   leaves   at a block P of 128 roots, X_P is the expansion of a
+//            generating function whose numerator is N(v_j) / (M/P)(v_j) at
+//            the block's roots; <q^P_j, X_P> with q^P_j = P / (z - v_j) gives
+//            N(v_j) directly (the quadratic method on 128 roots).
+//   denominators   M'(v_j) is the same evaluation with N = M', whose
+//            expansion M'/M = sum_k (sum_j v_j^k) z^(-k-1) holds the power
+//            sums of the nodes: rev(M') / rev(M) mod z^T, by Newton's
+//            iteration for the power-series inverse.
+//
+// The results are the unique solution, bit-identical to the quadratic path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "zr_device.cuh"
+#include "zr_internal.h"
+#include "zr_ntt.cuh"
+
+namespace zr {
+
+namespace {
+
+inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+inline int ilog2(int64_t x) {
+  int l = 0;
+  while ((1ll << l) < x) l++;
+  return l;
+}
+
+// ---- tables ----------------------------------------------------------------------
+
+__device__ uint32_t pow32(uint32_t a, uint32_t e, uint32_t q) {
+  uint64_t r = 1, x = a;
+  while (e) {
+    if (e & 1) r = r * x % q;
+    x = x * x % q;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+
+// tw[i N + k] = w_{2m}^brev(k - m), itw the inverse, m the largest power of
+// two <= k (w_{2m} a primitive 2m-th root of unity mod q_i), with Shoup
+// quotients.
+__global__ void k_ntt_tables(int logN, NttConsts C, uint2* __restrict__ tw, uint2* __restrict__ itw) {
+  const int64_t N = 1ll << logN;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kNP * N) return;
+  const int i = (int)(idx >> logN);
+  const uint32_t k = (uint32_t)(idx & (N - 1));
+  const uint32_t q = C.q[i];
+  uint32_t w = 1, wi = 1;
+  if (k >= 1) {
+    const int lm = 31 - __clz(k);
+    const uint32_t m = 1u << lm, j = k - m;
+    const uint32_t e = lm ? (__brev(j) >> (32 - lm)) : 0;
+    const uint32_t root = pow32(C.g[i], (q - 1) >> (lm + 1), q);
+    w = pow32(root, e, q);
+    wi = pow32(root, (2 * m - e) & (2 * m - 1), q);
+  }
+  tw[idx] = make_uint2(w, (uint32_t)(((uint64_t)w << 32) / q));
+  itw[idx] = make_uint2(wi, (uint32_t)(((uint64_t)wi << 32) / q));
+}
+
+// ---- transforms --------------------------------------------------------------------
+//
+// Data: planes of 2^plane_log residues, plane k holding prime k mod 5; each
+// plane is a run of transforms of size n = 2^logn.  Forward stage s (m = 2^s
+// groups of distance t = n / 2^(s+1)) pairs j and j + t of group j / 2t with
+// twiddle tw[m + group]; the inverse runs the stages in reverse order.
+// Stages with t < kNttTile / 2 act within contiguous tiles of kNttTile
+// elements (k_ntt_local); the first logn - 13 forward stages (last inverse
+// ones) act within columns of stride 2^13 (k_ntt_cols).
+
+template <bool INV>
+__device__ __forceinline__ void butterfly(uint32_t* a, uint32_t* b, uint2 w, uint32_t q) {
+  const uint32_t X = *a, Y = *b;
+  if (!INV) {
+    // X, Y < 4q -> outputs < 4q
+    const uint32_t x = sub_if(X, 2 * q);
+    const uint32_t t = shoup32(Y, w.x, w.y, q);
+    *a = x + t;
+    *b = x - t + 2 * q;
+  } else {
+    // X, Y < 2q -> outputs < 2q
+    *a = sub_if(X + Y, 2 * q);
+    *b = shoup32(X - Y + 2 * q, w.x, w.y, q);
+  }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict__ data, int64_t total, int logn,
+                                                           int plane_log, int s_lo, const uint2* __restrict__ tw,
+                                                           int logN, NttConsts C) {
+  __shared__ uint32_t sm[kNttTile];
+  const int64_t base = (int64_t)blockIdx.x * kNttTile;
+  const int len = (int)((total - base) < kNttTile ? (total - base) : kNttTile);
+  for (int e = threadIdx.x; e < len; e += kNttThreads) sm[e] = data[base + e];
+  __syncthreads();
+  const int half = len >> 1;
+  const int nst = logn - s_lo;
+  for (int step = 0; step < nst; step++) {
+    const int s = INV ? (logn - 1 - step) : (s_lo + step);
+    const int lt = logn - s - 1;                      // log2 t
+    const uint32_t m = 1u << s;
+    for (int b = threadIdx.x; b < half; b += kNttThreads) {
+      const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
+      const int64_t g = base + pos;
+      const int prime = (int)((g >> plane_log) % kNP);
+      const uint32_t grp = (uint32_t)((g & ((1ll << logn) - 1)) >> (lt + 1));
+      const uint2 w = __ldg(&tw[((int64_t)prime << logN) + m + grp]);
+      butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], w, C.q[prime]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < len; e += kNttThreads) data[base + e] = sm[e];
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__ data, int logn, int plane_log, int L1,
+                                                          const uint2* __restrict__ tw, int logN, NttConsts C) {
+  __shared__ uint32_t sm[kNttTile];
+  const int cwl = kNttTileLog - L1, CW = 1 << cwl;
+  const int64_t tbase = (int64_t)(blockIdx.x >> L1) << logn;
+  const int jlo0 = (blockIdx.x & ((1 << L1) - 1)) * CW;
+  for (int e = threadIdx.x; e < kNttTile; e += kNttThreads) {
+    const int h = e >> cwl, c = e & (CW - 1);
+    sm[e] = data[tbase + ((int64_t)h << kNttTileLog) + jlo0 + c];
+  }
+  __syncthreads();
+  const int prime = (int)((tbase >> plane_log) % kNP);
+  const uint32_t q = C.q[prime];
+  const uint2* __restrict__ twp = tw + ((int64_t)prime << logN);
+  for (int step = 0; step < L1; step++) {
+    const int s = INV ? (L1 - 1 - step) : step;
+    const int lth = L1 - s - 1;                       // log2 of the row distance
+    const uint32_t m = 1u << s;
+    for (int b = threadIdx.x; b < kNttTile / 2; b += kNttThreads) {
+      const int c = b & (CW - 1), hb = b >> cwl;
+      const int h = ((hb >> lth) << (lth + 1)) | (hb & ((1 << lth) - 1));
+      const uint2 w = __ldg(&twp[m + (uint32_t)(h >> (lth + 1))]);
+      butterfly<INV>(&sm[(h << cwl) + c], &sm[((h + (1 << lth)) << cwl) + c], w, q);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kNttTile; e += kNttThreads) {
+    const int h = e >> cwl, c = e & (CW - 1);
+    data[tbase + ((int64_t)h << kNttTileLog) + jlo0 + c] = sm[e];
+  }
+}
+
+// ---- loads, products, Chinese remaindering ---------------------------------------
+
+// Tree level l (nodes of size n = 2^l, children of size h = n/2): every child
+// c of node P as a full monic polynomial of its degree d_c (coefficients from
+// the level below, then 1, then zeros up to n), as residues:
+//   spec[i][P][c][k], plane of 2T' per prime.
+__global__ void k_tree_load(const uint64_t* __restrict__ below, int64_t T, int64_t Tp, int logn, NttConsts C,
+                            uint32_t* __restrict__ spec) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP * 2T'
+  if (idx >= kNP * 2 * Tp) return;
+  const int i = (int)(idx / (2 * Tp));
+  const int64_t r = idx - (int64_t)i * 2 * Tp;
+  const int64_t n = 1ll << logn, h = n >> 1;
+  const int64_t child = r >> logn;          // 2P + c
+  const int64_t k = r & (n - 1);
+  int64_t d = T - child * h;
+  d = d < 0 ? 0 : (d > h ? h : d);
+  uint32_t x = 0;
+  if (k < d) x = residue64(below[child * h + k], C, i);
+  else if (k == d) x = 1;
+  spec[idx] = x;
+}
+
+// Z[i][P][k] = spec_L[k] spec_R[k] (Montgomery), per prime plane of T'.
+__global__ void k_tree_mul(const uint32_t* __restrict__ spec, int64_t Tp, int logn, NttConsts C,
+                           uint32_t* __restrict__ Z) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP * T'
+  if (idx >= kNP * Tp) return;
+  const int i = (int)(idx / Tp);
+  const int64_t r = idx - (int64_t)i * Tp;
+  const int64_t P = r >> logn, k = r & ((1ll << logn) - 1);
+  const uint32_t q = C.q[i];
+  const uint32_t* s = spec + (int64_t)i * 2 * Tp + (2 * P << logn);
+  Z[idx] = mont32(sub_if(s[k], 2 * q), sub_if(s[(1ll << logn) + k], 2 * q), q, C.qinv[i]);
+}
+
+// coef[P n + k] = (L R)[k] for k < d_P, from the inverse transforms; when
+// d_P = n the leading z^n wrapped onto z^0 and is taken off.
+__global__ void k_tree_crt(const uint32_t* __restrict__ Z, int64_t T, int64_t Tp, int logn, NttConsts C, CrtScale sc,
+                           Mod M, uint64_t* __restrict__ coef) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= Tp) return;
+  const int64_t n = 1ll << logn;
+  const int64_t P = r >> logn, k = r & (n - 1);
+  int64_t d = T - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  if (k >= d) return;
+  uint32_t res[kNP];
+#pragma unroll
+  for (int i = 0; i < kNP; i++) res[i] = shoup32(Z[(int64_t)i * Tp + r], sc.s[i], sc.sp[i], C.q[i]);
+  uint64_t x = crt_to_p(res, C, M);
+  if (k == 0 && d == n) x = sub_mod(x, 1, M);
+  coef[r] = x;
+}
+
+// Descent load: XH[r][i][P n + k] = X_P[d_P - 1 - k] (k < d_P), else 0.
+__global__ void k_desc_load(const uint64_t* __restrict__ X, int R, int64_t T, int64_t Tp, int logn, NttConsts C,
+                            uint32_t* __restrict__ XH) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over R * kNP * T'
+  if (idx >= (int64_t)R * kNP * Tp) return;
+  const int64_t plane = idx / Tp;
+  const int64_t e = idx - plane * Tp;
+  const int rr = (int)(plane / kNP), i = (int)(plane - (int64_t)rr * kNP);
+  const int64_t n = 1ll << logn;
+  const int64_t P = e >> logn, k = e & (n - 1);
+  int64_t d = T - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  XH[idx] = k < d ? residue64(X[(int64_t)rr * Tp + P * n + d - 1 - k], C, i) : 0;
+}
+
+// Descent products: Y[c][r][i][P n + k] = XH[r][i][P n + k] spec[i][P][1 - c][k].
+__global__ void k_desc_mul(const uint32_t* __restrict__ XH, const uint32_t* __restrict__ spec, int R, int64_t Tp,
+                           int logn, NttConsts C, uint32_t* __restrict__ Y) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over R * kNP * T'
+  const int64_t all = (int64_t)R * kNP * Tp;
+  if (idx >= all) return;
+  const int64_t plane = idx / Tp;
+  const int64_t e = idx - plane * Tp;
+  const int i = (int)(plane % kNP);
+  const uint32_t q = C.q[i], qi = C.qinv[i];
+  const int64_t P = e >> logn, k = e & ((1ll << logn) - 1);
+  const uint32_t* s = spec + (int64_t)i * 2 * Tp + (2 * P << logn) + k;
+  const uint32_t x = sub_if(XH[idx], 2 * q);
+  Y[idx] = mont32(x, sub_if(s[1ll << logn], 2 * q), q, qi);          // child L: times R
+  Y[all + idx] = mont32(x, sub_if(s[0], 2 * q), q, qi);              // child R: times L
+}
+
+// Descent Chinese remaindering: X'[r][(2P + c) h + m] = y_c[d_P - 1 - m], m < d_c.
+__global__ void k_desc_crt(const uint32_t* __restrict__ Y, int R, int64_t T, int64_t Tp, int logn, NttConsts C,
+                           CrtScale sc, Mod M, uint64_t* __restrict__ Xn) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over R * T' (child slots)
+  if (idx >= (int64_t)R * Tp) return;
+  const int rr = (int)(idx / Tp);
+  const int64_t slot = idx - (int64_t)rr * Tp;             // (2P + c) h + m
+  const int64_t n = 1ll << logn, h = n >> 1;
+  const int64_t child = slot / h, m = slot - child * h;
+  const int64_t P = child >> 1;
+  const int c = (int)(child & 1);
+  int64_t d = T - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  const int64_t dl = d < h ? d : h;
+  const int64_t dc = c ? d - dl : dl;
+  if (m >= dc) return;
+  const int64_t all = (int64_t)R * kNP * Tp;
+  const uint32_t* y = Y + c * all + (int64_t)rr * kNP * Tp + P * n + (d - 1 - m);
+  uint32_t res[kNP];
+#pragma unroll
+  for (int i = 0; i < kNP; i++) res[i] = shoup32(y[(int64_t)i * Tp], sc.s[i], sc.sp[i], C.q[i]);
+  Xn[idx] = crt_to_p(res, C, M);
+}
+
+// ---- general cyclic products (Newton's iteration) ----------------------------------
+
+// A[i][k] = a[k] mod q_i for k < na, else 0 (planes of N)
+__global__ void k_cyc_load(const uint64_t* __restrict__ a, int64_t na, int logN, NttConsts C, uint32_t* __restrict__ A) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ((int64_t)kNP << logN)) return;
+  const int i = (int)(idx >> logN);
+  const int64_t k = idx & ((1ll << logN) - 1);
+  A[idx] = k < na ? residue64(a[k], C, i) : 0;
+}
+__global__ void k_cyc_mul(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B, int logN, NttConsts C,
+                          uint32_t* __restrict__ Z) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ((int64_t)kNP << logN)) return;
+  const int i = (int)(idx >> logN);
+  const uint32_t q = C.q[i];
+  Z[idx] = mont32(sub_if(A[idx], 2 * q), sub_if(B[idx], 2 * q), q, C.qinv[i]);
+}
+// out[t] = +-(a * b)[lo + t], t < cnt
+__global__ void k_cyc_crt(const uint32_t* __restrict__ Z, int logN, int64_t lo, int64_t cnt, int neg, NttConsts C,
+                          CrtScale sc, Mod M, uint64_t* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  uint32_t res[kNP];
+#pragma unroll
+  for (int i = 0; i < kNP; i++) res[i] = shoup32(Z[((int64_t)i << logN) + lo + t], sc.s[i], sc.sp[i], C.q[i]);
+  const uint64_t x = crt_to_p(res, C, M);
+  out[t] = neg ? (x ? M.p - x : 0) : x;
+}
+
+// f_t = coefficient t of rev(M) (f_0 = 1, f_t = m_{T-t}); rd_t = (T - t) m_{T-t}
+// (rev(M'), degree T - 1); g_0 = 1.
+__global__ void k_rev_poly(const uint64_t* __restrict__ m, int64_t T, Mod M, uint64_t* __restrict__ f,
+                           uint64_t* __restrict__ rd, uint64_t* __restrict__ g) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > T) return;
+  const uint64_t mt = t == 0 ? 1 : m[T - t];
+  f[t] = mt;
+  if (t < T) rd[t] = mul_mod((uint64_t)(T - t) % M.p, mt, M);
+  if (t == 0) g[0] = 1;
+}
+
+// ---- leaves --------------------------------------------------------------------------
+
+constexpr int kLeaf = 128;                     // roots per leaf block (tree level 7)
+constexpr int kLeafLog = 7;
+
+// Block polynomials prod_{j in block} (z - v_j), monic, degree d <= 128:
+// levels 0..6 of pairwise products in shared memory.
+__global__ void __launch_bounds__(kLeaf) k_fast_leafpoly(const uint64_t* __restrict__ v, int64_t T, Mod M,
+                                                         uint64_t* __restrict__ coef) {
+  __shared__ uint64_t buf[2][kLeaf];
+  const int64_t base = (int64_t)blockIdx.x * kLeaf;
+  const int cnt = (int)((T - base) < kLeaf ? (T - base) : kLeaf);
+  const int t = threadIdx.x;
+  if (t < cnt) {
+    const uint64_t x = v[base + t];
+    buf[0][t] = x ? M.p - x : 0;
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int l = 0; l < kLeafLog; l++) {
+    const int size = 1 << l, pair = 2 << l;
+    if (t < cnt) {
+      const int po = t & ~(pair - 1);
+      uint64_t r;
+      if (cnt - po <= size) r = buf[cur][t];
+      else r = conv_coef(buf[cur], po, size, min(size, cnt - po - size), t - po, M);
+      buf[cur ^ 1][t] = r;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (t < cnt) coef[base + t] = buf[cur][t];
+}
+
+// Leaf values: for root j of block P (degree d), val_r = <q^P_j, X_P^(r)>,
+// q^P_{j,d-1} = 1, q^P_{j,k-1} = p_k + v_j q^P_{j,k}.  Rows r < R - 1 are the
+// right-hand sides (written to part[r ldp + j]), row R - 1 the power sums
+// (M'(v_j), written to den[j]).  The chain is rerun per group of 8 rows.
+constexpr int kLeafCols = 8;
+__global__ void __launch_bounds__(kLeaf) k_fast_leafval(const uint64_t* __restrict__ coef7,
+                                                        const uint64_t* __restrict__ X, int R, int64_t T, int64_t Tp,
+                                                        const uint64_t* __restrict__ v, const uint64_t* __restrict__ vp,
+                                                        Mod M, uint64_t* __restrict__ part, int64_t ldp,
+                                                        uint64_t* __restrict__ den) {
+  extern __shared__ uint64_t lsm[];
+  uint64_t* pc = lsm;                 // block polynomial, kLeaf words
+  uint64_t* xs = lsm + kLeaf;         // X rows, R x kLeaf
+  const int64_t base = (int64_t)blockIdx.x * kLeaf;
+  const int d = (int)((T - base) < kLeaf ? (T - base) : kLeaf);
+  const int t = threadIdx.x;
+  if (t < d) pc[t] = coef7[base + t];
+  for (int r = 0; r < R; r++)
+    if (t < d) xs[r * kLeaf + t] = X[(int64_t)r * Tp + base + t];
+  __syncthreads();
+  if (t >= d) return;
+  const int64_t j = base + t;
+  const uint64_t vj = v[j], vpj = vp[j];
+  for (int r0 = 0; r0 < R; r0 += kLeafCols) {
+    Acc8 acc[kLeafCols];
+#pragma unroll
+    for (int c = 0; c < kLeafCols; c++) acc[c] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t q = 1;
+    for (int k = d - 1; k >= 0; k--) {
+      const uint64_t qc = canon(q, M);
+      const uint32_t x0 = lo32(qc), x1 = hi32(qc);
+#pragma unroll
+      for (int c = 0; c < kLeafCols; c++)
+        if (r0 + c < R) {
+          const uint64_t w = xs[(r0 + c) * kLeaf + k];
+          mac8(acc[c], x0, x1, lo32(w), hi32(w));
+        }
+      q = canon(shoup_lazy(qc, vj, vpj, M), M) + pc[k];
+    }
+#pragma unroll
+    for (int c = 0; c < kLeafCols; c++) {
+      const int r = r0 + c;
+      if (r < R - 1) part[(int64_t)r * ldp + j] = acc8_value(acc[c], M);
+      else if (r == R - 1) den[j] = acc8_value(acc[c], M);
+    }
+  }
+}
+
+// X0[r][k] = b[r ldb + k] (r < S), X0[S][k] = power sums (k < T)
+__global__ void k_stage_rhs(const uint64_t* __restrict__ b, int64_t ldb, int S, const uint64_t* __restrict__ ps,
+                            int64_t T, int64_t Tp, uint64_t* __restrict__ X0) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)(S + 1) * T) return;
+  const int r = (int)(idx / T);
+  const int64_t k = idx - (int64_t)r * T;
+  X0[(int64_t)r * Tp + k] = r < S ? b[(int64_t)r * ldb + k] : ps[k];
+}
+
+// ---- host side ---------------------------------------------------------------------
+
+uint32_t h_pow32(uint64_t a, uint64_t e, uint64_t q) {
+  uint64_t r = 1 % q;
+  a %= q;
+  while (e) {
+    if (e & 1) r = r * a % q;
+    a = a * a % q;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+uint32_t h_shoup(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32) / q); }
+
+constexpr uint32_t kPrimes[kNP] = {998244353u, 897581057u, 880803841u, 754974721u, 645922817u};
+constexpr uint32_t kRoots[kNP] = {3u, 3u, 26u, 11u, 3u};
+
+// 2^32 / n mod q_i (undoes one Montgomery factor and the inverse transform's n)
+CrtScale crt_scale(int logn) {
+  CrtScale s;
+  for (int i = 0; i < kNP; i++) {
+    const uint64_t q = kPrimes[i];
+    const uint64_t ninv = h_pow32(h_pow32(2, (uint64_t)logn, q), q - 2, q);
+    const uint32_t x = (uint32_t)(((uint64_t)1 << 32) % q * ninv % q);
+    s.s[i] = x;
+    s.sp[i] = h_shoup(x, (uint32_t)q);
+  }
+  return s;
+}
+
+void launch_ntt(uint32_t* data, int64_t count, int logn, int plane_log, bool inv, const uint2* tw, const uint2* itw,
+                int logN, const NttConsts& C, cudaStream_t st) {
+  if (logn <= 0 || count <= 0) return;
+  const int64_t total = count << logn;
+  const int L1 = logn > kNttTileLog ? logn - kNttTileLog : 0;
+  const unsigned tiles = cdivu(total, kNttTile);
+  if (!inv) {
+    if (L1) { k_ntt_cols<false><<<(unsigned)(count << L1), kNttThreads, 0, st>>>(data, logn, plane_log, L1, tw, logN, C); note_launch(); }
+    k_ntt_local<false><<<tiles, kNttThreads, 0, st>>>(data, total, logn, plane_log, L1, tw, logN, C);
+    note_launch();
+  } else {
+    k_ntt_local<true><<<tiles, kNttThreads, 0, st>>>(data, total, logn, plane_log, L1, itw, logN, C);
+    note_launch();
+    if (L1) { k_ntt_cols<true><<<(unsigned)(count << L1), kNttThreads, 0, st>>>(data, logn, plane_log, L1, itw, logN, C); note_launch(); }
+  }
+}
+
+// Workspace of one fast solve, carved in order.
+struct FastWs {
+  int64_t Tp = 0;
+  int Lt = 0, R = 0;
+  std::vector<uint64_t*> coef;     // levels 7 .. 7 + Lt, T' words each
+  std::vector<uint32_t*> spec;     // levels 8 .. 7 + Lt, kNP * 2T' words each
+  uint64_t *X0 = nullptr, *X1 = nullptr;   // R x T'
+  uint32_t *XH = nullptr, *Y = nullptr;    // R kNP T', 2 R kNP T'
+  uint64_t *f = nullptr, *rd = nullptr, *g = nullptr, *ps = nullptr, *e = nullptr;
+  uint32_t *A = nullptr, *B = nullptr, *Z = nullptr;   // kNP * 2T' each
+};
+
+FastWs carve_fast(Carver& cv, int64_t T, int R) {
+  FastWs w;
+  w.Lt = 0;
+  while ((int64_t)kLeaf << w.Lt < T) w.Lt++;
+  w.Tp = (int64_t)kLeaf << w.Lt;
+  w.R = R;
+  const int64_t Tp = w.Tp;
+  for (int l = 0; l <= w.Lt; l++) w.coef.push_back(cv.take<uint64_t>(Tp));
+  for (int l = 1; l <= w.Lt; l++) w.spec.push_back(cv.take<uint32_t>((size_t)kNP * 2 * Tp));
+  w.X0 = cv.take<uint64_t>((size_t)R * Tp);
+  w.X1 = cv.take<uint64_t>((size_t)R * Tp);
+  w.XH = cv.take<uint32_t>((size_t)R * kNP * Tp);
+  w.Y = cv.take<uint32_t>((size_t)2 * R * kNP * Tp);
+  w.f = cv.take<uint64_t>(Tp + 1);
+  w.rd = cv.take<uint64_t>(Tp);
+  w.g = cv.take<uint64_t>(2 * Tp);
+  w.ps = cv.take<uint64_t>(Tp);
+  w.e = cv.take<uint64_t>(Tp);
+  w.A = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
+  w.B = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
+  w.Z = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
+  return w;
+}
+
+struct FastRun {
+  zr_ctx* ctx;
+  const NttConsts& C;
+  const Mod& M;
+  const uint2 *tw, *itw;
+  int logN;
+  cudaStream_t st;
+  // out[t] = +-(a * b mod (z^N - 1))[lo + t], t < cnt; N = 2^logn
+  void cyc(const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb, int logn, int64_t lo, int64_t cnt, bool neg,
+           uint32_t* A, uint32_t* B, uint32_t* Z, uint64_t* out) {
+    const int64_t all = (int64_t)kNP << logn;
+    k_cyc_load<<<cdivu(all, 256), 256, 0, st>>>(a, na, logn, C, A);
+    k_cyc_load<<<cdivu(all, 256), 256, 0, st>>>(b, nb, logn, C, B);
+    note_launches(2);
+    launch_ntt(A, kNP, logn, logn, false, tw, itw, logN, C, st);
+    launch_ntt(B, kNP, logn, logn, false, tw, itw, logN, C, st);
+    k_cyc_mul<<<cdivu(all, 256), 256, 0, st>>>(A, B, logn, C, Z);
+    note_launch();
+    launch_ntt(Z, kNP, logn, logn, true, tw, itw, logN, C, st);
+    k_cyc_crt<<<cdivu(cnt, 256), 256, 0, st>>>(Z, logn, lo, cnt, neg ? 1 : 0, C, crt_scale(logn), M, out);
+    note_launch();
+  }
+};
+
+}  // namespace
+
+// ---- entry points used by the batch ------------------------------------------------
+
+size_t fast_ws_need(int64_t T, int R) {
+  Carver m0(nullptr);
+  carve_fast(m0, T, R);
+  return m0.off + 256;
+}
+
+int fast_ntt_log(int64_t T) {
+  int Lt = 0;
+  while ((int64_t)kLeaf << Lt < T) Lt++;
+  return kLeafLog + Lt + 1;           // the final power-sum product has size 2T'
+}
+
+NttConsts make_ntt_consts(uint64_t p) {
+  NttConsts C;
+  memset(&C, 0, sizeof(C));
+  typedef unsigned __int128 u128;
+  for (int i = 0; i < kNP; i++) {
+    const uint32_t q = kPrimes[i];
+    C.q[i] = q;
+    C.g[i] = kRoots[i];
+    uint32_t inv = 1;   // q^-1 mod 2^32 by Newton's iteration on 2-adic digits
+    for (int it = 0; it < 5; it++) inv *= 2u - q * inv;
+    C.qinv[i] = inv;
+    C.r32[i] = (uint32_t)((((uint64_t)1) << 32) % q);
+    C.r32p[i] = h_shoup(C.r32[i], q);
+    C.onep[i] = h_shoup(1, q);
+    for (int j = 0; j < i; j++) {
+      C.gc[i][j] = h_pow32(kPrimes[j], q - 2, q);
+      C.gcp[i][j] = h_shoup(C.gc[i][j], q);
+    }
+    u128 pre = 1;
+    for (int j = 0; j < i; j++) pre = pre * kPrimes[j] % p;
+    C.pre[i] = (uint64_t)pre;
+  }
+  return C;
+}
+
+// The tables for transforms up to 2^logN, grown on demand (context-owned).
+zr_status ensure_ntt_tables(zr_ctx* ctx, int logN, cudaStream_t st) {
+  if (ctx->ntt_logN >= logN) return ZR_OK;
+  if (logN > kNttMaxLog) return set_err(ctx, ZR_ERR_INVALID_ARG, "fast solve: transform too large");
+  if (ctx->ntt_tw) {
+    cudaStreamSynchronize(st);
+    cudaFree(ctx->ntt_tw);
+    ctx->ntt_tw = nullptr;
+    ctx->ntt_logN = 0;
+  }
+  const size_t words = (size_t)kNP << logN;
+  cudaError_t e = cudaMalloc(&ctx->ntt_tw, 2 * words * sizeof(uint2));
+  if (e != cudaSuccess) {
+    ctx->ntt_tw = nullptr;
+    return cuda_err(ctx, e, "transform tables");
+  }
+  uint2* tw = reinterpret_cast<uint2*>(ctx->ntt_tw);
+  k_ntt_tables<<<cdivu((int64_t)words, 256), 256, 0, st>>>(logN, ctx->ntt, tw, tw + words);
+  note_launch();
+  ctx->ntt_logN = logN;
+  return cuda_err(ctx, cudaGetLastError(), "transform tables");
+}
+
+// One system (or step entry) solved by the fast path: writes the numerators
+// <q_j, b_s> to part[s T + j] (s < S) and M'(v_j) to den[j], the layout the
+// finish kernels read for a single k-block.  v and vp (Shoup quotients of v)
+// are on the device already; ws holds fast_ws_need(T, S + 1) bytes.
+zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, const uint64_t* vp,
+                             const uint64_t* b, int64_t ldb, uint64_t* part, uint64_t* den, char* ws,
+                             cudaStream_t st) {
+  const int R = S + 1;
+  Carver cv(ws);
+  FastWs w = carve_fast(cv, T, R);
+  const int64_t Tp = w.Tp;
+  const int Lt = w.Lt;
+  const int logT = kLeafLog + Lt;
+  zr_status r = ensure_ntt_tables(ctx, logT + 1, st);
+  if (r) return r;
+  const NttConsts& C = ctx->ntt;
+  const Mod& M = ctx->M;
+  const uint2* tw = reinterpret_cast<const uint2*>(ctx->ntt_tw);
+  const uint2* itw = tw + ((size_t)kNP << ctx->ntt_logN);
+  const int logN = ctx->ntt_logN;
+  FastRun F{ctx, C, M, tw, itw, logN, st};
+
+  // tree: leaf blocks, then levels 8 .. 7 + Lt
+  k_fast_leafpoly<<<cdivu(T, kLeaf), kLeaf, 0, st>>>(v, T, M, w.coef[0]);
+  note_launch();
+  for (int l = 1; l <= Lt; l++) {
+    const int logn = kLeafLog + l;
+    uint32_t* spec = w.spec[l - 1];
+    k_tree_load<<<cdivu(kNP * 2 * Tp, 256), 256, 0, st>>>(w.coef[l - 1], T, Tp, logn, C, spec);
+    note_launch();
+    launch_ntt(spec, (kNP * 2 * Tp) >> logn, logn, logT + 1, false, tw, itw, logN, C, st);
+    k_tree_mul<<<cdivu(kNP * Tp, 256), 256, 0, st>>>(spec, Tp, logn, C, w.Z);
+    note_launch();
+    launch_ntt(w.Z, (kNP * Tp) >> logn, logn, logT, true, tw, itw, logN, C, st);
+    k_tree_crt<<<cdivu(Tp, 256), 256, 0, st>>>(w.Z, T, Tp, logn, C, crt_scale(logn), M, w.coef[l]);
+    note_launch();
+  }
+  const uint64_t* m = w.coef[Lt];   // M without its leading 1
+
+  // power sums: g = 1 / rev(M) mod z^T by Newton's iteration, ps = rev(M') g
+  k_rev_poly<<<cdivu(T + 1, 256), 256, 0, st>>>(m, T, M, w.f, w.rd, w.g);
+  note_launch();
+  for (int64_t k = 1; k < T; k *= 2) {
+    const int logk2 = ilog2(2 * k);
+    const int64_t fn = std::min<int64_t>(2 * k, T + 1);
+    // e = f g: its coefficients k .. 2k-1 (the low ones are 1, 0, ..)
+    F.cyc(w.f, fn, w.g, k, logk2, k, k, false, w.A, w.B, w.Z, w.e);
+    // g_{k..2k} = -(g e_hi mod z^k)
+    F.cyc(w.g, k, w.e, k, logk2, 0, k, true, w.A, w.B, w.Z, w.g + k);
+  }
+  F.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
+
+  // descent from the root (node size T') to the leaf blocks
+  k_stage_rhs<<<cdivu((int64_t)R * T, 256), 256, 0, st>>>(b, ldb, S, w.ps, T, Tp, w.X0);
+  note_launch();
+  uint64_t* X = w.X0;
+  uint64_t* Xn = w.X1;
+  for (int l = Lt; l >= 1; l--) {
+    const int logn = kLeafLog + l;
+    const int64_t all = (int64_t)R * kNP * Tp;
+    k_desc_load<<<cdivu(all, 256), 256, 0, st>>>(X, R, T, Tp, logn, C, w.XH);
+    note_launch();
+    launch_ntt(w.XH, all >> logn, logn, logT, false, tw, itw, logN, C, st);
+    k_desc_mul<<<cdivu(all, 256), 256, 0, st>>>(w.XH, w.spec[l - 1], R, Tp, logn, C, w.Y);
+    note_launch();
+    launch_ntt(w.Y, (2 * all) >> logn, logn, logT, true, tw, itw, logN, C, st);
+    k_desc_crt<<<cdivu((int64_t)R * Tp, 256), 256, 0, st>>>(w.Y, R, T, Tp, logn, C, crt_scale(logn), M, Xn);
+    note_launch();
+    std::swap(X, Xn);
+  }
+  // leaves
+  const size_t smem = sizeof(uint64_t) * (size_t)kLeaf * (1 + R);
+  static DeviceOnce attr;
+  attr.run([] {
+    cudaFuncSetAttribute(k_fast_leafval, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(uint64_t) * kLeaf * (1 + 65)));
+  });
+  k_fast_leafval<<<cdivu(T, kLeaf), kLeaf, smem, st>>>(w.coef[0], X, R, T, Tp, v, vp, M, part, T, den);
+  note_launch();
+  return cuda_err(ctx, cudaGetLastError(), "fast solve");
+}
+
+}  // namespace zr

@@ -9,10 +9,11 @@
 
 #include "zr.h"
 #include "zr_kernels.cuh"
+#include "zr_ntt.cuh"
 
 // Phases of a step timed by the optional profiler (CUDA events recorded on
 // the call's stream around each phase).
-enum zr_phase { PH_ANCHOR = 0, PH_MASTER, PH_EXPAND, PH_CARRY, PH_SOLVE, PH_NEWTON, PH_COMPACT, PH_EVAL, PH_N };
+enum zr_phase { PH_ANCHOR = 0, PH_MASTER, PH_EXPAND, PH_CARRY, PH_SOLVE, PH_NEWTON, PH_COMPACT, PH_EVAL, PH_FAST, PH_N };
 
 struct zr_prof {
   bool on = false;
@@ -56,6 +57,13 @@ struct zr_ctx {
   // there, overlapping the tree and the solve), with its fork/join events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the O(T log^2 T) solve: constants of the transform primes, the twiddle
+  // tables (grown on demand) and the choice between the two solve methods
+  zr::NttConsts ntt;
+  void* ntt_tw = nullptr;
+  int ntt_logN = 0;
+  int solve_method = 0;            // 0: by size, 1: quadratic, 2: fast where supported
+  int64_t fast_min_T = 0;          // size from which method 0 takes the fast path (0: built-in default)
   std::string err;
   std::mutex mu;                // guards err for the serve thread
 };
@@ -143,6 +151,15 @@ zr_status check_step_args(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, cons
 BatchItem step_item(const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S, const uint64_t* samples,
                     const uint64_t* probes, int64_t ldb, int32_t offset, uint8_t* out_exps, uint64_t* out_coef,
                     int64_t out_cap, int64_t* d_count);
+
+// the O(T log^2 T) solve (zr_fast.cu)
+constexpr int64_t kFastMaxT = 1ll << 21;   // largest T of the fast path (transforms up to 2^22)
+zr::NttConsts make_ntt_consts(uint64_t p);
+size_t fast_ws_need(int64_t T, int R);
+zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, const uint64_t* vp, const uint64_t* b,
+                             int64_t ldb, uint64_t* part, uint64_t* den, char* ws, cudaStream_t st);
+// whether a system of T unknowns takes the fast path in this context
+bool use_fast_solve(const zr_ctx* ctx, int64_t T);
 
 // evaluator (zr_eval.cu)
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);

@@ -75,7 +75,7 @@ def main():
     torch.cuda.synchronize()
     got = oc[:n].cpu().numpy().view(np.uint64)
     ok = n == wl.exps.shape[0] and np.array_equal(got, wl.coef)
-    phases = {ph: ctx.profile_query(ph)[0] / args.steps for ph in zr.Context.PHASES[:7]}
+    phases = {ph: ctx.profile_query(ph)[0] / args.steps for ph in zr.Context.PHASES[:7] + ("fast",)}
     line = {"workload": wl.name, "steps": args.steps, "plan": ctx.step_plan(wl.T, wl.S), "phase_ms": phases,
             "probe_ms": probe_ms, "check": "generator truth" if ok else "MISMATCH"}
     if not ok:

@@ -107,6 +107,7 @@ SIGNATURES = {
     "zr_profile_query": (_ST, [_V, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "zr_autotune_step": (_ST, [_V, _I64, _I32, _I32, _V]),
     "zr_step_plan": (_ST, [_V, _I64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "zr_solve_method": (_ST, [_V, _I32, _I64]),
     "zr_vandermonde_solve_batched": (_ST, [_V, _I32, _P, _V]),
     "zr_vandermonde_solve_plain": (_ST, [_V, _I32, _P, _V]),
     "zr_newton_batched": (_ST, [_V, _I64, _I32, _P, _P, _I64, _P, _V]),
@@ -237,7 +238,12 @@ class Context:
     def workspace_bytes(self) -> int:
         return int(self.L.zr_workspace_bytes(self._h))
 
-    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval")
+    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval", "fast")
+    SOLVE_AUTO, SOLVE_QUADRATIC, SOLVE_FAST = 0, 1, 2
+
+    def solve_method(self, method, crossover=0):
+        """zr_solve_method: 0 by size (fast from `crossover` terms), 1 always O(T^2), 2 fast where supported."""
+        self.check(self.L.zr_solve_method(self._h, method, crossover), "zr_solve_method")
 
     def profile(self, on: bool = True):
         self.check(self.L.zr_profile_enable(self._h, 1 if on else 0), "zr_profile_enable")

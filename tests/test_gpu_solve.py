@@ -21,6 +21,9 @@ def ctx():
     ge.build()
     assert torch.cuda.is_available()
     c = zr.Context(P63)
+    # these tests cover the O(T^2) kernels (the paper's method) at every size;
+    # tests/test_gpu_fast.py covers the O(T log^2 T) path
+    c.solve_method(c.SOLVE_QUADRATIC)
     yield c
     c.close()
 
