@@ -735,7 +735,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
     }
   }
   cudaEvent_t e5 = mark();
-  if (mode == 0 && nleaf) {
+  if (mode == 0 && nroots) {
     { k_b_scan<<<n, kScanB, 0, st>>>(dD); note_launch(); }
     {
       k_b_scatter<<<(unsigned)pre[o_nblk + n], kCompB, 0, st>>>(dD, dpre + o_nblk, n);
