@@ -491,7 +491,9 @@ def run_zr(args):
 
     def plain_step():
         ctx.anchor_values(T, nv, ske, k, y, 0, v)
+        ctx.solve_method(ctx.SOLVE_QUADRATIC)      # the paper's O(T^2) solve, one system per launch sequence
         ctx.vandermonde_solve(systems, plain=True)
+        ctx.solve_method(ctx.SOLVE_AUTO)
         ctx.newton_batched(T, S, cs, cpl, T, gpl)
 
     plain_reps = max(1, min(args.steps, 5))
@@ -612,6 +614,7 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
 
     wl = W.large_step_2p20()
     T, S, nv, k = wl.T, wl.S, wl.nv, wl.k
+    ctx.solve_method(ctx.SOLVE_AUTO)
     stream = torch.cuda.current_stream()
     fe, fc = torch.from_numpy(wl.exps).to(dev), d64(wl.coef)
     f = ctx.poly(nv, wl.exps.shape[0], fe, fc)
@@ -647,13 +650,30 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
     torch.cuda.synchronize()
     clk = clocks.stop()
     times = [a.elapsed_time(bb) for a, bb in evs]
-    solve_ms, solve_n = ctx.profile_query("solve")
+    fast_ms, fast_n = ctx.profile_query("fast")
     phases = {ph: ctx.profile_query(ph)[0] / max(steps, 1) for ph in ctx.PHASES[:7] + ("fast",)}
     ctx.profile(False)
     ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
         np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
-    del oe, oc
     ms = sum(times) / len(times)
+    # the same step with the paper's O(T^2) solve (k_solve): one warm-up, one timed
+    ctx.solve_method(ctx.SOLVE_QUADRATIC)
+    flush.zero_()
+    ctx.zippel_step(skel, k, y, S, cs, b, T, 0, oe, oc, cap)
+    ctx.profile(True)
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nq = ctx.zippel_step(skel, k, y, S, cs, b, T, 0, oe, oc, cap)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    quad_ms = e0.elapsed_time(e1)
+    solve_ms, solve_n = ctx.profile_query("solve")
+    qphases = {ph: ctx.profile_query(ph)[0] for ph in ctx.PHASES[:7]}
+    ctx.profile(False)
+    ctx.solve_method(ctx.SOLVE_AUTO)
+    qok = nq == wl.exps.shape[0] and np.array_equal(oc[:nq].cpu().numpy().view(np.uint64), wl.coef)
+    del oe, oc
     # the plain form: one single-right-hand-side system per launch sequence;
     # its S systems are identical in cost, so one is timed and scaled by S
     v = torch.empty(T, dtype=torch.int64, device=dev)
@@ -662,7 +682,9 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
     flush.zero_()
     torch.cuda.synchronize()
     e0.record(stream)
+    ctx.solve_method(ctx.SOLVE_QUADRATIC)
     ctx.vandermonde_solve([dict(T=T, S=1, v=v, b=b[0], ldb=T, c=c1, ldc=T)], plain=True)
+    ctx.solve_method(ctx.SOLVE_AUTO)
     e1.record(stream)
     torch.cuda.synchronize()
     plain_one_ms = e0.elapsed_time(e1)
@@ -680,11 +702,19 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
     W_ = (S + 2.5) * T * T
     return {
         "workload": wl.name, "T": T, "S": S, "nv": nv, "steps": steps, "warmup": warmup,
-        "ms_per_step": ms, "terms_per_s": T / (ms / 1e3), "mulmod_per_s": W_ / (ms / 1e3),
-        "roofline": solve_roofline(T, S, solve_ms / max(solve_n, 1) / 1e3, peaks, wl.name),
+        "solve": "O(T log^2 T) (subproduct tree, transforms over five 30-bit primes)",
+        "ms_per_step": ms, "terms_per_s": T / (ms / 1e3),
+        "fast_solve_ms": fast_ms / max(fast_n, 1),
         "phase_ms": phases,
+        "quadratic_form": {"ms_per_step": quad_ms, "terms_per_s": T / (quad_ms / 1e3),
+                           "mulmod_per_s": W_ / (quad_ms / 1e3), "fast_speedup": quad_ms / ms,
+                           "what": "the same step with the O(T^2) solve of Sec. 2.2 (k_solve); one warm-up, one timed",
+                           "roofline": solve_roofline(T, S, solve_ms / max(solve_n, 1) / 1e3, peaks, wl.name),
+                           "phase_ms": qphases,
+                           "check": "generator truth" if qok else "MISMATCH"},
         "plain_form": {"ms_per_step": plain_one_ms * S, "terms_per_s": T / (plain_one_ms * S / 1e3),
                        "batched_speedup": plain_one_ms * S / ms,
+                       "quadratic_batched_speedup": plain_one_ms * S / quad_ms,
                        "what": f"{S} single-RHS systems, one launch sequence each; one timed "
                                f"({plain_one_ms:.0f} ms) and scaled by {S} (identical cost)",
                        "check": "generator truth (64 sampled roots)" if plain_ok else "MISMATCH"},
@@ -692,7 +722,7 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
                       "frac_of_measured_mac_peak": S * T * T / (probe_ms * 1e-3) / peaks["mac_per_s"]},
         "clocks": clk,
         "l2": "flushed before each timed step (256 MB write); the step's inputs exceed L2",
-        "check": "generator truth" if ok else "MISMATCH",
+        "check": "generator truth" if (ok and qok and plain_ok) else "MISMATCH",
     }
 
 

@@ -402,10 +402,11 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
 
 extern "C" const char* zr_last_error(const zr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
-// Size from which the automatic choice takes the fast solve (measured on
-// GB300: below it the quadratic kernel's single pass beats the fast path's
-// chain of transform launches).
-static constexpr int64_t kFastDefaultMinT = 4096;
+// Size from which the automatic choice takes the fast solve.  Measured on
+// GB300 with 21 right-hand sides: 2.15 against 3.22 ms at T = 10^4, 5.1
+// against 3.2 ms at T = 16384 (the fast path's chain of transform launches
+// costs about 1 ms at any size).
+static constexpr int64_t kFastDefaultMinT = 12000;
 
 namespace zr {
 bool use_fast_solve(const zr_ctx* ctx, int64_t T) {
