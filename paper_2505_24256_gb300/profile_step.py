@@ -2,6 +2,7 @@
 
     python -m paper_2505_24256_gb300.profile_step [--workload batched|large]
         [--steps N] [--plan TILE,NB] [--probe-sets M] [--T N]
+        [--method auto|quadratic|fast]
 
 The probes are generated M times (default 1) by the GPU evaluator, each
 timed with CUDA events; then N steps run back to back (the first is a
@@ -9,6 +10,8 @@ warm-up when N > 1) with the given solve plan (else the planner's model),
 and the per-phase device times of the context profiler are printed.  Under
 ncu, select the solve kernel with -k regex:k_solve (or the evaluator's
 product with -k regex:k_eval_ring) and skip the warm-up launch with -s 1.
+--method picks the solve: the library's choice by size, always the O(T^2)
+kernels, or the O(T log^2 T) path (phase "fast").
 """
 from __future__ import annotations
 
@@ -30,6 +33,7 @@ def main():
     ap.add_argument("--probe-sets", type=int, default=1, help="probe generations, each timed")
     ap.add_argument("--T", type=int, default=0,
                     help="the large workload's recipe at this many terms (a smaller case for counters)")
+    ap.add_argument("--method", default="auto", choices=["auto", "quadratic", "fast"])
     args = ap.parse_args()
     if args.plan:
         os.environ["ZR_SOLVE_PLAN"] = args.plan
@@ -51,6 +55,7 @@ def main():
         return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(dev)
 
     ctx = zr.Context(wl.p)
+    ctx.solve_method({"auto": 0, "quadratic": 1, "fast": 2}[args.method])
     fe, fc = torch.from_numpy(wl.exps).to(dev), d64(wl.coef)     # kept alive: zr_poly holds raw pointers
     f = ctx.poly(wl.nv, wl.exps.shape[0], fe, fc)
     y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
@@ -76,7 +81,8 @@ def main():
     got = oc[:n].cpu().numpy().view(np.uint64)
     ok = n == wl.exps.shape[0] and np.array_equal(got, wl.coef)
     phases = {ph: ctx.profile_query(ph)[0] / args.steps for ph in zr.Context.PHASES[:7] + ("fast",)}
-    line = {"workload": wl.name, "steps": args.steps, "plan": ctx.step_plan(wl.T, wl.S), "phase_ms": phases,
+    line = {"workload": wl.name, "steps": args.steps, "method": args.method, "plan": ctx.step_plan(wl.T, wl.S),
+            "phase_ms": phases,
             "probe_ms": probe_ms, "check": "generator truth" if ok else "MISMATCH"}
     if not ok:
         line["terms"] = [int(n), int(wl.exps.shape[0])]
