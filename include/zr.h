@@ -135,10 +135,7 @@ zr_status zr_measure_peaks(zr_ctx* ctx, zr_peaks* out, void* stream);
  * count): times the `budget` best-ranked candidate plans on synthetic data of
  * shape (T, S) and records the fastest in the context; later calls with that
  * shape use it.  Plans change the schedule only, never the values.
- * zr_step_plan reports the plan a call of shape (T, S) would use: the k-block
- * count and, for the producer/consumer kernel, the right-hand sides per
- * consumer thread, or, negated, the column-group width of the kernel in
- * which every warp runs its own chain. */
+ * zr_step_plan reports the plan a call of shape (T, S) would use. */
 zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t budget, void* stream);
 zr_status zr_step_plan(zr_ctx* ctx, int64_t T, int32_t S, int32_t* s_tile, int32_t* nblocks);
 

@@ -181,8 +181,7 @@ static int occupancy_cached(int tile, int groups) {
 }
 
 // A forced plan: the context's tuned plan table, else ZR_SOLVE_PLAN="tile,NB"
-// in the environment (a tuning override; a negative tile -w selects the
-// per-warp-chain kernel with column groups of width w), else the model below.
+// in the environment (a tuning override), else the model below.
 static bool forced_plan(const zr_ctx* ctx, int64_t T, int S, StepDims& D) {
   if (ctx) {
     for (const auto& e : ctx->plans)
@@ -193,18 +192,15 @@ static bool forced_plan(const zr_ctx* ctx, int64_t T, int S, StepDims& D) {
   }
   const char* env = getenv("ZR_SOLVE_PLAN");
   int tile = 0, nb = 0;
-  if (!env || sscanf(env, "%d,%d", &tile, &nb) != 2 || tile == 0 || nb <= 0) return false;
-  const int kind = tile < 0 ? 1 : 0;
-  if (kind) tile = -tile;
-  int tiles[32];
-  const int nt = kind ? solve2_widths(tiles, 32) : solve_tiles(tiles, 32);
+  if (!env || sscanf(env, "%d,%d", &tile, &nb) != 2 || tile <= 0 || nb <= 0) return false;
+  int tiles[16];
+  const int nt = solve_tiles(tiles, 16);
   bool ok = false;
   for (int i = 0; i < nt; i++) ok |= tiles[i] == tile;
   if (!ok) return false;
   D.T = T;
   D.S = S;
   D.s_tile = tile;
-  D.kind = kind;
   int64_t BK = (T + nb - 1) / nb;
   BK = ((BK + 31) / 32) * 32;
   D.BK = BK < 32 ? 32 : BK;
@@ -248,59 +244,6 @@ double plan_cost(const zr_ctx* ctx, const StepDims& D) {
   return cost;
 }
 
-// The per-warp-chain kernel (k_solve2): a CTA of W warps owns 32 W roots of
-// one column group of width cg; every group reruns the chain q (16 units per
-// root and k), group 0 also u (16); each column costs 8 units per root and k.
-// Waves as above, a wave's warps per SM reaching full speed from 8 (each
-// warp has cg independent accumulators).
-static int occupancy2_cached(int cg) {
-  static DeviceValue cache[32];
-  if (cg < 1 || cg >= 32) return 1;
-  return cache[cg].get([&] {
-    const int n = solve2_occupancy(cg);
-    return n > 0 ? n : 1;
-  });
-}
-
-double plan_cost2(const zr_ctx* ctx, const StepDims& D) {
-  const int64_t sms = ctx && ctx->sms ? ctx->sms : 152;
-  const int cg = D.s_tile;
-  if (cg < 1 || solve2_occupancy(cg) <= 0) return 1e300;
-  const int groups = (D.S + cg - 1) / cg;
-  const int rt = solve2_roots_per_item(cg), W = rt / 32;
-  const int64_t rows = (D.T + rt - 1) / rt;
-  const int per_sm = occupancy2_cached(cg);
-  const int64_t slots = sms * per_sm;
-  const double cost_k = 8.0 * cg + 16.0 + 16.0 / groups;
-  const int64_t items = rows * D.NB * groups;
-  double cost = 0;
-  for (int64_t left = items; left > 0; left -= slots) {
-    const int64_t in_wave = left < slots ? left : slots;
-    const int64_t n = (in_wave + sms - 1) / sms;
-    const double warps = (double)n * W;
-    const double eff = warps >= 8 ? 1.0 : warps / 8.0;
-    cost += (double)D.BK * rt * cost_k * (double)n / eff;
-  }
-  cost += 1300.0 * (double)items;
-  cost += (double)D.NB * D.S * D.T;
-  if (D.NB > 1) {
-    const double through = 20.5 * (double)(D.NB - 1) * D.BK * D.T / (double)sms;
-    const double serial = 6960.0 * (double)D.BK;
-    cost += through > serial ? through : serial;
-  }
-  return cost;
-}
-
-// Which solve kernels the planner's model may pick: ZR_SOLVE_KERNEL=ring,
-// =tiled or =both (a tuning override).  By default the model plans the ring
-// kernel; the autotuner times both kernels' plans.
-static int kernel_choice() {
-  const char* env = getenv("ZR_SOLVE_KERNEL");
-  if (env && !strcmp(env, "tiled")) return 2;
-  if (env && !strcmp(env, "both")) return 3;
-  return 1;
-}
-
 StepDims plan_step(const zr_ctx* ctx, int64_t T, int S) {
   StepDims best;
   if (forced_plan(ctx, T, S, best)) return best;
@@ -310,9 +253,8 @@ StepDims plan_step(const zr_ctx* ctx, int64_t T, int S) {
   best.BK = ((T + 31) / 32) * 32;
   best.s_tile = 16;
   double best_cost = -1;
-  const int allow = kernel_choice();
   int tiles[16];
-  const int nt = (allow & 1) ? solve_tiles(tiles, 16) : 0;
+  const int nt = solve_tiles(tiles, 16);
   for (int ti = 0; ti < nt; ti++) {
     const int tile = tiles[ti];
     const int groups = (S + tile - 1) / tile;
@@ -330,31 +272,6 @@ StepDims plan_step(const zr_ctx* ctx, int64_t T, int S) {
       D.BK = BK;
       D.s_tile = tile;
       const double cost = plan_cost(ctx, D);
-      if (best_cost < 0 || cost < best_cost * 0.999) {
-        best_cost = cost;
-        best = D;
-      }
-    }
-  }
-  int widths[32];
-  const int nw = (allow & 2) ? solve2_widths(widths, 32) : 0;
-  for (int wi = 0; wi < nw; wi++) {
-    const int cg = widths[wi];
-    if ((S + cg - 1) / cg > 8) continue;
-    for (int NBw = 1; NBw <= 64; NBw++) {
-      int64_t BK = (T + NBw - 1) / NBw;
-      BK = ((BK + 31) / 32) * 32;
-      if (BK < 32) BK = 32;
-      const int NB = (int)((T + BK - 1) / BK);
-      if (NB != NBw) continue;
-      StepDims D;
-      D.T = T;
-      D.S = S;
-      D.NB = NB;
-      D.BK = BK;
-      D.s_tile = cg;
-      D.kind = 1;
-      const double cost = plan_cost2(ctx, D);
       if (best_cost < 0 || cost < best_cost * 0.999) {
         best_cost = cost;
         best = D;

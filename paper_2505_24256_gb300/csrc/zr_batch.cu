@@ -419,8 +419,6 @@ struct Prepared {
   size_t ws_bytes = 0, table_bytes = 0, fast_bytes = 0;
 };
 
-constexpr int kSolve2Key = 1000;   // work-list keys of the per-warp-chain kernel: kSolve2Key + width
-
 static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& P) {
   P.mode = items[0].mode;
   P.plan.resize(n);
@@ -474,22 +472,18 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
   }
   for (int i = 0; i < n; i++) {
     if (items[i].T == 0 || P.fast[i]) continue;
-    // one work list per solve kernel instance: (tile, consumer groups) of the
-    // ring kernel, or the column-group width of the per-warp-chain kernel
-    // (keys from kSolve2Key up), whose items also carry the column group
+    // one work list per (tile, consumer groups): the solve kernel instance
     const int tile = P.plan[i].s_tile, groups = (items[i].solve_S() + tile - 1) / tile;
-    const bool tiled = P.plan[i].kind == 1;
-    const int key = tiled ? kSolve2Key + tile : tile * 16 + groups;
+    const int key = tile * 16 + groups;
     int w = (int)(std::find(P.tiles_used.begin(), P.tiles_used.end(), key) - P.tiles_used.begin());
     if (w == (int)P.tiles_used.size()) {
       P.tiles_used.push_back(key);
       P.work.emplace_back();
     }
-    const int rt = tiled ? solve2_roots_per_item(tile) : solve_roots_per_item();
+    const int rt = solve_roots_per_item();
     const int rows = (int)((items[i].T + rt - 1) / rt);
     for (int kb = 0; kb < P.plan[i].NB; kb++)
-      for (int r = 0; r < rows; r++)
-        for (int g = 0; g < (tiled ? groups : 1); g++) P.work[w].push_back(make_int4(i, r, kb, g));
+      for (int r = 0; r < rows; r++) P.work[w].push_back(make_int4(i, r, kb, 0));
   }
   const std::vector<StepDims>& plan = P.plan;
   for (auto& wl : P.work)
@@ -708,14 +702,10 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   // a4 + a5
   if (ncarry) launch_b_carry(dD, dpre + o_carry, n, ncarry, M, st);
   cudaEvent_t e3 = mark();
-  for (size_t w = 0; w < work.size(); w++) {
-    const int sms = ctx->solve_persistent ? (ctx->sms ? ctx->sms : 152) : 0;
-    const bool ok = tiles_used[w] >= kSolve2Key
-                        ? launch_b_solve2(tiles_used[w] - kSolve2Key, dD, dwork[w], (int)work[w].size(), sms, M, st)
-                        : launch_b_solve(tiles_used[w] / 16, tiles_used[w] % 16, dD, dwork[w], (int)work[w].size(),
-                                         sms, M, st);
-    if (!ok) return set_err(ctx, ZR_ERR_INVALID_ARG, "no solve kernel for this launch plan");
-  }
+  for (size_t w = 0; w < work.size(); w++)
+    if (!launch_b_solve(tiles_used[w] / 16, tiles_used[w] % 16, dD, dwork[w], (int)work[w].size(),
+                        ctx->solve_persistent ? (ctx->sms ? ctx->sms : 152) : 0, M, st))
+      return set_err(ctx, ZR_ERR_INVALID_ARG, "no solve kernel for this launch plan");
   cudaEvent_t e4 = mark();
   // entries of the O(T log^2 T) solve: numerators and M'(v_j) into the
   // single-block partials the finish reads

@@ -97,8 +97,7 @@ zr_status cuda_err(zr_ctx* ctx, cudaError_t e, const char* where);
 zr_status ensure_ws(zr_ctx* ctx, size_t need, cudaStream_t st);
 zr_status status_from_flags(zr_ctx* ctx, uint32_t flags);
 StepDims plan_step(const zr_ctx* ctx, int64_t T, int S);
-double plan_cost(const zr_ctx* ctx, const StepDims& D);    // the ring kernel's plans
-double plan_cost2(const zr_ctx* ctx, const StepDims& D);   // the per-warp-chain kernel's plans
+double plan_cost(const zr_ctx* ctx, const StepDims& D);
 uint64_t hash_slots(int64_t T);
 
 // Workspace of one step or system (carved in the context workspace).

@@ -72,7 +72,6 @@ struct StepDims {
   int32_t NB;      // k-blocks
   int64_t BK;      // k-block length (the top block may be shorter)
   int32_t s_tile;  // right-hand sides per consumer thread of the solve
-  int32_t kind = 0;  // 0: producer/consumer ring kernel (k_solve), 1: per-warp chains (k_solve2)
 };
 
 // One step (mode 0: a Zippel step whose nodes are the anchor values of a
@@ -113,12 +112,6 @@ int solve_blocks_per_sm(int s_tile, int groups);
 bool solve_instance_exists(int s_tile, int groups);
 int solve_roots_per_item();   // roots of one work item
 int solve_max_groups();       // consumer groups per CTA: S <= groups * s_tile
-// the per-warp-chain solve (zr_solve2.cu): column-group widths it is built
-// for, resident CTAs per SM, roots per work item, launch (false: no instance)
-int solve2_widths(int* out, int cap);
-int solve2_occupancy(int cg);
-int solve2_roots_per_item(int cg);
-bool launch_b_solve2(int cg, const BDesc* Ds, const int4* items, int nitems, int sms, const Mod& M, cudaStream_t st);
 // Newton on shared nodes: W (S x S) from the nodes, then vals (npts x ld) ->
 // monomial coefficients coef (npts x ld) through W
 void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* W, uint32_t* status, cudaStream_t st);

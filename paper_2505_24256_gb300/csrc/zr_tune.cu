@@ -57,35 +57,8 @@ extern "C" zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t
       cand.push_back({plan_cost(ctx, D), D});
     }
   }
-  // the per-warp-chain kernel's plans, ranked by their own model: the best
-  // half of the budget from each kernel (the two models' units differ)
-  std::vector<std::pair<double, StepDims>> cand2;
-  int widths[32];
-  const int nw = solve2_widths(widths, 32);
-  for (int wi = 0; wi < nw; wi++) {
-    if ((S + widths[wi] - 1) / widths[wi] > 8) continue;
-    for (int nb : nbs) {
-      if (nb > 1 && T / nb < 64) continue;
-      StepDims D;
-      D.T = T;
-      D.S = S;
-      D.s_tile = widths[wi];
-      D.kind = 1;
-      int64_t BK = (T + nb - 1) / nb;
-      BK = ((BK + 31) / 32) * 32;
-      D.BK = BK < 32 ? 32 : BK;
-      D.NB = (int)((T + D.BK - 1) / D.BK);
-      cand2.push_back({plan_cost2(ctx, D), D});
-    }
-  }
-  auto by_cost = [](const auto& a, const auto& b) { return a.first < b.first; };
-  std::sort(cand.begin(), cand.end(), by_cost);
-  std::sort(cand2.begin(), cand2.end(), by_cost);
-  const int half = (budget + 1) / 2;
-  if ((int)cand.size() > budget - std::min(half, (int)cand2.size()))
-    cand.resize(budget - std::min(half, (int)cand2.size()));
-  if ((int)cand2.size() > budget - (int)cand.size()) cand2.resize(budget - (int)cand.size());
-  cand.insert(cand.end(), cand2.begin(), cand2.end());
+  std::sort(cand.begin(), cand.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  if ((int)cand.size() > budget) cand.resize(budget);
   // synthetic system of this shape in its own buffers (nodes, right-hand sides, output)
   uint64_t *v = nullptr, *b = nullptr, *cc = nullptr;
   cudaError_t e = cudaMalloc(&v, 8 * (size_t)T);
@@ -119,9 +92,6 @@ extern "C" zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t
   double best_ms = -1;
   StepDims best = cand.empty() ? plan_step(ctx, T, S) : cand[0].second;
   zr_status r = ZR_OK;
-  // the plans are those of the O(T^2) solve: tune it whatever the size
-  const int method = ctx->solve_method;
-  ctx->solve_method = 1;
   for (auto& c : cand) {
     ctx->plans = saved;
     ctx->plans.push_back({T, S, c.second});
@@ -144,7 +114,6 @@ extern "C" zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t
     }
   }
   ctx->plans = saved;
-  ctx->solve_method = method;
   cudaStreamSynchronize(st);
   cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);   // synthetic nodes may collide: not an error here
   cudaFree(v);
@@ -169,8 +138,7 @@ extern "C" zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t
 extern "C" zr_status zr_step_plan(zr_ctx* ctx, int64_t T, int32_t S, int32_t* s_tile, int32_t* nblocks) {
   if (!ctx || T < 0 || S < 1) return ZR_ERR_INVALID_ARG;
   StepDims D = plan_step(ctx, T, S);
-  // the per-warp-chain kernel's widths are reported negated
-  if (s_tile) *s_tile = D.kind == 1 ? -D.s_tile : D.s_tile;
+  if (s_tile) *s_tile = D.s_tile;
   if (nblocks) *nblocks = D.NB;
   return ZR_OK;
 }

@@ -146,32 +146,3 @@ def test_eval_points(ctx, orc):
     f = ctx.poly(nv, Tf, de := d8(exps), dc := d64(coef))
     ctx.eval_points(f, npts, d64(pts), out)
     assert np.array_equal(h64(out), orc.eval_points(exps, coef, pts))
-
-
-@pytest.mark.parametrize("plan", ["-1,1", "-3,2", "-9,1", "-11,3", "-14,2", "-16,4", "-6,5"])
-def test_per_warp_chain_kernel_matches_oracle(ctx, orc, plan, monkeypatch):
-    """The O(T^2) solve with every warp running its own chain (k_solve2),
-    forced through the plan override for several column widths and k-block
-    counts: element by element against the oracle, ragged root tiles, column
-    groups with padding, both offsets."""
-    monkeypatch.setenv("ZR_SOLVE_PLAN", plan)
-    rnd = random.Random(sum(map(ord, plan)))
-    for T, S, off in [(1, 1, 0), (37, 2, 1), (700, 21, 0), (1000, 9, 1), (300, 17, 0)]:
-        v = rand_nodes(rnd, T, P63)
-        b = rand_res(rnd, (S, T), P63)
-        got = _solve(ctx, v, b, off)
-        assert np.array_equal(got, orc.tvandermonde_solve(v, b, offset=off)), (plan, T, S, off)
-
-
-def test_per_warp_chain_kernel_kblocked_large(ctx, orc, monkeypatch):
-    """T = 20000 in 6 k-blocks, S = 21 in two column groups of 11: sampled roots."""
-    monkeypatch.setenv("ZR_SOLVE_PLAN", "-11,6")
-    rnd = random.Random(77)
-    T, S = 20000, 21
-    v = rand_nodes(rnd, T, P63)
-    b = rand_res(rnd, (S, T), P63)
-    got = _solve(ctx, v, b, 0)
-    roots = sorted(rnd.sample(range(T), 40) + [0, T - 1])
-    m = orc.master_poly(v)
-    want = orc.tvandermonde_solve_roots(v, m, b, roots)
-    assert np.array_equal(got[:, roots], want)
