@@ -94,6 +94,14 @@ __global__ void __launch_bounds__(SolveCfg<CG, G>::NT, SolveCfg<CG, G>::MINB)
       const uint64_t* __restrict__ m = D.m;
       const uint64_t* __restrict__ b = D.b;
       const int64_t ldb = D.ldb;
+      // m_k of a chunk, one per lane, is loaded a chunk ahead so that the
+      // chain never waits for it
+      auto m_chunk = [&](int c) -> uint64_t {
+        const int64_t chi = khi - (int64_t)c * C::KC;
+        const int64_t clo = chi - C::KC > klo ? chi - C::KC : klo;
+        return (c < nch && lane < chi - clo) ? __ldg(m + clo + lane) : 0;
+      };
+      uint64_t mnext = m_chunk(0);
       for (int c = 0; c < nch; c++, cc++) {
         const int st = cc % C::NST;
         const uint32_t ph = (cc / C::NST) & 1;
@@ -114,7 +122,8 @@ __global__ void __launch_bounds__(SolveCfg<CG, G>::NT, SolveCfg<CG, G>::MINB)
           }
         cp_async_commit();
         // m_k of the chunk, one per lane, broadcast by shuffle along the chain
-        const uint64_t mreg = lane < len ? __ldg(m + clo + lane) : 0;
+        const uint64_t mreg = mnext;
+        mnext = m_chunk(c + 1);
         uint64_t(*qw)[C::RT] = qb[st];
         for (int kk = len - 1; kk >= 0; kk--) {
           const uint64_t mk = __shfl_sync(0xffffffffu, mreg, kk);
