@@ -107,32 +107,55 @@ __device__ __forceinline__ void butterfly(uint32_t* a, uint32_t* b, uint2 w, uin
   }
 }
 
+// A tile of kNttTile elements starting at `base` (a multiple of kNttTile):
+// the transform of an element is prime (base >> plane_log) + (pos >>
+// plane_log) mod 5 (planes are powers of two, at most or at least a tile).
+// Each thread takes kNttPer butterflies per stage, unrolled, so that their
+// twiddle loads are in flight together.
+constexpr int kNttPer = kNttTile / 2 / kNttThreads;
+
 template <bool INV>
 __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict__ data, int64_t total, int logn,
                                                            int plane_log, int s_lo, const uint2* __restrict__ tw,
                                                            int logN, NttConsts C) {
-  __shared__ uint32_t sm[kNttTile];
+  __shared__ __align__(16) uint32_t sm[kNttTile];
   const int64_t base = (int64_t)blockIdx.x * kNttTile;
   const int len = (int)((total - base) < kNttTile ? (total - base) : kNttTile);
-  for (int e = threadIdx.x; e < len; e += kNttThreads) sm[e] = data[base + e];
+  if ((len & 3) == 0) {
+    const uint4* src = reinterpret_cast<const uint4*>(data + base);
+    for (int e = threadIdx.x; e < (len >> 2); e += kNttThreads) reinterpret_cast<uint4*>(sm)[e] = src[e];
+  } else {
+    for (int e = threadIdx.x; e < len; e += kNttThreads) sm[e] = data[base + e];
+  }
   __syncthreads();
   const int half = len >> 1;
   const int nst = logn - s_lo;
+  const int pb5 = (int)((base >> plane_log) % kNP);   // the tile's first plane, modulo 5
+  const bool uniform = plane_log >= kNttTileLog;
+  const uint32_t boff = (uint32_t)(base & ((1ll << logn) - 1));   // the tile's offset within its transform
   for (int step = 0; step < nst; step++) {
     const int s = INV ? (logn - 1 - step) : (s_lo + step);
     const int lt = logn - s - 1;                      // log2 t
     const uint32_t m = 1u << s;
-    for (int b = threadIdx.x; b < half; b += kNttThreads) {
-      const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-      const int64_t g = base + pos;
-      const int prime = (int)((g >> plane_log) % kNP);
-      const uint32_t grp = (uint32_t)((g & ((1ll << logn) - 1)) >> (lt + 1));
-      const uint2 w = __ldg(&tw[((int64_t)prime << logN) + m + grp]);
-      butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], w, C.q[prime]);
+#pragma unroll
+    for (int r = 0; r < kNttPer; r++) {
+      const int b = threadIdx.x + r * kNttThreads;
+      if (b < half) {
+        const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
+        const int prime = uniform ? pb5 : (pb5 + (pos >> plane_log)) % kNP;
+        const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
+        const uint2 w = __ldg(&tw[((int64_t)prime << logN) + m + grp]);
+        butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], w, C.q[prime]);
+      }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < len; e += kNttThreads) data[base + e] = sm[e];
+  if ((len & 3) == 0) {
+    uint4* dst = reinterpret_cast<uint4*>(data + base);
+    for (int e = threadIdx.x; e < (len >> 2); e += kNttThreads) dst[e] = reinterpret_cast<const uint4*>(sm)[e];
+  } else {
+    for (int e = threadIdx.x; e < len; e += kNttThreads) data[base + e] = sm[e];
+  }
 }
 
 template <bool INV>
@@ -154,7 +177,9 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__
     const int s = INV ? (L1 - 1 - step) : step;
     const int lth = L1 - s - 1;                       // log2 of the row distance
     const uint32_t m = 1u << s;
-    for (int b = threadIdx.x; b < kNttTile / 2; b += kNttThreads) {
+#pragma unroll
+    for (int r = 0; r < kNttPer; r++) {
+      const int b = threadIdx.x + r * kNttThreads;
       const int c = b & (CW - 1), hb = b >> cwl;
       const int h = ((hb >> lth) << (lth + 1)) | (hb & ((1 << lth) - 1));
       const uint2 w = __ldg(&twp[m + (uint32_t)(h >> (lth + 1))]);
@@ -223,36 +248,43 @@ __global__ void k_tree_crt(const uint32_t* __restrict__ Z, int64_t T, int64_t Tp
   coef[r] = x;
 }
 
-// Descent load: XH[r][i][P n + k] = X_P[d_P - 1 - k] (k < d_P), else 0.
+// Descent load: XH[r][i][P n + k] = X_P[d_P - 1 - k] (k < d_P), else 0; one
+// thread per (r, P n + k) writes all five primes' residues.
 __global__ void k_desc_load(const uint64_t* __restrict__ X, int R, int64_t T, int64_t Tp, int logn, NttConsts C,
                             uint32_t* __restrict__ XH) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over R * kNP * T'
-  if (idx >= (int64_t)R * kNP * Tp) return;
-  const int64_t plane = idx / Tp;
-  const int64_t e = idx - plane * Tp;
-  const int rr = (int)(plane / kNP), i = (int)(plane - (int64_t)rr * kNP);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over R * T'
+  if (idx >= (int64_t)R * Tp) return;
+  const int rr = (int)(idx / Tp);
+  const int64_t e = idx - (int64_t)rr * Tp;
   const int64_t n = 1ll << logn;
   const int64_t P = e >> logn, k = e & (n - 1);
   int64_t d = T - P * n;
   d = d < 0 ? 0 : (d > n ? n : d);
-  XH[idx] = k < d ? residue64(X[(int64_t)rr * Tp + P * n + d - 1 - k], C, i) : 0;
+  const uint64_t x = k < d ? X[(int64_t)rr * Tp + P * n + d - 1 - k] : 0;
+  uint32_t* out = XH + (int64_t)rr * kNP * Tp + e;
+#pragma unroll
+  for (int i = 0; i < kNP; i++) out[(int64_t)i * Tp] = k < d ? residue64(x, C, i) : 0u;
 }
 
-// Descent products: Y[c][r][i][P n + k] = XH[r][i][P n + k] spec[i][P][1 - c][k].
+// Descent products: Y[c][r][i][P n + k] = XH[r][i][P n + k] spec[i][P][1 - c][k];
+// one thread per (i, P n + k) loads the two spectra once for all R rows.
 __global__ void k_desc_mul(const uint32_t* __restrict__ XH, const uint32_t* __restrict__ spec, int R, int64_t Tp,
                            int logn, NttConsts C, uint32_t* __restrict__ Y) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over R * kNP * T'
-  const int64_t all = (int64_t)R * kNP * Tp;
-  if (idx >= all) return;
-  const int64_t plane = idx / Tp;
-  const int64_t e = idx - plane * Tp;
-  const int i = (int)(plane % kNP);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP * T'
+  if (idx >= (int64_t)kNP * Tp) return;
+  const int i = (int)(idx / Tp);
+  const int64_t e = idx - (int64_t)i * Tp;
   const uint32_t q = C.q[i], qi = C.qinv[i];
   const int64_t P = e >> logn, k = e & ((1ll << logn) - 1);
   const uint32_t* s = spec + (int64_t)i * 2 * Tp + (2 * P << logn) + k;
-  const uint32_t x = sub_if(XH[idx], 2 * q);
-  Y[idx] = mont32(x, sub_if(s[1ll << logn], 2 * q), q, qi);          // child L: times R
-  Y[all + idx] = mont32(x, sub_if(s[0], 2 * q), q, qi);              // child R: times L
+  const uint32_t sL = sub_if(s[0], 2 * q), sR = sub_if(s[1ll << logn], 2 * q);
+  const int64_t all = (int64_t)R * kNP * Tp;
+  for (int r = 0; r < R; r++) {
+    const int64_t at = ((int64_t)r * kNP + i) * Tp + e;
+    const uint32_t x = sub_if(XH[at], 2 * q);
+    Y[at] = mont32(x, sR, q, qi);                   // child L: times R
+    Y[all + at] = mont32(x, sL, q, qi);             // child R: times L
+  }
 }
 
 // Descent Chinese remaindering: X'[r][(2P + c) h + m] = y_c[d_P - 1 - m], m < d_c.
@@ -319,6 +351,211 @@ __global__ void k_rev_poly(const uint64_t* __restrict__ m, int64_t T, Mod M, uin
   f[t] = mt;
   if (t < T) rd[t] = mul_mod((uint64_t)(T - t) % M.p, mt, M);
   if (t == 0) g[0] = 1;
+}
+
+// ---- levels small enough for one CTA ------------------------------------------------
+//
+// For transforms of n <= kFusedMax, one CTA holds the five primes' transforms
+// of a node in shared memory and runs a whole level's work for it in one
+// launch: residues, forward transforms, products, inverse transforms and the
+// Chinese remaindering, with no trip through global memory in between.
+
+constexpr int kFusedLog = 12;
+constexpr int kFusedMax = 1 << kFusedLog;
+constexpr int kFusedThreads = 512;
+
+// ntr transforms of size 2^logn at sm + t 2^logn, transform t modulo prime
+// t mod 5; forward (CT) or inverse (GS) stages, as k_ntt_local.
+template <bool INV>
+__device__ void smem_ntt(uint32_t* sm, int ntr, int logn, const uint2* __restrict__ tw, int logN, const NttConsts& C) {
+  const int half = 1 << (logn - 1);
+  const int total = ntr * half;
+  for (int step = 0; step < logn; step++) {
+    const int s = INV ? (logn - 1 - step) : step;
+    const int lt = logn - s - 1;
+    const uint32_t m = 1u << s;
+    for (int i0 = 0; i0 < total; i0 += 4 * kFusedThreads) {
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const int idx = i0 + r * kFusedThreads + threadIdx.x;
+        if (idx < total) {
+          const int t = idx >> (logn - 1), b = idx & (half - 1);
+          const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
+          const int prime = t % kNP;
+          const uint2 w = __ldg(&tw[((int64_t)prime << logN) + m + (uint32_t)(pos >> (lt + 1))]);
+          uint32_t* base = sm + (t << logn);
+          butterfly<INV>(base + pos, base + pos + (1 << lt), w, C.q[prime]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Tree level l <= kFusedLog, one CTA per node P: the two children as full
+// monic polynomials -> spectra (kept in spec for the descent) -> product ->
+// coefficients of P (coef, the wrapped z^n taken off when deg P = n).
+__global__ void __launch_bounds__(kFusedThreads) k_tree_fused(const uint64_t* __restrict__ below, int64_t T,
+                                                              int64_t Tp, int logn, NttConsts C, CrtScale sc, Mod M,
+                                                              const uint2* __restrict__ tw, int logN,
+                                                              uint32_t* __restrict__ spec, uint64_t* __restrict__ coef) {
+  extern __shared__ uint32_t fsm[];              // [c][prime][n]
+  const int64_t P = blockIdx.x;
+  const int n = 1 << logn, h = n >> 1;
+  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
+    const int c = e >> logn, k = e & (n - 1);
+    const int64_t child = 2 * P + c;
+    int64_t d = T - child * h;
+    d = d < 0 ? 0 : (d > h ? h : d);
+    const uint64_t x = k < d ? below[child * h + k] : 0;
+#pragma unroll
+    for (int i = 0; i < kNP; i++) fsm[((c * kNP + i) << logn) + k] = k < d ? residue64(x, C, i) : (k == d ? 1u : 0u);
+  }
+  __syncthreads();
+  smem_ntt<false>(fsm, 2 * kNP, logn, tw, logN, C);
+  for (int e = threadIdx.x; e < kNP * n; e += blockDim.x) {
+    const int i = e >> logn, k = e & (n - 1);
+    const uint32_t q = C.q[i];
+    const uint32_t a = fsm[(i << logn) + k], b = fsm[((kNP + i) << logn) + k];
+    uint32_t* sp = spec + (int64_t)i * 2 * Tp + (2 * P << logn) + k;
+    sp[0] = a;
+    sp[n] = b;
+    fsm[(i << logn) + k] = mont32(sub_if(a, 2 * q), sub_if(b, 2 * q), q, C.qinv[i]);
+  }
+  __syncthreads();
+  smem_ntt<true>(fsm, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+  int64_t d = T - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    uint32_t res[kNP];
+#pragma unroll
+    for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[(i << logn) + k], sc.s[i], sc.sp[i], C.q[i]);
+    uint64_t x = crt_to_p(res, C, M);
+    if (k == 0 && d == n) x = sub_mod(x, 1, M);
+    coef[P * n + k] = x;
+  }
+}
+
+// Descent level l <= kFusedLog, one CTA per (right-hand side r, node P):
+// X_P reversed -> spectrum -> times each child's sibling spectrum -> inverse
+// -> Chinese remaindering into the children's expansions.
+__global__ void __launch_bounds__(kFusedThreads) k_desc_fused(const uint64_t* __restrict__ X, int64_t T, int64_t Tp,
+                                                              int logn, NttConsts C, CrtScale sc, Mod M,
+                                                              const uint2* __restrict__ tw, int logN,
+                                                              const uint32_t* __restrict__ spec,
+                                                              uint64_t* __restrict__ Xn, int64_t nodes) {
+  extern __shared__ uint32_t fsm[];              // XH [prime][n], then Y [prime][n]
+  const int64_t P = blockIdx.x % nodes;
+  const int r = (int)(blockIdx.x / nodes);
+  const int n = 1 << logn, h = n >> 1;
+  uint32_t* XH = fsm;
+  uint32_t* Y = fsm + (kNP << logn);
+  int64_t d = T - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  const uint64_t* x = X + (int64_t)r * Tp + P * n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const uint64_t v = k < d ? x[d - 1 - k] : 0;
+#pragma unroll
+    for (int i = 0; i < kNP; i++) XH[(i << logn) + k] = k < d ? residue64(v, C, i) : 0u;
+  }
+  __syncthreads();
+  smem_ntt<false>(XH, kNP, logn, tw, logN, C);
+  const int64_t dl = d < h ? d : h;
+  for (int c = 0; c < 2; c++) {
+    const int64_t dc = c ? d - dl : dl;
+    if (dc <= 0) break;
+    for (int e = threadIdx.x; e < kNP * n; e += blockDim.x) {
+      const int i = e >> logn, k = e & (n - 1);
+      const uint32_t q = C.q[i];
+      const uint32_t s = spec[(int64_t)i * 2 * Tp + ((2 * P + (1 - c)) << logn) + k];
+      Y[e] = mont32(sub_if(XH[e], 2 * q), sub_if(s, 2 * q), q, C.qinv[i]);
+    }
+    __syncthreads();
+    smem_ntt<true>(Y, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+    uint64_t* out = Xn + (int64_t)r * Tp + (2 * P + c) * h;
+    for (int m = threadIdx.x; m < dc; m += blockDim.x) {
+      uint32_t res[kNP];
+#pragma unroll
+      for (int i = 0; i < kNP; i++) res[i] = shoup32(Y[(i << logn) + (d - 1 - m)], sc.s[i], sc.sp[i], C.q[i]);
+      out[m] = crt_to_p(res, C, M);
+    }
+    __syncthreads();
+  }
+}
+
+// Newton's iteration for g = 1 / f mod z^K (K a power of two <= kFusedMax),
+// f_0 = 1, all in one CTA: for k = 1, 2, .., K/2, e = f g_k (its coefficients
+// k..2k-1, a cyclic product of size 2k), then g_{k..2k} = -(g_k e_hi mod z^k).
+// g (2K words) and e (K words) live in global memory; f has nf coefficients.
+__global__ void __launch_bounds__(kFusedThreads) k_newton_fused(const uint64_t* __restrict__ f, int64_t nf, int logK,
+                                                                NttConsts C, Mod M, const uint2* __restrict__ tw,
+                                                                int logN, uint64_t* __restrict__ g,
+                                                                uint64_t* __restrict__ e) {
+  extern __shared__ uint32_t fsm[];              // A [prime][2k], B [prime][2k]
+  if (threadIdx.x == 0) g[0] = 1;
+  __syncthreads();
+  for (int lk = 0; lk < logK; lk++) {
+    const int k = 1 << lk, logn = lk + 1, n = 2 * k;
+    uint32_t* A = fsm;
+    uint32_t* B = fsm + (kNP << logn);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const uint64_t fv = t < nf ? f[t] : 0;
+      const uint64_t gv = t < k ? g[t] : 0;
+#pragma unroll
+      for (int i = 0; i < kNP; i++) {
+        A[(i << logn) + t] = t < nf ? residue64(fv, C, i) : 0u;
+        B[(i << logn) + t] = t < k ? residue64(gv, C, i) : 0u;
+      }
+    }
+    __syncthreads();
+    smem_ntt<false>(fsm, 2 * kNP, logn, tw, logN, C);     // A and B are contiguous: ten transforms
+    for (int x = threadIdx.x; x < kNP * n; x += blockDim.x) {
+      const int i = x >> logn;
+      const uint32_t q = C.q[i];
+      A[x] = mont32(sub_if(A[x], 2 * q), sub_if(B[x], 2 * q), q, C.qinv[i]);
+    }
+    __syncthreads();
+    smem_ntt<true>(A, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+    // scale 2^32 / n per prime, computed here (n varies by step)
+    uint32_t s[kNP], sp[kNP];
+#pragma unroll
+    for (int i = 0; i < kNP; i++) {
+      const uint32_t q = C.q[i];
+      // 2^32 / 2^logn mod q: 2^(32 - logn) when logn <= 32 is exact
+      const uint32_t x = (uint32_t)(((uint64_t)1 << (32 - logn)) % q);
+      s[i] = x;
+      sp[i] = (uint32_t)(((uint64_t)x << 32) / q);
+    }
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      uint32_t res[kNP];
+#pragma unroll
+      for (int i = 0; i < kNP; i++) res[i] = shoup32(A[(i << logn) + k + t], s[i], sp[i], C.q[i]);
+      e[t] = crt_to_p(res, C, M);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const uint64_t ev = t < k ? e[t] : 0;
+#pragma unroll
+      for (int i = 0; i < kNP; i++) A[(i << logn) + t] = t < k ? residue64(ev, C, i) : 0u;
+    }
+    __syncthreads();
+    smem_ntt<false>(A, kNP, logn, tw, logN, C);
+    for (int x = threadIdx.x; x < kNP * n; x += blockDim.x) {
+      const int i = x >> logn;
+      const uint32_t q = C.q[i];
+      A[x] = mont32(sub_if(A[x], 2 * q), sub_if(B[x], 2 * q), q, C.qinv[i]);
+    }
+    __syncthreads();
+    smem_ntt<true>(A, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      uint32_t res[kNP];
+#pragma unroll
+      for (int i = 0; i < kNP; i++) res[i] = shoup32(A[(i << logn) + t], s[i], sp[i], C.q[i]);
+      const uint64_t x = crt_to_p(res, C, M);
+      g[k + t] = x ? M.p - x : 0;
+    }
+    __syncthreads();
+  }
 }
 
 // ---- leaves --------------------------------------------------------------------------
@@ -606,12 +843,26 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   const int logN = ctx->ntt_logN;
   FastRun F{ctx, C, M, tw, itw, logN, st};
 
+  static DeviceOnce fused_attr;
+  fused_attr.run([] {
+    const int bytes = (int)(sizeof(uint32_t) * 2 * kNP * kFusedMax);
+    cudaFuncSetAttribute(k_tree_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_desc_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_newton_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  });
   // tree: leaf blocks, then levels 8 .. 7 + Lt
   k_fast_leafpoly<<<cdivu(T, kLeaf), kLeaf, 0, st>>>(v, T, M, w.coef[0]);
   note_launch();
   for (int l = 1; l <= Lt; l++) {
     const int logn = kLeafLog + l;
     uint32_t* spec = w.spec[l - 1];
+    if (logn <= kFusedLog) {
+      const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
+      k_tree_fused<<<(unsigned)nodes, kFusedThreads, sizeof(uint32_t) * 2 * kNP << logn, st>>>(
+          w.coef[l - 1], T, Tp, logn, C, crt_scale(logn), M, tw, logN, spec, w.coef[l]);
+      note_launch();
+      continue;
+    }
     k_tree_load<<<cdivu(kNP * 2 * Tp, 256), 256, 0, st>>>(w.coef[l - 1], T, Tp, logn, C, spec);
     note_launch();
     launch_ntt(spec, (kNP * 2 * Tp) >> logn, logn, logT + 1, false, tw, itw, logN, C, st);
@@ -626,7 +877,12 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   // power sums: g = 1 / rev(M) mod z^T by Newton's iteration, ps = rev(M') g
   k_rev_poly<<<cdivu(T + 1, 256), 256, 0, st>>>(m, T, M, w.f, w.rd, w.g);
   note_launch();
-  for (int64_t k = 1; k < T; k *= 2) {
+  // the first steps (precision up to kFusedMax) in one CTA
+  const int logK0 = std::min(ilog2(T), kFusedLog);
+  k_newton_fused<<<1, kFusedThreads, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(w.f, T + 1, logK0, C, M, tw, logN,
+                                                                             w.g, w.e);
+  note_launch();
+  for (int64_t k = 1ll << logK0; k < T; k *= 2) {
     const int logk2 = ilog2(2 * k);
     const int64_t fn = std::min<int64_t>(2 * k, T + 1);
     // e = f g: its coefficients k .. 2k-1 (the low ones are 1, 0, ..)
@@ -643,11 +899,19 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   uint64_t* Xn = w.X1;
   for (int l = Lt; l >= 1; l--) {
     const int logn = kLeafLog + l;
+    if (logn <= kFusedLog) {
+      const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
+      k_desc_fused<<<(unsigned)(nodes * R), kFusedThreads, sizeof(uint32_t) * 2 * kNP << logn, st>>>(
+          X, T, Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn, nodes);
+      note_launch();
+      std::swap(X, Xn);
+      continue;
+    }
     const int64_t all = (int64_t)R * kNP * Tp;
-    k_desc_load<<<cdivu(all, 256), 256, 0, st>>>(X, R, T, Tp, logn, C, w.XH);
+    k_desc_load<<<cdivu((int64_t)R * Tp, 256), 256, 0, st>>>(X, R, T, Tp, logn, C, w.XH);
     note_launch();
     launch_ntt(w.XH, all >> logn, logn, logT, false, tw, itw, logN, C, st);
-    k_desc_mul<<<cdivu(all, 256), 256, 0, st>>>(w.XH, w.spec[l - 1], R, Tp, logn, C, w.Y);
+    k_desc_mul<<<cdivu((int64_t)kNP * Tp, 256), 256, 0, st>>>(w.XH, w.spec[l - 1], R, Tp, logn, C, w.Y);
     note_launch();
     launch_ntt(w.Y, (2 * all) >> logn, logn, logT, true, tw, itw, logN, C, st);
     k_desc_crt<<<cdivu((int64_t)R * Tp, 256), 256, 0, st>>>(w.Y, R, T, Tp, logn, C, crt_scale(logn), M, Xn);
