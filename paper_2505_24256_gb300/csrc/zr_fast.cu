@@ -137,15 +137,23 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict_
     const int s = INV ? (logn - 1 - step) : (s_lo + step);
     const int lt = logn - s - 1;                      // log2 t
     const uint32_t m = 1u << s;
+    // all of a thread's twiddles first, so that their loads overlap
+    uint2 w[kNttPer];
+#pragma unroll
+    for (int r = 0; r < kNttPer; r++) {
+      const int b = threadIdx.x + r * kNttThreads;
+      const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
+      const int prime = uniform ? pb5 : (pb5 + (pos >> plane_log)) % kNP;
+      const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
+      w[r] = b < half ? __ldg(&tw[((int64_t)prime << logN) + m + grp]) : make_uint2(0, 0);
+    }
 #pragma unroll
     for (int r = 0; r < kNttPer; r++) {
       const int b = threadIdx.x + r * kNttThreads;
       if (b < half) {
         const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
         const int prime = uniform ? pb5 : (pb5 + (pos >> plane_log)) % kNP;
-        const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
-        const uint2 w = __ldg(&tw[((int64_t)prime << logN) + m + grp]);
-        butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], w, C.q[prime]);
+        butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], w[r], C.q[prime]);
       }
     }
     __syncthreads();
@@ -177,13 +185,20 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__
     const int s = INV ? (L1 - 1 - step) : step;
     const int lth = L1 - s - 1;                       // log2 of the row distance
     const uint32_t m = 1u << s;
+    uint2 w[kNttPer];
+#pragma unroll
+    for (int r = 0; r < kNttPer; r++) {
+      const int b = threadIdx.x + r * kNttThreads;
+      const int hb = b >> cwl;
+      const int h = ((hb >> lth) << (lth + 1)) | (hb & ((1 << lth) - 1));
+      w[r] = __ldg(&twp[m + (uint32_t)(h >> (lth + 1))]);
+    }
 #pragma unroll
     for (int r = 0; r < kNttPer; r++) {
       const int b = threadIdx.x + r * kNttThreads;
       const int c = b & (CW - 1), hb = b >> cwl;
       const int h = ((hb >> lth) << (lth + 1)) | (hb & ((1 << lth) - 1));
-      const uint2 w = __ldg(&twp[m + (uint32_t)(h >> (lth + 1))]);
-      butterfly<INV>(&sm[(h << cwl) + c], &sm[((h + (1 << lth)) << cwl) + c], w, q);
+      butterfly<INV>(&sm[(h << cwl) + c], &sm[((h + (1 << lth)) << cwl) + c], w[r], q);
     }
     __syncthreads();
   }
@@ -374,17 +389,24 @@ __device__ void smem_ntt(uint32_t* sm, int ntr, int logn, const uint2* __restric
     const int s = INV ? (logn - 1 - step) : step;
     const int lt = logn - s - 1;
     const uint32_t m = 1u << s;
-    for (int i0 = 0; i0 < total; i0 += 4 * kFusedThreads) {
+    for (int i0 = 0; i0 < total; i0 += 8 * kFusedThreads) {
+      uint2 w[8];
 #pragma unroll
-      for (int r = 0; r < 4; r++) {
+      for (int r = 0; r < 8; r++) {
+        const int idx = i0 + r * kFusedThreads + threadIdx.x;
+        const int t = idx >> (logn - 1), b = idx & (half - 1);
+        const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
+        w[r] = idx < total ? __ldg(&tw[((int64_t)(t % kNP) << logN) + m + (uint32_t)(pos >> (lt + 1))])
+                           : make_uint2(0, 0);
+      }
+#pragma unroll
+      for (int r = 0; r < 8; r++) {
         const int idx = i0 + r * kFusedThreads + threadIdx.x;
         if (idx < total) {
           const int t = idx >> (logn - 1), b = idx & (half - 1);
           const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-          const int prime = t % kNP;
-          const uint2 w = __ldg(&tw[((int64_t)prime << logN) + m + (uint32_t)(pos >> (lt + 1))]);
           uint32_t* base = sm + (t << logn);
-          butterfly<INV>(base + pos, base + pos + (1 << lt), w, C.q[prime]);
+          butterfly<INV>(base + pos, base + pos + (1 << lt), w[r], C.q[t % kNP]);
         }
       }
     }
@@ -392,92 +414,119 @@ __device__ void smem_ntt(uint32_t* sm, int ntr, int logn, const uint2* __restric
   }
 }
 
-// Tree level l <= kFusedLog, one CTA per node P: the two children as full
+// Nodes a fused CTA takes at transform size 2^logn: enough for 2048
+// elements per prime (80 KB of shared memory, two CTAs per SM), at least one.
+__host__ __device__ inline int fused_npc(int logn) { return logn >= 11 ? 1 : (2048 >> logn); }
+
+// Tree level l <= kFusedLog, npc nodes P per CTA: the two children as full
 // monic polynomials -> spectra (kept in spec for the descent) -> product ->
 // coefficients of P (coef, the wrapped z^n taken off when deg P = n).
 __global__ void __launch_bounds__(kFusedThreads) k_tree_fused(const uint64_t* __restrict__ below, int64_t T,
                                                               int64_t Tp, int logn, NttConsts C, CrtScale sc, Mod M,
                                                               const uint2* __restrict__ tw, int logN,
-                                                              uint32_t* __restrict__ spec, uint64_t* __restrict__ coef) {
-  extern __shared__ uint32_t fsm[];              // [c][prime][n]
-  const int64_t P = blockIdx.x;
+                                                              uint32_t* __restrict__ spec, uint64_t* __restrict__ coef,
+                                                              int64_t nodes) {
+  extern __shared__ uint32_t fsm[];              // [c][node][prime][n]
+  const int npc = fused_npc(logn);
+  const int64_t P0 = (int64_t)blockIdx.x * npc;
   const int n = 1 << logn, h = n >> 1;
-  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
-    const int c = e >> logn, k = e & (n - 1);
-    const int64_t child = 2 * P + c;
+  const int half = (npc * kNP) << logn;         // the right children's transforms start here
+  for (int e = threadIdx.x; e < 2 * npc * n; e += blockDim.x) {
+    const int c = e / (npc * n), rest = e - c * npc * n;
+    const int a = rest >> logn, k = rest & (n - 1);
+    const int64_t child = 2 * (P0 + a) + c;
     int64_t d = T - child * h;
     d = d < 0 ? 0 : (d > h ? h : d);
     const uint64_t x = k < d ? below[child * h + k] : 0;
 #pragma unroll
-    for (int i = 0; i < kNP; i++) fsm[((c * kNP + i) << logn) + k] = k < d ? residue64(x, C, i) : (k == d ? 1u : 0u);
+    for (int i = 0; i < kNP; i++)
+      fsm[(((c * npc + a) * kNP + i) << logn) + k] = k < d ? residue64(x, C, i) : (k == d ? 1u : 0u);
   }
   __syncthreads();
-  smem_ntt<false>(fsm, 2 * kNP, logn, tw, logN, C);
-  for (int e = threadIdx.x; e < kNP * n; e += blockDim.x) {
-    const int i = e >> logn, k = e & (n - 1);
+  smem_ntt<false>(fsm, 2 * kNP * npc, logn, tw, logN, C);
+  for (int e = threadIdx.x; e < half; e += blockDim.x) {
+    const int t = e >> logn, k = e & (n - 1);    // t = a kNP + i
+    const int a = t / kNP, i = t - a * kNP;
+    const int64_t P = P0 + a;
     const uint32_t q = C.q[i];
-    const uint32_t a = fsm[(i << logn) + k], b = fsm[((kNP + i) << logn) + k];
-    uint32_t* sp = spec + (int64_t)i * 2 * Tp + (2 * P << logn) + k;
-    sp[0] = a;
-    sp[n] = b;
-    fsm[(i << logn) + k] = mont32(sub_if(a, 2 * q), sub_if(b, 2 * q), q, C.qinv[i]);
+    const uint32_t x = fsm[e], y = fsm[half + e];
+    if (P < nodes) {
+      uint32_t* sp = spec + (int64_t)i * 2 * Tp + (2 * P << logn) + k;
+      sp[0] = x;
+      sp[n] = y;
+    }
+    fsm[e] = mont32(sub_if(x, 2 * q), sub_if(y, 2 * q), q, C.qinv[i]);
   }
   __syncthreads();
-  smem_ntt<true>(fsm, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
-  int64_t d = T - P * n;
-  d = d < 0 ? 0 : (d > n ? n : d);
-  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+  smem_ntt<true>(fsm, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+  for (int e = threadIdx.x; e < npc * n; e += blockDim.x) {
+    const int a = e >> logn, k = e & (n - 1);
+    const int64_t P = P0 + a;
+    int64_t d = T - P * n;
+    d = d < 0 ? 0 : (d > n ? n : d);
+    if (k >= d) continue;
     uint32_t res[kNP];
 #pragma unroll
-    for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[(i << logn) + k], sc.s[i], sc.sp[i], C.q[i]);
+    for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[((a * kNP + i) << logn) + k], sc.s[i], sc.sp[i], C.q[i]);
     uint64_t x = crt_to_p(res, C, M);
     if (k == 0 && d == n) x = sub_mod(x, 1, M);
     coef[P * n + k] = x;
   }
 }
 
-// Descent level l <= kFusedLog, one CTA per (right-hand side r, node P):
-// X_P reversed -> spectrum -> times each child's sibling spectrum -> inverse
-// -> Chinese remaindering into the children's expansions.
+// Descent level l <= kFusedLog, npc nodes P of one right-hand side r per
+// CTA: X_P reversed -> spectrum -> times each child's sibling spectrum ->
+// inverse -> Chinese remaindering into the children's expansions.
 __global__ void __launch_bounds__(kFusedThreads) k_desc_fused(const uint64_t* __restrict__ X, int64_t T, int64_t Tp,
                                                               int logn, NttConsts C, CrtScale sc, Mod M,
                                                               const uint2* __restrict__ tw, int logN,
                                                               const uint32_t* __restrict__ spec,
                                                               uint64_t* __restrict__ Xn, int64_t nodes) {
-  extern __shared__ uint32_t fsm[];              // XH [prime][n], then Y [prime][n]
-  const int64_t P = blockIdx.x % nodes;
-  const int r = (int)(blockIdx.x / nodes);
+  extern __shared__ uint32_t fsm[];              // XH [node][prime][n], then Y [node][prime][n]
+  const int npc = fused_npc(logn);
+  const int64_t ctas = (nodes + npc - 1) / npc;
+  const int64_t P0 = (int64_t)(blockIdx.x % ctas) * npc;
+  const int r = (int)(blockIdx.x / ctas);
   const int n = 1 << logn, h = n >> 1;
+  const int span = (npc * kNP) << logn;
   uint32_t* XH = fsm;
-  uint32_t* Y = fsm + (kNP << logn);
-  int64_t d = T - P * n;
-  d = d < 0 ? 0 : (d > n ? n : d);
-  const uint64_t* x = X + (int64_t)r * Tp + P * n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const uint64_t v = k < d ? x[d - 1 - k] : 0;
+  uint32_t* Y = fsm + span;
+  const uint64_t* x = X + (int64_t)r * Tp;
+  for (int e = threadIdx.x; e < npc * n; e += blockDim.x) {
+    const int a = e >> logn, k = e & (n - 1);
+    const int64_t P = P0 + a;
+    int64_t d = T - P * n;
+    d = d < 0 ? 0 : (d > n ? n : d);
+    const uint64_t v = k < d ? x[P * n + d - 1 - k] : 0;
 #pragma unroll
-    for (int i = 0; i < kNP; i++) XH[(i << logn) + k] = k < d ? residue64(v, C, i) : 0u;
+    for (int i = 0; i < kNP; i++) XH[((a * kNP + i) << logn) + k] = k < d ? residue64(v, C, i) : 0u;
   }
   __syncthreads();
-  smem_ntt<false>(XH, kNP, logn, tw, logN, C);
-  const int64_t dl = d < h ? d : h;
+  smem_ntt<false>(XH, npc * kNP, logn, tw, logN, C);
   for (int c = 0; c < 2; c++) {
-    const int64_t dc = c ? d - dl : dl;
-    if (dc <= 0) break;
-    for (int e = threadIdx.x; e < kNP * n; e += blockDim.x) {
-      const int i = e >> logn, k = e & (n - 1);
+    for (int e = threadIdx.x; e < span; e += blockDim.x) {
+      const int t = e >> logn, k = e & (n - 1);
+      const int a = t / kNP, i = t - a * kNP;
+      const int64_t P = P0 + a;
       const uint32_t q = C.q[i];
-      const uint32_t s = spec[(int64_t)i * 2 * Tp + ((2 * P + (1 - c)) << logn) + k];
+      const uint32_t s = P < nodes ? spec[(int64_t)i * 2 * Tp + ((2 * P + (1 - c)) << logn) + k] : 0u;
       Y[e] = mont32(sub_if(XH[e], 2 * q), sub_if(s, 2 * q), q, C.qinv[i]);
     }
     __syncthreads();
-    smem_ntt<true>(Y, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
-    uint64_t* out = Xn + (int64_t)r * Tp + (2 * P + c) * h;
-    for (int m = threadIdx.x; m < dc; m += blockDim.x) {
+    smem_ntt<true>(Y, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+    for (int e = threadIdx.x; e < npc * h; e += blockDim.x) {
+      const int a = e / h, m = e - a * h;
+      const int64_t P = P0 + a;
+      int64_t d = T - P * n;
+      d = d < 0 ? 0 : (d > n ? n : d);
+      const int64_t dl = d < h ? d : h;
+      const int64_t dc = c ? d - dl : dl;
+      if (m >= dc) continue;
       uint32_t res[kNP];
 #pragma unroll
-      for (int i = 0; i < kNP; i++) res[i] = shoup32(Y[(i << logn) + (d - 1 - m)], sc.s[i], sc.sp[i], C.q[i]);
-      out[m] = crt_to_p(res, C, M);
+      for (int i = 0; i < kNP; i++)
+        res[i] = shoup32(Y[((a * kNP + i) << logn) + (d - 1 - m)], sc.s[i], sc.sp[i], C.q[i]);
+      Xn[(int64_t)r * Tp + (2 * P + c) * h + m] = crt_to_p(res, C, M);
     }
     __syncthreads();
   }
@@ -858,8 +907,10 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     uint32_t* spec = w.spec[l - 1];
     if (logn <= kFusedLog) {
       const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
-      k_tree_fused<<<(unsigned)nodes, kFusedThreads, sizeof(uint32_t) * 2 * kNP << logn, st>>>(
-          w.coef[l - 1], T, Tp, logn, C, crt_scale(logn), M, tw, logN, spec, w.coef[l]);
+      const int npc = fused_npc(logn);
+      k_tree_fused<<<(unsigned)((nodes + npc - 1) / npc), kFusedThreads,
+                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(w.coef[l - 1], T, Tp, logn, C, crt_scale(logn),
+                                                                     M, tw, logN, spec, w.coef[l], nodes);
       note_launch();
       continue;
     }
@@ -901,8 +952,10 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     const int logn = kLeafLog + l;
     if (logn <= kFusedLog) {
       const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
-      k_desc_fused<<<(unsigned)(nodes * R), kFusedThreads, sizeof(uint32_t) * 2 * kNP << logn, st>>>(
-          X, T, Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn, nodes);
+      const int npc = fused_npc(logn);
+      k_desc_fused<<<(unsigned)((nodes + npc - 1) / npc * R), kFusedThreads,
+                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(X, T, Tp, logn, C, crt_scale(logn), M, tw, logN,
+                                                                     w.spec[l - 1], Xn, nodes);
       note_launch();
       std::swap(X, Xn);
       continue;
