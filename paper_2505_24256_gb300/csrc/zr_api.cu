@@ -397,6 +397,7 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ntt_tw) cudaFree(ctx->ntt_tw);
+  if (ctx->fprobe_ws) cudaFree(ctx->fprobe_ws);
   delete ctx;
 }
 
@@ -413,6 +414,15 @@ bool use_fast_solve(const zr_ctx* ctx, int64_t T) {
   if (T < 1 || T > kFastMaxT || ctx->solve_method == 1) return false;
   if (ctx->solve_method == 2) return true;
   return T >= (ctx->fast_min_T > 0 ? ctx->fast_min_T : kFastDefaultMinT);
+}
+}  // namespace zr
+
+namespace zr {
+bool use_fast_probes(const zr_ctx* ctx, int64_t T, int64_t Tf, int S) {
+  if (T < 1 || Tf < 1 || T > kFastMaxT || S > kFastProbeMaxS || ctx->solve_method == 1) return false;
+  if (ctx->solve_method == 2) return true;
+  const int64_t m = ctx->fast_min_T > 0 ? ctx->fast_min_T : kFastDefaultMinT;
+  return T >= m && Tf >= m;
 }
 }  // namespace zr
 

@@ -543,7 +543,9 @@ struct EvalWs {
   int64_t *bsum, *cbsum, *start, *order, *Gdev, *total;
   int32_t *gid, *cnt, *tg, *tp;
 };
-static EvalWs carve_eval(Carver& cv, int64_t Tf, int nv, int k, int S, int64_t T, int gsplit) {
+// fast: the probes go through the transposed tree (its own workspace), so
+// the matrix-vector kernel's tables are not carved
+static EvalWs carve_eval(Carver& cv, int64_t Tf, int nv, int k, int S, int64_t T, int gsplit, bool fast = false) {
   EvalWs w;
   const int64_t Tn = Tf > 0 ? Tf : 1;
   const uint64_t H = hash_slots(Tn);
@@ -563,14 +565,40 @@ static EvalWs carve_eval(Carver& cv, int64_t Tf, int nv, int k, int S, int64_t T
   w.cbsum = cv.take<int64_t>(nbT + 1);
   w.start = cv.take<int64_t>(Tn);
   w.order = cv.take<int64_t>(Tn);
-  w.Wp = cv.take<uint64_t>((size_t)ring_words(S, Tn));
-  w.UP = cv.take<uint64_t>((size_t)Tn * 32);
-  w.UPq = cv.take<uint64_t>((size_t)Tn * 32);
-  w.Uq = cv.take<uint64_t>(Tn);
-  w.partial = cv.take<uint64_t>(gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
+  const int64_t Tr = (fast && Tn <= kFastMaxT) ? 1 : Tn;   // kept when the fast path may fall back
+  w.Wp = cv.take<uint64_t>((size_t)ring_words(S, Tr));
+  w.UP = cv.take<uint64_t>((size_t)Tr * 32);
+  w.UPq = cv.take<uint64_t>((size_t)Tr * 32);
+  w.Uq = cv.take<uint64_t>(Tr);
+  w.partial = cv.take<uint64_t>(Tr > 1 && gsplit > 1 ? (size_t)gsplit * S * (T > 0 ? T : 1) : 1);
   w.Gdev = cv.take<int64_t>(1);
   w.total = cv.take<int64_t>(1);
   return w;
+}
+
+// The merged weights in plain layout for the transposed tree:
+// W[s G + g] = sum over group g's terms of a_t c_s^{e_{t,k}}, times u_g when
+// the probes start at the first power (offset 1).
+__global__ void k_eval_weights(int64_t G, int S, const int64_t* __restrict__ start, const int32_t* __restrict__ cnt,
+                               const int64_t* __restrict__ order, const uint64_t* __restrict__ a,
+                               const uint8_t* __restrict__ exps, int nv, int k, const uint64_t* __restrict__ tabC,
+                               const uint64_t* __restrict__ U, int offset, Mod M, uint64_t* __restrict__ W) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < G * S; idx += stride) {
+    const int64_t g = idx / S;
+    const int s = (int)(idx - g * S);
+    Acc8 acc{0, 0, 0, 0, 0, 0, 0, 0};
+    const uint64_t* cs = tabC + (int64_t)s * kPowTab;
+    const int64_t r0 = start[g], n = cnt[g];
+    for (int64_t x = 0; x < n; x++) {
+      const int64_t t = order[r0 + x];
+      const uint64_t at = a[t], w = cs[exps[t * nv + k]];
+      mac8(acc, lo32(at), hi32(at), lo32(w), hi32(w));
+    }
+    uint64_t r = acc8_value(acc, M);
+    if (offset) r = mul_mod(r, U[g], M);
+    W[(int64_t)s * G + g] = r;
+  }
 }
 
 // The evaluation itself, with its scratch at `base` (capacity checked by the caller).
@@ -583,8 +611,9 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   const uint64_t H = hash_slots(Tf > 0 ? Tf : 1);
   const int64_t nbH = (int64_t)((H + kB - 1) / kB);
   const int gsplit = eval_gsplit(ctx, T, S, Tf);
+  const bool fast = use_fast_probes(ctx, T, Tf, S);
   Carver cv(base);
-  const EvalWs w = carve_eval(cv, Tf, nv, k, S, T, gsplit);
+  const EvalWs w = carve_eval(cv, Tf, nv, k, S, T, gsplit, fast);
 
   if (T <= 0) return ZR_OK;
   if (Tf == 0) {
@@ -609,6 +638,39 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   { k_scan_small<<<1, kB, 0, st>>>(nbT, w.cbsum, w.total); note_launch(); }
   { k_cnt_start<<<(unsigned)nbT, kB, 0, st>>>(Tn, w.cnt, w.cbsum, w.start); note_launch(); }
   { k_eval_scatter<<<cdiv(Tf, 256), 256, 0, st>>>(Tf, w.tg, w.tp, w.start, w.order); note_launch(); }
+  // the transposed tree: its sizes follow the group count, read here (the
+  // matrix-vector kernel below when there are more than kFastMaxT groups)
+  int64_t G = 0;
+  if (fast) {
+    cudaError_t e = cudaMemcpyAsync(&G, w.Gdev, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_probes: group count");
+    if (G < 1 || G > Tn) return set_err(ctx, ZR_ERR_CUDA, "zr_zippel_probes: group count out of range");
+  }
+  if (fast && G <= kFastMaxT) {
+    cudaError_t e = cudaSuccess;
+    const size_t wbytes = (((size_t)S * G * sizeof(uint64_t)) + 255) & ~(size_t)255;
+    const size_t need = wbytes + fast_probes_ws_need(G, T, S);
+    if (ctx->fprobe_cap < need) {
+      if (ctx->fprobe_ws) cudaFree(ctx->fprobe_ws);
+      ctx->fprobe_ws = nullptr;
+      ctx->fprobe_cap = 0;
+      e = cudaMalloc(&ctx->fprobe_ws, need + need / 4);
+      if (e != cudaSuccess) {
+        ctx->fprobe_ws = nullptr;
+        return cuda_err(ctx, e, "zr_zippel_probes: fast workspace");
+      }
+      ctx->fprobe_cap = need + need / 4;
+    }
+    uint64_t* W = reinterpret_cast<uint64_t*>(ctx->fprobe_ws);
+    {
+      const int64_t want = cdiv(G * S, 256), cap = 8ll * (ctx->sms ? ctx->sms : 152);
+      k_eval_weights<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(G, S, w.start, w.cnt, w.order, w.a, f->exps,
+                                                                          nv, k, w.tabC, w.U, offset, M, W);
+      note_launch();
+    }
+    return fast_probes_enqueue(ctx, G, w.U, W, G, S, T, out, ldo, ctx->fprobe_ws + wbytes, st);
+  }
   // the group count stays on the device: the kernels read it, sized for Tf groups
   const RingLayout L = ring_layout(S, Tn);
   int rw = 0;
@@ -627,7 +689,7 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
 
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T) {
   Carver cv(nullptr);
-  carve_eval(cv, f->T, f->nv, k, S, T, eval_gsplit(ctx, T, S, f->T));
+  carve_eval(cv, f->T, f->nv, k, S, T, eval_gsplit(ctx, T, S, f->T), use_fast_probes(ctx, T, f->T, S));
   return cv.off;
 }
 

@@ -357,14 +357,14 @@ __global__ void k_cyc_crt(const uint32_t* __restrict__ Z, int logN, int64_t lo, 
 }
 
 // f_t = coefficient t of rev(M) (f_0 = 1, f_t = m_{T-t}); rd_t = (T - t) m_{T-t}
-// (rev(M'), degree T - 1); g_0 = 1.
+// (rev(M'), degree T - 1; skipped when rd is null); g_0 = 1.
 __global__ void k_rev_poly(const uint64_t* __restrict__ m, int64_t T, Mod M, uint64_t* __restrict__ f,
                            uint64_t* __restrict__ rd, uint64_t* __restrict__ g) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t > T) return;
   const uint64_t mt = t == 0 ? 1 : m[T - t];
   f[t] = mt;
-  if (t < T) rd[t] = mul_mod((uint64_t)(T - t) % M.p, mt, M);
+  if (rd && t < T) rd[t] = mul_mod((uint64_t)(T - t) % M.p, mt, M);
   if (t == 0) g[0] = 1;
 }
 
@@ -699,6 +699,220 @@ __global__ void k_stage_rhs(const uint64_t* __restrict__ b, int64_t ldb, int S, 
   X0[(int64_t)r * Tp + k] = r < S ? b[(int64_t)r * ldb + k] : ps[k];
 }
 
+// ---- the transposed problem: weighted power sums (the probe evaluator) ----------------
+//
+// out[s][i] = sum_g w_{g,s} u_g^i, i < T, is the expansion of
+// sum_g w_{g,s} / (z - u_g) = N_s / M, M = prod_g (z - u_g): the transpose of
+// the descent.  N_s is built bottom-up on the same subproduct tree,
+// N_P = N_L M_R + N_R M_L (degree < deg P), and the expansion is
+// rev(N_s) / rev(M) mod z^T.
+
+// N_blk for every column s at a leaf block (the 128 roots of the block),
+// by the pairwise levels of the block polynomial.
+__device__ __forceinline__ uint64_t up_coef(const uint64_t* Nb, const uint64_t* Mb, int po, int a, int b, int kk,
+                                            const Mod& M) {
+  Acc8 acc = {0, 0, 0, 0, 0, 0, 0, 0};
+  // N_L[i] (i < a) times the full right polynomial (degree b) at kk - i
+  for (int i = (kk - b > 0 ? kk - b : 0); i <= (kk < a - 1 ? kk : a - 1); i++) {
+    const int j = kk - i;
+    const uint64_t x = Nb[po + i], y = j < b ? Mb[po + a + j] : 1;
+    mac8(acc, lo32(x), hi32(x), lo32(y), hi32(y));
+  }
+  // N_R[i] (i < b) times the full left polynomial (degree a) at kk - i
+  for (int i = (kk - a > 0 ? kk - a : 0); i <= (kk < b - 1 ? kk : b - 1); i++) {
+    const int j = kk - i;
+    const uint64_t x = Nb[po + a + i], y = j < a ? Mb[po + j] : 1;
+    mac8(acc, lo32(x), hi32(x), lo32(y), hi32(y));
+  }
+  return acc8_value(acc, M);
+}
+
+__global__ void __launch_bounds__(kLeaf) k_up_leaf(const uint64_t* __restrict__ U, int64_t G,
+                                                   const uint64_t* __restrict__ W, int64_t ldw, int S, Mod M,
+                                                   uint64_t* __restrict__ N7, int64_t Gp) {
+  extern __shared__ uint64_t usm[];              // M [2][128], then N [S][2][128]
+  uint64_t* Mb = usm;
+  uint64_t* Nb = usm + 2 * kLeaf;
+  const int64_t base = (int64_t)blockIdx.x * kLeaf;
+  const int cnt = (int)((G - base) < kLeaf ? (G - base) : kLeaf);
+  const int t = threadIdx.x;
+  if (t < cnt) {
+    const uint64_t x = U[base + t];
+    Mb[t] = x ? M.p - x : 0;                     // z - u
+    for (int c = 0; c < S; c++) Nb[c * 2 * kLeaf + t] = W[(int64_t)c * ldw + base + t];
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int l = 0; l < kLeafLog; l++) {
+    const int size = 1 << l, pair = 2 << l;
+    if (t < cnt) {
+      const int po = t & ~(pair - 1), kk = t - po;
+      const uint64_t* Mc = Mb + cur * kLeaf;
+      if (cnt - po <= size) {
+        Mb[(cur ^ 1) * kLeaf + t] = Mc[t];
+        for (int c = 0; c < S; c++) Nb[(c * 2 + (cur ^ 1)) * kLeaf + t] = Nb[(c * 2 + cur) * kLeaf + t];
+      } else {
+        const int a = size, b = min(size, cnt - po - size);
+        Mb[(cur ^ 1) * kLeaf + t] = conv_coef(Mc, po, a, b, kk, M);
+        for (int c = 0; c < S; c++)
+          Nb[(c * 2 + (cur ^ 1)) * kLeaf + t] = up_coef(Nb + (c * 2 + cur) * kLeaf, Mc, po, a, b, kk, M);
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (t < cnt)
+    for (int c = 0; c < S; c++) N7[(int64_t)c * Gp + base + t] = Nb[(c * 2 + cur) * kLeaf + t];
+}
+
+// Up level l <= kFusedLog, npc nodes of one column s per CTA: the children's
+// numerators -> spectra -> N_L M_R + N_R M_L with the tree's spectra ->
+// inverse -> N_P.
+__global__ void __launch_bounds__(kFusedThreads) k_up_fused(const uint64_t* __restrict__ Nprev, int64_t G, int64_t Gp,
+                                                            int logn, NttConsts C, CrtScale sc, Mod M,
+                                                            const uint2* __restrict__ tw, int logN,
+                                                            const uint32_t* __restrict__ spec,
+                                                            uint64_t* __restrict__ Nout, int64_t nodes) {
+  extern __shared__ uint32_t fsm[];              // [c][node][prime][n]
+  const int npc = fused_npc(logn);
+  const int64_t ctas = (nodes + npc - 1) / npc;
+  const int64_t P0 = (int64_t)(blockIdx.x % ctas) * npc;
+  const int col = (int)(blockIdx.x / ctas);
+  const int n = 1 << logn, h = n >> 1;
+  const int half = (npc * kNP) << logn;
+  const uint64_t* src = Nprev + (int64_t)col * Gp;
+  for (int e = threadIdx.x; e < 2 * npc * n; e += blockDim.x) {
+    const int c = e / (npc * n), rest = e - c * npc * n;
+    const int a = rest >> logn, k = rest & (n - 1);
+    const int64_t child = 2 * (P0 + a) + c;
+    int64_t d = G - child * h;
+    d = d < 0 ? 0 : (d > h ? h : d);
+    const uint64_t x = k < d ? src[child * h + k] : 0;
+#pragma unroll
+    for (int i = 0; i < kNP; i++) fsm[(((c * npc + a) * kNP + i) << logn) + k] = k < d ? residue64(x, C, i) : 0u;
+  }
+  __syncthreads();
+  smem_ntt<false>(fsm, 2 * kNP * npc, logn, tw, logN, C);
+  for (int e = threadIdx.x; e < half; e += blockDim.x) {
+    const int t = e >> logn, k = e & (n - 1);
+    const int a = t / kNP, i = t - a * kNP;
+    const int64_t P = P0 + a;
+    const uint32_t q = C.q[i], qi = C.qinv[i];
+    uint32_t sL = 0, sR = 0;
+    if (P < nodes) {
+      const uint32_t* sp = spec + (int64_t)i * 2 * Gp + (2 * P << logn) + k;
+      sL = sub_if(sp[0], 2 * q);
+      sR = sub_if(sp[n], 2 * q);
+    }
+    const uint32_t z = mont32(sub_if(fsm[e], 2 * q), sR, q, qi) + mont32(sub_if(fsm[half + e], 2 * q), sL, q, qi);
+    fsm[e] = z;                                  // < 2q
+  }
+  __syncthreads();
+  smem_ntt<true>(fsm, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+  uint64_t* dst = Nout + (int64_t)col * Gp;
+  for (int e = threadIdx.x; e < npc * n; e += blockDim.x) {
+    const int a = e >> logn, k = e & (n - 1);
+    const int64_t P = P0 + a;
+    int64_t d = G - P * n;
+    d = d < 0 ? 0 : (d > n ? n : d);
+    if (k >= d) continue;
+    uint32_t res[kNP];
+#pragma unroll
+    for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[((a * kNP + i) << logn) + k], sc.s[i], sc.sp[i], C.q[i]);
+    dst[P * n + k] = crt_to_p(res, C, M);
+  }
+}
+
+// Up level l > kFusedLog in separate passes: A[s][i][(2P + c) n + k] (planes
+// of 2 G'), forward transforms, Z[s][i][P n + k] = N_L M_R + N_R M_L (planes
+// of G'), inverse transforms, then Chinese remaindering into N_P.
+__global__ void k_up_load(const uint64_t* __restrict__ Nprev, int S, int64_t G, int64_t Gp, int logn, NttConsts C,
+                          uint32_t* __restrict__ A) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over S * 2 G'
+  if (idx >= (int64_t)S * 2 * Gp) return;
+  const int col = (int)(idx / (2 * Gp));
+  const int64_t e = idx - (int64_t)col * 2 * Gp;
+  const int64_t n = 1ll << logn, h = n >> 1;
+  const int64_t child = e >> logn, k = e & (n - 1);
+  int64_t d = G - child * h;
+  d = d < 0 ? 0 : (d > h ? h : d);
+  const uint64_t x = k < d ? Nprev[(int64_t)col * Gp + child * h + k] : 0;
+  uint32_t* out = A + (int64_t)col * kNP * 2 * Gp + e;
+#pragma unroll
+  for (int i = 0; i < kNP; i++) out[(int64_t)i * 2 * Gp] = k < d ? residue64(x, C, i) : 0u;
+}
+__global__ void k_up_mul(const uint32_t* __restrict__ A, const uint32_t* __restrict__ spec, int S, int64_t Gp, int logn,
+                         NttConsts C, uint32_t* __restrict__ Z) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP * G'
+  if (idx >= (int64_t)kNP * Gp) return;
+  const int i = (int)(idx / Gp);
+  const int64_t e = idx - (int64_t)i * Gp;
+  const uint32_t q = C.q[i], qi = C.qinv[i];
+  const int64_t n = 1ll << logn;
+  const int64_t P = e >> logn, k = e & (n - 1);
+  const uint32_t* sp = spec + (int64_t)i * 2 * Gp + (2 * P << logn) + k;
+  const uint32_t sL = sub_if(sp[0], 2 * q), sR = sub_if(sp[n], 2 * q);
+  for (int col = 0; col < S; col++) {
+    const uint32_t* a = A + ((int64_t)col * kNP + i) * 2 * Gp + (2 * P << logn) + k;
+    const uint32_t z = mont32(sub_if(a[0], 2 * q), sR, q, qi) + mont32(sub_if(a[n], 2 * q), sL, q, qi);
+    Z[((int64_t)col * kNP + i) * Gp + e] = z;
+  }
+}
+__global__ void k_up_crt(const uint32_t* __restrict__ Z, int S, int64_t G, int64_t Gp, int logn, NttConsts C,
+                         CrtScale sc, Mod M, uint64_t* __restrict__ Nout) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over S * G'
+  if (idx >= (int64_t)S * Gp) return;
+  const int col = (int)(idx / Gp);
+  const int64_t e = idx - (int64_t)col * Gp;
+  const int64_t n = 1ll << logn;
+  const int64_t P = e >> logn, k = e & (n - 1);
+  int64_t d = G - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  if (k >= d) return;
+  uint32_t res[kNP];
+#pragma unroll
+  for (int i = 0; i < kNP; i++)
+    res[i] = shoup32(Z[((int64_t)col * kNP + i) * Gp + e], sc.s[i], sc.sp[i], C.q[i]);
+  Nout[idx] = crt_to_p(res, C, M);
+}
+
+// The expansions: A[s][i][t] = N_s[G - 1 - t] (t < na), B = g (T terms), both
+// transformed at size 2^logn; Z[s] = A[s] B; out[s][t] = Z[s][t], t < T.
+__global__ void k_rows_load(const uint64_t* __restrict__ N, int S, int64_t G, int64_t Gp, int64_t na, int logn,
+                            NttConsts C, uint32_t* __restrict__ A) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over S 2^logn
+  if (idx >= ((int64_t)S << logn)) return;
+  const int col = (int)(idx >> logn);
+  const int64_t t = idx & ((1ll << logn) - 1);
+  const uint64_t x = t < na ? N[(int64_t)col * Gp + G - 1 - t] : 0;
+  uint32_t* out = A + ((int64_t)col * kNP << logn) + t;
+#pragma unroll
+  for (int i = 0; i < kNP; i++) out[(int64_t)i << logn] = t < na ? residue64(x, C, i) : 0u;
+}
+__global__ void k_rows_mul(uint32_t* __restrict__ A, const uint32_t* __restrict__ B, int S, int logn, NttConsts C) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP 2^logn
+  if (idx >= ((int64_t)kNP << logn)) return;
+  const int i = (int)(idx >> logn);
+  const uint32_t q = C.q[i], qi = C.qinv[i];
+  const uint32_t b = sub_if(B[idx], 2 * q);
+  for (int col = 0; col < S; col++) {
+    uint32_t* a = A + ((int64_t)col * kNP << logn) + idx;
+    *a = mont32(sub_if(*a, 2 * q), b, q, qi);
+  }
+}
+__global__ void k_rows_crt(const uint32_t* __restrict__ Z, int S, int64_t T, int logn, NttConsts C, CrtScale sc,
+                           Mod M, uint64_t* __restrict__ out, int64_t ldo) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over S T
+  if (idx >= (int64_t)S * T) return;
+  const int col = (int)(idx / T);
+  const int64_t t = idx - (int64_t)col * T;
+  uint32_t res[kNP];
+#pragma unroll
+  for (int i = 0; i < kNP; i++)
+    res[i] = shoup32(Z[(((int64_t)col * kNP + i) << logn) + t], sc.s[i], sc.sp[i], C.q[i]);
+  out[(int64_t)col * ldo + t] = crt_to_p(res, C, M);
+}
+
 // ---- host side ---------------------------------------------------------------------
 
 uint32_t h_pow32(uint64_t a, uint64_t e, uint64_t q) {
@@ -782,6 +996,8 @@ FastWs carve_fast(Carver& cv, int64_t T, int R) {
   return w;
 }
 
+void configure_fused();
+
 struct FastRun {
   zr_ctx* ctx;
   const NttConsts& C;
@@ -789,6 +1005,16 @@ struct FastRun {
   const uint2 *tw, *itw;
   int logN;
   cudaStream_t st;
+  // subproduct tree over the T roots v: coef[l] (levels 7 .. 7 + Lt, T' =
+  // 128 2^Lt words each) and the children's spectra spec[l - 1] (kNP 2T'
+  // words each); Z: kNP T' words of scratch
+  void tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::vector<uint64_t*>& coef,
+            const std::vector<uint32_t*>& spec, uint32_t* Z);
+  // g = 1 / f mod z^prec (f_0 = 1, nf coefficients): Newton's iteration, the
+  // first steps in one CTA; g holds 2 prec words, e prec words, A, B, Z
+  // kNP 2^ceil(log2(2 prec)) words each
+  void inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, uint64_t* e, uint32_t* A, uint32_t* B,
+               uint32_t* Z);
   // out[t] = +-(a * b mod (z^N - 1))[lo + t], t < cnt; N = 2^logn
   void cyc(const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb, int logn, int64_t lo, int64_t cnt, bool neg,
            uint32_t* A, uint32_t* B, uint32_t* Z, uint64_t* out) {
@@ -805,6 +1031,100 @@ struct FastRun {
     note_launch();
   }
 };
+
+void configure_fused() {
+  static DeviceOnce fused_attr;
+  fused_attr.run([] {
+    const int bytes = (int)(sizeof(uint32_t) * 2 * kNP * kFusedMax);
+    cudaFuncSetAttribute(k_tree_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_desc_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_up_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_newton_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_up_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(uint64_t) * 2 * kLeaf * (1 + kFastProbeMaxS)));
+  });
+}
+
+void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::vector<uint64_t*>& coef,
+                   const std::vector<uint32_t*>& spec, uint32_t* Z) {
+  const int logT = kLeafLog + Lt;
+  k_fast_leafpoly<<<cdivu(T, kLeaf), kLeaf, 0, st>>>(v, T, M, coef[0]);
+  note_launch();
+  for (int l = 1; l <= Lt; l++) {
+    const int logn = kLeafLog + l;
+    uint32_t* sp = spec[l - 1];
+    if (logn <= kFusedLog) {
+      const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
+      const int npc = fused_npc(logn);
+      k_tree_fused<<<(unsigned)((nodes + npc - 1) / npc), kFusedThreads,
+                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(coef[l - 1], T, Tp, logn, C, crt_scale(logn), M,
+                                                                     tw, logN, sp, coef[l], nodes);
+      note_launch();
+      continue;
+    }
+    k_tree_load<<<cdivu(kNP * 2 * Tp, 256), 256, 0, st>>>(coef[l - 1], T, Tp, logn, C, sp);
+    note_launch();
+    launch_ntt(sp, (kNP * 2 * Tp) >> logn, logn, logT + 1, false, tw, itw, logN, C, st);
+    k_tree_mul<<<cdivu(kNP * Tp, 256), 256, 0, st>>>(sp, Tp, logn, C, Z);
+    note_launch();
+    launch_ntt(Z, (kNP * Tp) >> logn, logn, logT, true, tw, itw, logN, C, st);
+    k_tree_crt<<<cdivu(Tp, 256), 256, 0, st>>>(Z, T, Tp, logn, C, crt_scale(logn), M, coef[l]);
+    note_launch();
+  }
+}
+
+void FastRun::inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, uint64_t* e, uint32_t* A,
+                      uint32_t* B, uint32_t* Z) {
+  const int logK0 = std::min(ilog2(prec), kFusedLog);
+  k_newton_fused<<<1, kFusedThreads, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(f, nf, logK0, C, M, tw, logN, g, e);
+  note_launch();
+  for (int64_t k = 1ll << logK0; k < prec; k *= 2) {
+    const int logk2 = ilog2(2 * k);
+    const int64_t fn = std::min<int64_t>(2 * k, nf);
+    // e = f g: its coefficients k .. 2k-1 (the low ones are 1, 0, ..)
+    cyc(f, fn, g, k, logk2, k, k, false, A, B, Z, e);
+    // g_{k..2k} = -(g e_hi mod z^k)
+    cyc(g, k, e, k, logk2, 0, k, true, A, B, Z, g + k);
+  }
+}
+
+// Workspace of the fast evaluator, carved in order: the tree over the G'
+// padded roots, the numerators (two ping-pong sets of S rows), the transform
+// planes of the up levels and of the final products, Newton's buffers.
+struct ProbeWs {
+  int64_t Gp = 0, Pp = 0;
+  int Lt = 0, logR = 0;
+  std::vector<uint64_t*> coef;
+  std::vector<uint32_t*> spec;
+  uint64_t *N0 = nullptr, *N1 = nullptr, *f = nullptr, *g = nullptr, *e = nullptr;
+  uint32_t *A = nullptr, *Z = nullptr, *Bg = nullptr, *A2 = nullptr, *B2 = nullptr, *Z2 = nullptr;
+};
+
+ProbeWs carve_probes(Carver& cv, int64_t G, int64_t T, int S) {
+  ProbeWs w;
+  while ((int64_t)kLeaf << w.Lt < G) w.Lt++;
+  w.Gp = (int64_t)kLeaf << w.Lt;
+  w.Pp = 1;
+  while (w.Pp < T) w.Pp *= 2;
+  w.logR = ilog2(2 * w.Pp);
+  const int64_t Gp = w.Gp, R2 = 2 * w.Pp;
+  for (int l = 0; l <= w.Lt; l++) w.coef.push_back(cv.take<uint64_t>(Gp));
+  for (int l = 1; l <= w.Lt; l++) w.spec.push_back(cv.take<uint32_t>((size_t)kNP * 2 * Gp));
+  w.N0 = cv.take<uint64_t>((size_t)S * Gp);
+  w.N1 = cv.take<uint64_t>((size_t)S * Gp);
+  // up levels: S kNP 2G' (children) and S kNP G' (products); the final
+  // products reuse A (S kNP 2P' words)
+  w.A = cv.take<uint32_t>((size_t)S * kNP * std::max(2 * Gp, R2));
+  w.Z = cv.take<uint32_t>((size_t)std::max<int64_t>(S, 1) * kNP * Gp);
+  w.Bg = cv.take<uint32_t>((size_t)kNP * R2);
+  w.f = cv.take<uint64_t>(Gp + 1);
+  w.g = cv.take<uint64_t>(R2);
+  w.e = cv.take<uint64_t>(w.Pp);
+  w.A2 = cv.take<uint32_t>((size_t)kNP * R2);
+  w.B2 = cv.take<uint32_t>((size_t)kNP * R2);
+  w.Z2 = cv.take<uint32_t>((size_t)kNP * std::max(R2, Gp));
+  return w;
+}
 
 }  // namespace
 
@@ -892,55 +1212,14 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   const int logN = ctx->ntt_logN;
   FastRun F{ctx, C, M, tw, itw, logN, st};
 
-  static DeviceOnce fused_attr;
-  fused_attr.run([] {
-    const int bytes = (int)(sizeof(uint32_t) * 2 * kNP * kFusedMax);
-    cudaFuncSetAttribute(k_tree_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_desc_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_newton_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  });
-  // tree: leaf blocks, then levels 8 .. 7 + Lt
-  k_fast_leafpoly<<<cdivu(T, kLeaf), kLeaf, 0, st>>>(v, T, M, w.coef[0]);
-  note_launch();
-  for (int l = 1; l <= Lt; l++) {
-    const int logn = kLeafLog + l;
-    uint32_t* spec = w.spec[l - 1];
-    if (logn <= kFusedLog) {
-      const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
-      const int npc = fused_npc(logn);
-      k_tree_fused<<<(unsigned)((nodes + npc - 1) / npc), kFusedThreads,
-                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(w.coef[l - 1], T, Tp, logn, C, crt_scale(logn),
-                                                                     M, tw, logN, spec, w.coef[l], nodes);
-      note_launch();
-      continue;
-    }
-    k_tree_load<<<cdivu(kNP * 2 * Tp, 256), 256, 0, st>>>(w.coef[l - 1], T, Tp, logn, C, spec);
-    note_launch();
-    launch_ntt(spec, (kNP * 2 * Tp) >> logn, logn, logT + 1, false, tw, itw, logN, C, st);
-    k_tree_mul<<<cdivu(kNP * Tp, 256), 256, 0, st>>>(spec, Tp, logn, C, w.Z);
-    note_launch();
-    launch_ntt(w.Z, (kNP * Tp) >> logn, logn, logT, true, tw, itw, logN, C, st);
-    k_tree_crt<<<cdivu(Tp, 256), 256, 0, st>>>(w.Z, T, Tp, logn, C, crt_scale(logn), M, w.coef[l]);
-    note_launch();
-  }
+  configure_fused();
+  F.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
   const uint64_t* m = w.coef[Lt];   // M without its leading 1
 
   // power sums: g = 1 / rev(M) mod z^T by Newton's iteration, ps = rev(M') g
   k_rev_poly<<<cdivu(T + 1, 256), 256, 0, st>>>(m, T, M, w.f, w.rd, w.g);
   note_launch();
-  // the first steps (precision up to kFusedMax) in one CTA
-  const int logK0 = std::min(ilog2(T), kFusedLog);
-  k_newton_fused<<<1, kFusedThreads, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(w.f, T + 1, logK0, C, M, tw, logN,
-                                                                             w.g, w.e);
-  note_launch();
-  for (int64_t k = 1ll << logK0; k < T; k *= 2) {
-    const int logk2 = ilog2(2 * k);
-    const int64_t fn = std::min<int64_t>(2 * k, T + 1);
-    // e = f g: its coefficients k .. 2k-1 (the low ones are 1, 0, ..)
-    F.cyc(w.f, fn, w.g, k, logk2, k, k, false, w.A, w.B, w.Z, w.e);
-    // g_{k..2k} = -(g e_hi mod z^k)
-    F.cyc(w.g, k, w.e, k, logk2, 0, k, true, w.A, w.B, w.Z, w.g + k);
-  }
+  F.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
   F.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
 
   // descent from the root (node size T') to the leaf blocks
@@ -981,6 +1260,79 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   k_fast_leafval<<<cdivu(T, kLeaf), kLeaf, smem, st>>>(w.coef[0], X, R, T, Tp, v, vp, M, part, T, den);
   note_launch();
   return cuda_err(ctx, cudaGetLastError(), "fast solve");
+}
+
+size_t fast_probes_ws_need(int64_t G, int64_t T, int S) {
+  Carver m0(nullptr);
+  carve_probes(m0, G, T, S);
+  return m0.off + 256;
+}
+
+// out[s ldo + i] = sum_{g < G} W[s ldw + g] U[g]^i, i < T (1 <= G, T <= 2^21,
+// S <= 256): the tree over U, the numerators N_s bottom-up, Newton's inverse
+// of rev(M) to precision T, and the S products rev(N_s) / rev(M) mod z^T.
+zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const uint64_t* W, int64_t ldw, int S,
+                              int64_t T, uint64_t* out, int64_t ldo, char* ws, cudaStream_t st) {
+  Carver cv(ws);
+  ProbeWs w = carve_probes(cv, G, T, S);
+  const int64_t Gp = w.Gp;
+  const int Lt = w.Lt;
+  const int logG = kLeafLog + Lt;
+  zr_status r = ensure_ntt_tables(ctx, std::max(logG + 1, w.logR), st);
+  if (r) return r;
+  const NttConsts& C = ctx->ntt;
+  const Mod& M = ctx->M;
+  const uint2* tw = reinterpret_cast<const uint2*>(ctx->ntt_tw);
+  const uint2* itw = tw + ((size_t)kNP << ctx->ntt_logN);
+  const int logN = ctx->ntt_logN;
+  FastRun F{ctx, C, M, tw, itw, logN, st};
+  configure_fused();
+  F.tree(U, G, Gp, Lt, w.coef, w.spec, w.Z2);
+
+  // numerators: leaf blocks, then the levels up to the root
+  k_up_leaf<<<cdivu(G, kLeaf), kLeaf, sizeof(uint64_t) * 2 * kLeaf * (1 + S), st>>>(U, G, W, ldw, S, M, w.N0, Gp);
+  note_launch();
+  uint64_t* Nc = w.N0;
+  uint64_t* Nn = w.N1;
+  for (int l = 1; l <= Lt; l++) {
+    const int logn = kLeafLog + l;
+    const int64_t nodes = (G + (1ll << logn) - 1) >> logn;
+    if (logn <= kFusedLog) {
+      const int npc = fused_npc(logn);
+      k_up_fused<<<(unsigned)((nodes + npc - 1) / npc * S), kFusedThreads, sizeof(uint32_t) * 2 * kNP * npc << logn,
+                   st>>>(Nc, G, Gp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Nn, nodes);
+      note_launch();
+    } else {
+      k_up_load<<<cdivu((int64_t)S * 2 * Gp, 256), 256, 0, st>>>(Nc, S, G, Gp, logn, C, w.A);
+      note_launch();
+      launch_ntt(w.A, ((int64_t)S * kNP * 2 * Gp) >> logn, logn, logG + 1, false, tw, itw, logN, C, st);
+      k_up_mul<<<cdivu((int64_t)kNP * Gp, 256), 256, 0, st>>>(w.A, w.spec[l - 1], S, Gp, logn, C, w.Z);
+      note_launch();
+      launch_ntt(w.Z, ((int64_t)S * kNP * Gp) >> logn, logn, logG, true, tw, itw, logN, C, st);
+      k_up_crt<<<cdivu((int64_t)S * Gp, 256), 256, 0, st>>>(w.Z, S, G, Gp, logn, C, crt_scale(logn), M, Nn);
+      note_launch();
+    }
+    std::swap(Nc, Nn);
+  }
+
+  // 1 / rev(M) to precision T, then rev(N_s) times it, the first T terms
+  k_rev_poly<<<cdivu(G + 1, 256), 256, 0, st>>>(w.coef[Lt], G, M, w.f, nullptr, w.g);
+  note_launch();
+  F.inverse(w.f, G + 1, T, w.g, w.e, w.A2, w.B2, w.Z2);
+  const int logR = w.logR;
+  const int64_t na = std::min(G, T);
+  k_rows_load<<<cdivu((int64_t)S << logR, 256), 256, 0, st>>>(Nc, S, G, Gp, na, logR, C, w.A);
+  note_launch();
+  k_cyc_load<<<cdivu((int64_t)kNP << logR, 256), 256, 0, st>>>(w.g, T, logR, C, w.Bg);
+  note_launch();
+  launch_ntt(w.A, (int64_t)S * kNP, logR, logR, false, tw, itw, logN, C, st);
+  launch_ntt(w.Bg, kNP, logR, logR, false, tw, itw, logN, C, st);
+  k_rows_mul<<<cdivu((int64_t)kNP << logR, 256), 256, 0, st>>>(w.A, w.Bg, S, logR, C);
+  note_launch();
+  launch_ntt(w.A, (int64_t)S * kNP, logR, logR, true, tw, itw, logN, C, st);
+  k_rows_crt<<<cdivu((int64_t)S * T, 256), 256, 0, st>>>(w.A, S, T, logR, C, crt_scale(logR), M, out, ldo);
+  note_launch();
+  return cuda_err(ctx, cudaGetLastError(), "fast probes");
 }
 
 }  // namespace zr

@@ -64,6 +64,10 @@ struct zr_ctx {
   int ntt_logN = 0;
   int solve_method = 0;            // 0: by size, 1: quadratic, 2: fast where supported
   int64_t fast_min_T = 0;          // size from which method 0 takes the fast path (0: built-in default)
+  // workspace of the fast probe evaluator, sized once the group count is
+  // known (grow-only, separate from the step workspace)
+  char* fprobe_ws = nullptr;
+  size_t fprobe_cap = 0;
   std::string err;
   std::mutex mu;                // guards err for the serve thread
 };
@@ -160,6 +164,14 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
                              int64_t ldb, uint64_t* part, uint64_t* den, char* ws, cudaStream_t st);
 // whether a system of T unknowns takes the fast path in this context
 bool use_fast_solve(const zr_ctx* ctx, int64_t T);
+// whether T probes of a function of Tf terms take the fast evaluator (the
+// transposed tree), which reads the group count G <= Tf on the host and
+// falls back to the matrix-vector kernel when G > kFastMaxT
+constexpr int kFastProbeMaxS = 64;            // columns of the fast evaluator
+bool use_fast_probes(const zr_ctx* ctx, int64_t T, int64_t Tf, int S);
+size_t fast_probes_ws_need(int64_t G, int64_t T, int S);
+zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const uint64_t* W, int64_t ldw, int S,
+                              int64_t T, uint64_t* out, int64_t ldo, char* ws, cudaStream_t st);
 
 // evaluator (zr_eval.cu)
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);

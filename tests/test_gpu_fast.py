@@ -150,3 +150,42 @@ def test_solve_method_arguments(ctx):
     for bad in ((3, 0), (-1, 0), (0, -5)):
         with pytest.raises(zr.ZrError):
             ctx.solve_method(*bad)
+
+
+@pytest.mark.parametrize("seed,T,k,maxe,S,off", [(61, 1, 2, 5, 3, 0), (62, 37, 2, 9, 5, 1), (63, 300, 3, 6, 9, 0),
+                                                 (64, 2000, 4, 12, 21, 1), (65, 9000, 5, 20, 4, 0)])
+def test_fast_probes_match_oracle(ctx, orc, seed, T, k, maxe, S, off):
+    """Probes by the transposed tree (weighted power sums rev(N)/rev(M)) equal
+    the oracle's and the matrix-vector evaluator's element by element."""
+    wl = W.step_workload(seed, T, k, maxe, S)
+    fe, fc = d8(wl.exps), d64(wl.coef)
+    f = ctx.poly(wl.nv, wl.exps.shape[0], fe, fc)
+    y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
+    got = {}
+    for method in (ctx.SOLVE_FAST, ctx.SOLVE_QUADRATIC):
+        b = zeros64(S, T + 3)
+        ctx.solve_method(method)
+        try:
+            ctx.zippel_probes(f, wl.k, y, S, cs, z, T, off, b, T + 3)
+        finally:
+            ctx.solve_method(0)
+        got[method] = h64(b)[:, :T]
+    want = orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, T, offset=off)
+    assert np.array_equal(got[ctx.SOLVE_FAST], want)
+    assert np.array_equal(got[ctx.SOLVE_QUADRATIC], want)
+
+
+def test_fast_probes_few_groups(ctx, orc):
+    """Many terms sharing few anchor monomials (G much smaller than T and Tf)."""
+    wl = W.step_workload(66, 3, 2, 1, 7)     # 3 skeleton terms, 7 samples: G = 3 groups of 7 terms
+    fe, fc = d8(wl.exps), d64(wl.coef)
+    f = ctx.poly(wl.nv, wl.exps.shape[0], fe, fc)
+    y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
+    T = 5000
+    b = zeros64(wl.S, T)
+    ctx.solve_method(ctx.SOLVE_FAST)
+    try:
+        ctx.zippel_probes(f, wl.k, y, wl.S, cs, z, T, 0, b, T)
+    finally:
+        ctx.solve_method(0)
+    assert np.array_equal(h64(b), orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, T))
