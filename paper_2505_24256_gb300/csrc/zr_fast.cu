@@ -137,23 +137,26 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict_
     const int s = INV ? (logn - 1 - step) : (s_lo + step);
     const int lt = logn - s - 1;                      // log2 t
     const uint32_t m = 1u << s;
-    // all of a thread's twiddles first, so that their loads overlap
-    uint2 w[kNttPer];
+    // a thread's twiddles in batches of eight, so that their loads overlap
 #pragma unroll
-    for (int r = 0; r < kNttPer; r++) {
-      const int b = threadIdx.x + r * kNttThreads;
-      const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-      const int prime = uniform ? pb5 : (pb5 + (pos >> plane_log)) % kNP;
-      const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
-      w[r] = b < half ? __ldg(&tw[((int64_t)prime << logN) + m + grp]) : make_uint2(0, 0);
-    }
+    for (int r0 = 0; r0 < kNttPer; r0 += 8) {
+      uint2 w[8];
 #pragma unroll
-    for (int r = 0; r < kNttPer; r++) {
-      const int b = threadIdx.x + r * kNttThreads;
-      if (b < half) {
+      for (int r = 0; r < 8; r++) {
+        const int b = threadIdx.x + (r0 + r) * kNttThreads;
         const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
         const int prime = uniform ? pb5 : (pb5 + (pos >> plane_log)) % kNP;
-        butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], w[r], C.q[prime]);
+        const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
+        w[r] = b < half ? __ldg(&tw[((int64_t)prime << logN) + m + grp]) : make_uint2(0, 0);
+      }
+#pragma unroll
+      for (int r = 0; r < 8; r++) {
+        const int b = threadIdx.x + (r0 + r) * kNttThreads;
+        if (b < half) {
+          const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
+          const int prime = uniform ? pb5 : (pb5 + (pos >> plane_log)) % kNP;
+          butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], w[r], C.q[prime]);
+        }
       }
     }
     __syncthreads();
@@ -377,7 +380,8 @@ __global__ void k_rev_poly(const uint64_t* __restrict__ m, int64_t T, Mod M, uin
 
 constexpr int kFusedLog = 12;
 constexpr int kFusedMax = 1 << kFusedLog;
-constexpr int kFusedThreads = 512;
+constexpr int kFusedThreads = 256;
+constexpr int kNewtonThreadsF = 1024;   // the single-CTA Newton kernel
 
 // ntr transforms of size 2^logn at sm + t 2^logn, transform t modulo prime
 // t mod 5; forward (CT) or inverse (GS) stages, as k_ntt_local.
@@ -389,19 +393,19 @@ __device__ void smem_ntt(uint32_t* sm, int ntr, int logn, const uint2* __restric
     const int s = INV ? (logn - 1 - step) : step;
     const int lt = logn - s - 1;
     const uint32_t m = 1u << s;
-    for (int i0 = 0; i0 < total; i0 += 8 * kFusedThreads) {
-      uint2 w[8];
+    for (int i0 = 0; i0 < total; i0 += 4 * (int)blockDim.x) {
+      uint2 w[4];
 #pragma unroll
-      for (int r = 0; r < 8; r++) {
-        const int idx = i0 + r * kFusedThreads + threadIdx.x;
+      for (int r = 0; r < 4; r++) {
+        const int idx = i0 + r * (int)blockDim.x + threadIdx.x;
         const int t = idx >> (logn - 1), b = idx & (half - 1);
         const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
         w[r] = idx < total ? __ldg(&tw[((int64_t)(t % kNP) << logN) + m + (uint32_t)(pos >> (lt + 1))])
                            : make_uint2(0, 0);
       }
 #pragma unroll
-      for (int r = 0; r < 8; r++) {
-        const int idx = i0 + r * kFusedThreads + threadIdx.x;
+      for (int r = 0; r < 4; r++) {
+        const int idx = i0 + r * (int)blockDim.x + threadIdx.x;
         if (idx < total) {
           const int t = idx >> (logn - 1), b = idx & (half - 1);
           const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
@@ -414,9 +418,10 @@ __device__ void smem_ntt(uint32_t* sm, int ntr, int logn, const uint2* __restric
   }
 }
 
-// Nodes a fused CTA takes at transform size 2^logn: enough for 2048
-// elements per prime (80 KB of shared memory, two CTAs per SM), at least one.
-__host__ __device__ inline int fused_npc(int logn) { return logn >= 11 ? 1 : (2048 >> logn); }
+// Nodes a fused CTA takes at transform size 2^logn: enough for 1024
+// elements per prime (40 KB of shared memory, so that four CTAs fit an SM),
+// at least one.
+__host__ __device__ inline int fused_npc(int logn) { return logn >= 10 ? 1 : (1024 >> logn); }
 
 // Tree level l <= kFusedLog, npc nodes P per CTA: the two children as full
 // monic polynomials -> spectra (kept in spec for the descent) -> product ->
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_desc_fused(const uint64_t* __
 // f_0 = 1, all in one CTA: for k = 1, 2, .., K/2, e = f g_k (its coefficients
 // k..2k-1, a cyclic product of size 2k), then g_{k..2k} = -(g_k e_hi mod z^k).
 // g (2K words) and e (K words) live in global memory; f has nf coefficients.
-__global__ void __launch_bounds__(kFusedThreads) k_newton_fused(const uint64_t* __restrict__ f, int64_t nf, int logK,
+__global__ void __launch_bounds__(kNewtonThreadsF) k_newton_fused(const uint64_t* __restrict__ f, int64_t nf, int logK,
                                                                 NttConsts C, Mod M, const uint2* __restrict__ tw,
                                                                 int logN, uint64_t* __restrict__ g,
                                                                 uint64_t* __restrict__ e) {
@@ -1076,7 +1081,8 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
 void FastRun::inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, uint64_t* e, uint32_t* A,
                       uint32_t* B, uint32_t* Z) {
   const int logK0 = std::min(ilog2(prec), kFusedLog);
-  k_newton_fused<<<1, kFusedThreads, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(f, nf, logK0, C, M, tw, logN, g, e);
+  k_newton_fused<<<1, kNewtonThreadsF, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(f, nf, logK0, C, M, tw, logN, g,
+                                                                                e);
   note_launch();
   for (int64_t k = 1ll << logK0; k < prec; k *= 2) {
     const int logk2 = ilog2(2 * k);
