@@ -137,25 +137,28 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict_
     const int s = INV ? (logn - 1 - step) : (s_lo + step);
     const int lt = logn - s - 1;                      // log2 t
     const uint32_t m = 1u << s;
-    // a thread's twiddles in batches of eight, so that their loads overlap
+    if (uniform) {
+      // one prime for the whole tile: the stage's twiddles start at twp
+      const uint2* __restrict__ twp = tw + ((int64_t)pb5 << logN) + m;
+      const uint32_t q = C.q[pb5];
 #pragma unroll
-    for (int r0 = 0; r0 < kNttPer; r0 += 8) {
-      uint2 w[8];
-#pragma unroll
-      for (int r = 0; r < 8; r++) {
-        const int b = threadIdx.x + (r0 + r) * kNttThreads;
-        const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-        const int prime = uniform ? pb5 : (pb5 + (pos >> plane_log)) % kNP;
-        const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
-        w[r] = b < half ? __ldg(&tw[((int64_t)prime << logN) + m + grp]) : make_uint2(0, 0);
-      }
-#pragma unroll
-      for (int r = 0; r < 8; r++) {
-        const int b = threadIdx.x + (r0 + r) * kNttThreads;
+      for (int r = 0; r < kNttPer; r++) {
+        const int b = threadIdx.x + r * kNttThreads;
         if (b < half) {
           const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-          const int prime = uniform ? pb5 : (pb5 + (pos >> plane_log)) % kNP;
-          butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], w[r], C.q[prime]);
+          const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
+          butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], __ldg(&twp[grp]), q);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < kNttPer; r++) {
+        const int b = threadIdx.x + r * kNttThreads;
+        if (b < half) {
+          const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
+          const int prime = (pb5 + (pos >> plane_log)) % kNP;
+          const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
+          butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], __ldg(&tw[((int64_t)prime << logN) + m + grp]), C.q[prime]);
         }
       }
     }
@@ -188,20 +191,13 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__
     const int s = INV ? (L1 - 1 - step) : step;
     const int lth = L1 - s - 1;                       // log2 of the row distance
     const uint32_t m = 1u << s;
-    uint2 w[kNttPer];
-#pragma unroll
-    for (int r = 0; r < kNttPer; r++) {
-      const int b = threadIdx.x + r * kNttThreads;
-      const int hb = b >> cwl;
-      const int h = ((hb >> lth) << (lth + 1)) | (hb & ((1 << lth) - 1));
-      w[r] = __ldg(&twp[m + (uint32_t)(h >> (lth + 1))]);
-    }
 #pragma unroll
     for (int r = 0; r < kNttPer; r++) {
       const int b = threadIdx.x + r * kNttThreads;
       const int c = b & (CW - 1), hb = b >> cwl;
       const int h = ((hb >> lth) << (lth + 1)) | (hb & ((1 << lth) - 1));
-      butterfly<INV>(&sm[(h << cwl) + c], &sm[((h + (1 << lth)) << cwl) + c], w[r], q);
+      butterfly<INV>(&sm[(h << cwl) + c], &sm[((h + (1 << lth)) << cwl) + c], __ldg(&twp[m + (uint32_t)(h >> (lth + 1))]),
+                     q);
     }
     __syncthreads();
   }
@@ -380,7 +376,7 @@ __global__ void k_rev_poly(const uint64_t* __restrict__ m, int64_t T, Mod M, uin
 
 constexpr int kFusedLog = 12;
 constexpr int kFusedMax = 1 << kFusedLog;
-constexpr int kFusedThreads = 256;
+constexpr int kFusedThreads = 512;
 constexpr int kNewtonThreadsF = 1024;   // the single-CTA Newton kernel
 
 // ntr transforms of size 2^logn at sm + t 2^logn, transform t modulo prime
@@ -394,23 +390,16 @@ __device__ void smem_ntt(uint32_t* sm, int ntr, int logn, const uint2* __restric
     const int lt = logn - s - 1;
     const uint32_t m = 1u << s;
     for (int i0 = 0; i0 < total; i0 += 4 * (int)blockDim.x) {
-      uint2 w[4];
-#pragma unroll
-      for (int r = 0; r < 4; r++) {
-        const int idx = i0 + r * (int)blockDim.x + threadIdx.x;
-        const int t = idx >> (logn - 1), b = idx & (half - 1);
-        const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-        w[r] = idx < total ? __ldg(&tw[((int64_t)(t % kNP) << logN) + m + (uint32_t)(pos >> (lt + 1))])
-                           : make_uint2(0, 0);
-      }
 #pragma unroll
       for (int r = 0; r < 4; r++) {
         const int idx = i0 + r * (int)blockDim.x + threadIdx.x;
         if (idx < total) {
           const int t = idx >> (logn - 1), b = idx & (half - 1);
           const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
+          const int prime = t % kNP;
           uint32_t* base = sm + (t << logn);
-          butterfly<INV>(base + pos, base + pos + (1 << lt), w[r], C.q[t % kNP]);
+          butterfly<INV>(base + pos, base + pos + (1 << lt),
+                         __ldg(&tw[((int64_t)prime << logN) + m + (uint32_t)(pos >> (lt + 1))]), C.q[prime]);
         }
       }
     }
@@ -418,10 +407,9 @@ __device__ void smem_ntt(uint32_t* sm, int ntr, int logn, const uint2* __restric
   }
 }
 
-// Nodes a fused CTA takes at transform size 2^logn: enough for 1024
-// elements per prime (40 KB of shared memory, so that four CTAs fit an SM),
-// at least one.
-__host__ __device__ inline int fused_npc(int logn) { return logn >= 10 ? 1 : (1024 >> logn); }
+// Nodes a fused CTA takes at transform size 2^logn.  One: packing several
+// small nodes into a CTA measured slower than one node per CTA.
+__host__ __device__ inline int fused_npc(int) { return 1; }
 
 // Tree level l <= kFusedLog, npc nodes P per CTA: the two children as full
 // monic polynomials -> spectra (kept in spec for the descent) -> product ->
