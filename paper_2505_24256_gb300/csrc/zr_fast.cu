@@ -107,13 +107,122 @@ __device__ __forceinline__ void butterfly(uint32_t* a, uint32_t* b, uint2 w, uin
   }
 }
 
+template <bool INV>
+__device__ __forceinline__ void butterfly_r(uint32_t& X, uint32_t& Y, uint2 w, uint32_t q) {
+  if (!INV) {
+    const uint32_t x = sub_if(X, 2 * q);
+    const uint32_t t = shoup32(Y, w.x, w.y, q);
+    X = x + t;
+    Y = x - t + 2 * q;
+  } else {
+    const uint32_t x = X, y = Y;
+    X = sub_if(x + y, 2 * q);
+    Y = shoup32(x - y + 2 * q, w.x, w.y, q);
+  }
+}
+
+// Shared-memory layout of the transform kernels: logical word x lives at
+// sw(x), its bank bits XORed with bits of its 32-word row (a permutation
+// within each row).  The register passes below touch words at strides 1, 8
+// and multiples of 32; with this swizzle each of those warp accesses, and
+// every run of 32 consecutive row-aligned words, hits 32 distinct banks.
+__device__ __forceinline__ int sw(int x) { return x ^ (((x >> 5) & 7) | ((x >> 3) & 24)); }
+
+// One pass of R <= 3 butterfly stages over groups of 2^R words held in
+// registers (a radix-2^R pass).  Forward (Cooley-Tukey) stages s .. s+R-1:
+// a group is the words a + i 2^u (u = lt - R + 1, lt = logn - 1 - s) of one
+// block of 2^(lt+1); stage s+j pairs words 2^(R-1-j) apart with the twiddle
+// of block (k 2^j + (i >> (R-j))) of that stage, k the group's block index.
+// Inverse (Gentleman-Sande) stages s .. s-R+1: the words a + i 2^lt of one
+// block of 2^(lt+R); stage s-j pairs words 2^j apart with the twiddle of
+// block (K 2^(R-1-j) + (i >> (j+1))).  Logical word x (from off) sits at
+// transform position (boff + x) mod 2^logn; prime_of(x) gives its prime.
+template <bool INV, int R, class PrimeOf>
+__device__ __forceinline__ void radix_pass(uint32_t* sm, int off, int len, int logn, int s, uint32_t boff,
+                                           const uint2* __restrict__ tw, int logN, const NttConsts& C,
+                                           PrimeOf prime_of) {
+  constexpr int NR = 1 << R;
+  const int lt = logn - 1 - s;
+  const int u = INV ? lt : lt - R + 1;           // log2 of the stride within a group
+  const int blog = INV ? lt + R : lt + 1;        // log2 of the group's block
+  const uint32_t pmask = (1u << logn) - 1;
+  const uint32_t m = 1u << s;
+  for (int g = threadIdx.x; g < (len >> R); g += blockDim.x) {
+    const int a = ((g >> u) << blog) + (g & ((1 << u) - 1));
+    const int prime = prime_of(a);
+    const uint32_t q = C.q[prime];
+    const uint32_t kb = ((boff + (uint32_t)a) & pmask) >> blog;
+    const uint2* __restrict__ twp = tw + ((int64_t)prime << logN);
+    uint2 w[NR - 1];
+    int wo = 0;
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+      const int cnt = INV ? (1 << (R - 1 - j)) : (1 << j);
+      const uint32_t base = INV ? (m >> j) + (kb << (R - 1 - j)) : (m << j) + (kb << j);
+#pragma unroll
+      for (int c = 0; c < cnt; c++) w[wo + c] = __ldg(&twp[base + c]);
+      wo += cnt;
+    }
+    uint32_t x[NR];
+#pragma unroll
+    for (int i = 0; i < NR; i++) x[i] = sm[sw(off + a + (i << u))];
+    wo = 0;
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+      const int hs = INV ? (1 << j) : (1 << (R - 1 - j));
+#pragma unroll
+      for (int i = 0; i < NR; i++)
+        if (!(i & hs)) butterfly_r<INV>(x[i], x[i + hs], w[wo + (INV ? (i >> (j + 1)) : (i >> (R - j)))], q);
+      wo += INV ? (1 << (R - 1 - j)) : (1 << j);
+    }
+#pragma unroll
+    for (int i = 0; i < NR; i++) sm[sw(off + a + (i << u))] = x[i];
+  }
+}
+
+// Stages s_lo .. logn-1 of the transforms in sm (logical words off ..
+// off + len), forward in increasing or inverse in decreasing stage order:
+// radix-8 passes, the leftover one or two stages as one pass on the
+// largest strides.  Callers synchronise before; the last pass is followed
+// by a barrier.
+template <bool INV, class PrimeOf>
+__device__ __forceinline__ void smem_stages(uint32_t* sm, int off, int len, int logn, int s_lo, uint32_t boff,
+                                            const uint2* __restrict__ tw, int logN, const NttConsts& C,
+                                            PrimeOf prime_of) {
+  const int rem = (logn - s_lo) % 3;
+  if (!INV) {
+    int s = s_lo;
+    if (rem == 1) {
+      radix_pass<false, 1>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      __syncthreads();
+    } else if (rem == 2) {
+      radix_pass<false, 2>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      __syncthreads();
+    }
+    for (s += rem; s < logn; s += 3) {
+      radix_pass<false, 3>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      __syncthreads();
+    }
+  } else {
+    int s = logn - 1;
+    for (; s - 2 >= s_lo; s -= 3) {
+      radix_pass<true, 3>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      __syncthreads();
+    }
+    if (rem == 2) {
+      radix_pass<true, 2>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      __syncthreads();
+    } else if (rem == 1) {
+      radix_pass<true, 1>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      __syncthreads();
+    }
+  }
+}
+
 // A tile of kNttTile elements starting at `base` (a multiple of kNttTile):
 // the transform of an element is prime (base >> plane_log) + (pos >>
-// plane_log) mod 5 (planes are powers of two, at most or at least a tile).
-// Each thread takes kNttPer butterflies per stage, unrolled, so that their
-// twiddle loads are in flight together.
-constexpr int kNttPer = kNttTile / 2 / kNttThreads;
-
+// plane_log) mod 5 (planes are powers of two, at most or at least a tile);
+// the tile runs the stages s_lo .. logn-1 that stay inside it.
 template <bool INV>
 __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict__ data, int64_t total, int logn,
                                                            int plane_log, int s_lo, const uint2* __restrict__ tw,
@@ -123,54 +232,35 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict_
   const int len = (int)((total - base) < kNttTile ? (total - base) : kNttTile);
   if ((len & 3) == 0) {
     const uint4* src = reinterpret_cast<const uint4*>(data + base);
-    for (int e = threadIdx.x; e < (len >> 2); e += kNttThreads) reinterpret_cast<uint4*>(sm)[e] = src[e];
+    for (int e = threadIdx.x; e < (len >> 2); e += kNttThreads) {
+      const uint4 v = src[e];
+      sm[sw(4 * e)] = v.x;
+      sm[sw(4 * e + 1)] = v.y;
+      sm[sw(4 * e + 2)] = v.z;
+      sm[sw(4 * e + 3)] = v.w;
+    }
   } else {
-    for (int e = threadIdx.x; e < len; e += kNttThreads) sm[e] = data[base + e];
+    for (int e = threadIdx.x; e < len; e += kNttThreads) sm[sw(e)] = data[base + e];
   }
   __syncthreads();
-  const int half = len >> 1;
-  const int nst = logn - s_lo;
   const int pb5 = (int)((base >> plane_log) % kNP);   // the tile's first plane, modulo 5
-  const bool uniform = plane_log >= kNttTileLog;
   const uint32_t boff = (uint32_t)(base & ((1ll << logn) - 1));   // the tile's offset within its transform
-  for (int step = 0; step < nst; step++) {
-    const int s = INV ? (logn - 1 - step) : (s_lo + step);
-    const int lt = logn - s - 1;                      // log2 t
-    const uint32_t m = 1u << s;
-    if (uniform) {
-      // one prime for the whole tile: the stage's twiddles start at twp
-      const uint2* __restrict__ twp = tw + ((int64_t)pb5 << logN) + m;
-      const uint32_t q = C.q[pb5];
-#pragma unroll
-      for (int r = 0; r < kNttPer; r++) {
-        const int b = threadIdx.x + r * kNttThreads;
-        if (b < half) {
-          const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-          const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
-          butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], __ldg(&twp[grp]), q);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < kNttPer; r++) {
-        const int b = threadIdx.x + r * kNttThreads;
-        if (b < half) {
-          const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-          const int prime = (pb5 + (pos >> plane_log)) % kNP;
-          const uint32_t grp = ((boff + (uint32_t)pos) & ((1u << logn) - 1)) >> (lt + 1);
-          butterfly<INV>(&sm[pos], &sm[pos + (1 << lt)], __ldg(&tw[((int64_t)prime << logN) + m + grp]), C.q[prime]);
-        }
-      }
-    }
-    __syncthreads();
-  }
+  if (plane_log >= kNttTileLog)
+    smem_stages<INV>(sm, 0, len, logn, s_lo, boff, tw, logN, C, [=](int) { return pb5; });
+  else
+    smem_stages<INV>(sm, 0, len, logn, s_lo, boff, tw, logN, C,
+                     [=](int x) { return (pb5 + (x >> plane_log)) % kNP; });
   if ((len & 3) == 0) {
     uint4* dst = reinterpret_cast<uint4*>(data + base);
-    for (int e = threadIdx.x; e < (len >> 2); e += kNttThreads) dst[e] = reinterpret_cast<const uint4*>(sm)[e];
+    for (int e = threadIdx.x; e < (len >> 2); e += kNttThreads)
+      dst[e] = make_uint4(sm[sw(4 * e)], sm[sw(4 * e + 1)], sm[sw(4 * e + 2)], sm[sw(4 * e + 3)]);
   } else {
-    for (int e = threadIdx.x; e < len; e += kNttThreads) data[base + e] = sm[e];
+    for (int e = threadIdx.x; e < len; e += kNttThreads) data[base + e] = sm[sw(e)];
   }
 }
+
+// The column kernel: each thread takes kNttPer butterflies per stage, unrolled.
+constexpr int kNttPer = kNttTile / 2 / kNttThreads;
 
 template <bool INV>
 __global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__ data, int logn, int plane_log, int L1,
@@ -379,32 +469,13 @@ constexpr int kFusedMax = 1 << kFusedLog;
 constexpr int kFusedThreads = 512;
 constexpr int kNewtonThreadsF = 1024;   // the single-CTA Newton kernel
 
-// ntr transforms of size 2^logn at sm + t 2^logn, transform t modulo prime
-// t mod 5; forward (CT) or inverse (GS) stages, as k_ntt_local.
+// ntr transforms of size 2^logn at logical words off + t 2^logn of sm (the
+// swizzled layout), transform t modulo prime t mod 5; forward (CT) or
+// inverse (GS) stages.
 template <bool INV>
-__device__ void smem_ntt(uint32_t* sm, int ntr, int logn, const uint2* __restrict__ tw, int logN, const NttConsts& C) {
-  const int half = 1 << (logn - 1);
-  const int total = ntr * half;
-  for (int step = 0; step < logn; step++) {
-    const int s = INV ? (logn - 1 - step) : step;
-    const int lt = logn - s - 1;
-    const uint32_t m = 1u << s;
-    for (int i0 = 0; i0 < total; i0 += 4 * (int)blockDim.x) {
-#pragma unroll
-      for (int r = 0; r < 4; r++) {
-        const int idx = i0 + r * (int)blockDim.x + threadIdx.x;
-        if (idx < total) {
-          const int t = idx >> (logn - 1), b = idx & (half - 1);
-          const int pos = ((b >> lt) << (lt + 1)) | (b & ((1 << lt) - 1));
-          const int prime = t % kNP;
-          uint32_t* base = sm + (t << logn);
-          butterfly<INV>(base + pos, base + pos + (1 << lt),
-                         __ldg(&tw[((int64_t)prime << logN) + m + (uint32_t)(pos >> (lt + 1))]), C.q[prime]);
-        }
-      }
-    }
-    __syncthreads();
-  }
+__device__ __forceinline__ void smem_ntt(uint32_t* sm, int off, int ntr, int logn, const uint2* __restrict__ tw,
+                                         int logN, const NttConsts& C) {
+  smem_stages<INV>(sm, off, ntr << logn, logn, 0, 0u, tw, logN, C, [=](int x) { return (x >> logn) % kNP; });
 }
 
 // Nodes a fused CTA takes at transform size 2^logn.  One: packing several
@@ -433,25 +504,25 @@ __global__ void __launch_bounds__(kFusedThreads) k_tree_fused(const uint64_t* __
     const uint64_t x = k < d ? below[child * h + k] : 0;
 #pragma unroll
     for (int i = 0; i < kNP; i++)
-      fsm[(((c * npc + a) * kNP + i) << logn) + k] = k < d ? residue64(x, C, i) : (k == d ? 1u : 0u);
+      fsm[sw((((c * npc + a) * kNP + i) << logn) + k)] = k < d ? residue64(x, C, i) : (k == d ? 1u : 0u);
   }
   __syncthreads();
-  smem_ntt<false>(fsm, 2 * kNP * npc, logn, tw, logN, C);
+  smem_ntt<false>(fsm, 0, 2 * kNP * npc, logn, tw, logN, C);
   for (int e = threadIdx.x; e < half; e += blockDim.x) {
     const int t = e >> logn, k = e & (n - 1);    // t = a kNP + i
     const int a = t / kNP, i = t - a * kNP;
     const int64_t P = P0 + a;
     const uint32_t q = C.q[i];
-    const uint32_t x = fsm[e], y = fsm[half + e];
+    const uint32_t x = fsm[sw(e)], y = fsm[sw(half + e)];
     if (P < nodes) {
       uint32_t* sp = spec + (int64_t)i * 2 * Tp + (2 * P << logn) + k;
       sp[0] = x;
       sp[n] = y;
     }
-    fsm[e] = mont32(sub_if(x, 2 * q), sub_if(y, 2 * q), q, C.qinv[i]);
+    fsm[sw(e)] = mont32(sub_if(x, 2 * q), sub_if(y, 2 * q), q, C.qinv[i]);
   }
   __syncthreads();
-  smem_ntt<true>(fsm, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+  smem_ntt<true>(fsm, 0, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
   for (int e = threadIdx.x; e < npc * n; e += blockDim.x) {
     const int a = e >> logn, k = e & (n - 1);
     const int64_t P = P0 + a;
@@ -460,7 +531,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_tree_fused(const uint64_t* __
     if (k >= d) continue;
     uint32_t res[kNP];
 #pragma unroll
-    for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[((a * kNP + i) << logn) + k], sc.s[i], sc.sp[i], C.q[i]);
+    for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[sw(((a * kNP + i) << logn) + k)], sc.s[i], sc.sp[i], C.q[i]);
     uint64_t x = crt_to_p(res, C, M);
     if (k == 0 && d == n) x = sub_mod(x, 1, M);
     coef[P * n + k] = x;
@@ -475,15 +546,13 @@ __global__ void __launch_bounds__(kFusedThreads) k_desc_fused(const uint64_t* __
                                                               const uint2* __restrict__ tw, int logN,
                                                               const uint32_t* __restrict__ spec,
                                                               uint64_t* __restrict__ Xn, int64_t nodes) {
-  extern __shared__ uint32_t fsm[];              // XH [node][prime][n], then Y [node][prime][n]
+  extern __shared__ uint32_t fsm[];              // XH [node][prime][n], then Y [node][prime][n] (logical words)
   const int npc = fused_npc(logn);
   const int64_t ctas = (nodes + npc - 1) / npc;
   const int64_t P0 = (int64_t)(blockIdx.x % ctas) * npc;
   const int r = (int)(blockIdx.x / ctas);
   const int n = 1 << logn, h = n >> 1;
   const int span = (npc * kNP) << logn;
-  uint32_t* XH = fsm;
-  uint32_t* Y = fsm + span;
   const uint64_t* x = X + (int64_t)r * Tp;
   for (int e = threadIdx.x; e < npc * n; e += blockDim.x) {
     const int a = e >> logn, k = e & (n - 1);
@@ -492,10 +561,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_desc_fused(const uint64_t* __
     d = d < 0 ? 0 : (d > n ? n : d);
     const uint64_t v = k < d ? x[P * n + d - 1 - k] : 0;
 #pragma unroll
-    for (int i = 0; i < kNP; i++) XH[((a * kNP + i) << logn) + k] = k < d ? residue64(v, C, i) : 0u;
+    for (int i = 0; i < kNP; i++) fsm[sw(((a * kNP + i) << logn) + k)] = k < d ? residue64(v, C, i) : 0u;
   }
   __syncthreads();
-  smem_ntt<false>(XH, npc * kNP, logn, tw, logN, C);
+  smem_ntt<false>(fsm, 0, npc * kNP, logn, tw, logN, C);
   for (int c = 0; c < 2; c++) {
     for (int e = threadIdx.x; e < span; e += blockDim.x) {
       const int t = e >> logn, k = e & (n - 1);
@@ -503,10 +572,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_desc_fused(const uint64_t* __
       const int64_t P = P0 + a;
       const uint32_t q = C.q[i];
       const uint32_t s = P < nodes ? spec[(int64_t)i * 2 * Tp + ((2 * P + (1 - c)) << logn) + k] : 0u;
-      Y[e] = mont32(sub_if(XH[e], 2 * q), sub_if(s, 2 * q), q, C.qinv[i]);
+      fsm[sw(span + e)] = mont32(sub_if(fsm[sw(e)], 2 * q), sub_if(s, 2 * q), q, C.qinv[i]);
     }
     __syncthreads();
-    smem_ntt<true>(Y, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+    smem_ntt<true>(fsm, span, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
     for (int e = threadIdx.x; e < npc * h; e += blockDim.x) {
       const int a = e / h, m = e - a * h;
       const int64_t P = P0 + a;
@@ -518,7 +587,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_desc_fused(const uint64_t* __
       uint32_t res[kNP];
 #pragma unroll
       for (int i = 0; i < kNP; i++)
-        res[i] = shoup32(Y[((a * kNP + i) << logn) + (d - 1 - m)], sc.s[i], sc.sp[i], C.q[i]);
+        res[i] = shoup32(fsm[sw(span + ((a * kNP + i) << logn) + (int)(d - 1 - m))], sc.s[i], sc.sp[i], C.q[i]);
       Xn[(int64_t)r * Tp + (2 * P + c) * h + m] = crt_to_p(res, C, M);
     }
     __syncthreads();
@@ -533,31 +602,30 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_fused(const uint64_t
                                                                 NttConsts C, Mod M, const uint2* __restrict__ tw,
                                                                 int logN, uint64_t* __restrict__ g,
                                                                 uint64_t* __restrict__ e) {
-  extern __shared__ uint32_t fsm[];              // A [prime][2k], B [prime][2k]
+  extern __shared__ uint32_t fsm[];              // A [prime][2k], then B [prime][2k] (logical words)
   if (threadIdx.x == 0) g[0] = 1;
   __syncthreads();
   for (int lk = 0; lk < logK; lk++) {
     const int k = 1 << lk, logn = lk + 1, n = 2 * k;
-    uint32_t* A = fsm;
-    uint32_t* B = fsm + (kNP << logn);
+    const int bo = kNP << logn;                  // B's first logical word
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const uint64_t fv = t < nf ? f[t] : 0;
       const uint64_t gv = t < k ? g[t] : 0;
 #pragma unroll
       for (int i = 0; i < kNP; i++) {
-        A[(i << logn) + t] = t < nf ? residue64(fv, C, i) : 0u;
-        B[(i << logn) + t] = t < k ? residue64(gv, C, i) : 0u;
+        fsm[sw((i << logn) + t)] = t < nf ? residue64(fv, C, i) : 0u;
+        fsm[sw(bo + (i << logn) + t)] = t < k ? residue64(gv, C, i) : 0u;
       }
     }
     __syncthreads();
-    smem_ntt<false>(fsm, 2 * kNP, logn, tw, logN, C);     // A and B are contiguous: ten transforms
+    smem_ntt<false>(fsm, 0, 2 * kNP, logn, tw, logN, C);  // A and B are contiguous: ten transforms
     for (int x = threadIdx.x; x < kNP * n; x += blockDim.x) {
       const int i = x >> logn;
       const uint32_t q = C.q[i];
-      A[x] = mont32(sub_if(A[x], 2 * q), sub_if(B[x], 2 * q), q, C.qinv[i]);
+      fsm[sw(x)] = mont32(sub_if(fsm[sw(x)], 2 * q), sub_if(fsm[sw(bo + x)], 2 * q), q, C.qinv[i]);
     }
     __syncthreads();
-    smem_ntt<true>(A, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+    smem_ntt<true>(fsm, 0, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
     // scale 2^32 / n per prime, computed here (n varies by step)
     uint32_t s[kNP], sp[kNP];
 #pragma unroll
@@ -571,28 +639,28 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_fused(const uint64_t
     for (int t = threadIdx.x; t < k; t += blockDim.x) {
       uint32_t res[kNP];
 #pragma unroll
-      for (int i = 0; i < kNP; i++) res[i] = shoup32(A[(i << logn) + k + t], s[i], sp[i], C.q[i]);
+      for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[sw((i << logn) + k + t)], s[i], sp[i], C.q[i]);
       e[t] = crt_to_p(res, C, M);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const uint64_t ev = t < k ? e[t] : 0;
 #pragma unroll
-      for (int i = 0; i < kNP; i++) A[(i << logn) + t] = t < k ? residue64(ev, C, i) : 0u;
+      for (int i = 0; i < kNP; i++) fsm[sw((i << logn) + t)] = t < k ? residue64(ev, C, i) : 0u;
     }
     __syncthreads();
-    smem_ntt<false>(A, kNP, logn, tw, logN, C);
+    smem_ntt<false>(fsm, 0, kNP, logn, tw, logN, C);
     for (int x = threadIdx.x; x < kNP * n; x += blockDim.x) {
       const int i = x >> logn;
       const uint32_t q = C.q[i];
-      A[x] = mont32(sub_if(A[x], 2 * q), sub_if(B[x], 2 * q), q, C.qinv[i]);
+      fsm[sw(x)] = mont32(sub_if(fsm[sw(x)], 2 * q), sub_if(fsm[sw(bo + x)], 2 * q), q, C.qinv[i]);
     }
     __syncthreads();
-    smem_ntt<true>(A, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+    smem_ntt<true>(fsm, 0, kNP, logn, tw + ((size_t)kNP << logN), logN, C);
     for (int t = threadIdx.x; t < k; t += blockDim.x) {
       uint32_t res[kNP];
 #pragma unroll
-      for (int i = 0; i < kNP; i++) res[i] = shoup32(A[(i << logn) + t], s[i], sp[i], C.q[i]);
+      for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[sw((i << logn) + t)], s[i], sp[i], C.q[i]);
       const uint64_t x = crt_to_p(res, C, M);
       g[k + t] = x ? M.p - x : 0;
     }
@@ -782,10 +850,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_up_fused(const uint64_t* __re
     d = d < 0 ? 0 : (d > h ? h : d);
     const uint64_t x = k < d ? src[child * h + k] : 0;
 #pragma unroll
-    for (int i = 0; i < kNP; i++) fsm[(((c * npc + a) * kNP + i) << logn) + k] = k < d ? residue64(x, C, i) : 0u;
+    for (int i = 0; i < kNP; i++) fsm[sw((((c * npc + a) * kNP + i) << logn) + k)] = k < d ? residue64(x, C, i) : 0u;
   }
   __syncthreads();
-  smem_ntt<false>(fsm, 2 * kNP * npc, logn, tw, logN, C);
+  smem_ntt<false>(fsm, 0, 2 * kNP * npc, logn, tw, logN, C);
   for (int e = threadIdx.x; e < half; e += blockDim.x) {
     const int t = e >> logn, k = e & (n - 1);
     const int a = t / kNP, i = t - a * kNP;
@@ -797,11 +865,12 @@ __global__ void __launch_bounds__(kFusedThreads) k_up_fused(const uint64_t* __re
       sL = sub_if(sp[0], 2 * q);
       sR = sub_if(sp[n], 2 * q);
     }
-    const uint32_t z = mont32(sub_if(fsm[e], 2 * q), sR, q, qi) + mont32(sub_if(fsm[half + e], 2 * q), sL, q, qi);
-    fsm[e] = z;                                  // < 2q
+    const uint32_t z =
+        mont32(sub_if(fsm[sw(e)], 2 * q), sR, q, qi) + mont32(sub_if(fsm[sw(half + e)], 2 * q), sL, q, qi);
+    fsm[sw(e)] = z;                              // < 2q
   }
   __syncthreads();
-  smem_ntt<true>(fsm, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
+  smem_ntt<true>(fsm, 0, npc * kNP, logn, tw + ((size_t)kNP << logN), logN, C);
   uint64_t* dst = Nout + (int64_t)col * Gp;
   for (int e = threadIdx.x; e < npc * n; e += blockDim.x) {
     const int a = e >> logn, k = e & (n - 1);
@@ -811,7 +880,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_up_fused(const uint64_t* __re
     if (k >= d) continue;
     uint32_t res[kNP];
 #pragma unroll
-    for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[((a * kNP + i) << logn) + k], sc.s[i], sc.sp[i], C.q[i]);
+    for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[sw(((a * kNP + i) << logn) + k)], sc.s[i], sc.sp[i], C.q[i]);
     dst[P * n + k] = crt_to_p(res, C, M);
   }
 }
