@@ -91,24 +91,10 @@ __global__ void k_ntt_tables(int logN, NttConsts C, uint2* __restrict__ tw, uint
 // elements (k_ntt_local); the first logn - 13 forward stages (last inverse
 // ones) act within columns of stride 2^13 (k_ntt_cols).
 
+// Harvey's butterflies with a Shoup twiddle: forward (CT) X, Y < 4q -> < 4q;
+// inverse (GS) X, Y < 2q -> < 2q.
 template <bool INV>
-__device__ __forceinline__ void butterfly(uint32_t* a, uint32_t* b, uint2 w, uint32_t q) {
-  const uint32_t X = *a, Y = *b;
-  if (!INV) {
-    // X, Y < 4q -> outputs < 4q
-    const uint32_t x = sub_if(X, 2 * q);
-    const uint32_t t = shoup32(Y, w.x, w.y, q);
-    *a = x + t;
-    *b = x - t + 2 * q;
-  } else {
-    // X, Y < 2q -> outputs < 2q
-    *a = sub_if(X + Y, 2 * q);
-    *b = shoup32(X - Y + 2 * q, w.x, w.y, q);
-  }
-}
-
-template <bool INV>
-__device__ __forceinline__ void butterfly_r(uint32_t& X, uint32_t& Y, uint2 w, uint32_t q) {
+__device__ __forceinline__ void butterfly(uint32_t& X, uint32_t& Y, uint2 w, uint32_t q) {
   if (!INV) {
     const uint32_t x = sub_if(X, 2 * q);
     const uint32_t t = shoup32(Y, w.x, w.y, q);
@@ -137,17 +123,22 @@ __device__ __forceinline__ int sw(int x) { return x ^ (((x >> 5) & 7) | ((x >> 3
 // block of 2^(lt+R); stage s-j pairs words 2^j apart with the twiddle of
 // block (K 2^(R-1-j) + (i >> (j+1))).  Logical word x (from off) sits at
 // transform position (boff + x) mod 2^logn; prime_of(x) gives its prime.
-template <bool INV, int R, class PrimeOf>
+// COLS: the buffer holds 2^cwl columns side by side instead (word x of
+// column c at x 2^cwl + c, no swizzle), one transform each; consecutive
+// threads take consecutive columns.
+template <bool INV, int R, bool COLS, class PrimeOf>
 __device__ __forceinline__ void radix_pass(uint32_t* sm, int off, int len, int logn, int s, uint32_t boff,
                                            const uint2* __restrict__ tw, int logN, const NttConsts& C,
-                                           PrimeOf prime_of) {
+                                           PrimeOf prime_of, int cwl) {
   constexpr int NR = 1 << R;
   const int lt = logn - 1 - s;
   const int u = INV ? lt : lt - R + 1;           // log2 of the stride within a group
   const int blog = INV ? lt + R : lt + 1;        // log2 of the group's block
   const uint32_t pmask = (1u << logn) - 1;
   const uint32_t m = 1u << s;
-  for (int g = threadIdx.x; g < (len >> R); g += blockDim.x) {
+  for (int g0 = threadIdx.x; g0 < (len >> R); g0 += blockDim.x) {
+    const int col = COLS ? (g0 & ((1 << cwl) - 1)) : 0;
+    const int g = COLS ? (g0 >> cwl) : g0;
     const int a = ((g >> u) << blog) + (g & ((1 << u) - 1));
     const int prime = prime_of(a);
     const uint32_t q = C.q[prime];
@@ -165,18 +156,18 @@ __device__ __forceinline__ void radix_pass(uint32_t* sm, int off, int len, int l
     }
     uint32_t x[NR];
 #pragma unroll
-    for (int i = 0; i < NR; i++) x[i] = sm[sw(off + a + (i << u))];
+    for (int i = 0; i < NR; i++) x[i] = sm[COLS ? (((a + (i << u)) << cwl) + col) : sw(off + a + (i << u))];
     wo = 0;
 #pragma unroll
     for (int j = 0; j < R; j++) {
       const int hs = INV ? (1 << j) : (1 << (R - 1 - j));
 #pragma unroll
       for (int i = 0; i < NR; i++)
-        if (!(i & hs)) butterfly_r<INV>(x[i], x[i + hs], w[wo + (INV ? (i >> (j + 1)) : (i >> (R - j)))], q);
+        if (!(i & hs)) butterfly<INV>(x[i], x[i + hs], w[wo + (INV ? (i >> (j + 1)) : (i >> (R - j)))], q);
       wo += INV ? (1 << (R - 1 - j)) : (1 << j);
     }
 #pragma unroll
-    for (int i = 0; i < NR; i++) sm[sw(off + a + (i << u))] = x[i];
+    for (int i = 0; i < NR; i++) sm[COLS ? (((a + (i << u)) << cwl) + col) : sw(off + a + (i << u))] = x[i];
   }
 }
 
@@ -185,35 +176,35 @@ __device__ __forceinline__ void radix_pass(uint32_t* sm, int off, int len, int l
 // radix-8 passes, the leftover one or two stages as one pass on the
 // largest strides.  Callers synchronise before; the last pass is followed
 // by a barrier.
-template <bool INV, class PrimeOf>
+template <bool INV, bool COLS = false, class PrimeOf>
 __device__ __forceinline__ void smem_stages(uint32_t* sm, int off, int len, int logn, int s_lo, uint32_t boff,
                                             const uint2* __restrict__ tw, int logN, const NttConsts& C,
-                                            PrimeOf prime_of) {
+                                            PrimeOf prime_of, int cwl = 0) {
   const int rem = (logn - s_lo) % 3;
   if (!INV) {
     int s = s_lo;
     if (rem == 1) {
-      radix_pass<false, 1>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      radix_pass<false, 1, COLS>(sm, off, len, logn, s, boff, tw, logN, C, prime_of, cwl);
       __syncthreads();
     } else if (rem == 2) {
-      radix_pass<false, 2>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      radix_pass<false, 2, COLS>(sm, off, len, logn, s, boff, tw, logN, C, prime_of, cwl);
       __syncthreads();
     }
     for (s += rem; s < logn; s += 3) {
-      radix_pass<false, 3>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      radix_pass<false, 3, COLS>(sm, off, len, logn, s, boff, tw, logN, C, prime_of, cwl);
       __syncthreads();
     }
   } else {
     int s = logn - 1;
     for (; s - 2 >= s_lo; s -= 3) {
-      radix_pass<true, 3>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      radix_pass<true, 3, COLS>(sm, off, len, logn, s, boff, tw, logN, C, prime_of, cwl);
       __syncthreads();
     }
     if (rem == 2) {
-      radix_pass<true, 2>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      radix_pass<true, 2, COLS>(sm, off, len, logn, s, boff, tw, logN, C, prime_of, cwl);
       __syncthreads();
     } else if (rem == 1) {
-      radix_pass<true, 1>(sm, off, len, logn, s, boff, tw, logN, C, prime_of);
+      radix_pass<true, 1, COLS>(sm, off, len, logn, s, boff, tw, logN, C, prime_of, cwl);
       __syncthreads();
     }
   }
@@ -259,9 +250,12 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict_
   }
 }
 
-// The column kernel: each thread takes kNttPer butterflies per stage, unrolled.
-constexpr int kNttPer = kNttTile / 2 / kNttThreads;
-
+// The first L1 = logn - 13 forward stages (the last inverse ones) of a
+// transform larger than a tile pair words 2^13 or more apart.  A CTA takes
+// 2^(13 - L1) adjacent columns of the transform's 2^L1 rows of 2^13 words:
+// stage s of the whole transform acts on each column as stage s of a
+// transform of size 2^L1, twiddles included, run as radix passes with
+// consecutive threads on consecutive columns.
 template <bool INV>
 __global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__ data, int logn, int plane_log, int L1,
                                                           const uint2* __restrict__ tw, int logN, NttConsts C) {
@@ -275,22 +269,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__
   }
   __syncthreads();
   const int prime = (int)((tbase >> plane_log) % kNP);
-  const uint32_t q = C.q[prime];
-  const uint2* __restrict__ twp = tw + ((int64_t)prime << logN);
-  for (int step = 0; step < L1; step++) {
-    const int s = INV ? (L1 - 1 - step) : step;
-    const int lth = L1 - s - 1;                       // log2 of the row distance
-    const uint32_t m = 1u << s;
-#pragma unroll
-    for (int r = 0; r < kNttPer; r++) {
-      const int b = threadIdx.x + r * kNttThreads;
-      const int c = b & (CW - 1), hb = b >> cwl;
-      const int h = ((hb >> lth) << (lth + 1)) | (hb & ((1 << lth) - 1));
-      butterfly<INV>(&sm[(h << cwl) + c], &sm[((h + (1 << lth)) << cwl) + c], __ldg(&twp[m + (uint32_t)(h >> (lth + 1))]),
-                     q);
-    }
-    __syncthreads();
-  }
+  smem_stages<INV, true>(sm, 0, kNttTile, L1, 0, 0u, tw, logN, C, [=](int) { return prime; }, cwl);
   for (int e = threadIdx.x; e < kNttTile; e += kNttThreads) {
     const int h = e >> cwl, c = e & (CW - 1);
     data[tbase + ((int64_t)h << kNttTileLog) + jlo0 + c] = sm[e];
@@ -666,6 +645,109 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_fused(const uint64_t
     }
     __syncthreads();
   }
+}
+
+// Thread-block cluster primitives (PTX): the CTA's rank in its cluster, a
+// cluster-wide barrier (arrive has release, wait acquire semantics at
+// cluster scope), and 32-bit loads from another CTA's shared memory.
+__device__ __forceinline__ int cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive;\n\tbarrier.cluster.wait;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ uint32_t ld_cluster(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// k_newton_fused spread over a cluster of kNP CTAs, CTA i holding prime i's
+// transforms in its shared memory: A (f, then f g), B (g's spectrum), C
+// (e_hi, then g e_hi) in the swizzled layout, and g mod q_i.  Each Chinese
+// remaindering reads the five CTAs' residues through distributed shared
+// memory, and every CTA remainders all k coefficients, so that each has e
+// (and the new g) for its own prime without a trip through global memory;
+// CTA 0 writes g.  A cluster barrier separates a product's last writes from
+// its remote reads, and those reads from the buffer's next writes (the next
+// barrier of the iteration); the last one keeps every CTA resident until
+// the others are done reading it.
+__global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64_t* __restrict__ f, int64_t nf,
+                                                                  int logK, NttConsts C, Mod M,
+                                                                  const uint2* __restrict__ tw, int logN,
+                                                                  uint64_t* __restrict__ g) {
+  extern __shared__ uint32_t fsm[];              // A [n], B [n] at 0, n; C [n] at 2K (logical); then g mod q
+  const int me = cluster_rank();
+  const int K = 1 << logK;
+  const int cb = 2 * K;
+  uint32_t* Gq = fsm + ((3 * K + 31) & ~31);
+  const uint32_t q = C.q[me], qi = C.qinv[me];
+  const uint2* __restrict__ itw = tw + ((size_t)kNP << logN);
+  uint32_t peer[kNP];
+#pragma unroll
+  for (int j = 0; j < kNP; j++) peer[j] = cluster_addr(fsm, j);
+  auto prime = [=](int) { return me; };
+  if (threadIdx.x == 0) {
+    Gq[0] = 1;
+    if (me == 0) g[0] = 1;
+  }
+  __syncthreads();
+  for (int lk = 0; lk < logK; lk++) {
+    const int k = 1 << lk, logn = lk + 1, n = 2 * k;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      fsm[sw(t)] = t < nf ? residue64(f[t], C, me) : 0u;
+      fsm[sw(n + t)] = t < k ? Gq[t] : 0u;
+    }
+    __syncthreads();
+    smem_stages<false>(fsm, 0, 2 * n, logn, 0, 0u, tw, logN, C, prime);   // A and B
+    for (int x = threadIdx.x; x < n; x += blockDim.x)
+      fsm[sw(x)] = mont32(sub_if(fsm[sw(x)], 2 * q), sub_if(fsm[sw(n + x)], 2 * q), q, qi);
+    __syncthreads();
+    smem_stages<true>(fsm, 0, n, logn, 0, 0u, itw, logN, C, prime);
+    uint32_t s[kNP], sp[kNP];                    // 2^32 / n mod q_j: 2^(32 - logn) mod q_j
+#pragma unroll
+    for (int j = 0; j < kNP; j++) {
+      s[j] = (uint32_t)(((uint64_t)1 << (32 - logn)) % C.q[j]);
+      sp[j] = (uint32_t)(((uint64_t)s[j] << 32) / C.q[j]);
+    }
+    cluster_sync();                              // every CTA's A holds f g mod its prime
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      uint32_t v = 0;
+      if (t < k) {
+        uint32_t res[kNP];
+#pragma unroll
+        for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(k + t)), s[j], sp[j], C.q[j]);
+        v = residue64(crt_to_p(res, C, M), C, me);
+      }
+      fsm[sw(cb + t)] = v;
+    }
+    __syncthreads();
+    smem_stages<false>(fsm, cb, n, logn, 0, 0u, tw, logN, C, prime);
+    for (int x = threadIdx.x; x < n; x += blockDim.x)
+      fsm[sw(cb + x)] = mont32(sub_if(fsm[sw(cb + x)], 2 * q), sub_if(fsm[sw(n + x)], 2 * q), q, qi);
+    __syncthreads();
+    smem_stages<true>(fsm, cb, n, logn, 0, 0u, itw, logN, C, prime);
+    cluster_sync();                              // every CTA's C holds g e_hi mod its prime
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      uint32_t res[kNP];
+#pragma unroll
+      for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(cb + t)), s[j], sp[j], C.q[j]);
+      const uint64_t x = crt_to_p(res, C, M);
+      const uint64_t gv = x ? M.p - x : 0;
+      Gq[k + t] = residue64(gv, C, me);
+      if (me == 0) g[k + t] = gv;
+    }
+    __syncthreads();
+  }
+  cluster_sync();
 }
 
 // ---- leaves --------------------------------------------------------------------------
@@ -1059,6 +1141,8 @@ FastWs carve_fast(Carver& cv, int64_t T, int R) {
 }
 
 void configure_fused();
+bool newton_cluster_ok();
+size_t newton_cluster_smem(int logK);
 
 struct FastRun {
   zr_ctx* ctx;
@@ -1093,6 +1177,44 @@ struct FastRun {
     note_launch();
   }
 };
+
+// Shared memory of k_newton_cluster for K = 2^logK: three swizzled
+// buffers of up to K words (rounded to whole 32-word rows) and g mod q.
+size_t newton_cluster_smem(int logK) {
+  const size_t K = (size_t)1 << logK;
+  return sizeof(uint32_t) * (((3 * K + 31) & ~(size_t)31) + K);
+}
+
+// Whether this device runs k_newton_cluster (a cluster of kNP CTAs with the
+// largest shared memory it needs); else the single-CTA kernel runs.
+bool newton_cluster_ok() {
+  static DeviceValue ok;
+  return ok.get([] {
+           const size_t bytes = newton_cluster_smem(kFusedLog);
+           if (cudaFuncSetAttribute(k_newton_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+               cudaSuccess) {
+             (void)cudaGetLastError();
+             return 2;
+           }
+           cudaLaunchConfig_t cfg = {};
+           cfg.gridDim = dim3(kNP);
+           cfg.blockDim = dim3(kNewtonThreadsF);
+           cfg.dynamicSmemBytes = bytes;
+           cudaLaunchAttribute attr[1];
+           attr[0].id = cudaLaunchAttributeClusterDimension;
+           attr[0].val.clusterDim.x = kNP;
+           attr[0].val.clusterDim.y = 1;
+           attr[0].val.clusterDim.z = 1;
+           cfg.attrs = attr;
+           cfg.numAttrs = 1;
+           int clusters = 0;
+           if (cudaOccupancyMaxActiveClusters(&clusters, k_newton_cluster, &cfg) != cudaSuccess) {
+             (void)cudaGetLastError();
+             return 2;
+           }
+           return clusters > 0 ? 1 : 2;
+         }) == 1;
+}
 
 void configure_fused() {
   static DeviceOnce fused_attr;
@@ -1138,8 +1260,26 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
 void FastRun::inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, uint64_t* e, uint32_t* A,
                       uint32_t* B, uint32_t* Z) {
   const int logK0 = std::min(ilog2(prec), kFusedLog);
-  k_newton_fused<<<1, kNewtonThreadsF, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(f, nf, logK0, C, M, tw, logN, g,
-                                                                                e);
+  bool done = false;
+  if (newton_cluster_ok()) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kNP);
+    cfg.blockDim = dim3(kNewtonThreadsF);
+    cfg.dynamicSmemBytes = newton_cluster_smem(logK0);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kNP;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    done = cudaLaunchKernelEx(&cfg, k_newton_cluster, f, nf, logK0, C, M, tw, logN, g) == cudaSuccess;
+    if (!done) (void)cudaGetLastError();
+  }
+  if (!done)
+    k_newton_fused<<<1, kNewtonThreadsF, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(f, nf, logK0, C, M, tw, logN, g,
+                                                                                  e);
   note_launch();
   for (int64_t k = 1ll << logK0; k < prec; k *= 2) {
     const int logk2 = ilog2(2 * k);
