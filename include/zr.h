@@ -166,8 +166,11 @@ typedef struct zr_vsys {
 
 /* Choice of solve method for the systems of every later call on the context
  * (steps, systems, reconstructions, the server):
- *   0  by size: the O(T log^2 T) method for T >= crossover (crossover 0: the
- *      library's measured default), the O(T^2) method below it;
+ *   0  by size: the O(T log^2 T) method for T >= crossover, the O(T^2)
+ *      method below it; crossover 0 takes the library's measured rule for a
+ *      system of S right-hand sides, T >= 4096 and T^2 (S + 15) >= 1.4e9
+ *      (about T >= 6100 for S = 21, 10000 for S = 1), and T >= 12000 for
+ *      the evaluator of the probes;
  *   1  always the O(T^2) method of Sec. 2.2 (Horner quotients, deferred dot
  *      products, one inverse per root);
  *   2  the O(T log^2 T) method for every T it supports.

@@ -403,25 +403,32 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
 
 extern "C" const char* zr_last_error(const zr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
-// Size from which the automatic choice takes the fast solve.  Measured on
-// GB300 with 21 right-hand sides: 2.15 against 3.22 ms at T = 10^4, 5.1
-// against 3.2 ms at T = 16384 (the fast path's chain of transform launches
-// costs about 1 ms at any size).
-static constexpr int64_t kFastDefaultMinT = 12000;
+// The automatic choice of solve method.  On GB300 the O(T^2) batch costs
+// about 0.3 ms + T^2 (5.5e-10 S + 7.7e-9) ms for one system of S right-hand
+// sides, the O(T log^2 T) path 0.8 to 1.5 ms from T = 4096 to 16384 almost
+// independently of S; they cross near T = 6100 (S = 21), 7800 (S = 5) and
+// 10000 (S = 1), which T^2 (S + 15) >= 1.4e9 follows within 10%.
+static constexpr double kFastCross = 1.4e9;
+static constexpr int64_t kFastFloorT = 4096;
 
 namespace zr {
-bool use_fast_solve(const zr_ctx* ctx, int64_t T) {
+bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S) {
   if (T < 1 || T > kFastMaxT || ctx->solve_method == 1) return false;
   if (ctx->solve_method == 2) return true;
-  return T >= (ctx->fast_min_T > 0 ? ctx->fast_min_T : kFastDefaultMinT);
+  if (ctx->fast_min_T > 0) return T >= ctx->fast_min_T;
+  return T >= kFastFloorT && (double)T * (double)T * (double)(S + 15) >= kFastCross;
 }
 }  // namespace zr
+
+// Size from which the automatic choice takes the fast evaluator for the
+// probes (both the terms of f and the probes per sample at least this many).
+static constexpr int64_t kFastProbeMinT = 12000;
 
 namespace zr {
 bool use_fast_probes(const zr_ctx* ctx, int64_t T, int64_t Tf, int S) {
   if (T < 1 || Tf < 1 || T > kFastMaxT || S > kFastProbeMaxS || ctx->solve_method == 1) return false;
   if (ctx->solve_method == 2) return true;
-  const int64_t m = ctx->fast_min_T > 0 ? ctx->fast_min_T : kFastDefaultMinT;
+  const int64_t m = ctx->fast_min_T > 0 ? ctx->fast_min_T : kFastProbeMinT;
   return T >= m && Tf >= m;
 }
 }  // namespace zr

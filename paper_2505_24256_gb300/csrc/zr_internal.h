@@ -163,7 +163,7 @@ size_t fast_ws_need(int64_t T, int R);
 zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, const uint64_t* vp, const uint64_t* b,
                              int64_t ldb, uint64_t* part, uint64_t* den, char* ws, cudaStream_t st);
 // whether a system of T unknowns takes the fast path in this context
-bool use_fast_solve(const zr_ctx* ctx, int64_t T);
+bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S);
 // whether T probes of a function of Tf terms take the fast evaluator (the
 // transposed tree), which reads the group count G <= Tf on the host and
 // falls back to the matrix-vector kernel when G > kFastMaxT
