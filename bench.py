@@ -49,17 +49,21 @@ METRIC = "Zippel-step skeleton terms/s and mulmod/s vs roofline; serve p50/p99 l
 SOLVE_SOURCES = ("zr_solve.cuh", "zr_ring.cuh")
 
 
-def solve_traffic(workload_name):
-    """DRAM bytes per solve launch from the committed ncu summary of this
-    workload, or None when there is none or the solve source changed since."""
+# the sources of the transform tile kernel k_ntt_local
+NTT_SOURCES = ("zr_fast.cu", "zr_ntt.cuh")
+
+
+def kernel_traffic(kernel, workload_name, sources):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of
+    this workload, or None when there is none or its sources changed since."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"k_solve_{workload_name}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.md")
     csrc = os.path.join(ROOT, "paper_2505_24256_gb300", "csrc")
     try:
         fields = dict(line.split(": ", 1) for line in open(path).read().splitlines()
                       if line.startswith(("traffic_bytes_per_launch: ", "source_sha256_prefix: ")))
         h = hashlib.sha256()
-        for name in SOLVE_SOURCES:
+        for name in sources:
             h.update(open(os.path.join(csrc, name), "rb").read())
         cur = h.hexdigest()[:16]
         if fields.get("source_sha256_prefix", "").strip() != cur:
@@ -67,6 +71,10 @@ def solve_traffic(workload_name):
         return int(fields["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def solve_traffic(workload_name):
+    return kernel_traffic("k_solve", workload_name, SOLVE_SOURCES)
 
 
 def workload(name):
@@ -368,6 +376,94 @@ def solve_roofline(T, S, solve_avg_s, peaks, workload_name):
                                  f"({chain_th / 1e9:.0f} G/s), weighted by the solve's mix"}
 
 
+def quadratic_form_bench(ctx, step, flush, stream, steps, wl, peaks, oe, oc, ms_auto):
+    """The step with the O(T^2) solve of Sec. 2.2 forced: one warm-up, then
+    `steps` timed with the L2 flushed before each; k_solve's roofline from
+    the profiler's solve phase; output against generator truth."""
+    import numpy as np
+    import torch
+    T, S = wl.T, wl.S
+    ctx.solve_method(ctx.SOLVE_QUADRATIC)
+    try:
+        flush.zero_()
+        step()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        n = 0
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            n = step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        solve_ms, solve_n = ctx.profile_query("solve")
+        phases = {ph: ctx.profile_query(ph)[0] / max(steps, 1) for ph in ctx.PHASES[:7]}
+        ctx.profile(False)
+    finally:
+        ctx.solve_method(ctx.SOLVE_AUTO)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
+        np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
+    return {"ms_per_step": ms, "terms_per_s": T / (ms / 1e3), "mulmod_per_s": (S + 2.5) * T * T / (ms / 1e3),
+            "fast_speedup": ms / ms_auto, "steps": steps,
+            "what": "the same step with the O(T^2) solve of Sec. 2.2 (k_solve) forced",
+            "roofline": solve_roofline(T, S, solve_ms / max(solve_n, 1) / 1e3, peaks, wl.name),
+            "phase_ms": phases, "check": "generator truth" if ok else "MISMATCH"}
+
+
+def evaluator_method(ctx, call):
+    """Which evaluator the library takes for a probe call: "transposed tree"
+    when the call launched the transform kernels, else "matrix-vector"."""
+    import torch
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    call()
+    torch.cuda.synchronize()
+    n = ctx.profile_query("ntt")[1]
+    ctx.profile(False)
+    return "transposed tree" if n else "matrix-vector"
+
+
+def probe_gen_entry(ms, S, T, G, peaks, method):
+    """The probe evaluator's figure: S x T probes of a function whose G terms
+    have distinct anchor monomials.  The matrix-vector evaluator does S T G
+    multiply-accumulates (rated against the measured MAC peak); the
+    transposed subproduct tree computes the same values with O((G + S T)
+    log^2) transform work, so only its time is given."""
+    e = {"ms": ms, "evaluator": method, "probes": S * T, "terms": G}
+    if method == "matrix-vector":
+        macs = S * T * G
+        e.update({"macs": macs, "mac_per_s": macs / (ms * 1e-3),
+                  "frac_of_measured_mac_peak": macs / (ms * 1e-3) / peaks["mac_per_s"]})
+    else:
+        e["probes_per_s"] = S * T / (ms * 1e-3)
+    return e
+
+
+def ntt_roofline(ctx, peaks, workload_name, steps, step_ms):
+    """Roofline entry of the O(T log^2 T) solve's transform tile kernel
+    k_ntt_local (the largest share of that path's time): its radix-2
+    butterflies per launch (n/2 per stage run, counted by the library's
+    profiler) over its average launch time (CUDA events around each launch on
+    the launching stream, this run), against the measured rate of the same
+    butterfly with its operands in registers (zr_measure_peaks, this run)."""
+    ms, n = ctx.profile_query("ntt")
+    work = ctx.profile_work("ntt")
+    if n <= 0 or ms <= 0:
+        return None
+    achieved = work / (ms * 1e-3)
+    peak = peaks["butterfly_per_s"]
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
+            "frac": achieved / peak, "traffic": kernel_traffic("k_ntt_local", workload_name, NTT_SOURCES),
+            "traffic_unit": "bytes/launch", "kernel": "k_ntt_local",
+            "ops": f"radix-2 butterflies, n/2 per stage run: {work / n:.4g} per launch on average, "
+                   f"{n / max(steps, 1):.0f} launches per step",
+            "launch_ms": ms / n, "share_of_step": ms / max(steps, 1) / step_ms,
+            "peak_basis": "measured (zr_measure_peaks on this GPU, this run): forward butterflies on 32-bit "
+                          f"residues with a Shoup twiddle, operands in registers, {peak / 1e9:.0f} G/s"}
+
+
 SM_MAX_MHZ = 2070.0   # GB300 maximum SM clock (the clocks record of each run gives the live value)
 
 
@@ -414,6 +510,7 @@ def run_zr(args):
         if probe_times[0] > 100.0:
             break
     probe_ms = probe_times[0] if len(probe_times) == 1 else sorted(probe_times[1:])[1]
+    probe_method = evaluator_method(ctx, lambda: ctx.zippel_probes(f, k, y, S, cs, z, T, 0, b, T))
     cap = T * S
     oe = torch.zeros((cap, nv), dtype=torch.uint8, device=dev)
     oc = torch.zeros(cap, dtype=torch.int64, device=dev)
@@ -457,12 +554,18 @@ def run_zr(args):
     median_ms = step_times[len(step_times) // 2] if len(step_times) % 2 else \
         0.5 * (step_times[len(step_times) // 2 - 1] + step_times[len(step_times) // 2])
     solve_ms, solve_n = ctx.profile_query("solve")
-    phases = {ph: ctx.profile_query(ph)[0] / max(args.steps, 1) for ph in zr.Context.PHASES[:7] + ("fast",)}
+    fast_n = ctx.profile_query("fast")[1]
+    phases = {ph: ctx.profile_query(ph)[0] / max(args.steps, 1) for ph in zr.Context.PHASES[:7] + ("fast", "ntt")}
+    ntt_roof = ntt_roofline(ctx, peaks, wl.name, args.steps, sum(step_times) / len(step_times)) if fast_n else None
     ctx.profile(False)
     total_ms = max_over_ranks(total_ms, world, dev)
     # the output of the last timed step against generator truth
     ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
         np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
+    # when the library chose the O(T log^2 T) solve: the same step with the
+    # paper's O(T^2) solve (k_solve), timed the same way, with its roofline
+    quad = quadratic_form_bench(ctx, step, flush, stream, args.steps, wl, peaks, oe, oc, total_ms / args.steps) \
+        if fast_n else None
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     h_exps = torch.from_numpy(wl.skel).pin_memory()
@@ -550,12 +653,17 @@ def run_zr(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": bench_config(wl, world),
-        "mulmod_per_s": world * W * args.steps / (total_ms / 1e3),
+        "solve": "O(T log^2 T) (subproduct tree, transforms over five 30-bit primes)" if fast_n
+                 else "O(T^2) (Sec. 2.2, k_solve)",
+        # mulmod/s of the O(T^2) form: S T^2 multiply-accumulates + 2.5 T^2 chain and denominator steps per step
+        "mulmod_per_s": quad["mulmod_per_s"] * world if quad else world * W * args.steps / (total_ms / 1e3),
         # the median step of this rank (the per-step figure the paper reports)
         "median": {"ms_per_step": median_ms, "terms_per_s": T / (median_ms / 1e3), "steps": len(step_times)},
-        "roofline": solve_roofline(T, S, solve_avg_s, peaks, wl.name),
+        "roofline": ntt_roof if fast_n else solve_roofline(T, S, solve_avg_s, peaks, wl.name),
+        "quadratic_form": quad,
         "peaks_measured": {"mac_per_s": peaks["mac_per_s"], "chain_per_s": peaks["chain_per_s"],
-                           "imad_lo_per_s": peaks["imad_lo_per_s"], "imad_hi_per_s": peaks["imad_hi_per_s"]},
+                           "imad_lo_per_s": peaks["imad_lo_per_s"], "imad_hi_per_s": peaks["imad_hi_per_s"],
+                           "butterfly_per_s": peaks["butterfly_per_s"]},
         "plain_form": {"ms_per_step": plain_ms, "terms_per_s": world * T / (plain_ms / 1e3),
                        "batched_speedup": plain_ms / ms_per_step,
                        "what": f"{S} single-RHS systems, one launch sequence each, + Newton",
@@ -568,10 +676,7 @@ def run_zr(args):
         "phase_ms": phases,
         "plan": {"s_tile": plan[0], "k_blocks": plan[1]},
         "probe_gen_ms": probe_ms,
-        # the evaluator's product: S x T probes over the G = T distinct anchor
-        # monomials of the hidden function (its terms share x' with the skeleton)
-        "probe_gen": {"ms": probe_ms, "macs": S * T * T, "mac_per_s": S * T * T / (probe_ms * 1e-3),
-                      "frac_of_measured_mac_peak": S * T * T / (probe_ms * 1e-3) / peaks["mac_per_s"]},
+        "probe_gen": probe_gen_entry(probe_ms, S, T, T, peaks, probe_method),
         "e2e": {"value": job_rate(T, world, e2e_s), "unit": "terms/s",
                 "h2d_bytes_per_step": T * nv + 8 * k + 8 * S + 8 * S * T,
                 "d2h_bytes_per_step": ne * (nv + 8) + 12},
@@ -629,6 +734,7 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
     e1.record(stream)
     torch.cuda.synchronize()
     probe_ms = e0.elapsed_time(e1)
+    probe_method = evaluator_method(ctx, lambda: ctx.zippel_probes(f, k, y, S, cs, z, T, 0, b, T))
     del fe, fc
     cap = T * S
     oe = torch.zeros((cap, nv), dtype=torch.uint8, device=dev)
@@ -651,7 +757,8 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
     clk = clocks.stop()
     times = [a.elapsed_time(bb) for a, bb in evs]
     fast_ms, fast_n = ctx.profile_query("fast")
-    phases = {ph: ctx.profile_query(ph)[0] / max(steps, 1) for ph in ctx.PHASES[:7] + ("fast",)}
+    phases = {ph: ctx.profile_query(ph)[0] / max(steps, 1) for ph in ctx.PHASES[:7] + ("fast", "ntt")}
+    fast_roof = ntt_roofline(ctx, peaks, wl.name, steps, sum(times) / len(times))
     ctx.profile(False)
     ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
         np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
@@ -705,6 +812,7 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
         "solve": "O(T log^2 T) (subproduct tree, transforms over five 30-bit primes)",
         "ms_per_step": ms, "terms_per_s": T / (ms / 1e3),
         "fast_solve_ms": fast_ms / max(fast_n, 1),
+        "roofline": fast_roof,
         "phase_ms": phases,
         "quadratic_form": {"ms_per_step": quad_ms, "terms_per_s": T / (quad_ms / 1e3),
                            "mulmod_per_s": W_ / (quad_ms / 1e3), "fast_speedup": quad_ms / ms,
@@ -718,8 +826,7 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
                        "what": f"{S} single-RHS systems, one launch sequence each; one timed "
                                f"({plain_one_ms:.0f} ms) and scaled by {S} (identical cost)",
                        "check": "generator truth (64 sampled roots)" if plain_ok else "MISMATCH"},
-        "probe_gen": {"ms": probe_ms, "macs": S * T * T, "mac_per_s": S * T * T / (probe_ms * 1e-3),
-                      "frac_of_measured_mac_peak": S * T * T / (probe_ms * 1e-3) / peaks["mac_per_s"]},
+        "probe_gen": probe_gen_entry(probe_ms, S, T, T, peaks, probe_method),
         "clocks": clk,
         "l2": "flushed before each timed step (256 MB write); the step's inputs exceed L2",
         "check": "generator truth" if (ok and qok and plain_ok) else "MISMATCH",

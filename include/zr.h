@@ -74,13 +74,17 @@ size_t zr_workspace_bytes(const zr_ctx* ctx);
  * polynomial, 2 right-hand sides in MAC form, 3 k-block carries, 4 the
  * synthetic-division/dot kernel, 5 denominators + inverses + Newton,
  * 6 compaction, 7 probe evaluation, 8 the O(T log^2 T) solve of the systems
- * that take it: tree, power sums, descent and leaves); zr_profile_enable
- * resets the totals,
- * zr_profile_query waits for the recorded events and returns the summed
- * milliseconds and the number of timed occurrences of a phase. */
+ * that take it: tree, power sums, descent and leaves; 9 each launch of that
+ * solve's transform tile kernel, inside phase 8); zr_profile_enable resets
+ * the totals, zr_profile_query waits for the recorded events and returns the
+ * summed milliseconds and the number of timed occurrences of a phase, and
+ * zr_profile_work the algorithmic work recorded with them (phase 9: radix-2
+ * butterflies, n/2 per stage of a transform of n words; 0 for the others).
+ * Errors: ZR_ERR_INVALID_ARG for a phase outside 0..9 or a null pointer. */
 uint64_t zr_launch_count(void);
 zr_status zr_profile_enable(zr_ctx* ctx, int32_t on);
 zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count);
+zr_status zr_profile_work(zr_ctx* ctx, int32_t phase, double* units);
 
 /* Self-check of the bounded device waits (the paper has no counterpart):
  * one warp waits on a shared-memory barrier that nothing arrives on, gives
@@ -124,9 +128,11 @@ zr_status zr_check_arith(zr_ctx* ctx, int32_t op, int64_t n, int64_t len, const 
  *   chain_per_s    synthetic-division steps q <- q v + m with Shoup's
  *                  precomputed quotient (Sec. 2.1)
  *   imad_lo_per_s, imad_hi_per_s   32-bit mad.lo / mad.hi
+ *   butterfly_per_s   forward transform butterflies on 32-bit residues
+ *                  with a Shoup twiddle (the O(T log^2 T) solve's transforms)
  * Synchronous; uses the context workspace. */
 typedef struct zr_peaks {
-  double mac_per_s, chain_per_s, imad_lo_per_s, imad_hi_per_s;
+  double mac_per_s, chain_per_s, imad_lo_per_s, imad_hi_per_s, butterfly_per_s;
   int32_t sms, pad;
 } zr_peaks;
 zr_status zr_measure_peaks(zr_ctx* ctx, zr_peaks* out, void* stream);

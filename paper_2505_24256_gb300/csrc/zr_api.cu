@@ -96,9 +96,9 @@ cudaEvent_t prof_mark(zr_ctx* ctx, cudaStream_t st) {
   return e;
 }
 
-void prof_add(zr_ctx* ctx, int phase, cudaEvent_t a, cudaEvent_t b) {
+void prof_add(zr_ctx* ctx, int phase, cudaEvent_t a, cudaEvent_t b, double work) {
   if (!a || !b) return;
-  ctx->prof.pending.push_back({phase, a, b});
+  ctx->prof.pending.push_back({phase, a, b, work});
 }
 
 void prof_collect(zr_ctx* ctx) {
@@ -109,6 +109,7 @@ void prof_collect(zr_ctx* ctx) {
     if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       ctx->prof.total_ms[p.phase] += ms;
       ctx->prof.count[p.phase] += 1;
+      ctx->prof.work[p.phase] += p.work;
     }
     used.push_back(p.a);
     used.push_back(p.b);
@@ -328,6 +329,7 @@ extern "C" zr_status zr_profile_enable(zr_ctx* ctx, int32_t on) {
   for (int i = 0; i < PH_N; i++) {
     ctx->prof.total_ms[i] = 0;
     ctx->prof.count[i] = 0;
+    ctx->prof.work[i] = 0;
   }
   return ZR_OK;
 }
@@ -337,6 +339,13 @@ extern "C" zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_
   prof_collect(ctx);
   if (total_ms) *total_ms = ctx->prof.total_ms[phase];
   if (count) *count = ctx->prof.count[phase];
+  return ZR_OK;
+}
+
+extern "C" zr_status zr_profile_work(zr_ctx* ctx, int32_t phase, double* units) {
+  if (!ctx || !units || phase < 0 || phase >= PH_N) return ZR_ERR_INVALID_ARG;
+  prof_collect(ctx);
+  *units = ctx->prof.work[phase];
   return ZR_OK;
 }
 

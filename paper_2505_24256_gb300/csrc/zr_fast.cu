@@ -91,22 +91,6 @@ __global__ void k_ntt_tables(int logN, NttConsts C, uint2* __restrict__ tw, uint
 // elements (k_ntt_local); the first logn - 13 forward stages (last inverse
 // ones) act within columns of stride 2^13 (k_ntt_cols).
 
-// Harvey's butterflies with a Shoup twiddle: forward (CT) X, Y < 4q -> < 4q;
-// inverse (GS) X, Y < 2q -> < 2q.
-template <bool INV>
-__device__ __forceinline__ void butterfly(uint32_t& X, uint32_t& Y, uint2 w, uint32_t q) {
-  if (!INV) {
-    const uint32_t x = sub_if(X, 2 * q);
-    const uint32_t t = shoup32(Y, w.x, w.y, q);
-    X = x + t;
-    Y = x - t + 2 * q;
-  } else {
-    const uint32_t x = X, y = Y;
-    X = sub_if(x + y, 2 * q);
-    Y = shoup32(x - y + 2 * q, w.x, w.y, q);
-  }
-}
-
 // Shared-memory layout of the transform kernels: logical word x lives at
 // sw(x), its bank bits XORed with bits of its 32-word row (a permutation
 // within each row).  The register passes below touch words at strides 1, 8
@@ -1087,20 +1071,38 @@ CrtScale crt_scale(int logn) {
   return s;
 }
 
-void launch_ntt(uint32_t* data, int64_t count, int logn, int plane_log, bool inv, const uint2* tw, const uint2* itw,
-                int logN, const NttConsts& C, cudaStream_t st) {
+// Transforms of count runs of 2^logn residues (see above).  With the
+// context's profiler on, each tile launch is timed as phase PH_NTT with its
+// butterflies (total / 2 per stage it runs) as the phase's work.
+void launch_ntt(zr_ctx* ctx, uint32_t* data, int64_t count, int logn, int plane_log, bool inv, const uint2* tw,
+                const uint2* itw, int logN, const NttConsts& C, cudaStream_t st) {
   if (logn <= 0 || count <= 0) return;
   const int64_t total = count << logn;
   const int L1 = logn > kNttTileLog ? logn - kNttTileLog : 0;
   const unsigned tiles = cdivu(total, kNttTile);
+  const unsigned cols = (unsigned)(count << L1);
+  auto local = [&](bool inverse) {
+    cudaEvent_t a = prof_mark(ctx, st);
+    if (inverse)
+      k_ntt_local<true><<<tiles, kNttThreads, 0, st>>>(data, total, logn, plane_log, L1, itw, logN, C);
+    else
+      k_ntt_local<false><<<tiles, kNttThreads, 0, st>>>(data, total, logn, plane_log, L1, tw, logN, C);
+    note_launch();
+    cudaEvent_t b = prof_mark(ctx, st);
+    prof_add(ctx, PH_NTT, a, b, (double)(total / 2) * (logn - L1));
+  };
   if (!inv) {
-    if (L1) { k_ntt_cols<false><<<(unsigned)(count << L1), kNttThreads, 0, st>>>(data, logn, plane_log, L1, tw, logN, C); note_launch(); }
-    k_ntt_local<false><<<tiles, kNttThreads, 0, st>>>(data, total, logn, plane_log, L1, tw, logN, C);
-    note_launch();
+    if (L1) {
+      k_ntt_cols<false><<<cols, kNttThreads, 0, st>>>(data, logn, plane_log, L1, tw, logN, C);
+      note_launch();
+    }
+    local(false);
   } else {
-    k_ntt_local<true><<<tiles, kNttThreads, 0, st>>>(data, total, logn, plane_log, L1, itw, logN, C);
-    note_launch();
-    if (L1) { k_ntt_cols<true><<<(unsigned)(count << L1), kNttThreads, 0, st>>>(data, logn, plane_log, L1, itw, logN, C); note_launch(); }
+    local(true);
+    if (L1) {
+      k_ntt_cols<true><<<cols, kNttThreads, 0, st>>>(data, logn, plane_log, L1, itw, logN, C);
+      note_launch();
+    }
   }
 }
 
@@ -1168,11 +1170,11 @@ struct FastRun {
     k_cyc_load<<<cdivu(all, 256), 256, 0, st>>>(a, na, logn, C, A);
     k_cyc_load<<<cdivu(all, 256), 256, 0, st>>>(b, nb, logn, C, B);
     note_launches(2);
-    launch_ntt(A, kNP, logn, logn, false, tw, itw, logN, C, st);
-    launch_ntt(B, kNP, logn, logn, false, tw, itw, logN, C, st);
+    launch_ntt(ctx, A, kNP, logn, logn, false, tw, itw, logN, C, st);
+    launch_ntt(ctx, B, kNP, logn, logn, false, tw, itw, logN, C, st);
     k_cyc_mul<<<cdivu(all, 256), 256, 0, st>>>(A, B, logn, C, Z);
     note_launch();
-    launch_ntt(Z, kNP, logn, logn, true, tw, itw, logN, C, st);
+    launch_ntt(ctx, Z, kNP, logn, logn, true, tw, itw, logN, C, st);
     k_cyc_crt<<<cdivu(cnt, 256), 256, 0, st>>>(Z, logn, lo, cnt, neg ? 1 : 0, C, crt_scale(logn), M, out);
     note_launch();
   }
@@ -1248,10 +1250,10 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
     }
     k_tree_load<<<cdivu(kNP * 2 * Tp, 256), 256, 0, st>>>(coef[l - 1], T, Tp, logn, C, sp);
     note_launch();
-    launch_ntt(sp, (kNP * 2 * Tp) >> logn, logn, logT + 1, false, tw, itw, logN, C, st);
+    launch_ntt(ctx, sp, (kNP * 2 * Tp) >> logn, logn, logT + 1, false, tw, itw, logN, C, st);
     k_tree_mul<<<cdivu(kNP * Tp, 256), 256, 0, st>>>(sp, Tp, logn, C, Z);
     note_launch();
-    launch_ntt(Z, (kNP * Tp) >> logn, logn, logT, true, tw, itw, logN, C, st);
+    launch_ntt(ctx, Z, (kNP * Tp) >> logn, logn, logT, true, tw, itw, logN, C, st);
     k_tree_crt<<<cdivu(Tp, 256), 256, 0, st>>>(Z, T, Tp, logn, C, crt_scale(logn), M, coef[l]);
     note_launch();
   }
@@ -1445,10 +1447,10 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     const int64_t all = (int64_t)R * kNP * Tp;
     k_desc_load<<<cdivu((int64_t)R * Tp, 256), 256, 0, st>>>(X, R, T, Tp, logn, C, w.XH);
     note_launch();
-    launch_ntt(w.XH, all >> logn, logn, logT, false, tw, itw, logN, C, st);
+    launch_ntt(ctx, w.XH, all >> logn, logn, logT, false, tw, itw, logN, C, st);
     k_desc_mul<<<cdivu((int64_t)kNP * Tp, 256), 256, 0, st>>>(w.XH, w.spec[l - 1], R, Tp, logn, C, w.Y);
     note_launch();
-    launch_ntt(w.Y, (2 * all) >> logn, logn, logT, true, tw, itw, logN, C, st);
+    launch_ntt(ctx, w.Y, (2 * all) >> logn, logn, logT, true, tw, itw, logN, C, st);
     k_desc_crt<<<cdivu((int64_t)R * Tp, 256), 256, 0, st>>>(w.Y, R, T, Tp, logn, C, crt_scale(logn), M, Xn);
     note_launch();
     std::swap(X, Xn);
@@ -1508,10 +1510,10 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
     } else {
       k_up_load<<<cdivu((int64_t)S * 2 * Gp, 256), 256, 0, st>>>(Nc, S, G, Gp, logn, C, w.A);
       note_launch();
-      launch_ntt(w.A, ((int64_t)S * kNP * 2 * Gp) >> logn, logn, logG + 1, false, tw, itw, logN, C, st);
+      launch_ntt(ctx, w.A, ((int64_t)S * kNP * 2 * Gp) >> logn, logn, logG + 1, false, tw, itw, logN, C, st);
       k_up_mul<<<cdivu((int64_t)kNP * Gp, 256), 256, 0, st>>>(w.A, w.spec[l - 1], S, Gp, logn, C, w.Z);
       note_launch();
-      launch_ntt(w.Z, ((int64_t)S * kNP * Gp) >> logn, logn, logG, true, tw, itw, logN, C, st);
+      launch_ntt(ctx, w.Z, ((int64_t)S * kNP * Gp) >> logn, logn, logG, true, tw, itw, logN, C, st);
       k_up_crt<<<cdivu((int64_t)S * Gp, 256), 256, 0, st>>>(w.Z, S, G, Gp, logn, C, crt_scale(logn), M, Nn);
       note_launch();
     }
@@ -1528,11 +1530,11 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
   note_launch();
   k_cyc_load<<<cdivu((int64_t)kNP << logR, 256), 256, 0, st>>>(w.g, T, logR, C, w.Bg);
   note_launch();
-  launch_ntt(w.A, (int64_t)S * kNP, logR, logR, false, tw, itw, logN, C, st);
-  launch_ntt(w.Bg, kNP, logR, logR, false, tw, itw, logN, C, st);
+  launch_ntt(ctx, w.A, (int64_t)S * kNP, logR, logR, false, tw, itw, logN, C, st);
+  launch_ntt(ctx, w.Bg, kNP, logR, logR, false, tw, itw, logN, C, st);
   k_rows_mul<<<cdivu((int64_t)kNP << logR, 256), 256, 0, st>>>(w.A, w.Bg, S, logR, C);
   note_launch();
-  launch_ntt(w.A, (int64_t)S * kNP, logR, logR, true, tw, itw, logN, C, st);
+  launch_ntt(ctx, w.A, (int64_t)S * kNP, logR, logR, true, tw, itw, logN, C, st);
   k_rows_crt<<<cdivu((int64_t)S * T, 256), 256, 0, st>>>(w.A, S, T, logR, C, crt_scale(logR), M, out, ldo);
   note_launch();
   return cuda_err(ctx, cudaGetLastError(), "fast probes");

@@ -13,15 +13,20 @@
 
 // Phases of a step timed by the optional profiler (CUDA events recorded on
 // the call's stream around each phase).
-enum zr_phase { PH_ANCHOR = 0, PH_MASTER, PH_EXPAND, PH_CARRY, PH_SOLVE, PH_NEWTON, PH_COMPACT, PH_EVAL, PH_FAST, PH_N };
+// PH_NTT times each launch of the transform tile kernel inside PH_FAST and
+// counts its butterflies as the phase's work.
+enum zr_phase {
+  PH_ANCHOR = 0, PH_MASTER, PH_EXPAND, PH_CARRY, PH_SOLVE, PH_NEWTON, PH_COMPACT, PH_EVAL, PH_FAST, PH_NTT, PH_N
+};
 
 struct zr_prof {
   bool on = false;
   std::vector<cudaEvent_t> pool;
-  struct Pending { int phase; cudaEvent_t a, b; };
+  struct Pending { int phase; cudaEvent_t a, b; double work; };
   std::vector<Pending> pending;
   double total_ms[PH_N] = {};
   long long count[PH_N] = {};
+  double work[PH_N] = {};
 };
 
 struct zr_plan_entry {
@@ -95,7 +100,7 @@ zr_status set_err(zr_ctx* ctx, zr_status st, const std::string& msg);
 bool mod_for_prime(uint64_t p, Mod* out);
 // profiler marks (no-ops when profiling is off)
 cudaEvent_t prof_mark(zr_ctx* ctx, cudaStream_t st);
-void prof_add(zr_ctx* ctx, int phase, cudaEvent_t a, cudaEvent_t b);
+void prof_add(zr_ctx* ctx, int phase, cudaEvent_t a, cudaEvent_t b, double work = 0);
 void prof_collect(zr_ctx* ctx);
 zr_status cuda_err(zr_ctx* ctx, cudaError_t e, const char* where);
 zr_status ensure_ws(zr_ctx* ctx, size_t need, cudaStream_t st);

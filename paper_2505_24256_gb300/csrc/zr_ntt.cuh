@@ -62,6 +62,22 @@ __device__ __forceinline__ uint32_t mont32(uint32_t a, uint32_t b, uint32_t q, u
 }
 __device__ __forceinline__ uint32_t sub_if(uint32_t x, uint32_t b) { return x >= b ? x - b : x; }
 
+// Harvey's butterflies with a Shoup twiddle: forward (CT) X, Y < 4q -> < 4q;
+// inverse (GS) X, Y < 2q -> < 2q.
+template <bool INV>
+__device__ __forceinline__ void butterfly(uint32_t& X, uint32_t& Y, uint2 w, uint32_t q) {
+  if (!INV) {
+    const uint32_t x = sub_if(X, 2 * q);
+    const uint32_t t = shoup32(Y, w.x, w.y, q);
+    X = x + t;
+    Y = x - t + 2 * q;
+  } else {
+    const uint32_t x = X, y = Y;
+    X = sub_if(x + y, 2 * q);
+    Y = shoup32(x - y + 2 * q, w.x, w.y, q);
+  }
+}
+
 // A 64-bit value's residue modulo q_i, in [0, 4q): hi 2^32 + lo.
 __device__ __forceinline__ uint32_t residue64(uint64_t x, const NttConsts& C, int i) {
   const uint32_t q = C.q[i];

@@ -6,10 +6,14 @@
 // probe below runs one of them, or a single 32-bit multiply-add form, with
 // every operand in registers and enough independent accumulators per thread
 // that nothing waits on a dependency; every SM runs as many blocks as fit.
-// The rates are what the roofline of the solve is measured against.
+// The rates are what the roofline of the solve is measured against.  A fifth
+// probe runs the butterfly of the number-theoretic transforms (Harvey's
+// forward butterfly on 32-bit residues with a Shoup twiddle), the ceiling of
+// the transform kernels of the O(T log^2 T) solve.
 #include <cuda_runtime.h>
 
 #include "zr_internal.h"
+#include "zr_ntt.cuh"
 
 namespace zr {
 
@@ -19,6 +23,7 @@ constexpr int kPeakThreads = 128;
 constexpr int kMacCols = 12;      // independent 160-bit accumulators per thread
 constexpr int kChains = 8;        // independent chains per thread
 constexpr int kMads = 16;         // independent 32-bit accumulators per thread
+constexpr int kBfly = 16;         // residues per thread in the butterfly probe: two radix-8 groups
 
 __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t r;
@@ -31,7 +36,9 @@ __device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
   return r;
 }
 
-// kind 0: mac8, kind 1: chain step, kind 2: mad.lo, kind 3: mad.hi.
+// kind 0: mac8, kind 1: chain step, kind 2: mad.lo, kind 3: mad.hi,
+// kind 4: forward butterflies, three radix-2 stages over each group of eight
+// residues per round (24 butterflies).
 template <int KIND>
 __global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, uint64_t seed, Mod M, uint32_t* __restrict__ sink,
                                                         int write) {
@@ -69,6 +76,31 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, uint64_t seed,
     }
 #pragma unroll
     for (int r = 0; r < kChains; r++) out ^= lo32(q[r]);
+  } else if (KIND == 4) {
+    constexpr uint32_t q = 998244353u;           // the first transform prime
+    uint32_t x[kBfly];
+    uint2 w[7];
+#pragma unroll
+    for (int r = 0; r < kBfly; r++) x[r] = (uint32_t)((h >> (r & 31)) % q);
+#pragma unroll
+    for (int r = 0; r < 7; r++) {
+      const uint32_t wv = (uint32_t)(((h >> 3) * (r + 1)) % q);
+      w[r] = make_uint2(wv, (uint32_t)(((uint64_t)wv << 32) / q));
+    }
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+      for (int gbase = 0; gbase < kBfly; gbase += 8) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) butterfly<false>(x[gbase + i], x[gbase + i + 4], w[0], q);
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+          if (!(i & 2)) butterfly<false>(x[gbase + i], x[gbase + i + 2], w[1 + (i >> 2)], q);
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) butterfly<false>(x[gbase + i], x[gbase + i + 1], w[3 + (i >> 1)], q);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kBfly; r++) out ^= x[r];
   } else {
     uint32_t a[kMads];
     const uint32_t x = lo32(h) | 1u, y = hi32(h);
@@ -137,6 +169,7 @@ extern "C" zr_status zr_measure_peaks(zr_ctx* ctx, zr_peaks* out, void* stream) 
   if (!r) r = time_probe<1>(ctx, st, sink, kChains, &p.chain_per_s);
   if (!r) r = time_probe<2>(ctx, st, sink, kMads, &p.imad_lo_per_s);
   if (!r) r = time_probe<3>(ctx, st, sink, kMads, &p.imad_hi_per_s);
+  if (!r) r = time_probe<4>(ctx, st, sink, 3 * kBfly / 2, &p.butterfly_per_s);
   if (r) return r;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess) p.sms = prop.multiProcessorCount;

@@ -76,7 +76,7 @@ class zr_result(ctypes.Structure):
 class zr_peaks(ctypes.Structure):
     _fields_ = [("mac_per_s", ctypes.c_double), ("chain_per_s", ctypes.c_double),
                 ("imad_lo_per_s", ctypes.c_double), ("imad_hi_per_s", ctypes.c_double),
-                ("sms", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("butterfly_per_s", ctypes.c_double), ("sms", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class zr_request(ctypes.Structure):
@@ -105,6 +105,7 @@ SIGNATURES = {
     "zr_launch_count": (_U64, []),
     "zr_profile_enable": (_ST, [_V, _I32]),
     "zr_profile_query": (_ST, [_V, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+    "zr_profile_work": (_ST, [_V, _I32, ctypes.POINTER(ctypes.c_double)]),
     "zr_autotune_step": (_ST, [_V, _I64, _I32, _I32, _V]),
     "zr_step_plan": (_ST, [_V, _I64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "zr_solve_method": (_ST, [_V, _I32, _I64]),
@@ -230,7 +231,7 @@ class Context:
                                          _ptr(hits), _stream(stream)), "zr_check_arith")
 
     def measure_peaks(self, stream=None) -> dict:
-        """Measured MAC / chain-step / IMAD rates (operations per second)."""
+        """Measured MAC / chain-step / IMAD / transform-butterfly rates (operations per second)."""
         p = zr_peaks()
         self.check(self.L.zr_measure_peaks(self._h, ctypes.byref(p), _stream(stream)), "zr_measure_peaks")
         return {f: getattr(p, f) for f, _ in zr_peaks._fields_ if f != "pad"}
@@ -238,7 +239,7 @@ class Context:
     def workspace_bytes(self) -> int:
         return int(self.L.zr_workspace_bytes(self._h))
 
-    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval", "fast")
+    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval", "fast", "ntt")
     SOLVE_AUTO, SOLVE_QUADRATIC, SOLVE_FAST = 0, 1, 2
 
     def solve_method(self, method, crossover=0):
@@ -262,6 +263,13 @@ class Context:
         n = ctypes.c_int64()
         self.check(self.L.zr_profile_query(self._h, idx, ctypes.byref(ms), ctypes.byref(n)), "zr_profile_query")
         return ms.value, n.value
+
+    def profile_work(self, phase):
+        """zr_profile_work: the algorithmic work recorded with a phase (butterflies for "ntt")."""
+        idx = self.PHASES.index(phase) if isinstance(phase, str) else int(phase)
+        u = ctypes.c_double()
+        self.check(self.L.zr_profile_work(self._h, idx, ctypes.byref(u)), "zr_profile_work")
+        return u.value
 
 
     # ------------------------------------------------------------------ calls

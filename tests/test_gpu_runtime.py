@@ -50,8 +50,10 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
 def test_measured_ceilings_are_consistent(ctx):
     p = ctx.measure_peaks()
     assert p["sms"] > 0
-    for k in ("mac_per_s", "chain_per_s", "imad_lo_per_s", "imad_hi_per_s"):
+    for k in ("mac_per_s", "chain_per_s", "imad_lo_per_s", "imad_hi_per_s", "butterfly_per_s"):
         assert p[k] > 1e9, (k, p[k])
+    # a butterfly takes one mad.hi (x w') and two 32-bit products
+    assert p["butterfly_per_s"] <= p["imad_hi_per_s"] * 1.05
     # a 64x64 multiply-accumulate needs four mad.lo and four mad.hi
     assert p["mac_per_s"] <= p["imad_lo_per_s"] / 4 * 1.05
     assert p["mac_per_s"] <= p["imad_hi_per_s"] / 4 * 1.05 * 2
