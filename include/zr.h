@@ -137,10 +137,12 @@ typedef struct zr_peaks {
 } zr_peaks;
 zr_status zr_measure_peaks(zr_ctx* ctx, zr_peaks* out, void* stream);
 
-/* Autotuner of the solve's launch plan (right-hand-side tile x k-block
- * count): times the `budget` best-ranked candidate plans on synthetic data of
- * shape (T, S) and records the fastest in the context; later calls with that
- * shape use it.  Plans change the schedule only, never the values.
+/* Autotuner of the O(T^2) solve's launch plan (right-hand-side tile x
+ * k-block count): times the `budget` best-ranked candidate plans of that
+ * method (whatever zr_solve_method chose) on synthetic data of shape (T, S)
+ * and records the fastest in the context; later calls with that shape that
+ * take the O(T^2) method use it.  Plans change the schedule only, never the
+ * values.
  * zr_step_plan reports the plan a call of shape (T, S) would use. */
 zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t budget, void* stream);
 zr_status zr_step_plan(zr_ctx* ctx, int64_t T, int32_t S, int32_t* s_tile, int32_t* nblocks);
@@ -175,8 +177,9 @@ typedef struct zr_vsys {
  *   0  by size: the O(T log^2 T) method for T >= crossover, the O(T^2)
  *      method below it; crossover 0 takes the library's measured rule for a
  *      system of S right-hand sides, T >= 4096 and T^2 (S + 15) >= 1.4e9
- *      (about T >= 6100 for S = 21, 10000 for S = 1), and T >= 12000 for
- *      the evaluator of the probes;
+ *      (about T >= 6100 for S = 21, 10000 for S = 1); for the probes of a
+ *      function of Tf terms, the transposed-tree evaluator when T, Tf >=
+ *      4096 and T Tf (S + 10) >= 3e9;
  *   1  always the O(T^2) method of Sec. 2.2 (Horner quotients, deferred dot
  *      products, one inverse per root);
  *   2  the O(T log^2 T) method for every T it supports.

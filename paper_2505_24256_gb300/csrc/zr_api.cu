@@ -429,16 +429,19 @@ bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S) {
 }
 }  // namespace zr
 
-// Size from which the automatic choice takes the fast evaluator for the
-// probes (both the terms of f and the probes per sample at least this many).
-static constexpr int64_t kFastProbeMinT = 12000;
+// The automatic choice of evaluator for T probes per sample of a function
+// of Tf terms and S samples.  Measured on GB300 (Tf = T): the matrix-vector
+// evaluator costs about S T Tf 5e-10 ms + 0.2 ms, the transposed tree 0.7 to
+// 2.4 ms from T = 4096 to 32768; they cross near T = 10000 (S = 21) and
+// 14500 (S = 5), which T Tf (S + 10) >= 3e9 follows.
+static constexpr double kFastProbeCross = 3e9;
 
 namespace zr {
 bool use_fast_probes(const zr_ctx* ctx, int64_t T, int64_t Tf, int S) {
   if (T < 1 || Tf < 1 || T > kFastMaxT || S > kFastProbeMaxS || ctx->solve_method == 1) return false;
   if (ctx->solve_method == 2) return true;
-  const int64_t m = ctx->fast_min_T > 0 ? ctx->fast_min_T : kFastProbeMinT;
-  return T >= m && Tf >= m;
+  if (ctx->fast_min_T > 0) return T >= ctx->fast_min_T && Tf >= ctx->fast_min_T;
+  return T >= kFastFloorT && Tf >= kFastFloorT && (double)T * (double)Tf * (double)(S + 10) >= kFastProbeCross;
 }
 }  // namespace zr
 

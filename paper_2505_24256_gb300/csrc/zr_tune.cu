@@ -92,6 +92,9 @@ extern "C" zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t
   double best_ms = -1;
   StepDims best = cand.empty() ? plan_step(ctx, T, S) : cand[0].second;
   zr_status r = ZR_OK;
+  // the plan is the O(T^2) solve's: time that method whatever the context's choice
+  const int method = ctx->solve_method;
+  ctx->solve_method = 1;
   for (auto& c : cand) {
     ctx->plans = saved;
     ctx->plans.push_back({T, S, c.second});
@@ -114,6 +117,7 @@ extern "C" zr_status zr_autotune_step(zr_ctx* ctx, int64_t T, int32_t S, int32_t
     }
   }
   ctx->plans = saved;
+  ctx->solve_method = method;
   cudaStreamSynchronize(st);
   cudaMemsetAsync(ctx->d_status_call, 0, sizeof(uint32_t), st);   // synthetic nodes may collide: not an error here
   cudaFree(v);
