@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "zr_device.cuh"
@@ -734,6 +735,119 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
   cluster_sync();
 }
 
+// ---- levels small enough for one CTA per prime: clusters of kNP CTAs ---------------
+//
+// The same levels as k_tree_fused / k_desc_fused / k_up_fused with a node's
+// five transforms spread over a cluster, CTA i holding prime i's: a fifth of
+// the shared memory and five times the CTAs of the one-CTA form.  After the
+// inverse transforms a cluster barrier makes every CTA's residues visible,
+// each CTA remainders a fifth of the node's outputs reading the five
+// residues of a coefficient through distributed shared memory, and a last
+// barrier keeps the CTAs resident until the others are done reading.
+
+// Threads of a cluster CTA at transform size 2^logn.
+inline int cluster_threads(int logn) { return std::min(kFusedThreads, std::max(64, (1 << logn) >> 2)); }
+
+// Tree level l <= kFusedLog: the children of node P as full monic
+// polynomials (modulo prime `me`) -> spectra (kept in spec for the descent)
+// -> product -> inverse -> coefficients of P (the wrapped z^n taken off).
+__global__ void __launch_bounds__(kFusedThreads) k_tree_cluster(const uint64_t* __restrict__ below, int64_t T,
+                                                                int64_t Tp, int logn, NttConsts C, CrtScale sc, Mod M,
+                                                                const uint2* __restrict__ tw, int logN,
+                                                                uint32_t* __restrict__ spec,
+                                                                uint64_t* __restrict__ coef) {
+  extern __shared__ uint32_t fsm[];              // L [n], R [n] (logical words)
+  const int me = cluster_rank();
+  const int64_t P = blockIdx.x / kNP;
+  const int n = 1 << logn, h = n >> 1;
+  const uint32_t q = C.q[me], qi = C.qinv[me];
+  auto prime = [=](int) { return me; };
+  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
+    const int c = e >> logn, k = e & (n - 1);
+    const int64_t child = 2 * P + c;
+    int64_t d = T - child * h;
+    d = d < 0 ? 0 : (d > h ? h : d);
+    fsm[sw(e)] = k < d ? residue64(below[child * h + k], C, me) : (k == d ? 1u : 0u);
+  }
+  __syncthreads();
+  smem_stages<false>(fsm, 0, 2 * n, logn, 0, 0u, tw, logN, C, prime);
+  uint32_t* sp = spec + (int64_t)me * 2 * Tp + (2 * P << logn);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const uint32_t x = fsm[sw(k)], y = fsm[sw(n + k)];
+    sp[k] = x;
+    sp[n + k] = y;
+    fsm[sw(k)] = mont32(sub_if(x, 2 * q), sub_if(y, 2 * q), q, qi);
+  }
+  __syncthreads();
+  smem_stages<true>(fsm, 0, n, logn, 0, 0u, tw + ((size_t)kNP << logN), logN, C, prime);
+  cluster_sync();
+  int64_t d = T - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  const int per = (int)((d + kNP - 1) / kNP);
+  const int lo = me * per, hi = (int)(d < (int64_t)lo + per ? d : (int64_t)lo + per);
+  uint32_t peer[kNP];
+#pragma unroll
+  for (int j = 0; j < kNP; j++) peer[j] = cluster_addr(fsm, j);
+  for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+    uint32_t res[kNP];
+#pragma unroll
+    for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(k)), sc.s[j], sc.sp[j], C.q[j]);
+    uint64_t x = crt_to_p(res, C, M);
+    if (k == 0 && d == n) x = sub_mod(x, 1, M);
+    coef[P * n + k] = x;
+  }
+  cluster_sync();
+}
+
+// Descent level l <= kFusedLog, node P and right-hand side r per cluster:
+// X_P reversed (modulo prime `me`) -> spectrum -> times each child's sibling
+// spectrum -> inverse -> the children's expansions.
+__global__ void __launch_bounds__(kFusedThreads) k_desc_cluster(const uint64_t* __restrict__ X, int64_t T, int64_t Tp,
+                                                                int logn, NttConsts C, CrtScale sc, Mod M,
+                                                                const uint2* __restrict__ tw, int logN,
+                                                                const uint32_t* __restrict__ spec,
+                                                                uint64_t* __restrict__ Xn, int64_t nodes) {
+  extern __shared__ uint32_t fsm[];              // XH [n], Y [2][n] at n (logical words)
+  const int me = cluster_rank();
+  const int64_t cl = blockIdx.x / kNP;
+  const int64_t P = cl % nodes;
+  const int r = (int)(cl / nodes);
+  const int n = 1 << logn, h = n >> 1;
+  const uint32_t q = C.q[me], qi = C.qinv[me];
+  auto prime = [=](int) { return me; };
+  int64_t d = T - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  const uint64_t* x = X + (int64_t)r * Tp + P * n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) fsm[sw(k)] = k < d ? residue64(x[d - 1 - k], C, me) : 0u;
+  __syncthreads();
+  smem_stages<false>(fsm, 0, n, logn, 0, 0u, tw, logN, C, prime);
+  const uint32_t* sp = spec + (int64_t)me * 2 * Tp + (2 * P << logn);
+  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
+    const int c = e >> logn, k = e & (n - 1);
+    const uint32_t sib = sp[((1 - c) << logn) + k];       // child c times its sibling
+    fsm[sw(n + e)] = mont32(sub_if(fsm[sw(k)], 2 * q), sub_if(sib, 2 * q), q, qi);
+  }
+  __syncthreads();
+  smem_stages<true>(fsm, n, 2 * n, logn, 0, 0u, tw + ((size_t)kNP << logN), logN, C, prime);
+  cluster_sync();
+  const int dl = (int)(d < h ? d : h);
+  const int per = (int)((d + kNP - 1) / kNP);
+  const int lo = me * per, hi = (int)(d < (int64_t)lo + per ? d : (int64_t)lo + per);
+  uint32_t peer[kNP];
+#pragma unroll
+  for (int j = 0; j < kNP; j++) peer[j] = cluster_addr(fsm, j);
+  for (int o = lo + threadIdx.x; o < hi; o += blockDim.x) {
+    const int c = o < dl ? 0 : 1;
+    const int m = c ? o - dl : o;
+    const int at = n + (c << logn) + (int)(d - 1 - m);
+    uint32_t res[kNP];
+#pragma unroll
+    for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(at)), sc.s[j], sc.sp[j], C.q[j]);
+    Xn[(int64_t)r * Tp + (2 * P + c) * h + m] = crt_to_p(res, C, M);
+  }
+  cluster_sync();
+}
+
 // ---- leaves --------------------------------------------------------------------------
 
 constexpr int kLeaf = 128;                     // roots per leaf block (tree level 7)
@@ -771,48 +885,50 @@ __global__ void __launch_bounds__(kLeaf) k_fast_leafpoly(const uint64_t* __restr
 // Leaf values: for root j of block P (degree d), val_r = <q^P_j, X_P^(r)>,
 // q^P_{j,d-1} = 1, q^P_{j,k-1} = p_k + v_j q^P_{j,k}.  Rows r < R - 1 are the
 // right-hand sides (written to part[r ldp + j]), row R - 1 the power sums
-// (M'(v_j), written to den[j]).  The chain is rerun per group of 8 rows.
-constexpr int kLeafCols = 8;
+// (M'(v_j), written to den[j]).  A CTA takes one block and one group of
+// kLeafCols rows (blockIdx.y), each thread one root, rerunning the chain per
+// group so that the groups run in parallel.
+constexpr int kLeafCols = 4;
+
 __global__ void __launch_bounds__(kLeaf) k_fast_leafval(const uint64_t* __restrict__ coef7,
                                                         const uint64_t* __restrict__ X, int R, int64_t T, int64_t Tp,
                                                         const uint64_t* __restrict__ v, const uint64_t* __restrict__ vp,
                                                         Mod M, uint64_t* __restrict__ part, int64_t ldp,
                                                         uint64_t* __restrict__ den) {
-  extern __shared__ uint64_t lsm[];
-  uint64_t* pc = lsm;                 // block polynomial, kLeaf words
-  uint64_t* xs = lsm + kLeaf;         // X rows, R x kLeaf
+  __shared__ uint64_t pc[kLeaf];                 // block polynomial
+  __shared__ uint64_t xs[kLeafCols][kLeaf];      // this group's X rows
   const int64_t base = (int64_t)blockIdx.x * kLeaf;
+  const int r0 = blockIdx.y * kLeafCols;
   const int d = (int)((T - base) < kLeaf ? (T - base) : kLeaf);
   const int t = threadIdx.x;
   if (t < d) pc[t] = coef7[base + t];
-  for (int r = 0; r < R; r++)
-    if (t < d) xs[r * kLeaf + t] = X[(int64_t)r * Tp + base + t];
+#pragma unroll
+  for (int c = 0; c < kLeafCols; c++)
+    if (t < d && r0 + c < R) xs[c][t] = X[(int64_t)(r0 + c) * Tp + base + t];
   __syncthreads();
   if (t >= d) return;
   const int64_t j = base + t;
   const uint64_t vj = v[j], vpj = vp[j];
-  for (int r0 = 0; r0 < R; r0 += kLeafCols) {
-    Acc8 acc[kLeafCols];
+  Acc8 acc[kLeafCols];
 #pragma unroll
-    for (int c = 0; c < kLeafCols; c++) acc[c] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
-    uint64_t q = 1;
-    for (int k = d - 1; k >= 0; k--) {
-      const uint64_t qc = canon(q, M);
-      const uint32_t x0 = lo32(qc), x1 = hi32(qc);
+  for (int c = 0; c < kLeafCols; c++) acc[c] = Acc8{0, 0, 0, 0, 0, 0, 0, 0};
+  uint64_t q = 1;
+  for (int k = d - 1; k >= 0; k--) {
+    const uint64_t qc = canon(q, M);
+    const uint32_t x0 = lo32(qc), x1 = hi32(qc);
 #pragma unroll
-      for (int c = 0; c < kLeafCols; c++)
-        if (r0 + c < R) {
-          const uint64_t w = xs[(r0 + c) * kLeaf + k];
-          mac8(acc[c], x0, x1, lo32(w), hi32(w));
-        }
-      q = canon(shoup_lazy(qc, vj, vpj, M), M) + pc[k];
-    }
+    for (int c = 0; c < kLeafCols; c++)
+      if (r0 + c < R) {
+        const uint64_t w = xs[c][k];
+        mac8(acc[c], x0, x1, lo32(w), hi32(w));
+      }
+    q = canon(shoup_lazy(qc, vj, vpj, M), M) + pc[k];
+  }
 #pragma unroll
-    for (int c = 0; c < kLeafCols; c++) {
-      const int r = r0 + c;
-      if (r < R - 1) part[(int64_t)r * ldp + j] = acc8_value(acc[c], M);
-      else if (r == R - 1) den[j] = acc8_value(acc[c], M);
-    }
+  for (int c = 0; c < kLeafCols; c++) {
+    const int r = r0 + c;
+    if (r < R - 1) part[(int64_t)r * ldp + j] = acc8_value(acc[c], M);
+    else if (r == R - 1) den[j] = acc8_value(acc[c], M);
   }
 }
 
@@ -949,6 +1065,57 @@ __global__ void __launch_bounds__(kFusedThreads) k_up_fused(const uint64_t* __re
     for (int i = 0; i < kNP; i++) res[i] = shoup32(fsm[sw(((a * kNP + i) << logn) + k)], sc.s[i], sc.sp[i], C.q[i]);
     dst[P * n + k] = crt_to_p(res, C, M);
   }
+}
+
+// Up level l <= kFusedLog on a cluster per (node P, column): the children's
+// numerators (modulo prime `me`) -> spectra -> N_L M_R + N_R M_L with the
+// tree's spectra -> inverse -> N_P (see the cluster levels of the solve).
+__global__ void __launch_bounds__(kFusedThreads) k_up_cluster(const uint64_t* __restrict__ Nprev, int64_t G,
+                                                              int64_t Gp, int logn, NttConsts C, CrtScale sc, Mod M,
+                                                              const uint2* __restrict__ tw, int logN,
+                                                              const uint32_t* __restrict__ spec,
+                                                              uint64_t* __restrict__ Nout, int64_t nodes) {
+  extern __shared__ uint32_t fsm[];              // N_L [n], N_R [n] (logical words)
+  const int me = cluster_rank();
+  const int64_t cl = blockIdx.x / kNP;
+  const int64_t P = cl % nodes;
+  const int col = (int)(cl / nodes);
+  const int n = 1 << logn, h = n >> 1;
+  const uint32_t q = C.q[me], qi = C.qinv[me];
+  auto prime = [=](int) { return me; };
+  const uint64_t* src = Nprev + (int64_t)col * Gp;
+  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
+    const int c = e >> logn, k = e & (n - 1);
+    const int64_t child = 2 * P + c;
+    int64_t d = G - child * h;
+    d = d < 0 ? 0 : (d > h ? h : d);
+    fsm[sw(e)] = k < d ? residue64(src[child * h + k], C, me) : 0u;
+  }
+  __syncthreads();
+  smem_stages<false>(fsm, 0, 2 * n, logn, 0, 0u, tw, logN, C, prime);
+  const uint32_t* sp = spec + (int64_t)me * 2 * Gp + (2 * P << logn);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const uint32_t sL = sub_if(sp[k], 2 * q), sR = sub_if(sp[n + k], 2 * q);
+    fsm[sw(k)] = mont32(sub_if(fsm[sw(k)], 2 * q), sR, q, qi) + mont32(sub_if(fsm[sw(n + k)], 2 * q), sL, q, qi);
+  }
+  __syncthreads();
+  smem_stages<true>(fsm, 0, n, logn, 0, 0u, tw + ((size_t)kNP << logN), logN, C, prime);
+  cluster_sync();
+  int64_t d = G - P * n;
+  d = d < 0 ? 0 : (d > n ? n : d);
+  const int per = (int)((d + kNP - 1) / kNP);
+  const int lo = me * per, hi = (int)(d < (int64_t)lo + per ? d : (int64_t)lo + per);
+  uint32_t peer[kNP];
+#pragma unroll
+  for (int j = 0; j < kNP; j++) peer[j] = cluster_addr(fsm, j);
+  uint64_t* dst = Nout + (int64_t)col * Gp + P * n;
+  for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+    uint32_t res[kNP];
+#pragma unroll
+    for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(k)), sc.s[j], sc.sp[j], C.q[j]);
+    dst[k] = crt_to_p(res, C, M);
+  }
+  cluster_sync();
 }
 
 // Up level l > kFusedLog in separate passes: A[s][i][(2P + c) n + k] (planes
@@ -1180,6 +1347,27 @@ struct FastRun {
   }
 };
 
+// Launches `kernel` on `clusters` clusters of kNP CTAs.
+template <class... P, class... A>
+cudaError_t launch_cluster(void (*kernel)(P...), int64_t clusters, int threads, size_t smem, cudaStream_t st,
+                           A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * kNP));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kNP;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+  note_launch();
+  return e;
+}
+
 // Shared memory of k_newton_cluster for K = 2^logK: three swizzled
 // buffers of up to K words (rounded to whole 32-word rows) and g mod q.
 size_t newton_cluster_smem(int logK) {
@@ -1226,6 +1414,10 @@ void configure_fused() {
     cudaFuncSetAttribute(k_desc_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_up_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_newton_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int cbytes = (int)(sizeof(uint32_t) * 3 * kFusedMax);
+    cudaFuncSetAttribute(k_tree_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, cbytes);
+    cudaFuncSetAttribute(k_desc_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, cbytes);
+    cudaFuncSetAttribute(k_up_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, cbytes);
     cudaFuncSetAttribute(k_up_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(uint64_t) * 2 * kLeaf * (1 + kFastProbeMaxS)));
   });
@@ -1241,6 +1433,13 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
     uint32_t* sp = spec[l - 1];
     if (logn <= kFusedLog) {
       const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
+      if (newton_cluster_ok()) {
+        const cudaError_t e = launch_cluster(k_tree_cluster, nodes, cluster_threads(logn),
+                                             sizeof(uint32_t) * 2 << logn, st, coef[l - 1], T, Tp, logn, C,
+                                             crt_scale(logn), M, tw, logN, sp, coef[l]);
+        if (e == cudaSuccess) continue;
+        (void)cudaGetLastError();
+      }
       const int npc = fused_npc(logn);
       k_tree_fused<<<(unsigned)((nodes + npc - 1) / npc), kFusedThreads,
                      sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(coef[l - 1], T, Tp, logn, C, crt_scale(logn), M,
@@ -1264,25 +1463,15 @@ void FastRun::inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, 
   const int logK0 = std::min(ilog2(prec), kFusedLog);
   bool done = false;
   if (newton_cluster_ok()) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kNP);
-    cfg.blockDim = dim3(kNewtonThreadsF);
-    cfg.dynamicSmemBytes = newton_cluster_smem(logK0);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kNP;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    done = cudaLaunchKernelEx(&cfg, k_newton_cluster, f, nf, logK0, C, M, tw, logN, g) == cudaSuccess;
+    done = launch_cluster(k_newton_cluster, 1, kNewtonThreadsF, newton_cluster_smem(logK0), st, f, nf, logK0, C, M,
+                          tw, logN, g) == cudaSuccess;
     if (!done) (void)cudaGetLastError();
   }
-  if (!done)
+  if (!done) {
     k_newton_fused<<<1, kNewtonThreadsF, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(f, nf, logK0, C, M, tw, logN, g,
                                                                                   e);
-  note_launch();
+    note_launch();
+  }
   for (int64_t k = 1ll << logK0; k < prec; k *= 2) {
     const int logk2 = ilog2(2 * k);
     const int64_t fn = std::min<int64_t>(2 * k, nf);
@@ -1436,11 +1625,20 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     const int logn = kLeafLog + l;
     if (logn <= kFusedLog) {
       const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
-      const int npc = fused_npc(logn);
-      k_desc_fused<<<(unsigned)((nodes + npc - 1) / npc * R), kFusedThreads,
-                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(X, T, Tp, logn, C, crt_scale(logn), M, tw, logN,
-                                                                     w.spec[l - 1], Xn, nodes);
-      note_launch();
+      bool done = false;
+      if (newton_cluster_ok()) {
+        done = launch_cluster(k_desc_cluster, nodes * R, cluster_threads(logn), sizeof(uint32_t) * 3 << logn, st, X,
+                              T, Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn,
+                              nodes) == cudaSuccess;
+        if (!done) (void)cudaGetLastError();
+      }
+      if (!done) {
+        const int npc = fused_npc(logn);
+        k_desc_fused<<<(unsigned)((nodes + npc - 1) / npc * R), kFusedThreads,
+                       sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(X, T, Tp, logn, C, crt_scale(logn), M, tw,
+                                                                       logN, w.spec[l - 1], Xn, nodes);
+        note_launch();
+      }
       std::swap(X, Xn);
       continue;
     }
@@ -1456,13 +1654,8 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     std::swap(X, Xn);
   }
   // leaves
-  const size_t smem = sizeof(uint64_t) * (size_t)kLeaf * (1 + R);
-  static DeviceOnce attr;
-  attr.run([] {
-    cudaFuncSetAttribute(k_fast_leafval, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(uint64_t) * kLeaf * (1 + 65)));
-  });
-  k_fast_leafval<<<cdivu(T, kLeaf), kLeaf, smem, st>>>(w.coef[0], X, R, T, Tp, v, vp, M, part, T, den);
+  k_fast_leafval<<<dim3(cdivu(T, kLeaf), (unsigned)((R + kLeafCols - 1) / kLeafCols)), kLeaf, 0, st>>>(
+      w.coef[0], X, R, T, Tp, v, vp, M, part, T, den);
   note_launch();
   return cuda_err(ctx, cudaGetLastError(), "fast solve");
 }
@@ -1503,10 +1696,19 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
     const int logn = kLeafLog + l;
     const int64_t nodes = (G + (1ll << logn) - 1) >> logn;
     if (logn <= kFusedLog) {
-      const int npc = fused_npc(logn);
-      k_up_fused<<<(unsigned)((nodes + npc - 1) / npc * S), kFusedThreads, sizeof(uint32_t) * 2 * kNP * npc << logn,
-                   st>>>(Nc, G, Gp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Nn, nodes);
-      note_launch();
+      bool done = false;
+      if (newton_cluster_ok()) {
+        done = launch_cluster(k_up_cluster, nodes * S, cluster_threads(logn), sizeof(uint32_t) * 2 << logn, st, Nc,
+                              G, Gp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Nn, nodes) == cudaSuccess;
+        if (!done) (void)cudaGetLastError();
+      }
+      if (!done) {
+        const int npc = fused_npc(logn);
+        k_up_fused<<<(unsigned)((nodes + npc - 1) / npc * S), kFusedThreads,
+                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(Nc, G, Gp, logn, C, crt_scale(logn), M, tw,
+                                                                     logN, w.spec[l - 1], Nn, nodes);
+        note_launch();
+      }
     } else {
       k_up_load<<<cdivu((int64_t)S * 2 * Gp, 256), 256, 0, st>>>(Nc, S, G, Gp, logn, C, w.A);
       note_launch();
