@@ -413,35 +413,36 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
 extern "C" const char* zr_last_error(const zr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 // The automatic choice of solve method.  On GB300 the O(T^2) batch costs
-// about 0.3 ms + T^2 (5.5e-10 S + 7.7e-9) ms for one system of S right-hand
-// sides, the O(T log^2 T) path 0.8 to 1.5 ms from T = 4096 to 16384 almost
-// independently of S; they cross near T = 6100 (S = 21), 7800 (S = 5) and
-// 10000 (S = 1), which T^2 (S + 15) >= 1.4e9 follows within 10%.
-static constexpr double kFastCross = 1.4e9;
-static constexpr int64_t kFastFloorT = 4096;
+// about 0.2 ms + T^2 (5e-10 S + 8e-9) ms for one system of S right-hand
+// sides, the O(T log^2 T) path 0.4 to 1.2 ms from T = 1024 to 16384 nearly
+// independently of S; they cross near T = 3300 (S = 21), 5000 (S = 5) and
+// 6500 (S = 1), which T^2 (S + 6) >= 2.9e8 follows within 10%.
+static constexpr double kFastCross = 2.9e8;
+static constexpr int64_t kFastFloorT = 2048;
 
 namespace zr {
 bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S) {
   if (T < 1 || T > kFastMaxT || ctx->solve_method == 1) return false;
   if (ctx->solve_method == 2) return true;
   if (ctx->fast_min_T > 0) return T >= ctx->fast_min_T;
-  return T >= kFastFloorT && (double)T * (double)T * (double)(S + 15) >= kFastCross;
+  return T >= kFastFloorT && (double)T * (double)T * (double)(S + 6) >= kFastCross;
 }
 }  // namespace zr
 
 // The automatic choice of evaluator for T probes per sample of a function
 // of Tf terms and S samples.  Measured on GB300 (Tf = T): the matrix-vector
-// evaluator costs about S T Tf 5e-10 ms + 0.2 ms, the transposed tree 0.7 to
-// 2.4 ms from T = 4096 to 32768; they cross near T = 10000 (S = 21) and
-// 14500 (S = 5), which T Tf (S + 10) >= 3e9 follows.
-static constexpr double kFastProbeCross = 3e9;
+// evaluator costs about S T Tf 5e-10 ms + 0.15 ms, the transposed tree 0.45
+// to 1.5 ms from T = 2048 to 16384; they cross near T = 8300 (S = 21),
+// 13500 (S = 5) and 15000 (S = 1), which T Tf (S + 8) >= 2e9 follows.
+static constexpr double kFastProbeCross = 2e9;
+static constexpr int64_t kFastProbeFloorT = 4096;
 
 namespace zr {
 bool use_fast_probes(const zr_ctx* ctx, int64_t T, int64_t Tf, int S) {
   if (T < 1 || Tf < 1 || T > kFastMaxT || S > kFastProbeMaxS || ctx->solve_method == 1) return false;
   if (ctx->solve_method == 2) return true;
   if (ctx->fast_min_T > 0) return T >= ctx->fast_min_T && Tf >= ctx->fast_min_T;
-  return T >= kFastFloorT && Tf >= kFastFloorT && (double)T * (double)Tf * (double)(S + 10) >= kFastProbeCross;
+  return T >= kFastProbeFloorT && Tf >= kFastProbeFloorT && (double)T * (double)Tf * (double)(S + 8) >= kFastProbeCross;
 }
 }  // namespace zr
 

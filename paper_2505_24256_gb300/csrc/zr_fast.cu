@@ -748,6 +748,13 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
 // Threads of a cluster CTA at transform size 2^logn.
 inline int cluster_threads(int logn) { return std::min(kFusedThreads, std::max(64, (1 << logn) >> 2)); }
 
+// Cluster levels go up to transforms of 2^14 (a descent CTA then holds
+// 192 KB); Newton's cluster runs to precision 2^13.  Above 2^12 a level
+// takes the cluster form only when its CTAs fit in two waves: with many
+// nodes the tile kernels' higher occupancy wins.
+constexpr int kClusterMaxLog = 14;
+constexpr int kNewtonClusterLog = 13;
+
 // Tree level l <= kFusedLog: the children of node P as full monic
 // polynomials (modulo prime `me`) -> spectra (kept in spec for the descent)
 // -> product -> inverse -> coefficients of P (the wrapped z^n taken off).
@@ -1312,6 +1319,7 @@ FastWs carve_fast(Carver& cv, int64_t T, int R) {
 void configure_fused();
 bool newton_cluster_ok();
 size_t newton_cluster_smem(int logK);
+bool cluster_level(const zr_ctx* ctx, int logn, int64_t clusters);
 
 struct FastRun {
   zr_ctx* ctx;
@@ -1380,7 +1388,7 @@ size_t newton_cluster_smem(int logK) {
 bool newton_cluster_ok() {
   static DeviceValue ok;
   return ok.get([] {
-           const size_t bytes = newton_cluster_smem(kFusedLog);
+           const size_t bytes = newton_cluster_smem(kNewtonClusterLog);
            if (cudaFuncSetAttribute(k_newton_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
                cudaSuccess) {
              (void)cudaGetLastError();
@@ -1406,6 +1414,13 @@ bool newton_cluster_ok() {
          }) == 1;
 }
 
+// Whether a level of `clusters` clusters at transform size 2^logn takes the
+// cluster kernels.
+bool cluster_level(const zr_ctx* ctx, int logn, int64_t clusters) {
+  if (!newton_cluster_ok() || logn > kClusterMaxLog) return false;
+  return logn <= kFusedLog || clusters * kNP <= 2 * (int64_t)ctx->sms;
+}
+
 void configure_fused() {
   static DeviceOnce fused_attr;
   fused_attr.run([] {
@@ -1414,10 +1429,10 @@ void configure_fused() {
     cudaFuncSetAttribute(k_desc_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_up_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_newton_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    const int cbytes = (int)(sizeof(uint32_t) * 3 * kFusedMax);
-    cudaFuncSetAttribute(k_tree_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, cbytes);
-    cudaFuncSetAttribute(k_desc_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, cbytes);
-    cudaFuncSetAttribute(k_up_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, cbytes);
+    const int c2 = (int)(sizeof(uint32_t) * 2 << kClusterMaxLog), c3 = (int)(sizeof(uint32_t) * 3 << kClusterMaxLog);
+    cudaFuncSetAttribute(k_tree_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, c2);
+    cudaFuncSetAttribute(k_desc_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, c3);
+    cudaFuncSetAttribute(k_up_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, c2);
     cudaFuncSetAttribute(k_up_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(uint64_t) * 2 * kLeaf * (1 + kFastProbeMaxS)));
   });
@@ -1431,15 +1446,15 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
   for (int l = 1; l <= Lt; l++) {
     const int logn = kLeafLog + l;
     uint32_t* sp = spec[l - 1];
+    const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
+    if (cluster_level(ctx, logn, nodes)) {
+      const cudaError_t e = launch_cluster(k_tree_cluster, nodes, cluster_threads(logn), sizeof(uint32_t) * 2 << logn,
+                                           st, coef[l - 1], T, Tp, logn, C, crt_scale(logn), M, tw, logN, sp,
+                                           coef[l]);
+      if (e == cudaSuccess) continue;
+      (void)cudaGetLastError();
+    }
     if (logn <= kFusedLog) {
-      const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
-      if (newton_cluster_ok()) {
-        const cudaError_t e = launch_cluster(k_tree_cluster, nodes, cluster_threads(logn),
-                                             sizeof(uint32_t) * 2 << logn, st, coef[l - 1], T, Tp, logn, C,
-                                             crt_scale(logn), M, tw, logN, sp, coef[l]);
-        if (e == cudaSuccess) continue;
-        (void)cudaGetLastError();
-      }
       const int npc = fused_npc(logn);
       k_tree_fused<<<(unsigned)((nodes + npc - 1) / npc), kFusedThreads,
                      sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(coef[l - 1], T, Tp, logn, C, crt_scale(logn), M,
@@ -1460,7 +1475,7 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
 
 void FastRun::inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, uint64_t* e, uint32_t* A,
                       uint32_t* B, uint32_t* Z) {
-  const int logK0 = std::min(ilog2(prec), kFusedLog);
+  int logK0 = std::min(ilog2(prec), kNewtonClusterLog);
   bool done = false;
   if (newton_cluster_ok()) {
     done = launch_cluster(k_newton_cluster, 1, kNewtonThreadsF, newton_cluster_smem(logK0), st, f, nf, logK0, C, M,
@@ -1468,6 +1483,7 @@ void FastRun::inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, 
     if (!done) (void)cudaGetLastError();
   }
   if (!done) {
+    logK0 = std::min(logK0, kFusedLog);
     k_newton_fused<<<1, kNewtonThreadsF, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(f, nf, logK0, C, M, tw, logN, g,
                                                                                   e);
     note_launch();
@@ -1623,22 +1639,22 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   uint64_t* Xn = w.X1;
   for (int l = Lt; l >= 1; l--) {
     const int logn = kLeafLog + l;
-    if (logn <= kFusedLog) {
-      const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
-      bool done = false;
-      if (newton_cluster_ok()) {
-        done = launch_cluster(k_desc_cluster, nodes * R, cluster_threads(logn), sizeof(uint32_t) * 3 << logn, st, X,
-                              T, Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn,
-                              nodes) == cudaSuccess;
-        if (!done) (void)cudaGetLastError();
-      }
-      if (!done) {
-        const int npc = fused_npc(logn);
-        k_desc_fused<<<(unsigned)((nodes + npc - 1) / npc * R), kFusedThreads,
-                       sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(X, T, Tp, logn, C, crt_scale(logn), M, tw,
-                                                                       logN, w.spec[l - 1], Xn, nodes);
-        note_launch();
-      }
+    const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
+    bool done = false;
+    if (cluster_level(ctx, logn, nodes * R)) {
+      done = launch_cluster(k_desc_cluster, nodes * R, cluster_threads(logn), sizeof(uint32_t) * 3 << logn, st, X, T,
+                            Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn, nodes) == cudaSuccess;
+      if (!done) (void)cudaGetLastError();
+    }
+    if (!done && logn <= kFusedLog) {
+      const int npc = fused_npc(logn);
+      k_desc_fused<<<(unsigned)((nodes + npc - 1) / npc * R), kFusedThreads,
+                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(X, T, Tp, logn, C, crt_scale(logn), M, tw, logN,
+                                                                     w.spec[l - 1], Xn, nodes);
+      note_launch();
+      done = true;
+    }
+    if (done) {
       std::swap(X, Xn);
       continue;
     }
@@ -1695,21 +1711,21 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
   for (int l = 1; l <= Lt; l++) {
     const int logn = kLeafLog + l;
     const int64_t nodes = (G + (1ll << logn) - 1) >> logn;
-    if (logn <= kFusedLog) {
-      bool done = false;
-      if (newton_cluster_ok()) {
-        done = launch_cluster(k_up_cluster, nodes * S, cluster_threads(logn), sizeof(uint32_t) * 2 << logn, st, Nc,
-                              G, Gp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Nn, nodes) == cudaSuccess;
-        if (!done) (void)cudaGetLastError();
-      }
-      if (!done) {
-        const int npc = fused_npc(logn);
-        k_up_fused<<<(unsigned)((nodes + npc - 1) / npc * S), kFusedThreads,
-                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(Nc, G, Gp, logn, C, crt_scale(logn), M, tw,
-                                                                     logN, w.spec[l - 1], Nn, nodes);
-        note_launch();
-      }
-    } else {
+    bool done = false;
+    if (cluster_level(ctx, logn, nodes * S)) {
+      done = launch_cluster(k_up_cluster, nodes * S, cluster_threads(logn), sizeof(uint32_t) * 2 << logn, st, Nc, G,
+                            Gp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Nn, nodes) == cudaSuccess;
+      if (!done) (void)cudaGetLastError();
+    }
+    if (!done && logn <= kFusedLog) {
+      const int npc = fused_npc(logn);
+      k_up_fused<<<(unsigned)((nodes + npc - 1) / npc * S), kFusedThreads,
+                   sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(Nc, G, Gp, logn, C, crt_scale(logn), M, tw, logN,
+                                                                   w.spec[l - 1], Nn, nodes);
+      note_launch();
+      done = true;
+    }
+    if (!done) {
       k_up_load<<<cdivu((int64_t)S * 2 * Gp, 256), 256, 0, st>>>(Nc, S, G, Gp, logn, C, w.A);
       note_launch();
       launch_ntt(ctx, w.A, ((int64_t)S * kNP * 2 * Gp) >> logn, logn, logG + 1, false, tw, itw, logN, C, st);
