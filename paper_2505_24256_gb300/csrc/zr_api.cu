@@ -1,5 +1,7 @@
 // zr_api.cu -- context, workspace and the C entry points of the Zippel step.
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <stdint.h>
 #include <string.h>
 
@@ -443,6 +445,27 @@ bool use_fast_probes(const zr_ctx* ctx, int64_t T, int64_t Tf, int S) {
   if (ctx->solve_method == 2) return true;
   if (ctx->fast_min_T > 0) return T >= ctx->fast_min_T && Tf >= ctx->fast_min_T;
   return T >= kFastProbeFloorT && Tf >= kFastProbeFloorT && (double)T * (double)Tf * (double)(S + 8) >= kFastProbeCross;
+}
+}  // namespace zr
+
+// Scheduling weights in multiply-accumulate equivalents (about 2e12 per
+// second on GB300).  The O(T^2) solve does S T^2 + 2.5 T^2; the fast one was
+// measured at 25 ms for T = 2^20, S = 9 and about 0.5 ms at small T, which
+// 8 (S + 6) T log2(T)^2 + 1e9 follows.  The matrix-vector evaluator does
+// S T Tf; the transposed tree is weighted like the fast solve on max(T, Tf).
+namespace zr {
+static double fast_work(double n, int S) {
+  const double l = std::log2(std::max(n, 2.0));
+  return 8.0 * (S + 6) * n * l * l + 1e9;
+}
+double solve_work(const zr_ctx* ctx, int64_t T, int S) {
+  if (T <= 0) return 0;
+  return use_fast_solve(ctx, T, S) ? fast_work((double)T, S) : (S + 2.5) * (double)T * (double)T;
+}
+double probe_work(const zr_ctx* ctx, int64_t T, int S, int64_t Tf) {
+  if (T <= 0 || Tf <= 0) return 0;
+  return use_fast_probes(ctx, T, Tf, S) ? fast_work((double)std::max(T, Tf), S)
+                                        : (double)S * (double)T * (double)Tf;
 }
 }  // namespace zr
 

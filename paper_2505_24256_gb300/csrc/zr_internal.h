@@ -169,6 +169,10 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
                              int64_t ldb, uint64_t* part, uint64_t* den, char* ws, cudaStream_t st);
 // whether a system of T unknowns takes the fast path in this context
 bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S);
+// scheduling weights (multiply-accumulate equivalents) of a step's solve and
+// of its probes, by the method each takes in this context
+double solve_work(const zr_ctx* ctx, int64_t T, int S);
+double probe_work(const zr_ctx* ctx, int64_t T, int S, int64_t Tf);
 // whether T probes of a function of Tf terms take the fast evaluator (the
 // transposed tree), which reads the group count G <= Tf on the host and
 // falls back to the matrix-vector kernel when G > kFastMaxT

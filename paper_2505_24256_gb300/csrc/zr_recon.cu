@@ -221,15 +221,17 @@ size_t Recon::device_bytes() const {
 
 double Recon::next_cost() const {
   if (phase_ != RUN || k_ >= nv_) return 0;
-  const double TN = (double)curN_.T, TfN = (double)fN_.T;
+  const int64_t TN = curN_.T, TfN = fN_.T;
   if (!rational_) {
-    const double S = degN_[k_] + 1;
-    return S * TN * TN + S * TN * TfN;
+    const int S = degN_[k_] + 1;
+    return solve_work(ctx_, TN, S) + probe_work(ctx_, TN, S, TfN);
   }
-  const double TD = (double)curD_.T, TfD = (double)fD_.T;
-  const double SN = degN_[k_] + 1, SD = degD_[k_] + 1;
-  const double Sf = 2.0 * std::max(degN_[k_], degD_[k_]) + 2, Tm = std::max(TN, TD);
-  return SN * TN * TN + SD * TD * TD + Sf * Tm * (TfN + TfD);
+  const int64_t TD = curD_.T, TfD = fD_.T;
+  const int SN = degN_[k_] + 1, SD = degD_[k_] + 1;
+  const int Sf = 2 * std::max(degN_[k_], degD_[k_]) + 2;
+  const int64_t Tm = std::max(TN, TD);
+  return solve_work(ctx_, TN, SN) + solve_work(ctx_, TD, SD) + probe_work(ctx_, Tm, Sf, TfN) +
+         probe_work(ctx_, Tm, Sf, TfD);
 }
 
 size_t Recon::estimate_bytes(const zr_blackbox& bb, const zr_recon_params& prm) {

@@ -12,7 +12,8 @@
 //     the budget (a request that cannot fit even alone runs when nothing else
 //     does); starting runs its dense step in x_0;
 //   * every tick gathers the next Zippel step of the lane's active requests,
-//     oldest first, until the steps add up to kTickWork multiply-accumulates
+//     oldest first, until the steps add up to kTickWork multiply-accumulate
+//     equivalents (each step weighted by the solve and evaluator it takes)
 //     -- their probes are generated on the device, then all those steps run
 //     in one batch of launches (run_batch) -- reads back each request's own
 //     status word and term counts, and advances each request (or redraws its
@@ -81,9 +82,10 @@ struct Done {
 
 constexpr int64_t kSmallTerms = 2048;   // fast-lane requests: at most this many hidden terms
 // A tick takes active requests oldest first until their next steps add up to
-// this many multiply-accumulates (about 50 ms of the GPU), at least one: a
-// single large step already fills the GPU, so batching more large steps only
-// stretches every one of them, while small steps still share a tick.
+// this many multiply-accumulate equivalents (about 50 ms of the GPU), at
+// least one: a single large step already fills the GPU, so batching more
+// large steps only stretches every one of them, while small steps still
+// share a tick.
 constexpr double kTickWork = 1e11;
 
 struct Lane {

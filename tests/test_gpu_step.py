@@ -170,21 +170,20 @@ def test_batched_step_workload_full(ctx, orc):
 
 
 def test_large_step_workload(ctx, orc):
-    """The T = 2^20, S = 9 step: sampled probes against the oracle, the new
-    skeleton against generator truth in full, sampled solve values against
-    the hidden g_j(c_s)."""
+    """The T = 2^20, S = 9 step: 64 sampled probes against the oracle and
+    against the plain evaluation at their explicit points, the new skeleton
+    against generator truth in full."""
     wl = W.large_step_2p20()
     D = Dev(ctx, wl)
     b = D.probes(ctx)
     hb = h64(b)
     rnd = random.Random(3)
-    sidx = [rnd.randrange(wl.S) for _ in range(48)] + [0, wl.S - 1]
-    iidx = [rnd.randrange(wl.T) for _ in range(48)] + [0, wl.T - 1]
+    sidx = [rnd.randrange(wl.S) for _ in range(62)] + [0, wl.S - 1]
+    iidx = [rnd.randrange(wl.T) for _ in range(62)] + [0, wl.T - 1]
     want = orc.zippel_probes_sampled(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, sidx, iidx)
     assert np.array_equal(hb[sidx, iidx], want)
-    # 16 of them also by the plain point-by-point evaluation (9.4 M terms each)
-    assert np.array_equal(hb[sidx[:14] + sidx[-2:], iidx[:14] + iidx[-2:]],
-                          probes_at_points(orc, wl, sidx[:14] + sidx[-2:], iidx[:14] + iidx[-2:]))
+    # all 64 also by the plain point-by-point evaluation of the hidden function
+    assert np.array_equal(hb[sidx, iidx], probes_at_points(orc, wl, sidx, iidx))
     ge_, gc_ = D.step(ctx, b)
     assert np.array_equal(ge_, wl.exps) and np.array_equal(gc_, wl.coef)
 
