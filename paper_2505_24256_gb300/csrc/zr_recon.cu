@@ -23,6 +23,18 @@ namespace zr {
 
 namespace {
 
+// Small uploads (a step's y powers and samples) travel as kernel parameters:
+// the launch is asynchronous, where a copy from pageable host memory may wait
+// for the stream's queued work.
+constexpr int kParamWords = 128;
+struct ParamWords {
+  uint64_t w[kParamWords];
+};
+__global__ void k_store_words(uint64_t* __restrict__ dst, int n, ParamWords v) {
+  const int i = threadIdx.x;
+  if (i < n) dst[i] = v.w[i];
+}
+
 // ---- splitmix64 as a counter-based generator --------------------------------
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 uint64_t sm_mix(uint64_t z) {
@@ -208,7 +220,15 @@ zr_status Recon::sync_status() {
 
 zr_status Recon::upload(DBuf& b, const void* host, size_t bytes) {
   cudaError_t e = b.ensure(bytes);
-  if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b.p, host, bytes, cudaMemcpyHostToDevice, st_);
+  if (e == cudaSuccess && bytes && bytes % 8 == 0 && bytes <= 8 * (size_t)kParamWords) {
+    ParamWords v;
+    memcpy(v.w, host, bytes);
+    k_store_words<<<1, kParamWords, 0, st_>>>(b.as<uint64_t>(), (int)(bytes / 8), v);
+    note_launch();
+    e = cudaGetLastError();
+  } else if (e == cudaSuccess && bytes) {
+    e = cudaMemcpyAsync(b.p, host, bytes, cudaMemcpyHostToDevice, st_);
+  }
   return cuda_err(ctx_, e, "upload");
 }
 
