@@ -432,6 +432,7 @@ constexpr int kFusedLog = 12;
 constexpr int kFusedMax = 1 << kFusedLog;
 constexpr int kFusedThreads = 512;
 constexpr int kNewtonThreadsF = 1024;   // the single-CTA Newton kernel
+constexpr int kClusterThreadsMax = 1024; // cluster levels of 2^13 and 2^14
 
 // ntr transforms of size 2^logn at logical words off + t 2^logn of sm (the
 // swizzled layout), transform t modulo prime t mod 5; forward (CT) or
@@ -655,6 +656,10 @@ __device__ __forceinline__ uint32_t ld_cluster(uint32_t addr) {
   return v;
 }
 
+// Precision up to which k_newton_cluster runs schoolbook steps.
+constexpr int kNewtonSchool = 256;
+__device__ __forceinline__ int ilog2_dev(int x) { return 31 - __clz(x); }   // x a power of two
+
 // k_newton_fused spread over a cluster of kNP CTAs, CTA i holding prime i's
 // transforms in its shared memory: A (f, then f g), B (g's spectrum), C
 // (e_hi, then g e_hi) in the swizzled layout, and g mod q_i.  Each Chinese
@@ -680,12 +685,44 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
 #pragma unroll
   for (int j = 0; j < kNP; j++) peer[j] = cluster_addr(fsm, j);
   auto prime = [=](int) { return me; };
-  if (threadIdx.x == 0) {
-    Gq[0] = 1;
-    if (me == 0) g[0] = 1;
+  // the first steps, to precision K1, by schoolbook products in 64-bit
+  // residues, every CTA computing the same g (no transforms, no exchange):
+  // e_t = (f g)_{k+t} = sum_{i<k} f_{k+t-i} g_i, then g_{k+t} = -sum_{i<=t} g_i e_{t-i}
+  const int K1 = K < kNewtonSchool ? K : kNewtonSchool;
+  uint64_t* g64 = reinterpret_cast<uint64_t*>(fsm);            // K1 words
+  uint64_t* e64 = g64 + K1;                                     // K1 / 2 words
+  if (threadIdx.x == 0) g64[0] = 1;
+  __syncthreads();
+  for (int k = 1; k < K1; k *= 2) {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      Acc8 acc = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int i = 0; i < k; i++) {
+        const int64_t fi = k + t - i;
+        if (fi < nf) {
+          const uint64_t x = f[fi], y = g64[i];
+          mac8(acc, lo32(x), hi32(x), lo32(y), hi32(y));
+        }
+      }
+      e64[t] = acc8_value(acc, M);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      Acc8 acc = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int i = 0; i <= t; i++) {
+        const uint64_t x = g64[i], y = e64[t - i];
+        mac8(acc, lo32(x), hi32(x), lo32(y), hi32(y));
+      }
+      const uint64_t v = acc8_value(acc, M);
+      g64[k + t] = v ? M.p - v : 0;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < K1; t += blockDim.x) {
+    Gq[t] = residue64(g64[t], C, me);
+    if (me == 0) g[t] = g64[t];
   }
   __syncthreads();
-  for (int lk = 0; lk < logK; lk++) {
+  for (int lk = ilog2_dev(K1); lk < logK; lk++) {
     const int k = 1 << lk, logn = lk + 1, n = 2 * k;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       fsm[sw(t)] = t < nf ? residue64(f[t], C, me) : 0u;
@@ -746,7 +783,9 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
 // barrier keeps the CTAs resident until the others are done reading.
 
 // Threads of a cluster CTA at transform size 2^logn.
-inline int cluster_threads(int logn) { return std::min(kFusedThreads, std::max(64, (1 << logn) >> 2)); }
+inline int cluster_threads(int logn) {
+  return logn >= 13 ? kClusterThreadsMax : std::min(kFusedThreads, std::max(64, (1 << logn) >> 2));
+}
 
 // Cluster levels go up to transforms of 2^14 (a descent CTA then holds
 // 192 KB); Newton's cluster runs to precision 2^13.  Above 2^12 a level
@@ -758,7 +797,7 @@ constexpr int kNewtonClusterLog = 13;
 // Tree level l <= kFusedLog: the children of node P as full monic
 // polynomials (modulo prime `me`) -> spectra (kept in spec for the descent)
 // -> product -> inverse -> coefficients of P (the wrapped z^n taken off).
-__global__ void __launch_bounds__(kFusedThreads) k_tree_cluster(const uint64_t* __restrict__ below, int64_t T,
+__global__ void __launch_bounds__(kClusterThreadsMax) k_tree_cluster(const uint64_t* __restrict__ below, int64_t T,
                                                                 int64_t Tp, int logn, NttConsts C, CrtScale sc, Mod M,
                                                                 const uint2* __restrict__ tw, int logN,
                                                                 uint32_t* __restrict__ spec,
@@ -809,7 +848,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_tree_cluster(const uint64_t* 
 // Descent level l <= kFusedLog, node P and right-hand side r per cluster:
 // X_P reversed (modulo prime `me`) -> spectrum -> times each child's sibling
 // spectrum -> inverse -> the children's expansions.
-__global__ void __launch_bounds__(kFusedThreads) k_desc_cluster(const uint64_t* __restrict__ X, int64_t T, int64_t Tp,
+__global__ void __launch_bounds__(kClusterThreadsMax) k_desc_cluster(const uint64_t* __restrict__ X, int64_t T, int64_t Tp,
                                                                 int logn, NttConsts C, CrtScale sc, Mod M,
                                                                 const uint2* __restrict__ tw, int logN,
                                                                 const uint32_t* __restrict__ spec,
@@ -1077,7 +1116,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_up_fused(const uint64_t* __re
 // Up level l <= kFusedLog on a cluster per (node P, column): the children's
 // numerators (modulo prime `me`) -> spectra -> N_L M_R + N_R M_L with the
 // tree's spectra -> inverse -> N_P (see the cluster levels of the solve).
-__global__ void __launch_bounds__(kFusedThreads) k_up_cluster(const uint64_t* __restrict__ Nprev, int64_t G,
+__global__ void __launch_bounds__(kClusterThreadsMax) k_up_cluster(const uint64_t* __restrict__ Nprev, int64_t G,
                                                               int64_t Gp, int logn, NttConsts C, CrtScale sc, Mod M,
                                                               const uint2* __restrict__ tw, int logN,
                                                               const uint32_t* __restrict__ spec,
