@@ -75,12 +75,14 @@ size_t zr_workspace_bytes(const zr_ctx* ctx);
  * synthetic-division/dot kernel, 5 denominators + inverses + Newton,
  * 6 compaction, 7 probe evaluation, 8 the O(T log^2 T) solve of the systems
  * that take it: tree, power sums, descent and leaves; 9 each launch of that
- * solve's transform tile kernel, inside phase 8); zr_profile_enable resets
- * the totals, zr_profile_query waits for the recorded events and returns the
- * summed milliseconds and the number of timed occurrences of a phase, and
- * zr_profile_work the algorithmic work recorded with them (phase 9: radix-2
- * butterflies, n/2 per stage of a transform of n words; 0 for the others).
- * Errors: ZR_ERR_INVALID_ARG for a phase outside 0..9 or a null pointer. */
+ * solve's transform tile kernel and 10 each launch of its descent's cluster
+ * level kernel, both inside phase 8); zr_profile_enable resets the totals,
+ * zr_profile_query waits for the recorded events and returns the summed
+ * milliseconds and the number of timed occurrences of a phase, and
+ * zr_profile_work the algorithmic work recorded with them (phases 9 and 10:
+ * radix-2 butterflies, n/2 per stage of each transform of n words; 0 for the
+ * others).  Errors: ZR_ERR_INVALID_ARG for a phase outside 0..10 or a null
+ * pointer. */
 uint64_t zr_launch_count(void);
 zr_status zr_profile_enable(zr_ctx* ctx, int32_t on);
 zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count);

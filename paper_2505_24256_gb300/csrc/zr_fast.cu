@@ -1681,9 +1681,13 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
     bool done = false;
     if (cluster_level(ctx, logn, nodes * R)) {
+      cudaEvent_t a = prof_mark(ctx, st);
       done = launch_cluster(k_desc_cluster, nodes * R, cluster_threads(logn), sizeof(uint32_t) * 3 << logn, st, X, T,
                             Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn, nodes) == cudaSuccess;
       if (!done) (void)cudaGetLastError();
+      cudaEvent_t b = prof_mark(ctx, st);
+      // one forward and two inverse transforms of 2^logn per prime of each cluster
+      if (done) prof_add(ctx, PH_DESC, a, b, (double)(nodes * R) * kNP * 3 * (double)((1ll << logn) / 2) * logn);
     }
     if (!done && logn <= kFusedLog) {
       const int npc = fused_npc(logn);

@@ -239,7 +239,7 @@ class Context:
     def workspace_bytes(self) -> int:
         return int(self.L.zr_workspace_bytes(self._h))
 
-    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval", "fast", "ntt")
+    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval", "fast", "ntt", "desc")
     SOLVE_AUTO, SOLVE_QUADRATIC, SOLVE_FAST = 0, 1, 2
 
     def solve_method(self, method, crossover=0):
@@ -265,7 +265,7 @@ class Context:
         return ms.value, n.value
 
     def profile_work(self, phase):
-        """zr_profile_work: the algorithmic work recorded with a phase (butterflies for "ntt")."""
+        """zr_profile_work: the algorithmic work recorded with a phase (butterflies for "ntt" and "desc")."""
         idx = self.PHASES.index(phase) if isinstance(phase, str) else int(phase)
         u = ctypes.c_double()
         self.check(self.L.zr_profile_work(self._h, idx, ctypes.byref(u)), "zr_profile_work")
