@@ -407,6 +407,11 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  for (int j = 0; j < 4; j++) {
+    if (ctx->fstream[j]) cudaStreamDestroy(ctx->fstream[j]);
+    if (ctx->fev_join[j]) cudaEventDestroy(ctx->fev_join[j]);
+  }
+  if (ctx->fev_fork) cudaEventDestroy(ctx->fev_fork);
   if (ctx->ntt_tw) cudaFree(ctx->ntt_tw);
   if (ctx->fprobe_ws) cudaFree(ctx->fprobe_ws);
   delete ctx;

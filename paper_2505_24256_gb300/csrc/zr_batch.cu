@@ -417,7 +417,16 @@ struct Prepared {
   std::vector<char> fast;             // entries solved by the O(T log^2 T) path
   int kmax = 0, smax = 0, lmax = 0, mode = 0;
   size_t ws_bytes = 0, table_bytes = 0, fast_bytes = 0;
+  int nfast = 0, fstreams = 0;        // fast entries, concurrent streams for them (0: the call's stream)
+  size_t fast_slot = 0;               // workspace of one fast stream
 };
+
+// A batch with several O(T log^2 T) entries, or such entries beside O(T^2)
+// ones, runs them on up to kFastStreams streams of their own (each with its
+// workspace slot, entries round-robin) from the anchor values on, beside the
+// tree, carries and ring solve of the others, and joins them before the
+// finish; a lone fast entry runs on the call's stream.
+constexpr int kFastStreams = 4;
 
 static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& P) {
   P.mode = items[0].mode;
@@ -437,7 +446,8 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
       D.BK = it.T;
       D.s_tile = 2;
       P.plan[i] = D;
-      P.fast_bytes = std::max(P.fast_bytes, fast_ws_need(it.T, it.solve_S() + 1));
+      P.fast_slot = std::max(P.fast_slot, (fast_ws_need(it.T, it.solve_S() + 1) + 255) & ~(size_t)255);
+      P.nfast++;
     } else {
       P.plan[i] = plan_step(ctx, it.T, it.solve_S());
       P.lmax = std::max(P.lmax, tree_levels(it.T));
@@ -492,6 +502,8 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
     });
   P.table_bytes = sizeof(BDesc) * n + sizeof(int64_t) * P.pre.size();
   for (auto& wl : P.work) P.table_bytes += sizeof(int4) * wl.size() + 16;
+  P.fstreams = (P.nfast >= 2 || (P.nfast >= 1 && P.nfast < n)) ? std::min(P.nfast, kFastStreams) : 0;
+  P.fast_bytes = P.nfast ? P.fast_slot * (size_t)std::max(P.fstreams, 1) : 0;
   return true;
 }
 
@@ -512,7 +524,7 @@ struct StagedBatch {
   std::vector<const int4*> dwork;
   std::vector<int64_t*> zero_counts;   // out_count of entries with T = 0
   std::vector<BDesc> hD;               // host copy of the descriptors (the fast entries' pointers)
-  char* fast_ws = nullptr;             // workspace of the fast entries (one at a time)
+  char* fast_ws = nullptr;             // workspace of the fast entries: one slot per fast stream
 };
 
 // Plans the batch, carves its workspace at `ws` (batch_ws_need bytes) and
@@ -673,6 +685,35 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   if (mode == 0 && kmax > 0) { k_b_powtab<<<dim3(kmax, n), kPowTab, 0, st>>>(dD, M); note_launch(); }
   if (nroots) { k_b_anchor<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
   cudaEvent_t e1 = mark();
+  // the O(T log^2 T) entries need only the anchor values: with several of
+  // them, or beside O(T^2) entries, they start here on their own streams
+  int fs_used = 0;
+  if (P.fstreams > 0) {
+    int64_t tmax = 0;
+    for (int i = 0; i < n; i++)
+      if (P.fast[i]) tmax = std::max(tmax, SB.hD[i].T);
+    if (zr_status r = fast_tables_for(ctx, tmax, st)) return r;
+    bool ok = true;
+    if (!ctx->fev_fork) ok = cudaEventCreateWithFlags(&ctx->fev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; ok && j < P.fstreams; j++) {
+      if (!ctx->fstream[j]) ok = cudaStreamCreateWithFlags(&ctx->fstream[j], cudaStreamNonBlocking) == cudaSuccess;
+      if (ok && !ctx->fev_join[j]) ok = cudaEventCreateWithFlags(&ctx->fev_join[j], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) return cuda_err(ctx, cudaErrorMemoryAllocation, "fast streams");
+    cudaEventRecord(ctx->fev_fork, st);
+    for (int j = 0; j < P.fstreams; j++) cudaStreamWaitEvent(ctx->fstream[j], ctx->fev_fork, 0);
+    int k = 0;
+    for (int i = 0; i < n; i++) {
+      if (!P.fast[i]) continue;
+      const int j = k++ % P.fstreams;
+      const BDesc& d = SB.hD[i];
+      zr_status r = fast_solve_enqueue(ctx, d.T, d.S, d.v, d.vp, d.b, d.ldb, d.part, d.denp,
+                                       SB.fast_ws + (size_t)j * P.fast_slot, ctx->fstream[j]);
+      if (r) return r;
+    }
+    fs_used = std::min(k, P.fstreams);
+    for (int j = 0; j < fs_used; j++) cudaEventRecord(ctx->fev_join[j], ctx->fstream[j]);
+  }
   // a3
   if (nleaf) { k_b_tree_leaf<<<(unsigned)nleaf, 1 << kTreeL1, 0, st>>>(dD, dpre + o_leaf, n, M); note_launch(); }
   for (int l = kTreeL1; l < lmax; l++) {
@@ -708,13 +749,16 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
       return set_err(ctx, ZR_ERR_INVALID_ARG, "no solve kernel for this launch plan");
   cudaEvent_t e4 = mark();
   // entries of the O(T log^2 T) solve: numerators and M'(v_j) into the
-  // single-block partials the finish reads
-  for (int i = 0; i < n; i++) {
-    if (!P.fast[i]) continue;
-    const BDesc& d = SB.hD[i];
-    zr_status r = fast_solve_enqueue(ctx, d.T, d.S, d.v, d.vp, d.b, d.ldb, d.part, d.denp, SB.fast_ws, st);
-    if (r) return r;
-  }
+  // single-block partials the finish reads (on this stream, or joined here
+  // from their own streams: the phase is then the wait for them)
+  if (P.fstreams == 0)
+    for (int i = 0; i < n; i++) {
+      if (!P.fast[i]) continue;
+      const BDesc& d = SB.hD[i];
+      zr_status r = fast_solve_enqueue(ctx, d.T, d.S, d.v, d.vp, d.b, d.ldb, d.part, d.denp, SB.fast_ws, st);
+      if (r) return r;
+    }
+  for (int j = 0; j < fs_used; j++) cudaStreamWaitEvent(st, ctx->fev_join[j], 0);
   cudaEvent_t e4f = mark();
   // a6 (or the plain finish of a system)
   if (nroots) {

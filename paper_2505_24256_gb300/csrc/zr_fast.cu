@@ -1639,6 +1639,14 @@ zr_status ensure_ntt_tables(zr_ctx* ctx, int logN, cudaStream_t st) {
   return cuda_err(ctx, cudaGetLastError(), "transform tables");
 }
 
+// The transform tables for fast solves of up to T unknowns (grown here, on
+// st, so that solves enqueued on other streams afterwards never grow them).
+zr_status fast_tables_for(zr_ctx* ctx, int64_t T, cudaStream_t st) {
+  int Lt = 0;
+  while ((int64_t)kLeaf << Lt < T) Lt++;
+  return ensure_ntt_tables(ctx, kLeafLog + Lt + 1, st);
+}
+
 // One system (or step entry) solved by the fast path: writes the numerators
 // <q_j, b_s> to part[s T + j] (s < S) and M'(v_j) to den[j], the layout the
 // finish kernels read for a single k-block.  v and vp (Shoup quotients of v)

@@ -64,6 +64,10 @@ struct zr_ctx {
   // there, overlapping the tree and the solve), with its fork/join events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // streams on which a batch's O(T log^2 T) entries run concurrently, with
+  // their fork and join events
+  cudaStream_t fstream[4] = {};
+  cudaEvent_t fev_fork = nullptr, fev_join[4] = {};
   // the O(T log^2 T) solve: constants of the transform primes, the twiddle
   // tables (grown on demand) and the choice between the two solve methods
   zr::NttConsts ntt;
@@ -171,6 +175,8 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
                              int64_t ldb, uint64_t* part, uint64_t* den, char* ws, cudaStream_t st);
 // whether a system of T unknowns takes the fast path in this context
 bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S);
+// grows the transform tables for fast solves of up to T unknowns
+zr_status fast_tables_for(zr_ctx* ctx, int64_t T, cudaStream_t st);
 // scheduling weights (multiply-accumulate equivalents) of a step's solve and
 // of its probes, by the method each takes in this context
 double solve_work(const zr_ctx* ctx, int64_t T, int S);

@@ -98,6 +98,27 @@ def test_both_methods_in_one_batch(ctx, orc):
         assert np.array_equal(h64(s["c"]), w)
 
 
+def test_many_fast_entries_in_one_batch(ctx, orc):
+    """Six systems above the crossover and one below in one call: the fast
+    ones run on four streams of their own, two of them twice, each with its
+    workspace slot; every result equals the oracle's."""
+    rnd = random.Random(9)
+    shapes = [(1100, 2, 0), (2048, 3, 1), (1500, 1, 0), (4100, 2, 0), (1200, 4, 1), (3333, 1, 0), (300, 2, 0)]
+    systems, want = [], []
+    for T, S, off in shapes:
+        v, b = rand_nodes(rnd, T, P63), rand_res(rnd, (S, T), P63)
+        c = zeros64(S, T)
+        systems.append(dict(T=T, S=S, offset=off, v=d64(v), b=d64(b), ldb=T, c=c, ldc=T))
+        want.append(orc.tvandermonde_solve(v, b, offset=off))
+    ctx.solve_method(0, 1000)
+    try:
+        ctx.vandermonde_solve(systems)
+    finally:
+        ctx.solve_method(0)
+    for sy, w in zip(systems, want):
+        assert np.array_equal(h64(sy["c"]), w)
+
+
 def step(ctx, wl, method):
     import torch
     fe, fc = d8(wl.exps), d64(wl.coef)
