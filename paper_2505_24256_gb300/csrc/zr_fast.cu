@@ -41,6 +41,30 @@ namespace zr {
 namespace {
 
 inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+// Launches in this file are programmatic dependent launches: a kernel may
+// become resident while the one before it on the stream drains.  Every
+// kernel here first waits (griddepcontrol.wait: until its predecessors have
+// completed and their memory is visible), then lets its own dependents start
+// launching (they run once all of its CTAs have started).
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <class... P, class... A>
+cudaError_t launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 inline int ilog2(int64_t x) {
   int l = 0;
   while ((1ll << l) < x) l++;
@@ -63,6 +87,7 @@ __device__ uint32_t pow32(uint32_t a, uint32_t e, uint32_t q) {
 // two <= k (w_{2m} a primitive 2m-th root of unity mod q_i), with Shoup
 // quotients.
 __global__ void k_ntt_tables(int logN, NttConsts C, uint2* __restrict__ tw, uint2* __restrict__ itw) {
+  pdl_enter();
   const int64_t N = 1ll << logN;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= kNP * N) return;
@@ -203,6 +228,7 @@ template <bool INV>
 __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict__ data, int64_t total, int logn,
                                                            int plane_log, int s_lo, const uint2* __restrict__ tw,
                                                            int logN, NttConsts C) {
+  pdl_enter();
   __shared__ __align__(16) uint32_t sm[kNttTile];
   const int64_t base = (int64_t)blockIdx.x * kNttTile;
   const int len = (int)((total - base) < kNttTile ? (total - base) : kNttTile);
@@ -244,6 +270,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_local(uint32_t* __restrict_
 template <bool INV>
 __global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__ data, int logn, int plane_log, int L1,
                                                           const uint2* __restrict__ tw, int logN, NttConsts C) {
+  pdl_enter();
   __shared__ uint32_t sm[kNttTile];
   const int cwl = kNttTileLog - L1, CW = 1 << cwl;
   const int64_t tbase = (int64_t)(blockIdx.x >> L1) << logn;
@@ -269,6 +296,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_cols(uint32_t* __restrict__
 //   spec[i][P][c][k], plane of 2T' per prime.
 __global__ void k_tree_load(const uint64_t* __restrict__ below, int64_t T, int64_t Tp, int logn, NttConsts C,
                             uint32_t* __restrict__ spec) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP * 2T'
   if (idx >= kNP * 2 * Tp) return;
   const int i = (int)(idx / (2 * Tp));
@@ -287,6 +315,7 @@ __global__ void k_tree_load(const uint64_t* __restrict__ below, int64_t T, int64
 // Z[i][P][k] = spec_L[k] spec_R[k] (Montgomery), per prime plane of T'.
 __global__ void k_tree_mul(const uint32_t* __restrict__ spec, int64_t Tp, int logn, NttConsts C,
                            uint32_t* __restrict__ Z) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP * T'
   if (idx >= kNP * Tp) return;
   const int i = (int)(idx / Tp);
@@ -301,6 +330,7 @@ __global__ void k_tree_mul(const uint32_t* __restrict__ spec, int64_t Tp, int lo
 // d_P = n the leading z^n wrapped onto z^0 and is taken off.
 __global__ void k_tree_crt(const uint32_t* __restrict__ Z, int64_t T, int64_t Tp, int logn, NttConsts C, CrtScale sc,
                            Mod M, uint64_t* __restrict__ coef) {
+  pdl_enter();
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= Tp) return;
   const int64_t n = 1ll << logn;
@@ -320,6 +350,7 @@ __global__ void k_tree_crt(const uint32_t* __restrict__ Z, int64_t T, int64_t Tp
 // thread per (r, P n + k) writes all five primes' residues.
 __global__ void k_desc_load(const uint64_t* __restrict__ X, int R, int64_t T, int64_t Tp, int logn, NttConsts C,
                             uint32_t* __restrict__ XH) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over R * T'
   if (idx >= (int64_t)R * Tp) return;
   const int rr = (int)(idx / Tp);
@@ -338,6 +369,7 @@ __global__ void k_desc_load(const uint64_t* __restrict__ X, int R, int64_t T, in
 // one thread per (i, P n + k) loads the two spectra once for all R rows.
 __global__ void k_desc_mul(const uint32_t* __restrict__ XH, const uint32_t* __restrict__ spec, int R, int64_t Tp,
                            int logn, NttConsts C, uint32_t* __restrict__ Y) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP * T'
   if (idx >= (int64_t)kNP * Tp) return;
   const int i = (int)(idx / Tp);
@@ -358,6 +390,7 @@ __global__ void k_desc_mul(const uint32_t* __restrict__ XH, const uint32_t* __re
 // Descent Chinese remaindering: X'[r][(2P + c) h + m] = y_c[d_P - 1 - m], m < d_c.
 __global__ void k_desc_crt(const uint32_t* __restrict__ Y, int R, int64_t T, int64_t Tp, int logn, NttConsts C,
                            CrtScale sc, Mod M, uint64_t* __restrict__ Xn) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over R * T' (child slots)
   if (idx >= (int64_t)R * Tp) return;
   const int rr = (int)(idx / Tp);
@@ -383,6 +416,7 @@ __global__ void k_desc_crt(const uint32_t* __restrict__ Y, int R, int64_t T, int
 
 // A[i][k] = a[k] mod q_i for k < na, else 0 (planes of N)
 __global__ void k_cyc_load(const uint64_t* __restrict__ a, int64_t na, int logN, NttConsts C, uint32_t* __restrict__ A) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= ((int64_t)kNP << logN)) return;
   const int i = (int)(idx >> logN);
@@ -391,6 +425,7 @@ __global__ void k_cyc_load(const uint64_t* __restrict__ a, int64_t na, int logN,
 }
 __global__ void k_cyc_mul(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B, int logN, NttConsts C,
                           uint32_t* __restrict__ Z) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= ((int64_t)kNP << logN)) return;
   const int i = (int)(idx >> logN);
@@ -400,6 +435,7 @@ __global__ void k_cyc_mul(const uint32_t* __restrict__ A, const uint32_t* __rest
 // out[t] = +-(a * b)[lo + t], t < cnt
 __global__ void k_cyc_crt(const uint32_t* __restrict__ Z, int logN, int64_t lo, int64_t cnt, int neg, NttConsts C,
                           CrtScale sc, Mod M, uint64_t* __restrict__ out) {
+  pdl_enter();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt) return;
   uint32_t res[kNP];
@@ -413,6 +449,7 @@ __global__ void k_cyc_crt(const uint32_t* __restrict__ Z, int logN, int64_t lo, 
 // (rev(M'), degree T - 1; skipped when rd is null); g_0 = 1.
 __global__ void k_rev_poly(const uint64_t* __restrict__ m, int64_t T, Mod M, uint64_t* __restrict__ f,
                            uint64_t* __restrict__ rd, uint64_t* __restrict__ g) {
+  pdl_enter();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t > T) return;
   const uint64_t mt = t == 0 ? 1 : m[T - t];
@@ -455,6 +492,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_tree_fused(const uint64_t* __
                                                               const uint2* __restrict__ tw, int logN,
                                                               uint32_t* __restrict__ spec, uint64_t* __restrict__ coef,
                                                               int64_t nodes) {
+  pdl_enter();
   extern __shared__ uint32_t fsm[];              // [c][node][prime][n]
   const int npc = fused_npc(logn);
   const int64_t P0 = (int64_t)blockIdx.x * npc;
@@ -511,6 +549,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_desc_fused(const uint64_t* __
                                                               const uint2* __restrict__ tw, int logN,
                                                               const uint32_t* __restrict__ spec,
                                                               uint64_t* __restrict__ Xn, int64_t nodes) {
+  pdl_enter();
   extern __shared__ uint32_t fsm[];              // XH [node][prime][n], then Y [node][prime][n] (logical words)
   const int npc = fused_npc(logn);
   const int64_t ctas = (nodes + npc - 1) / npc;
@@ -567,6 +606,7 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_fused(const uint64_t
                                                                 NttConsts C, Mod M, const uint2* __restrict__ tw,
                                                                 int logN, uint64_t* __restrict__ g,
                                                                 uint64_t* __restrict__ e) {
+  pdl_enter();
   extern __shared__ uint32_t fsm[];              // A [prime][2k], then B [prime][2k] (logical words)
   if (threadIdx.x == 0) g[0] = 1;
   __syncthreads();
@@ -674,6 +714,7 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
                                                                   int logK, NttConsts C, Mod M,
                                                                   const uint2* __restrict__ tw, int logN,
                                                                   uint64_t* __restrict__ g) {
+  pdl_enter();
   extern __shared__ uint32_t fsm[];              // A [n], B [n] at 0, n; C [n] at 2K (logical); then g mod q
   const int me = cluster_rank();
   const int K = 1 << logK;
@@ -802,6 +843,7 @@ __global__ void __launch_bounds__(kClusterThreadsMax) k_tree_cluster(const uint6
                                                                 const uint2* __restrict__ tw, int logN,
                                                                 uint32_t* __restrict__ spec,
                                                                 uint64_t* __restrict__ coef) {
+  pdl_enter();
   extern __shared__ uint32_t fsm[];              // L [n], R [n] (logical words)
   const int me = cluster_rank();
   const int64_t P = blockIdx.x / kNP;
@@ -853,6 +895,7 @@ __global__ void __launch_bounds__(kClusterThreadsMax) k_desc_cluster(const uint6
                                                                 const uint2* __restrict__ tw, int logN,
                                                                 const uint32_t* __restrict__ spec,
                                                                 uint64_t* __restrict__ Xn, int64_t nodes) {
+  pdl_enter();
   extern __shared__ uint32_t fsm[];              // XH [n], Y [2][n] at n (logical words)
   const int me = cluster_rank();
   const int64_t cl = blockIdx.x / kNP;
@@ -903,6 +946,7 @@ constexpr int kLeafLog = 7;
 // levels 0..6 of pairwise products in shared memory.
 __global__ void __launch_bounds__(kLeaf) k_fast_leafpoly(const uint64_t* __restrict__ v, int64_t T, Mod M,
                                                          uint64_t* __restrict__ coef) {
+  pdl_enter();
   __shared__ uint64_t buf[2][kLeaf];
   const int64_t base = (int64_t)blockIdx.x * kLeaf;
   const int cnt = (int)((T - base) < kLeaf ? (T - base) : kLeaf);
@@ -941,6 +985,7 @@ __global__ void __launch_bounds__(kLeaf) k_fast_leafval(const uint64_t* __restri
                                                         const uint64_t* __restrict__ v, const uint64_t* __restrict__ vp,
                                                         Mod M, uint64_t* __restrict__ part, int64_t ldp,
                                                         uint64_t* __restrict__ den) {
+  pdl_enter();
   __shared__ uint64_t pc[kLeaf];                 // block polynomial
   __shared__ uint64_t xs[kLeafCols][kLeaf];      // this group's X rows
   const int64_t base = (int64_t)blockIdx.x * kLeaf;
@@ -981,6 +1026,7 @@ __global__ void __launch_bounds__(kLeaf) k_fast_leafval(const uint64_t* __restri
 // X0[r][k] = b[r ldb + k] (r < S), X0[S][k] = power sums (k < T)
 __global__ void k_stage_rhs(const uint64_t* __restrict__ b, int64_t ldb, int S, const uint64_t* __restrict__ ps,
                             int64_t T, int64_t Tp, uint64_t* __restrict__ X0) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)(S + 1) * T) return;
   const int r = (int)(idx / T);
@@ -1019,6 +1065,7 @@ __device__ __forceinline__ uint64_t up_coef(const uint64_t* Nb, const uint64_t* 
 __global__ void __launch_bounds__(kLeaf) k_up_leaf(const uint64_t* __restrict__ U, int64_t G,
                                                    const uint64_t* __restrict__ W, int64_t ldw, int S, Mod M,
                                                    uint64_t* __restrict__ N7, int64_t Gp) {
+  pdl_enter();
   extern __shared__ uint64_t usm[];              // M [2][128], then N [S][2][128]
   uint64_t* Mb = usm;
   uint64_t* Nb = usm + 2 * kLeaf;
@@ -1062,6 +1109,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_up_fused(const uint64_t* __re
                                                             const uint2* __restrict__ tw, int logN,
                                                             const uint32_t* __restrict__ spec,
                                                             uint64_t* __restrict__ Nout, int64_t nodes) {
+  pdl_enter();
   extern __shared__ uint32_t fsm[];              // [c][node][prime][n]
   const int npc = fused_npc(logn);
   const int64_t ctas = (nodes + npc - 1) / npc;
@@ -1121,6 +1169,7 @@ __global__ void __launch_bounds__(kClusterThreadsMax) k_up_cluster(const uint64_
                                                               const uint2* __restrict__ tw, int logN,
                                                               const uint32_t* __restrict__ spec,
                                                               uint64_t* __restrict__ Nout, int64_t nodes) {
+  pdl_enter();
   extern __shared__ uint32_t fsm[];              // N_L [n], N_R [n] (logical words)
   const int me = cluster_rank();
   const int64_t cl = blockIdx.x / kNP;
@@ -1169,6 +1218,7 @@ __global__ void __launch_bounds__(kClusterThreadsMax) k_up_cluster(const uint64_
 // of G'), inverse transforms, then Chinese remaindering into N_P.
 __global__ void k_up_load(const uint64_t* __restrict__ Nprev, int S, int64_t G, int64_t Gp, int logn, NttConsts C,
                           uint32_t* __restrict__ A) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over S * 2 G'
   if (idx >= (int64_t)S * 2 * Gp) return;
   const int col = (int)(idx / (2 * Gp));
@@ -1184,6 +1234,7 @@ __global__ void k_up_load(const uint64_t* __restrict__ Nprev, int S, int64_t G, 
 }
 __global__ void k_up_mul(const uint32_t* __restrict__ A, const uint32_t* __restrict__ spec, int S, int64_t Gp, int logn,
                          NttConsts C, uint32_t* __restrict__ Z) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP * G'
   if (idx >= (int64_t)kNP * Gp) return;
   const int i = (int)(idx / Gp);
@@ -1201,6 +1252,7 @@ __global__ void k_up_mul(const uint32_t* __restrict__ A, const uint32_t* __restr
 }
 __global__ void k_up_crt(const uint32_t* __restrict__ Z, int S, int64_t G, int64_t Gp, int logn, NttConsts C,
                          CrtScale sc, Mod M, uint64_t* __restrict__ Nout) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over S * G'
   if (idx >= (int64_t)S * Gp) return;
   const int col = (int)(idx / Gp);
@@ -1221,6 +1273,7 @@ __global__ void k_up_crt(const uint32_t* __restrict__ Z, int S, int64_t G, int64
 // transformed at size 2^logn; Z[s] = A[s] B; out[s][t] = Z[s][t], t < T.
 __global__ void k_rows_load(const uint64_t* __restrict__ N, int S, int64_t G, int64_t Gp, int64_t na, int logn,
                             NttConsts C, uint32_t* __restrict__ A) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over S 2^logn
   if (idx >= ((int64_t)S << logn)) return;
   const int col = (int)(idx >> logn);
@@ -1231,6 +1284,7 @@ __global__ void k_rows_load(const uint64_t* __restrict__ N, int S, int64_t G, in
   for (int i = 0; i < kNP; i++) out[(int64_t)i << logn] = t < na ? residue64(x, C, i) : 0u;
 }
 __global__ void k_rows_mul(uint32_t* __restrict__ A, const uint32_t* __restrict__ B, int S, int logn, NttConsts C) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over kNP 2^logn
   if (idx >= ((int64_t)kNP << logn)) return;
   const int i = (int)(idx >> logn);
@@ -1243,6 +1297,7 @@ __global__ void k_rows_mul(uint32_t* __restrict__ A, const uint32_t* __restrict_
 }
 __global__ void k_rows_crt(const uint32_t* __restrict__ Z, int S, int64_t T, int logn, NttConsts C, CrtScale sc,
                            Mod M, uint64_t* __restrict__ out, int64_t ldo) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over S T
   if (idx >= (int64_t)S * T) return;
   const int col = (int)(idx / T);
@@ -1297,23 +1352,23 @@ void launch_ntt(zr_ctx* ctx, uint32_t* data, int64_t count, int logn, int plane_
   auto local = [&](bool inverse) {
     cudaEvent_t a = prof_mark(ctx, st);
     if (inverse)
-      k_ntt_local<true><<<tiles, kNttThreads, 0, st>>>(data, total, logn, plane_log, L1, itw, logN, C);
+      launch_k(k_ntt_local<true>, tiles, kNttThreads, 0, st, data, total, logn, plane_log, L1, itw, logN, C);
     else
-      k_ntt_local<false><<<tiles, kNttThreads, 0, st>>>(data, total, logn, plane_log, L1, tw, logN, C);
+      launch_k(k_ntt_local<false>, tiles, kNttThreads, 0, st, data, total, logn, plane_log, L1, tw, logN, C);
     note_launch();
     cudaEvent_t b = prof_mark(ctx, st);
     prof_add(ctx, PH_NTT, a, b, (double)(total / 2) * (logn - L1));
   };
   if (!inv) {
     if (L1) {
-      k_ntt_cols<false><<<cols, kNttThreads, 0, st>>>(data, logn, plane_log, L1, tw, logN, C);
+      launch_k(k_ntt_cols<false>, cols, kNttThreads, 0, st, data, logn, plane_log, L1, tw, logN, C);
       note_launch();
     }
     local(false);
   } else {
     local(true);
     if (L1) {
-      k_ntt_cols<true><<<cols, kNttThreads, 0, st>>>(data, logn, plane_log, L1, itw, logN, C);
+      launch_k(k_ntt_cols<true>, cols, kNttThreads, 0, st, data, logn, plane_log, L1, itw, logN, C);
       note_launch();
     }
   }
@@ -1381,15 +1436,15 @@ struct FastRun {
   void cyc(const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb, int logn, int64_t lo, int64_t cnt, bool neg,
            uint32_t* A, uint32_t* B, uint32_t* Z, uint64_t* out) {
     const int64_t all = (int64_t)kNP << logn;
-    k_cyc_load<<<cdivu(all, 256), 256, 0, st>>>(a, na, logn, C, A);
-    k_cyc_load<<<cdivu(all, 256), 256, 0, st>>>(b, nb, logn, C, B);
+    launch_k(k_cyc_load, cdivu(all, 256), 256, 0, st, a, na, logn, C, A);
+    launch_k(k_cyc_load, cdivu(all, 256), 256, 0, st, b, nb, logn, C, B);
     note_launches(2);
     launch_ntt(ctx, A, kNP, logn, logn, false, tw, itw, logN, C, st);
     launch_ntt(ctx, B, kNP, logn, logn, false, tw, itw, logN, C, st);
-    k_cyc_mul<<<cdivu(all, 256), 256, 0, st>>>(A, B, logn, C, Z);
+    launch_k(k_cyc_mul, cdivu(all, 256), 256, 0, st, A, B, logn, C, Z);
     note_launch();
     launch_ntt(ctx, Z, kNP, logn, logn, true, tw, itw, logN, C, st);
-    k_cyc_crt<<<cdivu(cnt, 256), 256, 0, st>>>(Z, logn, lo, cnt, neg ? 1 : 0, C, crt_scale(logn), M, out);
+    launch_k(k_cyc_crt, cdivu(cnt, 256), 256, 0, st, Z, logn, lo, cnt, neg ? 1 : 0, C, crt_scale(logn), M, out);
     note_launch();
   }
 };
@@ -1403,13 +1458,15 @@ cudaError_t launch_cluster(void (*kernel)(P...), int64_t clusters, int threads, 
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = kNP;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
   note_launch();
   return e;
@@ -1480,7 +1537,7 @@ void configure_fused() {
 void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::vector<uint64_t*>& coef,
                    const std::vector<uint32_t*>& spec, uint32_t* Z) {
   const int logT = kLeafLog + Lt;
-  k_fast_leafpoly<<<cdivu(T, kLeaf), kLeaf, 0, st>>>(v, T, M, coef[0]);
+  launch_k(k_fast_leafpoly, cdivu(T, kLeaf), kLeaf, 0, st, v, T, M, coef[0]);
   note_launch();
   for (int l = 1; l <= Lt; l++) {
     const int logn = kLeafLog + l;
@@ -1495,19 +1552,18 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
     }
     if (logn <= kFusedLog) {
       const int npc = fused_npc(logn);
-      k_tree_fused<<<(unsigned)((nodes + npc - 1) / npc), kFusedThreads,
-                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(coef[l - 1], T, Tp, logn, C, crt_scale(logn), M,
+      launch_k(k_tree_fused, (unsigned)((nodes + npc - 1) / npc), kFusedThreads, sizeof(uint32_t) * 2 * kNP * npc << logn, st, coef[l - 1], T, Tp, logn, C, crt_scale(logn), M,
                                                                      tw, logN, sp, coef[l], nodes);
       note_launch();
       continue;
     }
-    k_tree_load<<<cdivu(kNP * 2 * Tp, 256), 256, 0, st>>>(coef[l - 1], T, Tp, logn, C, sp);
+    launch_k(k_tree_load, cdivu(kNP * 2 * Tp, 256), 256, 0, st, coef[l - 1], T, Tp, logn, C, sp);
     note_launch();
     launch_ntt(ctx, sp, (kNP * 2 * Tp) >> logn, logn, logT + 1, false, tw, itw, logN, C, st);
-    k_tree_mul<<<cdivu(kNP * Tp, 256), 256, 0, st>>>(sp, Tp, logn, C, Z);
+    launch_k(k_tree_mul, cdivu(kNP * Tp, 256), 256, 0, st, sp, Tp, logn, C, Z);
     note_launch();
     launch_ntt(ctx, Z, (kNP * Tp) >> logn, logn, logT, true, tw, itw, logN, C, st);
-    k_tree_crt<<<cdivu(Tp, 256), 256, 0, st>>>(Z, T, Tp, logn, C, crt_scale(logn), M, coef[l]);
+    launch_k(k_tree_crt, cdivu(Tp, 256), 256, 0, st, Z, T, Tp, logn, C, crt_scale(logn), M, coef[l]);
     note_launch();
   }
 }
@@ -1523,7 +1579,7 @@ void FastRun::inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, 
   }
   if (!done) {
     logK0 = std::min(logK0, kFusedLog);
-    k_newton_fused<<<1, kNewtonThreadsF, sizeof(uint32_t) * 2 * kNP << logK0, st>>>(f, nf, logK0, C, M, tw, logN, g,
+    launch_k(k_newton_fused, 1, kNewtonThreadsF, sizeof(uint32_t) * 2 * kNP << logK0, st, f, nf, logK0, C, M, tw, logN, g,
                                                                                   e);
     note_launch();
   }
@@ -1633,7 +1689,7 @@ zr_status ensure_ntt_tables(zr_ctx* ctx, int logN, cudaStream_t st) {
     return cuda_err(ctx, e, "transform tables");
   }
   uint2* tw = reinterpret_cast<uint2*>(ctx->ntt_tw);
-  k_ntt_tables<<<cdivu((int64_t)words, 256), 256, 0, st>>>(logN, ctx->ntt, tw, tw + words);
+  launch_k(k_ntt_tables, cdivu((int64_t)words, 256), 256, 0, st, logN, ctx->ntt, tw, tw + words);
   note_launch();
   ctx->ntt_logN = logN;
   return cuda_err(ctx, cudaGetLastError(), "transform tables");
@@ -1674,13 +1730,13 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   const uint64_t* m = w.coef[Lt];   // M without its leading 1
 
   // power sums: g = 1 / rev(M) mod z^T by Newton's iteration, ps = rev(M') g
-  k_rev_poly<<<cdivu(T + 1, 256), 256, 0, st>>>(m, T, M, w.f, w.rd, w.g);
+  launch_k(k_rev_poly, cdivu(T + 1, 256), 256, 0, st, m, T, M, w.f, w.rd, w.g);
   note_launch();
   F.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
   F.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
 
   // descent from the root (node size T') to the leaf blocks
-  k_stage_rhs<<<cdivu((int64_t)R * T, 256), 256, 0, st>>>(b, ldb, S, w.ps, T, Tp, w.X0);
+  launch_k(k_stage_rhs, cdivu((int64_t)R * T, 256), 256, 0, st, b, ldb, S, w.ps, T, Tp, w.X0);
   note_launch();
   uint64_t* X = w.X0;
   uint64_t* Xn = w.X1;
@@ -1699,8 +1755,7 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     }
     if (!done && logn <= kFusedLog) {
       const int npc = fused_npc(logn);
-      k_desc_fused<<<(unsigned)((nodes + npc - 1) / npc * R), kFusedThreads,
-                     sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(X, T, Tp, logn, C, crt_scale(logn), M, tw, logN,
+      launch_k(k_desc_fused, (unsigned)((nodes + npc - 1) / npc * R), kFusedThreads, sizeof(uint32_t) * 2 * kNP * npc << logn, st, X, T, Tp, logn, C, crt_scale(logn), M, tw, logN,
                                                                      w.spec[l - 1], Xn, nodes);
       note_launch();
       done = true;
@@ -1710,18 +1765,18 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
       continue;
     }
     const int64_t all = (int64_t)R * kNP * Tp;
-    k_desc_load<<<cdivu((int64_t)R * Tp, 256), 256, 0, st>>>(X, R, T, Tp, logn, C, w.XH);
+    launch_k(k_desc_load, cdivu((int64_t)R * Tp, 256), 256, 0, st, X, R, T, Tp, logn, C, w.XH);
     note_launch();
     launch_ntt(ctx, w.XH, all >> logn, logn, logT, false, tw, itw, logN, C, st);
-    k_desc_mul<<<cdivu((int64_t)kNP * Tp, 256), 256, 0, st>>>(w.XH, w.spec[l - 1], R, Tp, logn, C, w.Y);
+    launch_k(k_desc_mul, cdivu((int64_t)kNP * Tp, 256), 256, 0, st, w.XH, w.spec[l - 1], R, Tp, logn, C, w.Y);
     note_launch();
     launch_ntt(ctx, w.Y, (2 * all) >> logn, logn, logT, true, tw, itw, logN, C, st);
-    k_desc_crt<<<cdivu((int64_t)R * Tp, 256), 256, 0, st>>>(w.Y, R, T, Tp, logn, C, crt_scale(logn), M, Xn);
+    launch_k(k_desc_crt, cdivu((int64_t)R * Tp, 256), 256, 0, st, w.Y, R, T, Tp, logn, C, crt_scale(logn), M, Xn);
     note_launch();
     std::swap(X, Xn);
   }
   // leaves
-  k_fast_leafval<<<dim3(cdivu(T, kLeaf), (unsigned)((R + kLeafCols - 1) / kLeafCols)), kLeaf, 0, st>>>(
+  launch_k(k_fast_leafval, dim3(cdivu(T, kLeaf), (unsigned)((R + kLeafCols - 1) / kLeafCols)), kLeaf, 0, st, 
       w.coef[0], X, R, T, Tp, v, vp, M, part, T, den);
   note_launch();
   return cuda_err(ctx, cudaGetLastError(), "fast solve");
@@ -1755,7 +1810,7 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
   F.tree(U, G, Gp, Lt, w.coef, w.spec, w.Z2);
 
   // numerators: leaf blocks, then the levels up to the root
-  k_up_leaf<<<cdivu(G, kLeaf), kLeaf, sizeof(uint64_t) * 2 * kLeaf * (1 + S), st>>>(U, G, W, ldw, S, M, w.N0, Gp);
+  launch_k(k_up_leaf, cdivu(G, kLeaf), kLeaf, sizeof(uint64_t) * 2 * kLeaf * (1 + S), st, U, G, W, ldw, S, M, w.N0, Gp);
   note_launch();
   uint64_t* Nc = w.N0;
   uint64_t* Nn = w.N1;
@@ -1770,41 +1825,40 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
     }
     if (!done && logn <= kFusedLog) {
       const int npc = fused_npc(logn);
-      k_up_fused<<<(unsigned)((nodes + npc - 1) / npc * S), kFusedThreads,
-                   sizeof(uint32_t) * 2 * kNP * npc << logn, st>>>(Nc, G, Gp, logn, C, crt_scale(logn), M, tw, logN,
+      launch_k(k_up_fused, (unsigned)((nodes + npc - 1) / npc * S), kFusedThreads, sizeof(uint32_t) * 2 * kNP * npc << logn, st, Nc, G, Gp, logn, C, crt_scale(logn), M, tw, logN,
                                                                    w.spec[l - 1], Nn, nodes);
       note_launch();
       done = true;
     }
     if (!done) {
-      k_up_load<<<cdivu((int64_t)S * 2 * Gp, 256), 256, 0, st>>>(Nc, S, G, Gp, logn, C, w.A);
+      launch_k(k_up_load, cdivu((int64_t)S * 2 * Gp, 256), 256, 0, st, Nc, S, G, Gp, logn, C, w.A);
       note_launch();
       launch_ntt(ctx, w.A, ((int64_t)S * kNP * 2 * Gp) >> logn, logn, logG + 1, false, tw, itw, logN, C, st);
-      k_up_mul<<<cdivu((int64_t)kNP * Gp, 256), 256, 0, st>>>(w.A, w.spec[l - 1], S, Gp, logn, C, w.Z);
+      launch_k(k_up_mul, cdivu((int64_t)kNP * Gp, 256), 256, 0, st, w.A, w.spec[l - 1], S, Gp, logn, C, w.Z);
       note_launch();
       launch_ntt(ctx, w.Z, ((int64_t)S * kNP * Gp) >> logn, logn, logG, true, tw, itw, logN, C, st);
-      k_up_crt<<<cdivu((int64_t)S * Gp, 256), 256, 0, st>>>(w.Z, S, G, Gp, logn, C, crt_scale(logn), M, Nn);
+      launch_k(k_up_crt, cdivu((int64_t)S * Gp, 256), 256, 0, st, w.Z, S, G, Gp, logn, C, crt_scale(logn), M, Nn);
       note_launch();
     }
     std::swap(Nc, Nn);
   }
 
   // 1 / rev(M) to precision T, then rev(N_s) times it, the first T terms
-  k_rev_poly<<<cdivu(G + 1, 256), 256, 0, st>>>(w.coef[Lt], G, M, w.f, nullptr, w.g);
+  launch_k(k_rev_poly, cdivu(G + 1, 256), 256, 0, st, w.coef[Lt], G, M, w.f, nullptr, w.g);
   note_launch();
   F.inverse(w.f, G + 1, T, w.g, w.e, w.A2, w.B2, w.Z2);
   const int logR = w.logR;
   const int64_t na = std::min(G, T);
-  k_rows_load<<<cdivu((int64_t)S << logR, 256), 256, 0, st>>>(Nc, S, G, Gp, na, logR, C, w.A);
+  launch_k(k_rows_load, cdivu((int64_t)S << logR, 256), 256, 0, st, Nc, S, G, Gp, na, logR, C, w.A);
   note_launch();
-  k_cyc_load<<<cdivu((int64_t)kNP << logR, 256), 256, 0, st>>>(w.g, T, logR, C, w.Bg);
+  launch_k(k_cyc_load, cdivu((int64_t)kNP << logR, 256), 256, 0, st, w.g, T, logR, C, w.Bg);
   note_launch();
   launch_ntt(ctx, w.A, (int64_t)S * kNP, logR, logR, false, tw, itw, logN, C, st);
   launch_ntt(ctx, w.Bg, kNP, logR, logR, false, tw, itw, logN, C, st);
-  k_rows_mul<<<cdivu((int64_t)kNP << logR, 256), 256, 0, st>>>(w.A, w.Bg, S, logR, C);
+  launch_k(k_rows_mul, cdivu((int64_t)kNP << logR, 256), 256, 0, st, w.A, w.Bg, S, logR, C);
   note_launch();
   launch_ntt(ctx, w.A, (int64_t)S * kNP, logR, logR, true, tw, itw, logN, C, st);
-  k_rows_crt<<<cdivu((int64_t)S * T, 256), 256, 0, st>>>(w.A, S, T, logR, C, crt_scale(logR), M, out, ldo);
+  launch_k(k_rows_crt, cdivu((int64_t)S * T, 256), 256, 0, st, w.A, S, T, logR, C, crt_scale(logR), M, out, ldo);
   note_launch();
   return cuda_err(ctx, cudaGetLastError(), "fast probes");
 }
