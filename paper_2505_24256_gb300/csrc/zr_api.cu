@@ -412,6 +412,11 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
     if (ctx->fev_join[j]) cudaEventDestroy(ctx->fev_join[j]);
   }
   if (ctx->fev_fork) cudaEventDestroy(ctx->fev_fork);
+  for (int j = 0; j < 5; j++) {
+    if (ctx->faux[j]) cudaStreamDestroy(ctx->faux[j]);
+    if (ctx->faux_fork[j]) cudaEventDestroy(ctx->faux_fork[j]);
+    if (ctx->faux_join[j]) cudaEventDestroy(ctx->faux_join[j]);
+  }
   if (ctx->ntt_tw) cudaFree(ctx->ntt_tw);
   if (ctx->fprobe_ws) cudaFree(ctx->fprobe_ws);
   delete ctx;

@@ -428,6 +428,24 @@ struct Prepared {
 // finish; a lone fast entry runs on the call's stream.
 constexpr int kFastStreams = 4;
 
+// The auxiliary stream and events of fast-solve slot j (created on first
+// use); false when they cannot be had (the solve then runs on one stream).
+static bool fast_aux(zr_ctx* ctx, int j) {
+  if (!ctx->faux[j] && cudaStreamCreateWithFlags(&ctx->faux[j], cudaStreamNonBlocking) != cudaSuccess) {
+    ctx->faux[j] = nullptr;
+    return false;
+  }
+  if (!ctx->faux_fork[j] && cudaEventCreateWithFlags(&ctx->faux_fork[j], cudaEventDisableTiming) != cudaSuccess) {
+    ctx->faux_fork[j] = nullptr;
+    return false;
+  }
+  if (!ctx->faux_join[j] && cudaEventCreateWithFlags(&ctx->faux_join[j], cudaEventDisableTiming) != cudaSuccess) {
+    ctx->faux_join[j] = nullptr;
+    return false;
+  }
+  return true;
+}
+
 static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& P) {
   P.mode = items[0].mode;
   P.plan.resize(n);
@@ -707,8 +725,10 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
       if (!P.fast[i]) continue;
       const int j = k++ % P.fstreams;
       const BDesc& d = SB.hD[i];
+      const bool ax = fast_aux(ctx, j);
       zr_status r = fast_solve_enqueue(ctx, d.T, d.S, d.v, d.vp, d.b, d.ldb, d.part, d.denp,
-                                       SB.fast_ws + (size_t)j * P.fast_slot, ctx->fstream[j]);
+                                       SB.fast_ws + (size_t)j * P.fast_slot, ctx->fstream[j],
+                                       ax ? ctx->faux[j] : nullptr, ctx->faux_fork[j], ctx->faux_join[j]);
       if (r) return r;
     }
     fs_used = std::min(k, P.fstreams);
@@ -755,7 +775,9 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
     for (int i = 0; i < n; i++) {
       if (!P.fast[i]) continue;
       const BDesc& d = SB.hD[i];
-      zr_status r = fast_solve_enqueue(ctx, d.T, d.S, d.v, d.vp, d.b, d.ldb, d.part, d.denp, SB.fast_ws, st);
+      const bool ax = fast_aux(ctx, 4);
+      zr_status r = fast_solve_enqueue(ctx, d.T, d.S, d.v, d.vp, d.b, d.ldb, d.part, d.denp, SB.fast_ws, st,
+                                       ax ? ctx->faux[4] : nullptr, ctx->faux_fork[4], ctx->faux_join[4]);
       if (r) return r;
     }
   for (int j = 0; j < fs_used; j++) cudaStreamWaitEvent(st, ctx->fev_join[j], 0);

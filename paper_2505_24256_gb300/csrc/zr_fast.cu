@@ -1023,14 +1023,14 @@ __global__ void __launch_bounds__(kLeaf) k_fast_leafval(const uint64_t* __restri
   }
 }
 
-// X0[r][k] = b[r ldb + k] (r < S), X0[S][k] = power sums (k < T)
+// X0[r][k] = b[r ldb + k] (r < S), X0[S][k] = power sums (k < T), rows r0 .. r0 + nr - 1
 __global__ void k_stage_rhs(const uint64_t* __restrict__ b, int64_t ldb, int S, const uint64_t* __restrict__ ps,
-                            int64_t T, int64_t Tp, uint64_t* __restrict__ X0) {
+                            int r0, int nr, int64_t T, int64_t Tp, uint64_t* __restrict__ X0) {
   pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)(S + 1) * T) return;
-  const int r = (int)(idx / T);
-  const int64_t k = idx - (int64_t)r * T;
+  if (idx >= (int64_t)nr * T) return;
+  const int r = r0 + (int)(idx / T);
+  const int64_t k = idx - (int64_t)(r - r0) * T;
   X0[(int64_t)r * Tp + k] = r < S ? b[(int64_t)r * ldb + k] : ps[k];
 }
 
@@ -1709,7 +1709,7 @@ zr_status fast_tables_for(zr_ctx* ctx, int64_t T, cudaStream_t st) {
 // are on the device already; ws holds fast_ws_need(T, S + 1) bytes.
 zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, const uint64_t* vp,
                              const uint64_t* b, int64_t ldb, uint64_t* part, uint64_t* den, char* ws,
-                             cudaStream_t st) {
+                             cudaStream_t st, cudaStream_t aux, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
   const int R = S + 1;
   Carver cv(ws);
   FastWs w = carve_fast(cv, T, R);
@@ -1729,52 +1729,81 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   F.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
   const uint64_t* m = w.coef[Lt];   // M without its leading 1
 
-  // power sums: g = 1 / rev(M) mod z^T by Newton's iteration, ps = rev(M') g
-  launch_k(k_rev_poly, cdivu(T + 1, 256), 256, 0, st, m, T, M, w.f, w.rd, w.g);
-  note_launch();
-  F.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
-  F.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
-
-  // descent from the root (node size T') to the leaf blocks
-  launch_k(k_stage_rhs, cdivu((int64_t)R * T, 256), 256, 0, st, b, ldb, S, w.ps, T, Tp, w.X0);
-  note_launch();
-  uint64_t* X = w.X0;
-  uint64_t* Xn = w.X1;
-  for (int l = Lt; l >= 1; l--) {
-    const int logn = kLeafLog + l;
-    const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
-    bool done = false;
-    if (cluster_level(ctx, logn, nodes * R)) {
-      cudaEvent_t a = prof_mark(ctx, st);
-      done = launch_cluster(k_desc_cluster, nodes * R, cluster_threads(logn), sizeof(uint32_t) * 3 << logn, st, X, T,
-                            Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn, nodes) == cudaSuccess;
-      if (!done) (void)cudaGetLastError();
-      cudaEvent_t b = prof_mark(ctx, st);
-      // one forward and two inverse transforms of 2^logn per prime of each cluster
-      if (done) prof_add(ctx, PH_DESC, a, b, (double)(nodes * R) * kNP * 3 * (double)((1ll << logn) / 2) * logn);
-    }
-    if (!done && logn <= kFusedLog) {
-      const int npc = fused_npc(logn);
-      launch_k(k_desc_fused, (unsigned)((nodes + npc - 1) / npc * R), kFusedThreads, sizeof(uint32_t) * 2 * kNP * npc << logn, st, X, T, Tp, logn, C, crt_scale(logn), M, tw, logN,
-                                                                     w.spec[l - 1], Xn, nodes);
-      note_launch();
-      done = true;
-    }
-    if (done) {
-      std::swap(X, Xn);
-      continue;
-    }
-    const int64_t all = (int64_t)R * kNP * Tp;
-    launch_k(k_desc_load, cdivu((int64_t)R * Tp, 256), 256, 0, st, X, R, T, Tp, logn, C, w.XH);
-    note_launch();
-    launch_ntt(ctx, w.XH, all >> logn, logn, logT, false, tw, itw, logN, C, st);
-    launch_k(k_desc_mul, cdivu((int64_t)kNP * Tp, 256), 256, 0, st, w.XH, w.spec[l - 1], R, Tp, logn, C, w.Y);
-    note_launch();
-    launch_ntt(ctx, w.Y, (2 * all) >> logn, logn, logT, true, tw, itw, logN, C, st);
-    launch_k(k_desc_crt, cdivu((int64_t)R * Tp, 256), 256, 0, st, w.Y, R, T, Tp, logn, C, crt_scale(logn), M, Xn);
-    note_launch();
-    std::swap(X, Xn);
+  // The right-hand sides' descent needs only the tree; the power sums' row
+  // needs Newton's inverse first.  With an auxiliary stream the power sums
+  // and their row's descent run there, beside the other rows' descent (each
+  // branch in its own rows of X and of the scratch), joined at the leaves.
+  const bool fork = aux != nullptr && ev_fork != nullptr && ev_join != nullptr;
+  cudaStream_t sa = fork ? aux : st;
+  FastRun Fa{ctx, C, M, tw, itw, logN, sa};
+  if (fork) {
+    cudaEventRecord(ev_fork, st);
+    cudaStreamWaitEvent(sa, ev_fork, 0);
   }
+  // descent from the root (node size T') to the leaf blocks of nr rows from
+  // row r0: every branch swaps X0 and X1 once per level
+  auto descend = [&](int r0, int nr, cudaStream_t s) {
+    uint64_t* X = w.X0 + (size_t)r0 * Tp;
+    uint64_t* Xn = w.X1 + (size_t)r0 * Tp;
+    uint32_t* XH = w.XH + (size_t)r0 * kNP * Tp;
+    uint32_t* Y = w.Y + (size_t)2 * r0 * kNP * Tp;
+    for (int l = Lt; l >= 1; l--) {
+      const int logn = kLeafLog + l;
+      const int64_t nodes = (T + (1ll << logn) - 1) >> logn;
+      bool done = false;
+      if (cluster_level(ctx, logn, nodes * nr)) {
+        cudaEvent_t a = prof_mark(ctx, s);
+        done = launch_cluster(k_desc_cluster, nodes * nr, cluster_threads(logn), sizeof(uint32_t) * 3 << logn, s, X,
+                              T, Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn, nodes) == cudaSuccess;
+        if (!done) (void)cudaGetLastError();
+        cudaEvent_t b2 = prof_mark(ctx, s);
+        // one forward and two inverse transforms of 2^logn per prime of each cluster
+        if (done) prof_add(ctx, PH_DESC, a, b2, (double)(nodes * nr) * kNP * 3 * (double)((1ll << logn) / 2) * logn);
+      }
+      if (!done && logn <= kFusedLog) {
+        const int npc = fused_npc(logn);
+        launch_k(k_desc_fused, (unsigned)((nodes + npc - 1) / npc * nr), kFusedThreads,
+                 sizeof(uint32_t) * 2 * kNP * npc << logn, s, X, T, Tp, logn, C, crt_scale(logn), M, tw, logN,
+                 w.spec[l - 1], Xn, nodes);
+        note_launch();
+        done = true;
+      }
+      if (!done) {
+        const int64_t all = (int64_t)nr * kNP * Tp;
+        launch_k(k_desc_load, cdivu((int64_t)nr * Tp, 256), 256, 0, s, X, nr, T, Tp, logn, C, XH);
+        note_launch();
+        launch_ntt(ctx, XH, all >> logn, logn, logT, false, tw, itw, logN, C, s);
+        launch_k(k_desc_mul, cdivu((int64_t)kNP * Tp, 256), 256, 0, s, XH, w.spec[l - 1], nr, Tp, logn, C, Y);
+        note_launch();
+        launch_ntt(ctx, Y, (2 * all) >> logn, logn, logT, true, tw, itw, logN, C, s);
+        launch_k(k_desc_crt, cdivu((int64_t)nr * Tp, 256), 256, 0, s, Y, nr, T, Tp, logn, C, crt_scale(logn), M,
+                 Xn);
+        note_launch();
+      }
+      std::swap(X, Xn);
+    }
+  };
+  // the right-hand sides (rows 0 .. S-1) on the call's stream
+  if (S > 0) {
+    launch_k(k_stage_rhs, cdivu((int64_t)S * T, 256), 256, 0, st, b, ldb, S, (const uint64_t*)nullptr, 0, S, T, Tp,
+             w.X0);
+    note_launch();
+    descend(0, S, st);
+  }
+  // power sums: g = 1 / rev(M) mod z^T by Newton's iteration, ps = rev(M') g;
+  // then their row S
+  launch_k(k_rev_poly, cdivu(T + 1, 256), 256, 0, sa, m, T, M, w.f, w.rd, w.g);
+  note_launch();
+  Fa.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
+  Fa.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
+  launch_k(k_stage_rhs, cdivu(T, 256), 256, 0, sa, b, ldb, S, (const uint64_t*)w.ps, S, 1, T, Tp, w.X0);
+  note_launch();
+  descend(S, 1, sa);
+  if (fork) {
+    cudaEventRecord(ev_join, sa);
+    cudaStreamWaitEvent(st, ev_join, 0);
+  }
+  uint64_t* X = (Lt & 1) ? w.X1 : w.X0;     // where Lt swaps leave the rows
   // leaves
   launch_k(k_fast_leafval, dim3(cdivu(T, kLeaf), (unsigned)((R + kLeafCols - 1) / kLeafCols)), kLeaf, 0, st, 
       w.coef[0], X, R, T, Tp, v, vp, M, part, T, den);

@@ -68,6 +68,10 @@ struct zr_ctx {
   // their fork and join events
   cudaStream_t fstream[4] = {};
   cudaEvent_t fev_fork = nullptr, fev_join[4] = {};
+  // the auxiliary stream and fork / join events of a fast solve on the call's
+  // stream (slot 4) or on fstream[j] (slot j)
+  cudaStream_t faux[5] = {};
+  cudaEvent_t faux_fork[5] = {}, faux_join[5] = {};
   // the O(T log^2 T) solve: constants of the transform primes, the twiddle
   // tables (grown on demand) and the choice between the two solve methods
   zr::NttConsts ntt;
@@ -171,8 +175,11 @@ BatchItem step_item(const zr_poly* skel, int32_t newvar, const uint64_t* y, int3
 constexpr int64_t kFastMaxT = 1ll << 21;   // largest T of the fast path (transforms up to 2^22)
 zr::NttConsts make_ntt_consts(uint64_t p);
 size_t fast_ws_need(int64_t T, int R);
+// (aux, ev_fork, ev_join: a second stream and two events on which the power
+// sums run beside the right-hand sides' descent; null: all on st)
 zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, const uint64_t* vp, const uint64_t* b,
-                             int64_t ldb, uint64_t* part, uint64_t* den, char* ws, cudaStream_t st);
+                             int64_t ldb, uint64_t* part, uint64_t* den, char* ws, cudaStream_t st,
+                             cudaStream_t aux = nullptr, cudaEvent_t ev_fork = nullptr, cudaEvent_t ev_join = nullptr);
 // whether a system of T unknowns takes the fast path in this context
 bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S);
 // grows the transform tables for fast solves of up to T unknowns
