@@ -81,8 +81,10 @@ size_t zr_workspace_bytes(const zr_ctx* ctx);
  * milliseconds and the number of timed occurrences of a phase, and
  * zr_profile_work the algorithmic work recorded with them (phases 9 and 10:
  * radix-2 butterflies, n/2 per stage of each transform of n words; 0 for the
- * others).  Errors: ZR_ERR_INVALID_ARG for a phase outside 0..10 or a null
- * pointer. */
+ * others).  While the profiler is on, the O(T log^2 T) solve runs its power
+ * sums on the call's stream instead of beside the right-hand sides' descent,
+ * so that each timed launch has the GPU to itself.  Errors:
+ * ZR_ERR_INVALID_ARG for a phase outside 0..10 or a null pointer. */
 uint64_t zr_launch_count(void);
 zr_status zr_profile_enable(zr_ctx* ctx, int32_t on);
 zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count);

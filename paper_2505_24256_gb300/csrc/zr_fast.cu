@@ -1733,7 +1733,9 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   // needs Newton's inverse first.  With an auxiliary stream the power sums
   // and their row's descent run there, beside the other rows' descent (each
   // branch in its own rows of X and of the scratch), joined at the leaves.
-  const bool fork = aux != nullptr && ev_fork != nullptr && ev_join != nullptr;
+  // (With the context's profiler on, everything runs on st, so that each
+  // timed launch has the GPU to itself.)
+  const bool fork = aux != nullptr && ev_fork != nullptr && ev_join != nullptr && !ctx->prof.on;
   cudaStream_t sa = fork ? aux : st;
   FastRun Fa{ctx, C, M, tw, itw, logN, sa};
   if (fork) {

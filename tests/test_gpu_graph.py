@@ -115,3 +115,43 @@ def test_graph_reports_duplicate_samples(ctx):
     with pytest.raises(zr.ZrError) as ei:
         ctx.step_graph([st.desc])
     assert ei.value.status == zr.SINGULAR
+
+
+def test_graph_fast_steps(ctx):
+    """Steps that take the O(T log^2 T) solve captured in one graph: a lone
+    fast step (its power sums on the auxiliary stream) and an uneven batch
+    with two fast entries beside an O(T^2) one (the fast entries on streams
+    of their own); replayed three times, each result equals generator truth
+    and the direct call's."""
+    ctx.solve_method(0, 1500)
+    try:
+        lone = Step(ctx, W.step_workload(531, 2600, 4, 12, 9))
+        g = ctx.step_graph([lone.desc])
+        try:
+            for _ in range(3):
+                lone.oc.zero_()
+                lone.cnt.zero_()
+                g.launch()
+            g.status()
+            e, c = lone.result()
+            assert np.array_equal(e, lone.wl.exps) and np.array_equal(c, lone.wl.coef)
+        finally:
+            g.close()
+        wls = [W.step_workload(532, 1800, 3, 10, 11), W.step_workload(533, 400, 5, 9, 21),
+               W.step_workload(534, 3100, 2, 14, 5)]
+        steps = [Step(ctx, wl, offset=i % 2) for i, wl in enumerate(wls)]
+        g = ctx.step_graph([s.desc for s in steps])
+        try:
+            for _ in range(3):
+                for s in steps:
+                    s.oc.zero_()
+                    s.cnt.zero_()
+                g.launch()
+            g.status()
+            for s, wl in zip(steps, wls):
+                e, c = s.result()
+                assert np.array_equal(e, wl.exps) and np.array_equal(c, wl.coef)
+        finally:
+            g.close()
+    finally:
+        ctx.solve_method(0)
