@@ -137,8 +137,8 @@ def test_graph_fast_steps(ctx):
             assert np.array_equal(e, lone.wl.exps) and np.array_equal(c, lone.wl.coef)
         finally:
             g.close()
-        wls = [W.step_workload(532, 1800, 3, 10, 11), W.step_workload(533, 400, 5, 9, 21),
-               W.step_workload(534, 3100, 2, 14, 5)]
+        wls = [W.step_workload(532, 1800, 4, 10, 11), W.step_workload(533, 400, 5, 9, 21),
+               W.step_workload(534, 3100, 3, 16, 5)]
         steps = [Step(ctx, wl, offset=i % 2) for i, wl in enumerate(wls)]
         g = ctx.step_graph([s.desc for s in steps])
         try:
