@@ -419,6 +419,10 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
   }
   if (ctx->ntt_tw) cudaFree(ctx->ntt_tw);
   if (ctx->fprobe_ws) cudaFree(ctx->fprobe_ws);
+  for (int j = 0; j < zr_ctx::kProbeLanes; j++) {
+    if (ctx->pl_ws[j]) cudaFree(ctx->pl_ws[j]);
+    if (ctx->pl_fws[j]) cudaFree(ctx->pl_fws[j]);
+  }
   delete ctx;
 }
 

@@ -531,10 +531,28 @@ size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t
 
 zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
                       const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
-                      cudaStream_t st) {
-  zr_status r = ensure_ws(ctx, probes_ws_need(ctx, f, k, S, T), st);
-  if (r) return r;
-  return probes_enqueue(ctx, f, k, y, S, samples, z, T, offset, out, ldo, status, ctx->ws, st);
+                      cudaStream_t st, int lane) {
+  if (lane < 0 || lane >= zr_ctx::kProbeLanes) {
+    zr_status r = ensure_ws(ctx, probes_ws_need(ctx, f, k, S, T), st);
+    if (r) return r;
+    return probes_enqueue(ctx, f, k, y, S, samples, z, T, offset, out, ldo, status, ctx->ws, st);
+  }
+  // the lane's own scratch, grown (rarely) after its stream's queued work
+  const size_t need = probes_ws_need(ctx, f, k, S, T);
+  if (ctx->pl_cap[lane] < need) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && ctx->pl_ws[lane]) e = cudaFree(ctx->pl_ws[lane]);
+    ctx->pl_ws[lane] = nullptr;
+    ctx->pl_cap[lane] = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->pl_ws[lane], need + need / 4);
+    if (e != cudaSuccess) {
+      ctx->pl_ws[lane] = nullptr;
+      return cuda_err(ctx, e, "probe lane workspace");
+    }
+    ctx->pl_cap[lane] = need + need / 4;
+  }
+  return probes_enqueue(ctx, f, k, y, S, samples, z, T, offset, out, ldo, status, ctx->pl_ws[lane], st,
+                        &ctx->pl_fws[lane], &ctx->pl_fcap[lane]);
 }
 
 // The evaluator's scratch, carved the same way for sizing and for use.
@@ -604,7 +622,11 @@ __global__ void k_eval_weights(int64_t G, int S, const int64_t* __restrict__ sta
 // The evaluation itself, with its scratch at `base` (capacity checked by the caller).
 zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
                          const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
-                         char* base, cudaStream_t st) {
+                         char* base, cudaStream_t st, char** fws, size_t* fcap) {
+  if (!fws || !fcap) {
+    fws = &ctx->fprobe_ws;
+    fcap = &ctx->fprobe_cap;
+  }
   const Mod& M = ctx->M;
   const int64_t Tf = f->T;
   const int nv = f->nv;
@@ -651,25 +673,25 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
     cudaError_t e = cudaSuccess;
     const size_t wbytes = (((size_t)S * G * sizeof(uint64_t)) + 255) & ~(size_t)255;
     const size_t need = wbytes + fast_probes_ws_need(G, T, S);
-    if (ctx->fprobe_cap < need) {
-      if (ctx->fprobe_ws) cudaFree(ctx->fprobe_ws);
-      ctx->fprobe_ws = nullptr;
-      ctx->fprobe_cap = 0;
-      e = cudaMalloc(&ctx->fprobe_ws, need + need / 4);
+    if (*fcap < need) {
+      if (*fws) cudaFree(*fws);
+      *fws = nullptr;
+      *fcap = 0;
+      e = cudaMalloc(fws, need + need / 4);
       if (e != cudaSuccess) {
-        ctx->fprobe_ws = nullptr;
+        *fws = nullptr;
         return cuda_err(ctx, e, "zr_zippel_probes: fast workspace");
       }
-      ctx->fprobe_cap = need + need / 4;
+      *fcap = need + need / 4;
     }
-    uint64_t* W = reinterpret_cast<uint64_t*>(ctx->fprobe_ws);
+    uint64_t* W = reinterpret_cast<uint64_t*>(*fws);
     {
       const int64_t want = cdiv(G * S, 256), cap = 8ll * (ctx->sms ? ctx->sms : 152);
       k_eval_weights<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(G, S, w.start, w.cnt, w.order, w.a, f->exps,
                                                                           nv, k, w.tabC, w.U, offset, M, W);
       note_launch();
     }
-    return fast_probes_enqueue(ctx, G, w.U, W, G, S, T, out, ldo, ctx->fprobe_ws + wbytes, st);
+    return fast_probes_enqueue(ctx, G, w.U, W, G, S, T, out, ldo, *fws + wbytes, st);
   }
   // the group count stays on the device: the kernels read it, sized for Tf groups
   const RingLayout L = ring_layout(S, Tn);

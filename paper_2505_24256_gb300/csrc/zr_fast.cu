@@ -1677,7 +1677,9 @@ zr_status ensure_ntt_tables(zr_ctx* ctx, int logN, cudaStream_t st) {
   if (ctx->ntt_logN >= logN) return ZR_OK;
   if (logN > kNttMaxLog) return set_err(ctx, ZR_ERR_INVALID_ARG, "fast solve: transform too large");
   if (ctx->ntt_tw) {
-    cudaStreamSynchronize(st);
+    // the old tables may be in use on any stream of the context (probe
+    // lanes, fast streams): wait for the whole device before freeing them
+    cudaDeviceSynchronize();
     cudaFree(ctx->ntt_tw);
     ctx->ntt_tw = nullptr;
     ctx->ntt_logN = 0;

@@ -83,6 +83,14 @@ struct zr_ctx {
   // known (grow-only, separate from the step workspace)
   char* fprobe_ws = nullptr;
   size_t fprobe_cap = 0;
+  // scratch of the probe lanes (probes generated on streams of their own,
+  // e.g. by the server for several requests at once): the evaluator's
+  // workspace and the fast evaluator's, per lane (grow-only)
+  static constexpr int kProbeLanes = 4;
+  char* pl_ws[kProbeLanes] = {};
+  size_t pl_cap[kProbeLanes] = {};
+  char* pl_fws[kProbeLanes] = {};
+  size_t pl_fcap[kProbeLanes] = {};
   std::string err;
   std::mutex mu;                // guards err for the serve thread
 };
@@ -199,12 +207,16 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
 
 // evaluator (zr_eval.cu)
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);
+// (fws, fcap: the grow-only workspace of the fast evaluator; null: the context's)
 zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
                          const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
-                         char* base, cudaStream_t st);
+                         char* base, cudaStream_t st, char** fws = nullptr, size_t* fcap = nullptr);
+// (lane: -1 the context's workspace, which the batch runner shares in stream
+// order; 0 .. kProbeLanes-1 that probe lane's own scratch, for probes run
+// concurrently on streams of their own)
 zr_status probes_impl(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
                       const uint64_t* z, int64_t T, int offset, uint64_t* out, int64_t ldo, uint32_t* status,
-                      cudaStream_t st);
+                      cudaStream_t st, int lane = -1);
 
 // argument check of a reconstruction request (zr_recon.cu)
 zr_status check_recon_args(zr_ctx* ctx, const zr_blackbox* bb, const zr_recon_params* prm);

@@ -482,8 +482,16 @@ zr_status Recon::prepare(std::vector<BatchItem>& items, uint32_t* d_status, int6
       if ((r = eval_at(fN_, (int64_t)(S - S1) * T, d_ppts_.as<uint64_t>(), b1))) return fail(r);
     } else if (T > 0) {
       zr_poly fv = fN_.view();
-      r = probes_impl(ctx_, &fv, k, d_y_.as<uint64_t>(), S - S1, cs1, d_z_.as<uint64_t>(), T, offset_, b1, T,
-                      d_status, st_);
+      if (pst_ && pev_in_ && pev_out_) {
+        cudaEventRecord(pev_in_, st_);
+        cudaStreamWaitEvent(pst_, pev_in_, 0);
+        r = probes_impl(ctx_, &fv, k, d_y_.as<uint64_t>(), S - S1, cs1, d_z_.as<uint64_t>(), T, offset_, b1, T,
+                        d_status, pst_, plane_);
+        cudaEventRecord(pev_out_, pst_);
+      } else {
+        r = probes_impl(ctx_, &fv, k, d_y_.as<uint64_t>(), S - S1, cs1, d_z_.as<uint64_t>(), T, offset_, b1, T,
+                        d_status, st_);
+      }
       if (r) return fail(r);
     }
     r = step_entry(curN_, S, d_b_.as<uint64_t>(), T > 0 ? T : 1, nextN_, d_status, d_counts, items);

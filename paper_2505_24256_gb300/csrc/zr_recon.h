@@ -72,6 +72,17 @@ class Recon {
   // slots (two int64).  Synchronises when the rational path must check the
   // univariate reconstruction before the step.
   zr_status prepare(std::vector<BatchItem>& items, uint32_t* d_status, int64_t* d_counts);
+  // The probe lane the next prepare() uses for a polynomial step's probes:
+  // they run on `st` with the context's scratch of `lane`, after ev_in (recorded on
+  // the request's stream once its inputs are there), and ev_out is recorded
+  // after them; the caller makes its batch wait for ev_out.  st null: the
+  // request's own stream, as for every other call.
+  void set_probe_lane(cudaStream_t st, int lane, cudaEvent_t ev_in, cudaEvent_t ev_out) {
+    pst_ = st;
+    plane_ = lane;
+    pev_in_ = ev_in;
+    pev_out_ = ev_out;
+  }
   // After the batch: this request's status flags and its count slots.
   zr_status finish(uint32_t flags, const int64_t* counts);
   zr_result* take_result();           // ownership passes to the caller
@@ -113,6 +124,9 @@ class Recon {
 
   zr_ctx* ctx_;
   cudaStream_t st_;
+  cudaStream_t pst_ = nullptr;        // probe lane (see set_probe_lane)
+  int plane_ = -1;
+  cudaEvent_t pev_in_ = nullptr, pev_out_ = nullptr;
   Mod M_;
   // request
   int nv_;

@@ -14,8 +14,9 @@
 //   * every tick gathers the next Zippel step of the lane's active requests,
 //     oldest first, until the steps add up to kTickWork multiply-accumulate
 //     equivalents (each step weighted by the solve and evaluator it takes)
-//     -- their probes are generated on the device, then all those steps run
-//     in one batch of launches (run_batch) -- reads back each request's own
+//     -- their probes are generated on the device (polynomial requests' on
+//     four probe streams at once, each with its own scratch), then all those
+//     steps run in one batch of launches (run_batch) -- reads back each request's own
 //     status word and term counts, and advances each request (or redraws its
 //     anchor);
 //   * finished requests leave their slot at once, so requests that arrive
@@ -101,6 +102,11 @@ struct Lane {
   uint32_t* h_status = nullptr;
   int64_t* d_counts = nullptr;
   int64_t* h_counts = nullptr;
+  // probe lanes: a tick's polynomial requests generate their probes on these
+  // streams (round-robin, each with its own scratch in the lane's context),
+  // and the batch waits for them
+  cudaStream_t pst[zr_ctx::kProbeLanes] = {};
+  cudaEvent_t pin[zr_ctx::kProbeLanes] = {}, pout[zr_ctx::kProbeLanes] = {};
 };
 
 struct zr_server {
@@ -204,15 +210,21 @@ static void server_loop(zr_server* s, int li) {
     std::vector<char> stepped(active.size(), 0);
     cudaMemsetAsync(L.d_status, 0, sizeof(uint32_t) * s->max_slots, L.stream);
     double work = 0;
+    int nprep = 0;
     for (size_t i = 0; i < active.size(); i++) {
       Active& a = active[i];
       const double c = a.recon->next_cost();
       if (i > 0 && work + c > kTickWork) continue;
       work += c;
       stepped[i] = 1;
+      const int j = nprep++ % zr_ctx::kProbeLanes;
+      if (L.pst[j]) a.recon->set_probe_lane(L.pst[j], j, L.pin[j], L.pout[j]);
       const zr_status st = a.recon->prepare(items, L.d_status + a.slot, L.d_counts + 2 * a.slot);
+      a.recon->set_probe_lane(nullptr, -1, nullptr, nullptr);
       in_batch[i] = st == ZR_OK;
     }
+    for (int j = 0; j < zr_ctx::kProbeLanes && j < nprep; j++)
+      if (L.pst[j]) cudaStreamWaitEvent(L.stream, L.pout[j], 0);
     zr_status bst = run_batch(L.ctx, items.data(), (int)items.size(), L.ctx->d_status_call, L.stream);
     cudaError_t e = cudaMemcpyAsync(L.h_status, L.d_status, sizeof(uint32_t) * s->max_slots, cudaMemcpyDeviceToHost,
                                     L.stream);
@@ -256,6 +268,13 @@ static void lane_free(Lane& L) {
   if (L.d_counts) cudaFree(L.d_counts);
   if (L.h_counts) cudaFreeHost(L.h_counts);
   if (L.stream) cudaStreamDestroy(L.stream);
+  for (int j = 0; j < zr_ctx::kProbeLanes; j++) {
+    if (L.pst[j]) cudaStreamDestroy(L.pst[j]);
+    if (L.pin[j]) cudaEventDestroy(L.pin[j]);
+    if (L.pout[j]) cudaEventDestroy(L.pout[j]);
+    L.pst[j] = nullptr;
+    L.pin[j] = L.pout[j] = nullptr;
+  }
   if (L.own_ctx && L.ctx) zr_destroy(L.ctx);
   L.d_status = L.h_status = nullptr;
   L.d_counts = L.h_counts = nullptr;
@@ -286,6 +305,11 @@ extern "C" zr_status zr_serve_create(zr_ctx* ctx, size_t mem_budget, int32_t max
       L.ctx->solve_persistent = false;   // let the fast lane's kernels in between work items
     }
     e = cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, li == 0 ? hi : lo);
+    for (int j = 0; j < zr_ctx::kProbeLanes && e == cudaSuccess; j++) {
+      e = cudaStreamCreateWithPriority(&L.pst[j], cudaStreamNonBlocking, li == 0 ? hi : lo);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.pin[j], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.pout[j], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&L.d_status, sizeof(uint32_t) * max_slots);
     if (e == cudaSuccess) e = cudaMallocHost(&L.h_status, sizeof(uint32_t) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&L.d_counts, sizeof(int64_t) * 2 * max_slots);
