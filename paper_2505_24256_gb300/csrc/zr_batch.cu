@@ -241,56 +241,63 @@ __global__ void __launch_bounds__(kNewtonThreads) k_b_newton_table(const BDesc* 
 // inverse (one inversion per warp), the S dot products from their k-block
 // partials, then the monomial coefficients through W.  Blocks of kFinB terms
 // never straddle entries (pre counts blocks), so W sits in shared memory.
-__global__ void __launch_bounds__(kFinB) k_b_finish_newton(const BDesc* __restrict__ Ds,
-                                                         const int64_t* __restrict__ pre_blk, int n, Mod M) {
+// kFinSplit warps share a block: the first inverts, all sum the partials of
+// every kFinSplit-th right-hand side and compute every kFinSplit-th output.
+__global__ void __launch_bounds__(kFinB * kFinSplit) k_b_finish_newton(const BDesc* __restrict__ Ds,
+                                                                      const int64_t* __restrict__ pre_blk, int n,
+                                                                      Mod M) {
   extern __shared__ uint64_t fsm[];
+  __shared__ uint64_t sh_inv[kFinB];
+  __shared__ int sh_cnt[kFinSplit][kFinB];
   const int i = seg_of(pre_blk, n, blockIdx.x);
   const BDesc& D = Ds[i];
   const int S = D.S, Sn = D.Sn, s1 = Sn - S;   // s1 = 1: sample 0 is given (c0)
   uint64_t* W = fsm;
   uint64_t* num = fsm + Sn * Sn;
   for (int idx = threadIdx.x; idx < Sn * Sn; idx += blockDim.x) W[idx] = D.invd[idx];
-  const int64_t j = (blockIdx.x - pre_blk[i]) * kFinB + threadIdx.x;
+  const int t = threadIdx.x & (kFinB - 1), q = threadIdx.x / kFinB;   // term, warp of the split
+  const int64_t j = (blockIdx.x - pre_blk[i]) * kFinB + t;
   const bool active = j < D.T;
-  uint64_t den = 1, mult = 1;
-  if (active) {
-    den = root_den(D, j, D.v[j], M, mult);
-    if (den == 0) atomicOr(D.status, ST_ZERO_DEN);
+  if (q == 0) {
+    uint64_t den = 1, mult = 1;
+    if (active) {
+      den = root_den(D, j, D.v[j], M, mult);
+      if (den == 0) atomicOr(D.status, ST_ZERO_DEN);
+    }
+    sh_inv[t] = mul_mod(warp_batch_inverse(den, M), mult, M);
   }
-  const uint64_t inv = mul_mod(warp_batch_inverse(den, M), mult, M);
   if (active) {
-    // sum of the k-block partials; the S loads of one k-block are independent
-    uint64_t* nm = num + threadIdx.x + s1 * kFinB;
-    for (int s = 0; s < S; s++) nm[s * kFinB] = D.part[(int64_t)s * D.T + j];
-    for (int kb = 1; kb < D.NB; kb++) {
-      const uint64_t* pp = D.part + (int64_t)kb * S * D.T + j;
-      for (int s0 = 0; s0 < S; s0 += 8) {
-        uint64_t x[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) x[q] = s0 + q < S ? pp[(int64_t)(s0 + q) * D.T] : 0;
-#pragma unroll
-        for (int q = 0; q < 8; q++)
-          if (s0 + q < S) nm[(s0 + q) * kFinB] = add_mod(nm[(s0 + q) * kFinB], x[q], M);
-      }
+    // sum of the k-block partials, right-hand sides q, q + kFinSplit, .. per warp
+    uint64_t* nm = num + t + s1 * kFinB;
+    for (int s = q; s < S; s += kFinSplit) {
+      uint64_t acc = D.part[(int64_t)s * D.T + j];
+      for (int kb = 1; kb < D.NB; kb++) acc = add_mod(acc, D.part[((int64_t)kb * S + s) * D.T + j], M);
+      nm[s * kFinB] = acc;
     }
   }
+  __syncthreads();
+  const uint64_t inv = sh_inv[t];
   if (active && s1) {
     // the given solution at sample 0, the solved ones scaled by the inverse
-    uint64_t* nm = num + threadIdx.x;
-    nm[0] = D.c0[j];
-    for (int s = 1; s < Sn; s++) nm[s * kFinB] = mul_mod(nm[s * kFinB], inv, M);
+    uint64_t* nm = num + t;
+    if (q == 0) nm[0] = D.c0[j];
+    for (int s = 1 + q; s < Sn; s += kFinSplit) nm[s * kFinB] = mul_mod(nm[s * kFinB], inv, M);
   }
   __syncthreads();
-  int cnt = 0;
-  if (active) {
-    cnt = newton_apply(Sn, W, num + threadIdx.x, kFinB, s1 ? 1 : inv, D.g + j, D.T, M);
-    D.cnt[j] = cnt;
+  // the monomial coefficients e = q, q + kFinSplit, .. of each term
+  sh_cnt[q][t] = active ? newton_apply(Sn, W, num + t, kFinB, s1 ? 1 : inv, D.g + j, D.T, M, q, kFinSplit) : 0;
+  __syncthreads();
+  if (q == 0) {
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kFinSplit; r++) cnt += sh_cnt[r][t];
+    if (active) D.cnt[j] = cnt;
+    // nonzero coefficients of this block of terms, for the compaction
+    int64_t total = cnt;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) total += __shfl_down_sync(0xffffffffu, total, off);
+    if (t == 0) D.bsum[blockIdx.x - pre_blk[i]] = total;
   }
-  // nonzero coefficients of this block of terms, for the compaction
-  __shared__ int64_t sh[33];
-  int64_t total;
-  block_exclusive_scan(cnt, sh, total);
-  if (threadIdx.x == 0) D.bsum[blockIdx.x - pre_blk[i]] = total;
 }
 
 __global__ void __launch_bounds__(256) k_b_finish_solve(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
@@ -793,7 +800,8 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
       }
       const int64_t nblk = pre[o_nblk + n];
       {
-        k_b_finish_newton<<<(unsigned)nblk, kFinB, newton_smem(smax, kFinB), st>>>(dD, dpre + o_nblk, n, M);
+        k_b_finish_newton<<<(unsigned)nblk, kFinB * kFinSplit, newton_smem(smax, kFinB), st>>>(dD, dpre + o_nblk, n,
+                                                                                                 M);
         note_launch();
       }
     } else {

@@ -155,8 +155,23 @@ __device__ inline void newton_table_block(int S, const uint64_t* __restrict__ xs
 // out[e * ld] = scale * sum_s W[e][s] val[s * stride] for e < S (W and val in
 // shared memory, val canonical); returns how many of them are nonzero.
 __device__ inline int newton_apply(int S, const uint64_t* W, const uint64_t* val, int stride, uint64_t scale,
-                                   uint64_t* out, int64_t ld, const Mod& M) {
+                                   uint64_t* out, int64_t ld, const Mod& M, int e_first = 0, int e_step = 1) {
   int cnt = 0;
+  if (e_step != 1) {
+    // the outputs e_first, e_first + e_step, ... only
+    for (int e = e_first; e < S; e += e_step) {
+      Acc8 acc = {0, 0, 0, 0, 0, 0, 0, 0};
+      const uint64_t* w = W + (int64_t)e * S;
+      for (int s = 0; s < S; s++) {
+        const uint64_t x = val[s * stride], y = w[s];
+        mac8(acc, lo32(x), hi32(x), lo32(y), hi32(y));
+      }
+      const uint64_t g = mul_mod(acc8_value(acc, M), scale, M);
+      out[(int64_t)e * ld] = g;
+      cnt += g != 0;
+    }
+    return cnt;
+  }
   for (int e0 = 0; e0 < S; e0 += 4) {
     Acc8 acc[4];
 #pragma unroll

@@ -118,6 +118,7 @@ void launch_newton_table(int S, const uint64_t* xs, const Mod& M, uint64_t* W, u
 void launch_newton(int64_t nterms, int npts, const uint64_t* W, const uint64_t* vals, int64_t ld, const Mod& M,
                    uint64_t* coef, cudaStream_t st);
 constexpr int kFinB = 32;                 // terms per block of a step's finish and compaction
+constexpr int kFinSplit = 4;              // warps sharing a block's terms in the finish (by right-hand side and output)
 size_t newton_smem(int S, int terms);     // dynamic shared memory of one block of `terms` terms
 int64_t scan_blocks(int64_t n);           // number of kFinB-term compaction blocks
 // split partials the product tree may use for T leaves (words = that x T)
