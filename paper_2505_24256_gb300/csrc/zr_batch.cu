@@ -351,10 +351,12 @@ __global__ void __launch_bounds__(kScanB) k_b_scan(const BDesc* __restrict__ Ds)
 }
 
 // The new skeleton: the nonzero coefficients of every term j in order of j,
-// then of the power s of x_k.  One block per kFinB terms; its threads walk the
-// block's output slots, so consecutive threads write consecutive outputs.
-__global__ void __launch_bounds__(kCompB) k_b_scatter(const BDesc* __restrict__ Ds,
-                                                      const int64_t* __restrict__ pre_blk, int n) {
+// then of the power s of x_k.  One block per kCompB terms and kFinSplit warps:
+// the first warp takes a term per lane (its nonzero mask and offset), then
+// all threads walk the block's output slots, so consecutive threads write
+// consecutive outputs.
+__global__ void __launch_bounds__(kCompB * kFinSplit) k_b_scatter(const BDesc* __restrict__ Ds,
+                                                                  const int64_t* __restrict__ pre_blk, int n) {
   __shared__ int64_t sh[33];
   __shared__ int32_t offs[kCompB];
   __shared__ uint64_t masks[kCompB];
@@ -364,26 +366,31 @@ __global__ void __launch_bounds__(kCompB) k_b_scatter(const BDesc* __restrict__ 
   const int64_t j0 = blk * kCompB, j = j0 + threadIdx.x;
   const int S = D.Sn;
   uint64_t mask = 0;
-  if (j < D.T)
+  if (threadIdx.x < kCompB && j < D.T)
     for (int s = 0; s < S; s++)
       if (D.g[(int64_t)s * D.T + j] != 0) mask |= 1ull << s;
   int64_t total;
   const int64_t ex = block_exclusive_scan(__popcll(mask), sh, total);
-  offs[threadIdx.x] = (int32_t)ex;
-  masks[threadIdx.x] = mask;
+  if (threadIdx.x < kCompB) {
+    offs[threadIdx.x] = (int32_t)ex;
+    masks[threadIdx.x] = mask;
+  }
   __syncthreads();
   const int64_t base = D.bsum[blk];
   const int nv = D.nv, k = D.k;
-  for (int slot = threadIdx.x; slot < total; slot += kCompB) {
+  for (int slot = threadIdx.x; slot < total; slot += blockDim.x) {
     int lo = 0, hi = kCompB - 1;   // the term owning this slot: largest t with offs[t] <= slot
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (offs[mid] <= slot) lo = mid;
       else hi = mid - 1;
     }
-    uint64_t m = masks[lo];
-    for (int r = slot - offs[lo]; r > 0; r--) m &= m - 1;
-    const int s = __ffsll((long long)m) - 1;
+    // the (slot - offs[lo])-th set bit of the term's mask
+    const uint64_t m = masks[lo];
+    const int r = slot - offs[lo];
+    const unsigned mlo = (unsigned)m, mhi = (unsigned)(m >> 32);
+    const int nlo = __popc(mlo);
+    const int s = r < nlo ? (int)__fns(mlo, 0, r + 1) : 32 + (int)__fns(mhi, 0, r - nlo + 1);
     const int64_t jj = j0 + lo, o = base + slot;
     if (o < D.out_cap) {
       const uint8_t* e = D.exps + jj * nv;
@@ -812,7 +819,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   if (mode == 0 && nroots) {
     { k_b_scan<<<n, kScanB, 0, st>>>(dD); note_launch(); }
     {
-      k_b_scatter<<<(unsigned)pre[o_nblk + n], kCompB, 0, st>>>(dD, dpre + o_nblk, n);
+      k_b_scatter<<<(unsigned)pre[o_nblk + n], kCompB * kFinSplit, 0, st>>>(dD, dpre + o_nblk, n);
       note_launch();
     }
   }
