@@ -777,7 +777,6 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
         flush.zero_()
         ctx.zippel_step(skel, k, y, S, cs, b, T, 0, oe, oc, cap)
     torch.cuda.synchronize()
-    ctx.profile(True)
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -790,9 +789,19 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
     torch.cuda.synchronize()
     clk = clocks.stop()
     times = [a.elapsed_time(bb) for a, bb in evs]
+    # phases and the dominant kernel's launches from a second, profiled pass
+    ctx.profile(True)
+    pevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        pevs[i][0].record(stream)
+        ctx.zippel_step(skel, k, y, S, cs, b, T, 0, oe, oc, cap)
+        pevs[i][1].record(stream)
+    torch.cuda.synchronize()
+    prof_ms = sum(a.elapsed_time(bb) for a, bb in pevs) / steps
     fast_ms, fast_n = ctx.profile_query("fast")
     phases = {ph: ctx.profile_query(ph)[0] / max(steps, 1) for ph in ctx.PHASES[:7] + ("fast", "ntt", "desc")}
-    fast_roof = fast_roofline(ctx, peaks, wl.name, steps, sum(times) / len(times))
+    fast_roof = fast_roofline(ctx, peaks, wl.name, steps, prof_ms)
     ctx.profile(False)
     ok = n == wl.exps.shape[0] and np.array_equal(oe[:n].cpu().numpy(), wl.exps) and \
         np.array_equal(oc[:n].cpu().numpy().view(np.uint64), wl.coef)
@@ -846,6 +855,7 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
         "solve": "O(T log^2 T) (subproduct tree, transforms over five 30-bit primes)",
         "ms_per_step": ms, "terms_per_s": T / (ms / 1e3),
         "fast_solve_ms": fast_ms / max(fast_n, 1),
+        "fast_solve_note": "from the profiled pass (the power sums then run on the call's stream)",
         "roofline": fast_roof,
         "phase_ms": phases,
         "quadratic_form": {"ms_per_step": quad_ms, "terms_per_s": T / (quad_ms / 1e3),
