@@ -210,3 +210,47 @@ def test_fast_probes_few_groups(ctx, orc):
     finally:
         ctx.solve_method(0)
     assert np.array_equal(h64(b), orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, T))
+
+
+def test_fast_probes_fall_back_above_64_samples(ctx, orc):
+    """With the fast method forced, 65 samples exceed the transposed tree's
+    column limit: the matrix-vector evaluator runs instead, and the probes
+    still equal the oracle's."""
+    wl = W.step_workload(67, 600, 3, 12, 65)
+    fe, fc = d8(wl.exps), d64(wl.coef)
+    f = ctx.poly(wl.nv, wl.exps.shape[0], fe, fc)
+    y, cs, z = d64(wl.y), d64(wl.cs), d64(wl.z)
+    b = zeros64(wl.S, wl.T)
+    ctx.solve_method(ctx.SOLVE_FAST)
+    try:
+        ctx.profile(True)
+        ctx.zippel_probes(f, wl.k, y, wl.S, cs, z, wl.T, 0, b, wl.T)
+        ntt_launches = ctx.profile_query("ntt")[1]
+        ctx.profile(False)
+    finally:
+        ctx.solve_method(0)
+    assert ntt_launches == 0
+    assert np.array_equal(h64(b), orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, wl.T))
+
+
+def test_profiler_counts_the_descent_butterflies(ctx):
+    """The profiler's work count for the descent's cluster levels is the
+    formula the bench's roofline uses: for each level of transform size
+    n = 2^l (l = 8 .. 10 at T = 1000), ceil(T / n) nodes x (S + 1) rows x
+    5 primes x 3 transforms x (n / 2) log2 n butterflies."""
+    T, S = 1000, 2
+    rnd = random.Random(21)
+    v, b = rand_nodes(rnd, T, P63), rand_res(rnd, (S, T), P63)
+    c = zeros64(S, T)
+    ctx.solve_method(ctx.SOLVE_FAST)
+    try:
+        ctx.profile(True)
+        ctx.vandermonde_solve([dict(T=T, S=S, offset=0, v=d64(v), b=d64(b), ldb=T, c=c, ldc=T)])
+        work = ctx.profile_work("desc")
+        launches = ctx.profile_query("desc")[1]
+        ctx.profile(False)
+    finally:
+        ctx.solve_method(0)
+    want = sum(-(-T // (1 << l)) * (S + 1) * 5 * 3 * (1 << (l - 1)) * l for l in (8, 9, 10))
+    assert launches == 6                   # three levels, the right-hand sides and the power sums apart
+    assert work == want
