@@ -228,7 +228,7 @@ zr_status zr_newton_batched(zr_ctx* ctx, int64_t nterms, int32_t npts, const uin
  * npts <= 64 (larger npts returns ZR_ERR_INVALID_ARG).  Its only scratch is a
  * fixed device array of 64*64+32 words that every GPU loading the library
  * holds until exit.  The first call on a device looks that array up with the
- * device current; make it before any stream capture.  All calls share the
+ * device current.  All calls share the
  * array (the call clears what must start at zero), so calls that overlap on
  * the GPU race: serialise them.  Waits for `stream`; ZR_ERR_SINGULAR when two
  * nodes coincide.  A CUDA error already pending on the calling thread belongs
