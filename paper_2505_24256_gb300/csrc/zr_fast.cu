@@ -160,13 +160,32 @@ __device__ __forceinline__ void radix_pass(uint32_t* sm, int off, int len, int l
     for (int j = 0; j < R; j++) {
       const int cnt = INV ? (1 << (R - 1 - j)) : (1 << j);
       const uint32_t base = INV ? (m >> j) + (kb << (R - 1 - j)) : (m << j) + (kb << j);
+      // a stage's twiddles are contiguous and start at a multiple of their
+      // count: pairs load as 16 bytes
+      if (cnt == 1) {
+        w[wo] = __ldg(&twp[base]);
+      } else {
 #pragma unroll
-      for (int c = 0; c < cnt; c++) w[wo + c] = __ldg(&twp[base + c]);
+        for (int c = 0; c < cnt; c += 2) {
+          const uint4 t2 = __ldg(reinterpret_cast<const uint4*>(twp + base + c));
+          w[wo + c] = make_uint2(t2.x, t2.y);
+          w[wo + c + 1] = make_uint2(t2.z, t2.w);
+        }
+      }
       wo += cnt;
     }
+    // word addresses: for stride 1 the group lies in one row (sw(base) ^ i),
+    // for strides of 256 and more the row bits of the swizzle are the
+    // base's (sw(base) + (i << u)); strides 8 and 64 swizzle each word
+    int at[NR];
+    const int sb = sw(off + a);
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+      at[i] = COLS ? (((a + (i << u)) << cwl) + col)
+                   : (u == 0 ? (sb ^ i) : (u >= 8 ? sb + (i << u) : sw(off + a + (i << u))));
     uint32_t x[NR];
 #pragma unroll
-    for (int i = 0; i < NR; i++) x[i] = sm[COLS ? (((a + (i << u)) << cwl) + col) : sw(off + a + (i << u))];
+    for (int i = 0; i < NR; i++) x[i] = sm[at[i]];
     wo = 0;
 #pragma unroll
     for (int j = 0; j < R; j++) {
@@ -177,7 +196,7 @@ __device__ __forceinline__ void radix_pass(uint32_t* sm, int off, int len, int l
       wo += INV ? (1 << (R - 1 - j)) : (1 << j);
     }
 #pragma unroll
-    for (int i = 0; i < NR; i++) sm[COLS ? (((a + (i << u)) << cwl) + col) : sw(off + a + (i << u))] = x[i];
+    for (int i = 0; i < NR; i++) sm[at[i]] = x[i];
   }
 }
 
