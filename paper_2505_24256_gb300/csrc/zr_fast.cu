@@ -715,30 +715,33 @@ __device__ __forceinline__ uint32_t ld_cluster(uint32_t addr) {
   return v;
 }
 
-// Precision up to which k_newton_cluster runs schoolbook steps.
+// Precision up to which k_newton_cluster runs schoolbook steps, and the
+// largest number of coefficients a thread holds in registers (precision up
+// to 2^14 = kNewtonPer x 1024 threads).
 constexpr int kNewtonSchool = 256;
+constexpr int kNewtonPer = 16;
 __device__ __forceinline__ int ilog2_dev(int x) { return 31 - __clz(x); }   // x a power of two
 
 // k_newton_fused spread over a cluster of kNP CTAs, CTA i holding prime i's
-// transforms in its shared memory: A (f, then f g), B (g's spectrum), C
-// (e_hi, then g e_hi) in the swizzled layout, and g mod q_i.  Each Chinese
+// transforms in its shared memory: A (f, then f g, then e_hi and g e_hi: the
+// second product takes A's place once every CTA has read it), B (g's
+// spectrum) in the swizzled layout, and g mod q_i.  Each Chinese
 // remaindering reads the five CTAs' residues through distributed shared
 // memory, and every CTA remainders all k coefficients, so that each has e
 // (and the new g) for its own prime without a trip through global memory;
 // CTA 0 writes g.  A cluster barrier separates a product's last writes from
-// its remote reads, and those reads from the buffer's next writes (the next
-// barrier of the iteration); the last one keeps every CTA resident until
-// the others are done reading it.
+// its remote reads, and another those reads from the buffer's next writes
+// (the remaindered values wait in registers meanwhile); the last one keeps
+// every CTA resident until the others are done reading it.
 __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64_t* __restrict__ f, int64_t nf,
                                                                   int logK, NttConsts C, Mod M,
                                                                   const uint2* __restrict__ tw, int logN,
                                                                   uint64_t* __restrict__ g) {
   pdl_enter();
-  extern __shared__ uint32_t fsm[];              // A [n], B [n] at 0, n; C [n] at 2K (logical); then g mod q
+  extern __shared__ uint32_t fsm[];              // A (= C) [n] at 0, B [n] at n (logical); then g mod q
   const int me = cluster_rank();
   const int K = 1 << logK;
-  const int cb = 2 * K;
-  uint32_t* Gq = fsm + ((3 * K + 31) & ~31);
+  uint32_t* Gq = fsm + ((2 * K + 31) & ~31);
   const uint32_t q = C.q[me], qi = C.qinv[me];
   const uint2* __restrict__ itw = tw + ((size_t)kNP << logN);
   uint32_t peer[kNP];
@@ -801,7 +804,11 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
       sp[j] = (uint32_t)(((uint64_t)s[j] << 32) / C.q[j]);
     }
     cluster_sync();                              // every CTA's A holds f g mod its prime
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    // e_hi mod this prime, held in registers until every CTA has read A
+    uint32_t ev[kNewtonPer];
+#pragma unroll
+    for (int r = 0; r < kNewtonPer; r++) {
+      const int t = threadIdx.x + r * (int)blockDim.x;
       uint32_t v = 0;
       if (t < k) {
         uint32_t res[kNP];
@@ -809,25 +816,31 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
         for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(k + t)), s[j], sp[j], C.q[j]);
         v = residue64(crt_to_p(res, C, M), C, me);
       }
-      fsm[sw(cb + t)] = v;
+      ev[r] = v;
+    }
+    cluster_sync();                              // A is no longer read: C takes its place
+#pragma unroll
+    for (int r = 0; r < kNewtonPer; r++) {
+      const int t = threadIdx.x + r * (int)blockDim.x;
+      if (t < n) fsm[sw(t)] = ev[r];
     }
     __syncthreads();
-    smem_stages<false>(fsm, cb, n, logn, 0, 0u, tw, logN, C, prime);
+    smem_stages<false>(fsm, 0, n, logn, 0, 0u, tw, logN, C, prime);
     for (int x = threadIdx.x; x < n; x += blockDim.x)
-      fsm[sw(cb + x)] = mont32(sub_if(fsm[sw(cb + x)], 2 * q), sub_if(fsm[sw(n + x)], 2 * q), q, qi);
+      fsm[sw(x)] = mont32(sub_if(fsm[sw(x)], 2 * q), sub_if(fsm[sw(n + x)], 2 * q), q, qi);
     __syncthreads();
-    smem_stages<true>(fsm, cb, n, logn, 0, 0u, itw, logN, C, prime);
+    smem_stages<true>(fsm, 0, n, logn, 0, 0u, itw, logN, C, prime);
     cluster_sync();                              // every CTA's C holds g e_hi mod its prime
     for (int t = threadIdx.x; t < k; t += blockDim.x) {
       uint32_t res[kNP];
 #pragma unroll
-      for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(cb + t)), s[j], sp[j], C.q[j]);
+      for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(t)), s[j], sp[j], C.q[j]);
       const uint64_t x = crt_to_p(res, C, M);
       const uint64_t gv = x ? M.p - x : 0;
       Gq[k + t] = residue64(gv, C, me);
       if (me == 0) g[k + t] = gv;
     }
-    __syncthreads();
+    cluster_sync();                              // C is no longer read: the next step may write A
   }
   cluster_sync();
 }
@@ -848,11 +861,11 @@ inline int cluster_threads(int logn) {
 }
 
 // Cluster levels go up to transforms of 2^14 (a descent CTA then holds
-// 192 KB); Newton's cluster runs to precision 2^13.  Above 2^12 a level
+// 192 KB); Newton's cluster runs to precision 2^14.  Above 2^12 a level
 // takes the cluster form only when its CTAs fit in two waves: with many
 // nodes the tile kernels' higher occupancy wins.
 constexpr int kClusterMaxLog = 14;
-constexpr int kNewtonClusterLog = 13;
+constexpr int kNewtonClusterLog = 14;
 
 // Tree level l <= kFusedLog: the children of node P as full monic
 // polynomials (modulo prime `me`) -> spectra (kept in spec for the descent)
@@ -1491,11 +1504,11 @@ cudaError_t launch_cluster(void (*kernel)(P...), int64_t clusters, int threads, 
   return e;
 }
 
-// Shared memory of k_newton_cluster for K = 2^logK: three swizzled
-// buffers of up to K words (rounded to whole 32-word rows) and g mod q.
+// Shared memory of k_newton_cluster for K = 2^logK: two swizzled buffers
+// of up to K words (rounded to whole 32-word rows) and g mod q.
 size_t newton_cluster_smem(int logK) {
   const size_t K = (size_t)1 << logK;
-  return sizeof(uint32_t) * (((3 * K + 31) & ~(size_t)31) + K);
+  return sizeof(uint32_t) * (((2 * K + 31) & ~(size_t)31) + K);
 }
 
 // Whether this device runs k_newton_cluster (a cluster of kNP CTAs with the
