@@ -180,10 +180,10 @@ typedef struct zr_vsys {
  * (steps, systems, reconstructions, the server):
  *   0  by size: the O(T log^2 T) method for T >= crossover, the O(T^2)
  *      method below it; crossover 0 takes the library's measured rule for a
- *      system of S right-hand sides, T >= 2048 and T^2 (S + 6) >= 2.9e8
- *      (about T >= 3300 for S = 21, 6500 for S = 1); for the probes of a
+ *      system of S right-hand sides, T >= 1024 and T^2 (S + 5) >= 8e7
+ *      (about T >= 1750 for S = 21, 3600 for S = 1); for the probes of a
  *      function of Tf terms, the transposed-tree evaluator when T, Tf >=
- *      4096 and T Tf (S + 8) >= 2e9;
+ *      4096 and T Tf (S + 8) >= 1.8e9;
  *   1  always the O(T^2) method of Sec. 2.2 (Horner quotients, deferred dot
  *      products, one inverse per root);
  *   2  the O(T log^2 T) method for every T it supports.

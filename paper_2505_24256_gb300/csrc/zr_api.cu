@@ -430,27 +430,27 @@ extern "C" const char* zr_last_error(const zr_ctx* ctx) { return ctx ? ctx->err.
 
 // The automatic choice of solve method.  On GB300 the O(T^2) batch costs
 // about 0.2 ms + T^2 (5e-10 S + 8e-9) ms for one system of S right-hand
-// sides, the O(T log^2 T) path 0.4 to 1.2 ms from T = 1024 to 16384 nearly
-// independently of S; they cross near T = 3300 (S = 21), 5000 (S = 5) and
-// 6500 (S = 1), which T^2 (S + 6) >= 2.9e8 follows within 10%.
-static constexpr double kFastCross = 2.9e8;
-static constexpr int64_t kFastFloorT = 2048;
+// sides, the O(T log^2 T) path 0.26 to 0.57 ms from T = 768 to 6144 nearly
+// independently of S; they cross near T = 1750 (S = 21), 3000 (S = 5) and
+// 3600 (S = 1), which T^2 (S + 5) >= 8e7 follows within 10%.
+static constexpr double kFastCross = 8e7;
+static constexpr int64_t kFastFloorT = 1024;
 
 namespace zr {
 bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S) {
   if (T < 1 || T > kFastMaxT || ctx->solve_method == 1) return false;
   if (ctx->solve_method == 2) return true;
   if (ctx->fast_min_T > 0) return T >= ctx->fast_min_T;
-  return T >= kFastFloorT && (double)T * (double)T * (double)(S + 6) >= kFastCross;
+  return T >= kFastFloorT && (double)T * (double)T * (double)(S + 5) >= kFastCross;
 }
 }  // namespace zr
 
 // The automatic choice of evaluator for T probes per sample of a function
 // of Tf terms and S samples.  Measured on GB300 (Tf = T): the matrix-vector
-// evaluator costs about S T Tf 5e-10 ms + 0.15 ms, the transposed tree 0.45
-// to 1.5 ms from T = 2048 to 16384; they cross near T = 8300 (S = 21),
-// 13500 (S = 5) and 15000 (S = 1), which T Tf (S + 8) >= 2e9 follows.
-static constexpr double kFastProbeCross = 2e9;
+// evaluator costs about S T Tf 5e-10 ms + 0.15 ms, the transposed tree 0.36
+// to 1.3 ms from T = 2048 to 16384; they cross near T = 7800 (S = 21),
+// 12500 (S = 5) and 14000 (S = 1), which T Tf (S + 8) >= 1.8e9 follows.
+static constexpr double kFastProbeCross = 1.8e9;
 static constexpr int64_t kFastProbeFloorT = 4096;
 
 namespace zr {
