@@ -180,7 +180,8 @@ typedef struct zr_vsys {
  * (steps, systems, reconstructions, the server):
  *   0  by size: the O(T log^2 T) method for T >= crossover, the O(T^2)
  *      method below it; crossover 0 takes the library's measured rule for a
- *      system of S right-hand sides, T >= 1024 and T^2 (S + 5) >= 8e7
+ *      system of S right-hand sides, T >= 1024 for a system alone in its
+ *      call and, in a call of several systems, also T^2 (S + 5) >= 8e7
  *      (about T >= 1750 for S = 21, 3600 for S = 1); for the probes of a
  *      function of Tf terms, the transposed-tree evaluator when T, Tf >=
  *      4096 and T Tf (S + 8) >= 1.8e9;

@@ -428,20 +428,25 @@ extern "C" void zr_destroy(zr_ctx* ctx) {
 
 extern "C" const char* zr_last_error(const zr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
-// The automatic choice of solve method.  On GB300 the O(T^2) batch costs
-// about 0.2 ms + T^2 (5e-10 S + 8e-9) ms for one system of S right-hand
-// sides, the O(T log^2 T) path 0.26 to 0.57 ms from T = 768 to 6144 nearly
-// independently of S; they cross near T = 1750 (S = 21), 3000 (S = 5) and
-// 3600 (S = 1), which T^2 (S + 5) >= 8e7 follows within 10%.
-static constexpr double kFastCross = 8e7;
+// The automatic choice of solve method.  On GB300, for one system alone,
+// the O(T log^2 T) path is faster than the O(T^2) batch from T = 768 at every
+// S measured (1, 5, 21: 0.18 - 0.19 against 0.22 - 0.24 ms at T = 768, 0.49
+// against 1.02 ms at T = 6144, S = 21); it is taken from T = 1024.  In a
+// batch of several systems the O(T^2) ones share their launches while each
+// fast system runs its own chain of about 45 kernels: there it is taken when
+// T^2 (S + 5) >= 8e7 (about T >= 1750 at S = 21, 3600 at S = 1), the rule
+// under which the serving mix measured best (1.53 - 1.57x the plain form,
+// against 1.46x with the single-system rule).
 static constexpr int64_t kFastFloorT = 1024;
+static constexpr double kFastBatchCross = 8e7;
 
 namespace zr {
-bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S) {
+bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S, int batch_n) {
   if (T < 1 || T > kFastMaxT || ctx->solve_method == 1) return false;
   if (ctx->solve_method == 2) return true;
   if (ctx->fast_min_T > 0) return T >= ctx->fast_min_T;
-  return T >= kFastFloorT && (double)T * (double)T * (double)(S + 5) >= kFastCross;
+  if (T < kFastFloorT) return false;
+  return batch_n <= 1 || (double)T * (double)T * (double)(S + 5) >= kFastBatchCross;
 }
 }  // namespace zr
 
@@ -474,7 +479,7 @@ static double fast_work(double n, int S) {
 }
 double solve_work(const zr_ctx* ctx, int64_t T, int S) {
   if (T <= 0) return 0;
-  return use_fast_solve(ctx, T, S) ? fast_work((double)T, S) : (S + 2.5) * (double)T * (double)T;
+  return use_fast_solve(ctx, T, S, 2) ? fast_work((double)T, S) : (S + 2.5) * (double)T * (double)T;
 }
 double probe_work(const zr_ctx* ctx, int64_t T, int S, int64_t Tf) {
   if (T <= 0 || Tf <= 0) return 0;

@@ -467,7 +467,7 @@ static bool prepare(const zr_ctx* ctx, const BatchItem* items, int n, Prepared& 
   for (int i = 0; i < n; i++) {
     const BatchItem& it = items[i];
     if (it.mode != P.mode) return false;
-    P.fast[i] = use_fast_solve(ctx, it.T, it.solve_S()) ? 1 : 0;
+    P.fast[i] = use_fast_solve(ctx, it.T, it.solve_S(), n) ? 1 : 0;
     if (P.fast[i]) {
       // one k-block: the finish kernels read the numerators and M'(v_j) as a
       // single block's partials

@@ -1416,7 +1416,16 @@ struct FastWs {
   uint32_t *XH = nullptr, *Y = nullptr;    // R kNP T', 2 R kNP T'
   uint64_t *f = nullptr, *rd = nullptr, *g = nullptr, *ps = nullptr, *e = nullptr;
   uint32_t *A = nullptr, *B = nullptr, *Z = nullptr;   // kNP * 2T' each
+  char* rps = nullptr;             // the matrix-vector power sums' scratch (T <= kRingPsMaxT)
 };
+
+// Up to this many unknowns the power sums come from the matrix-vector
+// evaluator (about T^2 Shoup steps, from the nodes alone, beside the tree)
+// rather than from Newton's inverse of rev(M) after it.  Measured on GB300
+// (S = 21, whole solve): 0.16 against 0.24 ms at T = 512, 0.34 against 0.44
+// ms at T = 4096, but 0.62 against 0.58 ms at T = 8192 and 1.56 against 0.92
+// ms at T = 16384, where the evaluator's T^2 powers outgrow the series.
+constexpr int64_t kRingPsMaxT = 6144;
 
 FastWs carve_fast(Carver& cv, int64_t T, int R) {
   FastWs w;
@@ -1439,6 +1448,7 @@ FastWs carve_fast(Carver& cv, int64_t T, int R) {
   w.A = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
   w.B = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
   w.Z = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
+  if (T <= kRingPsMaxT) w.rps = cv.take<char>(ring_power_sums_ws(T));
   return w;
 }
 
@@ -1760,19 +1770,28 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   FastRun F{ctx, C, M, tw, itw, logN, st};
 
   configure_fused();
-  F.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
-  const uint64_t* m = w.coef[Lt];   // M without its leading 1
-
   // The right-hand sides' descent needs only the tree; the power sums' row
-  // needs Newton's inverse first.  With an auxiliary stream the power sums
-  // and their row's descent run there, beside the other rows' descent (each
+  // needs the power sums first.  With an auxiliary stream the power sums and
+  // their row's descent run there, beside the other rows' descent (each
   // branch in its own rows of X and of the scratch), joined at the leaves.
+  // Up to kRingPsMaxT unknowns the power sums come from the nodes directly
+  // and start there beside the tree.
   // (With the context's profiler on, everything runs on st, so that each
   // timed launch has the GPU to itself.)
   const bool fork = aux != nullptr && ev_fork != nullptr && ev_join != nullptr && !ctx->prof.on;
+  const bool ring_ps = w.rps != nullptr;
   cudaStream_t sa = fork ? aux : st;
   FastRun Fa{ctx, C, M, tw, itw, logN, sa};
-  if (fork) {
+  if (ring_ps) {
+    if (fork) {
+      cudaEventRecord(ev_fork, st);
+      cudaStreamWaitEvent(sa, ev_fork, 0);
+    }
+    if ((r = ring_power_sums(ctx, v, T, w.ps, w.rps, ctx->d_status_call, sa))) return r;
+  }
+  F.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
+  const uint64_t* m = w.coef[Lt];   // M without its leading 1
+  if (fork) {                       // the tree (spectra, M) before the auxiliary branch goes on
     cudaEventRecord(ev_fork, st);
     cudaStreamWaitEvent(sa, ev_fork, 0);
   }
@@ -1826,12 +1845,14 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     note_launch();
     descend(0, S, st);
   }
-  // power sums: g = 1 / rev(M) mod z^T by Newton's iteration, ps = rev(M') g;
-  // then their row S
-  launch_k(k_rev_poly, cdivu(T + 1, 256), 256, 0, sa, m, T, M, w.f, w.rd, w.g);
-  note_launch();
-  Fa.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
-  Fa.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
+  // power sums (unless the evaluator gave them above): g = 1 / rev(M) mod z^T
+  // by Newton's iteration, ps = rev(M') g; then their row S
+  if (!ring_ps) {
+    launch_k(k_rev_poly, cdivu(T + 1, 256), 256, 0, sa, m, T, M, w.f, w.rd, w.g);
+    note_launch();
+    Fa.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
+    Fa.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
+  }
   launch_k(k_stage_rhs, cdivu(T, 256), 256, 0, sa, b, ldb, S, (const uint64_t*)w.ps, S, 1, T, Tp, w.X0);
   note_launch();
   descend(S, 1, sa);

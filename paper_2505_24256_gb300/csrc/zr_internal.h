@@ -189,7 +189,8 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
                              int64_t ldb, uint64_t* part, uint64_t* den, char* ws, cudaStream_t st,
                              cudaStream_t aux = nullptr, cudaEvent_t ev_fork = nullptr, cudaEvent_t ev_join = nullptr);
 // whether a system of T unknowns takes the fast path in this context
-bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S);
+// (batch_n: the number of systems in the call; alone, the fast path is taken from a smaller T)
+bool use_fast_solve(const zr_ctx* ctx, int64_t T, int S, int batch_n = 1);
 // grows the transform tables for fast solves of up to T unknowns
 zr_status fast_tables_for(zr_ctx* ctx, int64_t T, cudaStream_t st);
 // scheduling weights (multiply-accumulate equivalents) of a step's solve and
@@ -206,6 +207,11 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
                               int64_t T, uint64_t* out, int64_t ldo, char* ws, cudaStream_t st);
 
 // evaluator (zr_eval.cu)
+// power sums p_k = sum_{j<T} v_j^k, k < T, by the matrix-vector evaluator
+// (ws: ring_power_sums_ws(T) bytes; status: the call's flag word)
+size_t ring_power_sums_ws(int64_t T);
+zr_status ring_power_sums(zr_ctx* ctx, const uint64_t* v, int64_t T, uint64_t* ps, char* ws, uint32_t* status,
+                          cudaStream_t st);
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);
 // (fws, fcap: the grow-only workspace of the fast evaluator; null: the context's)
 zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,
