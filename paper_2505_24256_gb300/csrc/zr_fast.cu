@@ -722,6 +722,114 @@ constexpr int kNewtonSchool = 256;
 constexpr int kNewtonPer = 16;
 __device__ __forceinline__ int ilog2_dev(int x) { return 31 - __clz(x); }   // x a power of two
 
+// The division step of k_newton_cluster's quotient mode: g mod q_me in
+// Gq[0, k), k = n / 2; writes h = rd / f mod z^T (k < T <= n) to ps.  The
+// residues a CTA needs of a remaindered product wait in v across the barrier
+// that frees the buffer they go to.
+__device__ __forceinline__ void newton_cluster_divide(uint32_t* fsm, int me, const uint32_t* peer, int logn,
+                                                      const uint64_t* __restrict__ f, int64_t nf, const uint32_t* Gq,
+                                                      const uint64_t* __restrict__ rd, int64_t T, const NttConsts& C,
+                                                      const Mod& M, const uint2* __restrict__ tw,
+                                                      const uint2* __restrict__ itw, int logN,
+                                                      uint64_t* __restrict__ ps) {
+  const int n = 1 << logn, k = n / 2;
+  const int hi = (int)(T - k);                   // the coefficients the last product gives: 1 .. k
+  const uint32_t q = C.q[me], qi = C.qinv[me];
+  auto prime = [=](int) { return me; };
+  uint32_t s[kNP], sp[kNP];                      // 2^(32 - logn) mod q_j
+#pragma unroll
+  for (int j = 0; j < kNP; j++) {
+    s[j] = (uint32_t)(((uint64_t)1 << (32 - logn)) % C.q[j]);
+    sp[j] = (uint32_t)(((uint64_t)s[j] << 32) / C.q[j]);
+  }
+  uint32_t v[kNewtonPer];
+  // g's region (at 2n) into the transform layout, B := rd mod z^k
+#pragma unroll
+  for (int r = 0; r < kNewtonPer; r++) {
+    const int t = threadIdx.x + r * (int)blockDim.x;
+    v[r] = t < k ? Gq[t] : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kNewtonPer; r++) {
+    const int t = threadIdx.x + r * (int)blockDim.x;
+    if (t < n) fsm[sw(2 * n + t)] = v[r];
+  }
+  for (int t = threadIdx.x; t < n; t += blockDim.x) fsm[sw(n + t)] = t < k ? residue64(rd[t], C, me) : 0u;
+  __syncthreads();
+  smem_stages<false>(fsm, n, 2 * n, logn, 0, 0u, tw, logN, C, prime);   // B and g
+  for (int x = threadIdx.x; x < n; x += blockDim.x)
+    fsm[sw(n + x)] = mont32(sub_if(fsm[sw(n + x)], 2 * q), sub_if(fsm[sw(2 * n + x)], 2 * q), q, qi);
+  __syncthreads();
+  smem_stages<true>(fsm, n, n, logn, 0, 0u, itw, logN, C, prime);
+  cluster_sync();                                // every CTA's B holds rd g mod its prime
+  // q0 = h mod z^k: every CTA remainders all k coefficients, CTA 0 writes them
+#pragma unroll
+  for (int r = 0; r < kNewtonPer; r++) {
+    const int t = threadIdx.x + r * (int)blockDim.x;
+    uint32_t val = 0;
+    if (t < k) {
+      uint32_t res[kNP];
+#pragma unroll
+      for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(n + t)), s[j], sp[j], C.q[j]);
+      const uint64_t x = crt_to_p(res, C, M);
+      if (me == 0) ps[t] = x;
+      val = residue64(x, C, me);
+    }
+    v[r] = val;
+  }
+  cluster_sync();                                // B is no longer read
+  // A := f mod z^T, B := q0; their product's coefficients k .. T-1
+  for (int t = threadIdx.x; t < n; t += blockDim.x) fsm[sw(t)] = (t < T && t < nf) ? residue64(f[t], C, me) : 0u;
+#pragma unroll
+  for (int r = 0; r < kNewtonPer; r++) {
+    const int t = threadIdx.x + r * (int)blockDim.x;
+    if (t < n) fsm[sw(n + t)] = v[r];
+  }
+  __syncthreads();
+  smem_stages<false>(fsm, 0, 2 * n, logn, 0, 0u, tw, logN, C, prime);   // A and B
+  for (int x = threadIdx.x; x < n; x += blockDim.x)
+    fsm[sw(x)] = mont32(sub_if(fsm[sw(x)], 2 * q), sub_if(fsm[sw(n + x)], 2 * q), q, qi);
+  __syncthreads();
+  smem_stages<true>(fsm, 0, n, logn, 0, 0u, itw, logN, C, prime);
+  cluster_sync();                                // every CTA's A holds f q0 mod its prime
+  // r_t = rd_{k+t} - (f q0)_{k+t}, t < T - k
+#pragma unroll
+  for (int r = 0; r < kNewtonPer; r++) {
+    const int t = threadIdx.x + r * (int)blockDim.x;
+    uint32_t val = 0;
+    if (t < hi) {
+      uint32_t res[kNP];
+#pragma unroll
+      for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(k + t)), s[j], sp[j], C.q[j]);
+      const uint64_t fq = crt_to_p(res, C, M), a = rd[k + t];
+      val = residue64(a >= fq ? a - fq : a + (M.p - fq), C, me);
+    }
+    v[r] = val;
+  }
+  cluster_sync();                                // A is no longer read
+#pragma unroll
+  for (int r = 0; r < kNewtonPer; r++) {
+    const int t = threadIdx.x + r * (int)blockDim.x;
+    if (t < n) fsm[sw(t)] = v[r];
+  }
+  __syncthreads();
+  smem_stages<false>(fsm, 0, n, logn, 0, 0u, tw, logN, C, prime);
+  for (int x = threadIdx.x; x < n; x += blockDim.x)
+    fsm[sw(x)] = mont32(sub_if(fsm[sw(x)], 2 * q), sub_if(fsm[sw(2 * n + x)], 2 * q), q, qi);
+  __syncthreads();
+  smem_stages<true>(fsm, 0, n, logn, 0, 0u, itw, logN, C, prime);
+  cluster_sync();                                // every CTA's A holds g r mod its prime
+  // h_{k+t} = (g r)_t: each CTA remainders and writes a fifth
+  const int chunk = (hi + kNP - 1) / kNP, t0 = me * chunk, t1 = t0 + chunk < hi ? t0 + chunk : hi;
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    uint32_t res[kNP];
+#pragma unroll
+    for (int j = 0; j < kNP; j++) res[j] = shoup32(ld_cluster(peer[j] + 4u * sw(t)), s[j], sp[j], C.q[j]);
+    ps[k + t] = crt_to_p(res, C, M);
+  }
+}
+
 // k_newton_fused spread over a cluster of kNP CTAs, CTA i holding prime i's
 // transforms in its shared memory: A (f, then f g, then e_hi and g e_hi: the
 // second product takes A's place once every CTA has read it), B (g's
@@ -733,10 +841,24 @@ __device__ __forceinline__ int ilog2_dev(int x) { return 31 - __clz(x); }   // x
 // its remote reads, and another those reads from the buffer's next writes
 // (the remaindered values wait in registers meanwhile); the last one keeps
 // every CTA resident until the others are done reading it.
+//
+// With ps non-null the kernel returns the quotient h = rd / f mod z^T
+// instead (rd: T coefficients, 2^(logK-1) < T <= 2^logK, T > kNewtonSchool):
+// Newton's iteration stops at g = 1/f mod z^k, k = 2^(logK-1), and one
+// division step in the manner of Karp and Markstein finishes with three
+// products of n = 2k points: q0 = rd g mod z^k (= h mod z^k); r = (rd - f q0)
+// div z^k mod z^(T-k); h_{k+t} = (g r)_t for t < T - k.  (f h = rd mod z^T
+// and f q0 = rd mod z^k give f (h - q0) / z^k = r, so (h - q0) / z^k = g r
+// mod z^(T-k), T - k <= k.)  The cyclic products are exact where read: rd g
+// and g r have fewer than n coefficients, and f q0 (f mod z^T) wraps only
+// onto coefficients below T + k - n <= k.  Shared memory: A at 0, B at n
+// and g's region at 2n, each of n words.
 __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64_t* __restrict__ f, int64_t nf,
                                                                   int logK, NttConsts C, Mod M,
                                                                   const uint2* __restrict__ tw, int logN,
-                                                                  uint64_t* __restrict__ g) {
+                                                                  uint64_t* __restrict__ g,
+                                                                  const uint64_t* __restrict__ rd, int64_t T,
+                                                                  uint64_t* __restrict__ ps) {
   pdl_enter();
   extern __shared__ uint32_t fsm[];              // A (= C) [n] at 0, B [n] at n (logical); then g mod q
   const int me = cluster_rank();
@@ -748,10 +870,12 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
 #pragma unroll
   for (int j = 0; j < kNP; j++) peer[j] = cluster_addr(fsm, j);
   auto prime = [=](int) { return me; };
+  const int logG = ps ? logK - 1 : logK;         // Newton's iteration runs to precision 2^logG
+  const int KG = 1 << logG;
   // the first steps, to precision K1, by schoolbook products in 64-bit
   // residues, every CTA computing the same g (no transforms, no exchange):
   // e_t = (f g)_{k+t} = sum_{i<k} f_{k+t-i} g_i, then g_{k+t} = -sum_{i<=t} g_i e_{t-i}
-  const int K1 = K < kNewtonSchool ? K : kNewtonSchool;
+  const int K1 = KG < kNewtonSchool ? KG : kNewtonSchool;
   uint64_t* g64 = reinterpret_cast<uint64_t*>(fsm);            // K1 words
   uint64_t* e64 = g64 + K1;                                     // K1 / 2 words
   if (threadIdx.x == 0) g64[0] = 1;
@@ -785,7 +909,7 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
     if (me == 0) g[t] = g64[t];
   }
   __syncthreads();
-  for (int lk = ilog2_dev(K1); lk < logK; lk++) {
+  for (int lk = ilog2_dev(K1); lk < logG; lk++) {
     const int k = 1 << lk, logn = lk + 1, n = 2 * k;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       fsm[sw(t)] = t < nf ? residue64(f[t], C, me) : 0u;
@@ -842,6 +966,7 @@ __global__ void __launch_bounds__(kNewtonThreadsF) k_newton_cluster(const uint64
     }
     cluster_sync();                              // C is no longer read: the next step may write A
   }
+  if (ps) newton_cluster_divide(fsm, me, peer, logK, f, nf, Gq, rd, T, C, M, tw, itw, logN, ps);
   cluster_sync();
 }
 
@@ -1474,6 +1599,9 @@ struct FastRun {
   // kNP 2^ceil(log2(2 prec)) words each
   void inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, uint64_t* e, uint32_t* A, uint32_t* B,
                uint32_t* Z);
+  // h = rd / f mod z^T (rd: T coefficients) in one cluster, when T fits it
+  // (kNewtonSchool < T <= 2^kNewtonClusterLog); false: nothing was launched
+  bool quotient(const uint64_t* f, int64_t nf, const uint64_t* rd, int64_t T, uint64_t* g, uint64_t* h);
   // out[t] = +-(a * b mod (z^N - 1))[lo + t], t < cnt; N = 2^logn
   void cyc(const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb, int logn, int64_t lo, int64_t cnt, bool neg,
            uint32_t* A, uint32_t* B, uint32_t* Z, uint64_t* out) {
@@ -1610,13 +1738,23 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
   }
 }
 
+bool FastRun::quotient(const uint64_t* f, int64_t nf, const uint64_t* rd, int64_t T, uint64_t* g, uint64_t* h) {
+  const int logK = ilog2(T);
+  if (T <= kNewtonSchool || logK > kNewtonClusterLog || !newton_cluster_ok()) return false;
+  if (launch_cluster(k_newton_cluster, 1, kNewtonThreadsF, newton_cluster_smem(logK), st, f, nf, logK, C, M, tw, logN,
+                     g, rd, T, h) == cudaSuccess)
+    return true;
+  (void)cudaGetLastError();
+  return false;
+}
+
 void FastRun::inverse(const uint64_t* f, int64_t nf, int64_t prec, uint64_t* g, uint64_t* e, uint32_t* A,
                       uint32_t* B, uint32_t* Z) {
   int logK0 = std::min(ilog2(prec), kNewtonClusterLog);
   bool done = false;
   if (newton_cluster_ok()) {
     done = launch_cluster(k_newton_cluster, 1, kNewtonThreadsF, newton_cluster_smem(logK0), st, f, nf, logK0, C, M,
-                          tw, logN, g) == cudaSuccess;
+                          tw, logN, g, (const uint64_t*)nullptr, (int64_t)0, (uint64_t*)nullptr) == cudaSuccess;
     if (!done) (void)cudaGetLastError();
   }
   if (!done) {
@@ -1845,13 +1983,17 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     note_launch();
     descend(0, S, st);
   }
-  // power sums (unless the evaluator gave them above): g = 1 / rev(M) mod z^T
-  // by Newton's iteration, ps = rev(M') g; then their row S
+  // power sums (unless the evaluator gave them above): ps = rev(M') / rev(M)
+  // mod z^T, up to 2^14 in one cluster (Newton's iteration to half the
+  // precision, then a division step), else g = 1 / rev(M) by Newton's
+  // iteration and ps = rev(M') g; then their row S
   if (!ring_ps) {
     launch_k(k_rev_poly, cdivu(T + 1, 256), 256, 0, sa, m, T, M, w.f, w.rd, w.g);
     note_launch();
-    Fa.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
-    Fa.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
+    if (!Fa.quotient(w.f, T + 1, w.rd, T, w.g, w.ps)) {
+      Fa.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
+      Fa.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
+    }
   }
   launch_k(k_stage_rhs, cdivu(T, 256), 256, 0, sa, b, ldb, S, (const uint64_t*)w.ps, S, 1, T, Tp, w.X0);
   note_launch();

@@ -1,11 +1,14 @@
 """The O(T log^2 T) transposed Vandermonde solve (subproduct tree, scaled
-remainder tree, power sums by Newton's iteration) against the oracle.
+remainder tree, power sums) against the oracle.
 
 The solution is unique, so the fast path must give the oracle's values bit
 for bit: element by element for T up to 2^14 + 5 (every transform size from
 2^8 to 2^16, the column passes of transforms above 2^13, ragged last blocks,
-both offsets), through full Zippel steps at T = 10^4 and T = 2^20 against
-generator truth, in batches mixing both methods, and in reconstructions.
+both offsets, each way of computing the power sums: the matrix-vector
+evaluator up to 6144, the cluster's Newton iteration and division step from
+6145 to 2^14 including T = 2^13 + 1 and 2^14, Newton's inverse and a product
+above), through full Zippel steps at T = 10^4 and T = 2^20 against generator
+truth, in batches mixing both methods, and in reconstructions.
 """
 import random
 
@@ -45,7 +48,8 @@ def solve(ctx, v, b, offset, method):
 
 
 @pytest.mark.parametrize("T,S,offset", [(1, 1, 0), (2, 3, 1), (3, 2, 0), (127, 2, 0), (128, 3, 1), (129, 1, 0),
-                                        (1000, 5, 0), (4097, 3, 1), (9000, 2, 0), (16389, 2, 1)])
+                                        (1000, 5, 0), (4097, 3, 1), (6144, 1, 0), (6145, 2, 1), (8193, 1, 0),
+                                        (9000, 2, 0), (16384, 2, 1), (16389, 2, 1)])
 def test_fast_solve_matches_oracle(ctx, orc, T, S, offset):
     rnd = random.Random(T * 7 + S)
     v = rand_nodes(rnd, T, P63)
