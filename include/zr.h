@@ -192,8 +192,9 @@ typedef struct zr_vsys {
  * through a subproduct tree: products of polynomials modulo p by
  * number-theoretic transforms over five 30-bit primes and the Chinese
  * remainder theorem, and a descent of the tree with middle products (a scaled
- * remainder tree), with M'(v_j) from the power sums of the nodes (a
- * power-series inverse by Newton's iteration).  It handles 1 <= T <= 2^21;
+ * remainder tree), with M'(v_j) from the power sums of the nodes (summed
+ * directly, T^2 products on every SM beside the tree, up to T = 12288;
+ * above, rev(M') / rev(M) by Newton's iteration).  It handles 1 <= T <= 2^21;
  * larger systems always take the O(T^2) method.  Results are identical.
  * The paper's method is the O(T^2) one; this is a faster route to the same
  * values.  Errors: ZR_ERR_INVALID_ARG for a method outside 0..2 or a negative

@@ -709,71 +709,6 @@ zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y
   return cuda_err(ctx, cudaGetLastError(), "zr_zippel_probes");
 }
 
-// ---- power sums by the matrix-vector evaluator ---------------------------------------
-//
-// p_k = sum_{j < T} v_j^k for k < T is the evaluator's product with one
-// sample of unit weights over the T "groups" u_j = v_j: the ring kernel's
-// producer runs the powers, the consumers add them.  About T^2 Shoup steps,
-// and it needs the nodes only (no tree, no series inverse).
-
-namespace {
-struct PsWs {
-  uint64_t *UP, *UPq, *Uq, *Wr, *partial;
-  int64_t* Gdev;
-};
-PsWs carve_ps(Carver& cv, int64_t T) {
-  PsWs w;
-  const RingLayout L = ring_layout(1, T);
-  w.UP = cv.take<uint64_t>((size_t)32 * T);
-  w.UPq = cv.take<uint64_t>((size_t)32 * T);
-  w.Uq = cv.take<uint64_t>(T);
-  w.Wr = cv.take<uint64_t>((size_t)L.bw[0] * T);
-  w.partial = cv.take<uint64_t>((size_t)32 * T);    // at most 32 group splits
-  w.Gdev = cv.take<int64_t>(1);
-  return w;
-}
-
-// the ring's tables for u = v and unit weights in the one-sample layout
-__global__ void k_ps_prepare(const uint64_t* __restrict__ v, int64_t T, int bw, Mod M, uint64_t* __restrict__ Wr,
-                             uint64_t* __restrict__ UP, uint64_t* __restrict__ UPq, uint64_t* __restrict__ Uq,
-                             int64_t* __restrict__ Gdev) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx == 0) *Gdev = T;
-  if (idx >= T) return;
-  uint64_t x = v[idx];
-  Uq[idx] = shoup_pre(x, M);
-  for (int e = 0; e < 32; e++) {
-    UP[e * T + idx] = x;
-    UPq[e * T + idx] = shoup_pre(x, M);
-    x = mul_mod(x, x, M);
-  }
-  for (int j = 0; j < bw; j++) Wr[idx * bw + j] = j == 0 ? 1 : 0;
-}
-}  // namespace
-
-size_t ring_power_sums_ws(int64_t T) {
-  Carver cv(nullptr);
-  carve_ps(cv, T > 0 ? T : 1);
-  return cv.off + 256;
-}
-
-zr_status ring_power_sums(zr_ctx* ctx, const uint64_t* v, int64_t T, uint64_t* ps, char* ws, uint32_t* status,
-                          cudaStream_t st) {
-  if (T < 1) return ZR_OK;
-  Carver cv(ws);
-  const PsWs w = carve_ps(cv, T);
-  const RingLayout L = ring_layout(1, T);
-  const int gsplit = std::min(eval_gsplit(ctx, T, 1, T), 32);
-  k_ps_prepare<<<cdiv(T, 256), 256, 0, st>>>(v, T, L.bw[0], ctx->M, w.Wr, w.UP, w.UPq, w.Uq, w.Gdev);
-  note_launch();
-  launch_ring(T, 1, 0, w.Gdev, T, gsplit, w.UP, w.UPq, v, w.Uq, w.Wr, L, ctx->M, ps, T, w.partial, status, st);
-  if (gsplit > 1) {
-    k_eval_combine<<<cdiv(T, 256), 256, 0, st>>>(T, 1, gsplit, w.partial, ctx->M, ps, T);
-    note_launch();
-  }
-  return cuda_err(ctx, cudaGetLastError(), "power sums");
-}
-
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T) {
   Carver cv(nullptr);
   carve_eval(cv, f->T, f->nv, k, S, T, eval_gsplit(ctx, T, S, f->T), use_fast_probes(ctx, T, f->T, S));

@@ -1191,6 +1191,122 @@ __global__ void k_stage_rhs(const uint64_t* __restrict__ b, int64_t ldb, int S, 
   X0[(int64_t)r * Tp + k] = r < S ? b[(int64_t)r * ldb + k] : ps[k];
 }
 
+// ---- power sums directly: p_k = sum_j v_j^k ------------------------------------------
+//
+// T^2 Shoup steps over every SM, from the nodes alone, so that they run beside
+// the tree and the power sums' row joins the right-hand sides' descent.  Block
+// (kb, jb) takes the exponents [kb kr, (kb + 1) kr) and the nodes
+// [jb kPsNodes, (jb + 1) kPsNodes); each thread carries kPsJ powers v_j^k
+// (lazily in [0, 2p)) along the exponents, one Shoup product per step, and
+// adds them over a window of kPsWin exponents into 128-bit sums; the block
+// then adds its threads' windows through shared memory (one warp per
+// exponent: 8 partial sums a lane, then 5 shuffles) and reduces each sum
+// once, into part[jb T + k].  The starting powers v_j^(kb kr) come from
+// k_ps_start.
+constexpr int kPsThreads = 256;
+constexpr int kPsJ = 8;
+constexpr int kPsWin = 8;                     // kPsThreads = kPsWin warps
+constexpr int kPsNodes = kPsThreads * kPsJ;
+
+// start[kb T + j] = v_j^(kb kr) (lazily, in [0, 2p)), kb < nkb
+__global__ void k_ps_start(const uint64_t* __restrict__ v, int64_t T, int kr, int nkb, Mod M,
+                           uint64_t* __restrict__ start) {
+  pdl_enter();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= T) return;
+  const uint64_t w = pow_mod(v[j], (uint64_t)kr, M), wq = shoup_pre(w, M);
+  uint64_t x = 1;
+  for (int kb = 0; kb < nkb; kb++) {
+    start[(int64_t)kb * T + j] = x;
+    x = shoup_lazy(x, w, wq, M);
+  }
+}
+
+__global__ void __launch_bounds__(kPsThreads) k_power_sums(const uint64_t* __restrict__ v,
+                                                           const uint64_t* __restrict__ vp, int64_t T, int kr,
+                                                           const uint64_t* __restrict__ start, Mod M,
+                                                           uint64_t* __restrict__ part) {
+  pdl_enter();
+  __shared__ uint64_t red_lo[kPsThreads][kPsWin + 1];
+  __shared__ uint32_t red_hi[kPsThreads][kPsWin + 1];
+  const int64_t k0 = (int64_t)blockIdx.x * kr;
+  const int64_t k1 = k0 + kr < T ? k0 + kr : T;
+  const int64_t j0 = (int64_t)blockIdx.y * kPsNodes;
+  uint64_t x[kPsJ], w[kPsJ], wq[kPsJ];         // nodes past T carry 0
+#pragma unroll
+  for (int m = 0; m < kPsJ; m++) {
+    const int64_t j = j0 + m * kPsThreads + threadIdx.x;
+    const bool in = j < T;
+    w[m] = in ? v[j] : 0;
+    wq[m] = in ? vp[j] : 0;
+    x[m] = in ? start[(int64_t)blockIdx.x * T + j] : 0;
+  }
+  const int kk = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t kw = k0; kw < k1; kw += kPsWin) {
+    uint64_t lo[kPsWin];
+    uint32_t hi[kPsWin];
+#pragma unroll
+    for (int i = 0; i < kPsWin; i++) lo[i] = 0, hi[i] = 0;
+#pragma unroll
+    for (int m = 0; m < kPsJ; m++) {
+#pragma unroll
+      for (int i = 0; i < kPsWin; i++) {
+        lo[i] += x[m];
+        hi[i] += lo[i] < x[m];
+        x[m] = shoup_lazy(x[m], w[m], wq[m], M);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kPsWin; i++) red_lo[threadIdx.x][i] = lo[i], red_hi[threadIdx.x][i] = hi[i];
+    __syncthreads();
+    uint64_t sl = 0;
+    uint32_t sh = 0;
+#pragma unroll
+    for (int i = 0; i < kPsThreads / 32; i++) {
+      const uint64_t a = red_lo[lane + 32 * i][kk];
+      sl += a;
+      sh += red_hi[lane + 32 * i][kk] + (sl < a);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const uint64_t a = __shfl_xor_sync(0xffffffffu, sl, o);
+      const uint32_t b = __shfl_xor_sync(0xffffffffu, sh, o);
+      sl += a;
+      sh += b + (sl < a);
+    }
+    if (lane == 0 && kw + kk < k1) part[(int64_t)blockIdx.y * T + kw + kk] = reduce128(sh, sl, M);
+    __syncthreads();
+  }
+}
+
+// ps[k] = sum over the nb node blocks of part[jb T + k]
+__global__ void k_power_sums_add(const uint64_t* __restrict__ part, int64_t T, int nb, Mod M,
+                                 uint64_t* __restrict__ ps) {
+  pdl_enter();
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= T) return;
+  uint64_t sum = 0;
+  for (int jb = 0; jb < nb; jb++) sum = add_mod(sum, part[(int64_t)jb * T + k], M);
+  ps[k] = sum;
+}
+
+// The launch shape of k_power_sums: nb node blocks, nkb exponent blocks of kr
+// (a multiple of kPsWin) exponents, about two blocks per SM in all.
+struct PsShape {
+  int nb, nkb, kr;
+};
+PsShape ps_shape(int64_t T, int sms) {
+  PsShape s;
+  s.nb = (int)((T + kPsNodes - 1) / kPsNodes);
+  int want = 2 * sms / s.nb;
+  if (want < 1) want = 1;
+  int64_t kr = (T + want - 1) / want;
+  kr = (kr + kPsWin - 1) / kPsWin * kPsWin;
+  s.kr = (int)kr;
+  s.nkb = (int)((T + kr - 1) / kr);
+  return s;
+}
+
 // ---- the transposed problem: weighted power sums (the probe evaluator) ----------------
 //
 // out[s][i] = sum_g w_{g,s} u_g^i, i < T, is the expansion of
@@ -1541,16 +1657,20 @@ struct FastWs {
   uint32_t *XH = nullptr, *Y = nullptr;    // R kNP T', 2 R kNP T'
   uint64_t *f = nullptr, *rd = nullptr, *g = nullptr, *ps = nullptr, *e = nullptr;
   uint32_t *A = nullptr, *B = nullptr, *Z = nullptr;   // kNP * 2T' each
-  char* rps = nullptr;             // the matrix-vector power sums' scratch (T <= kRingPsMaxT)
+  uint64_t* psp = nullptr;         // k_power_sums' partial sums, T per node block (T <= kDirectPsMaxT)
+  uint64_t* pss = nullptr;         // its starting powers, T per exponent block
 };
 
-// Up to this many unknowns the power sums come from the matrix-vector
-// evaluator (about T^2 Shoup steps, from the nodes alone, beside the tree)
-// rather than from Newton's inverse of rev(M) after it.  Measured on GB300
-// (S = 21, whole solve): 0.16 against 0.24 ms at T = 512, 0.34 against 0.44
-// ms at T = 4096, but 0.62 against 0.58 ms at T = 8192 and 1.56 against 0.92
-// ms at T = 16384, where the evaluator's T^2 powers outgrow the series.
-constexpr int64_t kRingPsMaxT = 6144;
+// Up to this many unknowns the power sums come from k_power_sums (T^2 Shoup
+// steps from the nodes alone, beside the tree) rather than from rev(M') /
+// rev(M) after the tree.  Measured on GB300 (S = 21, whole solve): 0.31
+// against 0.34 ms at T = 4096, 0.48 against 0.54 ms at T = 8192, 0.67
+// against 0.81 ms at T = 10^4, but 0.95 against 0.86 ms at T = 16384, where
+// the T^2 steps (0.33 ms alone) outgrow the cluster's Newton iteration.
+constexpr int64_t kDirectPsMaxT = 12288;
+// k_power_sums is shaped for at most this many SMs (its starting powers'
+// workspace grows with the count)
+constexpr int kPsSmsMax = 256;
 
 FastWs carve_fast(Carver& cv, int64_t T, int R) {
   FastWs w;
@@ -1573,7 +1693,8 @@ FastWs carve_fast(Carver& cv, int64_t T, int R) {
   w.A = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
   w.B = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
   w.Z = cv.take<uint32_t>((size_t)kNP * 2 * Tp);
-  if (T <= kRingPsMaxT) w.rps = cv.take<char>(ring_power_sums_ws(T));
+  if (T <= kDirectPsMaxT) w.psp = cv.take<uint64_t>((size_t)cdivu(T, kPsNodes) * T);
+  if (T <= kDirectPsMaxT) w.pss = cv.take<uint64_t>((size_t)T * ps_shape(T, kPsSmsMax).nkb);
   return w;
 }
 
@@ -1909,30 +2030,32 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
 
   configure_fused();
   // The right-hand sides' descent needs only the tree; the power sums' row
-  // needs the power sums first.  With an auxiliary stream the power sums and
-  // their row's descent run there, beside the other rows' descent (each
-  // branch in its own rows of X and of the scratch), joined at the leaves.
-  // Up to kRingPsMaxT unknowns the power sums come from the nodes directly
-  // and start there beside the tree.
-  // (With the context's profiler on, everything runs on st, so that each
-  // timed launch has the GPU to itself.)
+  // needs the power sums.  Up to kDirectPsMaxT unknowns they come from the
+  // nodes alone: with an auxiliary stream k_power_sums runs there beside the
+  // tree, and one descent takes all S + 1 rows.  Above, they need the tree's
+  // root: with an auxiliary stream they and their row's descent run there,
+  // beside the other rows' descent (each branch in its own rows of X and of
+  // the scratch), joined at the leaves.  (With the context's profiler on,
+  // everything runs on st, so that each timed launch has the GPU to itself.)
   const bool fork = aux != nullptr && ev_fork != nullptr && ev_join != nullptr && !ctx->prof.on;
-  const bool ring_ps = w.rps != nullptr;
+  const bool direct_ps = w.psp != nullptr;
   cudaStream_t sa = fork ? aux : st;
   FastRun Fa{ctx, C, M, tw, itw, logN, sa};
-  if (ring_ps) {
+  if (direct_ps) {
     if (fork) {
       cudaEventRecord(ev_fork, st);
       cudaStreamWaitEvent(sa, ev_fork, 0);
     }
-    if ((r = ring_power_sums(ctx, v, T, w.ps, w.rps, ctx->d_status_call, sa))) return r;
+    const PsShape ps = ps_shape(T, ctx->sms < kPsSmsMax ? ctx->sms : kPsSmsMax);
+    launch_k(k_ps_start, cdivu(T, 256), 256, 0, sa, v, T, ps.kr, ps.nkb, M, w.pss);
+    launch_k(k_power_sums, dim3((unsigned)ps.nkb, (unsigned)ps.nb), kPsThreads, 0, sa, v, vp, T, ps.kr,
+             (const uint64_t*)w.pss, M, w.psp);
+    launch_k(k_power_sums_add, cdivu(T, 256), 256, 0, sa, (const uint64_t*)w.psp, T, ps.nb, M, w.ps);
+    note_launches(3);
+    if (fork) cudaEventRecord(ev_join, sa);
   }
   F.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
   const uint64_t* m = w.coef[Lt];   // M without its leading 1
-  if (fork) {                       // the tree (spectra, M) before the auxiliary branch goes on
-    cudaEventRecord(ev_fork, st);
-    cudaStreamWaitEvent(sa, ev_fork, 0);
-  }
   // descent from the root (node size T') to the leaf blocks of nr rows from
   // row r0: every branch swaps X0 and X1 once per level
   auto descend = [&](int r0, int nr, cudaStream_t s) {
@@ -1976,31 +2099,41 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
       std::swap(X, Xn);
     }
   };
-  // the right-hand sides (rows 0 .. S-1) on the call's stream
-  if (S > 0) {
-    launch_k(k_stage_rhs, cdivu((int64_t)S * T, 256), 256, 0, st, b, ldb, S, (const uint64_t*)nullptr, 0, S, T, Tp,
+  if (direct_ps) {
+    // all R rows in one descent on the call's stream, once the power sums are in
+    if (fork) cudaStreamWaitEvent(st, ev_join, 0);
+    launch_k(k_stage_rhs, cdivu((int64_t)R * T, 256), 256, 0, st, b, ldb, S, (const uint64_t*)w.ps, 0, R, T, Tp,
              w.X0);
     note_launch();
-    descend(0, S, st);
-  }
-  // power sums (unless the evaluator gave them above): ps = rev(M') / rev(M)
-  // mod z^T, up to 2^14 in one cluster (Newton's iteration to half the
-  // precision, then a division step), else g = 1 / rev(M) by Newton's
-  // iteration and ps = rev(M') g; then their row S
-  if (!ring_ps) {
+    descend(0, R, st);
+  } else {
+    if (fork) {                     // the tree (spectra, M) before the auxiliary branch goes on
+      cudaEventRecord(ev_fork, st);
+      cudaStreamWaitEvent(sa, ev_fork, 0);
+    }
+    // the right-hand sides (rows 0 .. S-1) on the call's stream
+    if (S > 0) {
+      launch_k(k_stage_rhs, cdivu((int64_t)S * T, 256), 256, 0, st, b, ldb, S, (const uint64_t*)nullptr, 0, S, T,
+               Tp, w.X0);
+      note_launch();
+      descend(0, S, st);
+    }
+    // power sums: ps = rev(M') / rev(M) mod z^T, up to 2^14 in one cluster
+    // (Newton's iteration to half the precision, then a division step), else
+    // g = 1 / rev(M) by Newton's iteration and ps = rev(M') g; then their row S
     launch_k(k_rev_poly, cdivu(T + 1, 256), 256, 0, sa, m, T, M, w.f, w.rd, w.g);
     note_launch();
     if (!Fa.quotient(w.f, T + 1, w.rd, T, w.g, w.ps)) {
       Fa.inverse(w.f, T + 1, T, w.g, w.e, w.A, w.B, w.Z);
       Fa.cyc(w.rd, T, w.g, T, logT + 1, 0, T, false, w.A, w.B, w.Z, w.ps);
     }
-  }
-  launch_k(k_stage_rhs, cdivu(T, 256), 256, 0, sa, b, ldb, S, (const uint64_t*)w.ps, S, 1, T, Tp, w.X0);
-  note_launch();
-  descend(S, 1, sa);
-  if (fork) {
-    cudaEventRecord(ev_join, sa);
-    cudaStreamWaitEvent(st, ev_join, 0);
+    launch_k(k_stage_rhs, cdivu(T, 256), 256, 0, sa, b, ldb, S, (const uint64_t*)w.ps, S, 1, T, Tp, w.X0);
+    note_launch();
+    descend(S, 1, sa);
+    if (fork) {
+      cudaEventRecord(ev_join, sa);
+      cudaStreamWaitEvent(st, ev_join, 0);
+    }
   }
   uint64_t* X = (Lt & 1) ? w.X1 : w.X0;     // where Lt swaps leave the rows
   // leaves

@@ -207,11 +207,6 @@ zr_status fast_probes_enqueue(zr_ctx* ctx, int64_t G, const uint64_t* U, const u
                               int64_t T, uint64_t* out, int64_t ldo, char* ws, cudaStream_t st);
 
 // evaluator (zr_eval.cu)
-// power sums p_k = sum_{j<T} v_j^k, k < T, by the matrix-vector evaluator
-// (ws: ring_power_sums_ws(T) bytes; status: the call's flag word)
-size_t ring_power_sums_ws(int64_t T);
-zr_status ring_power_sums(zr_ctx* ctx, const uint64_t* v, int64_t T, uint64_t* ps, char* ws, uint32_t* status,
-                          cudaStream_t st);
 size_t probes_ws_need(const zr_ctx* ctx, const zr_poly* f, int k, int S, int64_t T);
 // (fws, fcap: the grow-only workspace of the fast evaluator; null: the context's)
 zr_status probes_enqueue(zr_ctx* ctx, const zr_poly* f, int k, const uint64_t* y, int S, const uint64_t* samples,

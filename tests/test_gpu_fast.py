@@ -4,11 +4,11 @@ remainder tree, power sums) against the oracle.
 The solution is unique, so the fast path must give the oracle's values bit
 for bit: element by element for T up to 2^14 + 5 (every transform size from
 2^8 to 2^16, the column passes of transforms above 2^13, ragged last blocks,
-both offsets, each way of computing the power sums: the matrix-vector
-evaluator up to 6144, the cluster's Newton iteration and division step from
-6145 to 2^14 including T = 2^13 + 1 and 2^14, Newton's inverse and a product
-above), through full Zippel steps at T = 10^4 and T = 2^20 against generator
-truth, in batches mixing both methods, and in reconstructions.
+both offsets, each way of computing the power sums: the direct T^2 kernel
+up to 12288 including T = 2^13 + 1, the cluster's Newton iteration and
+division step from 12289 to 2^14, Newton's inverse and a product above),
+through full Zippel steps at T = 10^4 and T = 2^20 against generator truth,
+in batches mixing both methods, and in reconstructions.
 """
 import random
 
@@ -48,7 +48,7 @@ def solve(ctx, v, b, offset, method):
 
 
 @pytest.mark.parametrize("T,S,offset", [(1, 1, 0), (2, 3, 1), (3, 2, 0), (127, 2, 0), (128, 3, 1), (129, 1, 0),
-                                        (1000, 5, 0), (4097, 3, 1), (6144, 1, 0), (6145, 2, 1), (8193, 1, 0),
+                                        (1000, 5, 0), (4097, 3, 1), (8193, 1, 0), (12288, 1, 0), (12289, 2, 1),
                                         (9000, 2, 0), (16384, 2, 1), (16389, 2, 1)])
 def test_fast_solve_matches_oracle(ctx, orc, T, S, offset):
     rnd = random.Random(T * 7 + S)
@@ -256,5 +256,5 @@ def test_profiler_counts_the_descent_butterflies(ctx):
     finally:
         ctx.solve_method(0)
     want = sum(-(-T // (1 << l)) * (S + 1) * 5 * 3 * (1 << (l - 1)) * l for l in (8, 9, 10))
-    assert launches == 6                   # three levels, the right-hand sides and the power sums apart
+    assert launches == 3                   # three levels, all S + 1 rows in one descent (direct power sums)
     assert work == want
