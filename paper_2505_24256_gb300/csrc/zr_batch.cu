@@ -443,9 +443,13 @@ struct Prepared {
 constexpr int kFastStreams = 4;
 
 // The auxiliary stream and events of fast-solve slot j (created on first
-// use); false when they cannot be had (the solve then runs on one stream).
+// use, the stream with the device's greatest priority: it carries the
+// solve's critical branch); false when they cannot be had (the solve then
+// runs on one stream).
 static bool fast_aux(zr_ctx* ctx, int j) {
-  if (!ctx->faux[j] && cudaStreamCreateWithFlags(&ctx->faux[j], cudaStreamNonBlocking) != cudaSuccess) {
+  int least = 0, greatest = 0;
+  if (!ctx->faux[j] && cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) greatest = 0;
+  if (!ctx->faux[j] && cudaStreamCreateWithPriority(&ctx->faux[j], cudaStreamNonBlocking, greatest) != cudaSuccess) {
     ctx->faux[j] = nullptr;
     return false;
   }

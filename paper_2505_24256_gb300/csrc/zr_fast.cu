@@ -1207,6 +1207,7 @@ constexpr int kPsThreads = 256;
 constexpr int kPsJ = 8;
 constexpr int kPsWin = 8;                     // kPsThreads = kPsWin warps
 constexpr int kPsNodes = kPsThreads * kPsJ;
+constexpr int kPsWaves = 8;
 
 // start[kb T + j] = v_j^(kb kr) (lazily, in [0, 2p)), kb < nkb
 __global__ void k_ps_start(const uint64_t* __restrict__ v, int64_t T, int kr, int nkb, Mod M,
@@ -1291,14 +1292,16 @@ __global__ void k_power_sums_add(const uint64_t* __restrict__ part, int64_t T, i
 }
 
 // The launch shape of k_power_sums: nb node blocks, nkb exponent blocks of kr
-// (a multiple of kPsWin) exponents, about two blocks per SM in all.
+// (a multiple of kPsWin) exponents, about kPsWaves blocks per SM in all (two
+// resident at a time): short blocks, so that the SMs they free go to the
+// tree's clusters beside them.
 struct PsShape {
   int nb, nkb, kr;
 };
 PsShape ps_shape(int64_t T, int sms) {
   PsShape s;
   s.nb = (int)((T + kPsNodes - 1) / kPsNodes);
-  int want = 2 * sms / s.nb;
+  int want = kPsWaves * sms / s.nb;
   if (want < 1) want = 1;
   int64_t kr = (T + want - 1) / want;
   kr = (kr + kPsWin - 1) / kPsWin * kPsWin;
@@ -1670,7 +1673,7 @@ struct FastWs {
 constexpr int64_t kDirectPsMaxT = 12288;
 // k_power_sums is shaped for at most this many SMs (its starting powers'
 // workspace grows with the count)
-constexpr int kPsSmsMax = 256;
+constexpr int kPsSmsMax = 192;
 
 FastWs carve_fast(Carver& cv, int64_t T, int R) {
   FastWs w;
@@ -2031,8 +2034,9 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
   configure_fused();
   // The right-hand sides' descent needs only the tree; the power sums' row
   // needs the power sums.  Up to kDirectPsMaxT unknowns they come from the
-  // nodes alone: with an auxiliary stream k_power_sums runs there beside the
-  // tree, and one descent takes all S + 1 rows.  Above, they need the tree's
+  // nodes alone: with an auxiliary stream (of the greatest priority) the tree
+  // runs there and k_power_sums on st beside it, and one descent takes all
+  // S + 1 rows.  Above, they need the tree's
   // root: with an auxiliary stream they and their row's descent run there,
   // beside the other rows' descent (each branch in its own rows of X and of
   // the scratch), joined at the leaves.  (With the context's profiler on,
@@ -2047,14 +2051,16 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
       cudaStreamWaitEvent(sa, ev_fork, 0);
     }
     const PsShape ps = ps_shape(T, ctx->sms < kPsSmsMax ? ctx->sms : kPsSmsMax);
-    launch_k(k_ps_start, cdivu(T, 256), 256, 0, sa, v, T, ps.kr, ps.nkb, M, w.pss);
-    launch_k(k_power_sums, dim3((unsigned)ps.nkb, (unsigned)ps.nb), kPsThreads, 0, sa, v, vp, T, ps.kr,
+    launch_k(k_ps_start, cdivu(T, 256), 256, 0, st, v, T, ps.kr, ps.nkb, M, w.pss);
+    launch_k(k_power_sums, dim3((unsigned)ps.nkb, (unsigned)ps.nb), kPsThreads, 0, st, v, vp, T, ps.kr,
              (const uint64_t*)w.pss, M, w.psp);
-    launch_k(k_power_sums_add, cdivu(T, 256), 256, 0, sa, (const uint64_t*)w.psp, T, ps.nb, M, w.ps);
+    launch_k(k_power_sums_add, cdivu(T, 256), 256, 0, st, (const uint64_t*)w.psp, T, ps.nb, M, w.ps);
     note_launches(3);
+    Fa.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
     if (fork) cudaEventRecord(ev_join, sa);
+  } else {
+    F.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
   }
-  F.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
   const uint64_t* m = w.coef[Lt];   // M without its leading 1
   // descent from the root (node size T') to the leaf blocks of nr rows from
   // row r0: every branch swaps X0 and X1 once per level
