@@ -447,20 +447,21 @@ def probe_gen_entry(ms, S, T, G, peaks, method):
 
 
 # the profiler phases timing the fast path's transform kernels, their kernels
-FAST_KERNELS = (("desc", "k_desc_cluster"), ("ntt", "k_ntt_local"))
+FAST_KERNELS = (("desc", "k_desc_cluster"), ("ntt", "k_ntt_local"), ("psum", "k_power_sums"))
 
 
 def fast_roofline(ctx, peaks, workload_name, steps, step_ms):
-    """Roofline entry of the O(T log^2 T) solve's dominant transform kernel:
-    of the descent's cluster level kernel k_desc_cluster and the transform
-    tile kernel k_ntt_local, the one with the larger time in the timed steps.
-    Its radix-2 butterflies per launch (n/2 per stage of each transform it
-    runs, counted by the library's profiler) over its average launch time
-    (CUDA events around each launch on the launching stream, this run),
-    against the measured rate of the same butterfly with its operands in
-    registers (zr_measure_peaks, this run).  The other kernel's figures are
+    """Roofline entry of the O(T log^2 T) solve's dominant kernel: of the
+    descent's cluster level kernel k_desc_cluster, the transform tile kernel
+    k_ntt_local and the direct power sums kernel k_power_sums, the one with the
+    largest time in the profiled steps (each launch timed alone).  Its work
+    per launch (radix-2 butterflies, n/2 per stage of each transform it runs,
+    or the power sums' T^2 Shoup steps, counted by the library's profiler)
+    over its average launch time (CUDA events around each launch on the
+    launching stream, this run), against the measured rate of the same
+    operation with its operands in registers (zr_measure_peaks, this run):
+    the butterfly, or the Shoup chain step.  The other kernels' figures are
     given beside it."""
-    peak = peaks["butterfly_per_s"]
     entries = []
     for phase, kernel in FAST_KERNELS:
         ms, n = ctx.profile_query(phase)
@@ -468,22 +469,33 @@ def fast_roofline(ctx, peaks, workload_name, steps, step_ms):
         if n <= 0 or ms <= 0:
             continue
         achieved = work / (ms * 1e-3)
+        if phase == "psum":
+            peak = peaks["chain_per_s"]
+            ops = (f"Shoup steps v_j^k -> v_j^(k+1), T^2 per launch: {work / n:.4g} per launch on average, "
+                   f"{n / max(steps, 1):.0f} launches per step")
+            basis = ("measured (zr_measure_peaks on this GPU, this run): Shoup chain steps (mulhi64 + two "
+                     f"mullo64), operands in registers, {peak / 1e9:.0f} G/s")
+        else:
+            peak = peaks["butterfly_per_s"]
+            ops = (f"radix-2 butterflies, n/2 per stage of each transform: {work / n:.4g} per launch on average, "
+                   f"{n / max(steps, 1):.0f} launches per step")
+            basis = ("measured (zr_measure_peaks on this GPU, this run): forward butterflies on 32-bit "
+                     f"residues with a Shoup twiddle, operands in registers, {peak / 1e9:.0f} G/s")
         entries.append((ms, {
             "bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
             "frac": achieved / peak,
             "traffic": kernel_traffic(kernel, workload_name, NTT_SOURCES), "traffic_unit": "bytes/launch",
-            "kernel": kernel,
-            "ops": f"radix-2 butterflies, n/2 per stage of each transform: {work / n:.4g} per launch on average, "
-                   f"{n / max(steps, 1):.0f} launches per step",
+            "kernel": kernel, "ops": ops,
             "launch_ms": ms / n, "share_of_step": ms / max(steps, 1) / step_ms,
-            "peak_basis": "measured (zr_measure_peaks on this GPU, this run): forward butterflies on 32-bit "
-                          f"residues with a Shoup twiddle, operands in registers, {peak / 1e9:.0f} G/s"}))
+            "peak_basis": basis}))
     if not entries:
         return None
     entries.sort(key=lambda x: -x[0])
     main = dict(entries[0][1])
     if len(entries) > 1:
         main["next_kernel"] = entries[1][1]
+    if len(entries) > 2:
+        main["third_kernel"] = entries[2][1]
     return main
 
 

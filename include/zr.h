@@ -75,16 +75,17 @@ size_t zr_workspace_bytes(const zr_ctx* ctx);
  * synthetic-division/dot kernel, 5 denominators + inverses + Newton,
  * 6 compaction, 7 probe evaluation, 8 the O(T log^2 T) solve of the systems
  * that take it: tree, power sums, descent and leaves; 9 each launch of that
- * solve's transform tile kernel and 10 each launch of its descent's cluster
- * level kernel, both inside phase 8); zr_profile_enable resets the totals,
- * zr_profile_query waits for the recorded events and returns the summed
- * milliseconds and the number of timed occurrences of a phase, and
- * zr_profile_work the algorithmic work recorded with them (phases 9 and 10:
- * radix-2 butterflies, n/2 per stage of each transform of n words; 0 for the
- * others).  While the profiler is on, the O(T log^2 T) solve runs its power
- * sums on the call's stream instead of beside the right-hand sides' descent,
- * so that each timed launch has the GPU to itself.  Errors:
- * ZR_ERR_INVALID_ARG for a phase outside 0..10 or a null pointer. */
+ * solve's transform tile kernel, 10 each launch of its descent's cluster
+ * level kernel and 11 each launch of its direct power sums kernel, all inside
+ * phase 8); zr_profile_enable resets the totals, zr_profile_query waits for
+ * the recorded events and returns the summed milliseconds and the number of
+ * timed occurrences of a phase, and zr_profile_work the algorithmic work
+ * recorded with them (phases 9 and 10: radix-2 butterflies, n/2 per stage of
+ * each transform of n words; 11: the T^2 Shoup steps v_j^k -> v_j^(k+1); 0
+ * for the others).  While the profiler is on, the O(T log^2 T) solve runs
+ * everything on the call's stream (no auxiliary branch beside it), so that
+ * each timed launch has the GPU to itself.  Errors: ZR_ERR_INVALID_ARG for a
+ * phase outside 0..11 or a null pointer. */
 uint64_t zr_launch_count(void);
 zr_status zr_profile_enable(zr_ctx* ctx, int32_t on);
 zr_status zr_profile_query(zr_ctx* ctx, int32_t phase, double* total_ms, int64_t* count);

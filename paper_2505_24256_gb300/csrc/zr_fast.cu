@@ -2052,8 +2052,11 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     }
     const PsShape ps = ps_shape(T, ctx->sms < kPsSmsMax ? ctx->sms : kPsSmsMax);
     launch_k(k_ps_start, cdivu(T, 256), 256, 0, st, v, T, ps.kr, ps.nkb, M, w.pss);
+    cudaEvent_t pa = prof_mark(ctx, st);
     launch_k(k_power_sums, dim3((unsigned)ps.nkb, (unsigned)ps.nb), kPsThreads, 0, st, v, vp, T, ps.kr,
              (const uint64_t*)w.pss, M, w.psp);
+    cudaEvent_t pb = prof_mark(ctx, st);
+    prof_add(ctx, PH_PSUM, pa, pb, (double)T * (double)T);
     launch_k(k_power_sums_add, cdivu(T, 256), 256, 0, st, (const uint64_t*)w.psp, T, ps.nb, M, w.ps);
     note_launches(3);
     Fa.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);

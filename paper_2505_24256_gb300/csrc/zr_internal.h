@@ -15,10 +15,11 @@
 // the call's stream around each phase).
 // PH_NTT times each launch of the transform tile kernel, PH_DESC each launch
 // of the descent's cluster level kernel, inside PH_FAST; both count their
-// butterflies as the phase's work.
+// butterflies as the phase's work.  PH_PSUM times each launch of the direct
+// power sums kernel, its T^2 Shoup steps the work.
 enum zr_phase {
   PH_ANCHOR = 0, PH_MASTER, PH_EXPAND, PH_CARRY, PH_SOLVE, PH_NEWTON, PH_COMPACT, PH_EVAL, PH_FAST, PH_NTT, PH_DESC,
-  PH_N
+  PH_PSUM, PH_N
 };
 
 struct zr_prof {

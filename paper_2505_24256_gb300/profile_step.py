@@ -80,13 +80,15 @@ def main():
     torch.cuda.synchronize()
     got = oc[:n].cpu().numpy().view(np.uint64)
     ok = n == wl.exps.shape[0] and np.array_equal(got, wl.coef)
-    phases = {ph: ctx.profile_query(ph)[0] / args.steps for ph in zr.Context.PHASES[:7] + ("fast", "ntt", "desc")}
+    phases = {ph: ctx.profile_query(ph)[0] / args.steps for ph in zr.Context.PHASES[:7] + ("fast", "ntt", "desc", "psum")}
     ntt_ms, ntt_n = ctx.profile_query("ntt")
     line = {"workload": wl.name, "steps": args.steps, "method": args.method, "plan": ctx.step_plan(wl.T, wl.S),
             "phase_ms": phases,
             "ntt": {"launches": ntt_n, "ms": ntt_ms, "butterflies": ctx.profile_work("ntt")},
             "desc": {"launches": ctx.profile_query("desc")[1], "ms": ctx.profile_query("desc")[0],
                      "butterflies": ctx.profile_work("desc")},
+            "psum": {"launches": ctx.profile_query("psum")[1], "ms": ctx.profile_query("psum")[0],
+                     "shoup_steps": ctx.profile_work("psum")},
             "probe_ms": probe_ms, "check": "generator truth" if ok else "MISMATCH"}
     if not ok:
         line["terms"] = [int(n), int(wl.exps.shape[0])]

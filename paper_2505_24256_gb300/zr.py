@@ -239,7 +239,7 @@ class Context:
     def workspace_bytes(self) -> int:
         return int(self.L.zr_workspace_bytes(self._h))
 
-    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval", "fast", "ntt", "desc")
+    PHASES = ("anchor", "master", "expand", "carry", "solve", "newton", "compact", "eval", "fast", "ntt", "desc", "psum")
     SOLVE_AUTO, SOLVE_QUADRATIC, SOLVE_FAST = 0, 1, 2
 
     def solve_method(self, method, crossover=0):

@@ -252,9 +252,11 @@ def test_profiler_counts_the_descent_butterflies(ctx):
         ctx.vandermonde_solve([dict(T=T, S=S, offset=0, v=d64(v), b=d64(b), ldb=T, c=c, ldc=T)])
         work = ctx.profile_work("desc")
         launches = ctx.profile_query("desc")[1]
+        ps_launches, ps_work = ctx.profile_query("psum")[1], ctx.profile_work("psum")
         ctx.profile(False)
     finally:
         ctx.solve_method(0)
     want = sum(-(-T // (1 << l)) * (S + 1) * 5 * 3 * (1 << (l - 1)) * l for l in (8, 9, 10))
     assert launches == 3                   # three levels, all S + 1 rows in one descent (direct power sums)
     assert work == want
+    assert ps_launches == 1 and ps_work == T * T   # the direct power sums: T^2 Shoup steps
