@@ -1064,6 +1064,15 @@ __global__ void __launch_bounds__(kClusterThreadsMax) k_desc_cluster(const uint6
   int64_t d = T - P * n;
   d = d < 0 ? 0 : (d > n ? n : d);
   const uint64_t* x = X + (int64_t)r * Tp + P * n;
+  if (d <= h) {
+    // the right child holds no roots (R = 1): the left child's expansion is
+    // the node's, X_L[m] = X_P[m], at the same offset; the five CTAs copy a
+    // fifth each and leave together (no cluster barrier on this branch)
+    const int per = (int)((d + kNP - 1) / kNP);
+    const int lo = me * per, hi = (int)(d < (int64_t)lo + per ? d : (int64_t)lo + per);
+    for (int o = lo + threadIdx.x; o < hi; o += blockDim.x) Xn[(int64_t)r * Tp + P * n + o] = x[o];
+    return;
+  }
   for (int k = threadIdx.x; k < n; k += blockDim.x) fsm[sw(k)] = k < d ? residue64(x[d - 1 - k], C, me) : 0u;
   __syncthreads();
   smem_stages<false>(fsm, 0, n, logn, 0, 0u, tw, logN, C, prime);
@@ -2082,8 +2091,10 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
                               T, Tp, logn, C, crt_scale(logn), M, tw, logN, w.spec[l - 1], Xn, nodes) == cudaSuccess;
         if (!done) (void)cudaGetLastError();
         cudaEvent_t b2 = prof_mark(ctx, s);
-        // one forward and two inverse transforms of 2^logn per prime of each cluster
-        if (done) prof_add(ctx, PH_DESC, a, b2, (double)(nodes * nr) * kNP * 3 * (double)((1ll << logn) / 2) * logn);
+        // one forward and two inverse transforms of 2^logn per prime of each
+        // cluster, but for a last node whose right child holds no roots (copied)
+        const int64_t tx = nodes - ((T - (nodes - 1) * (1ll << logn)) <= (1ll << (logn - 1)) ? 1 : 0);
+        if (done) prof_add(ctx, PH_DESC, a, b2, (double)(tx * nr) * kNP * 3 * (double)((1ll << logn) / 2) * logn);
       }
       if (!done && logn <= kFusedLog) {
         const int npc = fused_npc(logn);

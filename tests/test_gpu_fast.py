@@ -237,12 +237,16 @@ def test_fast_probes_fall_back_above_64_samples(ctx, orc):
     assert np.array_equal(h64(b), orc.zippel_probes(wl.exps, wl.coef, wl.k, wl.y, wl.cs, wl.z, wl.T))
 
 
-def test_profiler_counts_the_descent_butterflies(ctx):
+@pytest.mark.parametrize("T,levels", [(1000, (8, 9, 10)), (1100, (8, 9, 10, 11))])
+def test_profiler_counts_the_descent_butterflies(ctx, orc, T, levels):
     """The profiler's work count for the descent's cluster levels is the
     formula the bench's roofline uses: for each level of transform size
-    n = 2^l (l = 8 .. 10 at T = 1000), ceil(T / n) nodes x (S + 1) rows x
-    5 primes x 3 transforms x (n / 2) log2 n butterflies."""
-    T, S = 1000, 2
+    n = 2^l, the nodes with roots in both children x (S + 1) rows x 5 primes
+    x 3 transforms x (n / 2) log2 n butterflies.  At T = 1000 every level's
+    nodes qualify (ceil(T / n) of them); at T = 1100 the last node of the
+    levels 2^8 .. 2^10 has its 76 roots in its left child and is copied
+    without a transform, and the solution is still the oracle's."""
+    S = 2
     rnd = random.Random(21)
     v, b = rand_nodes(rnd, T, P63), rand_res(rnd, (S, T), P63)
     c = zeros64(S, T)
@@ -256,7 +260,14 @@ def test_profiler_counts_the_descent_butterflies(ctx):
         ctx.profile(False)
     finally:
         ctx.solve_method(0)
-    want = sum(-(-T // (1 << l)) * (S + 1) * 5 * 3 * (1 << (l - 1)) * l for l in (8, 9, 10))
-    assert launches == 3                   # three levels, all S + 1 rows in one descent (direct power sums)
+
+    def transformed(l):
+        n = 1 << l
+        nodes = -(-T // n)
+        return nodes - (1 if T - (nodes - 1) * n <= n // 2 else 0)
+
+    want = sum(transformed(l) * (S + 1) * 5 * 3 * (1 << (l - 1)) * l for l in levels)
+    assert launches == len(levels)         # one launch a level, all S + 1 rows in one descent (direct power sums)
     assert work == want
     assert ps_launches == 1 and ps_work == T * T   # the direct power sums: T^2 Shoup steps
+    assert np.array_equal(h64(c), orc.tvandermonde_solve(v, b, offset=0))
