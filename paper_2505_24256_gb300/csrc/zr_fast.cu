@@ -1023,6 +1023,7 @@ __global__ void __launch_bounds__(kClusterThreadsMax) k_tree_cluster(const uint6
     sp[n + k] = y;
     fsm[sw(k)] = mont32(sub_if(x, 2 * q), sub_if(y, 2 * q), q, qi);
   }
+  if (coef == nullptr) return;                   // the children's spectra only (every CTA alike)
   __syncthreads();
   smem_stages<true>(fsm, 0, n, logn, 0, 0u, tw + ((size_t)kNP << logN), logN, C, prime);
   cluster_sync();
@@ -1724,9 +1725,11 @@ struct FastRun {
   cudaStream_t st;
   // subproduct tree over the T roots v: coef[l] (levels 7 .. 7 + Lt, T' =
   // 128 2^Lt words each) and the children's spectra spec[l - 1] (kNP 2T'
-  // words each); Z: kNP T' words of scratch
+  // words each); Z: kNP T' words of scratch.  Without `root` the top level
+  // may stop at its children's spectra (coef[Lt], M itself, left unwritten
+  // when that level runs on a cluster).
   void tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::vector<uint64_t*>& coef,
-            const std::vector<uint32_t*>& spec, uint32_t* Z);
+            const std::vector<uint32_t*>& spec, uint32_t* Z, bool root = true);
   // g = 1 / f mod z^prec (f_0 = 1, nf coefficients): Newton's iteration, the
   // first steps in one CTA; g holds 2 prec words, e prec words, A, B, Z
   // kNP 2^ceil(log2(2 prec)) words each
@@ -1838,7 +1841,7 @@ void configure_fused() {
 }
 
 void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::vector<uint64_t*>& coef,
-                   const std::vector<uint32_t*>& spec, uint32_t* Z) {
+                   const std::vector<uint32_t*>& spec, uint32_t* Z, bool root) {
   const int logT = kLeafLog + Lt;
   launch_k(k_fast_leafpoly, cdivu(T, kLeaf), kLeaf, 0, st, v, T, M, coef[0]);
   note_launch();
@@ -1849,7 +1852,7 @@ void FastRun::tree(const uint64_t* v, int64_t T, int64_t Tp, int Lt, const std::
     if (cluster_level(ctx, logn, nodes)) {
       const cudaError_t e = launch_cluster(k_tree_cluster, nodes, cluster_threads(logn), sizeof(uint32_t) * 2 << logn,
                                            st, coef[l - 1], T, Tp, logn, C, crt_scale(logn), M, tw, logN, sp,
-                                           coef[l]);
+                                           (l == Lt && !root) ? (uint64_t*)nullptr : coef[l]);
       if (e == cudaSuccess) continue;
       (void)cudaGetLastError();
     }
@@ -2068,12 +2071,12 @@ zr_status fast_solve_enqueue(zr_ctx* ctx, int64_t T, int S, const uint64_t* v, c
     prof_add(ctx, PH_PSUM, pa, pb, (double)T * (double)T);
     launch_k(k_power_sums_add, cdivu(T, 256), 256, 0, st, (const uint64_t*)w.psp, T, ps.nb, M, w.ps);
     note_launches(3);
-    Fa.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
+    Fa.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z, false);   // M itself is not needed: the descent takes its children
     if (fork) cudaEventRecord(ev_join, sa);
   } else {
     F.tree(v, T, Tp, Lt, w.coef, w.spec, w.Z);
   }
-  const uint64_t* m = w.coef[Lt];   // M without its leading 1
+  const uint64_t* m = w.coef[Lt];   // M without its leading 1 (written on the Newton path only)
   // descent from the root (node size T') to the leaf blocks of nr rows from
   // row r0: every branch swaps X0 and X1 once per level
   auto descend = [&](int r0, int nr, cudaStream_t s) {
