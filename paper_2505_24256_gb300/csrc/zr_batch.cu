@@ -22,6 +22,7 @@
 
 #include "zr_device.cuh"
 #include "zr_internal.h"
+#include "zr_launch.cuh"
 
 namespace zr {
 
@@ -30,6 +31,7 @@ static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1
 // ---- a2 ---------------------------------------------------------------------
 
 __global__ void k_b_fill_hash(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre, int n) {
+  pdl_enter();
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= pre[n]) return;
   const int i = seg_of(pre, n, x);
@@ -37,12 +39,14 @@ __global__ void k_b_fill_hash(const BDesc* __restrict__ Ds, const int64_t* __res
 }
 
 __global__ void k_b_powtab(const BDesc* __restrict__ Ds, Mod M) {
+  pdl_enter();
   const BDesc& D = Ds[blockIdx.y];
   const int m = blockIdx.x, e = threadIdx.x;
   if (D.mode == 0 && m < D.k) D.tab[m * kPowTab + e] = pow_mod(D.y[m], (uint64_t)e, M);
 }
 
 __global__ void k_b_anchor(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre, int n, Mod M) {
+  pdl_enter();
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= pre[n]) return;
   const int i = seg_of(pre, n, x);
@@ -231,6 +235,7 @@ __device__ __forceinline__ uint64_t root_den(const BDesc& D, int64_t j, uint64_t
 // W of every step entry (one block each): the values -> monomial map of Newton
 // interpolation on the entry's S samples.
 __global__ void __launch_bounds__(kNewtonThreads) k_b_newton_table(const BDesc* __restrict__ Ds, Mod M) {
+  pdl_enter();
   extern __shared__ uint64_t tsm[];
   const BDesc& D = Ds[blockIdx.x];
   if (D.mode != 0 || D.T == 0) return;
@@ -246,6 +251,7 @@ __global__ void __launch_bounds__(kNewtonThreads) k_b_newton_table(const BDesc* 
 __global__ void __launch_bounds__(kFinB * kFinSplit) k_b_finish_newton(const BDesc* __restrict__ Ds,
                                                                       const int64_t* __restrict__ pre_blk, int n,
                                                                       Mod M) {
+  pdl_enter();
   extern __shared__ uint64_t fsm[];
   __shared__ uint64_t sh_inv[kFinB];
   __shared__ int sh_cnt[kFinSplit][kFinB];
@@ -302,6 +308,7 @@ __global__ void __launch_bounds__(kFinB * kFinSplit) k_b_finish_newton(const BDe
 
 __global__ void __launch_bounds__(256) k_b_finish_solve(const BDesc* __restrict__ Ds, const int64_t* __restrict__ pre,
                                                         int n, Mod M) {
+  pdl_enter();
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = x < pre[n];
   const int i = active ? seg_of(pre, n, x) : 0;
@@ -335,6 +342,7 @@ constexpr int kCompB = kFinB;  // terms per compaction block (the finish kernel'
 
 // Exclusive offsets of the blocks' nonzero counts, one CTA per entry.
 __global__ void __launch_bounds__(kScanB) k_b_scan(const BDesc* __restrict__ Ds) {
+  pdl_enter();
   __shared__ int64_t sh[33];
   const BDesc& D = Ds[blockIdx.x];
   if (D.mode != 0) return;
@@ -357,6 +365,7 @@ __global__ void __launch_bounds__(kScanB) k_b_scan(const BDesc* __restrict__ Ds)
 // consecutive outputs.
 __global__ void __launch_bounds__(kCompB * kFinSplit) k_b_scatter(const BDesc* __restrict__ Ds,
                                                                   const int64_t* __restrict__ pre_blk, int n) {
+  pdl_enter();
   __shared__ int64_t sh[33];
   __shared__ int32_t offs[kCompB];
   __shared__ uint64_t masks[kCompB];
@@ -709,7 +718,7 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
       configure_newton_kernels();
       cudaEventRecord(ctx->ev_fork, st);
       cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-      k_b_newton_table<<<n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), ctx->side>>>(dD, M);
+      launch_k(k_b_newton_table, n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), ctx->side, dD, M);
       note_launch();
       cudaEventRecord(ctx->ev_join, ctx->side);
       side = true;
@@ -717,9 +726,11 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
   }
   cudaEvent_t e0 = mark();
   // a2
-  if (nhash) { k_b_fill_hash<<<cdiv(nhash, 256), 256, 0, st>>>(dD, dpre + o_hash, n); note_launch(); }
-  if (mode == 0 && kmax > 0) { k_b_powtab<<<dim3(kmax, n), kPowTab, 0, st>>>(dD, M); note_launch(); }
-  if (nroots) { k_b_anchor<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+  // the step's own kernels are programmatic dependent launches too (each
+  // starts with pdl_enter), like the O(T log^2 T) path's
+  if (nhash) { launch_k(k_b_fill_hash, cdiv(nhash, 256), 256, 0, st, dD, dpre + o_hash, n); note_launch(); }
+  if (mode == 0 && kmax > 0) { launch_k(k_b_powtab, dim3(kmax, n), kPowTab, 0, st, dD, M); note_launch(); }
+  if (nroots) { launch_k(k_b_anchor, cdiv(nroots, 256), 256, 0, st, dD, dpre + o_roots, n, M); note_launch(); }
   cudaEvent_t e1 = mark();
   // the O(T log^2 T) entries need only the anchor values: with several of
   // them, or beside O(T^2) entries, they start here on their own streams
@@ -806,24 +817,24 @@ static zr_status launch_batch(zr_ctx* ctx, const StagedBatch& SB, cudaStream_t s
       configure_newton_kernels();
       if (side) cudaStreamWaitEvent(st, ctx->ev_join, 0);   // W of every entry (forked above)
       else {
-        k_b_newton_table<<<n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), st>>>(dD, M);
+        launch_k(k_b_newton_table, n, kNewtonThreads, 8 * (size_t)newton_table_words(smax), st, dD, M);
         note_launch();
       }
       const int64_t nblk = pre[o_nblk + n];
       {
-        k_b_finish_newton<<<(unsigned)nblk, kFinB * kFinSplit, newton_smem(smax, kFinB), st>>>(dD, dpre + o_nblk, n,
-                                                                                                 M);
+        launch_k(k_b_finish_newton, (unsigned)nblk, kFinB * kFinSplit, newton_smem(smax, kFinB), st, dD,
+                 dpre + o_nblk, n, M);
         note_launch();
       }
     } else {
-      { k_b_finish_solve<<<cdiv(nroots, 256), 256, 0, st>>>(dD, dpre + o_roots, n, M); note_launch(); }
+      { launch_k(k_b_finish_solve, cdiv(nroots, 256), 256, 0, st, dD, dpre + o_roots, n, M); note_launch(); }
     }
   }
   cudaEvent_t e5 = mark();
   if (mode == 0 && nroots) {
-    { k_b_scan<<<n, kScanB, 0, st>>>(dD); note_launch(); }
+    { launch_k(k_b_scan, n, kScanB, 0, st, dD); note_launch(); }
     {
-      k_b_scatter<<<(unsigned)pre[o_nblk + n], kCompB * kFinSplit, 0, st>>>(dD, dpre + o_nblk, n);
+      launch_k(k_b_scatter, (unsigned)pre[o_nblk + n], kCompB * kFinSplit, 0, st, dD, dpre + o_nblk, n);
       note_launch();
     }
   }

@@ -34,6 +34,7 @@
 
 #include "zr_device.cuh"
 #include "zr_internal.h"
+#include "zr_launch.cuh"
 #include "zr_ntt.cuh"
 
 namespace zr {
@@ -41,29 +42,8 @@ namespace zr {
 namespace {
 
 inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
-// Launches in this file are programmatic dependent launches: a kernel may
-// become resident while the one before it on the stream drains.  Every
-// kernel here first waits (griddepcontrol.wait: until its predecessors have
-// completed and their memory is visible), then lets its own dependents start
-// launching (they run once all of its CTAs have started).
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-template <class... P, class... A>
-cudaError_t launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
-}
+// Launches in this file are programmatic dependent launches (launch_k, every
+// kernel starting with pdl_enter: zr_launch.cuh).
 
 inline int ilog2(int64_t x) {
   int l = 0;
