@@ -725,7 +725,7 @@ def run_zr(args):
         "probe_gen": probe_gen_entry(probe_ms, S, T, T, peaks, probe_method),
         "e2e": {"value": job_rate(T, world, e2e_s), "unit": "terms/s",
                 "h2d_bytes_per_step": T * nv + 8 * k + 8 * S + 8 * S * T,
-                "d2h_bytes_per_step": ne * (nv + 8) + 12},
+                "d2h_bytes_per_step": min(cap, T * S) * (nv + 8) + 12},
         "gpu_launches": int(launches),
         "clocks": clk,
         "check": "generator truth" if (ok and e2e_ok and (large is None or large["check"] == "generator truth")

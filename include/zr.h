@@ -334,7 +334,10 @@ void zr_step_graph_destroy(zr_step_graph* graph);
 
 /* The same step with every array in HOST memory (pinned or pageable): the
  * call copies the inputs in, runs the step on `stream` and copies the new
- * skeleton out.  out_exps / out_coef are host buffers of out_cap terms. */
+ * skeleton out.  out_exps / out_coef are host buffers of out_cap terms; the
+ * call copies min(T S, out_cap) terms out in one transfer together with the
+ * count, so the entries past *out_count are left unspecified (also when the
+ * call returns an error). */
 zr_status zr_zippel_step_host(zr_ctx* ctx, const zr_poly* skel, int32_t newvar, const uint64_t* y, int32_t S,
                               const uint64_t* samples, const uint64_t* probes, int64_t ldb, int32_t offset,
                               uint8_t* out_exps, uint64_t* out_coef, int64_t out_cap, int64_t* out_count,

@@ -793,17 +793,21 @@ extern "C" zr_status zr_zippel_step_host(zr_ctx* ctx, const zr_poly* skel, int32
     it = step_item(&dsk, newvar, d_y, S, d_s, d_b, T, offset, d_oe, d_oc, cap, ctx->d_count);
     if ((r = run_batch(ctx, &it, 1, ctx->d_status_call, st, io))) return r;
   }
+  // one transfer out and one synchronisation: the output's whole capacity
+  // (min(T S, out_cap) terms; entries past the count are left unspecified)
+  // goes out with the status and the count, instead of a second round trip
+  // once the count is known
+  const int64_t ncopy = cap < out_cap ? cap : out_cap;
+  if (ncopy > 0) {
+    e = cudaMemcpyAsync(out_exps, d_oe, (size_t)ncopy * nv, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_coef, d_oc, sizeof(uint64_t) * ncopy, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_step_host: copy out");
+  }
   int64_t n = 0;
   r = finish_sync_call(ctx, st, &n);
   if (out_count) *out_count = n;
   if (r) return r;
   if (n > out_cap) return set_err(ctx, ZR_ERR_CAPACITY, "output skeleton larger than out_cap");
-  if (n > 0) {
-    e = cudaMemcpyAsync(out_exps, d_oe, (size_t)n * nv, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_coef, d_oc, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "zr_zippel_step_host: copy out");
-  }
   return ZR_OK;
 }
 

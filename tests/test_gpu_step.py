@@ -136,6 +136,17 @@ def test_step_host_buffers(ctx, orc):
                              np.ascontiguousarray(b), wl.T, 0, oe, oc, cap)
     assert n == wl.exps.shape[0]
     assert np.array_equal(oe[:n], wl.exps) and np.array_equal(oc[:n], wl.coef)
+    # buffers of n terms and a sentinel: the one transfer out copies
+    # min(T S, out_cap) terms, so nothing is written past out_cap
+    oe2 = np.zeros((n + 1, wl.nv), dtype=np.uint8)
+    oc2 = np.zeros(n + 1, dtype=np.uint64)
+    oe2[n] = 77
+    oc2[n] = 12345
+    n2 = ctx.zippel_step_host(skel, wl.k, np.ascontiguousarray(wl.y), wl.S, np.ascontiguousarray(wl.cs),
+                              np.ascontiguousarray(b), wl.T, 0, oe2, oc2, n)
+    assert n2 == n
+    assert np.array_equal(oe2[:n], wl.exps) and np.array_equal(oc2[:n], wl.coef)
+    assert (oe2[n] == 77).all() and oc2[n] == 12345
 
 
 def probes_at_points(orc, wl, sidx, iidx, offset=0):
