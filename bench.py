@@ -867,7 +867,7 @@ def large_step_bench(ctx, dev, flush, peaks, steps, warmup):
         "solve": "O(T log^2 T) (subproduct tree, transforms over five 30-bit primes)",
         "ms_per_step": ms, "terms_per_s": T / (ms / 1e3),
         "fast_solve_ms": fast_ms / max(fast_n, 1),
-        "fast_solve_note": "from the profiled pass (the power sums then run on the call's stream)",
+        "fast_solve_note": "from the profiled pass (the whole solve then runs on the call's stream)",
         "roofline": fast_roof,
         "phase_ms": phases,
         "quadratic_form": {"ms_per_step": quad_ms, "terms_per_s": T / (quad_ms / 1e3),

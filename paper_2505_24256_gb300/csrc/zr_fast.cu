@@ -22,8 +22,11 @@
 //            N(v_j) directly (the quadratic method on 128 roots).
 //   denominators   M'(v_j) is the same evaluation with N = M', whose
 //            expansion M'/M = sum_k (sum_j v_j^k) z^(-k-1) holds the power
-//            sums of the nodes: rev(M') / rev(M) mod z^T, by Newton's
-//            iteration for the power-series inverse.
+//            sums of the nodes: summed directly (T^2 Shoup steps beside the
+//            tree, up to kDirectPsMaxT unknowns; their row then joins the
+//            right-hand sides' descent), else rev(M') / rev(M) mod z^T by
+//            Newton's iteration for the power-series inverse (with a final
+//            division step in one cluster up to 2^14).
 //
 // The results are the unique solution, bit-identical to the quadratic path.
 #include <cuda_runtime.h>
